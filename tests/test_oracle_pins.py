@@ -1,0 +1,620 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test ties one part of the oracle to a library routine, a published
+known answer, a closed form, an invariant of the method or a statistical
+expectation, chosen so that a dropped term, a wrong sign or index, or a
+transposed operand in that part fails here.
+"""
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2412_04634_gb300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lambert_record(n=(0.0, 0.0, 1.0), albedo=(0.25, 0.5, 0.75), material=scenes.MAT_LAMBERT,
+                    roughness=1.0, wo=None, p=(0.5, 0.5, 0.5)):
+    rec = np.zeros(1, scenes.RECORD_DTYPE)
+    n = np.asarray(n, np.float64)
+    n = n / np.linalg.norm(n)
+    rec["p"] = p
+    rec["n"] = n
+    rec["wo"] = n if wo is None else wo
+    rec["albedo"] = albedo
+    rec["roughness"] = roughness
+    rec["flags"] = 1 | (material << 1)
+    return rec
+
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10
+# ---------------------------------------------------------------------------
+
+def test_philox_known_answer(oracle):
+    for line in open(os.path.join(GOLDEN, "philox4x32_10.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = oracle.philox(w[0:4], w[4:6])
+        assert list(out) == w[6:10]
+
+
+_TRITON_SCRIPT = r"""
+import os, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+data = np.load(sys.argv[1])
+ctr, key = data["ctr"], data["key"]
+@triton.jit
+def k(out, c0p, c1p, c2p, c3p, seed, N: tl.constexpr):
+    i = tl.arange(0, N)
+    a, b, c, d = tl.philox(seed, tl.load(c0p + i), tl.load(c1p + i), tl.load(c2p + i), tl.load(c3p + i))
+    tl.store(out + i * 4 + 0, a); tl.store(out + i * 4 + 1, b)
+    tl.store(out + i * 4 + 2, c); tl.store(out + i * 4 + 3, d)
+res = []
+for j in range(key.shape[0]):
+    seed = int(key[j, 0]) | (int(key[j, 1]) << 32)
+    o = torch.zeros(4 * 16, dtype=torch.uint32)
+    cs = [torch.from_numpy(ctr[j * 16:(j + 1) * 16, q].copy()) for q in range(4)]
+    k[(1,)](o, cs[0], cs[1], cs[2], cs[3], seed, N=16)
+    res.append(o.numpy().reshape(16, 4))
+np.save(sys.argv[2], np.concatenate(res))
+"""
+
+
+def test_philox_matches_library(oracle, tmp_path):
+    """Triton's Philox4x32-10 (run on the CPU by its interpreter) is an
+    independent implementation of the same published generator."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(11)
+    nkeys = 4
+    ctr = rng.integers(0, 2**32, (nkeys * 16, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:16] = 0
+    ctr[1, 0] = 1
+    ctr[2, 3] = 0xFFFFFFFF
+    key = rng.integers(0, 2**32, (nkeys, 2), dtype=np.uint64).astype(np.uint32)
+    key[0] = 0
+    inp = tmp_path / "in.npz"
+    outp = tmp_path / "out.npy"
+    np.savez(inp, ctr=ctr, key=key)
+    script = tmp_path / "tri.py"
+    script.write_text(_TRITON_SCRIPT)
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, str(script), str(inp), str(outp)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    ref = np.load(outp)
+    for j in range(ctr.shape[0]):
+        got = oracle.philox(ctr[j], key[j // 16])
+        assert list(got) == list(ref[j]), (j, ctr[j], key[j // 16])
+
+
+def test_u01_exact_values(oracle):
+    assert oracle.u01(0) == 0.0
+    assert oracle.u01(0xFF) == 0.0
+    assert oracle.u01(0x80000000) == 0.5
+    assert oracle.u01(0xFFFFFFFF) == 1.0 - 2.0**-24
+    assert oracle.u01(0x00000100) == 2.0**-24
+
+
+# ---------------------------------------------------------------------------
+# Geometry: closed-form intersections
+# ---------------------------------------------------------------------------
+
+def _custom_scene():
+    prims = np.zeros(3, scenes.PRIM_DTYPE)
+    scenes._fill_sphere(prims[0], (0.0, 0.0, 5.0), 1.0, (0.5,) * 3, 1.0, scenes.MAT_LAMBERT)
+    # rectangle in the plane z = 10 spanning x, y in [-2, 2]
+    scenes._fill_rect(prims[1], (-2.0, -2.0, 10.0), (4.0, 0.0, 0.0), (0.0, 4.0, 0.0), (0.5,) * 3, 1.0,
+                      scenes.MAT_LAMBERT)
+    # rectangle in the plane x = 3 spanning y in [0, 1], z in [0, 2]
+    scenes._fill_rect(prims[2], (3.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 2.0), (0.5,) * 3, 1.0,
+                      scenes.MAT_LAMBERT)
+    cam = scenes._camera((0, 0, 0), 40.0, 4, 4)
+    return scenes.Scene(scenes._header(3, cam), prims, 4, 4).blob()
+
+
+def test_intersections_closed_form(oracle):
+    blob = _custom_scene()
+    # towards the sphere centre: first hit at |c - o| - r = 4
+    prim, t = oracle.trace(blob, (0, 0, 0), (0, 0, 1))
+    assert prim == 0 and t == 4.0
+    # from inside the sphere: exit at t = r = 1
+    prim, t = oracle.trace(blob, (0, 0, 5), (0, 0, 1))
+    assert prim == 0 and t == 1.0
+    # past the sphere (offset 1.5 > r) onto the z = 10 rectangle
+    prim, t = oracle.trace(blob, (1.5, 0, 0), (0, 0, 1))
+    assert prim == 1 and t == 10.0
+    # towards the x = 3 rectangle: t = 3; outside its y extent it misses
+    prim, t = oracle.trace(blob, (0, 0.5, 1.0), (1, 0, 0))
+    assert prim == 2 and t == 3.0
+    prim, _ = oracle.trace(blob, (0, 1.5, 1.0), (1, 0, 0))
+    assert prim == -1
+    # grazing the sphere tangentially at distance exactly r still hits (disc = 0)
+    prim, t = oracle.trace(blob, (1.0, 0, 0), (0, 0, 1))
+    assert prim == 0 and t == 5.0
+    # behind the origin (t < 0) is not a hit
+    prim, _ = oracle.trace(blob, (0, 0, 11), (0, 0, 1))
+    assert prim == -1
+
+
+def test_onb_orthonormal(oracle):
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        n = rng.normal(size=3)
+        n = (n / np.linalg.norm(n)).astype(np.float32)
+        t, b = oracle.onb(n)
+        m = np.stack([t, b, n]).astype(np.float64)
+        assert np.allclose(m @ m.T, np.eye(3), atol=2e-6)
+        assert np.allclose(np.cross(t, b), n, atol=2e-6)  # right-handed
+
+
+# ---------------------------------------------------------------------------
+# BSDF sampling
+# ---------------------------------------------------------------------------
+
+def test_cosine_sampling_statistics(oracle):
+    """Cosine-weighted hemisphere: E[cos] = 2/3, E[cos^2] = 1/2, azimuth
+    uniform; rejection from the square accepts with probability pi/4; the
+    Lambertian weight f cos / p is exactly the albedo."""
+    n_dir = np.array([0.3, -0.5, 0.8])
+    rec = _lambert_record(n=n_dir)
+    nn = rec["n"][0].astype(np.float64)
+    t, b = oracle.onb(rec["n"][0])
+    K = 20000
+    cos = np.empty(K)
+    az = np.empty((K, 2))
+    rej = np.empty(K)
+    for i in range(K):
+        wi, w, valid, r, lobe = oracle.sample_bsdf(rec, (1, 0), (i, 3, 2))
+        assert valid and lobe == 0
+        assert np.all(w == np.array([0.25, 0.5, 0.75], np.float32).astype(np.float64))
+        assert abs(np.linalg.norm(wi.astype(np.float64)) - 1.0) < 1e-6
+        cos[i] = wi @ nn
+        az[i] = (wi @ t, wi @ b)
+        rej[i] = r
+    se = 4.0 / math.sqrt(K)
+    assert abs(cos.mean() - 2.0 / 3.0) < se * cos.std()
+    assert abs((cos ** 2).mean() - 0.5) < se * (cos ** 2).std()
+    assert abs(az[:, 0].mean()) < se * az[:, 0].std()
+    assert abs(az[:, 1].mean()) < se * az[:, 1].std()
+    # number of rejections before acceptance is geometric with p = pi/4
+    p = math.pi / 4
+    mean_rej = (1 - p) / p
+    assert abs(rej.mean() - mean_rej) < se * math.sqrt((1 - p) / p ** 2)
+
+
+def _ggx_brdf(n, wo, wi, albedo, rough):
+    """Lambertian + GGX microfacet BRDF (Walter et al. 2007, Smith
+    height-correlated masking, Schlick Fresnel F0 = 0.04), vectorised over wi."""
+    a = float(np.float32(rough) * np.float32(rough))
+    a2 = a * a
+    ci = wi @ n
+    co = wo @ n
+    h = wi + wo[None, :]
+    h /= np.linalg.norm(h, axis=1, keepdims=True)
+    ch = h @ n
+    oh = np.clip(h @ wo, 0.0, 1.0)
+    D = a2 / (math.pi * (ch * ch * (a2 - 1) + 1) ** 2)
+    li = np.sqrt(a2 + (1 - a2) * ci * ci)
+    lo = math.sqrt(a2 + (1 - a2) * co * co)
+    G2 = 2 * ci * co / (co * li + ci * lo)
+    F = 0.04 + 0.96 * (1 - oh) ** 5
+    return np.asarray(albedo)[None, :] / math.pi + (F * D * G2 / (4 * ci * co))[:, None]
+
+
+@pytest.mark.parametrize("rough,theta_o", [(0.7, 0.4), (0.35, 1.0), (1.0, 1.3)])
+def test_ggx_mixture_weights_integrate_to_albedo(oracle, rough, theta_o):
+    """E[f cos / p] under the sampler equals the directional albedo
+    int f cos dw computed by deterministic quadrature of the BRDF alone, so a
+    sampler whose density differs from its stated pdf fails."""
+    n = np.array([0.0, 0.0, 1.0])
+    wo = np.array([math.sin(theta_o), 0.0, math.cos(theta_o)], np.float32)
+    albedo = (0.3, 0.5, 0.7)
+    rec = _lambert_record(n=n, albedo=albedo, material=scenes.MAT_GGX, roughness=rough, wo=wo)
+    K = 12000
+    ws = np.zeros((K, 3))
+    lobes = 0
+    for i in range(K):
+        wi, w, valid, r, lobe = oracle.sample_bsdf(rec, (3, 1), (i, 0, 2))
+        lobes += lobe
+        if valid:
+            assert wi @ n > 0
+            ws[i] = w
+    assert abs(lobes / K - 0.5) < 4 * 0.5 / math.sqrt(K)
+    # quadrature over the hemisphere in (cos theta, phi)
+    nt, nph = 400, 400
+    u = (np.arange(nt) + 0.5) / nt
+    ct = 1.0 - u ** 2  # concentrate nodes near the grazing / specular region
+    dct = 2.0 * u / nt
+    ph = (np.arange(nph) + 0.5) / nph * 2 * math.pi
+    C, PH = np.meshgrid(ct, ph, indexing="ij")
+    st = np.sqrt(1 - C ** 2)
+    wi = np.stack([st * np.cos(PH), st * np.sin(PH), C], -1).reshape(-1, 3)
+    dA = (np.broadcast_to(dct[:, None], C.shape) * (2 * math.pi / nph)).reshape(-1)
+    f = _ggx_brdf(n, wo.astype(np.float64), wi, albedo, rough)
+    integral = (f * wi[:, 2:3] * dA[:, None]).sum(0)
+    mean = ws.mean(0)
+    se = ws.std(0) / math.sqrt(K)
+    assert np.all(np.abs(mean - integral) < 4 * se + 2e-3 * integral), (mean, integral, se)
+
+
+def test_black_material_never_scatters(oracle):
+    rec = _lambert_record(material=scenes.MAT_BLACK)
+    wi, w, valid, r, lobe = oracle.sample_bsdf(rec, (1, 0), (0, 0, 2))
+    assert not valid and np.all(w == 0)
+
+
+# ---------------------------------------------------------------------------
+# Encodings and hash grid
+# ---------------------------------------------------------------------------
+
+def test_frequency_encoding_closed_form(oracle):
+    cfg = scenes.config_small()
+    params = scenes.init_params(cfg, 1)
+    rec = _lambert_record(n=(0.0, 0.0, 1.0), p=(0.0, 0.5, 1.0))
+    # w = +y: theta_hat = 1/2, phi_hat = 1/4
+    e = oracle.encode(cfg, params, rec, np.array([0.0, 1.0, 0.0], np.float32)).reshape(8, 4, 2)
+    def enc(v):
+        return np.array([[math.sin(math.pi * v * 2 ** k), math.cos(math.pi * v * 2 ** k)] for k in range(4)])
+    exact = {0.0: [[0, 1]] * 4, 0.5: [[1, 0], [0, -1], [0, 1], [0, 1]], 1.0: [[0, -1], [0, 1], [0, 1], [0, 1]],
+             0.25: [[math.sqrt(0.5), math.sqrt(0.5)], [1, 0], [0, -1], [0, 1]]}
+    dims = [0.0, 0.5, 1.0, 0.5, 0.25, 0.0, 0.0, 1.0]  # x0 x1 x2 theta phi n0 n1 n2
+    for d, v in enumerate(dims):
+        assert np.allclose(e[d], exact[v], atol=1e-12), (d, v, e[d])
+        assert np.allclose(e[d], enc(v), atol=1e-12)
+    # w = -y: phi_hat = 3/4 (atan2 wrapped into [0, 1)); w = +z: theta_hat = 0
+    e2 = oracle.encode(cfg, params, rec, np.array([0.0, -1.0, 0.0], np.float32)).reshape(8, 4, 2)
+    assert np.allclose(e2[4, 0], [math.sin(0.75 * math.pi), math.cos(0.75 * math.pi)], atol=1e-12)
+    e3 = oracle.encode(cfg, params, rec, np.array([0.0, 0.0, 1.0], np.float32)).reshape(8, 4, 2)
+    assert np.allclose(e3[3], [[0, 1]] * 4, atol=1e-12)
+
+
+def test_hash_indices_hand_computed(oracle):
+    cfg = scenes.config_1080p()
+    for line in open(os.path.join(GOLDEN, "hash_indices.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        level, x, corner, index = int(f[0]), [float(v) for v in f[1:4]], int(f[4]), int(f[5])
+        idx, w = oracle.hash_level(cfg, level, np.array(x, np.float32))
+        assert idx[corner] == index, (level, x, corner, idx)
+
+
+def test_grid_resolutions(oracle):
+    """floor(16 * 1.5^l): the published level resolutions for these settings."""
+    cfg = scenes.config_1080p()
+    expect = [16, 24, 36, 54, 81, 121, 182, 273, 410, 615, 922, 1383, 2075, 3113, 4670, 7006]
+    for l, r in enumerate(expect):
+        # at x = 1 the cell is clamped to res - 1 with fraction 1: corner 7 is vertex (res, res, res)
+        idx, w = oracle.hash_level(cfg, l, np.array([1.0, 1.0, 1.0], np.float32))
+        assert w[7] == 1.0
+        if (r + 1) ** 3 <= 2 ** 19:
+            assert idx[7] == r + r * (r + 1) + r * (r + 1) ** 2
+
+
+def test_trilinear_partition_of_unity_and_affine_reproduction(oracle):
+    """Trilinear weights sum to one, and interpolating a table that is an
+    affine function of the vertex coordinates reproduces that function at
+    x * res exactly (dense levels)."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=2, log2_table=12,
+                           base_res=6, growth=1.5)
+    T = 1 << cfg.log2_table
+    params = np.zeros(cfg.n_params, np.float64)
+    hash_off = cfg.n_mlp_params
+    # level 0: res 6, dense with side 7; feature 0 = 2i - 3j + 5k + 1, feature 1 = j
+    side = 7
+    for idx in range(side ** 3):
+        i, j, k = idx % side, (idx // side) % side, idx // side ** 2
+        params[hash_off + 2 * idx] = 2 * i - 3 * j + 5 * k + 1
+        params[hash_off + 2 * idx + 1] = j
+    rng = np.random.default_rng(4)
+    for _ in range(100):
+        x = rng.uniform(0, 1, 3).astype(np.float32)
+        idx, w = oracle.hash_level(cfg, 0, x)
+        assert abs(w.sum() - 1.0) < 1e-12
+        idx1, w1 = oracle.hash_level(cfg, 1, x)
+        assert abs(w1.sum() - 1.0) < 1e-12
+        rec = _lambert_record(p=x)
+        e = oracle.encode(cfg, params, rec, np.array([0, 0, 1], np.float32))
+        ps = (x * np.float32(6)).astype(np.float64)
+        assert abs(e[0] - (2 * ps[0] - 3 * ps[1] + 5 * ps[2] + 1)) < 1e-9
+        assert abs(e[1] - ps[1]) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Network
+# ---------------------------------------------------------------------------
+
+def _torch_mlp(cfg, params):
+    torch = pytest.importorskip("torch")
+    layers = []
+    off = 0
+    shapes = cfg.layer_shapes()
+    for li, (o, i) in enumerate(shapes):
+        lin = torch.nn.Linear(i, o, dtype=torch.float64)
+        with torch.no_grad():
+            lin.weight.copy_(torch.from_numpy(params[off:off + o * i].reshape(o, i).astype(np.float64)))
+            lin.bias.copy_(torch.from_numpy(params[off + o * i:off + o * i + o].astype(np.float64)))
+        off += o * i + o
+        layers.append(lin)
+        if li + 1 < len(shapes):
+            layers.append(torch.nn.ReLU())
+    return torch.nn.Sequential(*layers)
+
+
+@pytest.mark.parametrize("which", ["small", "1080p"])
+def test_mlp_matches_library(oracle, which):
+    torch = pytest.importorskip("torch")
+    cfg = scenes.config_small() if which == "small" else scenes.NetConfig(
+        pos_encoding=scenes.POS_HASHGRID, hidden_layers=4, log2_table=10)
+    rng = np.random.default_rng(5)
+    params = scenes.init_params(cfg, 2).astype(np.float64)
+    params[:cfg.n_mlp_params] += rng.normal(0, 0.05, cfg.n_mlp_params)  # nonzero biases
+    net = _torch_mlp(cfg, params)
+    for _ in range(20):
+        e = rng.normal(size=cfg.n_inputs)
+        z = oracle.mlp(cfg, params, e)
+        zt = net(torch.from_numpy(e)).detach().numpy()
+        assert np.allclose(z, zt, rtol=1e-12, atol=1e-12)
+
+
+def test_constant_network_outputs_constant(oracle):
+    cfg = scenes.config_small()
+    L = np.array([0.7, 1.3, 2.9])
+    params = scenes.constant_cache_params(cfg, L)
+    recs, dirs = scenes.random_query_rows(50)
+    out = oracle.query(cfg, params, recs, dirs)
+    assert np.allclose(out, np.exp(np.log(L).astype(np.float32).astype(np.float64)), rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Two-level estimator
+# ---------------------------------------------------------------------------
+
+def test_white_furnace_cache_level_exact(oracle):
+    """Constant incident radiance L on Lambertian surfaces: every cache
+    sample gives f cos / p * L = rho L, so L_c = rho L exactly per pixel."""
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(64, 64, seed=1)
+    L = (1.5, 2.0, 3.0)
+    fd = oracle.oframe(64, 64, 8, 1, 4, 0, 1, cache_mode=2, cache_const=L)
+    r = oracle.estimate(cfg, None, sc.blob(), fd)
+    # the albedo of the hit primitive, per pixel: recover it through a
+    # constant cache of 1 (L_c = rho exactly)
+    fd1 = oracle.oframe(64, 64, 8, 1, 4, 0, 1, cache_mode=2, cache_const=(1.0, 1.0, 1.0))
+    r1 = oracle.estimate(cfg, None, sc.blob(), fd1)
+    albedos = sc.prims["albedo"].astype(np.float64)
+    hit = r["count"] > 0
+    assert hit.mean() > 0.9
+    full = r["count"] == 9  # every cache and residual sample above the surface
+    assert full.sum() >= 0.99 * hit.sum()
+    for px in np.nonzero(full)[0]:
+        rho = r1["lc"][px]
+        assert any(np.array_equal(rho, a) for a in albedos), rho
+        assert np.allclose(r["lc"][px], rho * np.array(L), rtol=1e-15, atol=0)
+    # via network weights as well: n = exp(ln L) to rounding
+    params = scenes.constant_cache_params(cfg, L)
+    fdn = oracle.oframe(64, 64, 8, 1, 4, 0, 1)
+    rn = oracle.estimate(cfg, params, sc.blob(), fdn)
+    assert np.allclose(rn["lc"], r["lc"], rtol=1e-6, atol=0)
+
+
+def test_furnace_path_expectation(oracle):
+    """Camera inside an emitting Lambertian sphere (L_e, rho): with a zero
+    cache the pixel estimates L_e sum_{k=0}^{D} rho^k (D path segments after
+    the camera hit), Russian roulette included."""
+    rho, Le, D = 0.6, 1.0, 5
+    sc = scenes.furnace_scene(128, 128, rho=rho, emission=Le)
+    cfg = scenes.config_small()
+    vals = []
+    for frame in range(4):
+        fd = oracle.oframe(128, 128, 0, 2, D, frame, 9, cache_mode=1)
+        vals.append(oracle.estimate(cfg, None, sc.blob(), fd)["pixel"][:, 0])
+    v = np.concatenate(vals)
+    expect = Le * sum(rho ** k for k in range(D + 1))
+    se = v.std() / math.sqrt(v.size)
+    assert abs(v.mean() - expect) < 4 * se, (v.mean(), expect, se)
+    # and the depth cap matters: D = 1 gives L_e (1 + rho) exactly (no RR before the first segment)
+    fd = oracle.oframe(16, 16, 0, 1, 1, 0, 9, cache_mode=1)
+    v1 = oracle.estimate(cfg, None, scenes.furnace_scene(16, 16, rho=rho, emission=Le).blob(), fd)["pixel"]
+    assert np.allclose(v1, Le * (1 + np.float32(rho)), rtol=1e-7)
+
+
+def test_zero_cache_is_plain_path_tracing(oracle):
+    """n = 0: the cache level vanishes and the residual level is the plain
+    BSDF-sampled path tracer; adding cache samples does not perturb it."""
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(32, 32, seed=3)
+    a = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(32, 32, 8, 2, 4, 1, 5, cache_mode=1))
+    b = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(32, 32, 0, 2, 4, 1, 5, cache_mode=1))
+    assert np.all(a["lc"] == 0)
+    assert np.array_equal(a["pixel"], b["pixel"])
+    assert np.array_equal(a["sig"][:, 0], b["sig"][:, 0])
+    # pixel = L_e + L_r with L_e either 0 or the emitter's 10
+    le = a["pixel"] - a["lr"]
+    assert np.all((np.abs(le) < 1e-12) | (np.abs(le - 10.0) < 1e-12))
+
+
+def test_analytic_cache_residual_has_zero_mean(oracle):
+    """Furnace with the exact incident radiance L_e / (1 - rho) in the cache
+    and no effective depth cap: E[L_r] = 0 and L_c = rho L_i exactly."""
+    rho, Le = 0.5, 1.0
+    Li = Le / (1 - rho)
+    sc = scenes.furnace_scene(128, 128, rho=rho, emission=Le)
+    cfg = scenes.config_small()
+    fd = oracle.oframe(128, 128, 4, 1, 64, 0, 3, cache_mode=2, cache_const=(Li,) * 3)
+    r = oracle.estimate(cfg, None, sc.blob(), fd)
+    assert np.allclose(r["lc"], np.float32(rho) * Li, rtol=1e-15)
+    lr = r["lr"][:, 0]
+    se = lr.std() / math.sqrt(lr.size)
+    assert abs(lr.mean()) < 4 * se, (lr.mean(), se)
+    px = r["pixel"][:, 0]
+    assert abs(px.mean() - Li) < 4 * px.std() / math.sqrt(px.size)
+
+
+def test_two_level_estimator_is_unbiased(oracle):
+    """For any cache (random weights here), the two-level estimate and plain
+    path tracing on the same residual streams differ by
+    L_c - (1/M) sum_j w_j n_j, which has zero mean.  A wrong sign or
+    normalisation of either level fails."""
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(48, 48, seed=1)
+    params = scenes.init_params(cfg, 4)
+    diffs = []
+    lcs = []
+    for frame in range(12):
+        tl = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(48, 48, 4, 1, 4, frame, 2))
+        pt = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(48, 48, 0, 1, 4, frame, 2, cache_mode=1))
+        diffs.append((tl["pixel"] - pt["pixel"]).ravel())
+        lcs.append(tl["lc"].ravel())
+    d = np.concatenate(diffs).reshape(-1, 3).mean(1)
+    se = d.std() / math.sqrt(d.size)
+    assert abs(d.mean()) < 4 * se, (d.mean(), se)
+    assert np.concatenate(lcs).mean() > 20 * se  # the cache level is far from negligible
+
+
+def test_estimator_counts_and_signatures_deterministic(oracle):
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(16, 16, seed=1)
+    params = scenes.init_params(cfg, 1)
+    fd = oracle.oframe(16, 16, 8, 1, 4, 2, 1)
+    a = oracle.estimate(cfg, params, sc.blob(), fd)
+    b = oracle.estimate(cfg, params, sc.blob(), fd, pixels=np.arange(256)[::-1].copy())
+    assert np.array_equal(a["sig"][::-1], b["sig"])
+    assert np.array_equal(a["pixel"][::-1], b["pixel"])
+    assert set(np.unique(a["count"])) <= set(range(10))
+
+
+# ---------------------------------------------------------------------------
+# Training records, loss, gradients, Adam
+# ---------------------------------------------------------------------------
+
+def test_training_records_furnace(oracle):
+    """Training targets estimate L_i(x, w) = L_e sum_{k<D} rho^k in the furnace."""
+    rho, Le, D = 0.5, 1.0, 4
+    sc = scenes.furnace_scene(64, 64, rho=rho, emission=Le)
+    T = 20000
+    recs, dirs, tg, sig = oracle.gen_train(sc.blob(), 64, 64, T, 0, 1, D, scenes.RECORD_DTYPE)
+    assert np.all(recs["flags"] & 1)
+    assert np.allclose(np.linalg.norm(dirs, axis=1), 1, atol=1e-6)
+    assert np.all(np.einsum("ij,ij->i", dirs, recs["n"]) > 0)
+    expect = Le * sum(rho ** k for k in range(D))
+    se = tg[:, 0].std() / math.sqrt(T)
+    assert abs(tg[:, 0].mean() - expect) < 4 * se
+    # pixel picks are uniform over the image: the hit points spread over the
+    # whole visible part of the sphere, so the wo directions span the field of view
+    wo = recs["wo"]
+    assert wo[:, 0].min() < -0.3 and wo[:, 0].max() > 0.3
+
+
+def _fd_check(oracle, cfg, params, recs, dirs, tg, idx, h=1e-6, tol=2e-5):
+    """Central differences of the loss with the stop-gradient denominator
+    sg(n)^2 + eps frozen at the current network output: that function's
+    derivative is the training gradient of eq. 12."""
+    n0 = oracle.query(cfg, params, recs, dirs)
+    den = n0 * n0 + cfg.loss_eps
+    loss, g = oracle.loss_grad(cfg, params, recs, dirs, tg)
+    loss_f, g_f = oracle.loss_grad(cfg, params, recs, dirs, tg, den_fixed=den)
+    assert loss_f == loss and np.array_equal(g, g_f)
+    for i in idx:
+        pp = params.copy()
+        step = h * max(1.0, abs(pp[i]))
+        pp[i] += step
+        lp, _ = oracle.loss_grad(cfg, pp, recs, dirs, tg, den_fixed=den)
+        pp[i] -= 2 * step
+        lm, _ = oracle.loss_grad(cfg, pp, recs, dirs, tg, den_fixed=den)
+        fd = (lp - lm) / (2 * step)
+        scale = max(abs(fd), abs(g[i]), 1e-3 * np.abs(g).max())
+        assert abs(fd - g[i]) <= tol * scale, (i, fd, g[i])
+    return g
+
+
+def test_gradients_match_finite_differences_freq(oracle):
+    cfg = scenes.config_small()
+    params = scenes.init_params(cfg, 3).astype(np.float64)
+    params[:cfg.n_mlp_params] += np.random.default_rng(1).normal(0, 0.02, cfg.n_mlp_params)
+    recs, dirs, tg = scenes.training_batch(64, seed=9)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(cfg.n_mlp_params, 80, replace=False)
+    # include every bias of the output layer and some input-layer weights
+    idx = np.concatenate([idx, np.arange(cfg.n_mlp_params - 3, cfg.n_mlp_params), np.arange(0, 5)])
+    _fd_check(oracle, cfg, params, recs, dirs, tg.astype(np.float64), idx)
+
+
+def test_gradients_match_finite_differences_hashgrid(oracle):
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=6, log2_table=10,
+                           hidden_layers=4, base_res=4, growth=2.0)
+    params = scenes.init_params(cfg, 5).astype(np.float64)
+    rng = np.random.default_rng(2)
+    params[cfg.n_mlp_params:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params)  # features well away from 0
+    recs, dirs, tg = scenes.training_batch(48, seed=10)
+    loss, g = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    touched = np.nonzero(g[cfg.n_mlp_params:])[0] + cfg.n_mlp_params
+    assert touched.size > 100
+    idx = np.concatenate([rng.choice(touched, 60, replace=False), rng.choice(cfg.n_mlp_params, 40, replace=False)])
+    _fd_check(oracle, cfg, params, recs, dirs, tg.astype(np.float64), idx)
+    # untouched table entries get exactly zero gradient
+    untouched = np.setdiff1d(np.arange(cfg.n_mlp_params, cfg.n_params), touched)
+    assert np.all(g[untouched] == 0)
+
+
+def test_loss_closed_form_for_constant_network(oracle):
+    """With a constant network n = c the loss is mean (f - c)^2 / (c^2 + eps)."""
+    cfg = scenes.config_small()
+    c = np.array([0.5, 1.0, 2.0])
+    params = scenes.constant_cache_params(cfg, c).astype(np.float64)
+    cf = np.exp(np.log(c).astype(np.float32).astype(np.float64))
+    recs, dirs, tg = scenes.training_batch(100, seed=4)
+    loss, g = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    expect = np.mean((tg.astype(np.float64) - cf[None, :]) ** 2 / (cf[None, :] ** 2 + 1e-2))
+    assert abs(loss - expect) < 1e-12 * abs(expect)
+    # invalid records are excluded from the numerator, not the normalisation
+    recs2 = recs.copy()
+    recs2["flags"][50:] = 0
+    loss2, _ = oracle.loss_grad(cfg, params, recs2, dirs, tg.astype(np.float64))
+    expect2 = np.sum((tg[:50].astype(np.float64) - cf[None, :]) ** 2 / (cf[None, :] ** 2 + 1e-2)) / 300.0
+    assert abs(loss2 - expect2) < 1e-12 * abs(expect2)
+
+
+def test_adam_closed_form_steps(oracle):
+    """Bias-corrected Adam: with a constant gradient g every step moves a
+    parameter by lr g / (|g| + eps); a zero gradient moves nothing."""
+    n = 1000
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=n) * 10.0 ** rng.uniform(-6, 2, n)
+    g[:10] = 0.0
+    p0 = rng.normal(size=n)
+    p = p0.copy()
+    m = np.zeros(n)
+    v = np.zeros(n)
+    lr, b1, b2, eps = 1e-2, 0.9, 0.99, 1e-15
+    for step in range(1, 6):
+        oracle.adam_step(p, m, v, g, step, lr, b1, b2, eps)
+        expect = p0 - step * lr * g / (np.abs(g) + eps)
+        assert np.allclose(p, expect, rtol=0, atol=1e-12)
+    assert np.all(p[:10] == p0[:10])
+    # a sign flip of the gradient after one step: m_hat = (0.09 - 0.1) g / 0.19,
+    # v_hat = g^2, so the second step moves back by lr * (0.01 / 0.19)
+    p = p0.copy(); m[:] = 0; v[:] = 0
+    oracle.adam_step(p, m, v, g, 1, lr, b1, b2, 0.0)
+    oracle.adam_step(p, m, v, -g, 2, lr, b1, b2, 0.0)
+    nz = g != 0
+    assert np.allclose(p[nz], p0[nz] - lr * np.sign(g[nz]) + lr * (0.01 / 0.19) * np.sign(g[nz]), atol=1e-12)
+
+
+def test_mrse_closed_forms(oracle):
+    rng = np.random.default_rng(1)
+    ref = rng.uniform(1.0, 2.0, (100, 3))
+    assert oracle.mrse(ref, ref) == 0.0
+    img = 2 * ref
+    assert abs(oracle.mrse(img, ref, 1e-2) - np.mean(ref ** 2 / (ref ** 2 + 1e-2))) < 1e-14
+    zero = np.zeros((10, 3))
+    assert abs(oracle.mrse(zero + 0.1, zero, 1e-2) - 1.0) < 1e-12
