@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the NIRC two-level Monte Carlo hot path on one GB300 per rank.
+
+One step = one 1920x1080 frame of the whole path on synthetic input:
+  nirc_estimate_frame  camera hits, N = 16 cache + M = 1 residual BSDF samples
+                       per pixel, residual paths (depth 5, Russian roulette),
+                       cache integral over 35.3 M rows
+  nirc_gen_train       65,536 training paths (separate pass)
+  nirc_train_step      relative-L2 loss, backward, dense Adam over 16.8 M + 17 k
+                       parameters
+  nirc_frame_mrse      FP64 MRSE against a 256-spp path-traced reference
+The scene (256 primitives, moving emitter, GGX materials) is the dynamic
+procedural Cornell family; frames W..W+K-1 are timed after W warm-up frames.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain FP64 implementation in oracle/) on a bounded sample of the same
+workload instead.  Under torchrun every rank runs an independent replica
+(the path shards by frame; there is no cross-GPU exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2412_04634_gb300 import scenes  # noqa: E402
+
+METRIC = "NIRC queries/s & 1080p ms/frame, FP16 TC vs FP32 at equal MRSE; p50/p99"
+WORKLOAD = "1080p dynamic Cornell family (256 prims, GGX), hash-grid NIRC 16x2 T=2^19, MLP 64x4, N=16 M=1 depth 5, 65536 train samples/frame"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32"], default="fp32")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--n-cache", type=int, default=16)
+    ap.add_argument("--n-resid", type=int, default=1)
+    ap.add_argument("--depth", type=int, default=5)
+    ap.add_argument("--train", type=int, default=65536)
+    ap.add_argument("--prims", type=int, default=256)
+    ap.add_argument("--ref-spp", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd[1:1] = ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, maxs, reasons = [], [], set()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < len(self.FIELDS):
+                continue
+            try:
+                sms.append(float(f[0]))
+                maxs.append(float(f[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, f[3:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def build_workload(args, seed_offset=0):
+    W, H = args.width, args.height
+    base = scenes.cornell_scene(W, H, seed=1 + seed_offset, n_prims=args.prims, glossy=True, moving_emitter=True)
+    frames = [scenes.scene_at_frame(base, f) for f in range(60)]
+    cfg = scenes.config_1080p()
+    params = scenes.init_params(cfg, 1 + seed_offset)
+    return cfg, params, frames
+
+
+def rows_per_frame(args):
+    return args.width * args.height * (args.n_cache + args.n_resid)
+
+
+def flops_per_frame(cfg, args):
+    """Algorithmic FLOPs of the cache integral: per row the direction part of
+    layer 0, the hidden layers and the output layer; per pixel the shared
+    per-surface part of layer 0."""
+    per_row = 2 * (16 * 64 + (cfg.hidden_layers - 1) * 64 * 64 + 64 * 3)
+    n_pix_features = cfg.n_pos_features + 24
+    per_pixel = 2 * n_pix_features * 64
+    return rows_per_frame(args) * per_row + args.width * args.height * per_pixel, per_row, per_pixel
+
+
+def fp32_alu_peak_tflops(num_sms, sm_mhz):
+    # 128 FP32 FMA lanes per SM, 2 FLOP per FMA
+    return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2412_04634_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2412_04634_gb300 import nirc as N
+
+    cfg, params, frames = build_workload(args, seed_offset=rank)
+    W, H = args.width, args.height
+    P = W * H
+    S = args.n_cache + args.n_resid
+    precision = N.NIRC_FP32_SIMT
+    cache = N.Cache(cfg, precision)
+    cache.set_params(params)
+    scene_dev = [N.scene_to_tensor(f, dev) for f in frames]
+    n_prims = frames[0].n_prims
+    stream = torch.cuda.current_stream(dev)
+
+    img = torch.empty((P, 4), device=dev)
+    ref = torch.zeros((P, 4), device=dev)
+    tmp = torch.empty((P, 4), device=dev)
+    T = args.train
+    recs = torch.empty((T, 16), device=dev)
+    dirs = torch.empty((T, 3), device=dev)
+    tgts = torch.empty((T, 3), device=dev)
+    loss = torch.zeros(1, device=dev)
+    mrse = torch.zeros(1, dtype=torch.float64, device=dev)
+    seed = 1 + rank
+    first_timed = args.warmup
+    last_frame = (first_timed + args.steps - 1) % 60
+
+    # reference image of the last timed frame: plain path tracing (zero cache)
+    spp_per = 16
+    n_ref = max(1, args.ref_spp // spp_per)
+    for k in range(n_ref):
+        d = N.frame_desc(W, H, 0, spp_per, 16, 1000 + k, seed, n_prims, cache_mode=1)
+        N.nirc_estimate_frame(cache.h, scene_dev[last_frame], d, tmp)
+        ref += tmp
+    ref /= n_ref
+    torch.cuda.synchronize(dev)
+
+    def step(f):
+        fi = f % 60
+        d = N.frame_desc(W, H, args.n_cache, args.n_resid, args.depth, f, seed, n_prims)
+        N.nirc_estimate_frame(cache.h, scene_dev[fi], d, img)
+        N.nirc_gen_train(cache.h, scene_dev[fi], n_prims, W, H, T, f, seed, args.depth, recs, dirs, tgts)
+        N.nirc_train_step(cache.h, recs, dirs, tgts, loss)
+        N.nirc_frame_mrse(img, ref, mrse)
+
+    for f in range(args.warmup):
+        step(f)
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(props.uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    time.sleep(0.3)
+    N.nirc_timing_enable(cache.h, True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    evs[0].record(stream)
+    for k in range(args.steps):
+        step(first_timed + k)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    timing = N.nirc_timing_read(cache.h)
+    N.nirc_timing_enable(cache.h, False)
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    final_mrse = float(mrse.item())
+
+    # end to end through the public API with host buffers: pinned scene blob
+    # in, image + MRSE + loss out, every step
+    e2e = None
+    if not args.no_e2e:
+        host_scenes = [torch.from_numpy(f.blob()).pin_memory() for f in frames]
+        host_img = torch.empty((P, 4), pin_memory=True)
+        host_small = torch.empty(2, dtype=torch.float64, pin_memory=True)
+        dev_scene = torch.empty_like(scene_dev[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for k in range(args.steps):
+            f = first_timed + k
+            dev_scene.copy_(host_scenes[f % 60], non_blocking=True)
+            d = N.frame_desc(W, H, args.n_cache, args.n_resid, args.depth, f, seed, n_prims)
+            N.nirc_estimate_frame(cache.h, dev_scene, d, img)
+            N.nirc_gen_train(cache.h, dev_scene, n_prims, W, H, T, f, seed, args.depth, recs, dirs, tgts)
+            N.nirc_train_step(cache.h, recs, dirs, tgts, loss)
+            N.nirc_frame_mrse(img, ref, mrse)
+            host_img.copy_(img, non_blocking=True)
+            host_small[0:1].copy_(mrse, non_blocking=True)
+            host_small[1:2].copy_(loss.double(), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": world * rows_per_frame(args) * args.steps / (e2e_ms / 1e3), "unit": "queries/s",
+               "h2d_bytes_per_step": int(frames[0].blob().nbytes),
+               "d2h_bytes_per_step": int(P * 16 + 8 + 4)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    ms_per_step = total_ms / args.steps
+    value = world * rows_per_frame(args) * args.steps / (total_ms / 1e3)
+    kernel_ms = {k: (v[0] / max(1, v[1]), v[1]) for k, v in timing.items() if v[1]}
+    dominant = max(kernel_ms, key=lambda k: timing[k][0])
+    fl_frame, per_row, per_pixel = flops_per_frame(cfg, args)
+    launches = sum(v[1] for v in timing.values()) + args.steps  # + one MRSE launch per step
+    sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    roofline = None
+    if dominant == "cache":
+        avg_ms = kernel_ms["cache"][0]
+        achieved = fl_frame / (avg_ms / 1e3) / 1e12
+        peak = fp32_alu_peak_tflops(props.multi_processor_count, sm_max)
+        roofline = {"kernel": "k_cache_simt", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": f"FP32 FMA: {props.multi_processor_count} SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz",
+                    "algorithmic": f"{per_row} FLOP/row x {rows_per_frame(args)} rows + {per_pixel} FLOP/pixel x {P} pixels"}
+    else:
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(args, budget_s=args.cpu_budget_s)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": W, "height": H, "n_cache": args.n_cache, "n_resid": args.n_resid,
+                   "max_depth": args.depth, "prims": n_prims, "train_samples": T, "precision": "fp32_simt",
+                   "frames": f"{first_timed}..{first_timed + args.steps - 1} (mod 60)",
+                   "l2": "no flush: per-frame working set (~0.5 GB of records, rows, images, tables) > 129 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+        "frame_mrse": final_mrse, "mrse_reference": f"{n_ref * spp_per} spp path tracing, depth 16",
+        "kernel_ms": {k: round(v[0], 4) for k, v in kernel_ms.items()},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: cpu_baseline leg and the reference arm
+# ---------------------------------------------------------------------------
+
+def oracle_step(O, cfg, params64, m, v, blob, args, frame, pix, T_s, seed):
+    """One bounded sample of the frame step on the oracle: the listed pixels'
+    two-level estimates, T_s training paths, loss + gradient, Adam, MRSE."""
+    W, H = args.width, args.height
+    fd = O.oframe(W, H, args.n_cache, args.n_resid, args.depth, frame, seed)
+    est = O.estimate(cfg, params64, blob, fd, pixels=pix)
+    recs, dirs, tg, _ = O.gen_train(blob, W, H, T_s, frame, seed, args.depth, scenes.RECORD_DTYPE)
+    loss, g = O.loss_grad(cfg, params64, recs, dirs, tg)
+    O.adam_step(params64, m, v, g, 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps)
+    O.mrse(est["pixel"], est["pixel"])
+    return est
+
+
+def _oracle_setup(args):
+    from oracle import oracle as O
+    cfg, params, frames = build_workload(args)
+    p64 = params.astype(np.float64)
+    return O, cfg, p64, np.zeros_like(p64), np.zeros_like(p64), frames
+
+
+def _calibrate(O, cfg, p64, m, v, frames, args, budget_s):
+    P = args.width * args.height
+    rng = np.random.default_rng(0)
+    n = 1024
+    while True:
+        pix = np.sort(rng.choice(P, n, replace=False)).astype(np.uint32)
+        T_s = max(1, int(round(args.train * n / P)))
+        t0 = time.perf_counter()
+        oracle_step(O, cfg, p64, m, v, frames[10].blob(), args, 10, pix, T_s, 1)
+        dt = time.perf_counter() - t0
+        if dt >= 0.25 * budget_s or n >= P:
+            return n, dt
+        n = min(P, int(n * max(2.0, 0.5 * budget_s / max(dt, 1e-3))))
+
+
+def cpu_baseline(args, budget_s):
+    O, cfg, p64, m, v, frames = _oracle_setup(args)
+    S = args.n_cache + args.n_resid
+    n, _ = _calibrate(O, cfg, p64, m, v, frames, args, budget_s)
+    P = args.width * args.height
+    n = min(P, int(n * 2))
+    rng = np.random.default_rng(1)
+    pix = np.sort(rng.choice(P, n, replace=False)).astype(np.uint32)
+    T_s = max(1, int(round(args.train * n / P)))
+    t0 = time.perf_counter()
+    oracle_step(O, cfg, p64, m, v, frames[11].blob(), args, 11, pix, T_s, 1)
+    dt = time.perf_counter() - t0
+    return {"value": n * S / dt, "unit": "queries/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{n} random pixels of frame 11 ({n * S} queries) + {T_s} training paths "
+                      f"(same fraction of 65536), loss/grad, dense FP64 Adam over all "
+                      f"{cfg.n_params} parameters, MRSE; {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    O, cfg, p64, m, v, frames = _oracle_setup(args)
+    S = args.n_cache + args.n_resid
+    per_step_budget = max(0.5, 150.0 / (args.steps + args.warmup))
+    n, dt = _calibrate(O, cfg, p64, m, v, frames, args, per_step_budget * 4)
+    n = max(64, int(n * per_step_budget / max(dt, 1e-3)))
+    P = args.width * args.height
+    n = min(P, n)
+    rng = np.random.default_rng(2)
+    T_s = max(1, int(round(args.train * n / P)))
+    for k in range(args.warmup):
+        pix = np.sort(rng.choice(P, n, replace=False)).astype(np.uint32)
+        oracle_step(O, cfg, p64, m, v, frames[k % 60].blob(), args, k, pix, T_s, 1)
+    times = []
+    for k in range(args.steps):
+        f = args.warmup + k
+        pix = np.sort(rng.choice(P, n, replace=False)).astype(np.uint32)
+        t0 = time.perf_counter()
+        oracle_step(O, cfg, p64, m, v, frames[f % 60].blob(), args, f, pix, T_s, 1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * S * args.steps / total
+    sample = (f"{n} random pixels per step ({n * S} queries) + {T_s} training paths, loss/grad, "
+              f"FP64 Adam over {cfg.n_params} parameters, MRSE")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": args.width, "height": args.height, "n_cache": args.n_cache,
+                   "n_resid": args.n_resid, "max_depth": args.depth, "train_samples": args.train,
+                   "sample_pixels_per_step": n},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * nirc.h -- C ABI of libnirc.so, the GB300 (sm_103a) implementation of the
+ * Neural Incident Radiance Cache (NIRC) two-level Monte Carlo hot path of
+ * "Neural Two-Level Monte Carlo Real-Time Rendering" (arXiv 2412.04634).
+ *
+ * The method (paper section "Neural Incident Radiance Cache"): split the
+ * rendering equation's integral into a cache level and a residual level,
+ *   L_o = L_e + L_c + L_r                                         (eq. L_mlmc)
+ *   L_c = 1/N sum_i n(x, w_i) f_r cos / p(w_i)                    (eq. L_c)
+ *   L_r = 1/M sum_j (L_i(x, w_j) - n(x, w_j)) f_r cos / p(w_j)    (eq. L_r)
+ * where n is a small MLP over encodings of position, incident direction and
+ * surface features (the cache, eq. 11), the two direction sets are drawn
+ * independently by BSDF importance sampling (section "Cache application"),
+ * and the cache is trained on-line with the relative L2 loss (eq. 12) by
+ * Adam on paths from a separate training pass.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are DEVICE memory owned by the caller; the library
+ *    never frees them and keeps no reference after the call returns.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and is stream-ordered; calls return before the GPU finishes.
+ *  - Every call returns a status and never aborts the process.  On error
+ *    nirc_last_error() gives a message (thread-local); a failing call leaves
+ *    the handle's parameters and optimiser state unchanged unless the
+ *    failure is a CUDA error raised by already-enqueued work.
+ *  - Calls on one handle are not re-entrant; separate handles are
+ *    independent.
+ *  - Sizes of 0 are valid no-ops.
+ */
+#ifndef NIRC_H
+#define NIRC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nirc_status {
+    NIRC_OK = 0,
+    NIRC_ERR_INVALID = 1,     /* bad argument (null pointer, size, config) */
+    NIRC_ERR_OOM = 2,         /* device allocation failed */
+    NIRC_ERR_BUDGET = 3,      /* request exceeds a documented size limit */
+    NIRC_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    NIRC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+    NIRC_ERR_UNSUPPORTED = 6  /* configuration not implemented on this path */
+} nirc_status;
+
+/* Arithmetic of the network layers.  FP32_SIMT: plain FP32 FMA kernels.
+ * FP16_TC / BF16_TC: tcgen05 tensor-core MMAs with FP16 / BF16 operands and
+ * FP32 accumulation in tensor memory.  Encodings, sampling, pdfs and the
+ * per-pixel sums are FP32 in every mode. */
+typedef enum nirc_precision {
+    NIRC_FP32_SIMT = 0,
+    NIRC_FP16_TC = 1,
+    NIRC_BF16_TC = 2,
+    NIRC_FP8_E4M3_TC = 3
+} nirc_precision;
+
+typedef enum nirc_pos_encoding {
+    NIRC_POS_FREQ = 0,     /* 4-octave sin/cos of x (the 64x64 workload) */
+    NIRC_POS_HASHGRID = 1  /* multiresolution hash grid of x (paper: section
+                              "Neural Network Architecture", first bullet) */
+} nirc_pos_encoding;
+
+/* Cache hyper-parameters.  Network input, in order: position features
+ * (3 dims x 2 x freq_octaves, or hash_levels x feats_per_level), the
+ * incident direction as (theta/pi, phi/2pi) with 2 x 2 x freq_octaves
+ * features, and the shading normal with 3 x 2 x freq_octaves features.
+ * Frequency features of a scalar v are sin(2^k pi v), cos(2^k pi v).
+ * Hidden layers: `hidden_layers` ReLU layers of `width` (only 64 is
+ * supported), output 3 logits z, cache value n = exp(min(z, z_clamp)). */
+typedef struct nirc_config {
+    uint32_t pos_encoding;     /* nirc_pos_encoding */
+    uint32_t hash_levels;      /* L, e.g. 16 */
+    uint32_t feats_per_level;  /* F, only 2 supported */
+    uint32_t log2_table;       /* T = 2^log2_table entries per level, e.g. 19 */
+    uint32_t base_res;         /* N_min, e.g. 16 */
+    float growth;              /* b: level resolution floor(N_min * b^l) */
+    uint32_t freq_octaves;     /* only 4 supported */
+    uint32_t width;            /* only 64 supported */
+    uint32_t hidden_layers;    /* 1..8 */
+    uint32_t precision;        /* nirc_precision */
+    float lr;                  /* Adam learning rate (paper: 0.01) */
+    float beta1, beta2;        /* Adam moments, e.g. 0.9, 0.99 */
+    float adam_eps;            /* e.g. 1e-15 */
+    float loss_eps;            /* eps of eq. 12, e.g. 0.01 */
+    float z_clamp;             /* e.g. 15 */
+} nirc_config;
+
+/* Shading record: one surface point (paper: "surface parameter buffer",
+ * section "Memory consumption").  64 bytes, 16-byte aligned.
+ * flags bit 0 = valid, bits 1-2 = material (0 Lambertian, 1 Lambertian +
+ * GGX, 2 black/non-scattering).  n is the unit shading normal facing wo. */
+typedef struct nirc_record {
+    float p[3];
+    float n[3];
+    float wo[3];
+    float albedo[3];
+    float roughness;
+    uint32_t prim;
+    uint32_t flags;
+    uint32_t pad;
+} nirc_record;
+
+/* One frame of the two-level estimator.
+ * Scene blob (device): 96-byte header {u32 n_prims, u32 pad[3],
+ * f32 cam_origin[4], f32 cam_top_left[4], f32 cam_horizontal[4],
+ * f32 cam_vertical[4], u32 reserved[4]} followed by n_prims 96-byte
+ * primitives {f32 a[3], radius, u[3], inv_uu, v[3], inv_vv, n[3], u32 kind,
+ * f32 albedo[3], roughness, emission[3], u32 flags}; kind 0 sphere (centre
+ * a), 1 rectangle (corner a, perpendicular edges u, v, unit normal n);
+ * flags bits 0-1 material, bit 8 two-sided emission.  The blob must be
+ * 16-byte aligned and hold at least n_prims primitives. */
+typedef struct nirc_frame_desc {
+    uint32_t width, height;  /* W, H; pixel index = y * W + x, row 0 at top */
+    uint32_t n_cache;        /* N cache-level samples per pixel (0..1024) */
+    uint32_t n_resid;        /* M residual samples per pixel (0..64) */
+    uint32_t max_depth;      /* path segments of a residual path (1..64) */
+    uint32_t frame;          /* Philox key word 1 */
+    uint64_t seed;           /* Philox key word 0 = low 32 bits */
+    uint32_t n_prims;        /* primitives in the scene blob (1..NIRC_MAX_PRIMS) */
+    uint32_t cache_mode;     /* 0 network, 1 zero cache (n = 0: plain path
+                                tracing), 2 constant cache n = cache_const */
+    float cache_const[3];
+    uint32_t pad;
+} nirc_frame_desc;
+
+#define NIRC_MAX_PRIMS 1024u
+
+/* Optional per-pixel outputs of nirc_estimate_frame (device pointers, any
+ * may be NULL): lc, lr = the two levels (W*H x 3 floats); sig = two 64-bit
+ * FNV-1a signatures per pixel of the discrete decisions (path: primary hit,
+ * residual directions, hits, Russian roulette; cache: cache-direction
+ * rejection counts and lobes); count = valid (active) samples per pixel. */
+typedef struct nirc_frame_aux {
+    float* lc;
+    float* lr;
+    uint64_t* sig;
+    uint32_t* count;
+} nirc_frame_aux;
+
+typedef struct nirc_handle nirc_handle;
+
+/* Number of parameters of a configuration: for each layer W (fan_out x
+ * fan_in, row-major) then b (fan_out), input layer first, then the hash
+ * table [level][entry][feature] (hash-grid configs only). */
+uint64_t nirc_param_count(const nirc_config* cfg);
+
+/* Create a cache with zero parameters on the current CUDA device.  The
+ * handle owns the FP32 master parameters, their FP16/BF16 copies, the Adam
+ * moments, gradients and scratch.  Returns NIRC_ERR_UNSUPPORTED for widths
+ * other than 64, more than 8 hidden layers or other feature counts. */
+nirc_status nirc_create(const nirc_config* cfg, nirc_handle** out);
+nirc_status nirc_destroy(nirc_handle* h);
+
+/* Copy nirc_param_count() floats in (host or device pointer per
+ * `on_device`), refresh the low-precision copies and reset Adam (step 0,
+ * zero moments). */
+nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, void* stream);
+/* Copy the FP32 master parameters out. Synchronises `stream` for host output. */
+nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* stream);
+/* Copy out the gradient of the last nirc_train_step (same layout). */
+nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stream);
+/* Select the layer arithmetic for later calls (nirc_precision). */
+nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision);
+
+/* Bare cache queries (eq. 11's n_i): d_out_rgb[i] = n(record_i, dir_i),
+ * n rows, d_dirs = n x 3 unit world directions, d_out_rgb = n x 3. */
+nirc_status nirc_query(nirc_handle* h, const nirc_record* d_records, const float* d_dirs, uint64_t n,
+                       float* d_out_rgb, void* stream);
+
+/* One frame of the two-level estimator (eq. L_mlmc, L_c, L_r) at one shading
+ * point per pixel (the first camera hit, 1 spp): camera ray, N cache samples
+ * and M residual samples drawn independently by BSDF sampling, M residual
+ * paths traced with Russian roulette (continue with probability 0.9) up to
+ * max_depth segments, cache evaluated at all N + M directions.
+ * d_out_rgba = W*H float4 (alpha = 1).  Returns NIRC_ERR_BUDGET when the
+ * scratch for W*H*(N+M) rows cannot be allocated. */
+nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_frame_desc* desc,
+                                float* d_out_rgba, const nirc_frame_aux* aux, void* stream);
+
+/* Training records from a separate path-tracing pass (section "Cache
+ * application"): T paths, each from a uniformly drawn pixel, one record per
+ * path at its first hit with the BSDF-sampled direction and the path-traced
+ * incident radiance as target.  Records whose path has no usable direction
+ * get flags bit 0 cleared (excluded from the loss).  Philox key word 1 is
+ * frame ^ 0x80000000 so training draws never repeat rendering draws.
+ * d_records = T x 64 B, d_dirs = T x 3, d_targets = T x 3. */
+nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width,
+                           uint32_t height, uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth,
+                           nirc_record* d_records, float* d_dirs, float* d_targets, void* stream);
+
+/* One Adam step on the relative L2 loss of eq. 12 with p_r = 1:
+ *   L = 1/(3n) sum_t sum_rgb valid_t (f - n)^2 / (sg(n)^2 + loss_eps)
+ * over n records (forward, backward through the MLP and the encoding, hash
+ * table gradient scatter, dense bias-corrected Adam over all parameters).
+ * d_loss (optional, device float) receives L. */
+nirc_status nirc_train_step(nirc_handle* h, const nirc_record* d_records, const float* d_dirs,
+                            const float* d_targets, uint64_t n, float* d_loss, void* stream);
+
+/* Mean relative squared error over pixels and RGB (paper: MRSE),
+ * mean (I - R)^2 / (R^2 + eps), accumulated in FP64; images are float4 per
+ * pixel (alpha ignored); d_out = one device double. */
+nirc_status nirc_frame_mrse(const float* d_img_rgba, const float* d_ref_rgba, uint64_t n_pixels, float eps,
+                            double* d_out, void* stream);
+
+/* Kernel timers.  While enabled, every kernel the handle launches is
+ * bracketed by CUDA events on its stream; nirc_timing_read waits for the
+ * recorded events and returns the summed device time and launch count per
+ * kernel class since the last enable.  Classes: */
+enum {
+    NIRC_K_PATH_TRACE = 0,   /* camera hits, records, residual paths */
+    NIRC_K_CACHE = 1,        /* cache integral (encodings, MLP, per-pixel sums) */
+    NIRC_K_TRAIN_RECORDS = 2,/* training-path pass */
+    NIRC_K_TRAIN_FWD = 3,    /* training forward + loss */
+    NIRC_K_TRAIN_BWD = 4,    /* backward through the MLP + hash scatter */
+    NIRC_K_TRAIN_GRADW = 5,  /* weight-gradient reduction */
+    NIRC_K_ADAM = 6,         /* Adam + weight repacking */
+    NIRC_K_QUERY = 7,        /* bare cache queries */
+    NIRC_K_CLASSES = 8
+};
+typedef struct nirc_timing {
+    double ms[NIRC_K_CLASSES];
+    uint64_t launches[NIRC_K_CLASSES];
+} nirc_timing;
+nirc_status nirc_timing_enable(nirc_handle* h, int enable);
+nirc_status nirc_timing_read(nirc_handle* h, nirc_timing* out);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* nirc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NIRC_H */

@@ -1,0 +1,451 @@
+// nirc_capi.cu -- the extern "C" boundary of libnirc.so (declared in nirc.h).
+//
+// Validates arguments, owns device state of a cache handle, sizes scratch,
+// and enqueues the kernels on the caller's stream.  Every entry point
+// returns a status; failures record a thread-local message.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "nirc_internal.h"
+
+namespace nirc {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+nirc_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return NIRC_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? NIRC_ERR_OOM : NIRC_ERR_CUDA;
+}
+
+NetShape make_shape(const nirc_config& cfg) {
+    NetShape s{};
+    s.hashgrid = cfg.pos_encoding == NIRC_POS_HASHGRID;
+    s.levels = s.hashgrid ? cfg.hash_levels : 0;
+    s.log2_table = cfg.log2_table;
+    s.n_pos = s.hashgrid ? cfg.hash_levels * cfg.feats_per_level : 3 * 2 * cfg.freq_octaves;
+    s.n_in = s.n_pos + kDirFeatures + kNrmFeatures;
+    s.n_pix = s.n_pos + kNrmFeatures;
+    s.hidden = cfg.hidden_layers;
+    s.n_mlp = (uint64_t)kWidth * s.n_in + kWidth + (uint64_t)(s.hidden - 1) * (kWidth * kWidth + kWidth) +
+              3ull * kWidth + 3;
+    s.n_hash = s.hashgrid ? (uint64_t)cfg.hash_levels * (1ull << cfg.log2_table) * cfg.feats_per_level : 0;
+    s.off_wpix = 0;
+    s.off_wdir = s.n_pix * kWidth;
+    s.off_b0 = s.off_wdir + kDirFeatures * kWidth;
+    s.off_hidden = s.off_b0 + kWidth;
+    s.off_out = s.off_hidden + (s.hidden - 1) * (kWidth * kWidth + kWidth);
+    s.packed_floats = s.off_out + 4 * kWidth + 4;
+    return s;
+}
+
+GridParams make_grid(const nirc_config& cfg) {
+    GridParams g{};
+    if (cfg.pos_encoding != NIRC_POS_HASHGRID) return g;
+    g.n_levels = cfg.hash_levels;
+    const uint64_t T = 1ull << cfg.log2_table;
+    g.mask = (uint32_t)(T - 1);
+    for (uint32_t l = 0; l < cfg.hash_levels; ++l) {
+        const uint32_t res = (uint32_t)std::floor((double)cfg.base_res * std::pow((double)cfg.growth, (double)l));
+        const uint64_t side = (uint64_t)res + 1;
+        g.level[l].res = res;
+        g.level[l].dense = side * side * side <= T ? 1u : 0u;
+        g.level[l].fres = (float)res;
+        g.level[l].pad = 0;
+    }
+    return g;
+}
+
+static nirc_status check_config(const nirc_config* c) {
+    if (!c) {
+        set_error("config is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    if (c->width != kWidth) {
+        set_error("width %u unsupported (only 64)", c->width);
+        return NIRC_ERR_UNSUPPORTED;
+    }
+    if (c->hidden_layers < 1 || c->hidden_layers > kMaxHidden) {
+        set_error("hidden_layers %u outside 1..%u", c->hidden_layers, kMaxHidden);
+        return NIRC_ERR_UNSUPPORTED;
+    }
+    if (c->freq_octaves != 4) {
+        set_error("freq_octaves %u unsupported (only 4)", c->freq_octaves);
+        return NIRC_ERR_UNSUPPORTED;
+    }
+    if (c->pos_encoding == NIRC_POS_HASHGRID) {
+        if (c->feats_per_level != 2 || c->hash_levels < 1 || c->hash_levels > kMaxLevels || c->log2_table < 4 ||
+            c->log2_table > 24 || c->base_res < 1 || !(c->growth >= 1.0f) ||
+            std::floor((double)c->base_res * std::pow((double)c->growth, (double)(c->hash_levels - 1))) > 1e7) {
+            set_error("hash grid configuration unsupported (2 features, 1..16 levels, log2_table 4..24)");
+            return NIRC_ERR_UNSUPPORTED;
+        }
+        if (c->hash_levels * 2 + kNrmFeatures > kWidth) {
+            set_error("too many per-surface features");
+            return NIRC_ERR_UNSUPPORTED;
+        }
+    } else if (c->pos_encoding != NIRC_POS_FREQ) {
+        set_error("pos_encoding %u unknown", c->pos_encoding);
+        return NIRC_ERR_INVALID;
+    }
+    if (c->precision > NIRC_FP8_E4M3_TC) {
+        set_error("precision %u unknown", c->precision);
+        return NIRC_ERR_INVALID;
+    }
+    return NIRC_OK;
+}
+
+static nirc_status ensure(void** buf, size_t* cap, size_t bytes, const char* what) {
+    if (*cap >= bytes) return NIRC_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(buf, bytes);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        cudaGetLastError();
+        set_error("cannot allocate %zu bytes of %s scratch: %s", bytes, what, cudaGetErrorString(e));
+        return NIRC_ERR_BUDGET;
+    }
+    *cap = bytes;
+    return NIRC_OK;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+constexpr int kMaxPending = 2048;
+
+static void resolve_pending(nirc_handle* h) {
+    for (int i = 0; i < h->n_pending; ++i) {
+        const auto& p = h->pending[i];
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
+            h->timing_ms[p.cls] += ms;
+            h->timing_launches[p.cls] += 1;
+        }
+    }
+    h->n_pending = 0;
+}
+
+void timer_begin(const nirc_handle* hc, int cls, cudaStream_t st) {
+    auto* h = const_cast<nirc_handle*>(hc);
+    if (!h->timing || !h->pending) return;
+    if (h->n_pending >= kMaxPending) resolve_pending(h);
+    auto& p = h->pending[h->n_pending];
+    p.cls = cls;
+    p.start = h->event_pool[2 * h->n_pending];
+    p.stop = h->event_pool[2 * h->n_pending + 1];
+    cudaEventRecord(p.start, st);
+}
+
+void timer_end(const nirc_handle* hc, int cls, cudaStream_t st) {
+    (void)cls;
+    auto* h = const_cast<nirc_handle*>(hc);
+    if (!h->timing || !h->pending) return;
+    cudaEventRecord(h->pending[h->n_pending].stop, st);
+    h->n_pending += 1;
+}
+
+}  // namespace nirc
+
+using namespace nirc;
+
+extern "C" {
+
+const char* nirc_last_error(void) { return g_err; }
+
+nirc_status nirc_timing_enable(nirc_handle* h, int enable) {
+    if (!h) {
+        set_error("nirc_timing_enable: handle is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    if (enable && !h->pending) {
+        h->pending = new (std::nothrow) nirc_handle::Pending[kMaxPending];
+        h->event_pool = new (std::nothrow) cudaEvent_t[2 * kMaxPending];
+        if (!h->pending || !h->event_pool) {
+            set_error("nirc_timing_enable: host allocation failed");
+            return NIRC_ERR_OOM;
+        }
+        for (int i = 0; i < 2 * kMaxPending; ++i) {
+            cudaError_t e = cudaEventCreate(&h->event_pool[i]);
+            if (e != cudaSuccess) return cuda_status(e, "nirc_timing_enable");
+            h->n_pool = i + 1;
+        }
+    }
+    resolve_pending(h);
+    for (int c = 0; c < NIRC_K_CLASSES; ++c) {
+        h->timing_ms[c] = 0.0;
+        h->timing_launches[c] = 0;
+    }
+    h->timing = enable != 0;
+    return NIRC_OK;
+}
+
+nirc_status nirc_timing_read(nirc_handle* h, nirc_timing* out) {
+    if (!h || !out) {
+        set_error("nirc_timing_read: NULL argument");
+        return NIRC_ERR_INVALID;
+    }
+    resolve_pending(h);
+    for (int c = 0; c < NIRC_K_CLASSES; ++c) {
+        out->ms[c] = h->timing_ms[c];
+        out->launches[c] = h->timing_launches[c];
+    }
+    return cuda_status(cudaGetLastError(), "nirc_timing_read");
+}
+
+uint64_t nirc_param_count(const nirc_config* cfg) {
+    if (check_config(cfg) != NIRC_OK) return 0;
+    const NetShape s = make_shape(*cfg);
+    return s.n_mlp + s.n_hash;
+}
+
+nirc_status nirc_create(const nirc_config* cfg, nirc_handle** out) {
+    if (!out) {
+        set_error("out is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    *out = nullptr;
+    nirc_status st = check_config(cfg);
+    if (st != NIRC_OK) return st;
+    nirc_handle* h = new (std::nothrow) nirc_handle();
+    if (!h) {
+        set_error("host allocation failed");
+        return NIRC_ERR_OOM;
+    }
+    h->cfg = *cfg;
+    h->shape = make_shape(*cfg);
+    h->grid = make_grid(*cfg);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    const uint64_t np = h->shape.n_mlp + h->shape.n_hash;
+    if (e == cudaSuccess) e = cudaMalloc(&h->params, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->adam_m, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->adam_v, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->grad, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->packed, h->shape.packed_floats * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->loss_accum, sizeof(float));
+    if (e == cudaSuccess && h->shape.n_hash) e = cudaMalloc(&h->hash16, h->shape.n_hash * sizeof(__half));
+    if (e == cudaSuccess) e = cudaMemset(h->params, 0, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->adam_m, 0, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->adam_v, 0, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->grad, 0, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(h->packed, 0, h->shape.packed_floats * sizeof(float));
+    if (e == cudaSuccess && h->hash16) e = cudaMemset(h->hash16, 0, h->shape.n_hash * sizeof(__half));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        st = cuda_status(e, "nirc_create");
+        nirc_destroy(h);
+        return st;
+    }
+    *out = h;
+    return NIRC_OK;
+}
+
+nirc_status nirc_destroy(nirc_handle* h) {
+    if (!h) return NIRC_OK;
+    cudaFree(h->params);
+    cudaFree(h->adam_m);
+    cudaFree(h->adam_v);
+    cudaFree(h->grad);
+    cudaFree(h->packed);
+    cudaFree(h->loss_accum);
+    cudaFree(h->hash16);
+    cudaFree(h->packed_tc);
+    cudaFree(h->scratch);
+    cudaFree(h->train_scratch);
+    for (int i = 0; i < h->n_pool; ++i) cudaEventDestroy(h->event_pool[i]);
+    delete[] h->event_pool;
+    delete[] h->pending;
+    delete h;
+    return NIRC_OK;
+}
+
+nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, void* stream) {
+    if (!h || !params) {
+        set_error("nirc_set_params: NULL argument");
+        return NIRC_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint64_t np = h->shape.n_mlp + h->shape.n_hash;
+    cudaError_t e = cudaMemcpyAsync(h->params, params, np * sizeof(float),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->adam_m, 0, np * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->adam_v, 0, np * sizeof(float), st);
+    if (e == cudaSuccess) e = launch_repack_simt(h, st);
+    if (e == cudaSuccess) e = launch_hash_to_half(h, st);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);  // host buffer may be freed on return
+    if (e != cudaSuccess) return cuda_status(e, "nirc_set_params");
+    h->step = 0;
+    return NIRC_OK;
+}
+
+static nirc_status copy_out(const float* src, uint64_t n, float* out, int on_device, void* stream, const char* what) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(out, src, n * sizeof(float),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);
+    return cuda_status(e, what);
+}
+
+nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* stream) {
+    if (!h || !out) {
+        set_error("nirc_get_params: NULL argument");
+        return NIRC_ERR_INVALID;
+    }
+    return copy_out(h->params, h->shape.n_mlp + h->shape.n_hash, out, on_device, stream, "nirc_get_params");
+}
+
+nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stream) {
+    if (!h || !out) {
+        set_error("nirc_get_grads: NULL argument");
+        return NIRC_ERR_INVALID;
+    }
+    return copy_out(h->grad, h->shape.n_mlp + h->shape.n_hash, out, on_device, stream, "nirc_get_grads");
+}
+
+nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision) {
+    if (!h || precision > NIRC_FP8_E4M3_TC) {
+        set_error("nirc_set_precision: bad argument");
+        return NIRC_ERR_INVALID;
+    }
+    if (precision != NIRC_FP32_SIMT) {
+        set_error("precision %u is not available in this build", precision);
+        return NIRC_ERR_UNSUPPORTED;
+    }
+    h->cfg.precision = precision;
+    return NIRC_OK;
+}
+
+nirc_status nirc_query(nirc_handle* h, const nirc_record* d_records, const float* d_dirs, uint64_t n,
+                       float* d_out_rgb, void* stream) {
+    if (!h) {
+        set_error("nirc_query: handle is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    if (n == 0) return NIRC_OK;
+    if (!d_records || !d_dirs || !d_out_rgb || !aligned16(d_records)) {
+        set_error("nirc_query: NULL or misaligned pointer");
+        return NIRC_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    timer_begin(h, NIRC_K_QUERY, st);
+    cudaError_t e = launch_query_simt(h, d_records, d_dirs, n, d_out_rgb, st);
+    timer_end(h, NIRC_K_QUERY, st);
+    return cuda_status(e, "nirc_query");
+}
+
+nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_frame_desc* desc, float* d_out_rgba,
+                                const nirc_frame_aux* aux, void* stream) {
+    if (!h || !desc) {
+        set_error("nirc_estimate_frame: NULL handle or descriptor");
+        return NIRC_ERR_INVALID;
+    }
+    const nirc_frame_desc& fd = *desc;
+    const uint64_t P = (uint64_t)fd.width * fd.height;
+    if (P == 0) return NIRC_OK;
+    if (!d_scene || !d_out_rgba || !aligned16(d_scene) || !aligned16(d_out_rgba)) {
+        set_error("nirc_estimate_frame: NULL or misaligned scene/output pointer");
+        return NIRC_ERR_INVALID;
+    }
+    if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
+        fd.max_depth > 64 || fd.cache_mode > 2 || P > 0xFFFFFFFFull) {
+        set_error("nirc_estimate_frame: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64)",
+                  NIRC_MAX_PRIMS);
+        return NIRC_ERR_INVALID;
+    }
+    if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
+                (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)))) {
+        set_error("nirc_estimate_frame: misaligned aux pointer");
+        return NIRC_ERR_INVALID;
+    }
+    const size_t rec_bytes = P * sizeof(nirc_record);
+    const size_t base_bytes = P * sizeof(PixelBase);
+    const size_t rows_bytes = P * fd.n_resid * sizeof(ResidRow);
+    nirc_status s = ensure(&h->scratch, &h->scratch_bytes, rec_bytes + base_bytes + rows_bytes + 256, "frame");
+    if (s != NIRC_OK) return s;
+    char* sp = reinterpret_cast<char*>(h->scratch);
+    nirc_record* recs = reinterpret_cast<nirc_record*>(sp);
+    PixelBase* base = reinterpret_cast<PixelBase*>(sp + rec_bytes);
+    ResidRow* rows = reinterpret_cast<ResidRow*>(sp + rec_bytes + base_bytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t* sig = aux ? aux->sig : nullptr;
+    uint32_t* count = aux ? aux->count : nullptr;
+    timer_begin(h, NIRC_K_PATH_TRACE, st);
+    cudaError_t e = launch_primary_resid(h, d_scene, fd, recs, base, rows, sig, count, st);
+    timer_end(h, NIRC_K_PATH_TRACE, st);
+    if (e != cudaSuccess) return cuda_status(e, "nirc_estimate_frame (path tracing)");
+    timer_begin(h, NIRC_K_CACHE, st);
+    e = launch_cache_simt(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
+                          count, st);
+    timer_end(h, NIRC_K_CACHE, st);
+    return cuda_status(e, "nirc_estimate_frame (cache integral)");
+}
+
+nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width, uint32_t height,
+                           uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* d_records,
+                           float* d_dirs, float* d_targets, void* stream) {
+    if (!h) {
+        set_error("nirc_gen_train: handle is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    if (T == 0) return NIRC_OK;
+    if (!d_scene || !d_records || !d_dirs || !d_targets || !aligned16(d_scene) || !aligned16(d_records)) {
+        set_error("nirc_gen_train: NULL or misaligned pointer");
+        return NIRC_ERR_INVALID;
+    }
+    if (n_prims < 1 || n_prims > NIRC_MAX_PRIMS || width == 0 || height == 0 ||
+        (uint64_t)width * height > 0xFFFFFFFFull || max_depth < 1 || max_depth > 64 || T > 0xFFFFFFFFull) {
+        set_error("nirc_gen_train: argument out of range");
+        return NIRC_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    timer_begin(h, NIRC_K_TRAIN_RECORDS, st);
+    cudaError_t e = launch_gen_train(h, d_scene, n_prims, width, height, T, frame, seed, max_depth, d_records, d_dirs,
+                                     d_targets, st);
+    timer_end(h, NIRC_K_TRAIN_RECORDS, st);
+    return cuda_status(e, "nirc_gen_train");
+}
+
+nirc_status nirc_train_step(nirc_handle* h, const nirc_record* d_records, const float* d_dirs, const float* d_targets,
+                            uint64_t n, float* d_loss, void* stream) {
+    if (!h) {
+        set_error("nirc_train_step: handle is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    if (n == 0) return NIRC_OK;
+    if (!d_records || !d_dirs || !d_targets || !aligned16(d_records) || n > 0xFFFFFFFFull) {
+        set_error("nirc_train_step: NULL/misaligned pointer or n too large");
+        return NIRC_ERR_INVALID;
+    }
+    nirc_status s = ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h->shape, n), "training");
+    if (s != NIRC_OK) return s;
+    return cuda_status(launch_train_step(h, d_records, d_dirs, d_targets, n, d_loss, (cudaStream_t)stream),
+                       "nirc_train_step");
+}
+
+nirc_status nirc_frame_mrse(const float* d_img_rgba, const float* d_ref_rgba, uint64_t n_pixels, float eps,
+                            double* d_out, void* stream) {
+    if (!d_out) {
+        set_error("nirc_frame_mrse: output is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    if (n_pixels && (!d_img_rgba || !d_ref_rgba || !aligned16(d_img_rgba) || !aligned16(d_ref_rgba))) {
+        set_error("nirc_frame_mrse: NULL or misaligned image");
+        return NIRC_ERR_INVALID;
+    }
+    return cuda_status(launch_mrse(d_img_rgba, d_ref_rgba, n_pixels, eps, d_out, (cudaStream_t)stream),
+                       "nirc_frame_mrse");
+}
+
+}  // extern "C"

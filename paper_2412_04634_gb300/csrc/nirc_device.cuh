@@ -1,0 +1,470 @@
+// nirc_device.cuh -- device building blocks of the NIRC hot path (sm_103a).
+//
+// Counter-based sampling (Philox4x32-10), strict-IEEE binary32 geometry,
+// BSDF importance sampling and the network input encodings.  Everything that
+// decides an integer (hits, hit points, sampled directions, disk-rejection
+// and Russian-roulette tests, hash-grid cells) uses explicitly rounded
+// binary32 intrinsics (__fadd_rn, __fmul_rn, ...), which the compiler never
+// contracts into FMAs, in a fixed operation order: the decisions are then
+// the same on any IEEE-754 implementation that performs the same operations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+
+#include "nirc.h"
+
+namespace nirc {
+
+// ---------------------------------------------------------------------------
+// Binary layouts of the inputs (see nirc.h)
+// ---------------------------------------------------------------------------
+
+struct __align__(16) Prim {
+    float a[3];
+    float radius;
+    float u[3];
+    float inv_uu;
+    float v[3];
+    float inv_vv;
+    float n[3];
+    uint32_t kind;
+    float albedo[3];
+    float roughness;
+    float emission[3];
+    uint32_t flags;
+};
+static_assert(sizeof(Prim) == 96, "primitive layout");
+
+struct __align__(16) SceneHeader {
+    uint32_t n_prims;
+    uint32_t pad[3];
+    float origin[4];
+    float top_left[4];
+    float horizontal[4];
+    float vertical[4];
+    uint32_t reserved[4];
+};
+static_assert(sizeof(SceneHeader) == 96, "scene header layout");
+static_assert(sizeof(nirc_record) == 64, "record layout");
+
+// Geometry part of a primitive (first 64 bytes) staged in shared memory.
+struct __align__(16) PrimGeom {
+    float4 a_r;        // a.xyz, radius
+    float4 u_iuu;      // u.xyz, 1/(u.u)
+    float4 v_ivv;      // v.xyz, 1/(v.v)
+    float4 n_kind;     // n.xyz, kind (bit pattern)
+};
+
+enum : uint32_t { MAT_LAMBERT = 0, MAT_GGX = 1, MAT_BLACK = 2 };
+enum : uint32_t { KIND_SPHERE = 0, KIND_RECT = 1 };
+enum : uint32_t { EMIT_TWO_SIDED = 1u << 8 };
+
+// Philox counter word 3 (purpose of a draw); counter = (pixel or training
+// path, sample, call, purpose), key = (seed, frame) or (seed, frame ^ 2^31)
+// for the training pass.
+enum : uint32_t {
+    PURPOSE_CAMERA = 1,
+    PURPOSE_CACHE_DIR = 2,
+    PURPOSE_RESID_DIR = 3,
+    PURPOSE_BOUNCE = 4,  // + 16 * segment
+    PURPOSE_RR = 5,      // + 16 * segment
+    PURPOSE_TRAIN_PICK = 6
+};
+
+constexpr float kTMin = 1e-4f;
+constexpr float kRRContinue = 0.9f;  // Russian roulette terminates with probability 0.1
+constexpr float kF0 = 0.04f;
+constexpr float kPi = 3.14159265358979f;
+constexpr float kInvPi = 0.318309886183791f;
+constexpr uint32_t kTrainKeyBit = 0x80000000u;
+constexpr uint64_t kSigInit = 0xCBF29CE484222325ull;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c2,
+                                     uint32_t c3) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// High 24 bits -> [0, 1), exact.
+__device__ __forceinline__ float u01(uint32_t x) {
+    return __fmul_rn(__uint2float_rn(x >> 8), 1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ uint64_t sig_mix(uint64_t h, uint32_t w) {
+    return (h ^ (uint64_t)w) * 0x100000001B3ull;
+}
+
+// ---------------------------------------------------------------------------
+// Strict binary32 vector helpers
+// ---------------------------------------------------------------------------
+
+struct V3 {
+    float x, y, z;
+};
+
+__device__ __forceinline__ float sdot(V3 a, V3 b) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)), __fmul_rn(a.z, b.z));
+}
+__device__ __forceinline__ V3 ssub(V3 a, V3 b) {
+    return V3{__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z)};
+}
+__device__ __forceinline__ V3 sneg(V3 a) { return V3{-a.x, -a.y, -a.z}; }
+// o + t d
+__device__ __forceinline__ V3 smadd(V3 o, float t, V3 d) {
+    return V3{__fadd_rn(o.x, __fmul_rn(t, d.x)), __fadd_rn(o.y, __fmul_rn(t, d.y)),
+              __fadd_rn(o.z, __fmul_rn(t, d.z))};
+}
+__device__ __forceinline__ V3 snormalize(V3 v) {
+    const float len = __fsqrt_rn(sdot(v, v));
+    const float inv = __fdiv_rn(1.0f, len);
+    return V3{__fmul_rn(v.x, inv), __fmul_rn(v.y, inv), __fmul_rn(v.z, inv)};
+}
+// lx t + ly b + lz n, summed left to right per component
+__device__ __forceinline__ V3 sframe(float lx, float ly, float lz, V3 t, V3 b, V3 n) {
+    return V3{__fadd_rn(__fadd_rn(__fmul_rn(lx, t.x), __fmul_rn(ly, b.x)), __fmul_rn(lz, n.x)),
+              __fadd_rn(__fadd_rn(__fmul_rn(lx, t.y), __fmul_rn(ly, b.y)), __fmul_rn(lz, n.y)),
+              __fadd_rn(__fadd_rn(__fmul_rn(lx, t.z), __fmul_rn(ly, b.z)), __fmul_rn(lz, n.z))};
+}
+
+// ---------------------------------------------------------------------------
+// Ray / primitive intersection, nearest hit over shared-memory primitives
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool hit_sphere(const PrimGeom& g, V3 o, V3 d, float& t_out) {
+    const V3 oc = ssub(o, V3{g.a_r.x, g.a_r.y, g.a_r.z});
+    const float b = sdot(oc, d);
+    const float c = __fsub_rn(sdot(oc, oc), __fmul_rn(g.a_r.w, g.a_r.w));
+    const float disc = __fsub_rn(__fmul_rn(b, b), c);
+    if (!(disc >= 0.0f)) return false;
+    const float sq = __fsqrt_rn(disc);
+    const float t0 = __fsub_rn(-b, sq);
+    const float t1 = __fadd_rn(-b, sq);
+    if (t0 > kTMin) {
+        t_out = t0;
+        return true;
+    }
+    if (t1 > kTMin) {
+        t_out = t1;
+        return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool hit_rect(const PrimGeom& g, V3 o, V3 d, float& t_out) {
+    const V3 n{g.n_kind.x, g.n_kind.y, g.n_kind.z};
+    const float denom = sdot(n, d);
+    if (denom == 0.0f) return false;
+    const V3 a{g.a_r.x, g.a_r.y, g.a_r.z};
+    const float t = __fdiv_rn(sdot(n, ssub(a, o)), denom);
+    if (!(t > kTMin)) return false;
+    const V3 rel = ssub(smadd(o, t, d), a);
+    const float al = __fmul_rn(sdot(rel, V3{g.u_iuu.x, g.u_iuu.y, g.u_iuu.z}), g.u_iuu.w);
+    const float be = __fmul_rn(sdot(rel, V3{g.v_ivv.x, g.v_ivv.y, g.v_ivv.z}), g.v_ivv.w);
+    if (!(al >= 0.0f && al <= 1.0f && be >= 0.0f && be <= 1.0f)) return false;
+    t_out = t;
+    return true;
+}
+
+// Nearest hit with t > kTMin; ties resolve to the lowest index.
+__device__ __forceinline__ int trace_nearest(const PrimGeom* __restrict__ prims, uint32_t n_prims, V3 o, V3 d,
+                                             float& t_hit) {
+    float best = __int_as_float(0x7f800000);  // +inf
+    int idx = -1;
+    for (uint32_t i = 0; i < n_prims; ++i) {
+        const PrimGeom& g = prims[i];
+        float t;
+        const bool hit = (__float_as_uint(g.n_kind.w) == KIND_SPHERE) ? hit_sphere(g, o, d, t) : hit_rect(g, o, d, t);
+        if (hit && t < best) {
+            best = t;
+            idx = (int)i;
+        }
+    }
+    t_hit = best;
+    return idx;
+}
+
+struct Hit {
+    V3 p;
+    V3 n;       // unit, facing the incoming ray
+    bool front; // arrived on the side the stored normal points to
+};
+
+__device__ __forceinline__ Hit hit_info(const PrimGeom& g, V3 o, V3 d, float t) {
+    Hit h;
+    h.p = smadd(o, t, d);
+    V3 n;
+    if (__float_as_uint(g.n_kind.w) == KIND_SPHERE) {
+        n = snormalize(ssub(h.p, V3{g.a_r.x, g.a_r.y, g.a_r.z}));
+    } else {
+        n = V3{g.n_kind.x, g.n_kind.y, g.n_kind.z};
+    }
+    const float dn = sdot(n, d);
+    h.front = dn < 0.0f;
+    if (dn > 0.0f) n = sneg(n);
+    h.n = n;
+    return h;
+}
+
+// Camera ray through pixel (px, py) with jitter (jx, jy).
+__device__ __forceinline__ void camera_ray(const SceneHeader& hd, uint32_t W, uint32_t H, uint32_t px, uint32_t py,
+                                           float jx, float jy, V3& o, V3& d) {
+    const float s = __fdiv_rn(__fadd_rn(__uint2float_rn(px), jx), __uint2float_rn(W));
+    const float t = __fdiv_rn(__fadd_rn(__uint2float_rn(py), jy), __uint2float_rn(H));
+    o = V3{hd.origin[0], hd.origin[1], hd.origin[2]};
+    V3 dd;
+    dd.x = __fsub_rn(__fadd_rn(__fadd_rn(hd.top_left[0], __fmul_rn(s, hd.horizontal[0])), __fmul_rn(t, hd.vertical[0])),
+                     hd.origin[0]);
+    dd.y = __fsub_rn(__fadd_rn(__fadd_rn(hd.top_left[1], __fmul_rn(s, hd.horizontal[1])), __fmul_rn(t, hd.vertical[1])),
+                     hd.origin[1]);
+    dd.z = __fsub_rn(__fadd_rn(__fadd_rn(hd.top_left[2], __fmul_rn(s, hd.horizontal[2])), __fmul_rn(t, hd.vertical[2])),
+                     hd.origin[2]);
+    d = snormalize(dd);
+}
+
+// Load the geometry of n primitives into shared memory (whole block).
+__device__ __forceinline__ void stage_prims(PrimGeom* s_prims, const Prim* __restrict__ g_prims, uint32_t n) {
+    const float4* src = reinterpret_cast<const float4*>(g_prims);
+    float4* dst = reinterpret_cast<float4*>(s_prims);
+    for (uint32_t i = threadIdx.x; i < 4 * n; i += blockDim.x) {
+        const uint32_t p = i >> 2, q = i & 3;
+        dst[i] = __ldg(src + p * 6 + q);  // the first 4 of each primitive's 6 float4
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BSDF importance sampling (independent sets for L_c and L_r)
+// ---------------------------------------------------------------------------
+
+// Orthonormal basis around unit n (Duff et al., JCGT 2017).
+__device__ __forceinline__ void onb(V3 n, V3& t, V3& b) {
+    const float sign = copysignf(1.0f, n.z);
+    const float a = __fdiv_rn(-1.0f, __fadd_rn(sign, n.z));
+    const float bb = __fmul_rn(__fmul_rn(n.x, n.y), a);
+    t = V3{__fadd_rn(1.0f, __fmul_rn(__fmul_rn(__fmul_rn(sign, n.x), n.x), a)), __fmul_rn(sign, bb),
+           __fmul_rn(-sign, n.x)};
+    b = V3{bb, __fadd_rn(sign, __fmul_rn(__fmul_rn(n.y, n.y), a)), -n.y};
+}
+
+// Uniform point on the unit disk: rejection from the square, 2 candidates per
+// Philox call (counter word 2 = call 0..7).  Returns the rejected count.
+__device__ __forceinline__ uint32_t disk_sample(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3,
+                                                float& a, float& b) {
+    uint32_t rejected = 0;
+    for (uint32_t call = 0; call < 8; ++call) {
+        const U4 r = philox(k0, k1, c0, c1, call, c3);
+        float x = __fsub_rn(__fmul_rn(2.0f, u01(r.x)), 1.0f);
+        float y = __fsub_rn(__fmul_rn(2.0f, u01(r.y)), 1.0f);
+        if (__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)) < 1.0f) {
+            a = x;
+            b = y;
+            return rejected;
+        }
+        ++rejected;
+        x = __fsub_rn(__fmul_rn(2.0f, u01(r.z)), 1.0f);
+        y = __fsub_rn(__fmul_rn(2.0f, u01(r.w)), 1.0f);
+        if (__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)) < 1.0f) {
+            a = x;
+            b = y;
+            return rejected;
+        }
+        ++rejected;
+    }
+    a = 0.0f;
+    b = 0.0f;
+    return rejected;
+}
+
+// GGX visible-normal sampling (Heitz, JCGT 2018) with disk point (t1, t2);
+// returns the mirror direction about the sampled normal.
+__device__ __forceinline__ V3 ggx_vndf_reflect(V3 wo, V3 t, V3 b, V3 n, float alpha, float t1, float t2) {
+    const V3 wl{sdot(wo, t), sdot(wo, b), sdot(wo, n)};
+    const V3 vh = snormalize(V3{__fmul_rn(alpha, wl.x), __fmul_rn(alpha, wl.y), wl.z});
+    const float lensq = __fadd_rn(__fmul_rn(vh.x, vh.x), __fmul_rn(vh.y, vh.y));
+    V3 T1;
+    if (lensq > 0.0f) {
+        const float il = __fdiv_rn(1.0f, __fsqrt_rn(lensq));
+        T1 = V3{__fmul_rn(-vh.y, il), __fmul_rn(vh.x, il), 0.0f};
+    } else {
+        T1 = V3{1.0f, 0.0f, 0.0f};
+    }
+    const V3 T2{__fsub_rn(__fmul_rn(vh.y, T1.z), __fmul_rn(vh.z, T1.y)),
+                __fsub_rn(__fmul_rn(vh.z, T1.x), __fmul_rn(vh.x, T1.z)),
+                __fsub_rn(__fmul_rn(vh.x, T1.y), __fmul_rn(vh.y, T1.x))};
+    const float s = __fmul_rn(0.5f, __fadd_rn(1.0f, vh.z));
+    const float t2w = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, s), __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(t1, t1)))),
+                                __fmul_rn(s, t2));
+    const float nz = __fsqrt_rn(fmaxf(0.0f, __fsub_rn(__fsub_rn(1.0f, __fmul_rn(t1, t1)), __fmul_rn(t2w, t2w))));
+    const V3 nh{__fadd_rn(__fadd_rn(__fmul_rn(t1, T1.x), __fmul_rn(t2w, T2.x)), __fmul_rn(nz, vh.x)),
+                __fadd_rn(__fadd_rn(__fmul_rn(t1, T1.y), __fmul_rn(t2w, T2.y)), __fmul_rn(nz, vh.y)),
+                __fadd_rn(__fadd_rn(__fmul_rn(t1, T1.z), __fmul_rn(t2w, T2.z)), __fmul_rn(nz, vh.z))};
+    const V3 ne = snormalize(V3{__fmul_rn(alpha, nh.x), __fmul_rn(alpha, nh.y), fmaxf(0.0f, nh.z)});
+    const V3 h = sframe(ne.x, ne.y, ne.z, t, b, n);
+    const float two_dh = __fmul_rn(2.0f, sdot(wo, h));
+    const V3 wi{__fsub_rn(__fmul_rn(two_dh, h.x), wo.x), __fsub_rn(__fmul_rn(two_dh, h.y), wo.y),
+                __fsub_rn(__fmul_rn(two_dh, h.z), wo.z)};
+    return snormalize(wi);
+}
+
+// f_r cos / p of the Lambertian + GGX material under the 1/2 cosine + 1/2
+// visible-normal mixture (FP32, continuous).
+__device__ __forceinline__ float3 ggx_mix_weight(V3 n, V3 wo, V3 wi, float3 albedo, float rough) {
+    const float alpha = __fmul_rn(rough, rough);
+    const float a2 = alpha * alpha;
+    const float ci = n.x * wi.x + n.y * wi.y + n.z * wi.z;
+    const float co = n.x * wo.x + n.y * wo.y + n.z * wo.z;
+    float hx = wo.x + wi.x, hy = wo.y + wi.y, hz = wo.z + wi.z;
+    const float hinv = rsqrtf(hx * hx + hy * hy + hz * hz);
+    hx *= hinv;
+    hy *= hinv;
+    hz *= hinv;
+    const float ch = n.x * hx + n.y * hy + n.z * hz;
+    const float oh = fminf(fmaxf(wo.x * hx + wo.y * hy + wo.z * hz, 0.0f), 1.0f);
+    const float dd = ch * ch * (a2 - 1.0f) + 1.0f;
+    const float D = a2 / (kPi * dd * dd);
+    const float lam_o = sqrtf(a2 + (1.0f - a2) * co * co);
+    const float lam_i = sqrtf(a2 + (1.0f - a2) * ci * ci);
+    const float G2 = 2.0f * ci * co / (co * lam_i + ci * lam_o);
+    const float G1o = 2.0f * co / (co + lam_o);
+    const float m = 1.0f - oh;
+    const float m2 = m * m;
+    const float F = kF0 + (1.0f - kF0) * (m2 * m2 * m);
+    const float fs = F * D * G2 / (4.0f * ci * co);
+    const float pdf_s = G1o * D / (4.0f * co);
+    const float pdf = 0.5f * ci * kInvPi + 0.5f * pdf_s;
+    const float k = ci / pdf;
+    return make_float3((albedo.x * kInvPi + fs) * k, (albedo.y * kInvPi + fs) * k, (albedo.z * kInvPi + fs) * k);
+}
+
+struct BsdfSample {
+    V3 wi;
+    float3 w;        // f_r cos / p, zero when invalid
+    bool valid;
+    uint32_t word;   // rejected | lobe << 8 | valid << 9 (signature word)
+};
+
+// Sample at a shading record (p unused); Philox counter (c0, c1, call, c3).
+__device__ __forceinline__ BsdfSample sample_bsdf(V3 n, V3 wo, float3 albedo, float rough, uint32_t mat, uint32_t k0,
+                                                  uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3) {
+    BsdfSample s;
+    s.valid = false;
+    s.w = make_float3(0.f, 0.f, 0.f);
+    s.wi = n;
+    s.word = 0;
+    if (mat == MAT_BLACK) return s;
+    V3 t, b;
+    onb(n, t, b);
+    uint32_t lobe = 0;
+    if (mat == MAT_GGX) {
+        const U4 r = philox(k0, k1, c0, c1, 8u, c3);
+        lobe = u01(r.x) < 0.5f ? 0u : 1u;
+    }
+    float da, db;
+    const uint32_t rejected = disk_sample(k0, k1, c0, c1, c3, da, db);
+    if (lobe == 0) {
+        const float sq = __fadd_rn(__fmul_rn(da, da), __fmul_rn(db, db));
+        const float z = __fsqrt_rn(fmaxf(0.0f, __fsub_rn(1.0f, sq)));
+        s.wi = snormalize(sframe(da, db, z, t, b, n));
+    } else {
+        s.wi = ggx_vndf_reflect(wo, t, b, n, __fmul_rn(rough, rough), da, db);
+    }
+    s.valid = sdot(s.wi, n) > 0.0f;
+    s.word = rejected | (lobe << 8) | ((uint32_t)s.valid << 9);
+    if (!s.valid) return s;
+    if (mat == MAT_LAMBERT) {
+        s.w = albedo;  // (rho/pi) cos / (cos/pi)
+    } else {
+        s.w = ggx_mix_weight(n, wo, s.wi, albedo, rough);
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint32_t record_material(const nirc_record& r) { return (r.flags >> 1) & 3u; }
+
+// ---------------------------------------------------------------------------
+// Encodings
+// ---------------------------------------------------------------------------
+
+// sin(2^k pi v), cos(2^k pi v) for k = 0..3 (octave 0 by sincospi, higher
+// octaves by the double-angle identities).
+__device__ __forceinline__ void freq4(float v, float* e) {
+    float s, c;
+    sincospif(v, &s, &c);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        e[2 * k] = s;
+        e[2 * k + 1] = c;
+        const float s2 = 2.0f * s * c;
+        const float c2 = (c - s) * (c + s);
+        s = s2;
+        c = c2;
+    }
+}
+
+// (theta/pi, phi/2pi in [0,1)) of a unit direction.
+__device__ __forceinline__ void dir_angles(V3 w, float& th, float& ph) {
+    th = acosf(fminf(fmaxf(w.z, -1.0f), 1.0f)) * kInvPi;
+    float p = atan2f(w.y, w.x) * (0.5f * kInvPi);
+    if (p < 0.0f) p += 1.0f;
+    ph = p;
+}
+
+// Hash-grid level description (precomputed on the host).
+struct GridLevel {
+    uint32_t res;    // floor(base * growth^l)
+    uint32_t dense;  // (res + 1)^3 <= T
+    float fres;
+    uint32_t pad;
+};
+
+// Cell corner indices and trilinear weights of position x at one level.
+__device__ __forceinline__ void grid_corners(const GridLevel& L, uint32_t mask, V3 x, uint32_t idx[8], float w[8]) {
+    const float xc[3] = {fminf(fmaxf(x.x, 0.0f), 1.0f), fminf(fmaxf(x.y, 0.0f), 1.0f), fminf(fmaxf(x.z, 0.0f), 1.0f)};
+    uint32_t cell[3];
+    float fr[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float ps = __fmul_rn(xc[d], L.fres);
+        float fl = floorf(ps);
+        if (fl >= L.fres) fl = __fsub_rn(L.fres, 1.0f);
+        cell[d] = (uint32_t)fl;
+        fr[d] = __fsub_rn(ps, fl);
+    }
+    const uint32_t side = L.res + 1;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const uint32_t v0 = cell[0] + (c & 1), v1 = cell[1] + ((c >> 1) & 1), v2 = cell[2] + ((c >> 2) & 1);
+        idx[c] = L.dense ? v0 + v1 * side + v2 * side * side
+                         : ((v0 * 1u) ^ (v1 * 2654435761u) ^ (v2 * 805459861u)) & mask;
+        const float wx = (c & 1) ? fr[0] : 1.0f - fr[0];
+        const float wy = ((c >> 1) & 1) ? fr[1] : 1.0f - fr[1];
+        const float wz = ((c >> 2) & 1) ? fr[2] : 1.0f - fr[2];
+        w[c] = wx * wy * wz;
+    }
+}
+
+}  // namespace nirc

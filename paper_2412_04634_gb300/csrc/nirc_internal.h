@@ -1,0 +1,128 @@
+// nirc_internal.h -- state of a cache handle and the kernel launchers the
+// C-ABI layer (nirc_capi.cu) drives.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <string>
+
+#include "nirc.h"
+#include "nirc_device.cuh"
+
+namespace nirc {
+
+constexpr uint32_t kWidth = 64;
+constexpr uint32_t kMaxHidden = 8;
+constexpr uint32_t kMaxLevels = 16;
+constexpr uint32_t kDirFeatures = 16;  // (theta, phi) x 4 octaves x (sin, cos)
+constexpr uint32_t kNrmFeatures = 24;  // normal (3) x 4 octaves x (sin, cos)
+
+// Per-pixel data the path-tracing kernel hands to the cache kernel.
+struct __align__(16) PixelBase {
+    float4 le;  // L_e(x, wo) of the camera hit (w unused)
+    float4 wl;  // (1/M) sum_j w_j L_j: the path-traced part of L_r (w unused)
+};
+
+// One residual direction of a pixel.
+struct __align__(16) ResidRow {
+    float4 wi;  // direction, w = 1 if valid else 0
+    float4 w;   // f_r cos / p (w unused)
+};
+
+// Network shape derived from a config.
+struct NetShape {
+    uint32_t n_pos;     // position features
+    uint32_t n_in;      // network inputs = n_pos + 16 + 24
+    uint32_t n_pix;     // per-pixel features = n_pos + 24
+    uint32_t hidden;    // hidden layers (>= 1)
+    uint64_t n_mlp;     // MLP parameters in the master vector
+    uint64_t n_hash;    // hash-table parameters
+    uint32_t log2_table;
+    uint32_t levels;
+    uint32_t hashgrid;  // 1 = hash grid, 0 = frequency encoding of x
+    // Offsets (floats) in the packed FP32 SIMT weights:
+    uint32_t off_wpix, off_wdir, off_b0, off_hidden, off_out, packed_floats;
+};
+
+struct GridParams {
+    GridLevel level[kMaxLevels];
+    uint32_t n_levels;
+    uint32_t mask;  // T - 1
+};
+
+}  // namespace nirc
+
+struct nirc_handle {
+    nirc_config cfg;
+    int device = 0;
+    int num_sms = 0;
+    nirc::NetShape shape{};
+    nirc::GridParams grid{};
+    float* params = nullptr;        // FP32 master parameters
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* grad = nullptr;
+    float* packed = nullptr;        // transposed FP32 weights for the SIMT kernels
+    __half* hash16 = nullptr;       // FP16 copy of the hash table (tensor-core path)
+    void* packed_tc = nullptr;      // tensor-core operand images of the weights
+    size_t packed_tc_bytes = 0;
+    uint32_t step = 0;              // Adam steps taken
+    void* scratch = nullptr;        // estimate_frame intermediates
+    size_t scratch_bytes = 0;
+    void* train_scratch = nullptr;  // training activations
+    size_t train_scratch_bytes = 0;
+    float* loss_accum = nullptr;    // one float
+    // kernel timers (nirc_timing_enable / nirc_timing_read)
+    bool timing = false;
+    struct Pending {
+        int cls;
+        cudaEvent_t start, stop;
+    };
+    Pending* pending = nullptr;     // recorded, not yet read
+    int n_pending = 0;
+    cudaEvent_t* event_pool = nullptr;
+    int n_pool = 0;
+    double timing_ms[NIRC_K_CLASSES] = {};
+    uint64_t timing_launches[NIRC_K_CLASSES] = {};
+};
+
+namespace nirc {
+
+void set_error(const char* fmt, ...);
+nirc_status cuda_status(cudaError_t e, const char* what);
+
+// Bracket one kernel launch with timer events when timing is enabled.
+void timer_begin(const nirc_handle* h, int cls, cudaStream_t st);
+void timer_end(const nirc_handle* h, int cls, cudaStream_t st);
+
+NetShape make_shape(const nirc_config& cfg);
+GridParams make_grid(const nirc_config& cfg);
+
+// nirc_pt.cu
+cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
+                                 nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig,
+                                 uint32_t* count, cudaStream_t st);
+cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
+                             uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* recs,
+                             float* dirs, float* targets, cudaStream_t st);
+
+// nirc_cache_simt.cu
+cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
+                              const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
+                              uint64_t* sig, uint32_t* count, cudaStream_t st);
+cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, const float* dirs, uint64_t n,
+                              float* out, cudaStream_t st);
+cudaError_t launch_repack_simt(const nirc_handle* h, cudaStream_t st);
+
+// nirc_train.cu
+size_t train_scratch_bytes(const NetShape& s, uint64_t n);
+cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
+                              uint64_t n, float* d_loss, cudaStream_t st);
+cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st);
+
+// nirc_metrics.cu
+cudaError_t launch_mrse(const float* img, const float* ref, uint64_t n, float eps, double* out, cudaStream_t st);
+
+}  // namespace nirc

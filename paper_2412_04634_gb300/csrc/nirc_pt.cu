@@ -1,0 +1,230 @@
+// nirc_pt.cu -- path-tracing kernels of the two-level estimator.
+//
+// k_primary_resid: per pixel, the camera ray (1 spp, Philox jitter), the
+//   shading record of the first hit (paper: surface parameter buffer), and
+//   the residual level's M BSDF-sampled directions with their path-traced
+//   incident radiance L_j (eq. L_r, the L_i term), Russian roulette with
+//   termination probability 0.1 (paper: section "Results", implementation
+//   paragraph).
+// k_gen_train: the separate training pass (section "Cache application"):
+//   T paths from uniformly drawn pixels, one record per path.
+//
+// Primitive geometry is staged in shared memory; every thread intersects
+// the same primitive at the same time (broadcast reads).
+#include "nirc_internal.h"
+
+namespace nirc {
+
+struct FrameArgs {
+    uint32_t W, H, N, M, D, n_prims;
+    uint32_t k0, k1;
+};
+
+// Incident radiance along (o, d) from the path's vertices.
+__device__ __forceinline__ float3 trace_path(const PrimGeom* __restrict__ sp, const Prim* __restrict__ gp,
+                                             uint32_t n_prims, V3 o, V3 d, uint32_t k0, uint32_t k1, uint32_t c0,
+                                             uint32_t c1, uint32_t max_depth, uint64_t& sig) {
+    float3 L = make_float3(0.f, 0.f, 0.f);
+    float3 beta = make_float3(1.f, 1.f, 1.f);
+    for (uint32_t seg = 1; seg <= max_depth; ++seg) {
+        float t;
+        const int prim = trace_nearest(sp, n_prims, o, d, t);
+        sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+        if (prim < 0) break;
+        const Hit h = hit_info(sp[prim], o, d, t);
+        const Prim* P = gp + prim;
+        const uint32_t flags = __ldg(&P->flags);
+        if (h.front || (flags & EMIT_TWO_SIDED)) {
+            L.x += beta.x * __ldg(&P->emission[0]);
+            L.y += beta.y * __ldg(&P->emission[1]);
+            L.z += beta.z * __ldg(&P->emission[2]);
+        }
+        if (seg == max_depth) break;
+        const U4 r = philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg);
+        const bool cont = u01(r.x) < kRRContinue;
+        sig = sig_mix(sig, (uint32_t)cont);
+        if (!cont) break;
+        beta.x /= kRRContinue;
+        beta.y /= kRRContinue;
+        beta.z /= kRRContinue;
+        const float3 alb = make_float3(__ldg(&P->albedo[0]), __ldg(&P->albedo[1]), __ldg(&P->albedo[2]));
+        const BsdfSample s = sample_bsdf(h.n, sneg(d), alb, __ldg(&P->roughness), flags & 3u, k0, k1, c0, c1,
+                                         PURPOSE_BOUNCE + 16u * seg);
+        sig = sig_mix(sig, s.word);
+        if (!s.valid) break;
+        beta.x *= s.w.x;
+        beta.y *= s.w.y;
+        beta.z *= s.w.z;
+        o = h.p;
+        d = s.wi;
+    }
+    return L;
+}
+
+__device__ __forceinline__ void write_record(nirc_record* dst, const Hit& h, V3 d, const Prim* P, uint32_t prim,
+                                             uint32_t flags) {
+    float4* q = reinterpret_cast<float4*>(dst);
+    q[0] = make_float4(h.p.x, h.p.y, h.p.z, h.n.x);
+    q[1] = make_float4(h.n.y, h.n.z, -d.x, -d.y);
+    q[2] = make_float4(-d.z, __ldg(&P->albedo[0]), __ldg(&P->albedo[1]), __ldg(&P->albedo[2]));
+    q[3] = make_float4(__ldg(&P->roughness), __uint_as_float(prim), __uint_as_float(flags), 0.f);
+}
+
+__global__ void __launch_bounds__(128) k_primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
+                                                       FrameArgs a, nirc_record* __restrict__ recs,
+                                                       PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
+                                                       uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PrimGeom* sp = reinterpret_cast<PrimGeom*>(smem_raw);
+    stage_prims(sp, gp, a.n_prims);
+    __shared__ SceneHeader hd;
+    if (threadIdx.x < sizeof(SceneHeader) / 16)
+        reinterpret_cast<float4*>(&hd)[threadIdx.x] = __ldg(reinterpret_cast<const float4*>(hd_g) + threadIdx.x);
+    __syncthreads();
+
+    const uint64_t P = (uint64_t)a.W * a.H;
+    const uint64_t pix64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix64 >= P) return;
+    const uint32_t pix = (uint32_t)pix64;
+    const uint32_t px = pix % a.W, py = pix / a.W;
+
+    const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
+    V3 o, d;
+    camera_ray(hd, a.W, a.H, px, py, u01(r.x), u01(r.y), o, d);
+    float t;
+    const int prim = trace_nearest(sp, a.n_prims, o, d, t);
+    uint64_t sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+    ResidRow* my_rows = rows + (uint64_t)pix * a.M;
+    if (prim < 0) {
+        float4* q = reinterpret_cast<float4*>(recs + pix);
+        q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
+        base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t j = 0; j < a.M; ++j) {
+            my_rows[j].wi = make_float4(0.f, 0.f, 1.f, 0.f);
+            my_rows[j].w = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+        if (count) count[pix] = 0;
+        return;
+    }
+    const Hit h = hit_info(sp[prim], o, d, t);
+    const Prim* Pp = gp + prim;
+    const uint32_t pflags = __ldg(&Pp->flags);
+    const uint32_t mat = pflags & 3u;
+    write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (mat << 1));
+    float3 le = make_float3(0.f, 0.f, 0.f);
+    if (h.front || (pflags & EMIT_TWO_SIDED))
+        le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
+    const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+    const float rough = __ldg(&Pp->roughness);
+    const V3 wo = sneg(d);
+
+    float3 wl = make_float3(0.f, 0.f, 0.f);
+    uint32_t nvalid = 0;
+    for (uint32_t j = 0; j < a.M; ++j) {
+        const BsdfSample s = sample_bsdf(h.n, wo, alb, rough, mat, a.k0, a.k1, pix, j, PURPOSE_RESID_DIR);
+        sig = sig_mix(sig, s.word);
+        my_rows[j].wi = make_float4(s.wi.x, s.wi.y, s.wi.z, s.valid ? 1.f : 0.f);
+        my_rows[j].w = make_float4(s.w.x, s.w.y, s.w.z, 0.f);
+        if (!s.valid) continue;
+        const float3 L = trace_path(sp, gp, a.n_prims, h.p, s.wi, a.k0, a.k1, pix, j, a.D, sig);
+        wl.x += s.w.x * L.x;
+        wl.y += s.w.y * L.y;
+        wl.z += s.w.z * L.z;
+        ++nvalid;
+    }
+    if (a.M) {
+        const float inv = 1.0f / (float)a.M;
+        wl.x *= inv;
+        wl.y *= inv;
+        wl.z *= inv;
+    }
+    base[pix].le = make_float4(le.x, le.y, le.z, 0.f);
+    base[pix].wl = make_float4(wl.x, wl.y, wl.z, 0.f);
+    if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+    if (count) count[pix] = nvalid;
+}
+
+__global__ void __launch_bounds__(128) k_gen_train(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
+                                                   uint32_t n_prims, uint32_t W, uint32_t H, uint64_t T, uint32_t k0,
+                                                   uint32_t k1, uint32_t max_depth, nirc_record* __restrict__ recs,
+                                                   float* __restrict__ dirs, float* __restrict__ targets) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PrimGeom* sp = reinterpret_cast<PrimGeom*>(smem_raw);
+    stage_prims(sp, gp, n_prims);
+    __shared__ SceneHeader hd;
+    if (threadIdx.x < sizeof(SceneHeader) / 16)
+        reinterpret_cast<float4*>(&hd)[threadIdx.x] = __ldg(reinterpret_cast<const float4*>(hd_g) + threadIdx.x);
+    __syncthreads();
+
+    const uint64_t ti = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ti >= T) return;
+    const uint32_t tr = (uint32_t)ti;
+    const uint32_t P = W * H;
+    const U4 r = philox(k0, k1, tr, 0u, 0u, PURPOSE_TRAIN_PICK);
+    const uint32_t pix = __umulhi(r.x, P);
+    V3 o, d;
+    camera_ray(hd, W, H, pix % W, pix / W, u01(r.y), u01(r.z), o, d);
+    float t;
+    const int prim = trace_nearest(sp, n_prims, o, d, t);
+    float* dir = dirs + 3 * ti;
+    float* tg = targets + 3 * ti;
+    dir[0] = dir[1] = dir[2] = 0.f;
+    tg[0] = tg[1] = tg[2] = 0.f;
+    if (prim < 0) {
+        float4* q = reinterpret_cast<float4*>(recs + ti);
+        q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const Hit h = hit_info(sp[prim], o, d, t);
+    const Prim* Pp = gp + prim;
+    const uint32_t mat = __ldg(&Pp->flags) & 3u;
+    const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+    const BsdfSample s = sample_bsdf(h.n, sneg(d), alb, __ldg(&Pp->roughness), mat, k0, k1, tr, 0u, PURPOSE_RESID_DIR);
+    write_record(recs + ti, h, d, Pp, (uint32_t)prim, (s.valid ? 1u : 0u) | (mat << 1));
+    if (!s.valid) return;
+    uint64_t sig = 0;
+    const float3 L = trace_path(sp, gp, n_prims, h.p, s.wi, k0, k1, tr, 0u, max_depth, sig);
+    dir[0] = s.wi.x;
+    dir[1] = s.wi.y;
+    dir[2] = s.wi.z;
+    tg[0] = L.x;
+    tg[1] = L.y;
+    tg[2] = L.z;
+}
+
+cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
+                                 nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig, uint32_t* count,
+                                 cudaStream_t st) {
+    (void)h;
+    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
+    const uint64_t P = (uint64_t)fd.width * fd.height;
+    const uint32_t threads = 128;
+    const uint32_t blocks = (uint32_t)((P + threads - 1) / threads);
+    const size_t smem = (size_t)fd.n_prims * sizeof(PrimGeom);
+    const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
+    const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
+    cudaError_t e = cudaFuncSetAttribute(k_primary_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_primary_resid<<<blocks, threads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
+                             uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* recs,
+                             float* dirs, float* targets, cudaStream_t st) {
+    (void)h;
+    const uint32_t threads = 128;
+    const uint32_t blocks = (uint32_t)((T + threads - 1) / threads);
+    const size_t smem = (size_t)n_prims * sizeof(PrimGeom);
+    const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
+    const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
+    cudaError_t e = cudaFuncSetAttribute(k_gen_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_gen_train<<<blocks, threads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
+                                               max_depth, recs, dirs, targets);
+    return cudaGetLastError();
+}
+
+}  // namespace nirc

@@ -1,0 +1,99 @@
+// nirc_simt.cuh -- FP32 SIMT building blocks shared by the cache and
+// training kernels: packed FP32x2 FMA rows over transposed weights in
+// shared memory, the per-surface encoding and compensated sums.
+#pragma once
+
+#include "nirc_internal.h"
+
+namespace nirc {
+
+__device__ __forceinline__ void fma_row(float2 (&acc)[32], const float* __restrict__ wrow, float a) {
+    const float4* w4 = reinterpret_cast<const float4*>(wrow);
+    const float2 aa = make_float2(a, a);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float4 w = w4[q];
+        acc[2 * q] = __ffma2_rn(make_float2(w.x, w.y), aa, acc[2 * q]);
+        acc[2 * q + 1] = __ffma2_rn(make_float2(w.z, w.w), aa, acc[2 * q + 1]);
+    }
+}
+
+__device__ __forceinline__ void load_bias(float2 (&acc)[32], const float* __restrict__ b) {
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float4 v = b4[q];
+        acc[2 * q] = make_float2(v.x, v.y);
+        acc[2 * q + 1] = make_float2(v.z, v.w);
+    }
+}
+
+__device__ __forceinline__ void store_relu(const float2 (&acc)[32], float* act, int stride) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        act[(2 * q) * stride] = fmaxf(acc[q].x, 0.f);
+        act[(2 * q + 1) * stride] = fmaxf(acc[q].y, 0.f);
+    }
+}
+
+// Per-surface features [position (n_pos)][normal (24)] into act[k * stride].
+__device__ __forceinline__ void encode_surface(const NetShape& s, const GridParams& g, const float* __restrict__ table,
+                                               V3 p, V3 n, float* act, int stride) {
+    float e[8];
+    uint32_t k = 0;
+    if (s.hashgrid) {
+        const uint64_t T = (uint64_t)g.mask + 1;
+        for (uint32_t l = 0; l < g.n_levels; ++l) {
+            uint32_t idx[8];
+            float w[8];
+            grid_corners(g.level[l], g.mask, p, idx, w);
+            const float2* tab = reinterpret_cast<const float2*>(table) + (uint64_t)l * T;
+            float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float2 v = __ldg(tab + idx[c]);
+                f0 += w[c] * v.x;
+                f1 += w[c] * v.y;
+            }
+            act[(k++) * stride] = f0;
+            act[(k++) * stride] = f1;
+        }
+    } else {
+        const float pv[3] = {p.x, p.y, p.z};
+        for (int d = 0; d < 3; ++d) {
+            freq4(pv[d], e);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) act[(k++) * stride] = e[q];
+        }
+    }
+    const float nv[3] = {n.x, n.y, n.z};
+    for (int d = 0; d < 3; ++d) {
+        freq4(nv[d], e);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) act[(k++) * stride] = e[q];
+    }
+}
+
+__device__ __forceinline__ void stage_weights(float* sw, const float* __restrict__ packed, uint32_t n_floats) {
+    const float4* src = reinterpret_cast<const float4*>(packed);
+    float4* dst = reinterpret_cast<float4*>(sw);
+    for (uint32_t i = threadIdx.x; i < n_floats / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+struct Kahan3 {
+    float3 s = make_float3(0.f, 0.f, 0.f);
+    float3 c = make_float3(0.f, 0.f, 0.f);
+    __device__ __forceinline__ void add(float x, float& sum, float& comp) {
+        const float y = x - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    __device__ __forceinline__ void add(float3 v) {
+        add(v.x, s.x, c.x);
+        add(v.y, s.y, c.y);
+        add(v.z, s.z, c.z);
+    }
+};
+
+}  // namespace nirc

@@ -1,0 +1,368 @@
+// nirc_train.cu -- on-line training step of the cache (FP32 SIMT).
+//
+// Loss: relative L2 of eq. 12 with p_r = 1,
+//   L = 1/(3n) sum_t sum_rgb valid_t (f - n)^2 / (sg(n)^2 + eps),
+// so dL/dn = -2 (f - n) / ((n^2 + eps) 3n) with the denominator held
+// constant (stop-gradient), and dL/dz = dL/dn * n below the output clamp.
+//
+//  k_train_fwd   per sample: encoding, layers with stored activations
+//                ([feature][sample] columns, coalesced), loss, dL/dz
+//  k_train_bwd   per sample: deltas through the ReLU layers (transposed
+//                weights in shared memory), then the hash-feature gradient
+//                scattered into the table gradient with float atomics
+//  k_grad_w      per layer: dW = delta x^T and db = sum delta, 4x4 register
+//                tiles over 32-sample chunks staged in shared memory,
+//                split over blocks and combined with float atomics
+//  k_adam        dense bias-corrected Adam over every parameter (untouched
+//                hash entries have g = 0), FP32 master weights and moments,
+//                FP16 copy of the hash table refreshed in the same pass
+#include <cmath>
+
+#include "nirc_internal.h"
+#include "nirc_simt.cuh"
+
+namespace nirc {
+
+constexpr int kTrainThreads = 128;
+constexpr int kGradChunk = 32;
+constexpr int kGradThreads = 352;  // 16 x 22 tiles of 4 x 4
+
+struct TrainPtrs {
+    float* e;      // [n_in][n]
+    float* act;    // [hidden][64][n]
+    float* dz;     // [3][n]
+    float* delta;  // [hidden][64][n]
+};
+
+size_t train_scratch_bytes(const NetShape& s, uint64_t n) {
+    return (size_t)n * ((size_t)s.n_in + 2ull * kWidth * s.hidden + 3) * sizeof(float) + 256;
+}
+
+static TrainPtrs carve(void* base, const NetShape& s, uint64_t n) {
+    float* f = reinterpret_cast<float*>(base);
+    TrainPtrs t;
+    t.e = f;
+    t.act = t.e + (size_t)s.n_in * n;
+    t.dz = t.act + (size_t)s.hidden * kWidth * n;
+    t.delta = t.dz + 3 * n;
+    return t;
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1)
+    k_train_fwd(NetShape s, GridParams g, float z_clamp, float loss_eps, float scale, const float* __restrict__ packed,
+                const float* __restrict__ table, const nirc_record* __restrict__ recs, const float* __restrict__ dirs,
+                const float* __restrict__ targets, uint64_t n, TrainPtrs tp, float* __restrict__ loss_accum) {
+    extern __shared__ __align__(16) float smem[];
+    float* sw = smem;
+    float* act = smem + s.packed_floats + threadIdx.x;
+    const int stride = kTrainThreads;
+    stage_weights(sw, packed, s.packed_floats);
+    __syncthreads();
+    // Uniform trip count per block: the loss reduction below uses full-warp shuffles.
+    for (uint64_t first = (uint64_t)blockIdx.x * kTrainThreads; first < n; first += (uint64_t)gridDim.x * kTrainThreads) {
+        const bool in_range = first + threadIdx.x < n;
+        const uint64_t t = in_range ? first + threadIdx.x : 0;
+        const float4* rq = reinterpret_cast<const float4*>(recs + t);
+        const float4 r0 = __ldg(rq), r1 = __ldg(rq + 1), r3 = __ldg(rq + 3);
+        const bool valid = in_range && (__float_as_uint(r3.z) & 1u);
+        const V3 p{r0.x, r0.y, r0.z}, nn{r0.w, r1.x, r1.y};
+        const V3 wi{__ldg(dirs + 3 * t), __ldg(dirs + 3 * t + 1), __ldg(dirs + 3 * t + 2)};
+        encode_surface(s, g, table, p, nn, act, stride);  // [pos][nrm]
+        float th, ph, edir[16];
+        dir_angles(wi, th, ph);
+        freq4(th, edir);
+        freq4(ph, edir + 8);
+        // network input in parameter order [pos][dir][nrm]
+        if (in_range) {
+            for (uint32_t k = 0; k < s.n_pos; ++k) tp.e[(uint64_t)k * n + t] = act[k * stride];
+#pragma unroll
+            for (uint32_t k = 0; k < 16; ++k) tp.e[(uint64_t)(s.n_pos + k) * n + t] = edir[k];
+            for (uint32_t k = 0; k < kNrmFeatures; ++k)
+                tp.e[(uint64_t)(s.n_pos + 16 + k) * n + t] = act[(s.n_pos + k) * stride];
+        }
+
+        float2 acc[32];
+        load_bias(acc, sw + s.off_b0);
+        for (uint32_t i = 0; i < s.n_pix; ++i) fma_row(acc, sw + s.off_wpix + i * kWidth, act[i * stride]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) fma_row(acc, sw + s.off_wdir + i * kWidth, edir[i]);
+        for (uint32_t l = 0; l < s.hidden; ++l) {
+            float* ag = tp.act + ((uint64_t)l * kWidth) * n + t;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const float a0 = fmaxf(acc[q].x, 0.f), a1 = fmaxf(acc[q].y, 0.f);
+                if (in_range) {
+                    ag[(uint64_t)(2 * q) * n] = a0;
+                    ag[(uint64_t)(2 * q + 1) * n] = a1;
+                }
+                act[(2 * q) * stride] = a0;
+                act[(2 * q + 1) * stride] = a1;
+            }
+            if (l + 1 == s.hidden) break;
+            const float* Wl = sw + s.off_hidden + l * (kWidth * kWidth + kWidth);
+            load_bias(acc, Wl + kWidth * kWidth);
+#pragma unroll 2
+            for (int i = 0; i < (int)kWidth; ++i) fma_row(acc, Wl + i * kWidth, act[i * stride]);
+        }
+        const float* Wo = sw + s.off_out;
+        float z[3] = {Wo[256], Wo[257], Wo[258]};
+        for (int i = 0; i < (int)kWidth; ++i) {
+            const float a = act[i * stride];
+            z[0] += Wo[4 * i] * a;
+            z[1] += Wo[4 * i + 1] * a;
+            z[2] += Wo[4 * i + 2] * a;
+        }
+        float lt = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const bool clamped = !(z[c] <= z_clamp);
+            const float nv = expf(clamped ? z_clamp : z[c]);
+            const float f = __ldg(targets + 3 * t + c);
+            const float den = nv * nv + loss_eps;
+            const float diff = f - nv;
+            float dz = 0.f;
+            if (valid) {
+                lt += diff * diff / den;
+                dz = clamped ? 0.f : -2.f * diff / den * scale * nv;
+            }
+            if (in_range) tp.dz[(uint64_t)c * n + t] = dz;
+        }
+        lt *= scale;
+        for (int o = 16; o > 0; o >>= 1) lt += __shfl_xor_sync(0xffffffffu, lt, o);
+        if ((threadIdx.x & 31) == 0 && loss_accum) atomicAdd(loss_accum, lt);
+    }
+}
+
+__device__ __forceinline__ float dot64(const float* __restrict__ wrow, const float (&d)[64]) {
+    const float4* w4 = reinterpret_cast<const float4*>(wrow);
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const float4 w = w4[q];
+        s0 += w.x * d[4 * q];
+        s1 += w.y * d[4 * q + 1];
+        s2 += w.z * d[4 * q + 2];
+        s3 += w.w * d[4 * q + 3];
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+__global__ void __launch_bounds__(kTrainThreads, 1)
+    k_train_bwd(NetShape s, GridParams g, const float* __restrict__ packed, const nirc_record* __restrict__ recs,
+                uint64_t n, TrainPtrs tp, float* __restrict__ grad_table) {
+    extern __shared__ __align__(16) float smem[];
+    float* sw = smem;
+    stage_weights(sw, packed, s.packed_floats);
+    __syncthreads();
+    for (uint64_t t = (uint64_t)blockIdx.x * kTrainThreads + threadIdx.x; t < n; t += (uint64_t)gridDim.x * kTrainThreads) {
+        const float dz0 = tp.dz[t], dz1 = tp.dz[n + t], dz2 = tp.dz[2 * n + t];
+        float d[64];
+        const float* Wo = sw + s.off_out;
+        const uint32_t H = s.hidden;
+        {
+            const float* ag = tp.act + ((uint64_t)(H - 1) * kWidth) * n + t;
+            float* dg = tp.delta + ((uint64_t)(H - 1) * kWidth) * n + t;
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                const float4 w = *reinterpret_cast<const float4*>(Wo + 4 * i);
+                const float v = w.x * dz0 + w.y * dz1 + w.z * dz2;
+                d[i] = ag[(uint64_t)i * n] > 0.f ? v : 0.f;
+                dg[(uint64_t)i * n] = d[i];
+            }
+        }
+        for (int l = (int)H - 1; l >= 1; --l) {
+            // delta_{l-1}[i] = (sum_o W_l[o][i] delta_l[o]) [act_{l-1}[i] > 0]; W_l^T row i = W_l[:, i]
+            const float* Wl = sw + s.off_hidden + (l - 1) * (kWidth * kWidth + kWidth);
+            const float* ag = tp.act + ((uint64_t)(l - 1) * kWidth) * n + t;
+            float* dg = tp.delta + ((uint64_t)(l - 1) * kWidth) * n + t;
+            float dn[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                const float v = dot64(Wl + i * kWidth, d);
+                dn[i] = ag[(uint64_t)i * n] > 0.f ? v : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 64; ++i) {
+                d[i] = dn[i];
+                dg[(uint64_t)i * n] = dn[i];
+            }
+        }
+        if (s.hashgrid) {
+            const float4* rq = reinterpret_cast<const float4*>(recs + t);
+            const float4 r0 = __ldg(rq), r3 = __ldg(rq + 3);
+            if (!(__float_as_uint(r3.z) & 1u)) continue;
+            const V3 p{r0.x, r0.y, r0.z};
+            const uint64_t T = (uint64_t)g.mask + 1;
+            for (uint32_t l = 0; l < g.n_levels; ++l) {
+                // dL/de for the two features of level l: W0[:, k] = Wpix^T row k
+                const float de0 = dot64(sw + s.off_wpix + (2 * l) * kWidth, d);
+                const float de1 = dot64(sw + s.off_wpix + (2 * l + 1) * kWidth, d);
+                uint32_t idx[8];
+                float w[8];
+                grid_corners(g.level[l], g.mask, p, idx, w);
+                float* gt = grad_table + (uint64_t)l * T * 2;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    atomicAdd(gt + 2 * (uint64_t)idx[c], w[c] * de0);
+                    atomicAdd(gt + 2 * (uint64_t)idx[c] + 1, w[c] * de1);
+                }
+            }
+        }
+    }
+}
+
+struct GradJob {
+    const float* dl;  // [out][n]
+    const float* x;   // [in][n]
+    float* gw;        // W [out][in] followed by b [out]
+    uint32_t out, in;
+};
+struct GradJobs {
+    GradJob j[kMaxHidden + 1];
+};
+
+__global__ void __launch_bounds__(kGradThreads) k_grad_w(GradJobs jobs, uint64_t n) {
+    const GradJob J = jobs.j[blockIdx.y];
+    __shared__ __align__(16) float ds[kGradChunk][64 + 4];
+    __shared__ __align__(16) float xs[kGradChunk][88 + 4];
+    const int tid = threadIdx.x;
+    const int ot = tid / 22, it = tid % 22;
+    float acc[4][4] = {};
+    for (int k = tid; k < kGradChunk * (64 + 4); k += kGradThreads) (&ds[0][0])[k] = 0.f;
+    for (int k = tid; k < kGradChunk * (88 + 4); k += kGradThreads) (&xs[0][0])[k] = 0.f;
+    const uint64_t n_chunks = (n + kGradChunk - 1) / kGradChunk;
+    for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const uint64_t t0 = c * kGradChunk;
+        __syncthreads();
+        for (int k = tid; k < (int)J.out * kGradChunk; k += kGradThreads) {
+            const int o = k / kGradChunk, tt = k % kGradChunk;
+            ds[tt][o] = t0 + tt < n ? J.dl[(uint64_t)o * n + t0 + tt] : 0.f;
+        }
+        for (int k = tid; k < (int)J.in * kGradChunk; k += kGradThreads) {
+            const int i = k / kGradChunk, tt = k % kGradChunk;
+            xs[tt][i] = t0 + tt < n ? J.x[(uint64_t)i * n + t0 + tt] : 0.f;
+        }
+        for (int tt = tid; tt < kGradChunk; tt += kGradThreads) xs[tt][J.in] = 1.f;  // bias column
+        __syncthreads();
+        if (4 * ot < (int)J.out && 4 * it <= (int)J.in) {
+#pragma unroll 8
+            for (int tt = 0; tt < kGradChunk; ++tt) {
+                const float4 dv = *reinterpret_cast<const float4*>(&ds[tt][4 * ot]);
+                const float4 xv = *reinterpret_cast<const float4*>(&xs[tt][4 * it]);
+                const float da[4] = {dv.x, dv.y, dv.z, dv.w}, xa[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc[a][b] += da[a] * xa[b];
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int o = 4 * ot + a, i = 4 * it + b;
+            if (o < (int)J.out && i <= (int)J.in) {
+                float* dst = i < (int)J.in ? J.gw + (uint64_t)o * J.in + i : J.gw + (uint64_t)J.out * J.in + o;
+                atomicAdd(dst, acc[a][b]);
+            }
+        }
+}
+
+__global__ void k_adam(uint64_t n_params, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ g, float lr, float b1, float b2, float eps, float inv_bc1,
+                       float inv_bc2, __half* __restrict__ hash16, uint64_t hash_off) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_params;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
+        p[i] = pi;
+        if (hash16 && i >= hash_off) hash16[i - hash_off] = __float2half_rn(pi);
+    }
+}
+
+__global__ void k_hash_to_half(uint64_t n, const float* __restrict__ src, __half* __restrict__ dst) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = __float2half_rn(src[i]);
+}
+
+cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st) {
+    if (!h->shape.n_hash || !h->hash16) return cudaSuccess;
+    k_hash_to_half<<<4 * h->num_sms, 256, 0, st>>>(h->shape.n_hash, h->params + h->shape.n_mlp, h->hash16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
+                              uint64_t n, float* d_loss, cudaStream_t st) {
+    const NetShape& s = h->shape;
+    TrainPtrs tp = carve(h->train_scratch, s, n);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->grad, 0, (s.n_mlp + s.n_hash) * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
+    const size_t smem_f = (size_t)s.packed_floats * 4 + (size_t)kTrainThreads * kWidth * 4;
+    const size_t smem_b = (size_t)s.packed_floats * 4;
+    if ((e = cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b)) != cudaSuccess)
+        return e;
+    uint64_t blocks = (n + kTrainThreads - 1) / kTrainThreads;
+    if (blocks > (uint64_t)h->num_sms) blocks = h->num_sms;
+    const float scale = 1.0f / (3.0f * (float)n);
+    const float* table = h->params + s.n_mlp;
+    timer_begin(h, NIRC_K_TRAIN_FWD, st);
+    k_train_fwd<<<(uint32_t)blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
+                                                                 h->packed, table, recs, dirs, targets, n, tp,
+                                                                 h->loss_accum);
+    timer_end(h, NIRC_K_TRAIN_FWD, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    timer_begin(h, NIRC_K_TRAIN_BWD, st);
+    k_train_bwd<<<(uint32_t)blocks, kTrainThreads, smem_b, st>>>(s, h->grid, h->packed, recs, n, tp,
+                                                                 h->grad + s.n_mlp);
+    timer_end(h, NIRC_K_TRAIN_BWD, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    // weight gradients, layer 0 = input layer
+    GradJobs jobs;
+    uint64_t off = 0;
+    for (uint32_t l = 0; l <= s.hidden; ++l) {
+        GradJob& J = jobs.j[l];
+        J.out = l == s.hidden ? 3 : kWidth;
+        J.in = l == 0 ? s.n_in : kWidth;
+        J.dl = l == s.hidden ? tp.dz : tp.delta + (uint64_t)l * kWidth * n;
+        J.x = l == 0 ? tp.e : tp.act + (uint64_t)(l - 1) * kWidth * n;
+        J.gw = h->grad + off;
+        off += (uint64_t)J.out * J.in + J.out;
+    }
+    const uint64_t n_chunks = (n + kGradChunk - 1) / kGradChunk;
+    uint64_t gx = (2ull * h->num_sms + s.hidden) / (s.hidden + 1);
+    if (gx > n_chunks) gx = n_chunks;
+    if (gx < 1) gx = 1;
+    timer_begin(h, NIRC_K_TRAIN_GRADW, st);
+    k_grad_w<<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, n);
+    timer_end(h, NIRC_K_TRAIN_GRADW, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+    h->step += 1;
+    const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
+    const float inv_bc1 = (float)(1.0 / (1.0 - std::pow(b1, (double)h->step)));
+    const float inv_bc2 = (float)(1.0 / (1.0 - std::pow(b2, (double)h->step)));
+    const uint64_t np = s.n_mlp + s.n_hash;
+    timer_begin(h, NIRC_K_ADAM, st);
+    k_adam<<<8 * h->num_sms, 256, 0, st>>>(np, h->params, h->adam_m, h->adam_v, h->grad, h->cfg.lr, h->cfg.beta1,
+                                          h->cfg.beta2, h->cfg.adam_eps, inv_bc1, inv_bc2, h->hash16, s.n_mlp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_repack_simt(h, st);
+    timer_end(h, NIRC_K_ADAM, st);
+    if (e != cudaSuccess) return e;
+    if (d_loss) {
+        if ((e = cudaMemcpyAsync(d_loss, h->loss_accum, sizeof(float), cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace nirc

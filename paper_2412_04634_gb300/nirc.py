@@ -1,0 +1,270 @@
+"""Thin ctypes binding of libnirc.so (include/nirc.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch CUDA tensors for device buffers (passed as raw pointers) and a torch
+stream (defaults to the current stream).  All arithmetic runs in the
+library's CUDA kernels; importing this module loads the library and raises
+if it has not been built (``python -m paper_2412_04634_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import scenes
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnirc.so")
+
+NIRC_OK, NIRC_ERR_INVALID, NIRC_ERR_OOM, NIRC_ERR_BUDGET, NIRC_ERR_CUDA, NIRC_ERR_TIMEOUT, NIRC_ERR_UNSUPPORTED = range(7)
+NIRC_FP32_SIMT, NIRC_FP16_TC, NIRC_BF16_TC, NIRC_FP8_E4M3_TC = range(4)
+NIRC_MAX_PRIMS = 1024
+
+
+class NircError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[nirc status {status}] {msg}")
+        self.status = status
+
+
+class nirc_config(ctypes.Structure):
+    _fields_ = [
+        ("pos_encoding", ctypes.c_uint32), ("hash_levels", ctypes.c_uint32),
+        ("feats_per_level", ctypes.c_uint32), ("log2_table", ctypes.c_uint32),
+        ("base_res", ctypes.c_uint32), ("growth", ctypes.c_float),
+        ("freq_octaves", ctypes.c_uint32), ("width", ctypes.c_uint32),
+        ("hidden_layers", ctypes.c_uint32), ("precision", ctypes.c_uint32),
+        ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+        ("adam_eps", ctypes.c_float), ("loss_eps", ctypes.c_float), ("z_clamp", ctypes.c_float),
+    ]
+
+
+class nirc_frame_desc(ctypes.Structure):
+    _fields_ = [
+        ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+        ("n_cache", ctypes.c_uint32), ("n_resid", ctypes.c_uint32),
+        ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64), ("n_prims", ctypes.c_uint32),
+        ("cache_mode", ctypes.c_uint32), ("cache_const", ctypes.c_float * 3),
+        ("pad", ctypes.c_uint32),
+    ]
+
+
+class nirc_frame_aux(ctypes.Structure):
+    _fields_ = [("lc", ctypes.c_void_p), ("lr", ctypes.c_void_p),
+                ("sig", ctypes.c_void_p), ("count", ctypes.c_void_p)]
+
+
+K_CLASSES = ["path_trace", "cache", "train_records", "train_fwd", "train_bwd", "train_gradw", "adam", "query"]
+
+
+class nirc_timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2412_04634_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "nirc_param_count": ([P], u64),
+        "nirc_create": ([P, P], st),
+        "nirc_destroy": ([P], st),
+        "nirc_set_params": ([P, P, i32, P], st),
+        "nirc_get_params": ([P, P, i32, P], st),
+        "nirc_get_grads": ([P, P, i32, P], st),
+        "nirc_set_precision": ([P, u32], st),
+        "nirc_query": ([P, P, P, u64, P, P], st),
+        "nirc_estimate_frame": ([P, P, P, P, P, P], st),
+        "nirc_gen_train": ([P, P, u32, u32, u32, u64, u32, u64, u32, P, P, P, P], st),
+        "nirc_train_step": ([P, P, P, P, u64, P, P], st),
+        "nirc_frame_mrse": ([P, P, u64, ctypes.c_float, P, P], st),
+        "nirc_timing_enable": ([P, i32], st),
+        "nirc_timing_read": ([P, P], st),
+        "nirc_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def exported_symbols():
+    return [n for n in dir(_lib) if n.startswith("nirc_")]
+
+
+def _check(status: int):
+    if status != NIRC_OK:
+        raise NircError(status, _lib.nirc_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensor must be contiguous"
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_config(cfg: scenes.NetConfig, precision: int = NIRC_FP32_SIMT) -> nirc_config:
+    return nirc_config(cfg.pos_encoding, cfg.hash_levels, cfg.feats_per_level, cfg.log2_table, cfg.base_res,
+                       cfg.growth, cfg.freq_octaves, cfg.width, cfg.hidden_layers, precision,
+                       cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps, cfg.loss_eps, cfg.z_clamp)
+
+
+def frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode=0,
+               cache_const=(0.0, 0.0, 0.0)) -> nirc_frame_desc:
+    d = nirc_frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode)
+    for k in range(3):
+        d.cache_const[k] = float(cache_const[k])
+    return d
+
+
+# --- entry points (same names as the C ABI) ----------------------------------
+
+def nirc_param_count(cfg: nirc_config) -> int:
+    return int(_lib.nirc_param_count(ctypes.byref(cfg)))
+
+
+def nirc_create(cfg: nirc_config):
+    h = ctypes.c_void_p()
+    _check(_lib.nirc_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def nirc_destroy(h):
+    _check(_lib.nirc_destroy(h))
+
+
+def nirc_set_params(h, params: torch.Tensor, stream=None):
+    on_dev = 1 if params.is_cuda else 0
+    p = params.contiguous()
+    _check(_lib.nirc_set_params(h, _ptr(p), on_dev, _stream(stream)))
+
+
+def nirc_get_params(h, out: torch.Tensor, stream=None):
+    _check(_lib.nirc_get_params(h, _ptr(out), 1 if out.is_cuda else 0, _stream(stream)))
+
+
+def nirc_get_grads(h, out: torch.Tensor, stream=None):
+    _check(_lib.nirc_get_grads(h, _ptr(out), 1 if out.is_cuda else 0, _stream(stream)))
+
+
+def nirc_set_precision(h, precision: int):
+    _check(_lib.nirc_set_precision(h, precision))
+
+
+def nirc_query(h, records: torch.Tensor, dirs: torch.Tensor, out: torch.Tensor, stream=None):
+    n = dirs.shape[0]
+    _check(_lib.nirc_query(h, _ptr(records), _ptr(dirs), n, _ptr(out), _stream(stream)))
+
+
+def nirc_estimate_frame(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba: torch.Tensor,
+                        lc=None, lr=None, sig=None, count=None, stream=None):
+    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count))
+    use_aux = any(x is not None for x in (lc, lr, sig, count))
+    _check(_lib.nirc_estimate_frame(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
+                                    ctypes.byref(aux) if use_aux else None, _stream(stream)))
+
+
+def nirc_gen_train(h, scene: torch.Tensor, n_prims, width, height, T, frame, seed, max_depth,
+                   records: torch.Tensor, dirs: torch.Tensor, targets: torch.Tensor, stream=None):
+    _check(_lib.nirc_gen_train(h, _ptr(scene), n_prims, width, height, T, frame, seed, max_depth,
+                               _ptr(records), _ptr(dirs), _ptr(targets), _stream(stream)))
+
+
+def nirc_train_step(h, records: torch.Tensor, dirs: torch.Tensor, targets: torch.Tensor, loss=None, stream=None):
+    n = dirs.shape[0]
+    _check(_lib.nirc_train_step(h, _ptr(records), _ptr(dirs), _ptr(targets), n, _ptr(loss), _stream(stream)))
+
+
+def nirc_frame_mrse(img: torch.Tensor, ref: torch.Tensor, out: torch.Tensor, eps: float = 1e-2, stream=None):
+    n = img.numel() // 4
+    _check(_lib.nirc_frame_mrse(_ptr(img), _ptr(ref), n, eps, _ptr(out), _stream(stream)))
+
+
+def nirc_timing_enable(h, enable: bool = True):
+    _check(_lib.nirc_timing_enable(h, 1 if enable else 0))
+
+
+def nirc_timing_read(h) -> dict:
+    """{class: (total ms, launches)} since the last enable."""
+    t = nirc_timing()
+    _check(_lib.nirc_timing_read(h, ctypes.byref(t)))
+    return {name: (t.ms[i], int(t.launches[i])) for i, name in enumerate(K_CLASSES)}
+
+
+# --- convenience ----------------------------------------------------------------
+
+def records_to_tensor(recs, device="cuda") -> torch.Tensor:
+    """Structured numpy records (scenes.RECORD_DTYPE) -> (n, 16) float32 device tensor (64 B rows)."""
+    import numpy as np
+    raw = np.ascontiguousarray(recs).view(np.float32).reshape(-1, 16)
+    return torch.from_numpy(raw.copy()).to(device)
+
+
+def records_from_tensor(t: torch.Tensor):
+    import numpy as np
+    raw = t.detach().cpu().contiguous().numpy().astype(np.float32, copy=False)
+    return raw.view(scenes.RECORD_DTYPE).reshape(-1)
+
+
+def scene_to_tensor(scene: scenes.Scene, device="cuda") -> torch.Tensor:
+    """Scene blob as a 16-byte aligned uint8 device tensor."""
+    blob = scene.blob()
+    return torch.from_numpy(blob.copy()).to(device)
+
+
+class Cache:
+    """Owning wrapper of a nirc_handle."""
+
+    def __init__(self, cfg: scenes.NetConfig, precision: int = NIRC_FP32_SIMT):
+        self.cfg = cfg
+        self.ccfg = make_config(cfg, precision)
+        self.h = nirc_create(self.ccfg)
+        self.n_params = nirc_param_count(self.ccfg)
+
+    def close(self):
+        if self.h is not None:
+            nirc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params, stream=None):
+        t = params if isinstance(params, torch.Tensor) else torch.from_numpy(params)
+        assert t.numel() == self.n_params
+        nirc_set_params(self.h, t.float().contiguous(), stream)
+
+    def get_params(self) -> torch.Tensor:
+        out = torch.empty(self.n_params, dtype=torch.float32)
+        nirc_get_params(self.h, out)
+        return out
+
+    def get_grads(self) -> torch.Tensor:
+        out = torch.empty(self.n_params, dtype=torch.float32)
+        nirc_get_grads(self.h, out)
+        return out

@@ -78,6 +78,8 @@ class Scene:
     prims: np.ndarray    # PRIM_DTYPE, shape (n,)
     width: int
     height: int
+    emitter_phase: float = 0.0
+    moving_emitter: bool = False
 
     def blob(self) -> np.ndarray:
         """Header followed by primitives, as a uint8 array."""
@@ -231,7 +233,24 @@ def cornell_scene(width: int, height: int, seed: int = 1, n_prims: int = 8,
                 _fill_rect(prims[i], corner, u, v, albedo(), rough(), mat)
 
     cam = _camera((0.5, 0.5, -1.2), 40.0, width, height)
-    return Scene(_header(n_prims, cam), prims, width, height)
+    sc = Scene(_header(n_prims, cam), prims, width, height)
+    sc.emitter_phase = phase
+    sc.moving_emitter = moving_emitter
+    return sc
+
+
+def scene_at_frame(scene: Scene, frame: int) -> Scene:
+    """Copy of a Cornell scene with the emitter moved to its position at
+    ``frame`` (the dynamic-scene workload); other primitives unchanged."""
+    prims = scene.prims.copy()
+    cx, cy, cz = emitter_centre(frame, scene.emitter_phase, scene.moving_emitter)
+    h = EMITTER_SIZE / 2.0
+    _fill_rect(prims[5], (cx - h, cy, cz - h), (EMITTER_SIZE, 0, 0), (0, 0, EMITTER_SIZE),
+               (0, 0, 0), 1.0, MAT_BLACK, emission=(EMITTER_RADIANCE,) * 3)
+    out = Scene(scene.header.copy(), prims, scene.width, scene.height)
+    out.emitter_phase = scene.emitter_phase
+    out.moving_emitter = scene.moving_emitter
+    return out
 
 
 def furnace_scene(width: int, height: int, rho: float = 0.5, emission: float = 1.0) -> Scene:

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Element by element on the same seeded inputs: integer work (hit primitives,
+sample counts, decision signatures, record bits) bit-exact; floating point
+within 1e-4 relative per output for the FP32 path, the relative error of a
+pixel being |a - b| / max(|b|, 1e-3 mean|b|) so that values that cancel to
+near zero are measured against the image scale.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2412_04634_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def N():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_04634_gb300 import build
+    build.build()
+    from paper_2412_04634_gb300 import nirc
+    return nirc
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    floor = 1e-3 * max(np.abs(b).mean(), 1e-30)
+    return np.abs(a - b) / np.maximum(np.abs(b), floor)
+
+
+def _hash_cfg():
+    return scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=16, log2_table=14, hidden_layers=4,
+                            lr=1e-2)
+
+
+def _run_frame(N, cfg, params, scene, W, H, Nc, M, D, frame, seed, cache_mode=0, cache_const=(0, 0, 0)):
+    import torch
+    cache = N.Cache(cfg)
+    if params is not None:
+        cache.set_params(params)
+    sc = N.scene_to_tensor(scene)
+    P = W * H
+    out = torch.empty((P, 4), device="cuda")
+    lc = torch.empty((P, 3), device="cuda")
+    lr = torch.empty((P, 3), device="cuda")
+    sig = torch.empty((P, 2), device="cuda", dtype=torch.int64)
+    cnt = torch.empty(P, device="cuda", dtype=torch.int32)
+    desc = N.frame_desc(W, H, Nc, M, D, frame, seed, scene.n_prims, cache_mode, cache_const)
+    N.nirc_estimate_frame(cache.h, sc, desc, out, lc, lr, sig, cnt)
+    torch.cuda.synchronize()
+    cache.close()
+    return dict(pixel=out[:, :3].cpu().numpy(), alpha=out[:, 3].cpu().numpy(), lc=lc.cpu().numpy(),
+                lr=lr.cpu().numpy(), sig=sig.cpu().numpy().view(np.uint64), count=cnt.cpu().numpy().view(np.uint32))
+
+
+def _compare_frames(g, o):
+    assert np.array_equal(g["sig"][:, 0], o["sig"][:, 0]), "path decision signatures differ"
+    assert np.array_equal(g["sig"][:, 1], o["sig"][:, 1]), "cache sample signatures differ"
+    assert np.array_equal(g["count"], o["count"])
+    for key in ("pixel", "lc", "lr"):
+        err = rel_err(g[key], o[key])
+        assert err.max() <= FP32_TOL, (key, err.max(), np.unravel_index(err.argmax(), err.shape))
+    assert np.all(g["alpha"] == 1.0)
+
+
+# ---------------------------------------------------------------------------
+# cache queries
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["freq", "hash"])
+@pytest.mark.parametrize("n", [1, 127, 129, 300, 5000])
+def test_query_matches_oracle(N, oracle, which, n):
+    import torch
+    cfg = scenes.config_small() if which == "freq" else _hash_cfg()
+    params = scenes.init_params(cfg, 3)
+    rng = np.random.default_rng(n)
+    params[:cfg.n_mlp_params] += rng.normal(0, 0.05, cfg.n_mlp_params).astype(np.float32)
+    if cfg.n_hash_params:
+        params[cfg.n_mlp_params:] = rng.uniform(-1, 1, cfg.n_hash_params).astype(np.float32)
+    recs, dirs = scenes.random_query_rows(n, seed=n)
+    cache = N.Cache(cfg)
+    cache.set_params(params)
+    out = torch.empty((n, 3), device="cuda")
+    N.nirc_query(cache.h, N.records_to_tensor(recs), torch.from_numpy(dirs).cuda(), out)
+    got = out.cpu().numpy()
+    ref = oracle.query(cfg, params, recs, dirs)
+    err = np.abs(got - ref) / np.abs(ref)
+    assert err.max() <= FP32_TOL, err.max()
+
+
+# ---------------------------------------------------------------------------
+# two-level frame estimate
+# ---------------------------------------------------------------------------
+
+def test_frame_small_workload(N, oracle):
+    """64x64 Cornell box, frequency encoding, N = 8, M = 1, depth 4."""
+    cfg = scenes.config_small()
+    params = scenes.init_params(cfg, 1)
+    sc = scenes.cornell_scene(64, 64, seed=1)
+    for frame in (0, 3):
+        g = _run_frame(N, cfg, params, sc, 64, 64, 8, 1, 4, frame, 1)
+        o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(64, 64, 8, 1, 4, frame, 1))
+        _compare_frames(g, o)
+
+
+def test_frame_glossy_hashgrid(N, oracle):
+    """256-primitive glossy scene with the hash-grid cache at 96x54, N = 16, M = 1, depth 5."""
+    cfg = _hash_cfg()
+    params = scenes.init_params(cfg, 2)
+    params[cfg.n_mlp_params:] = np.random.default_rng(0).uniform(-0.5, 0.5, cfg.n_hash_params).astype(np.float32)
+    sc = scenes.cornell_scene(96, 54, seed=1, n_prims=256, glossy=True, moving_emitter=True, frame=7)
+    g = _run_frame(N, cfg, params, sc, 96, 54, 16, 1, 5, 7, 1)
+    o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(96, 54, 16, 1, 5, 7, 1))
+    _compare_frames(g, o)
+
+
+@pytest.mark.parametrize("W,H,Nc,M", [(1, 1, 8, 1), (3, 5, 4, 2), (17, 9, 0, 3), (16, 16, 5, 0), (33, 7, 64, 4)])
+def test_frame_edge_shapes(N, oracle, W, H, Nc, M):
+    cfg = scenes.config_small()
+    params = scenes.init_params(cfg, 5)
+    sc = scenes.cornell_scene(W, H, seed=2)
+    g = _run_frame(N, cfg, params, sc, W, H, Nc, M, 4, 1, 9)
+    o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(W, H, Nc, M, 4, 1, 9))
+    _compare_frames(g, o)
+
+
+def test_zero_and_constant_cache_modes(N, oracle):
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(32, 32, seed=1)
+    g = _run_frame(N, cfg, None, sc, 32, 32, 8, 2, 6, 0, 4, cache_mode=1)
+    o = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(32, 32, 8, 2, 6, 0, 4, cache_mode=1))
+    _compare_frames(g, o)
+    assert np.all(g["lc"] == 0)
+    L = (1.5, 2.0, 3.0)
+    g = _run_frame(N, cfg, None, sc, 32, 32, 8, 1, 4, 0, 4, cache_mode=2, cache_const=L)
+    o = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(32, 32, 8, 1, 4, 0, 4, cache_mode=2, cache_const=L))
+    _compare_frames(g, o)
+
+
+def test_furnace_scene(N, oracle):
+    cfg = scenes.config_small()
+    sc = scenes.furnace_scene(48, 48, rho=0.5, emission=1.0)
+    g = _run_frame(N, cfg, None, sc, 48, 48, 4, 1, 64, 0, 3, cache_mode=2, cache_const=(2.0, 2.0, 2.0))
+    o = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(48, 48, 4, 1, 64, 0, 3, cache_mode=2,
+                                                            cache_const=(2.0, 2.0, 2.0)))
+    _compare_frames(g, o)
+    assert np.allclose(g["lc"], 1.0, rtol=1e-6)
+
+
+def test_full_size_sampled_pixels(N, oracle):
+    """1920x1080, 256 primitives, hash grid (2^19 entries), N = 16, M = 1,
+    depth 5: the launch the benchmark times, checked on sampled pixels."""
+    import torch
+    cfg = scenes.config_1080p()
+    params = scenes.init_params(cfg, 1)
+    rng = np.random.default_rng(1)
+    params[cfg.n_mlp_params:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params).astype(np.float32)
+    W, H = 1920, 1080
+    sc = scenes.cornell_scene(W, H, seed=1, n_prims=256, glossy=True, moving_emitter=True, frame=11)
+    g = _run_frame(N, cfg, params, sc, W, H, 16, 1, 5, 11, 1)
+    pix = np.unique(np.concatenate([rng.integers(0, W * H, 400), [0, W - 1, W * H - 1, (H // 2) * W + W // 2]]))
+    o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(W, H, 16, 1, 5, 11, 1), pixels=pix.astype(np.uint32))
+    sub = {k: v[pix] for k, v in g.items()}
+    _compare_frames(sub, o)
+
+
+# ---------------------------------------------------------------------------
+# training records, training step, metrics
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["small", "glossy"])
+def test_gen_train_matches_oracle(N, oracle, which):
+    import torch
+    if which == "small":
+        cfg, sc, W, H, D = scenes.config_small(), scenes.cornell_scene(64, 64, seed=1), 64, 64, 4
+    else:
+        W, H, D = 160, 90, 5
+        cfg, sc = _hash_cfg(), scenes.cornell_scene(W, H, seed=1, n_prims=256, glossy=True, moving_emitter=True)
+    T = 4099
+    cache = N.Cache(cfg)
+    recs = torch.empty((T, 16), device="cuda")
+    dirs = torch.empty((T, 3), device="cuda")
+    tg = torch.empty((T, 3), device="cuda")
+    N.nirc_gen_train(cache.h, N.scene_to_tensor(sc), sc.n_prims, W, H, T, 2, 1, D, recs, dirs, tg)
+    orec, odir, otg, _ = oracle.gen_train(sc.blob(), W, H, T, 2, 1, D, scenes.RECORD_DTYPE)
+    grec = N.records_from_tensor(recs)
+    assert np.array_equal(grec.view(np.uint8), orec.view(np.uint8)), "training records differ"
+    assert np.array_equal(dirs.cpu().numpy().view(np.uint32), odir.view(np.uint32)), "training directions differ"
+    err = rel_err(tg.cpu().numpy(), otg)
+    assert err.max() <= FP32_TOL, err.max()
+    cache.close()
+
+
+@pytest.mark.parametrize("which", ["freq", "hash"])
+def test_train_step_matches_oracle(N, oracle, which):
+    import torch
+    cfg = scenes.config_small() if which == "freq" else _hash_cfg()
+    params = scenes.init_params(cfg, 4)
+    n = 3000
+    recs, dirs, tg = scenes.training_batch(n, seed=21)
+    recs["flags"][::17] = 0  # some invalid records
+    cache = N.Cache(cfg)
+    cache.set_params(params)
+    loss = torch.zeros(1, device="cuda")
+    N.nirc_train_step(cache.h, N.records_to_tensor(recs), torch.from_numpy(dirs).cuda(),
+                      torch.from_numpy(tg).cuda(), loss)
+    torch.cuda.synchronize()
+    g_gpu = cache.get_grads().numpy().astype(np.float64)
+    p_gpu = cache.get_params().numpy().astype(np.float64)
+    loss_or, g_or = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    assert abs(loss.item() - loss_or) <= 1e-5 * abs(loss_or)
+    for lo, hi in ((0, cfg.n_mlp_params), (cfg.n_mlp_params, cfg.n_params)):
+        if hi <= lo:
+            continue
+        scale = np.abs(g_or[lo:hi]).max()
+        assert np.abs(g_gpu[lo:hi] - g_or[lo:hi]).max() <= FP32_TOL * scale
+    # one Adam step (lr, beta1 0.9, beta2 0.99, eps 1e-15)
+    p_or = params.astype(np.float64)
+    m = np.zeros_like(p_or)
+    v = np.zeros_like(p_or)
+    oracle.adam_step(p_or, m, v, g_or, 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps)
+    strong = np.abs(g_or) > 1e-3 * np.abs(g_or).max()
+    assert np.abs(p_gpu[strong] - p_or[strong]).max() <= 1e-6 + 1e-5 * cfg.lr
+    # weak gradients: the step can be +-lr (sign at rounding level) but never more
+    assert np.all(np.abs(p_gpu - params) <= cfg.lr * (1 + 1e-5) + 1e-7)
+    untouched = g_or == 0
+    assert np.array_equal(p_gpu[untouched], params[untouched].astype(np.float64))
+    cache.close()
+
+
+def test_mrse_matches_oracle(N, oracle):
+    import torch
+    rng = np.random.default_rng(3)
+    n = 100003
+    img = rng.uniform(0, 2, (n, 4)).astype(np.float32)
+    ref = rng.uniform(0, 2, (n, 4)).astype(np.float32)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    N.nirc_frame_mrse(torch.from_numpy(img).cuda(), torch.from_numpy(ref).cuda(), out)
+    want = oracle.mrse(img[:, :3].astype(np.float64), ref[:, :3].astype(np.float64), 1e-2)
+    assert abs(out.item() - want) <= 1e-12 * want
