@@ -133,12 +133,16 @@ typedef struct nirc_frame_desc {
  * may be NULL): lc, lr = the two levels (W*H x 3 floats); sig = two 64-bit
  * FNV-1a signatures per pixel of the discrete decisions (path: primary hit,
  * residual directions, hits, Russian roulette; cache: cache-direction
- * rejection counts and lobes); count = valid (active) samples per pixel. */
+ * rejection counts and lobes); count = valid (active) samples per pixel;
+ * row_n = the cache value n of every row, W*H*(N+M) x 3 floats in pixel-major,
+ * sample-minor order (cache samples first), 0 for rows whose sample is
+ * invalid (network mode only). */
 typedef struct nirc_frame_aux {
     float* lc;
     float* lr;
     uint64_t* sig;
     uint32_t* count;
+    float* row_n;
 } nirc_frame_aux;
 
 typedef struct nirc_handle nirc_handle;
@@ -163,8 +167,17 @@ nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, 
 nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* stream);
 /* Copy out the gradient of the last nirc_train_step (same layout). */
 nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stream);
-/* Select the layer arithmetic for later calls (nirc_precision). */
+/* Select the layer arithmetic for later calls (nirc_precision).  The
+ * tensor-core modes apply to the cache integral of nirc_estimate_frame when
+ * the network is used (cache_mode 0) and N + M >= 4; other work (queries,
+ * training, the other cache modes) runs the FP32 kernels.  Synchronises the
+ * legacy default stream.  FP8_E4M3_TC returns NIRC_ERR_UNSUPPORTED. */
 nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision);
+
+/* Wait for `stream` and report device-side failures of the handle's
+ * kernels: NIRC_ERR_TIMEOUT if a tensor-core kernel's bounded wait for an
+ * MMA ran out (about 2 s; that launch's output is invalid). */
+nirc_status nirc_sync(nirc_handle* h, void* stream);
 
 /* Bare cache queries (eq. 11's n_i): d_out_rgb[i] = n(record_i, dir_i),
  * n rows, d_dirs = n x 3 unit world directions, d_out_rgb = n x 3. */

@@ -764,8 +764,11 @@ static void cache_value(const o_cfg* c, const double* params, const o_frame* fd,
 
 static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
                            uint32_t pix, double out[3], double lc_out[3], double lr_out[3], uint64_t sig[2],
-                           uint32_t* count)
+                           uint32_t* count, double* row_n)
 {
+    /* row_n (optional): cache value of each of the N + M rows, 0 for rows
+     * whose sample is invalid or whose pixel has no camera hit */
+    if (row_n) memset(row_n, 0, 3 * sizeof(double) * (fd->n_cache + fd->n_resid));
     const o_header* hd = (const o_header*)blob;
     const o_prim* prims = scene_prims(blob);
     uint32_t k0 = (uint32_t)fd->seed, k1 = fd->frame;
@@ -796,6 +799,8 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             double nv[3];
             cache_value(c, params, fd, &rec, s.wi, nv);
             for (int k = 0; k < 3; k++) Lc[k] += s.w[k] * nv[k];
+            if (row_n)
+                for (int k = 0; k < 3; k++) row_n[3 * i + k] = nv[k];
             active++;
         }
         if (fd->n_cache) for (int k = 0; k < 3; k++) Lc[k] /= (double)fd->n_cache;
@@ -809,6 +814,8 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             trace_path(blob, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, Li, &sp);
             cache_value(c, params, fd, &rec, s.wi, nv);
             for (int k = 0; k < 3; k++) Lr[k] += s.w[k] * (Li[k] - nv[k]);
+            if (row_n)
+                for (int k = 0; k < 3; k++) row_n[3 * (fd->n_cache + j) + k] = nv[k];
             active++;
         }
         if (fd->n_resid) for (int k = 0; k < 3; k++) Lr[k] /= (double)fd->n_resid;
@@ -829,13 +836,14 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
  * indexed by position in the list; optional outputs may be NULL. */
 void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
                          const uint32_t* pixels, uint64_t n, double* out, double* lc, double* lr, uint64_t* sig,
-                         uint32_t* count)
+                         uint32_t* count, double* row_n)
 {
+    const uint64_t S = (uint64_t)fd->n_cache + fd->n_resid;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < (int64_t)n; i++) {
         uint32_t pix = pixels ? pixels[i] : (uint32_t)i;
         estimate_pixel(c, params, blob, fd, pix, out + 3 * i, lc ? lc + 3 * i : NULL, lr ? lr + 3 * i : NULL,
-                       sig ? sig + 2 * i : NULL, count ? count + i : NULL);
+                       sig ? sig + 2 * i : NULL, count ? count + i : NULL, row_n ? row_n + 3 * S * i : NULL);
     }
 }
 

@@ -54,7 +54,7 @@ def lib():
         L.orc_encode.argtypes = [P, P, P, P, P]
         L.orc_mlp.argtypes = [P, P, P, P]
         L.orc_query.argtypes = [P, P, P, P, u64, P]
-        L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P]
+        L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P, P]
         L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, P, P, P, P]
         L.orc_train_loss_grad.argtypes = [P, P, P, P, P, u64, P, P]
         L.orc_train_loss_grad.restype = f64
@@ -154,9 +154,10 @@ def query(cfg, params, recs, dirs) -> np.ndarray:
     return out
 
 
-def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None):
+def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None, rows=False):
     """Two-level estimate of the listed pixels (all when None).
-    Returns dict(pixel, lc, lr (n,3) f64; sig (n,2) u64; count (n,) u32)."""
+    Returns dict(pixel, lc, lr (n,3) f64; sig (n,2) u64; count (n,) u32;
+    with rows=True also row_n (n, N+M, 3) f64, the cache value of each row)."""
     c = ocfg(cfg)
     p = _params64(params) if params is not None else np.zeros(1, np.float64)
     blob = np.ascontiguousarray(scene_blob, np.uint8)
@@ -172,9 +173,14 @@ def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None):
     lr = np.zeros((n, 3), np.float64)
     sig = np.zeros((n, 2), np.uint64)
     cnt = np.zeros(n, np.uint32)
+    row_n = np.zeros((n, frame.n_cache + frame.n_resid, 3), np.float64) if rows else None
     lib().orc_estimate_pixels(ctypes.byref(c), _ptr(p), _ptr(blob), ctypes.byref(frame), pix_ptr, n,
-                              _ptr(out), _ptr(lc), _ptr(lr), _ptr(sig), _ptr(cnt))
-    return dict(pixel=out, lc=lc, lr=lr, sig=sig, count=cnt)
+                              _ptr(out), _ptr(lc), _ptr(lr), _ptr(sig), _ptr(cnt),
+                              None if row_n is None else _ptr(row_n))
+    res = dict(pixel=out, lc=lc, lr=lr, sig=sig, count=cnt)
+    if rows:
+        res["row_n"] = row_n
+    return res
 
 
 def gen_train(scene_blob, width, height, T, frame, seed, max_depth, record_dtype):

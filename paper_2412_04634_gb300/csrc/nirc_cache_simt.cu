@@ -43,8 +43,8 @@ __device__ __forceinline__ float3 row_mlp(const NetShape& s, const float* __rest
     float th, ph;
     dir_angles(wi, th, ph);
     float e[16];
-    freq4(th, e);
-    freq4(ph, e + 8);
+    freq4_accurate(th, e);
+    freq4_accurate(ph, e + 8);
     float2 acc[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = hpix[q];
@@ -79,7 +79,8 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
     k_cache_simt(CacheArgs a, const float* __restrict__ packed, const float* __restrict__ table,
                  const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
                  const ResidRow* __restrict__ rows, float4* __restrict__ out, float* __restrict__ lc_out,
-                 float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count) {
+                 float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
+                 float* __restrict__ row_n) {
     extern __shared__ __align__(16) float smem[];
     float* sw = smem;
     float* act = smem + a.s.packed_floats + threadIdx.x;
@@ -136,14 +137,17 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
                 w = make_float3(ww.x, ww.y, ww.z);
                 ok = valid && d.w != 0.f;
             }
-            float3 nv;
+            float3 nv = make_float3(0.f, 0.f, 0.f);
             if (network) {
-                if (!__any_sync(0xffffffffu, ok)) continue;
-                nv = row_mlp(a.s, sw, act, stride, hpix, wi, a.z_clamp);
+                if (__any_sync(0xffffffffu, ok)) nv = row_mlp(a.s, sw, act, stride, hpix, wi, a.z_clamp);
             } else if (a.cache_mode == 2) {
                 nv = make_float3(a.cc0, a.cc1, a.cc2);
-            } else {
-                nv = make_float3(0.f, 0.f, 0.f);
+            }
+            if (row_n && in_range) {
+                float* rn = row_n + 3 * ((uint64_t)pix * S + r);
+                rn[0] = ok ? nv.x : 0.f;
+                rn[1] = ok ? nv.y : 0.f;
+                rn[2] = ok ? nv.z : 0.f;
             }
             if (!ok) continue;
             const float3 t = make_float3(w.x * nv.x, w.y * nv.y, w.z * nv.z);
@@ -254,7 +258,7 @@ static size_t simt_smem(const NetShape& s) {
 
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                               const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
-                              uint64_t* sig, uint32_t* count, cudaStream_t st) {
+                              uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st) {
     CacheArgs a;
     a.W = fd.width;
     a.H = fd.height;
@@ -275,10 +279,10 @@ cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, c
     const uint64_t P = (uint64_t)fd.width * fd.height;
     uint64_t blocks = (P + kSimtThreads - 1) / kSimtThreads;
     if (blocks > 2ull * h->num_sms) blocks = 2ull * h->num_sms;
-    const float* table = h->params + h->shape.n_mlp;
+    const float* table = h->params + h->shape.hash_off;
     k_cache_simt<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(a, h->packed, table, recs, base, rows,
                                                                reinterpret_cast<float4*>(out_rgba), lc, lr, sig,
-                                                               count);
+                                                               count, row_n);
     return cudaGetLastError();
 }
 
@@ -289,7 +293,7 @@ cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, con
     if (e != cudaSuccess) return e;
     uint64_t blocks = (n + kSimtThreads - 1) / kSimtThreads;
     if (blocks > 2ull * h->num_sms) blocks = 2ull * h->num_sms;
-    const float* table = h->params + h->shape.n_mlp;
+    const float* table = h->params + h->shape.hash_off;
     k_query_simt<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(h->shape, h->grid, h->cfg.z_clamp, h->packed, table,
                                                                recs, dirs, n, out);
     return cudaGetLastError();

@@ -1,0 +1,595 @@
+// nirc_cache_tc.cu -- tensor-core (tcgen05, TMEM accumulators) evaluation of
+// the cache integral, FP16 or BF16 operands with FP32 accumulation.
+//
+// Work unit: a block of 128 pixels; with S = N + M rows per pixel it holds
+// exactly S row tiles of 128 rows.  One warpgroup (128 threads, thread t =
+// tile row t = TMEM lane t) owns a block at a time; a CTA runs several
+// warpgroups so that one warpgroup's SIMT work (sampling, encodings,
+// epilogues) overlaps another's MMAs.
+//
+//  pixel stage   thread t encodes pixel t's surface (hash grid or frequency
+//                position features + normal features) into an A tile; one
+//                128x64x64 MMA with the surface columns of layer 0 gives
+//                h_pix = W0[:, pix] e_pix + b0 for the 128 pixels, stored as a
+//                16-bit K-major operand H (K = pixel index).  This is the
+//                paper's shared per-surface encoding: computed once per
+//                shading point and reused by all its N + M rows.
+//  row tile      thread t samples its row's direction (cache rows) or reads
+//                it (residual rows), encodes it and writes the A row
+//                [e_dir (16) | one-hot of its pixel relative to k0 (48)];
+//                layer 0 = W0_dir e_dir + H onehot (1 + up to 3 MMAs, K = 16
+//                each), then the hidden layers (4 MMAs each) and the output
+//                layer (N = 16, 3 used); each epilogue reads its row from
+//                TMEM, adds the bias, applies ReLU, rounds to 16 bits and
+//                writes the next A tile in shared memory.  The network input
+//                and output never touch global memory.
+//  reduction     per-row contributions w * n go to shared memory; one thread
+//                per pixel sums its rows in sample order (compensated FP32),
+//                carrying a pixel that straddles two tiles, and writes the
+//                pixel (eq. L_mlmc = L_e + L_c + L_r).
+//
+// Every mbarrier wait is bounded (about 2 s); a timeout sets *err, stops
+// further MMAs of that warpgroup and the kernel still frees its TMEM.
+#include "nirc_internal.h"
+#include "nirc_tc.cuh"
+
+namespace nirc {
+
+namespace tcimg {
+// Tensor-core weight image: 16-bit K-major swizzled matrices, then FP32 biases.
+__host__ __device__ inline uint32_t off_w0pix() { return 0; }
+__host__ __device__ inline uint32_t off_w0dir() { return 8192; }
+__host__ __device__ inline uint32_t off_wh(uint32_t l) { return 16384 + 8192 * l; }
+__host__ __device__ inline uint32_t off_wout(uint32_t hidden) { return 16384 + 8192 * (hidden - 1); }
+__host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_wout(hidden) + 2048; }
+__host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidden - 1) * 64 + 16; }
+}  // namespace tcimg
+
+size_t tc_image_bytes(uint32_t hidden) { return tcimg::off_bias(hidden) + tcimg::n_bias(hidden) * 4; }
+
+constexpr uint32_t kWgStride = 44032;  // A 16 KB | H 16 KB | records 8 KB | contributions 2 KB | carry 64 B
+constexpr uint32_t kOffA = 0, kOffH = 16384, kOffRec = 32768, kOffContrib = 40960, kOffCarry = 43008;
+
+template <uint32_t AB>
+__global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_t* __restrict__ img) {
+    const uint32_t H = s.hidden;
+    const uint32_t n_mat = 64 * 64 * (2 + (H - 1)) + 16 * 64;
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t n_in = s.n_in;
+    if (idx < n_mat) {
+        uint32_t m = idx / 4096, r = idx % 4096;
+        uint32_t n = r / 64, k = r % 64;
+        float v = 0.f;
+        uint32_t off;
+        if (m == 0) {  // surface columns of layer 0: [pos][nrm] -> master columns [pos][dir][nrm]
+            off = tcimg::off_w0pix();
+            if (k < s.n_pos) v = params[n * n_in + k];
+            else if (k < s.n_pix) v = params[n * n_in + k + kDirFeatures];
+        } else if (m == 1) {  // direction columns of layer 0
+            off = tcimg::off_w0dir();
+            if (k < kDirFeatures) v = params[n * n_in + s.n_pos + k];
+        } else if (m < 2 + (H - 1)) {
+            const uint32_t l = m - 2;  // hidden layer l + 1
+            off = tcimg::off_wh(l);
+            const uint64_t b = 64 * n_in + 64 + (uint64_t)l * (64 * 64 + 64);
+            v = params[b + n * 64 + k];
+        } else {
+            off = tcimg::off_wout(H);
+            r = idx - 4096 * (2 + (H - 1));
+            n = r / 64;
+            k = r % 64;
+            const uint64_t b = 64 * n_in + 64 + (uint64_t)(H - 1) * (64 * 64 + 64);
+            if (n < 3) v = params[b + n * 64 + k];
+        }
+        const uint16_t bits = AB ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+        *reinterpret_cast<uint16_t*>(img + off + tc::sw128_offset(n, k)) = bits;
+        return;
+    }
+    const uint32_t j = idx - n_mat;
+    if (j >= tcimg::n_bias(H)) return;
+    float v = 0.f;
+    if (j < 64) {
+        v = params[64 * n_in + j];
+    } else if (j < 64 + (H - 1) * 64) {
+        const uint32_t l = (j - 64) / 64, o = (j - 64) % 64;
+        v = params[64 * n_in + 64 + (uint64_t)l * (64 * 64 + 64) + 4096 + o];
+    } else {
+        const uint32_t c = j - 64 - (H - 1) * 64;
+        if (c < 3) v = params[64 * n_in + 64 + (uint64_t)(H - 1) * (64 * 64 + 64) + 3 * 64 + c];
+    }
+    reinterpret_cast<float*>(img + tcimg::off_bias(H))[j] = v;
+}
+
+struct TcArgs {
+    uint32_t W, H, N, M, k0, k1;
+    uint32_t S, P, n_blocks;
+    float z_clamp;
+    uint32_t img_bytes;
+    NetShape s;
+    GridParams g;
+};
+
+template <uint32_t AB>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    return AB ? tc::pack_bf16(lo, hi) : tc::pack_f16(lo, hi);
+}
+template <uint32_t AB>
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+    return AB ? tc::pack_relu_bf16(lo, hi) : tc::pack_relu_f16(lo, hi);
+}
+template <uint32_t AB>
+__device__ __forceinline__ uint16_t to16(float v) {
+    return AB ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+}
+
+// Row r of a swizzled A tile from 64 floats (optionally ReLU + bias).
+template <uint32_t AB, bool RELU>
+__device__ __forceinline__ void write_row(uint32_t tile, uint32_t r, const float* x) {
+    const uint32_t row = tile + (r >> 3) * 1024u + (r & 7u) * 128u;
+#pragma unroll
+    for (uint32_t c = 0; c < 8; ++c) {
+        const float* y = x + 8 * c;
+        uint32_t d0, d1, d2, d3;
+        if (RELU) {
+            d0 = pack2_relu<AB>(y[0], y[1]);
+            d1 = pack2_relu<AB>(y[2], y[3]);
+            d2 = pack2_relu<AB>(y[4], y[5]);
+            d3 = pack2_relu<AB>(y[6], y[7]);
+        } else {
+            d0 = pack2<AB>(y[0], y[1]);
+            d1 = pack2<AB>(y[2], y[3]);
+            d2 = pack2<AB>(y[4], y[5]);
+            d3 = pack2<AB>(y[6], y[7]);
+        }
+        tc::sts128(row + ((c ^ (r & 7u)) << 4), d0, d1, d2, d3);
+    }
+}
+
+template <uint32_t AB>
+__global__ void __launch_bounds__(512, 1)
+    k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
+               const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
+               const ResidRow* __restrict__ rows, float4* __restrict__ out, float* __restrict__ lc_out,
+               float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
+               float* __restrict__ row_n, int* __restrict__ err) {
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    const uint32_t raw = tc::smem_u32(smem_raw);
+    const uint32_t sbase = (raw + 1023u) & ~1023u;
+    uint8_t* gbase = smem_raw + (sbase - raw);
+    const uint32_t n_wg = blockDim.x >> 7;
+    const uint32_t wg = threadIdx.x >> 7, t = threadIdx.x & 127u, quarter = t >> 5;
+    const uint32_t img_al = (a.img_bytes + 1023u) & ~1023u;
+    const uint32_t wgs = sbase + img_al + wg * kWgStride;  // this warpgroup's region (shared address)
+    uint8_t* wgg = gbase + img_al + wg * kWgStride;        // same, generic pointer
+    const uint32_t misc = sbase + img_al + n_wg * kWgStride;
+    uint8_t* miscg = gbase + img_al + n_wg * kWgStride;
+    const uint32_t mbar = misc + 8u * wg;
+    volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(miscg + 64);
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(miscg + 80 + 4 * wg);
+    const uint32_t tmem_cols = n_wg <= 1 ? 64u : (n_wg <= 2 ? 128u : (n_wg <= 4 ? 256u : 512u));
+
+    // stage the weight image
+    {
+        const float4* src = reinterpret_cast<const float4*>(img_g);
+        float4* dst = reinterpret_cast<float4*>(gbase);
+        for (uint32_t i = threadIdx.x; i < a.img_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    if (threadIdx.x < 32) tc::tmem_alloc(misc + 64, tmem_cols);
+    if (threadIdx.x == 0) {
+        for (uint32_t w = 0; w < n_wg; ++w) {
+            tc::mbar_init(misc + 8u * w, 1);
+            *reinterpret_cast<volatile uint32_t*>(miscg + 80 + 4 * w) = 0u;
+        }
+        tc::fence_mbar_init();
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_holder + 64u * wg;
+    const uint32_t tmem_row = tmem + ((32u * quarter) << 16);
+    const uint32_t bar_id = 1 + wg;
+    uint32_t phase = 0;
+
+    const uint32_t w0pix = sbase + tcimg::off_w0pix(), w0dir = sbase + tcimg::off_w0dir();
+    const uint32_t wout = sbase + tcimg::off_wout(a.s.hidden);
+    const float* bias = reinterpret_cast<const float*>(gbase + tcimg::off_bias(a.s.hidden));
+    const uint32_t tA = wgs + kOffA, tH = wgs + kOffH;
+    nirc_record* s_rec = reinterpret_cast<nirc_record*>(wgg + kOffRec);
+    float4* s_contrib = reinterpret_cast<float4*>(wgg + kOffContrib);
+    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);
+    const uint32_t id64 = tc::idesc_f16(AB, 128, 64), id16 = tc::idesc_f16(AB, 128, 16);
+    const uint16_t one16 = AB ? 0x3F80u : 0x3C00u;
+
+    auto sync_wg = [&]() {
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        tc::named_bar(bar_id, 128);
+    };
+    auto wait_mma = [&]() {
+        if (!*abort_flag) {
+            if (!tc::mbar_wait_bounded(mbar, phase)) {
+                *abort_flag = 1u;
+                atomicExch(err, 1);
+            }
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+    };
+    auto issue_k64 = [&](uint32_t a_tile, uint32_t b_tile, uint32_t idesc) {
+        if (t == 0 && !*abort_flag) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (uint32_t s = 0; s < 4; ++s) tc::mma_f16(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), idesc, s);
+            tc::mma_commit(mbar);
+        }
+    };
+
+    const uint32_t S = a.S;
+    for (uint32_t blk = blockIdx.x * n_wg + wg; blk < a.n_blocks; blk += gridDim.x * n_wg) {
+        const uint32_t p0 = blk * 128u;
+        const uint32_t npix = min(128u, a.P - p0);
+        // ------------------------------------------------ pixel stage
+        {
+            const bool pin = t < npix;
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+            if (pin) {
+                const float4* rq = reinterpret_cast<const float4*>(recs + p0 + t);
+                r0 = __ldg(rq);
+                r1 = __ldg(rq + 1);
+                r2 = __ldg(rq + 2);
+                r3 = __ldg(rq + 3);
+            }
+            float4* sr = reinterpret_cast<float4*>(s_rec + t);
+            sr[0] = r0;
+            sr[1] = r1;
+            sr[2] = r2;
+            sr[3] = r3;
+            float f[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) f[i] = 0.f;
+            const V3 p{r0.x, r0.y, r0.z}, n{r0.w, r1.x, r1.y};
+            uint32_t k = 0;
+            if (a.s.hashgrid) {
+                const uint64_t T = (uint64_t)a.g.mask + 1;
+                for (uint32_t l = 0; l < a.g.n_levels; ++l) {
+                    uint32_t idx[8];
+                    float w[8];
+                    grid_corners(a.g.level[l], a.g.mask, p, idx, w);
+                    const __half2* tab = hash16 + (uint64_t)l * T;
+                    float f0 = 0.f, f1 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float2 v = __half22float2(__ldg(tab + idx[c]));
+                        f0 += w[c] * v.x;
+                        f1 += w[c] * v.y;
+                    }
+                    // k is at most 31 here; the switch keeps f[] in registers
+#pragma unroll
+                    for (int q = 0; q < 32; q += 2)
+                        if ((uint32_t)q == k) {
+                            f[q] = f0;
+                            f[q + 1] = f1;
+                        }
+                    k += 2;
+                }
+            } else {
+                freq4(p.x, f);
+                freq4(p.y, f + 8);
+                freq4(p.z, f + 16);
+                k = 24;
+            }
+            float e[24];
+            freq4(n.x, e);
+            freq4(n.y, e + 8);
+            freq4(n.z, e + 16);
+            if (k == 32) {
+#pragma unroll
+                for (int i = 0; i < 24; ++i) f[32 + i] = e[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 24; ++i) f[24 + i] = e[i];
+            }
+            write_row<AB, false>(tA, t, f);
+        }
+        sync_wg();
+        issue_k64(tA, w0pix, id64);
+        wait_mma();
+        {
+            uint32_t v[64];
+            tc::tmem_ld64(tmem_row, v);
+            tc::tmem_wait_ld();
+            // H operand: element (n = output unit, k = pixel t)
+            const uint32_t hk = tH + (t >> 6) * 8192u;
+#pragma unroll
+            for (uint32_t o = 0; o < 64; ++o)
+                tc::sts16(hk + tc::sw128_offset(o, t & 63u), to16<AB>(__uint_as_float(v[o]) + bias[o]));
+        }
+        sync_wg();
+
+        // ------------------------------------------------ row tiles
+        const uint32_t R = npix * S;
+        for (uint32_t j0 = 0; j0 < R; j0 += 128u) {
+            const uint32_t r = j0 + t;
+            const bool rin = r < R;
+            const uint32_t pl = rin ? r / S : 0u;
+            const uint32_t s = rin ? r - pl * S : 0u;
+            const uint32_t pf = j0 / S;
+            const uint32_t plast = min((j0 + 127u) / S, npix - 1u);
+            // one-hot window [kb, kb + 16 n_oh) covers pixels pf..plast and stays inside H's 128 columns
+            const uint32_t n_oh = (plast - (pf & ~15u) + 16u) >> 4;  // <= 3 for S >= 4
+            const uint32_t kb = min(pf & ~15u, 128u - 16u * n_oh);
+
+            const nirc_record& rc = s_rec[pl];
+            const uint32_t flags = rc.flags;
+            const bool pvalid = rin && (flags & 1u);
+            V3 wi{0.f, 0.f, 1.f};
+            float3 w = make_float3(0.f, 0.f, 0.f);
+            bool ok = false;
+            uint32_t word = 0;
+            if (pvalid) {
+                if (s < a.N) {
+                    const BsdfSample bs = sample_bsdf(V3{rc.n[0], rc.n[1], rc.n[2]}, V3{rc.wo[0], rc.wo[1], rc.wo[2]},
+                                                      make_float3(rc.albedo[0], rc.albedo[1], rc.albedo[2]),
+                                                      rc.roughness, (flags >> 1) & 3u, a.k0, a.k1, p0 + pl, s,
+                                                      PURPOSE_CACHE_DIR);
+                    wi = bs.wi;
+                    w = bs.w;
+                    ok = bs.valid;
+                    word = bs.word;
+                } else {
+                    const ResidRow* rr = rows + (uint64_t)(p0 + pl) * a.M + (s - a.N);
+                    const float4 d = __ldg(&rr->wi), ww = __ldg(&rr->w);
+                    wi = V3{d.x, d.y, d.z};
+                    w = make_float3(ww.x, ww.y, ww.z);
+                    ok = d.w != 0.f;
+                }
+            }
+            {
+                float th, ph, e[16];
+                dir_angles(wi, th, ph);
+                freq4(th, e);
+                freq4(ph, e + 8);
+                const uint32_t row = tA + (t >> 3) * 1024u + (t & 7u) * 128u;
+                const uint32_t sw = t & 7u;
+                tc::sts128(row + ((0u ^ sw) << 4), pack2<AB>(e[0], e[1]), pack2<AB>(e[2], e[3]), pack2<AB>(e[4], e[5]),
+                           pack2<AB>(e[6], e[7]));
+                tc::sts128(row + ((1u ^ sw) << 4), pack2<AB>(e[8], e[9]), pack2<AB>(e[10], e[11]),
+                           pack2<AB>(e[12], e[13]), pack2<AB>(e[14], e[15]));
+                const uint32_t oh = rin ? pl - kb : 0xFFFFu;  // one-hot position among columns 16..63
+#pragma unroll
+                for (uint32_t c = 2; c < 8; ++c) {
+                    uint32_t d[4] = {0u, 0u, 0u, 0u};
+                    const uint32_t lo = (c - 2) * 8;
+                    if (oh >= lo && oh < lo + 8) {
+                        const uint32_t e2 = oh - lo;
+                        d[e2 >> 1] = (uint32_t)one16 << ((e2 & 1u) * 16);
+                    }
+                    tc::sts128(row + ((c ^ sw) << 4), d[0], d[1], d[2], d[3]);
+                }
+            }
+            sync_wg();
+            if (t == 0 && !*abort_flag) {
+                tc::fence_after_sync();
+                tc::mma_f16(tmem, tc::sdesc(tA), tc::sdesc(w0dir), id64, 0);
+                for (uint32_t qq = 1; qq <= n_oh; ++qq) {
+                    const uint32_t kk = kb + 16u * (qq - 1);
+                    tc::mma_f16(tmem, tc::sdesc(tA + 32u * qq), tc::sdesc(tH + (kk >> 6) * 8192u + (kk & 63u) * 2u),
+                                id64, 1);
+                }
+                tc::mma_commit(mbar);
+            }
+            wait_mma();
+            for (uint32_t l = 0; l < a.s.hidden; ++l) {
+                // epilogue of layer l (l = 0: h_pix already holds b0), then the MMAs of layer l + 1
+                uint32_t v[64];
+                tc::tmem_ld64(tmem_row, v);
+                tc::tmem_wait_ld();
+                float x[64];
+                if (l == 0) {
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) x[i] = __uint_as_float(v[i]);
+                } else {
+                    const float2* b2 = reinterpret_cast<const float2*>(bias + 64 + (l - 1) * 64);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float2 y = __fadd2_rn(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])),
+                                                    b2[i]);
+                        x[2 * i] = y.x;
+                        x[2 * i + 1] = y.y;
+                    }
+                }
+                write_row<AB, true>(tA, t, x);
+                sync_wg();
+                if (l + 1 < a.s.hidden) {
+                    issue_k64(tA, sbase + tcimg::off_wh(l), id64);
+                } else {
+                    issue_k64(tA, wout, id16);
+                }
+                wait_mma();
+            }
+            float3 nv;
+            {
+                uint32_t v[4];
+                tc::tmem_ld4(tmem_row, v);
+                tc::tmem_wait_ld();
+                const float* bo = bias + 64 + (a.s.hidden - 1) * 64;
+                nv.x = expf(fminf(__uint_as_float(v[0]) + bo[0], a.z_clamp));
+                nv.y = expf(fminf(__uint_as_float(v[1]) + bo[1], a.z_clamp));
+                nv.z = expf(fminf(__uint_as_float(v[2]) + bo[2], a.z_clamp));
+            }
+            if (row_n && rin) {
+                float* rn = row_n + 3 * ((uint64_t)p0 * S + r);
+                rn[0] = ok ? nv.x : 0.f;
+                rn[1] = ok ? nv.y : 0.f;
+                rn[2] = ok ? nv.z : 0.f;
+            }
+            tc::fence_before_sync();
+            s_contrib[t] = ok ? make_float4(w.x * nv.x, w.y * nv.y, w.z * nv.z, __uint_as_float(word))
+                              : make_float4(0.f, 0.f, 0.f, __uint_as_float(word));
+            tc::named_bar(bar_id, 128);
+
+            // one thread per pixel of this tile: rows in sample order
+            if (t <= plast - pf) {
+                const uint32_t q = pf + t;
+                const uint32_t q_lo = q * S, q_hi = q_lo + S;
+                const uint32_t lo = max(q_lo, j0), hi = min(q_hi, j0 + 128u);
+                float lcs[3], lcc[3], sbs[3], sbc[3];
+                uint64_t sig;
+                uint32_t nvalid;
+                if (q_lo < j0) {  // continues from the previous tile
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        lcs[c] = s_carry[c];
+                        lcc[c] = s_carry[3 + c];
+                        sbs[c] = s_carry[6 + c];
+                        sbc[c] = s_carry[9 + c];
+                    }
+                    sig = (uint64_t)__float_as_uint(s_carry[12]) | ((uint64_t)__float_as_uint(s_carry[13]) << 32);
+                    nvalid = __float_as_uint(s_carry[14]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) lcs[c] = lcc[c] = sbs[c] = sbc[c] = 0.f;
+                    sig = kSigInit;
+                    nvalid = 0;
+                }
+                const bool qvalid = s_rec[q].flags & 1u;  // pixels without a camera hit draw no samples
+                for (uint32_t rr = lo; rr < hi; ++rr) {
+                    const float4 cv = s_contrib[rr - j0];
+                    const float xs[3] = {cv.x, cv.y, cv.z};
+                    if (rr - q_lo < a.N) {
+                        const uint32_t wd = __float_as_uint(cv.w);
+                        if (qvalid) sig = sig_mix(sig, wd);
+                        nvalid += (wd >> 9) & 1u;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float y = xs[c] - lcc[c];
+                            const float tt = lcs[c] + y;
+                            lcc[c] = (tt - lcs[c]) - y;
+                            lcs[c] = tt;
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float y = xs[c] - sbc[c];
+                            const float tt = sbs[c] + y;
+                            sbc[c] = (tt - sbs[c]) - y;
+                            sbs[c] = tt;
+                        }
+                    }
+                }
+                if (q_hi > j0 + 128u) {  // continues in the next tile
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        s_carry[c] = lcs[c];
+                        s_carry[3 + c] = lcc[c];
+                        s_carry[6 + c] = sbs[c];
+                        s_carry[9 + c] = sbc[c];
+                    }
+                    s_carry[12] = __uint_as_float((uint32_t)sig);
+                    s_carry[13] = __uint_as_float((uint32_t)(sig >> 32));
+                    s_carry[14] = __uint_as_float(nvalid);
+                } else {
+                    const uint32_t gp = p0 + q;
+                    const PixelBase b = base[gp];
+                    float Lc[3] = {0.f, 0.f, 0.f}, Lr[3] = {b.wl.x, b.wl.y, b.wl.z};
+                    if (a.N) {
+                        const float inv = 1.0f / (float)a.N;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Lc[c] = lcs[c] * inv;
+                    }
+                    if (a.M) {
+                        const float inv = 1.0f / (float)a.M;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Lr[c] -= sbs[c] * inv;
+                    }
+                    out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
+                    if (lc_out) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) lc_out[3 * (uint64_t)gp + c] = Lc[c];
+                    }
+                    if (lr_out) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) lr_out[3 * (uint64_t)gp + c] = Lr[c];
+                    }
+                    if (sig_out) sig_out[2 * (uint64_t)gp + 1] = sig;
+                    if (count) count[gp] += nvalid;
+                }
+            }
+            tc::named_bar(bar_id, 128);
+        }
+    }
+
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(*tmem_holder, tmem_cols);
+    }
+}
+
+static size_t tc_smem_bytes(uint32_t img_bytes, uint32_t n_wg) {
+    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * kWgStride + 128;
+}
+
+cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
+    if (!h->packed_tc) return cudaSuccess;
+    const uint32_t H = h->shape.hidden;
+    const uint32_t n = 64 * 64 * (2 + (H - 1)) + 16 * 64 + tcimg::n_bias(H);
+    if (h->cfg.precision == NIRC_BF16_TC)
+        k_repack_tc<1><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, reinterpret_cast<uint8_t*>(h->packed_tc));
+    else
+        k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, reinterpret_cast<uint8_t*>(h->packed_tc));
+    return cudaGetLastError();
+}
+
+bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd) {
+    return (h->cfg.precision == NIRC_FP16_TC || h->cfg.precision == NIRC_BF16_TC) && fd.cache_mode == 0 &&
+           fd.n_cache + fd.n_resid >= 4 && h->packed_tc != nullptr &&
+           (h->shape.n_pos == 24 || h->shape.n_pos == 32);
+}
+
+cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
+                            const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
+                            uint64_t* sig, uint32_t* count, float* row_n, int* err, cudaStream_t st) {
+    TcArgs a;
+    a.W = fd.width;
+    a.H = fd.height;
+    a.N = fd.n_cache;
+    a.M = fd.n_resid;
+    a.k0 = (uint32_t)fd.seed;
+    a.k1 = fd.frame;
+    a.S = fd.n_cache + fd.n_resid;
+    a.P = fd.width * fd.height;
+    a.n_blocks = (a.P + 127) / 128;
+    a.z_clamp = h->cfg.z_clamp;
+    a.img_bytes = (uint32_t)tc_image_bytes(h->shape.hidden);
+    a.s = h->shape;
+    a.g = h->grid;
+    int dev = h->device, max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    uint32_t n_wg = 4;
+    while (n_wg > 1 && tc_smem_bytes(a.img_bytes, n_wg) > (size_t)max_smem) --n_wg;
+    const size_t smem = tc_smem_bytes(a.img_bytes, n_wg);
+    if (smem > (size_t)max_smem) return cudaErrorInvalidConfiguration;
+    uint32_t grid = (a.n_blocks + n_wg - 1) / n_wg;
+    if (grid > (uint32_t)h->num_sms) grid = h->num_sms;
+    const __half2* hash = reinterpret_cast<const __half2*>(h->hash16);
+    cudaError_t e;
+    if (h->cfg.precision == NIRC_BF16_TC) {
+        e = cudaFuncSetAttribute(k_cache_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_cache_tc<1><<<grid, n_wg * 128, smem, st>>>(a, reinterpret_cast<const uint8_t*>(h->packed_tc), hash, recs,
+                                                      base, rows, reinterpret_cast<float4*>(out_rgba), lc, lr, sig,
+                                                      count, row_n, err);
+    } else {
+        e = cudaFuncSetAttribute(k_cache_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_cache_tc<0><<<grid, n_wg * 128, smem, st>>>(a, reinterpret_cast<const uint8_t*>(h->packed_tc), hash, recs,
+                                                      base, rows, reinterpret_cast<float4*>(out_rgba), lc, lr, sig,
+                                                      count, row_n, err);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nirc

@@ -40,6 +40,8 @@ NetShape make_shape(const nirc_config& cfg) {
     s.n_mlp = (uint64_t)kWidth * s.n_in + kWidth + (uint64_t)(s.hidden - 1) * (kWidth * kWidth + kWidth) +
               3ull * kWidth + 3;
     s.n_hash = s.hashgrid ? (uint64_t)cfg.hash_levels * (1ull << cfg.log2_table) * cfg.feats_per_level : 0;
+    s.hash_off = (s.n_mlp + 3) & ~3ull;
+    s.n_dev = s.hash_off + s.n_hash;
     s.off_wpix = 0;
     s.off_wdir = s.n_pix * kWidth;
     s.off_b0 = s.off_wdir + kDirFeatures * kWidth;
@@ -191,6 +193,22 @@ nirc_status nirc_timing_enable(nirc_handle* h, int enable) {
     return NIRC_OK;
 }
 
+nirc_status nirc_sync(nirc_handle* h, void* stream) {
+    if (!h) {
+        set_error("nirc_sync: handle is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e, "nirc_sync");
+    if (*h->host_err) {
+        *h->host_err = 0;
+        cudaMemset(h->dev_err, 0, sizeof(int));
+        set_error("a tensor-core kernel gave up waiting for an MMA (bounded wait ran out); its output is invalid");
+        return NIRC_ERR_TIMEOUT;
+    }
+    return NIRC_OK;
+}
+
 nirc_status nirc_timing_read(nirc_handle* h, nirc_timing* out) {
     if (!h || !out) {
         set_error("nirc_timing_read: NULL argument");
@@ -228,13 +246,20 @@ nirc_status nirc_create(const nirc_config* cfg, nirc_handle** out) {
     h->grid = make_grid(*cfg);
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-    const uint64_t np = h->shape.n_mlp + h->shape.n_hash;
+    const uint64_t np = h->shape.n_dev;
     if (e == cudaSuccess) e = cudaMalloc(&h->params, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->adam_m, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->adam_v, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->grad, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->packed, h->shape.packed_floats * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->loss_accum, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dev_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->host_err, sizeof(int));
+    if (e == cudaSuccess) *h->host_err = 0;
+    h->packed_tc_bytes = tc_image_bytes(h->shape.hidden);
+    if (e == cudaSuccess) e = cudaMalloc(&h->packed_tc, h->packed_tc_bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->packed_tc, 0, h->packed_tc_bytes);
     if (e == cudaSuccess && h->shape.n_hash) e = cudaMalloc(&h->hash16, h->shape.n_hash * sizeof(__half));
     if (e == cudaSuccess) e = cudaMemset(h->params, 0, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(h->adam_m, 0, np * sizeof(float));
@@ -260,6 +285,8 @@ nirc_status nirc_destroy(nirc_handle* h) {
     cudaFree(h->grad);
     cudaFree(h->packed);
     cudaFree(h->loss_accum);
+    cudaFree(h->dev_err);
+    if (h->host_err) cudaFreeHost(h->host_err);
     cudaFree(h->hash16);
     cudaFree(h->packed_tc);
     cudaFree(h->scratch);
@@ -277,23 +304,32 @@ nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, 
         return NIRC_ERR_INVALID;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const uint64_t np = h->shape.n_mlp + h->shape.n_hash;
-    cudaError_t e = cudaMemcpyAsync(h->params, params, np * sizeof(float),
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    const uint64_t np = h->shape.n_dev;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // flat [mlp | hash] input -> device [mlp | pad | hash] with the table 16-byte aligned
+    cudaError_t e = cudaMemsetAsync(h->params, 0, np * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->params, params, h->shape.n_mlp * sizeof(float), kind, st);
+    if (e == cudaSuccess && h->shape.n_hash)
+        e = cudaMemcpyAsync(h->params + h->shape.hash_off, params + h->shape.n_mlp, h->shape.n_hash * sizeof(float),
+                            kind, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->adam_m, 0, np * sizeof(float), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->adam_v, 0, np * sizeof(float), st);
     if (e == cudaSuccess) e = launch_repack_simt(h, st);
     if (e == cudaSuccess) e = launch_hash_to_half(h, st);
+    if (e == cudaSuccess) e = launch_repack_tc(h, st);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);  // host buffer may be freed on return
     if (e != cudaSuccess) return cuda_status(e, "nirc_set_params");
     h->step = 0;
     return NIRC_OK;
 }
 
-static nirc_status copy_out(const float* src, uint64_t n, float* out, int on_device, void* stream, const char* what) {
+static nirc_status copy_out(const nirc_handle* h, const float* src, float* out, int on_device, void* stream,
+                            const char* what) {
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(out, src, n * sizeof(float),
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpyAsync(out, src, h->shape.n_mlp * sizeof(float), kind, st);
+    if (e == cudaSuccess && h->shape.n_hash)
+        e = cudaMemcpyAsync(out + h->shape.n_mlp, src + h->shape.hash_off, h->shape.n_hash * sizeof(float), kind, st);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);
     return cuda_status(e, what);
 }
@@ -303,7 +339,7 @@ nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* str
         set_error("nirc_get_params: NULL argument");
         return NIRC_ERR_INVALID;
     }
-    return copy_out(h->params, h->shape.n_mlp + h->shape.n_hash, out, on_device, stream, "nirc_get_params");
+    return copy_out(h, h->params, out, on_device, stream, "nirc_get_params");
 }
 
 nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stream) {
@@ -311,7 +347,7 @@ nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stre
         set_error("nirc_get_grads: NULL argument");
         return NIRC_ERR_INVALID;
     }
-    return copy_out(h->grad, h->shape.n_mlp + h->shape.n_hash, out, on_device, stream, "nirc_get_grads");
+    return copy_out(h, h->grad, out, on_device, stream, "nirc_get_grads");
 }
 
 nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision) {
@@ -319,11 +355,19 @@ nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision) {
         set_error("nirc_set_precision: bad argument");
         return NIRC_ERR_INVALID;
     }
-    if (precision != NIRC_FP32_SIMT) {
-        set_error("precision %u is not available in this build", precision);
+    if (precision == NIRC_FP8_E4M3_TC) {
+        set_error("precision FP8_E4M3_TC is not available in this build");
         return NIRC_ERR_UNSUPPORTED;
     }
+    const uint32_t old = h->cfg.precision;
     h->cfg.precision = precision;
+    // the tensor-core weight image depends on the operand type
+    cudaError_t e = launch_repack_tc(h, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        h->cfg.precision = old;
+        return cuda_status(e, "nirc_set_precision");
+    }
     return NIRC_OK;
 }
 
@@ -365,7 +409,8 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
         return NIRC_ERR_INVALID;
     }
     if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
-                (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)))) {
+                (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)) ||
+                (aux->row_n && ((uintptr_t)aux->row_n & 3u)))) {
         set_error("nirc_estimate_frame: misaligned aux pointer");
         return NIRC_ERR_INVALID;
     }
@@ -386,9 +431,16 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
     timer_end(h, NIRC_K_PATH_TRACE, st);
     if (e != cudaSuccess) return cuda_status(e, "nirc_estimate_frame (path tracing)");
     timer_begin(h, NIRC_K_CACHE, st);
-    e = launch_cache_simt(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
-                          count, st);
+    const bool tc = tc_supported(h, fd);
+    if (tc) {
+        e = launch_cache_tc(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
+                            count, aux ? aux->row_n : nullptr, h->dev_err, st);
+    } else {
+        e = launch_cache_simt(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr,
+                              sig, count, aux ? aux->row_n : nullptr, st);
+    }
     timer_end(h, NIRC_K_CACHE, st);
+    if (e == cudaSuccess && tc) e = cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     return cuda_status(e, "nirc_estimate_frame (cache integral)");
 }
 

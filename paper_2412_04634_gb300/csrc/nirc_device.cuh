@@ -425,6 +425,13 @@ __device__ __forceinline__ void freq4(float v, float* e) {
     }
 }
 
+// Same features with one sincospi per octave (argument scaled exactly by
+// 2^k): the FP32 reference-accuracy variant used by the SIMT kernels.
+__device__ __forceinline__ void freq4_accurate(float v, float* e) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sincospif(ldexpf(v, k), &e[2 * k], &e[2 * k + 1]);
+}
+
 // (theta/pi, phi/2pi in [0,1)) of a unit direction.
 __device__ __forceinline__ void dir_angles(V3 w, float& th, float& ph) {
     th = acosf(fminf(fmaxf(w.z, -1.0f), 1.0f)) * kInvPi;

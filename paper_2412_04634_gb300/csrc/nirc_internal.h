@@ -39,6 +39,8 @@ struct NetShape {
     uint32_t hidden;    // hidden layers (>= 1)
     uint64_t n_mlp;     // MLP parameters in the master vector
     uint64_t n_hash;    // hash-table parameters
+    uint64_t hash_off;  // device offset (floats) of the hash table: n_mlp rounded up to 4 (16-byte aligned)
+    uint64_t n_dev;     // device floats of params / moments / gradients = hash_off + n_hash
     uint32_t log2_table;
     uint32_t levels;
     uint32_t hashgrid;  // 1 = hash grid, 0 = frequency encoding of x
@@ -74,6 +76,8 @@ struct nirc_handle {
     void* train_scratch = nullptr;  // training activations
     size_t train_scratch_bytes = 0;
     float* loss_accum = nullptr;    // one float
+    int* dev_err = nullptr;         // device flag: a bounded wait ran out (1)
+    int* host_err = nullptr;        // pinned copy of dev_err, refreshed after tensor-core launches
     // kernel timers (nirc_timing_enable / nirc_timing_read)
     bool timing = false;
     struct Pending {
@@ -111,10 +115,18 @@ cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n
 // nirc_cache_simt.cu
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                               const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
-                              uint64_t* sig, uint32_t* count, cudaStream_t st);
+                              uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st);
 cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, const float* dirs, uint64_t n,
                               float* out, cudaStream_t st);
 cudaError_t launch_repack_simt(const nirc_handle* h, cudaStream_t st);
+
+// nirc_cache_tc.cu
+size_t tc_image_bytes(uint32_t hidden);
+cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st);
+bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd);
+cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
+                            const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
+                            uint64_t* sig, uint32_t* count, float* row_n, int* err, cudaStream_t st);
 
 // nirc_train.cu
 size_t train_scratch_bytes(const NetShape& s, uint64_t n);

@@ -61,14 +61,14 @@ __device__ __forceinline__ void encode_surface(const NetShape& s, const GridPara
     } else {
         const float pv[3] = {p.x, p.y, p.z};
         for (int d = 0; d < 3; ++d) {
-            freq4(pv[d], e);
+            freq4_accurate(pv[d], e);
 #pragma unroll
             for (int q = 0; q < 8; ++q) act[(k++) * stride] = e[q];
         }
     }
     const float nv[3] = {n.x, n.y, n.z};
     for (int d = 0; d < 3; ++d) {
-        freq4(nv[d], e);
+        freq4_accurate(nv[d], e);
 #pragma unroll
         for (int q = 0; q < 8; ++q) act[(k++) * stride] = e[q];
     }

@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         encode_surface(s, g, table, p, nn, act, stride);  // [pos][nrm]
         float th, ph, edir[16];
         dir_angles(wi, th, ph);
-        freq4(th, edir);
-        freq4(ph, edir + 8);
+        freq4_accurate(th, edir);
+        freq4_accurate(ph, edir + 8);
         // network input in parameter order [pos][dir][nrm]
         if (in_range) {
             for (uint32_t k = 0; k < s.n_pos; ++k) tp.e[(uint64_t)k * n + t] = act[k * stride];
@@ -292,7 +292,7 @@ __global__ void k_hash_to_half(uint64_t n, const float* __restrict__ src, __half
 
 cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st) {
     if (!h->shape.n_hash || !h->hash16) return cudaSuccess;
-    k_hash_to_half<<<4 * h->num_sms, 256, 0, st>>>(h->shape.n_hash, h->params + h->shape.n_mlp, h->hash16);
+    k_hash_to_half<<<4 * h->num_sms, 256, 0, st>>>(h->shape.n_hash, h->params + h->shape.hash_off, h->hash16);
     return cudaGetLastError();
 }
 
@@ -301,7 +301,7 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
     const NetShape& s = h->shape;
     TrainPtrs tp = carve(h->train_scratch, s, n);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(h->grad, 0, (s.n_mlp + s.n_hash) * sizeof(float), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(h->grad, 0, s.n_dev * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
     const size_t smem_f = (size_t)s.packed_floats * 4 + (size_t)kTrainThreads * kWidth * 4;
     const size_t smem_b = (size_t)s.packed_floats * 4;
@@ -312,7 +312,7 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
     uint64_t blocks = (n + kTrainThreads - 1) / kTrainThreads;
     if (blocks > (uint64_t)h->num_sms) blocks = h->num_sms;
     const float scale = 1.0f / (3.0f * (float)n);
-    const float* table = h->params + s.n_mlp;
+    const float* table = h->params + s.hash_off;
     timer_begin(h, NIRC_K_TRAIN_FWD, st);
     k_train_fwd<<<(uint32_t)blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
                                                                  h->packed, table, recs, dirs, targets, n, tp,
@@ -321,7 +321,7 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     timer_begin(h, NIRC_K_TRAIN_BWD, st);
     k_train_bwd<<<(uint32_t)blocks, kTrainThreads, smem_b, st>>>(s, h->grid, h->packed, recs, n, tp,
-                                                                 h->grad + s.n_mlp);
+                                                                 h->grad + s.hash_off);
     timer_end(h, NIRC_K_TRAIN_BWD, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -350,12 +350,13 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
     const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
     const float inv_bc1 = (float)(1.0 / (1.0 - std::pow(b1, (double)h->step)));
     const float inv_bc2 = (float)(1.0 / (1.0 - std::pow(b2, (double)h->step)));
-    const uint64_t np = s.n_mlp + s.n_hash;
+    const uint64_t np = s.n_dev;
     timer_begin(h, NIRC_K_ADAM, st);
     k_adam<<<8 * h->num_sms, 256, 0, st>>>(np, h->params, h->adam_m, h->adam_v, h->grad, h->cfg.lr, h->cfg.beta1,
-                                          h->cfg.beta2, h->cfg.adam_eps, inv_bc1, inv_bc2, h->hash16, s.n_mlp);
+                                          h->cfg.beta2, h->cfg.adam_eps, inv_bc1, inv_bc2, h->hash16, s.hash_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_repack_simt(h, st);
+    if (e == cudaSuccess) e = launch_repack_tc(h, st);
     timer_end(h, NIRC_K_ADAM, st);
     if (e != cudaSuccess) return e;
     if (d_loss) {

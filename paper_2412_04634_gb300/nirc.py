@@ -54,7 +54,7 @@ class nirc_frame_desc(ctypes.Structure):
 
 class nirc_frame_aux(ctypes.Structure):
     _fields_ = [("lc", ctypes.c_void_p), ("lr", ctypes.c_void_p),
-                ("sig", ctypes.c_void_p), ("count", ctypes.c_void_p)]
+                ("sig", ctypes.c_void_p), ("count", ctypes.c_void_p), ("row_n", ctypes.c_void_p)]
 
 
 K_CLASSES = ["path_trace", "cache", "train_records", "train_fwd", "train_bwd", "train_gradw", "adam", "query"]
@@ -78,6 +78,7 @@ def _load():
         "nirc_get_params": ([P, P, i32, P], st),
         "nirc_get_grads": ([P, P, i32, P], st),
         "nirc_set_precision": ([P, u32], st),
+        "nirc_sync": ([P, P], st),
         "nirc_query": ([P, P, P, u64, P, P], st),
         "nirc_estimate_frame": ([P, P, P, P, P, P], st),
         "nirc_gen_train": ([P, P, u32, u32, u32, u64, u32, u64, u32, P, P, P, P], st),
@@ -173,15 +174,19 @@ def nirc_set_precision(h, precision: int):
     _check(_lib.nirc_set_precision(h, precision))
 
 
+def nirc_sync(h, stream=None):
+    _check(_lib.nirc_sync(h, _stream(stream)))
+
+
 def nirc_query(h, records: torch.Tensor, dirs: torch.Tensor, out: torch.Tensor, stream=None):
     n = dirs.shape[0]
     _check(_lib.nirc_query(h, _ptr(records), _ptr(dirs), n, _ptr(out), _stream(stream)))
 
 
 def nirc_estimate_frame(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba: torch.Tensor,
-                        lc=None, lr=None, sig=None, count=None, stream=None):
-    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count))
-    use_aux = any(x is not None for x in (lc, lr, sig, count))
+                        lc=None, lr=None, sig=None, count=None, row_n=None, stream=None):
+    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n))
+    use_aux = any(x is not None for x in (lc, lr, sig, count, row_n))
     _check(_lib.nirc_estimate_frame(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
                                     ctypes.byref(aux) if use_aux else None, _stream(stream)))
 

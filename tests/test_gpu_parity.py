@@ -41,11 +41,14 @@ def _hash_cfg():
                             lr=1e-2)
 
 
-def _run_frame(N, cfg, params, scene, W, H, Nc, M, D, frame, seed, cache_mode=0, cache_const=(0, 0, 0)):
+def _run_frame(N, cfg, params, scene, W, H, Nc, M, D, frame, seed, cache_mode=0, cache_const=(0, 0, 0),
+               precision=0, rows=False):
     import torch
     cache = N.Cache(cfg)
     if params is not None:
         cache.set_params(params)
+    if precision:
+        N.nirc_set_precision(cache.h, precision)
     sc = N.scene_to_tensor(scene)
     P = W * H
     out = torch.empty((P, 4), device="cuda")
@@ -53,22 +56,42 @@ def _run_frame(N, cfg, params, scene, W, H, Nc, M, D, frame, seed, cache_mode=0,
     lr = torch.empty((P, 3), device="cuda")
     sig = torch.empty((P, 2), device="cuda", dtype=torch.int64)
     cnt = torch.empty(P, device="cuda", dtype=torch.int32)
+    row_n = torch.full((P, Nc + M, 3), -1.0, device="cuda") if rows else None
     desc = N.frame_desc(W, H, Nc, M, D, frame, seed, scene.n_prims, cache_mode, cache_const)
-    N.nirc_estimate_frame(cache.h, sc, desc, out, lc, lr, sig, cnt)
+    N.nirc_estimate_frame(cache.h, sc, desc, out, lc, lr, sig, cnt, row_n)
+    N.nirc_sync(cache.h)
     torch.cuda.synchronize()
     cache.close()
-    return dict(pixel=out[:, :3].cpu().numpy(), alpha=out[:, 3].cpu().numpy(), lc=lc.cpu().numpy(),
-                lr=lr.cpu().numpy(), sig=sig.cpu().numpy().view(np.uint64), count=cnt.cpu().numpy().view(np.uint32))
+    res = dict(pixel=out[:, :3].cpu().numpy(), alpha=out[:, 3].cpu().numpy(), lc=lc.cpu().numpy(),
+               lr=lr.cpu().numpy(), sig=sig.cpu().numpy().view(np.uint64), count=cnt.cpu().numpy().view(np.uint32))
+    if rows:
+        res["row_n"] = row_n.cpu().numpy()
+    return res
 
 
-def _compare_frames(g, o):
+def frame_errors(g, o):
+    """Relative errors of the two levels (each against its own magnitude,
+    floored at 1e-3 of its mean) and of the pixel.  The pixel is L_e + L_c +
+    L_r and the levels cancel by design (L_r subtracts the cache's
+    prediction), so its error is measured against the largest of |pixel|,
+    |L_c| and |L_r|."""
+    errs = {k: rel_err(g[k], o[k]) for k in ("lc", "lr")}
+    scale = np.maximum.reduce([np.abs(o["pixel"]), np.abs(o["lc"]), np.abs(o["lr"])])
+    scale = np.maximum(scale, 1e-3 * max(np.abs(o["pixel"]).mean(), 1e-30))
+    errs["pixel"] = np.abs(np.asarray(g["pixel"], np.float64) - o["pixel"]) / scale
+    return errs
+
+
+def _compare_frames(g, o, tol=FP32_TOL):
     assert np.array_equal(g["sig"][:, 0], o["sig"][:, 0]), "path decision signatures differ"
     assert np.array_equal(g["sig"][:, 1], o["sig"][:, 1]), "cache sample signatures differ"
     assert np.array_equal(g["count"], o["count"])
-    for key in ("pixel", "lc", "lr"):
-        err = rel_err(g[key], o[key])
-        assert err.max() <= FP32_TOL, (key, err.max(), np.unravel_index(err.argmax(), err.shape))
+    errs = frame_errors(g, o)
+    stats = {k: (float(e.max()), float(np.percentile(e, 99))) for k, e in errs.items()}
+    for key, err in errs.items():
+        assert err.max() <= tol, (key, stats, np.unravel_index(err.argmax(), err.shape))
     assert np.all(g["alpha"] == 1.0)
+    return stats
 
 
 # ---------------------------------------------------------------------------
@@ -106,9 +129,14 @@ def test_frame_small_workload(N, oracle):
     params = scenes.init_params(cfg, 1)
     sc = scenes.cornell_scene(64, 64, seed=1)
     for frame in (0, 3):
-        g = _run_frame(N, cfg, params, sc, 64, 64, 8, 1, 4, frame, 1)
-        o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(64, 64, 8, 1, 4, frame, 1))
+        g = _run_frame(N, cfg, params, sc, 64, 64, 8, 1, 4, frame, 1, rows=True)
+        o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(64, 64, 8, 1, 4, frame, 1), rows=True)
         _compare_frames(g, o)
+        # every cache output (row) against the oracle's
+        valid = o["row_n"] > 0
+        assert np.array_equal(valid, g["row_n"] > 0)
+        err = np.abs(g["row_n"][valid] - o["row_n"][valid]) / o["row_n"][valid]
+        assert err.max() <= FP32_TOL, err.max()
 
 
 def test_frame_glossy_hashgrid(N, oracle):
@@ -199,6 +227,24 @@ def test_gen_train_matches_oracle(N, oracle, which):
     cache.close()
 
 
+def _near_kink(oracle, cfg, params, recs, dirs, margin=1e-4):
+    """Samples with a hidden pre-activation within `margin` of zero (FP64
+    forward of the oracle's encodings; used only to choose test inputs)."""
+    p = params.astype(np.float64)
+    E = np.stack([oracle.encode(cfg, p, recs[i:i + 1], dirs[i]) for i in range(len(recs))])
+    off = 0
+    x = E
+    mask = np.zeros(len(recs), bool)
+    for li, (o, i) in enumerate(cfg.layer_shapes()[:-1]):
+        W = p[off:off + o * i].reshape(o, i)
+        b = p[off + o * i:off + o * i + o]
+        off += o * i + o
+        pre = x @ W.T + b
+        mask |= (np.abs(pre) < margin).any(1)
+        x = np.maximum(pre, 0.0)
+    return mask
+
+
 @pytest.mark.parametrize("which", ["freq", "hash"])
 def test_train_step_matches_oracle(N, oracle, which):
     import torch
@@ -207,6 +253,10 @@ def test_train_step_matches_oracle(N, oracle, which):
     n = 3000
     recs, dirs, tg = scenes.training_batch(n, seed=21)
     recs["flags"][::17] = 0  # some invalid records
+    # a sample whose pre-activation sits within rounding of a ReLU kink can
+    # switch sides between FP32 and FP64 and move the gradient by a whole
+    # sample's contribution: leave such samples out (marked invalid)
+    recs["flags"][_near_kink(oracle, cfg, params, recs, dirs)] = 0
     cache = N.Cache(cfg)
     cache.set_params(params)
     loss = torch.zeros(1, device="cuda")
@@ -243,6 +293,7 @@ def test_mrse_matches_oracle(N, oracle):
     img = rng.uniform(0, 2, (n, 4)).astype(np.float32)
     ref = rng.uniform(0, 2, (n, 4)).astype(np.float32)
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
-    N.nirc_frame_mrse(torch.from_numpy(img).cuda(), torch.from_numpy(ref).cuda(), out)
-    want = oracle.mrse(img[:, :3].astype(np.float64), ref[:, :3].astype(np.float64), 1e-2)
+    N.nirc_frame_mrse(torch.from_numpy(img).cuda(), torch.from_numpy(ref).cuda(), out, eps=1e-2)
+    # the call takes eps as a binary32 value
+    want = oracle.mrse(img[:, :3].astype(np.float64), ref[:, :3].astype(np.float64), float(np.float32(1e-2)))
     assert abs(out.item() - want) <= 1e-12 * want
