@@ -45,7 +45,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp16")
+    ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--n-cache", type=int, default=16)
@@ -163,6 +164,142 @@ def measured_tensor_peak():
         return 1700.0, "fallback sustained bf16 1.7 PFLOP/s (of fallback)"
 
 
+def _precision_code(N, name):
+    return {"fp32": N.NIRC_FP32_SIMT, "fp16": N.NIRC_FP16_TC, "bf16": N.NIRC_BF16_TC}[name]
+
+
+class FrameRunner:
+    """Device buffers and the per-frame step of one cache replica."""
+
+    def __init__(self, N, args, cfg, params, frames, dev, seed):
+        import torch
+        self.N, self.args, self.dev, self.seed = N, args, dev, seed
+        self.W, self.H = args.width, args.height
+        self.P = self.W * self.H
+        self.cache = N.Cache(cfg)
+        self.cache.set_params(params)
+        self.scene_dev = [N.scene_to_tensor(f, dev) for f in frames]
+        self.n_prims = frames[0].n_prims
+        T = args.train
+        self.img = torch.empty((self.P, 4), device=dev)
+        self.recs = torch.empty((T, 16), device=dev)
+        self.dirs = torch.empty((T, 3), device=dev)
+        self.tgts = torch.empty((T, 3), device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.mrse = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def set_precision(self, name):
+        self.N.nirc_set_precision(self.cache.h, _precision_code(self.N, name))
+
+    def reference(self, frame_index, spp):
+        """Plain path tracing (zero cache) of one frame, averaged over launches."""
+        import torch
+        N, a = self.N, self.args
+        per = min(16, spp)
+        n = max(1, spp // per)
+        ref = torch.zeros((self.P, 4), device=self.dev)
+        tmp = torch.empty((self.P, 4), device=self.dev)
+        for k in range(n):
+            d = N.frame_desc(self.W, self.H, 0, per, 16, 1000 + k, self.seed, self.n_prims, cache_mode=1)
+            N.nirc_estimate_frame(self.cache.h, self.scene_dev[frame_index], d, tmp)
+            ref += tmp
+        ref /= n
+        return ref, n * per
+
+    def step(self, f, ref, scene=None):
+        N, a = self.N, self.args
+        sc = self.scene_dev[f % 60] if scene is None else scene
+        h = self.cache.h
+        d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims)
+        N.nirc_estimate_frame(h, sc, d, self.img)
+        N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs, self.dirs,
+                         self.tgts)
+        N.nirc_train_step(h, self.recs, self.dirs, self.tgts, self.loss)
+        N.nirc_frame_mrse(self.img, ref, self.mrse)
+
+    def timed(self, ref, first, steps, stream, sampler=None):
+        """Time `steps` frames on the device (CUDA events on `stream`)."""
+        import torch
+        N = self.N
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        N.nirc_timing_enable(self.cache.h, True)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        world = dist_info()[0]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(self.dev)
+        evs[0].record(stream)
+        for k in range(steps):
+            self.step(first + k, ref)
+            evs[k + 1].record(stream)
+        torch.cuda.synchronize(self.dev)
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop() if sampler else None
+        N.nirc_sync(self.cache.h)  # raises if a tensor-core kernel reported a bounded-wait timeout
+        timing = N.nirc_timing_read(self.cache.h)
+        N.nirc_timing_enable(self.cache.h, False)
+        step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+        total_ms = evs[0].elapsed_time(evs[-1])
+        if world > 1:
+            t = torch.tensor([total_ms], device=self.dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return dict(total_ms=total_ms, step_ms=step_ms, timing=timing, clocks=clocks, mrse=float(self.mrse.item()))
+
+    def e2e(self, ref, first, steps, frames, stream):
+        """Same steps through the public API with host buffers: the frame's
+        scene blob copied in from pinned memory, image + MRSE + loss copied out."""
+        import torch
+        host_scenes = [torch.from_numpy(f.blob()).pin_memory() for f in frames]
+        host_img = torch.empty((self.P, 4), pin_memory=True)
+        host_small = torch.empty(2, dtype=torch.float64, pin_memory=True)
+        dev_scene = torch.empty_like(self.scene_dev[0])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(self.dev)
+        e0.record(stream)
+        for k in range(steps):
+            f = first + k
+            dev_scene.copy_(host_scenes[f % 60], non_blocking=True)
+            self.step(f, ref, scene=dev_scene)
+            host_img.copy_(self.img, non_blocking=True)
+            host_small[0:1].copy_(self.mrse, non_blocking=True)
+            host_small[1:2].copy_(self.loss.double(), non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(self.dev)
+        ms = e0.elapsed_time(e1)
+        if dist_info()[0] > 1:
+            t = torch.tensor([ms], device=self.dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, int(frames[0].blob().nbytes), int(self.P * 16 + 8 + 4)
+
+
+def _roofline(args, cfg, props, kernel_ms, dominant, sm_max):
+    fl_frame, per_row, per_pixel = flops_per_frame(cfg, args)
+    P = args.width * args.height
+    avg_ms = kernel_ms["cache"][0]
+    achieved = fl_frame / (avg_ms / 1e3) / 1e12
+    algorithmic = f"{per_row} FLOP/row x {rows_per_frame(args)} rows + {per_pixel} FLOP/pixel x {P} pixels"
+    if args.precision == "fp32":
+        peak = fp32_alu_peak_tflops(props.multi_processor_count, sm_max)
+        roof = {"kernel": "k_cache_simt", "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"derived FP32 FMA rate: {props.multi_processor_count} SMs x 128 lanes x 2 FLOP "
+                               f"x {sm_max:.0f} MHz"}
+    else:
+        peak, src = measured_tensor_peak()
+        roof = {"kernel": f"k_cache_tc<{args.precision}>", "bound": "tensor", "achieved": round(achieved, 3),
+                "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": src}
+    roof["algorithmic"] = algorithmic
+    roof["launch_ms"] = round(avg_ms, 4)
+    roof["dominant_kernel"] = dominant
+    return roof
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_info()
@@ -179,167 +316,77 @@ def run_ours(args):
     from paper_2412_04634_gb300 import nirc as N
 
     cfg, params, frames = build_workload(args, seed_offset=rank)
-    W, H = args.width, args.height
-    P = W * H
-    S = args.n_cache + args.n_resid
-    precision = {"fp32": N.NIRC_FP32_SIMT, "fp16": N.NIRC_FP16_TC, "bf16": N.NIRC_BF16_TC}[args.precision]
-    cache = N.Cache(cfg)
-    cache.set_params(params)
-    N.nirc_set_precision(cache.h, precision)
-    scene_dev = [N.scene_to_tensor(f, dev) for f in frames]
-    n_prims = frames[0].n_prims
     stream = torch.cuda.current_stream(dev)
-
-    img = torch.empty((P, 4), device=dev)
-    ref = torch.zeros((P, 4), device=dev)
-    tmp = torch.empty((P, 4), device=dev)
-    T = args.train
-    recs = torch.empty((T, 16), device=dev)
-    dirs = torch.empty((T, 3), device=dev)
-    tgts = torch.empty((T, 3), device=dev)
-    loss = torch.zeros(1, device=dev)
-    mrse = torch.zeros(1, dtype=torch.float64, device=dev)
-    seed = 1 + rank
-    first_timed = args.warmup
-    last_frame = (first_timed + args.steps - 1) % 60
-
-    # reference image of the last timed frame: plain path tracing (zero cache)
-    spp_per = 16
-    n_ref = max(1, args.ref_spp // spp_per)
-    for k in range(n_ref):
-        d = N.frame_desc(W, H, 0, spp_per, 16, 1000 + k, seed, n_prims, cache_mode=1)
-        N.nirc_estimate_frame(cache.h, scene_dev[last_frame], d, tmp)
-        ref += tmp
-    ref /= n_ref
-    torch.cuda.synchronize(dev)
-
-    def step(f):
-        fi = f % 60
-        d = N.frame_desc(W, H, args.n_cache, args.n_resid, args.depth, f, seed, n_prims)
-        N.nirc_estimate_frame(cache.h, scene_dev[fi], d, img)
-        N.nirc_gen_train(cache.h, scene_dev[fi], n_prims, W, H, T, f, seed, args.depth, recs, dirs, tgts)
-        N.nirc_train_step(cache.h, recs, dirs, tgts, loss)
-        N.nirc_frame_mrse(img, ref, mrse)
-
-    for f in range(args.warmup):
-        step(f)
-    torch.cuda.synchronize(dev)
-
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
     try:
         gpu_id = "GPU-" + str(props.uuid)
     except Exception:
         pass
-    sampler = ClockSampler(gpu_id)
-    sampler.start()
-    time.sleep(0.3)
-    N.nirc_timing_enable(cache.h, True)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    evs[0].record(stream)
-    for k in range(args.steps):
-        step(first_timed + k)
-        evs[k + 1].record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = sampler.stop()
-    N.nirc_sync(cache.h)  # raises if a tensor-core kernel reported a bounded-wait timeout
-    timing = N.nirc_timing_read(cache.h)
-    N.nirc_timing_enable(cache.h, False)
-    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    final_mrse = float(mrse.item())
+    seed = 1 + rank
+    first = args.warmup
+    last_frame = (first + args.steps - 1) % 60
 
-    # end to end through the public API with host buffers: pinned scene blob
-    # in, image + MRSE + loss out, every step
+    run = FrameRunner(N, args, cfg, params, frames, dev, seed)
+    ref, ref_spp = run.reference(last_frame, args.ref_spp)
+    run.set_precision(args.precision)
+    for f in range(args.warmup):
+        run.step(f, ref)
+    res = run.timed(ref, first, args.steps, stream, ClockSampler(gpu_id))
     e2e = None
     if not args.no_e2e:
-        host_scenes = [torch.from_numpy(f.blob()).pin_memory() for f in frames]
-        host_img = torch.empty((P, 4), pin_memory=True)
-        host_small = torch.empty(2, dtype=torch.float64, pin_memory=True)
-        dev_scene = torch.empty_like(scene_dev[0])
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for k in range(args.steps):
-            f = first_timed + k
-            dev_scene.copy_(host_scenes[f % 60], non_blocking=True)
-            d = N.frame_desc(W, H, args.n_cache, args.n_resid, args.depth, f, seed, n_prims)
-            N.nirc_estimate_frame(cache.h, dev_scene, d, img)
-            N.nirc_gen_train(cache.h, dev_scene, n_prims, W, H, T, f, seed, args.depth, recs, dirs, tgts)
-            N.nirc_train_step(cache.h, recs, dirs, tgts, loss)
-            N.nirc_frame_mrse(img, ref, mrse)
-            host_img.copy_(img, non_blocking=True)
-            host_small[0:1].copy_(mrse, non_blocking=True)
-            host_small[1:2].copy_(loss.double(), non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        e2e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * rows_per_frame(args) * args.steps / (e2e_ms / 1e3), "unit": "queries/s",
-               "h2d_bytes_per_step": int(frames[0].blob().nbytes),
-               "d2h_bytes_per_step": int(P * 16 + 8 + 4)}
+        ms, bi, bo = run.e2e(ref, first, args.steps, frames, stream)
+        e2e = {"value": world * rows_per_frame(args) * args.steps / (ms / 1e3), "unit": "queries/s",
+               "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+
+    # the FP32 SIMT twin on the same frames, training data and parameter trajectory
+    cmp = None
+    if args.compare_fp32 and args.precision != "fp32":
+        run.cache.close()
+        run32 = FrameRunner(N, args, cfg, params, frames, dev, seed)
+        run32.set_precision("fp32")
+        for f in range(args.warmup):
+            run32.step(f, ref)
+        r32 = run32.timed(ref, first, args.steps, stream)
+        cmp = {"value": world * rows_per_frame(args) * args.steps / (r32["total_ms"] / 1e3),
+               "ms_per_step": r32["total_ms"] / args.steps, "p50_ms": float(np.percentile(r32["step_ms"], 50)),
+               "p99_ms": float(np.percentile(r32["step_ms"], 99)), "frame_mrse": r32["mrse"],
+               "cache_kernel_ms": round(r32["timing"]["cache"][0] / max(1, r32["timing"]["cache"][1]), 4)}
+        run32.cache.close()
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
-    ms_per_step = total_ms / args.steps
-    value = world * rows_per_frame(args) * args.steps / (total_ms / 1e3)
+    timing, clocks = res["timing"], res["clocks"]
+    ms_per_step = res["total_ms"] / args.steps
+    value = world * rows_per_frame(args) * args.steps / (res["total_ms"] / 1e3)
     kernel_ms = {k: (v[0] / max(1, v[1]), v[1]) for k, v in timing.items() if v[1]}
     dominant = max(kernel_ms, key=lambda k: timing[k][0])
-    fl_frame, per_row, per_pixel = flops_per_frame(cfg, args)
     launches = sum(v[1] for v in timing.values()) + args.steps  # + one MRSE launch per step
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    # roofline of the cache-integral kernel (a dense contraction)
-    avg_ms = kernel_ms["cache"][0]
-    achieved = fl_frame / (avg_ms / 1e3) / 1e12
-    algorithmic = f"{per_row} FLOP/row x {rows_per_frame(args)} rows + {per_pixel} FLOP/pixel x {P} pixels"
-    if args.precision == "fp32":
-        peak = fp32_alu_peak_tflops(props.multi_processor_count, sm_max)
-        cache_roof = {"kernel": "k_cache_simt", "bound": "alu", "achieved": round(achieved, 3),
-                      "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                      "peak_source": f"derived FP32 FMA rate: {props.multi_processor_count} SMs x 128 lanes x 2 FLOP "
-                                     f"x {sm_max:.0f} MHz",
-                      "algorithmic": algorithmic}
-    else:
-        peak, src = measured_tensor_peak()
-        cache_roof = {"kernel": f"k_cache_tc<{args.precision}>", "bound": "tensor", "achieved": round(achieved, 3),
-                      "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                      "peak_source": src, "algorithmic": algorithmic}
-    roofline = dict(cache_roof)
-    roofline["dominant_kernel"] = dominant
-
+    roofline = _roofline(args, cfg, props, kernel_ms, dominant, sm_max)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(args, budget_s=args.cpu_budget_s)
-
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": W, "height": H, "n_cache": args.n_cache, "n_resid": args.n_resid,
-                   "max_depth": args.depth, "prims": n_prims, "train_samples": T,
+        "config": {"workload": WORKLOAD, "width": args.width, "height": args.height, "n_cache": args.n_cache,
+                   "n_resid": args.n_resid, "max_depth": args.depth, "prims": run.n_prims,
+                   "train_samples": args.train,
                    "precision": {"fp32": "fp32_simt", "fp16": "fp16_tc", "bf16": "bf16_tc"}[args.precision],
-                   "frames": f"{first_timed}..{first_timed + args.steps - 1} (mod 60)",
-                   "l2": "no flush: per-frame working set (~0.5 GB of records, rows, images, tables) > 129 MB L2",
+                   "frames": f"{first}..{first + args.steps - 1} (mod 60)",
+                   "l2": "no flush: per-frame working set (~0.6 GB of records, rows, images, tables) > 129 MB L2",
                    "parallelism": f"replicas x{world}"},
-        "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-        "frame_mrse": final_mrse, "mrse_reference": f"{n_ref * spp_per} spp path tracing, depth 16",
+        "p50_ms": float(np.percentile(res["step_ms"], 50)), "p99_ms": float(np.percentile(res["step_ms"], 99)),
+        "frame_mrse": res["mrse"], "mrse_reference": f"{ref_spp} spp path tracing, depth 16, frame {last_frame}",
         "kernel_ms": {k: round(v[0], 4) for k, v in kernel_ms.items()},
+        "fp32_simt": cmp,
+        "mrse_rel_diff_vs_fp32": (abs(res["mrse"] - cmp["frame_mrse"]) / cmp["frame_mrse"]) if cmp else None,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clocks,
     }
