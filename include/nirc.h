@@ -194,6 +194,26 @@ nirc_status nirc_query(nirc_handle* h, const nirc_record* d_records, const float
 nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_frame_desc* desc,
                                 float* d_out_rgba, const nirc_frame_aux* aux, void* stream);
 
+/* nirc_estimate_frame for callers that cannot allocate device memory during
+ * the call (the paper has no counterpart: it is an interface addition).
+ * nirc_estimate_frame grows handle-owned scratch with cudaMalloc the first
+ * time a larger frame arrives; callers that have reserved all device memory
+ * up front, real-time frame loops that must not pay cudaMalloc/cudaFree's
+ * implicit synchronisation, or applications whose allocation policy forbids
+ * it use this entry point instead.  It runs the same kernels, with the same
+ * arguments and results, on a fixed 4 MiB scratch area compiled into the
+ * library, and calls no cudaMalloc, cudaFree or other allocating routine.
+ * Limit: W * H * (96 + 32 * M) bytes (each of the three parts rounded up to
+ * 256) must fit in 4 MiB, e.g. 32,768 pixels at M = 1; larger frames return
+ * NIRC_ERR_BUDGET.  The first call on each device looks up the area's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call on a device shares the area
+ * and it keeps the last call's contents: calls that overlap on the GPU race
+ * on it, so order them on one stream.  Every GPU that loads the library holds
+ * the 4 MiB until the process exits. */
+nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d_scene, const nirc_frame_desc* desc,
+                                        float* d_out_rgba, const nirc_frame_aux* aux, void* stream);
+
 /* Training records from a separate path-tracing pass (section "Cache
  * application"): T paths, each from a uniformly drawn pixel, one record per
  * path at its first hit with the BSDF-sampled direction and the path-traced

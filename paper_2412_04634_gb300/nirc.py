@@ -81,6 +81,7 @@ def _load():
         "nirc_sync": ([P, P], st),
         "nirc_query": ([P, P, P, u64, P, P], st),
         "nirc_estimate_frame": ([P, P, P, P, P, P], st),
+        "nirc_estimate_frame_noalloc": ([P, P, P, P, P, P], st),
         "nirc_gen_train": ([P, P, u32, u32, u32, u64, u32, u64, u32, P, P, P, P], st),
         "nirc_train_step": ([P, P, P, P, u64, P, P], st),
         "nirc_frame_mrse": ([P, P, u64, ctypes.c_float, P, P], st),
@@ -189,6 +190,16 @@ def nirc_estimate_frame(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba:
     use_aux = any(x is not None for x in (lc, lr, sig, count, row_n))
     _check(_lib.nirc_estimate_frame(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
                                     ctypes.byref(aux) if use_aux else None, _stream(stream)))
+
+
+def nirc_estimate_frame_noalloc(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba: torch.Tensor,
+                                lc=None, lr=None, sig=None, count=None, row_n=None, stream=None):
+    """nirc_estimate_frame on the library's fixed scratch area (no device
+    allocation during the call; frames up to W*H*(96+32*M) <= 4 MiB)."""
+    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n))
+    use_aux = any(x is not None for x in (lc, lr, sig, count, row_n))
+    _check(_lib.nirc_estimate_frame_noalloc(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
+                                            ctypes.byref(aux) if use_aux else None, _stream(stream)))
 
 
 def nirc_gen_train(h, scene: torch.Tensor, n_prims, width, height, T, frame, seed, max_depth,
