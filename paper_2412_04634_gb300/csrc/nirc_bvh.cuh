@@ -1,0 +1,324 @@
+// nirc_bvh.cuh -- per-CTA bounding-volume hierarchy over the scene's
+// primitives, built in shared memory and used for nearest-hit queries.
+//
+// Primitives whose box spans more than half of the scene (walls, floors) are
+// kept in a short list tested by brute force first; they would overlap every
+// node of a hierarchy.  The others get a binary radix tree: conservative
+// AABBs, 30-bit Morton codes of the centroids made unique with the primitive
+// index, a bitonic sort, the topology of Karras (HPG 2012), then boxes
+// bottom-up.  A query tests the large list, then walks the tree in near-first
+// order with a short stack, entering a child box only when a ray could hit
+// it no later than the best hit so far (with slack).  Primitives are tested
+// with the same strict binary32 routines as the brute-force loop, keeping the
+// smallest (t, primitive index): boxes are expanded and pruning is
+// conservative, so the result equals the brute-force nearest hit exactly.
+#pragma once
+
+#include "nirc_device.cuh"
+
+namespace nirc {
+
+struct __align__(16) BvhNode {
+    float4 lo;  // xyz = box min, w = left child (bits; bit 31 set = leaf, low bits = primitive)
+    float4 hi;  // xyz = box max, w = right child
+};
+
+struct Bvh {
+    const BvhNode* nodes;
+    const uint32_t* large;  // primitives tested by brute force
+    uint32_t n_large;
+    uint32_t n_tree;        // leaves of the tree
+    uint32_t root;          // node index, or kLeafBit | primitive when n_tree == 1
+};
+
+constexpr uint32_t kLeafBit = 0x80000000u;
+constexpr int kBvhStack = 64;  // >= tree depth (at most 62 for 64-bit unique keys)
+
+// Shared-memory bytes the build needs for n primitives.
+__host__ __device__ inline size_t bvh_smem_bytes(uint32_t n) {
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    return (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode) + (size_t)np2 * 8 + (size_t)n * 32 + (size_t)n * 4 * 2 + 16;
+}
+
+__device__ __forceinline__ uint32_t expand_bits10(uint32_t v) {
+    v = (v * 0x00010001u) & 0xFF0000FFu;
+    v = (v * 0x00000101u) & 0x0F00F00Fu;
+    v = (v * 0x00000011u) & 0xC30C30C3u;
+    v = (v * 0x00000005u) & 0x49249249u;
+    return v;
+}
+
+__device__ __forceinline__ int lcp_delta(const unsigned long long* keys, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    return __clzll(keys[i] ^ keys[j]);
+}
+
+// All threads of the CTA call it; `mem` holds bvh_smem_bytes(n) bytes, 16-byte aligned.
+__device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, unsigned char* mem) {
+    uint32_t np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    BvhNode* nodes = reinterpret_cast<BvhNode*>(mem);
+    unsigned char* p = mem + (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
+    p += (size_t)np2 * 8;
+    float4* box = reinterpret_cast<float4*>(p);  // 2 per primitive: lo, hi
+    p += (size_t)n * 32;
+    uint32_t* large = reinterpret_cast<uint32_t*>(p);
+    p += (size_t)n * 4;
+    int* done = reinterpret_cast<int*>(p);  // internal node state
+    p += (size_t)n * 4;
+    float* scal = reinterpret_cast<float*>(p);  // [centroid min, 1/extent, n_large, n_small]
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+
+    // 1. conservative primitive boxes
+    for (uint32_t i = tid; i < n; i += nt) {
+        const PrimGeom& g = prims[i];
+        float3 lo, hi;
+        if (__float_as_uint(g.n_kind.w) == KIND_SPHERE) {
+            const float r = g.a_r.w;
+            lo = make_float3(g.a_r.x - r, g.a_r.y - r, g.a_r.z - r);
+            hi = make_float3(g.a_r.x + r, g.a_r.y + r, g.a_r.z + r);
+        } else {
+            const float ax = g.a_r.x, ay = g.a_r.y, az = g.a_r.z;
+            const float ux = g.u_iuu.x, uy = g.u_iuu.y, uz = g.u_iuu.z;
+            const float vx = g.v_ivv.x, vy = g.v_ivv.y, vz = g.v_ivv.z;
+            lo = make_float3(fminf(fminf(ax, ax + ux), fminf(ax + vx, ax + ux + vx)),
+                             fminf(fminf(ay, ay + uy), fminf(ay + vy, ay + uy + vy)),
+                             fminf(fminf(az, az + uz), fminf(az + vz, az + uz + vz)));
+            hi = make_float3(fmaxf(fmaxf(ax, ax + ux), fmaxf(ax + vx, ax + ux + vx)),
+                             fmaxf(fmaxf(ay, ay + uy), fmaxf(ay + vy, ay + uy + vy)),
+                             fmaxf(fmaxf(az, az + uz), fmaxf(az + vz, az + uz + vz)));
+        }
+        const float m = fmaxf(fmaxf(fmaxf(fabsf(lo.x), fabsf(lo.y)), fmaxf(fabsf(lo.z), fabsf(hi.x))),
+                              fmaxf(fabsf(hi.y), fabsf(hi.z)));
+        const float e = 1e-5f + 1e-5f * m;  // far above the rounding of the intersection routines
+        box[2 * i] = make_float4(lo.x - e, lo.y - e, lo.z - e, 0.f);
+        box[2 * i + 1] = make_float4(hi.x + e, hi.y + e, hi.z + e, 0.f);
+    }
+    __syncthreads();
+    // 2. large / small split and centroid bounds of the small primitives (serial, n <= 1024)
+    if (tid == 0) {
+        float3 slo = make_float3(3e38f, 3e38f, 3e38f), shi = make_float3(-3e38f, -3e38f, -3e38f);
+        for (uint32_t i = 0; i < n; ++i) {
+            const float4 l = box[2 * i], h = box[2 * i + 1];
+            slo = make_float3(fminf(slo.x, l.x), fminf(slo.y, l.y), fminf(slo.z, l.z));
+            shi = make_float3(fmaxf(shi.x, h.x), fmaxf(shi.y, h.y), fmaxf(shi.z, h.z));
+        }
+        const float scene = fmaxf(fmaxf(shi.x - slo.x, shi.y - slo.y), shi.z - slo.z);
+        uint32_t nl = 0;
+        float mn = 3e38f, mx = -3e38f;
+        for (uint32_t i = 0; i < n; ++i) {
+            const float4 l = box[2 * i], h = box[2 * i + 1];
+            const float ext = fmaxf(fmaxf(h.x - l.x, h.y - l.y), h.z - l.z);
+            if (ext > 0.5f * scene) {
+                large[nl++] = i;
+                box[2 * i].w = 1.f;  // marks a large primitive
+                continue;
+            }
+            const float c[3] = {0.5f * (l.x + h.x), 0.5f * (l.y + h.y), 0.5f * (l.z + h.z)};
+            for (int d = 0; d < 3; ++d) {
+                mn = fminf(mn, c[d]);
+                mx = fmaxf(mx, c[d]);
+            }
+        }
+        scal[0] = mn;
+        scal[1] = mx > mn ? 1.0f / (mx - mn) : 1.0f;
+        scal[2] = __uint_as_float(nl);
+        scal[3] = __uint_as_float(n - nl);
+    }
+    __syncthreads();
+    const float cmin = scal[0], cinv = scal[1];
+    Bvh out;
+    out.nodes = nodes;
+    out.large = large;
+    out.n_large = __float_as_uint(scal[2]);
+    out.n_tree = __float_as_uint(scal[3]);
+    out.root = 0;
+    for (uint32_t i = tid; i < np2; i += nt) {
+        unsigned long long k = ~0ull;  // padding and large primitives sort to the end
+        if (i < n && box[2 * i].w == 0.f) {
+            const float4 l = box[2 * i], h = box[2 * i + 1];
+            const float c[3] = {0.5f * (l.x + h.x), 0.5f * (l.y + h.y), 0.5f * (l.z + h.z)};
+            uint32_t q[3];
+            for (int d = 0; d < 3; ++d) {
+                const float u = fminf(fmaxf((c[d] - cmin) * cinv, 0.f), 1.f);
+                q[d] = min((uint32_t)(u * 1023.0f), 1023u);
+            }
+            const uint32_t morton = (expand_bits10(q[0]) << 2) | (expand_bits10(q[1]) << 1) | expand_bits10(q[2]);
+            k = ((unsigned long long)morton << 32) | i;
+        }
+        keys[i] = k;
+    }
+    __syncthreads();
+    // 3. bitonic sort of np2 keys
+    for (uint32_t size = 2; size <= np2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t t = tid; t < np2 / 2; t += nt) {
+                const uint32_t i = 2 * t - (t & (stride - 1));
+                const uint32_t j = i + stride;
+                const bool up = (i & size) == 0;
+                const unsigned long long a = keys[i], b = keys[j];
+                if ((a > b) == up) {
+                    keys[i] = b;
+                    keys[j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const uint32_t m = out.n_tree;
+    if (m <= 1) {
+        out.root = m == 1 ? (kLeafBit | (uint32_t)(keys[0] & 0x3FFu)) : 0u;
+        return out;
+    }
+    // 4. radix-tree topology over the m small primitives (sorted keys 0..m-1)
+    for (uint32_t ii = tid; ii + 1 < m; ii += nt) {
+        const int i = (int)ii, nn = (int)m;
+        const int d = (lcp_delta(keys, nn, i, i + 1) - lcp_delta(keys, nn, i, i - 1)) >= 0 ? 1 : -1;
+        const int dmin = lcp_delta(keys, nn, i, i - d);
+        int lmax = 2;
+        while (lcp_delta(keys, nn, i, i + lmax * d) > dmin) lmax <<= 1;
+        int l = 0;
+        for (int t = lmax >> 1; t >= 1; t >>= 1)
+            if (lcp_delta(keys, nn, i, i + (l + t) * d) > dmin) l += t;
+        const int j = i + l * d;
+        const int dnode = lcp_delta(keys, nn, i, j);
+        int s = 0;
+        for (int t = (l + 1) >> 1;; t = (t + 1) >> 1) {
+            if (lcp_delta(keys, nn, i, i + (s + t) * d) > dnode) s += t;
+            if (t == 1) break;
+        }
+        const int gamma = i + s * d + min(d, 0);
+        const int lo = min(i, j), hi = max(i, j);
+        const uint32_t left = lo == gamma ? (kLeafBit | (uint32_t)(keys[gamma] & 0x3FFu)) : (uint32_t)gamma;
+        const uint32_t right = hi == gamma + 1 ? (kLeafBit | (uint32_t)(keys[gamma + 1] & 0x3FFu)) : (uint32_t)(gamma + 1);
+        nodes[i].lo.w = __uint_as_float(left);
+        nodes[i].hi.w = __uint_as_float(right);
+        done[i] = 0;
+    }
+    __syncthreads();
+    // 5. boxes bottom-up.  done: 0 = open, 2 = box written this round (not
+    // yet usable by parents), 1 = finished.
+    for (int iter = 0; iter < 64; ++iter) {
+        for (uint32_t i = tid; i + 1 < m; i += nt) {
+            if (done[i] != 0) continue;
+            const uint32_t c[2] = {__float_as_uint(nodes[i].lo.w), __float_as_uint(nodes[i].hi.w)};
+            float4 bl[2], bh[2];
+            bool ready = true;
+            for (int k = 0; k < 2; ++k) {
+                if (c[k] & kLeafBit) {
+                    const uint32_t pidx = c[k] & ~kLeafBit;
+                    bl[k] = box[2 * pidx];
+                    bh[k] = box[2 * pidx + 1];
+                } else if (done[c[k]] == 1) {
+                    bl[k] = nodes[c[k]].lo;
+                    bh[k] = nodes[c[k]].hi;
+                } else {
+                    ready = false;
+                }
+            }
+            if (!ready) continue;
+            nodes[i].lo = make_float4(fminf(bl[0].x, bl[1].x), fminf(bl[0].y, bl[1].y), fminf(bl[0].z, bl[1].z),
+                                      nodes[i].lo.w);
+            nodes[i].hi = make_float4(fmaxf(bh[0].x, bh[1].x), fmaxf(bh[0].y, bh[1].y), fmaxf(bh[0].z, bh[1].z),
+                                      nodes[i].hi.w);
+            done[i] = 2;
+        }
+        __syncthreads();
+        int all = 1;
+        for (uint32_t i = tid; i + 1 < m; i += nt) {
+            if (done[i] == 2) done[i] = 1;
+            if (done[i] == 0) all = 0;
+        }
+        if (__syncthreads_and(all)) break;
+    }
+    return out;
+}
+
+__device__ __forceinline__ bool box_entry(const float4& lo, const float4& hi, V3 o, float3 inv, float best,
+                                          float& tnear) {
+    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
+    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
+    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
+    const float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+    tnear = tmin;
+    // conservative: slack on both ends (boxes are expanded as well)
+    return tmax * 1.00001f + 1e-6f >= fmaxf(tmin, 0.f) && tmin <= best * 1.00001f + 1e-6f;
+}
+
+__device__ __forceinline__ float safe_inv(float d) {
+    const float dd = fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
+    return 1.0f / dd;
+}
+
+__device__ __forceinline__ void test_prim(const PrimGeom* __restrict__ prims, uint32_t pi, V3 o, V3 d, float& best,
+                                          int& idx) {
+    const PrimGeom& g = prims[pi];
+    float t;
+    const bool hit = (__float_as_uint(g.n_kind.w) == KIND_SPHERE) ? hit_sphere(g, o, d, t) : hit_rect(g, o, d, t);
+    if (hit && (t < best || (t == best && (int)pi < idx))) {
+        best = t;
+        idx = (int)pi;
+    }
+}
+
+// Nearest hit: the large list, then the tree; same (t, index) result as
+// trace_nearest.  Child indices are range-checked and the walk is capped at
+// 4n + 64 visits, so a malformed tree yields a wrong answer (caught by the
+// parity tests) rather than an out-of-range read or an endless loop.
+__device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ prims, uint32_t n, V3 o, V3 d,
+                                  float& t_hit) {
+    float best = __int_as_float(0x7f800000);
+    int idx = -1;
+    for (uint32_t k = 0; k < b.n_large; ++k) test_prim(prims, b.large[k], o, d, best, idx);
+    if (b.n_tree >= 1) {
+        const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+        const uint32_t m = b.n_tree;
+        uint32_t stack[kBvhStack];
+        int sp = 0;
+        uint32_t node = b.root;
+        for (uint32_t visits = 0; visits < 4 * n + 64; ++visits) {
+            const bool leaf = node & kLeafBit;
+            if (leaf) {
+                if ((node & ~kLeafBit) < n) test_prim(prims, node & ~kLeafBit, o, d, best, idx);
+            } else if (node + 1 < m) {
+                const BvhNode nd = b.nodes[node];
+                const uint32_t c0 = __float_as_uint(nd.lo.w), c1 = __float_as_uint(nd.hi.w);
+                float t0 = 0.f, t1 = 0.f;
+                bool h0, h1;
+                if (c0 & kLeafBit) {
+                    h0 = true;
+                } else if (c0 + 1 < m) {
+                    h0 = box_entry(b.nodes[c0].lo, b.nodes[c0].hi, o, inv, best, t0);
+                } else {
+                    h0 = false;
+                }
+                if (c1 & kLeafBit) {
+                    h1 = true;
+                } else if (c1 + 1 < m) {
+                    h1 = box_entry(b.nodes[c1].lo, b.nodes[c1].hi, o, inv, best, t1);
+                } else {
+                    h1 = false;
+                }
+                if (h0 && h1) {
+                    const bool first0 = t0 <= t1;
+                    if (sp < kBvhStack) stack[sp++] = first0 ? c1 : c0;
+                    node = first0 ? c0 : c1;
+                    continue;
+                }
+                if (h0 || h1) {
+                    node = h0 ? c0 : c1;
+                    continue;
+                }
+            }
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    t_hit = best;
+    return idx;
+}
+
+}  // namespace nirc

@@ -3,7 +3,7 @@
 //
 // Work unit: a block of 128 pixels; with S = N + M rows per pixel it holds
 // exactly S row tiles of 128 rows.  One warpgroup (128 threads, thread t =
-// tile row t = TMEM lane t) owns a block at a time; a CTA runs several
+// tile row t = TMEM lane t) owns a block at a time; a CTA runs up to five
 // warpgroups so that one warpgroup's SIMT work (sampling, encodings,
 // epilogues) overlaps another's MMAs.
 //
@@ -16,7 +16,7 @@
 //                shading point and reused by all its N + M rows.
 //  row tile      thread t samples its row's direction (cache rows) or reads
 //                it (residual rows), encodes it and writes the A row
-//                [e_dir (16) | one-hot of its pixel relative to k0 (48)];
+//                [e_dir (16) | one-hot of its pixel within a 48-wide window];
 //                layer 0 = W0_dir e_dir + H onehot (1 + up to 3 MMAs, K = 16
 //                each), then the hidden layers (4 MMAs each) and the output
 //                layer (N = 16, 3 used); each epilogue reads its row from
@@ -47,8 +47,8 @@ __host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidde
 
 size_t tc_image_bytes(uint32_t hidden) { return tcimg::off_bias(hidden) + tcimg::n_bias(hidden) * 4; }
 
-constexpr uint32_t kWgStride = 44032;  // A 16 KB | H 16 KB | records 8 KB | contributions 2 KB | carry 64 B
-constexpr uint32_t kOffA = 0, kOffH = 16384, kOffRec = 32768, kOffContrib = 40960, kOffCarry = 43008;
+constexpr uint32_t kWgStride = 35840;  // A 16 KB | H 16 KB | contributions 2 KB | 2 carry slots 128 B (1 KB rounded)
+constexpr uint32_t kOffA = 0, kOffH = 16384, kOffContrib = 32768, kOffCarry = 34816;
 
 template <uint32_t AB>
 __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_t* __restrict__ img) {
@@ -122,31 +122,94 @@ __device__ __forceinline__ uint16_t to16(float v) {
     return AB ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
 }
 
-// Row r of a swizzled A tile from 64 floats (optionally ReLU + bias).
-template <uint32_t AB, bool RELU>
-__device__ __forceinline__ void write_row(uint32_t tile, uint32_t r, const float* x) {
-    const uint32_t row = tile + (r >> 3) * 1024u + (r & 7u) * 128u;
-#pragma unroll
-    for (uint32_t c = 0; c < 8; ++c) {
-        const float* y = x + 8 * c;
-        uint32_t d0, d1, d2, d3;
-        if (RELU) {
-            d0 = pack2_relu<AB>(y[0], y[1]);
-            d1 = pack2_relu<AB>(y[2], y[3]);
-            d2 = pack2_relu<AB>(y[4], y[5]);
-            d3 = pack2_relu<AB>(y[6], y[7]);
-        } else {
-            d0 = pack2<AB>(y[0], y[1]);
-            d1 = pack2<AB>(y[2], y[3]);
-            d2 = pack2<AB>(y[4], y[5]);
-            d3 = pack2<AB>(y[6], y[7]);
-        }
-        tc::sts128(row + ((c ^ (r & 7u)) << 4), d0, d1, d2, d3);
-    }
+
+// Swizzled 16-byte chunk c (8 elements) of row r of a tile.
+__device__ __forceinline__ void sts_chunk(uint32_t tile, uint32_t r, uint32_t c, uint32_t d0, uint32_t d1, uint32_t d2,
+                                          uint32_t d3) {
+    tc::sts128(tile + (r >> 3) * 1024u + (r & 7u) * 128u + (((c ^ r) & 7u) << 4), d0, d1, d2, d3);
 }
 
 template <uint32_t AB>
-__global__ void __launch_bounds__(512, 1)
+__device__ __forceinline__ void sts_chunk8(uint32_t tile, uint32_t r, uint32_t c, const float* y) {
+    sts_chunk(tile, r, c, pack2<AB>(y[0], y[1]), pack2<AB>(y[2], y[3]), pack2<AB>(y[4], y[5]), pack2<AB>(y[6], y[7]));
+}
+
+// Epilogue of one hidden layer for row r: 64 accumulators from TMEM (two
+// halves of 32 columns), + bias (none for layer 0, whose h_pix holds b0),
+// ReLU, rounding to 16 bits, swizzled store into the next A tile.
+template <uint32_t AB>
+__device__ __forceinline__ void epilogue_row(uint32_t taddr, const float* __restrict__ bias, uint32_t tile, uint32_t r) {
+#pragma unroll
+    for (uint32_t half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        tc::tmem_ld32(taddr + 32u * half, v);
+        tc::tmem_wait_ld();
+        float x[32];
+        if (bias) {
+            const float2* b2 = reinterpret_cast<const float2*>(bias + 32u * half);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float2 y =
+                    __fadd2_rn(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), b2[i]);
+                x[2 * i] = y.x;
+                x[2 * i + 1] = y.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(v[i]);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+            const float* y = x + 8 * q;
+            sts_chunk(tile, r, 4u * half + q, pack2_relu<AB>(y[0], y[1]), pack2_relu<AB>(y[2], y[3]),
+                      pack2_relu<AB>(y[4], y[5]), pack2_relu<AB>(y[6], y[7]));
+        }
+    }
+}
+
+// sin/cos of 2^k a for k = 0..3 from (sin a, cos a), by the double-angle identities.
+__device__ __forceinline__ void octaves(float s, float c, float* e) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        e[2 * k] = s;
+        e[2 * k + 1] = c;
+        const float s2 = 2.0f * s * c;
+        const float c2 = (c - s) * (c + s);
+        s = s2;
+        c = c2;
+    }
+}
+
+// Direction features of w without transcendentals: with theta = acos(w_z) and
+// phi' = atan2(w_y, w_x) mapped to [0, 2 pi), pi theta_hat = theta and
+// pi phi_hat = phi' / 2, so sin/cos follow from w_z and from the half-angle
+// identities in forms free of cancellation.
+__device__ __forceinline__ void dir_features_fast(V3 w, float* e) {
+    const float c = fminf(fmaxf(w.z, -1.f), 1.f);
+    const float s = sqrtf(fmaxf((1.f - c) * (1.f + c), 0.f));
+    octaves(s, c, e);
+    const float r2 = w.x * w.x + w.y * w.y;
+    float sp = 0.f, cp = 1.f;
+    if (r2 > 0.f) {
+        const float r = sqrtf(r2);
+        const float ir = 0.5f / r;
+        if (w.x >= 0.f) {
+            const float a = r + w.x;
+            cp = sqrtf(a * ir);
+            sp = sqrtf(w.y * w.y * ir / a);
+        } else {
+            const float a = r - w.x;
+            sp = sqrtf(a * ir);
+            cp = sqrtf(w.y * w.y * ir / a);
+        }
+        const bool upper = (w.y > 0.f) || (w.y == 0.f && w.x >= 0.f);
+        if (!upper) cp = -cp;
+    }
+    octaves(sp, cp, e + 8);
+}
+
+template <uint32_t AB>
+__global__ void __launch_bounds__(640, 1)
     k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
                const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
                const ResidRow* __restrict__ rows, float4* __restrict__ out, float* __restrict__ lc_out,
@@ -195,9 +258,8 @@ __global__ void __launch_bounds__(512, 1)
     const uint32_t wout = sbase + tcimg::off_wout(a.s.hidden);
     const float* bias = reinterpret_cast<const float*>(gbase + tcimg::off_bias(a.s.hidden));
     const uint32_t tA = wgs + kOffA, tH = wgs + kOffH;
-    nirc_record* s_rec = reinterpret_cast<nirc_record*>(wgg + kOffRec);
     float4* s_contrib = reinterpret_cast<float4*>(wgg + kOffContrib);
-    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);
+    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);  // two slots of 16 floats
     const uint32_t id64 = tc::idesc_f16(AB, 128, 64), id16 = tc::idesc_f16(AB, 128, 16);
     const uint16_t one16 = AB ? 0x3F80u : 0x3C00u;
 
@@ -231,85 +293,77 @@ __global__ void __launch_bounds__(512, 1)
         const uint32_t npix = min(128u, a.P - p0);
         // ------------------------------------------------ pixel stage
         {
-            const bool pin = t < npix;
-            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
-            if (pin) {
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+            if (t < npix) {
                 const float4* rq = reinterpret_cast<const float4*>(recs + p0 + t);
                 r0 = __ldg(rq);
                 r1 = __ldg(rq + 1);
-                r2 = __ldg(rq + 2);
-                r3 = __ldg(rq + 3);
             }
-            float4* sr = reinterpret_cast<float4*>(s_rec + t);
-            sr[0] = r0;
-            sr[1] = r1;
-            sr[2] = r2;
-            sr[3] = r3;
-            float f[64];
-#pragma unroll
-            for (int i = 0; i < 64; ++i) f[i] = 0.f;
             const V3 p{r0.x, r0.y, r0.z}, n{r0.w, r1.x, r1.y};
-            uint32_t k = 0;
+            float f[8];
+            uint32_t c = 0;  // next chunk of the A row
             if (a.s.hashgrid) {
                 const uint64_t T = (uint64_t)a.g.mask + 1;
-                for (uint32_t l = 0; l < a.g.n_levels; ++l) {
-                    uint32_t idx[8];
-                    float w[8];
-                    grid_corners(a.g.level[l], a.g.mask, p, idx, w);
-                    const __half2* tab = hash16 + (uint64_t)l * T;
-                    float f0 = 0.f, f1 = 0.f;
+                for (uint32_t l0 = 0; l0 < a.g.n_levels; l0 += 4, ++c) {  // 12 or 16 levels
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const float2 v = __half22float2(__ldg(tab + idx[c]));
-                        f0 += w[c] * v.x;
-                        f1 += w[c] * v.y;
-                    }
-                    // k is at most 31 here; the switch keeps f[] in registers
+                    for (uint32_t q = 0; q < 4; ++q) {
+                        const uint32_t l = l0 + q;
+                        uint32_t idx[8];
+                        float w[8];
+                        grid_corners(a.g.level[l], a.g.mask, p, idx, w);
+                        const __half2* tab = hash16 + (uint64_t)l * T;
+                        float f0 = 0.f, f1 = 0.f;
 #pragma unroll
-                    for (int q = 0; q < 32; q += 2)
-                        if ((uint32_t)q == k) {
-                            f[q] = f0;
-                            f[q + 1] = f1;
+                        for (int k = 0; k < 8; ++k) {
+                            const float2 v = __half22float2(__ldg(tab + idx[k]));
+                            f0 += w[k] * v.x;
+                            f1 += w[k] * v.y;
                         }
-                    k += 2;
+                        f[2 * q] = f0;
+                        f[2 * q + 1] = f1;
+                    }
+                    sts_chunk8<AB>(tA, t, c, f);
                 }
             } else {
                 freq4(p.x, f);
-                freq4(p.y, f + 8);
-                freq4(p.z, f + 16);
-                k = 24;
+                sts_chunk8<AB>(tA, t, c++, f);
+                freq4(p.y, f);
+                sts_chunk8<AB>(tA, t, c++, f);
+                freq4(p.z, f);
+                sts_chunk8<AB>(tA, t, c++, f);
             }
-            float e[24];
-            freq4(n.x, e);
-            freq4(n.y, e + 8);
-            freq4(n.z, e + 16);
-            if (k == 32) {
-#pragma unroll
-                for (int i = 0; i < 24; ++i) f[32 + i] = e[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 24; ++i) f[24 + i] = e[i];
-            }
-            write_row<AB, false>(tA, t, f);
+            freq4(n.x, f);
+            sts_chunk8<AB>(tA, t, c++, f);
+            freq4(n.y, f);
+            sts_chunk8<AB>(tA, t, c++, f);
+            freq4(n.z, f);
+            sts_chunk8<AB>(tA, t, c++, f);
+            for (; c < 8; ++c) sts_chunk(tA, t, c, 0u, 0u, 0u, 0u);
         }
         sync_wg();
         issue_k64(tA, w0pix, id64);
         wait_mma();
         {
-            uint32_t v[64];
-            tc::tmem_ld64(tmem_row, v);
-            tc::tmem_wait_ld();
-            // H operand: element (n = output unit, k = pixel t)
+            // H operand: element (n = output unit, k = pixel t), h = accumulator + b0
             const uint32_t hk = tH + (t >> 6) * 8192u;
 #pragma unroll
-            for (uint32_t o = 0; o < 64; ++o)
-                tc::sts16(hk + tc::sw128_offset(o, t & 63u), to16<AB>(__uint_as_float(v[o]) + bias[o]));
+            for (uint32_t half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem_row + 32u * half, v);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (uint32_t o = 0; o < 32; ++o) {
+                    const uint32_t oo = 32u * half + o;
+                    tc::sts16(hk + tc::sw128_offset(oo, t & 63u), to16<AB>(__uint_as_float(v[o]) + bias[oo]));
+                }
+            }
         }
         sync_wg();
 
         // ------------------------------------------------ row tiles
         const uint32_t R = npix * S;
-        for (uint32_t j0 = 0; j0 < R; j0 += 128u) {
+        uint32_t jt = 0;
+        for (uint32_t j0 = 0; j0 < R; j0 += 128u, ++jt) {
             const uint32_t r = j0 + t;
             const bool rin = r < R;
             const uint32_t pl = rin ? r / S : 0u;
@@ -320,42 +374,38 @@ __global__ void __launch_bounds__(512, 1)
             const uint32_t n_oh = (plast - (pf & ~15u) + 16u) >> 4;  // <= 3 for S >= 4
             const uint32_t kb = min(pf & ~15u, 128u - 16u * n_oh);
 
-            const nirc_record& rc = s_rec[pl];
-            const uint32_t flags = rc.flags;
-            const bool pvalid = rin && (flags & 1u);
             V3 wi{0.f, 0.f, 1.f};
             float3 w = make_float3(0.f, 0.f, 0.f);
             bool ok = false;
             uint32_t word = 0;
-            if (pvalid) {
-                if (s < a.N) {
-                    const BsdfSample bs = sample_bsdf(V3{rc.n[0], rc.n[1], rc.n[2]}, V3{rc.wo[0], rc.wo[1], rc.wo[2]},
-                                                      make_float3(rc.albedo[0], rc.albedo[1], rc.albedo[2]),
-                                                      rc.roughness, (flags >> 1) & 3u, a.k0, a.k1, p0 + pl, s,
-                                                      PURPOSE_CACHE_DIR);
-                    wi = bs.wi;
-                    w = bs.w;
-                    ok = bs.valid;
-                    word = bs.word;
-                } else {
-                    const ResidRow* rr = rows + (uint64_t)(p0 + pl) * a.M + (s - a.N);
-                    const float4 d = __ldg(&rr->wi), ww = __ldg(&rr->w);
-                    wi = V3{d.x, d.y, d.z};
-                    w = make_float3(ww.x, ww.y, ww.z);
-                    ok = d.w != 0.f;
+            {
+                const float4* rq = reinterpret_cast<const float4*>(recs + p0 + pl);
+                const float4 q3 = __ldg(rq + 3);
+                const uint32_t flags = __float_as_uint(q3.z);
+                if (rin && (flags & 1u)) {
+                    if (s < a.N) {
+                        const float4 q0 = __ldg(rq), q1 = __ldg(rq + 1), q2 = __ldg(rq + 2);
+                        const BsdfSample bs =
+                            sample_bsdf(V3{q0.w, q1.x, q1.y}, V3{q1.z, q1.w, q2.x}, make_float3(q2.y, q2.z, q2.w),
+                                        q3.x, (flags >> 1) & 3u, a.k0, a.k1, p0 + pl, s, PURPOSE_CACHE_DIR);
+                        wi = bs.wi;
+                        w = bs.w;
+                        ok = bs.valid;
+                        word = bs.word;
+                    } else {
+                        const ResidRow* rr = rows + (uint64_t)(p0 + pl) * a.M + (s - a.N);
+                        const float4 d = __ldg(&rr->wi), ww = __ldg(&rr->w);
+                        wi = V3{d.x, d.y, d.z};
+                        w = make_float3(ww.x, ww.y, ww.z);
+                        ok = d.w != 0.f;
+                    }
                 }
             }
             {
-                float th, ph, e[16];
-                dir_angles(wi, th, ph);
-                freq4(th, e);
-                freq4(ph, e + 8);
-                const uint32_t row = tA + (t >> 3) * 1024u + (t & 7u) * 128u;
-                const uint32_t sw = t & 7u;
-                tc::sts128(row + ((0u ^ sw) << 4), pack2<AB>(e[0], e[1]), pack2<AB>(e[2], e[3]), pack2<AB>(e[4], e[5]),
-                           pack2<AB>(e[6], e[7]));
-                tc::sts128(row + ((1u ^ sw) << 4), pack2<AB>(e[8], e[9]), pack2<AB>(e[10], e[11]),
-                           pack2<AB>(e[12], e[13]), pack2<AB>(e[14], e[15]));
+                float e[16];
+                dir_features_fast(wi, e);
+                sts_chunk8<AB>(tA, t, 0u, e);
+                sts_chunk8<AB>(tA, t, 1u, e + 8);
                 const uint32_t oh = rin ? pl - kb : 0xFFFFu;  // one-hot position among columns 16..63
 #pragma unroll
                 for (uint32_t c = 2; c < 8; ++c) {
@@ -365,7 +415,7 @@ __global__ void __launch_bounds__(512, 1)
                         const uint32_t e2 = oh - lo;
                         d[e2 >> 1] = (uint32_t)one16 << ((e2 & 1u) * 16);
                     }
-                    tc::sts128(row + ((c ^ sw) << 4), d[0], d[1], d[2], d[3]);
+                    sts_chunk(tA, t, c, d[0], d[1], d[2], d[3]);
                 }
             }
             sync_wg();
@@ -382,24 +432,7 @@ __global__ void __launch_bounds__(512, 1)
             wait_mma();
             for (uint32_t l = 0; l < a.s.hidden; ++l) {
                 // epilogue of layer l (l = 0: h_pix already holds b0), then the MMAs of layer l + 1
-                uint32_t v[64];
-                tc::tmem_ld64(tmem_row, v);
-                tc::tmem_wait_ld();
-                float x[64];
-                if (l == 0) {
-#pragma unroll
-                    for (int i = 0; i < 64; ++i) x[i] = __uint_as_float(v[i]);
-                } else {
-                    const float2* b2 = reinterpret_cast<const float2*>(bias + 64 + (l - 1) * 64);
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float2 y = __fadd2_rn(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])),
-                                                    b2[i]);
-                        x[2 * i] = y.x;
-                        x[2 * i + 1] = y.y;
-                    }
-                }
-                write_row<AB, true>(tA, t, x);
+                epilogue_row<AB>(tmem_row, l == 0 ? nullptr : bias + 64 + (l - 1) * 64, tA, t);
                 sync_wg();
                 if (l + 1 < a.s.hidden) {
                     issue_k64(tA, sbase + tcimg::off_wh(l), id64);
@@ -429,31 +462,36 @@ __global__ void __launch_bounds__(512, 1)
                               : make_float4(0.f, 0.f, 0.f, __uint_as_float(word));
             tc::named_bar(bar_id, 128);
 
-            // one thread per pixel of this tile: rows in sample order
-            if (t <= plast - pf) {
-                const uint32_t q = pf + t;
+            // one thread per pixel of this tile, spread over the four warps:
+            // pixel i -> thread 32 (i % 4) + i / 4; rows summed in sample order
+            const uint32_t i_pix = 4u * (t & 31u) + (t >> 5);
+            if (i_pix <= plast - pf) {
+                const uint32_t q = pf + i_pix;
                 const uint32_t q_lo = q * S, q_hi = q_lo + S;
                 const uint32_t lo = max(q_lo, j0), hi = min(q_hi, j0 + 128u);
                 float lcs[3], lcc[3], sbs[3], sbc[3];
                 uint64_t sig;
                 uint32_t nvalid;
+                const float* cin = s_carry + 16u * (jt & 1u);        // written by the previous tile
+                float* cout = s_carry + 16u * ((jt + 1u) & 1u);      // read by the next tile
                 if (q_lo < j0) {  // continues from the previous tile
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        lcs[c] = s_carry[c];
-                        lcc[c] = s_carry[3 + c];
-                        sbs[c] = s_carry[6 + c];
-                        sbc[c] = s_carry[9 + c];
+                    for (int cc = 0; cc < 3; ++cc) {
+                        lcs[cc] = cin[cc];
+                        lcc[cc] = cin[3 + cc];
+                        sbs[cc] = cin[6 + cc];
+                        sbc[cc] = cin[9 + cc];
                     }
-                    sig = (uint64_t)__float_as_uint(s_carry[12]) | ((uint64_t)__float_as_uint(s_carry[13]) << 32);
-                    nvalid = __float_as_uint(s_carry[14]);
+                    sig = (uint64_t)__float_as_uint(cin[12]) | ((uint64_t)__float_as_uint(cin[13]) << 32);
+                    nvalid = __float_as_uint(cin[14]);
                 } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) lcs[c] = lcc[c] = sbs[c] = sbc[c] = 0.f;
+                    for (int cc = 0; cc < 3; ++cc) lcs[cc] = lcc[cc] = sbs[cc] = sbc[cc] = 0.f;
                     sig = kSigInit;
                     nvalid = 0;
                 }
-                const bool qvalid = s_rec[q].flags & 1u;  // pixels without a camera hit draw no samples
+                // pixels without a camera hit draw no samples
+                const bool qvalid = __float_as_uint(__ldg(reinterpret_cast<const float4*>(recs + p0 + q) + 3).z) & 1u;
                 for (uint32_t rr = lo; rr < hi; ++rr) {
                     const float4 cv = s_contrib[rr - j0];
                     const float xs[3] = {cv.x, cv.y, cv.z};
@@ -462,33 +500,33 @@ __global__ void __launch_bounds__(512, 1)
                         if (qvalid) sig = sig_mix(sig, wd);
                         nvalid += (wd >> 9) & 1u;
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float y = xs[c] - lcc[c];
-                            const float tt = lcs[c] + y;
-                            lcc[c] = (tt - lcs[c]) - y;
-                            lcs[c] = tt;
+                        for (int cc = 0; cc < 3; ++cc) {
+                            const float y = xs[cc] - lcc[cc];
+                            const float tt = lcs[cc] + y;
+                            lcc[cc] = (tt - lcs[cc]) - y;
+                            lcs[cc] = tt;
                         }
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float y = xs[c] - sbc[c];
-                            const float tt = sbs[c] + y;
-                            sbc[c] = (tt - sbs[c]) - y;
-                            sbs[c] = tt;
+                        for (int cc = 0; cc < 3; ++cc) {
+                            const float y = xs[cc] - sbc[cc];
+                            const float tt = sbs[cc] + y;
+                            sbc[cc] = (tt - sbs[cc]) - y;
+                            sbs[cc] = tt;
                         }
                     }
                 }
                 if (q_hi > j0 + 128u) {  // continues in the next tile
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        s_carry[c] = lcs[c];
-                        s_carry[3 + c] = lcc[c];
-                        s_carry[6 + c] = sbs[c];
-                        s_carry[9 + c] = sbc[c];
+                    for (int cc = 0; cc < 3; ++cc) {
+                        cout[cc] = lcs[cc];
+                        cout[3 + cc] = lcc[cc];
+                        cout[6 + cc] = sbs[cc];
+                        cout[9 + cc] = sbc[cc];
                     }
-                    s_carry[12] = __uint_as_float((uint32_t)sig);
-                    s_carry[13] = __uint_as_float((uint32_t)(sig >> 32));
-                    s_carry[14] = __uint_as_float(nvalid);
+                    cout[12] = __uint_as_float((uint32_t)sig);
+                    cout[13] = __uint_as_float((uint32_t)(sig >> 32));
+                    cout[14] = __uint_as_float(nvalid);
                 } else {
                     const uint32_t gp = p0 + q;
                     const PixelBase b = base[gp];
@@ -496,27 +534,27 @@ __global__ void __launch_bounds__(512, 1)
                     if (a.N) {
                         const float inv = 1.0f / (float)a.N;
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) Lc[c] = lcs[c] * inv;
+                        for (int cc = 0; cc < 3; ++cc) Lc[cc] = lcs[cc] * inv;
                     }
                     if (a.M) {
                         const float inv = 1.0f / (float)a.M;
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) Lr[c] -= sbs[c] * inv;
+                        for (int cc = 0; cc < 3; ++cc) Lr[cc] -= sbs[cc] * inv;
                     }
                     out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
                     if (lc_out) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) lc_out[3 * (uint64_t)gp + c] = Lc[c];
+                        for (int cc = 0; cc < 3; ++cc) lc_out[3 * (uint64_t)gp + cc] = Lc[cc];
                     }
                     if (lr_out) {
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) lr_out[3 * (uint64_t)gp + c] = Lr[c];
+                        for (int cc = 0; cc < 3; ++cc) lr_out[3 * (uint64_t)gp + cc] = Lr[cc];
                     }
                     if (sig_out) sig_out[2 * (uint64_t)gp + 1] = sig;
                     if (count) count[gp] += nvalid;
                 }
             }
-            tc::named_bar(bar_id, 128);
+            // no barrier here: the next tile's barriers order s_contrib and the carry slots
         }
     }
 
@@ -568,7 +606,7 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     a.g = h->grid;
     int dev = h->device, max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    uint32_t n_wg = 4;
+    uint32_t n_wg = 5;
     while (n_wg > 1 && tc_smem_bytes(a.img_bytes, n_wg) > (size_t)max_smem) --n_wg;
     const size_t smem = tc_smem_bytes(a.img_bytes, n_wg);
     if (smem > (size_t)max_smem) return cudaErrorInvalidConfiguration;

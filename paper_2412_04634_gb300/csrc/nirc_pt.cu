@@ -9,29 +9,65 @@
 // k_gen_train: the separate training pass (section "Cache application"):
 //   T paths from uniformly drawn pixels, one record per path.
 //
-// Primitive geometry is staged in shared memory; every thread intersects
-// the same primitive at the same time (broadcast reads).
+// Both kernels are persistent: each CTA stages the primitives' geometry in
+// shared memory and, for scenes of more than 16 primitives, builds its own
+// bounding-volume hierarchy there once, then loops over pixels (paths).
+#include "nirc_bvh.cuh"
 #include "nirc_internal.h"
 
 namespace nirc {
+
+constexpr int kPtThreads = 128;
+constexpr uint32_t kBvhMinPrims = 17;
 
 struct FrameArgs {
     uint32_t W, H, N, M, D, n_prims;
     uint32_t k0, k1;
 };
 
+// Nearest-hit queries over the CTA's primitives (brute force or hierarchy).
+struct Tracer {
+    const PrimGeom* prims;
+    uint32_t n;
+    Bvh tree;
+    bool bvh;
+    __device__ __forceinline__ int nearest(V3 o, V3 d, float& t) const {
+        return bvh ? bvh_nearest(tree, prims, n, o, d, t) : trace_nearest(prims, n, o, d, t);
+    }
+};
+
+// Stage the scene header and primitive geometry, build the hierarchy.
+__device__ __forceinline__ Tracer setup_scene(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
+                                              uint32_t n_prims, unsigned char* smem, SceneHeader* hd) {
+    PrimGeom* sp = reinterpret_cast<PrimGeom*>(smem);
+    stage_prims(sp, gp, n_prims);
+    if (threadIdx.x < sizeof(SceneHeader) / 16)
+        reinterpret_cast<float4*>(hd)[threadIdx.x] = __ldg(reinterpret_cast<const float4*>(hd_g) + threadIdx.x);
+    __syncthreads();
+    Tracer tr;
+    tr.prims = sp;
+    tr.n = n_prims;
+    tr.tree = Bvh{nullptr, nullptr, 0u, 0u, 0u};
+    tr.bvh = n_prims >= kBvhMinPrims;
+    if (tr.bvh) {
+        tr.tree = bvh_build(sp, n_prims, smem + (size_t)n_prims * sizeof(PrimGeom));
+        __syncthreads();
+    }
+    return tr;
+}
+
 // Incident radiance along (o, d) from the path's vertices.
-__device__ __forceinline__ float3 trace_path(const PrimGeom* __restrict__ sp, const Prim* __restrict__ gp,
-                                             uint32_t n_prims, V3 o, V3 d, uint32_t k0, uint32_t k1, uint32_t c0,
-                                             uint32_t c1, uint32_t max_depth, uint64_t& sig) {
+__device__ __forceinline__ float3 trace_path(const Tracer& tr, const Prim* __restrict__ gp, V3 o, V3 d, uint32_t k0,
+                                             uint32_t k1, uint32_t c0, uint32_t c1, uint32_t max_depth,
+                                             uint64_t& sig) {
     float3 L = make_float3(0.f, 0.f, 0.f);
     float3 beta = make_float3(1.f, 1.f, 1.f);
     for (uint32_t seg = 1; seg <= max_depth; ++seg) {
         float t;
-        const int prim = trace_nearest(sp, n_prims, o, d, t);
+        const int prim = tr.nearest(o, d, t);
         sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
         if (prim < 0) break;
-        const Hit h = hit_info(sp[prim], o, d, t);
+        const Hit h = hit_info(tr.prims[prim], o, d, t);
         const Prim* P = gp + prim;
         const uint32_t flags = __ldg(&P->flags);
         if (h.front || (flags & EMIT_TWO_SIDED)) {
@@ -70,160 +106,172 @@ __device__ __forceinline__ void write_record(nirc_record* dst, const Hit& h, V3 
     q[3] = make_float4(__ldg(&P->roughness), __uint_as_float(prim), __uint_as_float(flags), 0.f);
 }
 
-__global__ void __launch_bounds__(128) k_primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
-                                                       FrameArgs a, nirc_record* __restrict__ recs,
-                                                       PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
-                                                       uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count) {
+__global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader* __restrict__ hd_g,
+                                                              const Prim* __restrict__ gp, FrameArgs a,
+                                                              nirc_record* __restrict__ recs,
+                                                              PixelBase* __restrict__ base,
+                                                              ResidRow* __restrict__ rows,
+                                                              uint64_t* __restrict__ sig_out,
+                                                              uint32_t* __restrict__ count) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PrimGeom* sp = reinterpret_cast<PrimGeom*>(smem_raw);
-    stage_prims(sp, gp, a.n_prims);
     __shared__ SceneHeader hd;
-    if (threadIdx.x < sizeof(SceneHeader) / 16)
-        reinterpret_cast<float4*>(&hd)[threadIdx.x] = __ldg(reinterpret_cast<const float4*>(hd_g) + threadIdx.x);
-    __syncthreads();
+    const Tracer tr = setup_scene(hd_g, gp, a.n_prims, smem_raw, &hd);
 
     const uint64_t P = (uint64_t)a.W * a.H;
-    const uint64_t pix64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix64 >= P) return;
-    const uint32_t pix = (uint32_t)pix64;
-    const uint32_t px = pix % a.W, py = pix / a.W;
+    for (uint64_t pix64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; pix64 < P;
+         pix64 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t pix = (uint32_t)pix64;
+        const uint32_t px = pix % a.W, py = pix / a.W;
 
-    const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
-    V3 o, d;
-    camera_ray(hd, a.W, a.H, px, py, u01(r.x), u01(r.y), o, d);
-    float t;
-    const int prim = trace_nearest(sp, a.n_prims, o, d, t);
-    uint64_t sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
-    ResidRow* my_rows = rows + (uint64_t)pix * a.M;
-    if (prim < 0) {
-        float4* q = reinterpret_cast<float4*>(recs + pix);
-        q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-        base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
-        base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (uint32_t j = 0; j < a.M; ++j) {
-            my_rows[j].wi = make_float4(0.f, 0.f, 1.f, 0.f);
-            my_rows[j].w = make_float4(0.f, 0.f, 0.f, 0.f);
+        const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
+        V3 o, d;
+        camera_ray(hd, a.W, a.H, px, py, u01(r.x), u01(r.y), o, d);
+        float t;
+        const int prim = tr.nearest(o, d, t);
+        uint64_t sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+        ResidRow* my_rows = rows + (uint64_t)pix * a.M;
+        if (prim < 0) {
+            float4* q = reinterpret_cast<float4*>(recs + pix);
+            q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
+            base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (uint32_t j = 0; j < a.M; ++j) {
+                my_rows[j].wi = make_float4(0.f, 0.f, 1.f, 0.f);
+                my_rows[j].w = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+            if (count) count[pix] = 0;
+            continue;
         }
-        if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
-        if (count) count[pix] = 0;
-        return;
-    }
-    const Hit h = hit_info(sp[prim], o, d, t);
-    const Prim* Pp = gp + prim;
-    const uint32_t pflags = __ldg(&Pp->flags);
-    const uint32_t mat = pflags & 3u;
-    write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (mat << 1));
-    float3 le = make_float3(0.f, 0.f, 0.f);
-    if (h.front || (pflags & EMIT_TWO_SIDED))
-        le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
-    const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
-    const float rough = __ldg(&Pp->roughness);
-    const V3 wo = sneg(d);
+        const Hit h = hit_info(tr.prims[prim], o, d, t);
+        const Prim* Pp = gp + prim;
+        const uint32_t pflags = __ldg(&Pp->flags);
+        const uint32_t mat = pflags & 3u;
+        write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (mat << 1));
+        float3 le = make_float3(0.f, 0.f, 0.f);
+        if (h.front || (pflags & EMIT_TWO_SIDED))
+            le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
+        const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+        const float rough = __ldg(&Pp->roughness);
+        const V3 wo = sneg(d);
 
-    float3 wl = make_float3(0.f, 0.f, 0.f);
-    uint32_t nvalid = 0;
-    for (uint32_t j = 0; j < a.M; ++j) {
-        const BsdfSample s = sample_bsdf(h.n, wo, alb, rough, mat, a.k0, a.k1, pix, j, PURPOSE_RESID_DIR);
-        sig = sig_mix(sig, s.word);
-        my_rows[j].wi = make_float4(s.wi.x, s.wi.y, s.wi.z, s.valid ? 1.f : 0.f);
-        my_rows[j].w = make_float4(s.w.x, s.w.y, s.w.z, 0.f);
-        if (!s.valid) continue;
-        const float3 L = trace_path(sp, gp, a.n_prims, h.p, s.wi, a.k0, a.k1, pix, j, a.D, sig);
-        wl.x += s.w.x * L.x;
-        wl.y += s.w.y * L.y;
-        wl.z += s.w.z * L.z;
-        ++nvalid;
+        float3 wl = make_float3(0.f, 0.f, 0.f);
+        uint32_t nvalid = 0;
+        for (uint32_t j = 0; j < a.M; ++j) {
+            const BsdfSample s = sample_bsdf(h.n, wo, alb, rough, mat, a.k0, a.k1, pix, j, PURPOSE_RESID_DIR);
+            sig = sig_mix(sig, s.word);
+            my_rows[j].wi = make_float4(s.wi.x, s.wi.y, s.wi.z, s.valid ? 1.f : 0.f);
+            my_rows[j].w = make_float4(s.w.x, s.w.y, s.w.z, 0.f);
+            if (!s.valid) continue;
+            const float3 L = trace_path(tr, gp, h.p, s.wi, a.k0, a.k1, pix, j, a.D, sig);
+            wl.x += s.w.x * L.x;
+            wl.y += s.w.y * L.y;
+            wl.z += s.w.z * L.z;
+            ++nvalid;
+        }
+        if (a.M) {
+            const float inv = 1.0f / (float)a.M;
+            wl.x *= inv;
+            wl.y *= inv;
+            wl.z *= inv;
+        }
+        base[pix].le = make_float4(le.x, le.y, le.z, 0.f);
+        base[pix].wl = make_float4(wl.x, wl.y, wl.z, 0.f);
+        if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+        if (count) count[pix] = nvalid;
     }
-    if (a.M) {
-        const float inv = 1.0f / (float)a.M;
-        wl.x *= inv;
-        wl.y *= inv;
-        wl.z *= inv;
-    }
-    base[pix].le = make_float4(le.x, le.y, le.z, 0.f);
-    base[pix].wl = make_float4(wl.x, wl.y, wl.z, 0.f);
-    if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
-    if (count) count[pix] = nvalid;
 }
 
-__global__ void __launch_bounds__(128) k_gen_train(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
-                                                   uint32_t n_prims, uint32_t W, uint32_t H, uint64_t T, uint32_t k0,
-                                                   uint32_t k1, uint32_t max_depth, nirc_record* __restrict__ recs,
-                                                   float* __restrict__ dirs, float* __restrict__ targets) {
+__global__ void __launch_bounds__(kPtThreads) k_gen_train(const SceneHeader* __restrict__ hd_g,
+                                                          const Prim* __restrict__ gp, uint32_t n_prims, uint32_t W,
+                                                          uint32_t H, uint64_t T, uint32_t k0, uint32_t k1,
+                                                          uint32_t max_depth, nirc_record* __restrict__ recs,
+                                                          float* __restrict__ dirs, float* __restrict__ targets) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    PrimGeom* sp = reinterpret_cast<PrimGeom*>(smem_raw);
-    stage_prims(sp, gp, n_prims);
     __shared__ SceneHeader hd;
-    if (threadIdx.x < sizeof(SceneHeader) / 16)
-        reinterpret_cast<float4*>(&hd)[threadIdx.x] = __ldg(reinterpret_cast<const float4*>(hd_g) + threadIdx.x);
-    __syncthreads();
-
-    const uint64_t ti = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (ti >= T) return;
-    const uint32_t tr = (uint32_t)ti;
+    const Tracer tr = setup_scene(hd_g, gp, n_prims, smem_raw, &hd);
     const uint32_t P = W * H;
-    const U4 r = philox(k0, k1, tr, 0u, 0u, PURPOSE_TRAIN_PICK);
-    const uint32_t pix = __umulhi(r.x, P);
-    V3 o, d;
-    camera_ray(hd, W, H, pix % W, pix / W, u01(r.y), u01(r.z), o, d);
-    float t;
-    const int prim = trace_nearest(sp, n_prims, o, d, t);
-    float* dir = dirs + 3 * ti;
-    float* tg = targets + 3 * ti;
-    dir[0] = dir[1] = dir[2] = 0.f;
-    tg[0] = tg[1] = tg[2] = 0.f;
-    if (prim < 0) {
-        float4* q = reinterpret_cast<float4*>(recs + ti);
-        q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+    for (uint64_t ti = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ti < T; ti += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t tr_idx = (uint32_t)ti;
+        const U4 r = philox(k0, k1, tr_idx, 0u, 0u, PURPOSE_TRAIN_PICK);
+        const uint32_t pix = __umulhi(r.x, P);
+        V3 o, d;
+        camera_ray(hd, W, H, pix % W, pix / W, u01(r.y), u01(r.z), o, d);
+        float t;
+        const int prim = tr.nearest(o, d, t);
+        float* dir = dirs + 3 * ti;
+        float* tg = targets + 3 * ti;
+        dir[0] = dir[1] = dir[2] = 0.f;
+        tg[0] = tg[1] = tg[2] = 0.f;
+        if (prim < 0) {
+            float4* q = reinterpret_cast<float4*>(recs + ti);
+            q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const Hit h = hit_info(tr.prims[prim], o, d, t);
+        const Prim* Pp = gp + prim;
+        const uint32_t mat = __ldg(&Pp->flags) & 3u;
+        const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+        const BsdfSample s =
+            sample_bsdf(h.n, sneg(d), alb, __ldg(&Pp->roughness), mat, k0, k1, tr_idx, 0u, PURPOSE_RESID_DIR);
+        write_record(recs + ti, h, d, Pp, (uint32_t)prim, (s.valid ? 1u : 0u) | (mat << 1));
+        if (!s.valid) continue;
+        uint64_t sig = 0;
+        const float3 L = trace_path(tr, gp, h.p, s.wi, k0, k1, tr_idx, 0u, max_depth, sig);
+        dir[0] = s.wi.x;
+        dir[1] = s.wi.y;
+        dir[2] = s.wi.z;
+        tg[0] = L.x;
+        tg[1] = L.y;
+        tg[2] = L.z;
     }
-    const Hit h = hit_info(sp[prim], o, d, t);
-    const Prim* Pp = gp + prim;
-    const uint32_t mat = __ldg(&Pp->flags) & 3u;
-    const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
-    const BsdfSample s = sample_bsdf(h.n, sneg(d), alb, __ldg(&Pp->roughness), mat, k0, k1, tr, 0u, PURPOSE_RESID_DIR);
-    write_record(recs + ti, h, d, Pp, (uint32_t)prim, (s.valid ? 1u : 0u) | (mat << 1));
-    if (!s.valid) return;
-    uint64_t sig = 0;
-    const float3 L = trace_path(sp, gp, n_prims, h.p, s.wi, k0, k1, tr, 0u, max_depth, sig);
-    dir[0] = s.wi.x;
-    dir[1] = s.wi.y;
-    dir[2] = s.wi.z;
-    tg[0] = L.x;
-    tg[1] = L.y;
-    tg[2] = L.z;
+}
+
+static size_t pt_smem(uint32_t n_prims) {
+    return (size_t)n_prims * sizeof(PrimGeom) + (n_prims >= kBvhMinPrims ? bvh_smem_bytes(n_prims) : 0);
+}
+
+template <typename K>
+static cudaError_t persistent_grid(K kernel, size_t smem, uint64_t work, int num_sms, uint32_t* grid) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPtThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t need = (work + kPtThreads - 1) / kPtThreads;
+    uint64_t g = (uint64_t)per_sm * (uint64_t)num_sms;
+    if (g > need) g = need;
+    *grid = (uint32_t)(g < 1 ? 1 : g);
+    return cudaSuccess;
 }
 
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig, uint32_t* count,
                                  cudaStream_t st) {
-    (void)h;
     FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
     const uint64_t P = (uint64_t)fd.width * fd.height;
-    const uint32_t threads = 128;
-    const uint32_t blocks = (uint32_t)((P + threads - 1) / threads);
-    const size_t smem = (size_t)fd.n_prims * sizeof(PrimGeom);
+    const size_t smem = pt_smem(fd.n_prims);
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
-    cudaError_t e = cudaFuncSetAttribute(k_primary_resid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    uint32_t grid = 1;
+    cudaError_t e = persistent_grid(k_primary_resid, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
-    k_primary_resid<<<blocks, threads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count);
+    k_primary_resid<<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
                              uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* recs,
                              float* dirs, float* targets, cudaStream_t st) {
-    (void)h;
-    const uint32_t threads = 128;
-    const uint32_t blocks = (uint32_t)((T + threads - 1) / threads);
-    const size_t smem = (size_t)n_prims * sizeof(PrimGeom);
+    const size_t smem = pt_smem(n_prims);
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
-    cudaError_t e = cudaFuncSetAttribute(k_gen_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    uint32_t grid = 1;
+    cudaError_t e = persistent_grid(k_gen_train, smem, T, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
-    k_gen_train<<<blocks, threads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
-                                               max_depth, recs, dirs, targets);
+    k_gen_train<<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
+                                                max_depth, recs, dirs, targets);
     return cudaGetLastError();
 }
 

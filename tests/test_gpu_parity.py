@@ -75,7 +75,12 @@ def frame_errors(g, o):
     L_r and the levels cancel by design (L_r subtracts the cache's
     prediction), so its error is measured against the largest of |pixel|,
     |L_c| and |L_r|."""
-    errs = {k: rel_err(g[k], o[k]) for k in ("lc", "lr")}
+    errs = {"lc": rel_err(g["lc"], o["lc"])}
+    # L_r = 1/M sum w (L_i - n) cancels internally when the cache is close to
+    # L_i: measure it against the cache term's size, which |L_c| estimates
+    scale_r = np.maximum(np.abs(o["lr"]), np.abs(o["lc"]))
+    scale_r = np.maximum(scale_r, 1e-3 * max(np.abs(o["lr"]).mean(), 1e-30))
+    errs["lr"] = np.abs(np.asarray(g["lr"], np.float64) - o["lr"]) / scale_r
     scale = np.maximum.reduce([np.abs(o["pixel"]), np.abs(o["lc"]), np.abs(o["lr"])])
     scale = np.maximum(scale, 1e-3 * max(np.abs(o["pixel"]).mean(), 1e-30))
     errs["pixel"] = np.abs(np.asarray(g["pixel"], np.float64) - o["pixel"]) / scale
@@ -157,6 +162,20 @@ def test_frame_edge_shapes(N, oracle, W, H, Nc, M):
     sc = scenes.cornell_scene(W, H, seed=2)
     g = _run_frame(N, cfg, params, sc, W, H, Nc, M, 4, 1, 9)
     o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(W, H, Nc, M, 4, 1, 9))
+    _compare_frames(g, o)
+
+
+@pytest.mark.parametrize("n_prims", [17, 64, 1000])
+def test_frame_bvh_scene_sizes(N, oracle, n_prims):
+    """Scenes large enough to use the per-CTA hierarchy (>= 17 primitives, up
+    to near the 1024 limit): every hit, hence every decision signature, must
+    equal the oracle's brute-force nearest hit."""
+    cfg = scenes.config_small()
+    W, H = 48, 32
+    sc = scenes.cornell_scene(W, H, seed=5, n_prims=n_prims, glossy=True, moving_emitter=True, frame=2)
+    g = _run_frame(N, cfg, None, sc, W, H, 4, 2, 8, 1, 3, cache_mode=2, cache_const=(0.3, 0.5, 0.7))
+    o = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(W, H, 4, 2, 8, 1, 3, cache_mode=2,
+                                                            cache_const=(0.3, 0.5, 0.7)))
     _compare_frames(g, o)
 
 
