@@ -432,7 +432,7 @@ static uint32_t sample_word(const o_sample* s)
 }
 
 /* BSDF importance sample at a shading record; Philox counter
- * (c0, c1, call, c3).  The lobe choice uses call 8, word 0. */
+ * (c0, c1, call, c3).  The lobe choice uses the low byte of call 0, word 0. */
 static void sample_bsdf(const o_record* rec, uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3,
                         o_sample* out)
 {
@@ -447,9 +447,11 @@ static void sample_bsdf(const o_record* rec, uint32_t k0, uint32_t k1, uint32_t 
     float t[3], b[3];
     onb(rec->n, t, b);
     if (mat == MAT_GGX) {
+        /* mixture lobe: low byte of word 0 of the first Philox call (the disk
+         * candidates use only the high 24 bits of each word) */
         uint32_t r[4];
-        philox(k0, k1, c0, c1, 8u, c3, r);
-        out->lobe = u01(r[0]) < 0.5f ? 0u : 1u;
+        philox(k0, k1, c0, c1, 0u, c3, r);
+        out->lobe = (r[0] & 0xFFu) < 128u ? 0u : 1u;
     }
     float da, db;
     out->rejected = disk_sample(k0, k1, c0, c1, c3, &da, &db);

@@ -457,76 +457,82 @@ __global__ void __launch_bounds__(640, 1)
                 rn[1] = ok ? nv.y : 0.f;
                 rn[2] = ok ? nv.z : 0.f;
             }
+            // ---- per-pixel sums.  Rows are ordered by pixel, so each pixel is a
+            // contiguous segment: a pairwise tree over the warp's lanes (shuffle
+            // down by 1, 2, 4, 8, 16, adding only within the segment) leaves each
+            // segment's warp-local sum in its first lane, in an order fixed by
+            // the row positions.  That lane then adds the partials of later
+            // warps whose first rows belong to the same pixel and the previous
+            // tile's carry, and either writes the pixel or carries it on.
+            const uint32_t lane = t & 31u, warp = t >> 5;
+            const uint32_t s_row = rin ? r - pl * S : 0u;
+            const bool is_cache = s_row < a.N;
+            float v[7];
+            {
+                const float3 cw = ok ? make_float3(w.x * nv.x, w.y * nv.y, w.z * nv.z) : make_float3(0.f, 0.f, 0.f);
+                v[0] = is_cache ? cw.x : 0.f;
+                v[1] = is_cache ? cw.y : 0.f;
+                v[2] = is_cache ? cw.z : 0.f;
+                v[3] = is_cache ? 0.f : cw.x;
+                v[4] = is_cache ? 0.f : cw.y;
+                v[5] = is_cache ? 0.f : cw.z;
+                v[6] = (is_cache && ok) ? 1.f : 0.f;
+            }
+            const uint32_t seg = rin ? pl : 0xFFFFFFFFu;
+#pragma unroll
+            for (uint32_t off = 1; off < 32; off <<= 1) {
+                const uint32_t oseg = __shfl_down_sync(0xffffffffu, seg, off);
+                float o[7];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) o[k] = __shfl_down_sync(0xffffffffu, v[k], off);
+                if (lane + off < 32u && oseg == seg) {
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) v[k] += o[k];
+                }
+            }
+            float* s_part = s_carry + 32;                                              // 4 warps x 8 floats
+            uint64_t* s_sigc = reinterpret_cast<uint64_t*>(s_carry + 64);              // 2 signature carry slots
+            if (lane == 0) {
+#pragma unroll
+                for (int k = 0; k < 7; ++k) s_part[8 * warp + k] = v[k];
+                s_part[8 * warp + 7] = __uint_as_float(seg);
+            }
+            if (sig_out) s_contrib[t] = make_float4(0.f, 0.f, 0.f, __uint_as_float(word));
             tc::fence_before_sync();
-            s_contrib[t] = ok ? make_float4(w.x * nv.x, w.y * nv.y, w.z * nv.z, __uint_as_float(word))
-                              : make_float4(0.f, 0.f, 0.f, __uint_as_float(word));
             tc::named_bar(bar_id, 128);
 
-            // one thread per pixel of this tile, spread over the four warps:
-            // pixel i -> thread 32 (i % 4) + i / 4; rows summed in sample order
-            const uint32_t i_pix = 4u * (t & 31u) + (t >> 5);
-            if (i_pix <= plast - pf) {
-                const uint32_t q = pf + i_pix;
+            const uint32_t prev_seg = __shfl_up_sync(0xffffffffu, seg, 1);
+            const bool head = rin && (lane > 0 ? prev_seg != seg
+                                               : (warp == 0 || (j0 + 32u * warp - 1u) / S != pl));
+            if (head) {
+                const uint32_t q = pl;
                 const uint32_t q_lo = q * S, q_hi = q_lo + S;
-                const uint32_t lo = max(q_lo, j0), hi = min(q_hi, j0 + 128u);
-                float lcs[3], lcc[3], sbs[3], sbc[3];
-                uint64_t sig;
-                uint32_t nvalid;
-                const float* cin = s_carry + 16u * (jt & 1u);        // written by the previous tile
-                float* cout = s_carry + 16u * ((jt + 1u) & 1u);      // read by the next tile
-                if (q_lo < j0) {  // continues from the previous tile
+                const float* cin = s_carry + 16u * (jt & 1u);    // written by the previous tile
+                float* cout = s_carry + 16u * ((jt + 1u) & 1u);  // read by the next tile
+                float acc[7];
+                const bool cont_in = q_lo < j0;
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        lcs[cc] = cin[cc];
-                        lcc[cc] = cin[3 + cc];
-                        sbs[cc] = cin[6 + cc];
-                        sbc[cc] = cin[9 + cc];
-                    }
-                    sig = (uint64_t)__float_as_uint(cin[12]) | ((uint64_t)__float_as_uint(cin[13]) << 32);
-                    nvalid = __float_as_uint(cin[14]);
-                } else {
+                for (int k = 0; k < 7; ++k) acc[k] = cont_in ? cin[k] : 0.f;
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) lcs[cc] = lcc[cc] = sbs[cc] = sbc[cc] = 0.f;
-                    sig = kSigInit;
-                    nvalid = 0;
+                for (int k = 0; k < 7; ++k) acc[k] += v[k];
+                for (uint32_t ww = warp + 1; ww < 4; ++ww) {
+                    if (__float_as_uint(s_part[8 * ww + 7]) != seg) break;
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) acc[k] += s_part[8 * ww + k];
                 }
-                // pixels without a camera hit draw no samples
-                const bool qvalid = __float_as_uint(__ldg(reinterpret_cast<const float4*>(recs + p0 + q) + 3).z) & 1u;
-                for (uint32_t rr = lo; rr < hi; ++rr) {
-                    const float4 cv = s_contrib[rr - j0];
-                    const float xs[3] = {cv.x, cv.y, cv.z};
-                    if (rr - q_lo < a.N) {
-                        const uint32_t wd = __float_as_uint(cv.w);
-                        if (qvalid) sig = sig_mix(sig, wd);
-                        nvalid += (wd >> 9) & 1u;
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            const float y = xs[cc] - lcc[cc];
-                            const float tt = lcs[cc] + y;
-                            lcc[cc] = (tt - lcs[cc]) - y;
-                            lcs[cc] = tt;
-                        }
-                    } else {
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            const float y = xs[cc] - sbc[cc];
-                            const float tt = sbs[cc] + y;
-                            sbc[cc] = (tt - sbs[cc]) - y;
-                            sbs[cc] = tt;
-                        }
-                    }
+                // decision signature of the cache samples (sequential, only when requested)
+                uint64_t sig = 0;
+                if (sig_out) {
+                    sig = cont_in ? s_sigc[jt & 1u] : kSigInit;
+                    const bool qvalid = __float_as_uint(__ldg(reinterpret_cast<const float4*>(recs + p0 + q) + 3).z) & 1u;
+                    const uint32_t lo = max(q_lo, j0), hi = min(min(q_hi, j0 + 128u), q_lo + a.N);
+                    if (qvalid)
+                        for (uint32_t rr = lo; rr < hi; ++rr) sig = sig_mix(sig, __float_as_uint(s_contrib[rr - j0].w));
                 }
                 if (q_hi > j0 + 128u) {  // continues in the next tile
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        cout[cc] = lcs[cc];
-                        cout[3 + cc] = lcc[cc];
-                        cout[6 + cc] = sbs[cc];
-                        cout[9 + cc] = sbc[cc];
-                    }
-                    cout[12] = __uint_as_float((uint32_t)sig);
-                    cout[13] = __uint_as_float((uint32_t)(sig >> 32));
-                    cout[14] = __uint_as_float(nvalid);
+                    for (int k = 0; k < 7; ++k) cout[k] = acc[k];
+                    if (sig_out) s_sigc[(jt + 1u) & 1u] = sig;
                 } else {
                     const uint32_t gp = p0 + q;
                     const PixelBase b = base[gp];
@@ -534,12 +540,12 @@ __global__ void __launch_bounds__(640, 1)
                     if (a.N) {
                         const float inv = 1.0f / (float)a.N;
 #pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) Lc[cc] = lcs[cc] * inv;
+                        for (int cc = 0; cc < 3; ++cc) Lc[cc] = acc[cc] * inv;
                     }
                     if (a.M) {
                         const float inv = 1.0f / (float)a.M;
 #pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) Lr[cc] -= sbs[cc] * inv;
+                        for (int cc = 0; cc < 3; ++cc) Lr[cc] -= acc[3 + cc] * inv;
                     }
                     out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
                     if (lc_out) {
@@ -551,7 +557,7 @@ __global__ void __launch_bounds__(640, 1)
                         for (int cc = 0; cc < 3; ++cc) lr_out[3 * (uint64_t)gp + cc] = Lr[cc];
                     }
                     if (sig_out) sig_out[2 * (uint64_t)gp + 1] = sig;
-                    if (count) count[gp] += nvalid;
+                    if (count) count[gp] += (uint32_t)acc[6];
                 }
             }
             // no barrier here: the next tile's barriers order s_contrib and the carry slots

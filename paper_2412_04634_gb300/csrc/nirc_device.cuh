@@ -271,12 +271,13 @@ __device__ __forceinline__ void onb(V3 n, V3& t, V3& b) {
 }
 
 // Uniform point on the unit disk: rejection from the square, 2 candidates per
-// Philox call (counter word 2 = call 0..7).  Returns the rejected count.
+// Philox call (counter word 2 = call 0..7; `first` is call 0, already drawn).
+// Returns the rejected count.
 __device__ __forceinline__ uint32_t disk_sample(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3,
-                                                float& a, float& b) {
+                                                const U4& first, float& a, float& b) {
     uint32_t rejected = 0;
     for (uint32_t call = 0; call < 8; ++call) {
-        const U4 r = philox(k0, k1, c0, c1, call, c3);
+        const U4 r = call == 0 ? first : philox(k0, k1, c0, c1, call, c3);
         float x = __fsub_rn(__fmul_rn(2.0f, u01(r.x)), 1.0f);
         float y = __fsub_rn(__fmul_rn(2.0f, u01(r.y)), 1.0f);
         if (__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)) < 1.0f) {
@@ -345,18 +346,18 @@ __device__ __forceinline__ float3 ggx_mix_weight(V3 n, V3 wo, V3 wi, float3 albe
     const float ch = n.x * hx + n.y * hy + n.z * hz;
     const float oh = fminf(fmaxf(wo.x * hx + wo.y * hy + wo.z * hz, 0.0f), 1.0f);
     const float dd = ch * ch * (a2 - 1.0f) + 1.0f;
-    const float D = a2 / (kPi * dd * dd);
+    const float D = __fdividef(a2, kPi * dd * dd);
     const float lam_o = sqrtf(a2 + (1.0f - a2) * co * co);
     const float lam_i = sqrtf(a2 + (1.0f - a2) * ci * ci);
-    const float G2 = 2.0f * ci * co / (co * lam_i + ci * lam_o);
-    const float G1o = 2.0f * co / (co + lam_o);
     const float m = 1.0f - oh;
     const float m2 = m * m;
     const float F = kF0 + (1.0f - kF0) * (m2 * m2 * m);
-    const float fs = F * D * G2 / (4.0f * ci * co);
-    const float pdf_s = G1o * D / (4.0f * co);
+    // F D G2 / (4 ci co) with G2 = 2 ci co / (co lam_i + ci lam_o), and the
+    // visible-normal pdf G1(wo) D / (4 co) with G1 = 2 co / (co + lam_o)
+    const float fs = __fdividef(F * D, 2.0f * (co * lam_i + ci * lam_o));
+    const float pdf_s = __fdividef(D, 2.0f * (co + lam_o));
     const float pdf = 0.5f * ci * kInvPi + 0.5f * pdf_s;
-    const float k = ci / pdf;
+    const float k = __fdividef(ci, pdf);
     return make_float3((albedo.x * kInvPi + fs) * k, (albedo.y * kInvPi + fs) * k, (albedo.z * kInvPi + fs) * k);
 }
 
@@ -368,6 +369,8 @@ struct BsdfSample {
 };
 
 // Sample at a shading record (p unused); Philox counter (c0, c1, call, c3).
+// The mixture lobe (GGX materials) is the low byte of word 0 of call 0 (< 128:
+// cosine lobe), bits the disk candidates, which use the high 24 bits, leave free.
 __device__ __forceinline__ BsdfSample sample_bsdf(V3 n, V3 wo, float3 albedo, float rough, uint32_t mat, uint32_t k0,
                                                   uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3) {
     BsdfSample s;
@@ -378,13 +381,10 @@ __device__ __forceinline__ BsdfSample sample_bsdf(V3 n, V3 wo, float3 albedo, fl
     if (mat == MAT_BLACK) return s;
     V3 t, b;
     onb(n, t, b);
-    uint32_t lobe = 0;
-    if (mat == MAT_GGX) {
-        const U4 r = philox(k0, k1, c0, c1, 8u, c3);
-        lobe = u01(r.x) < 0.5f ? 0u : 1u;
-    }
+    const U4 first = philox(k0, k1, c0, c1, 0u, c3);
+    const uint32_t lobe = (mat == MAT_GGX && (first.x & 0xFFu) >= 128u) ? 1u : 0u;
     float da, db;
-    const uint32_t rejected = disk_sample(k0, k1, c0, c1, c3, da, db);
+    const uint32_t rejected = disk_sample(k0, k1, c0, c1, c3, first, da, db);
     if (lobe == 0) {
         const float sq = __fadd_rn(__fmul_rn(da, da), __fmul_rn(db, db));
         const float z = __fsqrt_rn(fmaxf(0.0f, __fsub_rn(1.0f, sq)));
