@@ -163,6 +163,11 @@ nirc_status nirc_destroy(nirc_handle* h);
  * `on_device`), refresh the low-precision copies and reset Adam (step 0,
  * zero moments). */
 nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, void* stream);
+/* Copy nirc_param_count() floats in and refresh the low-precision copies,
+ * keeping the Adam moments and step (for callers that update the weights
+ * with their own optimiser, e.g. through the autograd wrapper).  Host input
+ * synchronises `stream`. */
+nirc_status nirc_load_params(nirc_handle* h, const float* params, int on_device, void* stream);
 /* Copy the FP32 master parameters out. Synchronises `stream` for host output. */
 nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* stream);
 /* Copy out the gradient of the last nirc_train_step (same layout). */
@@ -232,6 +237,29 @@ nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims
  * d_loss (optional, device float) receives L. */
 nirc_status nirc_train_step(nirc_handle* h, const nirc_record* d_records, const float* d_dirs,
                             const float* d_targets, uint64_t n, float* d_loss, void* stream);
+
+/* Activation memory of nirc_train_step and nirc_query_bwd.  store != 0
+ * (default): the forward stores every layer's output for the whole batch,
+ * n * (n_in + 128 * hidden_layers) floats.  store == 0: the forward keeps
+ * only dL/dz (3 floats per sample) and the backward walks the batch in
+ * chunks of `recompute_chunk` samples (1024..2^26), running each chunk's
+ * forward again into a chunk-sized buffer before its backward, one extra
+ * forward in exchange for O(chunk) memory.  Results agree up to the order of
+ * the float atomics in the gradient sums. */
+nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t recompute_chunk);
+
+/* Backward of the bare query (for a torch.autograd.Function around
+ * nirc_query): with d_grad_out = dL/dn (n x 3 floats, device) it computes
+ * d_grad_params = sum_i dL/dn_i . dn_i/dparams over every row (the valid flag
+ * is ignored, as in nirc_query), through the output exp and clamp, the ReLU
+ * layers, the frequency encodings and the trilinear hash-grid interpolation
+ * (table gradient scattered with warp-aggregated atomics).  The gradient is
+ * left in the handle's gradient buffer (nirc_get_grads; it replaces the last
+ * training gradient) and, when d_grad_params != NULL, copied there in the
+ * nirc_param_count() layout (device pointer).  d_value (optional, device
+ * float) receives sum dL/dn * n.  Same FP32 arithmetic as nirc_query. */
+nirc_status nirc_query_bwd(nirc_handle* h, const nirc_record* d_records, const float* d_dirs,
+                           const float* d_grad_out, uint64_t n, float* d_grad_params, float* d_value, void* stream);
 
 /* Mean relative squared error over pixels and RGB (paper: MRSE),
  * mean (I - R)^2 / (R^2 + eps), accumulated in FP64; images are float4 per

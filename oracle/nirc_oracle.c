@@ -910,8 +910,14 @@ void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint
  * both the loss and the gradient: the loss is then a plain function of the
  * parameters whose derivative at the point where den_fixed was taken is the
  * training gradient (used by the finite-difference pin). */
-double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
-                           const double* targets, uint64_t T, const double* den_fixed, double* grad)
+/* Shared core of the training loss gradient and of the query gradient.
+ * With gout == NULL it is the loss above (valid records only); with gout
+ * (T x 3) given it returns sum_t sum_ch gout * n over every record and adds
+ * the gradient of that sum, i.e. the vector-Jacobian product of eq. 11's
+ * cache with the upstream gradient gout. */
+static double loss_grad_core(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
+                             const double* targets, const double* gout, uint64_t T, const double* den_fixed,
+                             double* grad)
 {
     uint64_t n_mlp = mlp_param_count(c);
     const double* hash = params + n_mlp;
@@ -944,7 +950,7 @@ double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record*
         double delta[MAX_WIDTH], delta_prev[MAX_WIDTH > 1024 ? MAX_WIDTH : 1024];
 #pragma omp for schedule(static)
         for (int64_t t = 0; t < (int64_t)T; t++) {
-            if (!(recs[t].flags & 1u)) continue;
+            if (!gout && !(recs[t].flags & 1u)) continue;
             double z[3];
             encode(c, hash, recs[t].p, recs[t].n, dirs + 3 * t, e);
             mlp_forward(c, params, e, pre, act, z);
@@ -953,13 +959,19 @@ double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record*
             for (int k = 0; k < 3; k++) {
                 int clamped = !(z[k] <= c->z_clamp);
                 double nv = exp(clamped ? c->z_clamp : z[k]);
-                double f = targets[3 * t + k];
-                double den = den_fixed ? den_fixed[3 * t + k] : nv * nv + c->loss_eps; /* sg(n)^2 + eps */
-                lt += (f - nv) * (f - nv) / den;
-                double dn = -2.0 * (f - nv) / den * scale;
+                double dn;
+                if (gout) {
+                    lt += gout[3 * t + k] * nv;
+                    dn = gout[3 * t + k];
+                } else {
+                    double f = targets[3 * t + k];
+                    double den = den_fixed ? den_fixed[3 * t + k] : nv * nv + c->loss_eps; /* sg(n)^2 + eps */
+                    lt += (f - nv) * (f - nv) / den * scale;
+                    dn = -2.0 * (f - nv) / den * scale;
+                }
                 dz[k] = clamped ? 0.0 : dn * nv;
             }
-            loss_part[t] = lt * scale;
+            loss_part[t] = lt;
             /* Walk the layers backwards: delta = dL/d(pre-activation). */
             for (int k = 0; k < 3; k++) delta[k] = dz[k];
             int out = 3;
@@ -997,7 +1009,7 @@ double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record*
     if (c->pos_encoding == 1) {
         double* gh = grad + n_mlp;
         for (uint64_t t = 0; t < T; t++) {
-            if (!(recs[t].flags & 1u)) continue;
+            if (!gout && !(recs[t].flags & 1u)) continue;
             for (int l = 0; l < L; l++) {
                 uint32_t idx[8];
                 double wts[8];
@@ -1013,6 +1025,21 @@ double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record*
     free(mlp_part);
     free(loss_part);
     return loss;
+}
+
+double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
+                           const double* targets, uint64_t T, const double* den_fixed, double* grad)
+{
+    return loss_grad_core(c, params, recs, dirs, targets, NULL, T, den_fixed, grad);
+}
+
+/* Gradient of sum_t sum_ch gout[t][ch] * n(record_t, dir_t) with respect to
+ * every parameter (MLP and hash table), added into grad; returns the sum.
+ * Every record counts (like orc_query, which ignores the valid flag). */
+double orc_query_grad(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
+                      const double* gout, uint64_t T, double* grad)
+{
+    return loss_grad_core(c, params, recs, dirs, NULL, gout, T, NULL, grad);
 }
 
 /* ------------------------------------------------------------------------ */

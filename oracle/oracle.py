@@ -58,6 +58,8 @@ def lib():
         L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, P, P, P, P]
         L.orc_train_loss_grad.argtypes = [P, P, P, P, P, u64, P, P]
         L.orc_train_loss_grad.restype = f64
+        L.orc_query_grad.argtypes = [P, P, P, P, P, u64, P]
+        L.orc_query_grad.restype = f64
         L.orc_adam_step.argtypes = [u64, P, P, P, P, u32, f64, f64, f64, f64]
         L.orc_mrse.argtypes = [P, P, u64, f64]
         L.orc_mrse.restype = f64
@@ -207,6 +209,19 @@ def loss_grad(cfg, params, recs, dirs, targets, den_fixed=None):
     loss = lib().orc_train_loss_grad(ctypes.byref(c), _ptr(p), _ptr(r), _ptr(d), _ptr(t), r.shape[0],
                                      None if den is None else _ptr(den), _ptr(g))
     return float(loss), g
+
+
+def query_grad(cfg, params, recs, dirs, gout):
+    """Vector-Jacobian product of the bare cache query: returns
+    (sum gout * n, d(sum gout * n)/dparams) over every record."""
+    c = ocfg(cfg)
+    p = _params64(params)
+    r = np.ascontiguousarray(recs)
+    d = np.ascontiguousarray(dirs, np.float32)
+    go = np.ascontiguousarray(gout, np.float64)
+    g = np.zeros(p.shape[0], np.float64)
+    val = lib().orc_query_grad(ctypes.byref(c), _ptr(p), _ptr(r), _ptr(d), _ptr(go), r.shape[0], _ptr(g))
+    return float(val), g
 
 
 def adam_step(params, m, v, g, step, lr, beta1, beta2, eps):

@@ -323,6 +323,24 @@ nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, 
     return NIRC_OK;
 }
 
+nirc_status nirc_load_params(nirc_handle* h, const float* params, int on_device, void* stream) {
+    if (!h || !params) {
+        set_error("nirc_load_params: NULL argument");
+        return NIRC_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(h->params, params, h->shape.n_mlp * sizeof(float), kind, st);
+    if (e == cudaSuccess && h->shape.n_hash)
+        e = cudaMemcpyAsync(h->params + h->shape.hash_off, params + h->shape.n_mlp, h->shape.n_hash * sizeof(float),
+                            kind, st);
+    if (e == cudaSuccess) e = launch_repack_simt(h, st);
+    if (e == cudaSuccess) e = launch_hash_to_half(h, st);
+    if (e == cudaSuccess) e = launch_repack_tc(h, st);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);
+    return cuda_status(e, "nirc_load_params");
+}
+
 static nirc_status copy_out(const nirc_handle* h, const float* src, float* out, int on_device, void* stream,
                             const char* what) {
     cudaStream_t st = (cudaStream_t)stream;
@@ -480,10 +498,47 @@ nirc_status nirc_train_step(nirc_handle* h, const nirc_record* d_records, const 
         set_error("nirc_train_step: NULL/misaligned pointer or n too large");
         return NIRC_ERR_INVALID;
     }
-    nirc_status s = ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h->shape, n), "training");
+    nirc_status s = ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h, n), "training");
     if (s != NIRC_OK) return s;
     return cuda_status(launch_train_step(h, d_records, d_dirs, d_targets, n, d_loss, (cudaStream_t)stream),
                        "nirc_train_step");
+}
+
+nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t recompute_chunk) {
+    if (!h || (!store_activations && (recompute_chunk < 1024 || recompute_chunk > (1ull << 26)))) {
+        set_error("nirc_set_train_mode: NULL handle or recompute_chunk outside 1024..2^26");
+        return NIRC_ERR_INVALID;
+    }
+    h->store_activations = store_activations ? 1 : 0;
+    if (!store_activations) h->recompute_chunk = recompute_chunk;
+    return NIRC_OK;
+}
+
+nirc_status nirc_query_bwd(nirc_handle* h, const nirc_record* d_records, const float* d_dirs,
+                           const float* d_grad_out, uint64_t n, float* d_grad_params, float* d_value, void* stream) {
+    if (!h) {
+        set_error("nirc_query_bwd: handle is NULL");
+        return NIRC_ERR_INVALID;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        cudaError_t e = cudaMemsetAsync(h->grad, 0, h->shape.n_dev * sizeof(float), st);
+        if (e == cudaSuccess && d_value) e = cudaMemsetAsync(d_value, 0, sizeof(float), st);
+        if (e == cudaSuccess && d_grad_params) {
+            e = cudaMemsetAsync(d_grad_params, 0, (h->shape.n_mlp + h->shape.n_hash) * sizeof(float), st);
+        }
+        return cuda_status(e, "nirc_query_bwd");
+    }
+    if (!d_records || !d_dirs || !d_grad_out || !aligned16(d_records) || n > 0xFFFFFFFFull) {
+        set_error("nirc_query_bwd: NULL/misaligned pointer or n too large");
+        return NIRC_ERR_INVALID;
+    }
+    nirc_status s = ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h, n), "training");
+    if (s != NIRC_OK) return s;
+    cudaError_t e = launch_query_bwd(h, d_records, d_dirs, d_grad_out, n, d_value, st);
+    if (e != cudaSuccess) return cuda_status(e, "nirc_query_bwd");
+    if (!d_grad_params) return NIRC_OK;
+    return copy_out(h, h->grad, d_grad_params, 1, stream, "nirc_query_bwd");
 }
 
 nirc_status nirc_frame_mrse(const float* d_img_rgba, const float* d_ref_rgba, uint64_t n_pixels, float eps,

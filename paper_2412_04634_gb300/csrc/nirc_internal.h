@@ -75,6 +75,8 @@ struct nirc_handle {
     size_t scratch_bytes = 0;
     void* train_scratch = nullptr;  // training activations
     size_t train_scratch_bytes = 0;
+    int store_activations = 1;      // 0: recompute activations chunk by chunk
+    uint64_t recompute_chunk = 1ull << 15;
     float* loss_accum = nullptr;    // one float
     int* dev_err = nullptr;         // device flag: a bounded wait ran out (1)
     int* host_err = nullptr;        // pinned copy of dev_err, refreshed after tensor-core launches
@@ -129,9 +131,11 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
                             uint64_t* sig, uint32_t* count, float* row_n, int* err, cudaStream_t st);
 
 // nirc_train.cu
-size_t train_scratch_bytes(const NetShape& s, uint64_t n);
+size_t train_scratch_bytes(const nirc_handle* h, uint64_t n);
 cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
                               uint64_t n, float* d_loss, cudaStream_t st);
+cudaError_t launch_query_bwd(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* grad_out,
+                             uint64_t n, float* d_value, cudaStream_t st);
 cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st);
 
 // nirc_metrics.cu

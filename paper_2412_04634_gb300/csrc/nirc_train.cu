@@ -1,21 +1,35 @@
-// nirc_train.cu -- on-line training step of the cache (FP32 SIMT).
+// nirc_train.cu -- on-line training step of the cache (FP32 SIMT) and the
+// backward pass of the bare query.
 //
 // Loss: relative L2 of eq. 12 with p_r = 1,
 //   L = 1/(3n) sum_t sum_rgb valid_t (f - n)^2 / (sg(n)^2 + eps),
 // so dL/dn = -2 (f - n) / ((n^2 + eps) 3n) with the denominator held
 // constant (stop-gradient), and dL/dz = dL/dn * n below the output clamp.
+// The query backward takes dL/dn from the caller instead (every row counts).
 //
-//  k_train_fwd   per sample: encoding, layers with stored activations
-//                ([feature][sample] columns, coalesced), loss, dL/dz
+//  k_train_fwd   per sample: encoding, layers, loss, dL/dz; optionally the
+//                network input and ReLU outputs as [feature][sample]
+//                columns (coalesced) for the backward
 //  k_train_bwd   per sample: deltas through the ReLU layers (transposed
 //                weights in shared memory), then the hash-feature gradient
-//                scattered into the table gradient with float atomics
+//                scattered into the table gradient: lanes of a warp that hit
+//                the same table entry are combined first (__match_any_sync)
+//                and the group leader issues one float2 atomic for both
+//                features
 //  k_grad_w      per layer: dW = delta x^T and db = sum delta, 4x4 register
 //                tiles over 32-sample chunks staged in shared memory,
 //                split over blocks and combined with float atomics
 //  k_adam        dense bias-corrected Adam over every parameter (untouched
 //                hash entries have g = 0), FP32 master weights and moments,
 //                FP16 copy of the hash table refreshed in the same pass
+//
+// Activations: stored (one forward writes every layer's output for the whole
+// batch, n x (n_in + 2 x 64 x hidden) floats) or recomputed (the first
+// forward keeps only dL/dz; the batch is then walked in chunks whose
+// forward is run again with stores into a chunk-sized buffer, followed by
+// that chunk's backward and weight gradients).  Recomputation trades one
+// extra forward for O(chunk) instead of O(n) activation memory; a chunk of
+// 2^15 samples keeps the activation buffer (~78 MB) inside the 129 MB L2.
 #include <cmath>
 
 #include "nirc_internal.h"
@@ -27,31 +41,53 @@ constexpr int kTrainThreads = 128;
 constexpr int kGradChunk = 32;
 constexpr int kGradThreads = 352;  // 16 x 22 tiles of 4 x 4
 
+// Column-major per-sample buffers.  e / act / delta hold `ld` samples (the
+// whole batch when stored, one chunk when recomputed); dz covers the whole
+// batch with its own leading dimension, already offset to the launch's first
+// sample.
 struct TrainPtrs {
-    float* e;      // [n_in][n]
-    float* act;    // [hidden][64][n]
-    float* dz;     // [3][n]
-    float* delta;  // [hidden][64][n]
+    float* e;      // [n_in][ld]
+    float* act;    // [hidden][64][ld]
+    float* delta;  // [hidden][64][ld]
+    uint64_t ld;
+    float* dz;     // [3][dz_ld]
+    uint64_t dz_ld;
 };
 
-size_t train_scratch_bytes(const NetShape& s, uint64_t n) {
-    return (size_t)n * ((size_t)s.n_in + 2ull * kWidth * s.hidden + 3) * sizeof(float) + 256;
+enum LossKind : int {
+    kLossRelL2 = 0,    // eq. 12 against targets, valid records only
+    kLossUpstream = 1, // dL/dn given per row (query backward), every row
+    kLossNone = 2      // recompute pass: dz already known
+};
+
+static uint64_t act_floats_per_sample(const NetShape& s) { return (uint64_t)s.n_in + 2ull * kWidth * s.hidden; }
+
+static uint64_t chunk_of(const nirc_handle* h, uint64_t n) {
+    return h->store_activations ? n : (n < h->recompute_chunk ? n : h->recompute_chunk);
 }
 
-static TrainPtrs carve(void* base, const NetShape& s, uint64_t n) {
+size_t train_scratch_bytes(const nirc_handle* h, uint64_t n) {
+    const uint64_t c = chunk_of(h, n);
+    return (size_t)(3 * n + c * act_floats_per_sample(h->shape)) * sizeof(float) + 256;
+}
+
+static TrainPtrs carve(void* base, const NetShape& s, uint64_t n, uint64_t chunk) {
     float* f = reinterpret_cast<float*>(base);
     TrainPtrs t;
-    t.e = f;
-    t.act = t.e + (size_t)s.n_in * n;
-    t.dz = t.act + (size_t)s.hidden * kWidth * n;
-    t.delta = t.dz + 3 * n;
+    t.dz = f;
+    t.dz_ld = n;
+    t.e = f + 3 * n;
+    t.act = t.e + (size_t)s.n_in * chunk;
+    t.delta = t.act + (size_t)s.hidden * kWidth * chunk;
+    t.ld = chunk;
     return t;
 }
 
 __global__ void __launch_bounds__(kTrainThreads, 1)
     k_train_fwd(NetShape s, GridParams g, float z_clamp, float loss_eps, float scale, const float* __restrict__ packed,
                 const float* __restrict__ table, const nirc_record* __restrict__ recs, const float* __restrict__ dirs,
-                const float* __restrict__ targets, uint64_t n, TrainPtrs tp, float* __restrict__ loss_accum) {
+                const float* __restrict__ targets, uint64_t n, TrainPtrs tp, int store, int kind,
+                float* __restrict__ loss_accum) {
     extern __shared__ __align__(16) float smem[];
     float* sw = smem;
     float* act = smem + s.packed_floats + threadIdx.x;
@@ -64,7 +100,8 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         const uint64_t t = in_range ? first + threadIdx.x : 0;
         const float4* rq = reinterpret_cast<const float4*>(recs + t);
         const float4 r0 = __ldg(rq), r1 = __ldg(rq + 1), r3 = __ldg(rq + 3);
-        const bool valid = in_range && (__float_as_uint(r3.z) & 1u);
+        const bool valid = in_range && (kind == kLossUpstream || (__float_as_uint(r3.z) & 1u));
+        const bool keep = in_range && store;
         const V3 p{r0.x, r0.y, r0.z}, nn{r0.w, r1.x, r1.y};
         const V3 wi{__ldg(dirs + 3 * t), __ldg(dirs + 3 * t + 1), __ldg(dirs + 3 * t + 2)};
         encode_surface(s, g, table, p, nn, act, stride);  // [pos][nrm]
@@ -73,12 +110,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
         freq4_accurate(th, edir);
         freq4_accurate(ph, edir + 8);
         // network input in parameter order [pos][dir][nrm]
-        if (in_range) {
-            for (uint32_t k = 0; k < s.n_pos; ++k) tp.e[(uint64_t)k * n + t] = act[k * stride];
+        if (keep) {
+            const uint64_t ld = tp.ld;
+            for (uint32_t k = 0; k < s.n_pos; ++k) tp.e[(uint64_t)k * ld + t] = act[k * stride];
 #pragma unroll
-            for (uint32_t k = 0; k < 16; ++k) tp.e[(uint64_t)(s.n_pos + k) * n + t] = edir[k];
+            for (uint32_t k = 0; k < 16; ++k) tp.e[(uint64_t)(s.n_pos + k) * ld + t] = edir[k];
             for (uint32_t k = 0; k < kNrmFeatures; ++k)
-                tp.e[(uint64_t)(s.n_pos + 16 + k) * n + t] = act[(s.n_pos + k) * stride];
+                tp.e[(uint64_t)(s.n_pos + 16 + k) * ld + t] = act[(s.n_pos + k) * stride];
         }
 
         float2 acc[32];
@@ -87,13 +125,13 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
 #pragma unroll
         for (int i = 0; i < 16; ++i) fma_row(acc, sw + s.off_wdir + i * kWidth, edir[i]);
         for (uint32_t l = 0; l < s.hidden; ++l) {
-            float* ag = tp.act + ((uint64_t)l * kWidth) * n + t;
+            float* ag = tp.act + ((uint64_t)l * kWidth) * tp.ld + t;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const float a0 = fmaxf(acc[q].x, 0.f), a1 = fmaxf(acc[q].y, 0.f);
-                if (in_range) {
-                    ag[(uint64_t)(2 * q) * n] = a0;
-                    ag[(uint64_t)(2 * q + 1) * n] = a1;
+                if (keep) {
+                    ag[(uint64_t)(2 * q) * tp.ld] = a0;
+                    ag[(uint64_t)(2 * q + 1) * tp.ld] = a1;
                 }
                 act[(2 * q) * stride] = a0;
                 act[(2 * q + 1) * stride] = a1;
@@ -112,25 +150,59 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             z[1] += Wo[4 * i + 1] * a;
             z[2] += Wo[4 * i + 2] * a;
         }
+        if (kind == kLossNone) continue;  // block-uniform
         float lt = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const bool clamped = !(z[c] <= z_clamp);
             const float nv = expf(clamped ? z_clamp : z[c]);
-            const float f = __ldg(targets + 3 * t + c);
-            const float den = nv * nv + loss_eps;
-            const float diff = f - nv;
+            const float f = in_range ? __ldg(targets + 3 * t + c) : 0.f;
             float dz = 0.f;
-            if (valid) {
-                lt += diff * diff / den;
-                dz = clamped ? 0.f : -2.f * diff / den * scale * nv;
+            if (kind == kLossUpstream) {
+                // f holds dL/dn; the accumulated value is sum dL/dn * n
+                if (valid) {
+                    lt += f * nv;
+                    dz = clamped ? 0.f : f * nv;
+                }
+            } else {
+                const float den = nv * nv + loss_eps;
+                const float diff = f - nv;
+                if (valid) {
+                    lt += diff * diff / den * scale;
+                    dz = clamped ? 0.f : -2.f * diff / den * scale * nv;
+                }
             }
-            if (in_range) tp.dz[(uint64_t)c * n + t] = dz;
+            if (in_range) tp.dz[(uint64_t)c * tp.dz_ld + t] = dz;
         }
-        lt *= scale;
         for (int o = 16; o > 0; o >>= 1) lt += __shfl_xor_sync(0xffffffffu, lt, o);
         if ((threadIdx.x & 31) == 0 && loss_accum) atomicAdd(loss_accum, lt);
     }
+}
+
+// Add (g0, g1) into the two features of table entry idx.  Lanes of the warp
+// holding the same entry are summed first; the lowest lane of each group
+// issues one 8-byte atomic.  Every lane of the warp must call this together
+// (the caller's loop is warp-uniform); lanes with valid == false contribute
+// nothing.
+__device__ __forceinline__ void scatter_pair(float* __restrict__ gt, uint32_t idx, bool valid, float g0, float g1) {
+    const uint32_t key = valid ? idx : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const unsigned groups = __reduce_max_sync(0xffffffffu, valid ? (unsigned)__popc(peers) : 1u);
+    float s0 = g0, s1 = g1;
+    unsigned rest = peers & ~(1u << lane);
+    for (unsigned i = 1; i < groups; ++i) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        rest &= rest - 1u;
+        const float a0 = __shfl_sync(0xffffffffu, g0, src);
+        const float a1 = __shfl_sync(0xffffffffu, g1, src);
+        if (src != lane) {
+            s0 += a0;
+            s1 += a1;
+        }
+    }
+    if (valid && lane == __ffs(peers) - 1)
+        atomicAdd(reinterpret_cast<float2*>(gt + 2 * (uint64_t)idx), make_float2(s0, s1));
 }
 
 __device__ __forceinline__ float dot64(const float* __restrict__ wrow, const float (&d)[64]) {
@@ -149,48 +221,52 @@ __device__ __forceinline__ float dot64(const float* __restrict__ wrow, const flo
 
 __global__ void __launch_bounds__(kTrainThreads, 1)
     k_train_bwd(NetShape s, GridParams g, const float* __restrict__ packed, const nirc_record* __restrict__ recs,
-                uint64_t n, TrainPtrs tp, float* __restrict__ grad_table) {
+                uint64_t n, TrainPtrs tp, int all_records, float* __restrict__ grad_table) {
     extern __shared__ __align__(16) float smem[];
     float* sw = smem;
     stage_weights(sw, packed, s.packed_floats);
     __syncthreads();
-    for (uint64_t t = (uint64_t)blockIdx.x * kTrainThreads + threadIdx.x; t < n; t += (uint64_t)gridDim.x * kTrainThreads) {
-        const float dz0 = tp.dz[t], dz1 = tp.dz[n + t], dz2 = tp.dz[2 * n + t];
+    const uint64_t ld = tp.ld;
+    // Uniform trip count per block: the hash scatter uses full-warp collectives.
+    for (uint64_t first = (uint64_t)blockIdx.x * kTrainThreads; first < n; first += (uint64_t)gridDim.x * kTrainThreads) {
+        const bool in_range = first + threadIdx.x < n;
+        const uint64_t t = in_range ? first + threadIdx.x : first;
+        const float dz0 = tp.dz[t], dz1 = tp.dz[tp.dz_ld + t], dz2 = tp.dz[2 * tp.dz_ld + t];
         float d[64];
         const float* Wo = sw + s.off_out;
         const uint32_t H = s.hidden;
         {
-            const float* ag = tp.act + ((uint64_t)(H - 1) * kWidth) * n + t;
-            float* dg = tp.delta + ((uint64_t)(H - 1) * kWidth) * n + t;
+            const float* ag = tp.act + ((uint64_t)(H - 1) * kWidth) * ld + t;
+            float* dg = tp.delta + ((uint64_t)(H - 1) * kWidth) * ld + t;
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
                 const float4 w = *reinterpret_cast<const float4*>(Wo + 4 * i);
                 const float v = w.x * dz0 + w.y * dz1 + w.z * dz2;
-                d[i] = ag[(uint64_t)i * n] > 0.f ? v : 0.f;
-                dg[(uint64_t)i * n] = d[i];
+                d[i] = ag[(uint64_t)i * ld] > 0.f ? v : 0.f;
+                if (in_range) dg[(uint64_t)i * ld] = d[i];
             }
         }
         for (int l = (int)H - 1; l >= 1; --l) {
             // delta_{l-1}[i] = (sum_o W_l[o][i] delta_l[o]) [act_{l-1}[i] > 0]; W_l^T row i = W_l[:, i]
             const float* Wl = sw + s.off_hidden + (l - 1) * (kWidth * kWidth + kWidth);
-            const float* ag = tp.act + ((uint64_t)(l - 1) * kWidth) * n + t;
-            float* dg = tp.delta + ((uint64_t)(l - 1) * kWidth) * n + t;
+            const float* ag = tp.act + ((uint64_t)(l - 1) * kWidth) * ld + t;
+            float* dg = tp.delta + ((uint64_t)(l - 1) * kWidth) * ld + t;
             float dn[64];
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
                 const float v = dot64(Wl + i * kWidth, d);
-                dn[i] = ag[(uint64_t)i * n] > 0.f ? v : 0.f;
+                dn[i] = ag[(uint64_t)i * ld] > 0.f ? v : 0.f;
             }
 #pragma unroll
             for (int i = 0; i < 64; ++i) {
                 d[i] = dn[i];
-                dg[(uint64_t)i * n] = dn[i];
+                if (in_range) dg[(uint64_t)i * ld] = dn[i];
             }
         }
         if (s.hashgrid) {
             const float4* rq = reinterpret_cast<const float4*>(recs + t);
             const float4 r0 = __ldg(rq), r3 = __ldg(rq + 3);
-            if (!(__float_as_uint(r3.z) & 1u)) continue;
+            const bool valid = in_range && (all_records || (__float_as_uint(r3.z) & 1u));
             const V3 p{r0.x, r0.y, r0.z};
             const uint64_t T = (uint64_t)g.mask + 1;
             for (uint32_t l = 0; l < g.n_levels; ++l) {
@@ -202,19 +278,17 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                 grid_corners(g.level[l], g.mask, p, idx, w);
                 float* gt = grad_table + (uint64_t)l * T * 2;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    atomicAdd(gt + 2 * (uint64_t)idx[c], w[c] * de0);
-                    atomicAdd(gt + 2 * (uint64_t)idx[c] + 1, w[c] * de1);
-                }
+                for (int c = 0; c < 8; ++c) scatter_pair(gt, idx[c], valid, w[c] * de0, w[c] * de1);
             }
         }
     }
 }
 
 struct GradJob {
-    const float* dl;  // [out][n]
-    const float* x;   // [in][n]
+    const float* dl;  // [out][ld_dl]
+    const float* x;   // [in][ld_x]
     float* gw;        // W [out][in] followed by b [out]
+    uint64_t ld_dl, ld_x;
     uint32_t out, in;
 };
 struct GradJobs {
@@ -236,11 +310,11 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_w(GradJobs jobs, uint64_t
         __syncthreads();
         for (int k = tid; k < (int)J.out * kGradChunk; k += kGradThreads) {
             const int o = k / kGradChunk, tt = k % kGradChunk;
-            ds[tt][o] = t0 + tt < n ? J.dl[(uint64_t)o * n + t0 + tt] : 0.f;
+            ds[tt][o] = t0 + tt < n ? J.dl[(uint64_t)o * J.ld_dl + t0 + tt] : 0.f;
         }
         for (int k = tid; k < (int)J.in * kGradChunk; k += kGradThreads) {
             const int i = k / kGradChunk, tt = k % kGradChunk;
-            xs[tt][i] = t0 + tt < n ? J.x[(uint64_t)i * n + t0 + tt] : 0.f;
+            xs[tt][i] = t0 + tt < n ? J.x[(uint64_t)i * J.ld_x + t0 + tt] : 0.f;
         }
         for (int tt = tid; tt < kGradChunk; tt += kGradThreads) xs[tt][J.in] = 1.f;  // bias column
         __syncthreads();
@@ -296,10 +370,14 @@ cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
-                              uint64_t n, float* d_loss, cudaStream_t st) {
+// Forward, backward and weight gradients of n samples into h->grad (zeroed
+// first); the loss (or sum dL/dn * n) lands in h->loss_accum.
+static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
+                              uint64_t n, int kind, cudaStream_t st) {
     const NetShape& s = h->shape;
-    TrainPtrs tp = carve(h->train_scratch, s, n);
+    const uint64_t chunk = chunk_of(h, n);
+    const bool store = chunk == n;
+    TrainPtrs tp = carve(h->train_scratch, s, n, chunk);
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->grad, 0, s.n_dev * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
@@ -309,43 +387,69 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
         return e;
     if ((e = cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b)) != cudaSuccess)
         return e;
-    uint64_t blocks = (n + kTrainThreads - 1) / kTrainThreads;
-    if (blocks > (uint64_t)h->num_sms) blocks = h->num_sms;
     const float scale = 1.0f / (3.0f * (float)n);
     const float* table = h->params + s.hash_off;
+    auto blocks_for = [&](uint64_t m) {
+        uint64_t b = (m + kTrainThreads - 1) / kTrainThreads;
+        return (uint32_t)(b > (uint64_t)h->num_sms ? h->num_sms : b);
+    };
+    // full-batch forward: loss and dL/dz, activations only when stored
     timer_begin(h, NIRC_K_TRAIN_FWD, st);
-    k_train_fwd<<<(uint32_t)blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
-                                                                 h->packed, table, recs, dirs, targets, n, tp,
-                                                                 h->loss_accum);
+    k_train_fwd<<<blocks_for(n), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
+                                                             h->packed, table, recs, dirs, targets, n, tp,
+                                                             store ? 1 : 0, kind, h->loss_accum);
     timer_end(h, NIRC_K_TRAIN_FWD, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    timer_begin(h, NIRC_K_TRAIN_BWD, st);
-    k_train_bwd<<<(uint32_t)blocks, kTrainThreads, smem_b, st>>>(s, h->grid, h->packed, recs, n, tp,
-                                                                 h->grad + s.hash_off);
-    timer_end(h, NIRC_K_TRAIN_BWD, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (uint64_t c0 = 0; c0 < n; c0 += chunk) {
+        const uint64_t m = n - c0 < chunk ? n - c0 : chunk;
+        TrainPtrs tc = tp;
+        tc.dz = tp.dz + c0;
+        if (!store) {
+            timer_begin(h, NIRC_K_TRAIN_FWD, st);
+            k_train_fwd<<<blocks_for(m), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps,
+                                                                     scale, h->packed, table, recs + c0,
+                                                                     dirs + 3 * c0, targets + 3 * c0, m, tc, 1,
+                                                                     kLossNone, nullptr);
+            timer_end(h, NIRC_K_TRAIN_FWD, st);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        timer_begin(h, NIRC_K_TRAIN_BWD, st);
+        k_train_bwd<<<blocks_for(m), kTrainThreads, smem_b, st>>>(s, h->grid, h->packed, recs + c0, m, tc,
+                                                                 kind == kLossUpstream ? 1 : 0, h->grad + s.hash_off);
+        timer_end(h, NIRC_K_TRAIN_BWD, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
-    // weight gradients, layer 0 = input layer
-    GradJobs jobs;
-    uint64_t off = 0;
-    for (uint32_t l = 0; l <= s.hidden; ++l) {
-        GradJob& J = jobs.j[l];
-        J.out = l == s.hidden ? 3 : kWidth;
-        J.in = l == 0 ? s.n_in : kWidth;
-        J.dl = l == s.hidden ? tp.dz : tp.delta + (uint64_t)l * kWidth * n;
-        J.x = l == 0 ? tp.e : tp.act + (uint64_t)(l - 1) * kWidth * n;
-        J.gw = h->grad + off;
-        off += (uint64_t)J.out * J.in + J.out;
+        // weight gradients, layer 0 = input layer
+        GradJobs jobs;
+        uint64_t off = 0;
+        for (uint32_t l = 0; l <= s.hidden; ++l) {
+            GradJob& J = jobs.j[l];
+            J.out = l == s.hidden ? 3 : kWidth;
+            J.in = l == 0 ? s.n_in : kWidth;
+            J.dl = l == s.hidden ? tc.dz : tc.delta + (uint64_t)l * kWidth * tc.ld;
+            J.ld_dl = l == s.hidden ? tc.dz_ld : tc.ld;
+            J.x = l == 0 ? tc.e : tc.act + (uint64_t)(l - 1) * kWidth * tc.ld;
+            J.ld_x = tc.ld;
+            J.gw = h->grad + off;
+            off += (uint64_t)J.out * J.in + J.out;
+        }
+        const uint64_t n_chunks = (m + kGradChunk - 1) / kGradChunk;
+        uint64_t gx = (2ull * h->num_sms + s.hidden) / (s.hidden + 1);
+        if (gx > n_chunks) gx = n_chunks;
+        if (gx < 1) gx = 1;
+        timer_begin(h, NIRC_K_TRAIN_GRADW, st);
+        k_grad_w<<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+        timer_end(h, NIRC_K_TRAIN_GRADW, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const uint64_t n_chunks = (n + kGradChunk - 1) / kGradChunk;
-    uint64_t gx = (2ull * h->num_sms + s.hidden) / (s.hidden + 1);
-    if (gx > n_chunks) gx = n_chunks;
-    if (gx < 1) gx = 1;
-    timer_begin(h, NIRC_K_TRAIN_GRADW, st);
-    k_grad_w<<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, n);
-    timer_end(h, NIRC_K_TRAIN_GRADW, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaSuccess;
+}
 
+cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
+                              uint64_t n, float* d_loss, cudaStream_t st) {
+    const NetShape& s = h->shape;
+    cudaError_t e = train_pass(h, recs, dirs, targets, n, kLossRelL2, st);
+    if (e != cudaSuccess) return e;
     h->step += 1;
     const double b1 = h->cfg.beta1, b2 = h->cfg.beta2;
     const float inv_bc1 = (float)(1.0 / (1.0 - std::pow(b1, (double)h->step)));
@@ -364,6 +468,14 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
             return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_query_bwd(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* grad_out,
+                             uint64_t n, float* d_value, cudaStream_t st) {
+    cudaError_t e = train_pass(h, recs, dirs, grad_out, n, kLossUpstream, st);
+    if (e == cudaSuccess && d_value)
+        e = cudaMemcpyAsync(d_value, h->loss_accum, sizeof(float), cudaMemcpyDeviceToDevice, st);
+    return e;
 }
 
 }  // namespace nirc

@@ -75,6 +75,9 @@ def _load():
         "nirc_create": ([P, P], st),
         "nirc_destroy": ([P], st),
         "nirc_set_params": ([P, P, i32, P], st),
+        "nirc_load_params": ([P, P, i32, P], st),
+        "nirc_set_train_mode": ([P, i32, u64], st),
+        "nirc_query_bwd": ([P, P, P, P, u64, P, P, P], st),
         "nirc_get_params": ([P, P, i32, P], st),
         "nirc_get_grads": ([P, P, i32, P], st),
         "nirc_set_precision": ([P, u32], st),
@@ -161,6 +164,23 @@ def nirc_set_params(h, params: torch.Tensor, stream=None):
     on_dev = 1 if params.is_cuda else 0
     p = params.contiguous()
     _check(_lib.nirc_set_params(h, _ptr(p), on_dev, _stream(stream)))
+
+
+def nirc_load_params(h, params: torch.Tensor, stream=None):
+    on_dev = 1 if params.is_cuda else 0
+    p = params.contiguous()
+    _check(_lib.nirc_load_params(h, _ptr(p), on_dev, _stream(stream)))
+
+
+def nirc_set_train_mode(h, store_activations: bool = True, recompute_chunk: int = 1 << 15):
+    _check(_lib.nirc_set_train_mode(h, 1 if store_activations else 0, recompute_chunk))
+
+
+def nirc_query_bwd(h, records: torch.Tensor, dirs: torch.Tensor, grad_out: torch.Tensor,
+                   grad_params: torch.Tensor | None = None, value: torch.Tensor | None = None, stream=None):
+    n = dirs.shape[0]
+    _check(_lib.nirc_query_bwd(h, _ptr(records), _ptr(dirs), _ptr(grad_out), n, _ptr(grad_params), _ptr(value),
+                               _stream(stream)))
 
 
 def nirc_get_params(h, out: torch.Tensor, stream=None):
@@ -284,3 +304,36 @@ class Cache:
         out = torch.empty(self.n_params, dtype=torch.float32)
         nirc_get_grads(self.h, out)
         return out
+
+
+class NircQuery(torch.autograd.Function):
+    """Differentiable cache query: ``NircQuery.apply(params, records, dirs, cache)``
+    returns n = exp(min(MLP(enc(x, w, n)), z_clamp)) per row, (n, 3) float32.
+
+    ``params`` is the flat FP32 parameter vector (nirc_param_count layout, a
+    CUDA tensor); the forward loads it into the handle (nirc_load_params,
+    the handle's Adam state is kept) and calls nirc_query; the backward
+    reloads the same parameters and calls nirc_query_bwd.  Records and directions are not differentiated (they are
+    samples of the estimator, not parameters)."""
+
+    @staticmethod
+    def forward(ctx, params, records, dirs, cache):
+        assert params.is_cuda and params.dtype == torch.float32 and params.numel() == cache.n_params
+        records = records.contiguous()
+        dirs = dirs.contiguous().float()
+        nirc_load_params(cache.h, params.detach().contiguous())
+        out = torch.empty(dirs.shape[0], 3, device=dirs.device, dtype=torch.float32)
+        nirc_query(cache.h, records, dirs, out)
+        ctx.cache = cache
+        ctx.save_for_backward(params.detach(), records, dirs)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        params, records, dirs = ctx.saved_tensors
+        cache = ctx.cache
+        # the handle may have been loaded with other weights since the forward
+        nirc_load_params(cache.h, params.contiguous())
+        g = torch.empty(cache.n_params, device=dirs.device, dtype=torch.float32)
+        nirc_query_bwd(cache.h, records, dirs, grad_out.contiguous().float(), g)
+        return g, None, None, None

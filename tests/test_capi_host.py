@@ -59,6 +59,9 @@ def test_bad_arguments_return_status(N):
     assert N.lib().nirc_query(None, None, None, 5, None, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_train_step(None, None, None, None, 5, None, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_frame_mrse(None, None, 5, ctypes.c_float(0.01), None, None) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_query_bwd(None, None, None, None, 5, None, None, None) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_load_params(None, None, 0, None) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_set_train_mode(None, 1, 0) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_destroy(None) == N.NIRC_OK
     assert N.nirc_param_count(N.make_config(scenes.NetConfig(width=48))) == 0
 

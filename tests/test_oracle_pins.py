@@ -566,6 +566,75 @@ def test_gradients_match_finite_differences_hashgrid(oracle):
     assert np.all(g[untouched] == 0)
 
 
+def test_gradients_finite_differences_1024_samples(oracle):
+    """The training gradient on 1024 samples of the analytic radiance field
+    (uniform x, uniform directions and normals) against FP64 central
+    differences, hash-grid network with every kind of parameter sampled."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=8, log2_table=12,
+                           hidden_layers=4, base_res=4, growth=1.5)
+    params = scenes.init_params(cfg, 11).astype(np.float64)
+    rng = np.random.default_rng(12)
+    params[cfg.n_mlp_params:] = rng.uniform(-0.3, 0.3, cfg.n_hash_params)
+    recs, dirs, tg = scenes.training_batch(1024, seed=13)
+    _, g = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    touched = np.nonzero(g[cfg.n_mlp_params:])[0] + cfg.n_mlp_params
+    idx = np.concatenate([rng.choice(touched, 30, replace=False), rng.choice(cfg.n_mlp_params, 30, replace=False),
+                          np.arange(cfg.n_mlp_params - 3, cfg.n_mlp_params)])
+    _fd_check(oracle, cfg, params, recs, dirs, tg.astype(np.float64), idx)
+
+
+@pytest.mark.parametrize("hashgrid", [False, True])
+def test_query_gradient_matches_finite_differences(oracle, hashgrid):
+    """d(sum gout * n)/dparams of the bare query against central differences
+    of the query itself; records with the valid flag cleared still count."""
+    if hashgrid:
+        cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=6, log2_table=10,
+                               hidden_layers=3, base_res=4, growth=2.0)
+    else:
+        cfg = scenes.config_small()
+    params = scenes.init_params(cfg, 21).astype(np.float64)
+    rng = np.random.default_rng(22)
+    params[:cfg.n_mlp_params] += rng.normal(0, 0.02, cfg.n_mlp_params)
+    if hashgrid:
+        params[cfg.n_mlp_params:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params)
+    recs, dirs = scenes.random_query_rows(40, seed=23)
+    recs["flags"][::3] &= ~np.uint32(1)
+    gout = rng.normal(0, 1, (40, 3))
+    val, g = oracle.query_grad(cfg, params, recs, dirs, gout)
+    n0 = oracle.query(cfg, params, recs, dirs)
+    assert abs(val - float(np.sum(gout * n0))) <= 1e-12 * np.abs(gout * n0).sum()
+    nz = np.nonzero(g)[0]
+    idx = np.concatenate([rng.choice(nz, 60, replace=False), np.arange(cfg.n_mlp_params - 3, cfg.n_mlp_params)])
+    for i in idx:
+        pp = params.copy()
+        step = 1e-6 * max(1.0, abs(pp[i]))
+        pp[i] += step
+        fp = np.sum(gout * oracle.query(cfg, pp, recs, dirs))
+        pp[i] -= 2 * step
+        fm = np.sum(gout * oracle.query(cfg, pp, recs, dirs))
+        fd = (fp - fm) / (2 * step)
+        scale = max(abs(fd), abs(g[i]), 1e-3 * np.abs(g).max())
+        assert abs(fd - g[i]) <= 2e-5 * scale, (i, fd, g[i])
+
+
+def test_query_gradient_with_loss_upstream_is_training_gradient(oracle):
+    """The loss gradient is the query's vector-Jacobian product with
+    dL/dn = -2 (f - n) / ((n^2 + eps) 3T) on valid records and 0 elsewhere."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=4, log2_table=8,
+                           hidden_layers=2, base_res=4, growth=2.0)
+    params = scenes.init_params(cfg, 31).astype(np.float64)
+    params[cfg.n_mlp_params:] = np.random.default_rng(32).uniform(-0.5, 0.5, cfg.n_hash_params)
+    recs, dirs, tg = scenes.training_batch(100, seed=33)
+    recs["flags"][::7] &= ~np.uint32(1)
+    tg = tg.astype(np.float64)
+    n0 = oracle.query(cfg, params, recs, dirs)
+    gout = -2.0 * (tg - n0) / (n0 * n0 + cfg.loss_eps) / (3 * 100)
+    gout[(recs["flags"] & 1) == 0] = 0.0
+    _, g_loss = oracle.loss_grad(cfg, params, recs, dirs, tg)
+    _, g_vjp = oracle.query_grad(cfg, params, recs, dirs, gout)
+    assert np.allclose(g_vjp, g_loss, rtol=1e-10, atol=1e-14 * np.abs(g_loss).max())
+
+
 def test_loss_closed_form_for_constant_network(oracle):
     """With a constant network n = c the loss is mean (f - c)^2 / (c^2 + eps)."""
     cfg = scenes.config_small()
