@@ -248,6 +248,19 @@ nirc_status nirc_train_step(nirc_handle* h, const nirc_record* d_records, const 
  * the float atomics in the gradient sums. */
 nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t recompute_chunk);
 
+/* Deterministic training (on != 0): nirc_train_step and nirc_query_bwd give
+ * bit-identical losses, gradients and weights for identical inputs and
+ * state, however the GPU schedules the work (the default sums gradients with
+ * float atomics, whose order varies; with Adam's sign-like first steps that
+ * moves near-zero-gradient parameters by +-lr between runs).  Weight
+ * gradients and the loss are summed from per-block partials in a fixed
+ * order; the hash-table gradient is accumulated in 64-bit fixed point with a
+ * power-of-two scale per level (2^61 / (8 n max|dL/de|) rounded down), so
+ * each contribution keeps FP32 relative precision and the sum is exact.
+ * Costs extra scratch (2 x levels floats per sample, 8 bytes per table
+ * entry) and one more pass over the table gradient. */
+nirc_status nirc_set_deterministic(nirc_handle* h, int on);
+
 /* Backward of the bare query (for a torch.autograd.Function around
  * nirc_query): with d_grad_out = dL/dn (n x 3 floats, device) it computes
  * d_grad_params = sum_i dL/dn_i . dn_i/dparams over every row (the valid flag

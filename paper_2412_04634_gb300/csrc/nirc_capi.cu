@@ -158,6 +158,75 @@ void timer_end(const nirc_handle* hc, int cls, cudaStream_t st) {
     h->n_pending += 1;
 }
 
+static size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+size_t frame_scratch_bytes(uint64_t P, uint32_t M) {
+    return round256(P * sizeof(nirc_record)) + round256(P * sizeof(PixelBase)) + round256(P * M * sizeof(ResidRow));
+}
+
+nirc_status check_frame_args(const char* who, const void* scene, const nirc_frame_desc& fd, const float* out,
+                             const nirc_frame_aux* aux) {
+    const uint64_t P = (uint64_t)fd.width * fd.height;
+    if (!scene || !out || !aligned16(scene) || !aligned16(out)) {
+        set_error("%s: NULL or misaligned scene/output pointer", who);
+        return NIRC_ERR_INVALID;
+    }
+    if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
+        fd.max_depth > 64 || fd.cache_mode > 2 || P > 0xFFFFFFFFull) {
+        set_error("%s: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64)", who, NIRC_MAX_PRIMS);
+        return NIRC_ERR_INVALID;
+    }
+    if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
+                (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)) ||
+                (aux->row_n && ((uintptr_t)aux->row_n & 3u)))) {
+        set_error("%s: misaligned aux pointer", who);
+        return NIRC_ERR_INVALID;
+    }
+    return NIRC_OK;
+}
+
+nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
+                          float* out, const nirc_frame_aux* aux, void* scratch, cudaStream_t st) {
+    const uint64_t P = (uint64_t)fd.width * fd.height;
+    char* sp = reinterpret_cast<char*>(scratch);
+    const size_t rec_bytes = round256(P * sizeof(nirc_record));
+    const size_t base_bytes = round256(P * sizeof(PixelBase));
+    // The path-tracing kernel writes every record, base and residual row that
+    // the cache kernel reads, so no part of the scratch has to start at zero.
+    nirc_record* recs = reinterpret_cast<nirc_record*>(sp);
+    PixelBase* base = reinterpret_cast<PixelBase*>(sp + rec_bytes);
+    ResidRow* rows = reinterpret_cast<ResidRow*>(sp + rec_bytes + base_bytes);
+    uint64_t* sig = aux ? aux->sig : nullptr;
+    uint32_t* count = aux ? aux->count : nullptr;
+    timer_begin(h, NIRC_K_PATH_TRACE, st);
+    cudaError_t e = launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st);
+    timer_end(h, NIRC_K_PATH_TRACE, st);
+    if (e != cudaSuccess) {
+        set_error("%s (path tracing): %s", who, cudaGetErrorString(e));
+        return NIRC_ERR_CUDA;
+    }
+    timer_begin(h, NIRC_K_CACHE, st);
+    const bool tc = tc_supported(h, fd);
+    if (tc) {
+        e = launch_cache_tc(h, fd, recs, base, rows, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig, count,
+                            aux ? aux->row_n : nullptr, h->dev_err, st);
+    } else {
+        e = launch_cache_simt(h, fd, recs, base, rows, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
+                              count, aux ? aux->row_n : nullptr, st);
+    }
+    timer_end(h, NIRC_K_CACHE, st);
+    if (e == cudaSuccess && tc) e = cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) {
+        set_error("%s (cache integral): %s", who, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? NIRC_ERR_OOM : NIRC_ERR_CUDA;
+    }
+    return NIRC_OK;
+}
+
+nirc_status reserve_train_scratch(nirc_handle* h, uint64_t n) {
+    return ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h, n), "training");
+}
+
 }  // namespace nirc
 
 using namespace nirc;
@@ -416,50 +485,11 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
     const nirc_frame_desc& fd = *desc;
     const uint64_t P = (uint64_t)fd.width * fd.height;
     if (P == 0) return NIRC_OK;
-    if (!d_scene || !d_out_rgba || !aligned16(d_scene) || !aligned16(d_out_rgba)) {
-        set_error("nirc_estimate_frame: NULL or misaligned scene/output pointer");
-        return NIRC_ERR_INVALID;
-    }
-    if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
-        fd.max_depth > 64 || fd.cache_mode > 2 || P > 0xFFFFFFFFull) {
-        set_error("nirc_estimate_frame: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64)",
-                  NIRC_MAX_PRIMS);
-        return NIRC_ERR_INVALID;
-    }
-    if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
-                (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)) ||
-                (aux->row_n && ((uintptr_t)aux->row_n & 3u)))) {
-        set_error("nirc_estimate_frame: misaligned aux pointer");
-        return NIRC_ERR_INVALID;
-    }
-    const size_t rec_bytes = P * sizeof(nirc_record);
-    const size_t base_bytes = P * sizeof(PixelBase);
-    const size_t rows_bytes = P * fd.n_resid * sizeof(ResidRow);
-    nirc_status s = ensure(&h->scratch, &h->scratch_bytes, rec_bytes + base_bytes + rows_bytes + 256, "frame");
+    nirc_status s = check_frame_args("nirc_estimate_frame", d_scene, fd, d_out_rgba, aux);
     if (s != NIRC_OK) return s;
-    char* sp = reinterpret_cast<char*>(h->scratch);
-    nirc_record* recs = reinterpret_cast<nirc_record*>(sp);
-    PixelBase* base = reinterpret_cast<PixelBase*>(sp + rec_bytes);
-    ResidRow* rows = reinterpret_cast<ResidRow*>(sp + rec_bytes + base_bytes);
-    cudaStream_t st = (cudaStream_t)stream;
-    uint64_t* sig = aux ? aux->sig : nullptr;
-    uint32_t* count = aux ? aux->count : nullptr;
-    timer_begin(h, NIRC_K_PATH_TRACE, st);
-    cudaError_t e = launch_primary_resid(h, d_scene, fd, recs, base, rows, sig, count, st);
-    timer_end(h, NIRC_K_PATH_TRACE, st);
-    if (e != cudaSuccess) return cuda_status(e, "nirc_estimate_frame (path tracing)");
-    timer_begin(h, NIRC_K_CACHE, st);
-    const bool tc = tc_supported(h, fd);
-    if (tc) {
-        e = launch_cache_tc(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
-                            count, aux ? aux->row_n : nullptr, h->dev_err, st);
-    } else {
-        e = launch_cache_simt(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr,
-                              sig, count, aux ? aux->row_n : nullptr, st);
-    }
-    timer_end(h, NIRC_K_CACHE, st);
-    if (e == cudaSuccess && tc) e = cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
-    return cuda_status(e, "nirc_estimate_frame (cache integral)");
+    s = ensure(&h->scratch, &h->scratch_bytes, frame_scratch_bytes(P, fd.n_resid), "frame");
+    if (s != NIRC_OK) return s;
+    return enqueue_frame("nirc_estimate_frame", h, d_scene, fd, d_out_rgba, aux, h->scratch, (cudaStream_t)stream);
 }
 
 nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width, uint32_t height,
@@ -511,6 +541,15 @@ nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t 
     }
     h->store_activations = store_activations ? 1 : 0;
     if (!store_activations) h->recompute_chunk = recompute_chunk;
+    return NIRC_OK;
+}
+
+nirc_status nirc_set_deterministic(nirc_handle* h, int on) {
+    if (!h) {
+        set_error("nirc_set_deterministic: NULL handle");
+        return NIRC_ERR_INVALID;
+    }
+    h->deterministic = on ? 1 : 0;
     return NIRC_OK;
 }
 

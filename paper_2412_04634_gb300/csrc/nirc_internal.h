@@ -76,6 +76,7 @@ struct nirc_handle {
     void* train_scratch = nullptr;  // training activations
     size_t train_scratch_bytes = 0;
     int store_activations = 1;      // 0: recompute activations chunk by chunk
+    int deterministic = 0;          // 1: order-independent gradient sums
     uint64_t recompute_chunk = 1ull << 15;
     float* loss_accum = nullptr;    // one float
     int* dev_err = nullptr;         // device flag: a bounded wait ran out (1)
@@ -137,6 +138,20 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
 cudaError_t launch_query_bwd(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* grad_out,
                              uint64_t n, float* d_value, cudaStream_t st);
 cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st);
+
+// nirc_capi.cu: shared by the public frame entry points and the server.
+// Frame scratch = records | per-pixel bases | residual rows, each part
+// rounded up to 256 bytes.
+size_t frame_scratch_bytes(uint64_t P, uint32_t M);
+// Argument checks of a frame call (message prefixed with `who`).
+nirc_status check_frame_args(const char* who, const void* scene, const nirc_frame_desc& fd, const float* out,
+                             const nirc_frame_aux* aux);
+// Enqueue the path-tracing and cache-integral kernels of one frame on `st`
+// with the given scratch (frame_scratch_bytes bytes).
+nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
+                          float* out, const nirc_frame_aux* aux, void* scratch, cudaStream_t st);
+// Grow the handle's training scratch for batches of n (cudaMalloc).
+nirc_status reserve_train_scratch(nirc_handle* h, uint64_t n);
 
 // nirc_metrics.cu
 cudaError_t launch_mrse(const float* img, const float* ref, uint64_t n, float eps, double* out, cudaStream_t st);

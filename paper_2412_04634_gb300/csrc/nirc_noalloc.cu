@@ -53,8 +53,6 @@ static nirc_status scratch_address(int device, unsigned char** out) {
     return NIRC_OK;
 }
 
-static size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
-
 }  // namespace nirc
 
 using namespace nirc;
@@ -68,26 +66,9 @@ extern "C" nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d
     const nirc_frame_desc& fd = *desc;
     const uint64_t P = (uint64_t)fd.width * fd.height;
     if (P == 0) return NIRC_OK;
-    if (!d_scene || !d_out_rgba || ((uintptr_t)d_scene & 15u) || ((uintptr_t)d_out_rgba & 15u)) {
-        set_error("nirc_estimate_frame_noalloc: NULL or misaligned scene/output pointer");
-        return NIRC_ERR_INVALID;
-    }
-    if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
-        fd.max_depth > 64 || fd.cache_mode > 2 || P > 0xFFFFFFFFull) {
-        set_error("nirc_estimate_frame_noalloc: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64)",
-                  NIRC_MAX_PRIMS);
-        return NIRC_ERR_INVALID;
-    }
-    if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
-                (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)) ||
-                (aux->row_n && ((uintptr_t)aux->row_n & 3u)))) {
-        set_error("nirc_estimate_frame_noalloc: misaligned aux pointer");
-        return NIRC_ERR_INVALID;
-    }
-    const size_t rec_bytes = round256(P * sizeof(nirc_record));
-    const size_t base_bytes = round256(P * sizeof(PixelBase));
-    const size_t rows_bytes = round256(P * fd.n_resid * sizeof(ResidRow));
-    const size_t need = rec_bytes + base_bytes + rows_bytes;
+    nirc_status st = check_frame_args("nirc_estimate_frame_noalloc", d_scene, fd, d_out_rgba, aux);
+    if (st != NIRC_OK) return st;
+    const size_t need = frame_scratch_bytes(P, fd.n_resid);
     if (need > kNoAllocScratchBytes) {
         set_error("nirc_estimate_frame_noalloc: frame needs %zu bytes of scratch (W*H*(96 + 32*M) rounded), more than "
                   "the fixed %zu-byte area; use nirc_estimate_frame or a smaller tile",
@@ -98,30 +79,7 @@ extern "C" nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_status(e, "nirc_estimate_frame_noalloc");
     unsigned char* sp = nullptr;
-    const nirc_status st = scratch_address(dev, &sp);
+    st = scratch_address(dev, &sp);
     if (st != NIRC_OK) return st;
-    // The path-tracing kernel writes every record, base and residual row that
-    // the cache kernel reads, so no part of the array has to start at zero.
-    nirc_record* recs = reinterpret_cast<nirc_record*>(sp);
-    PixelBase* base = reinterpret_cast<PixelBase*>(sp + rec_bytes);
-    ResidRow* rows = reinterpret_cast<ResidRow*>(sp + rec_bytes + base_bytes);
-    cudaStream_t s = (cudaStream_t)stream;
-    uint64_t* sig = aux ? aux->sig : nullptr;
-    uint32_t* count = aux ? aux->count : nullptr;
-    timer_begin(h, NIRC_K_PATH_TRACE, s);
-    e = launch_primary_resid(h, d_scene, fd, recs, base, rows, sig, count, s);
-    timer_end(h, NIRC_K_PATH_TRACE, s);
-    if (e != cudaSuccess) return cuda_status(e, "nirc_estimate_frame_noalloc (path tracing)");
-    timer_begin(h, NIRC_K_CACHE, s);
-    const bool tc = tc_supported(h, fd);
-    if (tc) {
-        e = launch_cache_tc(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
-                            count, aux ? aux->row_n : nullptr, h->dev_err, s);
-    } else {
-        e = launch_cache_simt(h, fd, recs, base, rows, d_out_rgba, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr,
-                              sig, count, aux ? aux->row_n : nullptr, s);
-    }
-    timer_end(h, NIRC_K_CACHE, s);
-    if (e == cudaSuccess && tc) e = cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    return cuda_status(e, "nirc_estimate_frame_noalloc (cache integral)");
+    return enqueue_frame("nirc_estimate_frame_noalloc", h, d_scene, fd, d_out_rgba, aux, sp, (cudaStream_t)stream);
 }

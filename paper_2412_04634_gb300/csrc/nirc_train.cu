@@ -12,16 +12,28 @@
 //                columns (coalesced) for the backward
 //  k_train_bwd   per sample: deltas through the ReLU layers (transposed
 //                weights in shared memory), then the hash-feature gradient
-//                scattered into the table gradient: lanes of a warp that hit
-//                the same table entry are combined first (__match_any_sync)
-//                and the group leader issues one float2 atomic for both
-//                features
+//                scattered into the table gradient with one float2 atomic
+//                for both features of an entry; on the coarse dense levels
+//                (few cells, many samples per cell) lanes of a warp that hit
+//                the same entry are combined first (__match_any_sync) and
+//                only the group leader issues the atomic
 //  k_grad_w      per layer: dW = delta x^T and db = sum delta, 4x4 register
 //                tiles over 32-sample chunks staged in shared memory,
 //                split over blocks and combined with float atomics
 //  k_adam        dense bias-corrected Adam over every parameter (untouched
 //                hash entries have g = 0), FP32 master weights and moments,
 //                FP16 copy of the hash table refreshed in the same pass
+//
+// Deterministic mode (nirc_set_deterministic): identical inputs give
+// bit-identical losses, gradients and weights whatever the scheduling.  Block
+// partial sums of the loss and of dW are written out and added in a fixed
+// order; the hash-table gradient goes through a separate pass: the backward
+// stores dL/de per sample and level with the level's max |dL/de|, then
+// k_hash_scatter_fixed adds w * dL/de into 64-bit fixed-point accumulators
+// (integer atomics are order-independent) with a power-of-two scale per level
+// chosen so that no entry can overflow, and k_hash_fixed_to_float converts
+// them back.  Each contribution keeps FP32 relative precision; the sum is
+// exact.
 //
 // Activations: stored (one forward writes every layer's output for the whole
 // batch, n x (n_in + 2 x 64 x hidden) floats) or recomputed (the first
@@ -66,9 +78,30 @@ static uint64_t chunk_of(const nirc_handle* h, uint64_t n) {
     return h->store_activations ? n : (n < h->recompute_chunk ? n : h->recompute_chunk);
 }
 
+static uint64_t round64(uint64_t floats) { return (floats + 63) & ~63ull; }
+
+// Extra buffers of deterministic mode (all offsets 256-byte aligned).
+struct DetPtrs {
+    float* de;                 // [2 levels][n]: dL/de of the hash features
+    unsigned* lvl_max;         // [16]: max |dL/de| per level (float bits)
+    float* loss_part;          // [grid]: per-block loss sums
+    float* gw_part;            // [gx][n_mlp]: per-block weight gradients
+    unsigned long long* acc;   // [n_hash]: fixed-point hash gradient
+};
+
+static uint64_t max_grad_blocks(const nirc_handle* h) { return 2ull * (uint64_t)h->num_sms + 1; }
+
+static uint64_t det_floats(const nirc_handle* h, uint64_t n) {
+    const NetShape& s = h->shape;
+    return round64(2ull * s.levels * n) + 64 + round64((uint64_t)h->num_sms) + round64(max_grad_blocks(h) * s.n_mlp) +
+           2 * round64(s.n_hash);
+}
+
 size_t train_scratch_bytes(const nirc_handle* h, uint64_t n) {
     const uint64_t c = chunk_of(h, n);
-    return (size_t)(3 * n + c * act_floats_per_sample(h->shape)) * sizeof(float) + 256;
+    uint64_t f = round64(3 * n + c * act_floats_per_sample(h->shape));
+    if (h->deterministic) f += det_floats(h, n);
+    return (size_t)f * sizeof(float) + 256;
 }
 
 static TrainPtrs carve(void* base, const NetShape& s, uint64_t n, uint64_t chunk) {
@@ -83,12 +116,39 @@ static TrainPtrs carve(void* base, const NetShape& s, uint64_t n, uint64_t chunk
     return t;
 }
 
+static DetPtrs carve_det(const nirc_handle* h, void* base, uint64_t n, uint64_t chunk) {
+    const NetShape& s = h->shape;
+    float* f = reinterpret_cast<float*>(base) + round64(3 * n + chunk * act_floats_per_sample(s));
+    DetPtrs d;
+    d.de = f;
+    f += round64(2ull * s.levels * n);
+    d.lvl_max = reinterpret_cast<unsigned*>(f);
+    f += 64;
+    d.loss_part = f;
+    f += round64((uint64_t)h->num_sms);
+    d.gw_part = f;
+    f += round64(max_grad_blocks(h) * s.n_mlp);
+    d.acc = reinterpret_cast<unsigned long long*>(f);
+    return d;
+}
+
+// Power-of-two scale of level sums: every entry receives at most 8 n
+// contributions of magnitude <= m, so |sum| * scale < 2^61.
+__device__ __forceinline__ float fixed_scale(float m, uint64_t n) {
+    if (!(m > 0.f)) return 1.f;
+    int e = 0;
+    frexpf(8.f * (float)n * m, &e);
+    return ldexpf(1.f, min(61 - e, 100));
+}
+
 __global__ void __launch_bounds__(kTrainThreads, 1)
     k_train_fwd(NetShape s, GridParams g, float z_clamp, float loss_eps, float scale, const float* __restrict__ packed,
                 const float* __restrict__ table, const nirc_record* __restrict__ recs, const float* __restrict__ dirs,
                 const float* __restrict__ targets, uint64_t n, TrainPtrs tp, int store, int kind,
-                float* __restrict__ loss_accum) {
+                float* __restrict__ loss_accum, float* __restrict__ loss_part) {
     extern __shared__ __align__(16) float smem[];
+    __shared__ float warp_loss[kTrainThreads / 32];
+    float loss_run = 0.f;  // this lane's warp sums over the iterations (lane 0)
     float* sw = smem;
     float* act = smem + s.packed_floats + threadIdx.x;
     const int stride = kTrainThreads;
@@ -175,7 +235,18 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
             if (in_range) tp.dz[(uint64_t)c * tp.dz_ld + t] = dz;
         }
         for (int o = 16; o > 0; o >>= 1) lt += __shfl_xor_sync(0xffffffffu, lt, o);
-        if ((threadIdx.x & 31) == 0 && loss_accum) atomicAdd(loss_accum, lt);
+        loss_run += lt;
+    }
+    if (kind == kLossNone) return;
+    // block sum in a fixed order: one atomic per block, or one partial per
+    // block in deterministic mode
+    if ((threadIdx.x & 31) == 0) warp_loss[threadIdx.x >> 5] = loss_run;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int w = 0; w < kTrainThreads / 32; ++w) b += warp_loss[w];
+        if (loss_part) loss_part[blockIdx.x] = b;
+        else if (loss_accum) atomicAdd(loss_accum, b);
     }
 }
 
@@ -221,7 +292,8 @@ __device__ __forceinline__ float dot64(const float* __restrict__ wrow, const flo
 
 __global__ void __launch_bounds__(kTrainThreads, 1)
     k_train_bwd(NetShape s, GridParams g, const float* __restrict__ packed, const nirc_record* __restrict__ recs,
-                uint64_t n, TrainPtrs tp, int all_records, float* __restrict__ grad_table) {
+                uint64_t n, TrainPtrs tp, int all_records, float* __restrict__ grad_table, float* __restrict__ de_out,
+                uint64_t de_ld, unsigned* __restrict__ lvl_max) {
     extern __shared__ __align__(16) float smem[];
     float* sw = smem;
     stage_weights(sw, packed, s.packed_floats);
@@ -273,14 +345,82 @@ __global__ void __launch_bounds__(kTrainThreads, 1)
                 // dL/de for the two features of level l: W0[:, k] = Wpix^T row k
                 const float de0 = dot64(sw + s.off_wpix + (2 * l) * kWidth, d);
                 const float de1 = dot64(sw + s.off_wpix + (2 * l + 1) * kWidth, d);
+                if (de_out) {
+                    // deterministic mode: k_hash_scatter_fixed adds these later
+                    const float a0 = valid ? de0 : 0.f, a1 = valid ? de1 : 0.f;
+                    if (in_range) {
+                        de_out[(uint64_t)(2 * l) * de_ld + t] = a0;
+                        de_out[(uint64_t)(2 * l + 1) * de_ld + t] = a1;
+                    }
+                    const unsigned mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(a0), fabsf(a1))));
+                    if ((threadIdx.x & 31) == 0) atomicMax(lvl_max + l, mx);
+                    continue;
+                }
                 uint32_t idx[8];
                 float w[8];
                 grid_corners(g.level[l], g.mask, p, idx, w);
                 float* gt = grad_table + (uint64_t)l * T * 2;
+                if (g.level[l].dense) {
+                    // coarse levels: few cells, many samples per cell
 #pragma unroll
-                for (int c = 0; c < 8; ++c) scatter_pair(gt, idx[c], valid, w[c] * de0, w[c] * de1);
+                    for (int c = 0; c < 8; ++c) scatter_pair(gt, idx[c], valid, w[c] * de0, w[c] * de1);
+                } else if (valid) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        atomicAdd(reinterpret_cast<float2*>(gt + 2 * (uint64_t)idx[c]),
+                                  make_float2(w[c] * de0, w[c] * de1));
+                }
             }
         }
+    }
+}
+
+// Deterministic hash-table gradient: acc[l][idx][f] += w * dL/de[l][f] *
+// scale_l as 64-bit integers.
+__global__ void __launch_bounds__(256)
+    k_hash_scatter_fixed(GridParams g, const nirc_record* __restrict__ recs, uint64_t n,
+                         const float* __restrict__ de, const unsigned* __restrict__ lvl_max,
+                         unsigned long long* __restrict__ acc) {
+    const uint64_t T = (uint64_t)g.mask + 1;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        const float4 r0 = __ldg(reinterpret_cast<const float4*>(recs + t));
+        const V3 p{r0.x, r0.y, r0.z};
+        for (uint32_t l = 0; l < g.n_levels; ++l) {
+            const float de0 = de[(uint64_t)(2 * l) * n + t], de1 = de[(uint64_t)(2 * l + 1) * n + t];
+            if (de0 == 0.f && de1 == 0.f) continue;
+            const float sc = fixed_scale(__uint_as_float(lvl_max[l]), n);
+            uint32_t idx[8];
+            float w[8];
+            grid_corners(g.level[l], g.mask, p, idx, w);
+            unsigned long long* a = acc + (uint64_t)l * T * 2;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const long long v0 = __float2ll_rn(w[c] * de0 * sc), v1 = __float2ll_rn(w[c] * de1 * sc);
+                if (v0) atomicAdd(a + 2 * (uint64_t)idx[c], (unsigned long long)v0);
+                if (v1) atomicAdd(a + 2 * (uint64_t)idx[c] + 1, (unsigned long long)v1);
+            }
+        }
+    }
+}
+
+__global__ void k_hash_fixed_to_float(GridParams g, uint64_t n, const unsigned* __restrict__ lvl_max,
+                                      const unsigned long long* __restrict__ acc, float* __restrict__ grad_table) {
+    const uint64_t per_level = ((uint64_t)g.mask + 1) * 2;
+    const uint64_t total = per_level * g.n_levels;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t l = (uint32_t)(i / per_level);
+        const float inv = 1.f / fixed_scale(__uint_as_float(lvl_max[l]), n);  // power of two: exact
+        grad_table[i] = __ll2float_rn((long long)acc[i]) * inv;
+    }
+}
+
+// dst[j] (+)= sum_r src[r * cols + j] over r = 0..rows-1 in order.
+__global__ void k_sum_rows(const float* __restrict__ src, uint64_t rows, uint64_t cols, float* __restrict__ dst,
+                           int accumulate) {
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += (uint64_t)gridDim.x * blockDim.x) {
+        float v = accumulate ? dst[j] : 0.f;
+        for (uint64_t r = 0; r < rows; ++r) v += src[r * cols + j];
+        dst[j] = v;
     }
 }
 
@@ -293,8 +433,12 @@ struct GradJob {
 };
 struct GradJobs {
     GradJob j[kMaxHidden + 1];
+    float* part;     // deterministic mode: block b writes W/b of job l at
+    uint64_t pstride;//   part + b * pstride + (gw - grad); else atomics into gw
+    const float* grad_base;
 };
 
+template <bool kPartial>
 __global__ void __launch_bounds__(kGradThreads) k_grad_w(GradJobs jobs, uint64_t n) {
     const GradJob J = jobs.j[blockIdx.y];
     __shared__ __align__(16) float ds[kGradChunk][64 + 4];
@@ -338,7 +482,8 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_w(GradJobs jobs, uint64_t
             const int o = 4 * ot + a, i = 4 * it + b;
             if (o < (int)J.out && i <= (int)J.in) {
                 float* dst = i < (int)J.in ? J.gw + (uint64_t)o * J.in + i : J.gw + (uint64_t)J.out * J.in + o;
-                atomicAdd(dst, acc[a][b]);
+                if constexpr (kPartial) jobs.part[blockIdx.x * jobs.pstride + (uint64_t)(dst - jobs.grad_base)] = acc[a][b];
+                else atomicAdd(dst, acc[a][b]);
             }
         }
 }
@@ -378,9 +523,17 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     const uint64_t chunk = chunk_of(h, n);
     const bool store = chunk == n;
     TrainPtrs tp = carve(h->train_scratch, s, n, chunk);
+    const bool det = h->deterministic != 0;
+    const bool det_hash = det && s.hashgrid;
+    DetPtrs dp{};
+    if (det) dp = carve_det(h, h->train_scratch, n, chunk);
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->grad, 0, s.n_dev * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
+    if (det_hash) {
+        if ((e = cudaMemsetAsync(dp.lvl_max, 0, 64 * sizeof(unsigned), st)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(dp.acc, 0, s.n_hash * sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    }
     const size_t smem_f = (size_t)s.packed_floats * 4 + (size_t)kTrainThreads * kWidth * 4;
     const size_t smem_b = (size_t)s.packed_floats * 4;
     if ((e = cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f)) != cudaSuccess)
@@ -395,11 +548,17 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     };
     // full-batch forward: loss and dL/dz, activations only when stored
     timer_begin(h, NIRC_K_TRAIN_FWD, st);
-    k_train_fwd<<<blocks_for(n), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
-                                                             h->packed, table, recs, dirs, targets, n, tp,
-                                                             store ? 1 : 0, kind, h->loss_accum);
+    const uint32_t fwd_blocks = blocks_for(n);
+    k_train_fwd<<<fwd_blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
+                                                          h->packed, table, recs, dirs, targets, n, tp,
+                                                          store ? 1 : 0, kind, h->loss_accum,
+                                                          det ? dp.loss_part : nullptr);
     timer_end(h, NIRC_K_TRAIN_FWD, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (det) {
+        k_sum_rows<<<1, 32, 0, st>>>(dp.loss_part, fwd_blocks, 1, h->loss_accum, 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     for (uint64_t c0 = 0; c0 < n; c0 += chunk) {
         const uint64_t m = n - c0 < chunk ? n - c0 : chunk;
         TrainPtrs tc = tp;
@@ -409,13 +568,14 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             k_train_fwd<<<blocks_for(m), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps,
                                                                      scale, h->packed, table, recs + c0,
                                                                      dirs + 3 * c0, targets + 3 * c0, m, tc, 1,
-                                                                     kLossNone, nullptr);
+                                                                     kLossNone, nullptr, nullptr);
             timer_end(h, NIRC_K_TRAIN_FWD, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         timer_begin(h, NIRC_K_TRAIN_BWD, st);
         k_train_bwd<<<blocks_for(m), kTrainThreads, smem_b, st>>>(s, h->grid, h->packed, recs + c0, m, tc,
-                                                                 kind == kLossUpstream ? 1 : 0, h->grad + s.hash_off);
+                                                                 kind == kLossUpstream ? 1 : 0, h->grad + s.hash_off,
+                                                                 det_hash ? dp.de + c0 : nullptr, n, dp.lvl_max);
         timer_end(h, NIRC_K_TRAIN_BWD, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
@@ -433,13 +593,30 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             J.gw = h->grad + off;
             off += (uint64_t)J.out * J.in + J.out;
         }
+        jobs.part = det ? dp.gw_part : nullptr;
+        jobs.pstride = s.n_mlp;
+        jobs.grad_base = h->grad;
         const uint64_t n_chunks = (m + kGradChunk - 1) / kGradChunk;
         uint64_t gx = (2ull * h->num_sms + s.hidden) / (s.hidden + 1);
         if (gx > n_chunks) gx = n_chunks;
         if (gx < 1) gx = 1;
         timer_begin(h, NIRC_K_TRAIN_GRADW, st);
-        k_grad_w<<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+        if (det) k_grad_w<true><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+        else k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+        if (det && (e = cudaGetLastError()) == cudaSuccess) {
+            // chunks add their block partials into grad in chunk order
+            k_sum_rows<<<(uint32_t)((s.n_mlp + 255) / 256), 256, 0, st>>>(dp.gw_part, gx, s.n_mlp, h->grad, 1);
+        }
         timer_end(h, NIRC_K_TRAIN_GRADW, st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (det_hash) {
+        timer_begin(h, NIRC_K_TRAIN_BWD, st);
+        k_hash_scatter_fixed<<<4 * h->num_sms, 256, 0, st>>>(h->grid, recs, n, dp.de, dp.lvl_max, dp.acc);
+        if ((e = cudaGetLastError()) == cudaSuccess)
+            k_hash_fixed_to_float<<<4 * h->num_sms, 256, 0, st>>>(h->grid, n, dp.lvl_max, dp.acc,
+                                                                  h->grad + s.hash_off);
+        timer_end(h, NIRC_K_TRAIN_BWD, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -64,6 +64,30 @@ class nirc_timing(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8)]
 
 
+class nirc_server_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32), ("max_batches", ctypes.c_uint32),
+                ("train_samples", ctypes.c_uint32), ("use_graphs", ctypes.c_uint32)]
+
+
+class nirc_request(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("scene", ctypes.c_uint32), ("width", ctypes.c_uint32),
+                ("height", ctypes.c_uint32), ("n_cache", ctypes.c_uint32), ("n_resid", ctypes.c_uint32),
+                ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
+class nirc_completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_uint32),
+                ("d_image", ctypes.c_void_p), ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class nirc_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "batches",
+                                                 "graph_instantiations", "graph_updates", "arena_bytes",
+                                                 "arena_peak_bytes", "resident_bytes")] + \
+               [(n, ctypes.c_uint32) for n in ("queued", "in_flight", "max_batch_seen", "pad")]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run paper_2412_04634_gb300.build.build()")
@@ -77,6 +101,7 @@ def _load():
         "nirc_set_params": ([P, P, i32, P], st),
         "nirc_load_params": ([P, P, i32, P], st),
         "nirc_set_train_mode": ([P, i32, u64], st),
+        "nirc_set_deterministic": ([P, i32], st),
         "nirc_query_bwd": ([P, P, P, P, u64, P, P, P], st),
         "nirc_get_params": ([P, P, i32, P], st),
         "nirc_get_grads": ([P, P, i32, P], st),
@@ -91,6 +116,16 @@ def _load():
         "nirc_timing_enable": ([P, i32], st),
         "nirc_timing_read": ([P, P], st),
         "nirc_last_error": ([], ctypes.c_char_p),
+        "nirc_server_create": ([P, P], st),
+        "nirc_server_add_scene": ([P, P, P, u32, u64, u32, u64, P], st),
+        "nirc_server_submit": ([P, P], st),
+        "nirc_server_poll": ([P, P, u32, P, i32], st),
+        "nirc_server_release": ([P, u64], st),
+        "nirc_server_copy_image": ([P, u64, P, P], st),
+        "nirc_server_drain": ([P], st),
+        "nirc_server_stats_read": ([P, P], st),
+        "nirc_server_clock": ([P], ctypes.c_double),
+        "nirc_server_destroy": ([P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -174,6 +209,10 @@ def nirc_load_params(h, params: torch.Tensor, stream=None):
 
 def nirc_set_train_mode(h, store_activations: bool = True, recompute_chunk: int = 1 << 15):
     _check(_lib.nirc_set_train_mode(h, 1 if store_activations else 0, recompute_chunk))
+
+
+def nirc_set_deterministic(h, on: bool = True):
+    _check(_lib.nirc_set_deterministic(h, 1 if on else 0))
 
 
 def nirc_query_bwd(h, records: torch.Tensor, dirs: torch.Tensor, grad_out: torch.Tensor,
@@ -337,3 +376,115 @@ class NircQuery(torch.autograd.Function):
         g = torch.empty(cache.n_params, device=dirs.device, dtype=torch.float32)
         nirc_query_bwd(cache.h, records, dirs, grad_out.contiguous().float(), g)
         return g, None, None, None
+
+
+# --- frame-request server (include/nirc_serve.h) -------------------------------
+
+def nirc_server_create(cfg: nirc_server_config):
+    h = ctypes.c_void_p()
+    _check(_lib.nirc_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def nirc_server_add_scene(srv, cache_h, frames: torch.Tensor, n_frames: int, frame_stride: int, n_prims: int,
+                          seed: int) -> int:
+    idx = ctypes.c_uint32()
+    _check(_lib.nirc_server_add_scene(srv, cache_h, _ptr(frames), n_frames, frame_stride, n_prims, seed,
+                                      ctypes.byref(idx)))
+    return idx.value
+
+
+def nirc_server_submit(srv, req: nirc_request):
+    _check(_lib.nirc_server_submit(srv, ctypes.byref(req)))
+
+
+def nirc_server_poll(srv, max_n: int = 64, wait: bool = False):
+    buf = (nirc_completion * max(1, max_n))()
+    n = ctypes.c_uint32()
+    _check(_lib.nirc_server_poll(srv, buf, max_n, ctypes.byref(n), 1 if wait else 0))
+    return [buf[i] for i in range(n.value)]
+
+
+def nirc_server_copy_image(srv, rid: int, out: torch.Tensor, stream=None):
+    _check(_lib.nirc_server_copy_image(srv, rid, _ptr(out), _stream(stream)))
+
+
+def nirc_server_release(srv, rid: int):
+    _check(_lib.nirc_server_release(srv, rid))
+
+
+def nirc_server_drain(srv):
+    _check(_lib.nirc_server_drain(srv))
+
+
+def nirc_server_stats_read(srv) -> dict:
+    st = nirc_server_stats()
+    _check(_lib.nirc_server_stats_read(srv, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in nirc_server_stats._fields_ if n != "pad"}
+
+
+def nirc_server_clock(srv) -> float:
+    return float(_lib.nirc_server_clock(srv))
+
+
+def nirc_server_destroy(srv):
+    _check(_lib.nirc_server_destroy(srv))
+
+
+class Server:
+    """Owning wrapper of a nirc_server.  Scenes are (Cache, list of
+    scenes.Scene key frames, seed); their blobs are uploaded into one device
+    tensor per scene that the server reads for the scene's lifetime."""
+
+    def __init__(self, budget_bytes: int, slots: int = 8, max_batches: int = 2, train_samples: int = 65536,
+                 use_graphs: bool = True):
+        self.h = nirc_server_create(nirc_server_config(budget_bytes, slots, max_batches, train_samples,
+                                                       1 if use_graphs else 0))
+        self._keep = []
+
+    def add_scene(self, cache: "Cache", frames, seed: int) -> int:
+        import numpy as np
+        blobs = [f.blob() for f in frames]
+        stride = (max(b.nbytes for b in blobs) + 15) // 16 * 16
+        buf = np.zeros(stride * len(blobs), np.uint8)
+        for k, b in enumerate(blobs):
+            buf[k * stride:k * stride + b.nbytes] = b
+        dev = torch.from_numpy(buf).cuda()
+        self._keep.append((cache, dev))
+        return nirc_server_add_scene(self.h, cache.h, dev, len(blobs), stride, frames[0].n_prims, seed)
+
+    def submit(self, rid, scene, width, height, n_cache, n_resid, max_depth, frame):
+        nirc_server_submit(self.h, nirc_request(rid, scene, width, height, n_cache, n_resid, max_depth, frame, 0))
+
+    def poll(self, wait=False, max_n=64):
+        return nirc_server_poll(self.h, max_n, wait)
+
+    def image(self, c: nirc_completion, width: int, height: int) -> torch.Tensor:
+        """Copy a completed request's image (W*H x 4) into a new CUDA tensor."""
+        out = torch.empty((width * height, 4), device="cuda")
+        nirc_server_copy_image(self.h, c.id, out)
+        return out
+
+    def release(self, rid):
+        nirc_server_release(self.h, rid)
+
+    def drain(self):
+        nirc_server_drain(self.h)
+
+    def stats(self):
+        return nirc_server_stats_read(self.h)
+
+    def clock(self):
+        return nirc_server_clock(self.h)
+
+    def close(self):
+        if self.h is not None:
+            nirc_server_destroy(self.h)
+            self.h = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

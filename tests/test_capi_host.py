@@ -62,11 +62,27 @@ def test_bad_arguments_return_status(N):
     assert N.lib().nirc_query_bwd(None, None, None, None, 5, None, None, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_load_params(None, None, 0, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_set_train_mode(None, 1, 0) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_server_create(None, None) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_server_submit(None, None) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_server_poll(None, None, 0, None, 0) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_server_destroy(None) == N.NIRC_OK
     assert N.lib().nirc_destroy(None) == N.NIRC_OK
     assert N.nirc_param_count(N.make_config(scenes.NetConfig(width=48))) == 0
 
 
+def test_server_config_rejected_without_device(N):
+    """Bad server configurations are refused before any device call."""
+    h = ctypes.c_void_p()
+    for cfg in (N.nirc_server_config(1 << 10, 4, 1, 0, 1), N.nirc_server_config(1 << 30, 0, 1, 0, 1),
+                N.nirc_server_config(1 << 30, 17, 1, 0, 1), N.nirc_server_config(1 << 30, 4, 5, 0, 1)):
+        assert N.lib().nirc_server_create(ctypes.byref(cfg), ctypes.byref(h)) == N.NIRC_ERR_INVALID
+        assert b"slots" in N.lib().nirc_last_error()
+
+
 def test_struct_layouts(N):
+    assert ctypes.sizeof(N.nirc_request) == 40
+    assert ctypes.sizeof(N.nirc_completion) == 48
+    assert ctypes.sizeof(N.nirc_server_config) == 24
     assert ctypes.sizeof(N.nirc_frame_desc) == 56
     assert scenes.RECORD_DTYPE.itemsize == 64
     assert scenes.PRIM_DTYPE.itemsize == 96 and scenes.HEADER_DTYPE.itemsize == 96

@@ -181,7 +181,9 @@ def test_scatter_with_colliding_entries(N, oracle):
     """Many rows share a few positions, so whole warps hit the same table
     entries: the aggregated scatter must still add every contribution."""
     import torch
-    cfg = _hash_cfg(levels=6, log2_table=10, hidden=2)
+    # 2^14 entries: levels 0-1 (16^3, 24^3 cells) are dense and take the
+    # warp-aggregated path, levels 2-5 are hashed
+    cfg = _hash_cfg(levels=6, log2_table=14, hidden=2)
     params = scenes.init_params(cfg, 71)
     n = 4096
     recs, dirs, tg = scenes.training_batch(n, seed=72)
@@ -202,4 +204,65 @@ def test_scatter_with_colliding_entries(N, oracle):
     touched = np.nonzero(g_or[cfg.n_mlp_params:])[0]
     assert 0 < touched.size <= 5 * 8 * 6 * 2
     _assert_grad_close(cfg, g_gpu, g_or)
+    cache.close()
+
+
+@pytest.mark.parametrize("store", [True, False])
+def test_deterministic_training_is_bit_reproducible(N, oracle, store):
+    """Deterministic mode: two handles given the same state and batch take
+    bit-identical training steps (loss, gradient, weights), and the
+    gradient still matches the oracle within the FP32 tolerance."""
+    import torch
+    cfg = _hash_cfg()
+    params = scenes.init_params(cfg, 81)
+    n = 5000
+    recs, dirs, tg = scenes.training_batch(n, seed=82)
+    recs["flags"][::11] = 0
+    recs["flags"][_near_kink(oracle, cfg, params, recs, dirs)] = 0
+    rt = N.records_to_tensor(recs)
+    dt = torch.from_numpy(dirs).cuda()
+    tt = torch.from_numpy(tg).cuda()
+    runs = []
+    for _ in range(2):
+        cache = N.Cache(cfg)
+        cache.set_params(params)
+        N.nirc_set_deterministic(cache.h, True)
+        N.nirc_set_train_mode(cache.h, store, 1024)
+        losses = []
+        for _ in range(2):
+            loss = torch.zeros(1, device="cuda")
+            N.nirc_train_step(cache.h, rt, dt, tt, loss)
+            losses.append(loss.item())
+            if not runs and len(losses) == 1:
+                g_first = cache.get_grads().numpy().astype(np.float64)
+        torch.cuda.synchronize()
+        runs.append((losses, cache.get_grads().numpy(), cache.get_params().numpy()))
+        cache.close()
+    (l0, g0, p0), (l1, g1, p1) = runs
+    assert l0 == l1
+    assert np.array_equal(g0, g1) and np.array_equal(p0, p1)
+    _, g_or = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    _assert_grad_close(cfg, g_first, g_or)
+
+
+def test_deterministic_query_bwd(N, oracle):
+    import torch
+    cfg = _hash_cfg()
+    params = scenes.init_params(cfg, 91)
+    n = 3000
+    recs, dirs = scenes.random_query_rows(n, seed=92)
+    gout = np.random.default_rng(93).normal(0, 1, (n, 3)).astype(np.float32)
+    gout[_near_kink(oracle, cfg, params, recs, dirs)] = 0.0
+    cache = N.Cache(cfg)
+    cache.set_params(params)
+    N.nirc_set_deterministic(cache.h, True)
+    rt, dt, gt = N.records_to_tensor(recs), torch.from_numpy(dirs).cuda(), torch.from_numpy(gout).cuda()
+    g1 = torch.empty(cfg.n_params, device="cuda")
+    g2 = torch.empty(cfg.n_params, device="cuda")
+    N.nirc_query_bwd(cache.h, rt, dt, gt, g1)
+    N.nirc_query_bwd(cache.h, rt, dt, gt, g2)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    _, g_or = oracle.query_grad(cfg, params, recs, dirs, gout.astype(np.float64))
+    _assert_grad_close(cfg, g1.cpu().numpy().astype(np.float64), g_or)
     cache.close()
