@@ -49,7 +49,12 @@ typedef enum nirc_status {
 
 /* Arithmetic of the network layers.  FP32_SIMT: plain FP32 FMA kernels.
  * FP16_TC / BF16_TC: tcgen05 tensor-core MMAs with FP16 / BF16 operands and
- * FP32 accumulation in tensor memory.  Encodings, sampling, pdfs and the
+ * FP32 accumulation in tensor memory.  FP8_E4M3_TC: the hidden 64x64 layers
+ * take E4M3 operands (kind::f8f6f4) with per-layer scales, weights scaled
+ * by amax|W| / 448 and activations by the amax of the previous launch / 448
+ * (delayed scaling; the first launch after new weights or a precision change
+ * runs one extra FP16 pass to measure it), FP32 accumulation; the first
+ * layer and the output layer stay FP16.  Encodings, sampling, pdfs and the
  * per-pixel sums are FP32 in every mode. */
 typedef enum nirc_precision {
     NIRC_FP32_SIMT = 0,
@@ -176,7 +181,7 @@ nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stre
  * tensor-core modes apply to the cache integral of nirc_estimate_frame when
  * the network is used (cache_mode 0) and N + M >= 4; other work (queries,
  * training, the other cache modes) runs the FP32 kernels.  Synchronises the
- * legacy default stream.  FP8_E4M3_TC returns NIRC_ERR_UNSUPPORTED. */
+ * legacy default stream. */
 nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision);
 
 /* Wait for `stream` and report device-side failures of the handle's

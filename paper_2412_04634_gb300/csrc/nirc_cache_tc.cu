@@ -28,6 +28,16 @@
 //                carrying a pixel that straddles two tiles, and writes the
 //                pixel (eq. L_mlmc = L_e + L_c + L_r).
 //
+// FP8 (E4M3) mode: the hidden 64x64 layers run as kind::f8f6f4 MMAs (K = 32,
+// two per layer) on E4M3 weights and activations with per-layer scales:
+// weights W / s_w with s_w = amax|W| / 448 (taken when the weights are
+// packed), activations a / s_a with s_a = amax(a) / 448 from the previous
+// launch (delayed scaling: every FP8 launch records the amax of each hidden
+// layer's input, which the next launch uses); the accumulator is multiplied
+// back by s_w s_a in the epilogue.  Layer 0 (with the per-pixel product) and
+// the output layer stay FP16.  The first FP8 launch after new weights is
+// preceded by one FP16 launch that only records the activation amax.
+//
 // Every mbarrier wait is bounded (about 2 s); a timeout sets *err, stops
 // further MMAs of that warpgroup and the kernel still frees its TMEM.
 #include "nirc_internal.h"
@@ -43,10 +53,46 @@ __host__ __device__ inline uint32_t off_wh(uint32_t l) { return 16384 + 8192 * l
 __host__ __device__ inline uint32_t off_wout(uint32_t hidden) { return 16384 + 8192 * (hidden - 1); }
 __host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_wout(hidden) + 2048; }
 __host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidden - 1) * 64 + 16; }
+// FP8 weight scales s_w of the hidden layers (16 floats)
+__host__ __device__ inline uint32_t off_scales(uint32_t hidden) { return off_bias(hidden) + n_bias(hidden) * 4; }
 }  // namespace tcimg
 
-size_t tc_image_bytes(uint32_t hidden) { return tcimg::off_bias(hidden) + tcimg::n_bias(hidden) * 4; }
+size_t tc_image_bytes(uint32_t hidden) { return tcimg::off_scales(hidden) + 64; }
 
+constexpr float kE4M3Max = 448.f;
+
+__device__ __forceinline__ uint8_t to_e4m3(float v) { return (uint8_t)(tc::pack_e4m3x4(v, 0.f, 0.f, 0.f) & 0xFFu); }
+
+// s_w of each hidden layer (one block per layer): amax |W| / 448, 1 for an all-zero layer.
+__global__ void k_weight_scales(NetShape s, const float* __restrict__ params, uint8_t* __restrict__ img) {
+    __shared__ float red[256];
+    const uint32_t l = blockIdx.x;  // hidden slot: layer l + 1
+    const uint64_t b = 64ull * s.n_in + 64 + (uint64_t)l * (64 * 64 + 64);
+    float m = 0.f;
+    for (uint32_t i = threadIdx.x; i < 64 * 64; i += blockDim.x) m = fmaxf(m, fabsf(params[b + i]));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (uint32_t o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        reinterpret_cast<float*>(img + tcimg::off_scales(s.hidden))[l] = red[0] > 0.f ? red[0] / kE4M3Max : 1.f;
+}
+
+// Delayed activation scaling: the amax recorded by the last launch becomes
+// the history the next launch scales with.  buf[0..8) history (float),
+// buf[8..16) current (float bits, atomicMax).
+__global__ void k_amax_roll(uint32_t* buf, uint32_t n) {
+    const uint32_t j = threadIdx.x;
+    if (j < n) {
+        const uint32_t cur = buf[8 + j];
+        if (cur) buf[j] = cur;
+        buf[8 + j] = 0u;
+    }
+}
+
+constexpr uint32_t kMiscBytes = 256;     // mbarriers, TMEM holder, abort flags, FP8 scales and amax
 constexpr uint32_t kWgStride = 35840;  // A 16 KB | H 16 KB | contributions 2 KB | 2 carry slots 128 B (1 KB rounded)
 constexpr uint32_t kOffA = 0, kOffH = 16384, kOffContrib = 32768, kOffCarry = 34816;
 
@@ -81,7 +127,12 @@ __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_
             const uint64_t b = 64 * n_in + 64 + (uint64_t)(H - 1) * (64 * 64 + 64);
             if (n < 3) v = params[b + n * 64 + k];
         }
-        const uint16_t bits = AB ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+        if (AB == 2 && m >= 2 && m < 2 + (H - 1)) {  // FP8 hidden layer, scaled by s_w
+            const float sw = reinterpret_cast<const float*>(img + tcimg::off_scales(H))[m - 2];
+            img[off + tc::sw128_offset_b8(n, k)] = to_e4m3(v / sw);
+            return;
+        }
+        const uint16_t bits = AB == 1 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
         *reinterpret_cast<uint16_t*>(img + off + tc::sw128_offset(n, k)) = bits;
         return;
     }
@@ -134,11 +185,16 @@ __device__ __forceinline__ void sts_chunk8(uint32_t tile, uint32_t r, uint32_t c
     sts_chunk(tile, r, c, pack2<AB>(y[0], y[1]), pack2<AB>(y[2], y[3]), pack2<AB>(y[4], y[5]), pack2<AB>(y[6], y[7]));
 }
 
-// Epilogue of one hidden layer for row r: 64 accumulators from TMEM (two
-// halves of 32 columns), + bias (none for layer 0, whose h_pix holds b0),
-// ReLU, rounding to 16 bits, swizzled store into the next A tile.
-template <uint32_t AB>
-__device__ __forceinline__ void epilogue_row(uint32_t taddr, const float* __restrict__ bias, uint32_t tile, uint32_t r) {
+// Epilogue of one layer for row r: 64 accumulators from TMEM (two halves of
+// 32 columns), times `mul` (kMul: the FP8 scales s_w s_a of the layer),
+// + bias (none for layer 0, whose h_pix holds b0), ReLU, then either 16-bit
+// rounding into the next A tile (chunks 0-7) or, kF8Out, scaling by 1/s_a of
+// the next layer and E4M3 rounding (chunks 0-3).  kRec: the warp's amax of
+// the ReLU outputs goes into the shared word at s_amax (atomicMax on bits).
+template <uint32_t AB16, bool kF8Out, bool kMul, bool kRec>
+__device__ __forceinline__ void epilogue(uint32_t taddr, const float* __restrict__ bias, float mul, float inv_sa,
+                                         uint32_t tile, uint32_t r, uint32_t* s_amax) {
+    float mx = 0.f;
 #pragma unroll
     for (uint32_t half = 0; half < 2; ++half) {
         uint32_t v[32];
@@ -149,21 +205,46 @@ __device__ __forceinline__ void epilogue_row(uint32_t taddr, const float* __rest
             const float2* b2 = reinterpret_cast<const float2*>(bias + 32u * half);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const float2 y =
-                    __fadd2_rn(make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), b2[i]);
+                const float2 acc = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+                const float2 y = kMul ? __ffma2_rn(acc, make_float2(mul, mul), b2[i]) : __fadd2_rn(acc, b2[i]);
                 x[2 * i] = y.x;
                 x[2 * i + 1] = y.y;
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = __uint_as_float(v[i]);
+            for (int i = 0; i < 32; ++i) x[i] = kMul ? __uint_as_float(v[i]) * mul : __uint_as_float(v[i]);
         }
+        if constexpr (kRec || kF8Out) {
 #pragma unroll
-        for (uint32_t q = 0; q < 4; ++q) {
-            const float* y = x + 8 * q;
-            sts_chunk(tile, r, 4u * half + q, pack2_relu<AB>(y[0], y[1]), pack2_relu<AB>(y[2], y[3]),
-                      pack2_relu<AB>(y[4], y[5]), pack2_relu<AB>(y[6], y[7]));
+            for (int i = 0; i < 32; ++i) x[i] = fmaxf(x[i], 0.f);
         }
+        if constexpr (kRec) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) mx = fmaxf(mx, x[i]);
+        }
+        if constexpr (kF8Out) {
+#pragma unroll
+            for (uint32_t q = 0; q < 2; ++q) {
+                const float* y = x + 16 * q;
+                uint32_t d[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    d[j] = tc::pack_e4m3x4(y[4 * j] * inv_sa, y[4 * j + 1] * inv_sa, y[4 * j + 2] * inv_sa,
+                                           y[4 * j + 3] * inv_sa);
+                sts_chunk(tile, r, 2u * half + q, d[0], d[1], d[2], d[3]);
+            }
+        } else {
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                const float* y = x + 8 * q;
+                sts_chunk(tile, r, 4u * half + q, pack2_relu<AB16>(y[0], y[1]), pack2_relu<AB16>(y[2], y[3]),
+                          pack2_relu<AB16>(y[4], y[5]), pack2_relu<AB16>(y[6], y[7]));
+            }
+        }
+    }
+    if constexpr (kRec) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+        if ((threadIdx.x & 31u) == 0) atomicMax(s_amax, m);
     }
 }
 
@@ -208,13 +289,17 @@ __device__ __forceinline__ void dir_features_fast(V3 w, float* e) {
     octaves(sp, cp, e + 8);
 }
 
-template <uint32_t AB>
+// AB: 0 FP16, 1 BF16, 2 FP8 hidden layers (FP16 elsewhere).  kAmax: record
+// the amax of every hidden layer's input activations into amax[8 + l].
+template <uint32_t AB, bool kAmax>
 __global__ void __launch_bounds__(640, 1)
     k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
                const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
                const ResidRow* __restrict__ rows, float4* __restrict__ out, float* __restrict__ lc_out,
                float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
-               float* __restrict__ row_n, int* __restrict__ err) {
+               float* __restrict__ row_n, int* __restrict__ err, uint32_t* __restrict__ amax) {
+    constexpr uint32_t AB16 = AB == 1 ? 1u : 0u;  // type of the 16-bit layers
+    constexpr bool kF8 = AB == 2;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -231,6 +316,10 @@ __global__ void __launch_bounds__(640, 1)
     volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(miscg + 80 + 4 * wg);
     const uint32_t tmem_cols = n_wg <= 1 ? 64u : (n_wg <= 2 ? 128u : (n_wg <= 4 ? 256u : 512u));
 
+    uint32_t* s_amax = reinterpret_cast<uint32_t*>(miscg + 128);  // [8]
+    float* s_mul = reinterpret_cast<float*>(miscg + 160);         // [8] s_w s_a per hidden slot
+    float* s_inv = reinterpret_cast<float*>(miscg + 192);         // [8] 1 / s_a per hidden slot
+
     // stage the weight image
     {
         const float4* src = reinterpret_cast<const float4*>(img_g);
@@ -244,6 +333,19 @@ __global__ void __launch_bounds__(640, 1)
             *reinterpret_cast<volatile uint32_t*>(miscg + 80 + 4 * w) = 0u;
         }
         tc::fence_mbar_init();
+        for (uint32_t j = 0; j < 8; ++j) {
+            s_amax[j] = 0u;
+            float sa = 1.f;
+            if (kF8 && j + 1 < a.s.hidden) {
+                const float h = __uint_as_float(amax[j]);
+                sa = h > 0.f ? h / kE4M3Max : 1.f;
+            }
+            const float sw = kF8 && j + 1 < a.s.hidden
+                                 ? reinterpret_cast<const float*>(img_g + tcimg::off_scales(a.s.hidden))[j]
+                                 : 1.f;
+            s_mul[j] = sw * sa;
+            s_inv[j] = 1.f / sa;
+        }
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
@@ -260,8 +362,9 @@ __global__ void __launch_bounds__(640, 1)
     const uint32_t tA = wgs + kOffA, tH = wgs + kOffH;
     float4* s_contrib = reinterpret_cast<float4*>(wgg + kOffContrib);
     float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);  // two slots of 16 floats
-    const uint32_t id64 = tc::idesc_f16(AB, 128, 64), id16 = tc::idesc_f16(AB, 128, 16);
-    const uint16_t one16 = AB ? 0x3F80u : 0x3C00u;
+    const uint32_t id64 = tc::idesc_f16(AB16, 128, 64), id16 = tc::idesc_f16(AB16, 128, 16);
+    const uint32_t id64_e4m3 = tc::idesc_f16(0, 128, 64);  // E4M3 x E4M3 has type code 0 too
+    const uint16_t one16 = AB16 ? 0x3F80u : 0x3C00u;
 
     auto sync_wg = [&]() {
         tc::fence_proxy_async();
@@ -283,6 +386,15 @@ __global__ void __launch_bounds__(640, 1)
             tc::fence_after_sync();
 #pragma unroll
             for (uint32_t s = 0; s < 4; ++s) tc::mma_f16(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), idesc, s);
+            tc::mma_commit(mbar);
+        }
+    };
+    auto issue_k64_e4m3 = [&](uint32_t a_tile, uint32_t b_tile) {
+        if (t == 0 && !*abort_flag) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (uint32_t s = 0; s < 2; ++s)
+                tc::mma_e4m3(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), id64_e4m3, s);
             tc::mma_commit(mbar);
         }
     };
@@ -322,22 +434,22 @@ __global__ void __launch_bounds__(640, 1)
                         f[2 * q] = f0;
                         f[2 * q + 1] = f1;
                     }
-                    sts_chunk8<AB>(tA, t, c, f);
+                    sts_chunk8<AB16>(tA, t, c, f);
                 }
             } else {
                 freq4(p.x, f);
-                sts_chunk8<AB>(tA, t, c++, f);
+                sts_chunk8<AB16>(tA, t, c++, f);
                 freq4(p.y, f);
-                sts_chunk8<AB>(tA, t, c++, f);
+                sts_chunk8<AB16>(tA, t, c++, f);
                 freq4(p.z, f);
-                sts_chunk8<AB>(tA, t, c++, f);
+                sts_chunk8<AB16>(tA, t, c++, f);
             }
             freq4(n.x, f);
-            sts_chunk8<AB>(tA, t, c++, f);
+            sts_chunk8<AB16>(tA, t, c++, f);
             freq4(n.y, f);
-            sts_chunk8<AB>(tA, t, c++, f);
+            sts_chunk8<AB16>(tA, t, c++, f);
             freq4(n.z, f);
-            sts_chunk8<AB>(tA, t, c++, f);
+            sts_chunk8<AB16>(tA, t, c++, f);
             for (; c < 8; ++c) sts_chunk(tA, t, c, 0u, 0u, 0u, 0u);
         }
         sync_wg();
@@ -354,7 +466,7 @@ __global__ void __launch_bounds__(640, 1)
 #pragma unroll
                 for (uint32_t o = 0; o < 32; ++o) {
                     const uint32_t oo = 32u * half + o;
-                    tc::sts16(hk + tc::sw128_offset(oo, t & 63u), to16<AB>(__uint_as_float(v[o]) + bias[oo]));
+                    tc::sts16(hk + tc::sw128_offset(oo, t & 63u), to16<AB16>(__uint_as_float(v[o]) + bias[oo]));
                 }
             }
         }
@@ -404,8 +516,8 @@ __global__ void __launch_bounds__(640, 1)
             {
                 float e[16];
                 dir_features_fast(wi, e);
-                sts_chunk8<AB>(tA, t, 0u, e);
-                sts_chunk8<AB>(tA, t, 1u, e + 8);
+                sts_chunk8<AB16>(tA, t, 0u, e);
+                sts_chunk8<AB16>(tA, t, 1u, e + 8);
                 const uint32_t oh = rin ? pl - kb : 0xFFFFu;  // one-hot position among columns 16..63
 #pragma unroll
                 for (uint32_t c = 2; c < 8; ++c) {
@@ -432,10 +544,22 @@ __global__ void __launch_bounds__(640, 1)
             wait_mma();
             for (uint32_t l = 0; l < a.s.hidden; ++l) {
                 // epilogue of layer l (l = 0: h_pix already holds b0), then the MMAs of layer l + 1
-                epilogue_row<AB>(tmem_row, l == 0 ? nullptr : bias + 64 + (l - 1) * 64, tA, t);
+                const float* bl = l == 0 ? nullptr : bias + 64 + (l - 1) * 64;
+                const bool next_hidden = l + 1 < a.s.hidden;
+                if constexpr (kF8) {
+                    const float mul = l == 0 ? 1.f : s_mul[l - 1];
+                    if (next_hidden) epilogue<0, true, true, true>(tmem_row, bl, mul, s_inv[l], tA, t, s_amax + l);
+                    else epilogue<0, false, true, false>(tmem_row, bl, mul, 1.f, tA, t, nullptr);
+                } else if constexpr (kAmax) {
+                    if (next_hidden) epilogue<AB16, false, false, true>(tmem_row, bl, 1.f, 1.f, tA, t, s_amax + l);
+                    else epilogue<AB16, false, false, false>(tmem_row, bl, 1.f, 1.f, tA, t, nullptr);
+                } else {
+                    epilogue<AB16, false, false, false>(tmem_row, bl, 1.f, 1.f, tA, t, nullptr);
+                }
                 sync_wg();
-                if (l + 1 < a.s.hidden) {
-                    issue_k64(tA, sbase + tcimg::off_wh(l), id64);
+                if (next_hidden) {
+                    if constexpr (kF8) issue_k64_e4m3(tA, sbase + tcimg::off_wh(l));
+                    else issue_k64(tA, sbase + tcimg::off_wh(l), id64);
                 } else {
                     issue_k64(tA, wout, id16);
                 }
@@ -570,27 +694,52 @@ __global__ void __launch_bounds__(640, 1)
         tc::fence_after_sync();
         tc::tmem_dealloc(*tmem_holder, tmem_cols);
     }
+    if constexpr (kAmax) {
+        if (threadIdx.x < a.s.hidden - 1) atomicMax(amax + 8 + threadIdx.x, s_amax[threadIdx.x]);
+    }
 }
 
 static size_t tc_smem_bytes(uint32_t img_bytes, uint32_t n_wg) {
-    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * kWgStride + 128;
+    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * kWgStride + kMiscBytes;
 }
 
 cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
     if (!h->packed_tc) return cudaSuccess;
     const uint32_t H = h->shape.hidden;
     const uint32_t n = 64 * 64 * (2 + (H - 1)) + 16 * 64 + tcimg::n_bias(H);
-    if (h->cfg.precision == NIRC_BF16_TC)
-        k_repack_tc<1><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, reinterpret_cast<uint8_t*>(h->packed_tc));
-    else
-        k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, reinterpret_cast<uint8_t*>(h->packed_tc));
+    uint8_t* img = reinterpret_cast<uint8_t*>(h->packed_tc);
+    if (h->cfg.precision == NIRC_BF16_TC) {
+        k_repack_tc<1><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+    } else if (h->cfg.precision == NIRC_FP8_E4M3_TC) {
+        if (H > 1) k_weight_scales<<<H - 1, 256, 0, st>>>(h->shape, h->params, img);
+        k_repack_tc<2><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        // FP16 image for the launch that calibrates the activation scales
+        k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params,
+                                                       reinterpret_cast<uint8_t*>(h->packed_tc16));
+    } else {
+        k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+    }
     return cudaGetLastError();
 }
 
 bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd) {
-    return (h->cfg.precision == NIRC_FP16_TC || h->cfg.precision == NIRC_BF16_TC) && fd.cache_mode == 0 &&
-           fd.n_cache + fd.n_resid >= 4 && h->packed_tc != nullptr &&
+    return (h->cfg.precision == NIRC_FP16_TC || h->cfg.precision == NIRC_BF16_TC ||
+            h->cfg.precision == NIRC_FP8_E4M3_TC) &&
+           fd.cache_mode == 0 && fd.n_cache + fd.n_resid >= 4 && h->packed_tc != nullptr &&
            (h->shape.n_pos == 24 || h->shape.n_pos == 32);
+}
+
+template <uint32_t AB, bool kAmax>
+static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
+                                      const void* img, const __half2* hash, const nirc_record* recs,
+                                      const PixelBase* base, const ResidRow* rows, float* out, float* lc, float* lr,
+                                      uint64_t* sig, uint32_t* count, float* row_n, int* err, uint32_t* amax) {
+    cudaError_t e = cudaFuncSetAttribute(k_cache_tc<AB, kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cache_tc<AB, kAmax><<<grid, threads, smem, st>>>(a, reinterpret_cast<const uint8_t*>(img), hash, recs, base, rows,
+                                                      reinterpret_cast<float4*>(out), lc, lr, sig, count, row_n, err,
+                                                      amax);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
@@ -619,21 +768,29 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     uint32_t grid = (a.n_blocks + n_wg - 1) / n_wg;
     if (grid > (uint32_t)h->num_sms) grid = h->num_sms;
     const __half2* hash = reinterpret_cast<const __half2*>(h->hash16);
-    cudaError_t e;
-    if (h->cfg.precision == NIRC_BF16_TC) {
-        e = cudaFuncSetAttribute(k_cache_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const uint32_t threads = n_wg * 128;
+    if (h->cfg.precision == NIRC_BF16_TC)
+        return launch_tc_instance<1, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, out_rgba,
+                                            lc, lr, sig, count, row_n, err, nullptr);
+    if (h->cfg.precision != NIRC_FP8_E4M3_TC)
+        return launch_tc_instance<0, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, out_rgba,
+                                            lc, lr, sig, count, row_n, err, nullptr);
+    cudaError_t e = cudaSuccess;
+    uint32_t* amax = h->fp8_amax;
+    const uint32_t n_slots = h->shape.hidden - 1;
+    if (!h->fp8_calibrated) {
+        // one FP16 launch records the activation amax (its image is overwritten below)
+        e = launch_tc_instance<0, true>(grid, threads, smem, st, a, h->packed_tc16, hash, recs, base, rows, out_rgba,
+                                        nullptr, nullptr, nullptr, nullptr, nullptr, err, amax);
+        if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
+        if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        k_cache_tc<1><<<grid, n_wg * 128, smem, st>>>(a, reinterpret_cast<const uint8_t*>(h->packed_tc), hash, recs,
-                                                      base, rows, reinterpret_cast<float4*>(out_rgba), lc, lr, sig,
-                                                      count, row_n, err);
-    } else {
-        e = cudaFuncSetAttribute(k_cache_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_cache_tc<0><<<grid, n_wg * 128, smem, st>>>(a, reinterpret_cast<const uint8_t*>(h->packed_tc), hash, recs,
-                                                      base, rows, reinterpret_cast<float4*>(out_rgba), lc, lr, sig,
-                                                      count, row_n, err);
+        const_cast<nirc_handle*>(h)->fp8_calibrated = true;
     }
-    return cudaGetLastError();
+    e = launch_tc_instance<2, true>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, out_rgba, lc, lr,
+                                    sig, count, row_n, err, amax);
+    if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
+    return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 }  // namespace nirc

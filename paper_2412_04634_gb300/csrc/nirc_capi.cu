@@ -322,6 +322,7 @@ nirc_status nirc_create(const nirc_config* cfg, nirc_handle** out) {
     if (e == cudaSuccess) e = cudaMalloc(&h->grad, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->packed, h->shape.packed_floats * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&h->loss_accum, sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&h->work_counter, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&h->dev_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_err, sizeof(int));
@@ -329,6 +330,10 @@ nirc_status nirc_create(const nirc_config* cfg, nirc_handle** out) {
     h->packed_tc_bytes = tc_image_bytes(h->shape.hidden);
     if (e == cudaSuccess) e = cudaMalloc(&h->packed_tc, h->packed_tc_bytes);
     if (e == cudaSuccess) e = cudaMemset(h->packed_tc, 0, h->packed_tc_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->packed_tc16, h->packed_tc_bytes);
+    if (e == cudaSuccess) e = cudaMemset(h->packed_tc16, 0, h->packed_tc_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->fp8_amax, 16 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->fp8_amax, 0, 16 * sizeof(uint32_t));
     if (e == cudaSuccess && h->shape.n_hash) e = cudaMalloc(&h->hash16, h->shape.n_hash * sizeof(__half));
     if (e == cudaSuccess) e = cudaMemset(h->params, 0, np * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(h->adam_m, 0, np * sizeof(float));
@@ -355,9 +360,12 @@ nirc_status nirc_destroy(nirc_handle* h) {
     cudaFree(h->packed);
     cudaFree(h->loss_accum);
     cudaFree(h->dev_err);
+    cudaFree(h->work_counter);
     if (h->host_err) cudaFreeHost(h->host_err);
     cudaFree(h->hash16);
     cudaFree(h->packed_tc);
+    cudaFree(h->packed_tc16);
+    cudaFree(h->fp8_amax);
     cudaFree(h->scratch);
     cudaFree(h->train_scratch);
     for (int i = 0; i < h->n_pool; ++i) cudaEventDestroy(h->event_pool[i]);
@@ -389,6 +397,7 @@ nirc_status nirc_set_params(nirc_handle* h, const float* params, int on_device, 
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);  // host buffer may be freed on return
     if (e != cudaSuccess) return cuda_status(e, "nirc_set_params");
     h->step = 0;
+    h->fp8_calibrated = false;
     return NIRC_OK;
 }
 
@@ -407,6 +416,7 @@ nirc_status nirc_load_params(nirc_handle* h, const float* params, int on_device,
     if (e == cudaSuccess) e = launch_hash_to_half(h, st);
     if (e == cudaSuccess) e = launch_repack_tc(h, st);
     if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(st);
+    h->fp8_calibrated = false;
     return cuda_status(e, "nirc_load_params");
 }
 
@@ -442,12 +452,9 @@ nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision) {
         set_error("nirc_set_precision: bad argument");
         return NIRC_ERR_INVALID;
     }
-    if (precision == NIRC_FP8_E4M3_TC) {
-        set_error("precision FP8_E4M3_TC is not available in this build");
-        return NIRC_ERR_UNSUPPORTED;
-    }
     const uint32_t old = h->cfg.precision;
     h->cfg.precision = precision;
+    h->fp8_calibrated = false;
     // the tensor-core weight image depends on the operand type
     cudaError_t e = launch_repack_tc(h, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);

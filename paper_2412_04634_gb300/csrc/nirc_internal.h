@@ -70,6 +70,9 @@ struct nirc_handle {
     __half* hash16 = nullptr;       // FP16 copy of the hash table (tensor-core path)
     void* packed_tc = nullptr;      // tensor-core operand images of the weights
     size_t packed_tc_bytes = 0;
+    void* packed_tc16 = nullptr;    // FP16 image used to calibrate FP8 activation scales
+    uint32_t* fp8_amax = nullptr;   // [0,8) activation amax history, [8,16) current launch (float bits)
+    bool fp8_calibrated = false;    // history valid for the current weights
     uint32_t step = 0;              // Adam steps taken
     void* scratch = nullptr;        // estimate_frame intermediates
     size_t scratch_bytes = 0;
@@ -79,6 +82,7 @@ struct nirc_handle {
     int deterministic = 0;          // 1: order-independent gradient sums
     uint64_t recompute_chunk = 1ull << 15;
     float* loss_accum = nullptr;    // one float
+    unsigned long long* work_counter = nullptr;  // pixel counter of the path-tracing kernel
     int* dev_err = nullptr;         // device flag: a bounded wait ran out (1)
     int* host_err = nullptr;        // pinned copy of dev_err, refreshed after tensor-core launches
     // kernel timers (nirc_timing_enable / nirc_timing_read)

@@ -5,7 +5,8 @@
 //   the residual level's M BSDF-sampled directions with their path-traced
 //   incident radiance L_j (eq. L_r, the L_i term), Russian roulette with
 //   termination probability 0.1 (paper: section "Results", implementation
-//   paragraph).
+//   paragraph).  Lanes regenerate work: one ray per busy lane per iteration,
+//   new pixels from a work counter as old ones finish.
 // k_gen_train: the separate training pass (section "Cache application"):
 //   T paths from uniformly drawn pixels, one record per path.
 //
@@ -106,79 +107,184 @@ __device__ __forceinline__ void write_record(nirc_record* dst, const Hit& h, V3 
     q[3] = make_float4(__ldg(&P->roughness), __uint_as_float(prim), __uint_as_float(flags), 0.f);
 }
 
+// Lane state of k_primary_resid: which pixel, which ray is in flight.
+enum : uint32_t { kNeedPixel = 0, kCameraRay = 1, kResidRay = 2, kNoMoreWork = 3 };
+
+// Per pixel: the camera ray, the shading record, then for j = 0..M-1 a
+// residual direction and its path (eq. L_r's L_j), exactly in the order and
+// with the Philox counters of a sequential loop.  The loop is organised as a
+// per-lane state machine so that every iteration traces one ray per busy
+// lane: a lane whose pixel is done takes the next pixel from a work counter
+// (one atomic per warp), so lanes do not idle while others finish long paths.
 __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader* __restrict__ hd_g,
                                                               const Prim* __restrict__ gp, FrameArgs a,
                                                               nirc_record* __restrict__ recs,
                                                               PixelBase* __restrict__ base,
                                                               ResidRow* __restrict__ rows,
                                                               uint64_t* __restrict__ sig_out,
-                                                              uint32_t* __restrict__ count) {
+                                                              uint32_t* __restrict__ count,
+                                                              unsigned long long* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
     const Tracer tr = setup_scene(hd_g, gp, a.n_prims, smem_raw, &hd);
 
     const uint64_t P = (uint64_t)a.W * a.H;
-    for (uint64_t pix64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; pix64 < P;
-         pix64 += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t pix = (uint32_t)pix64;
-        const uint32_t px = pix % a.W, py = pix / a.W;
+    const uint32_t lane = threadIdx.x & 31u;
+    uint32_t stage = kNeedPixel;
+    uint32_t pix = 0, j = 0, seg = 0, nvalid = 0;
+    V3 o{0.f, 0.f, 0.f}, d{0.f, 0.f, 1.f};
+    V3 sp{0.f, 0.f, 0.f}, sn{0.f, 0.f, 1.f}, swo{0.f, 0.f, 1.f};  // shading point, normal, wo
+    float3 salb = make_float3(0.f, 0.f, 0.f), le = salb, wl = salb, L = salb, beta = salb, sw = salb;
+    float srough = 1.f;
+    uint32_t smat = 0;
+    uint64_t sig = kSigInit;
 
-        const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
-        V3 o, d;
-        camera_ray(hd, a.W, a.H, px, py, u01(r.x), u01(r.y), o, d);
-        float t;
-        const int prim = tr.nearest(o, d, t);
-        uint64_t sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+    // Next residual sample of the current pixel: the first valid one becomes
+    // the ray in flight; with none left the pixel's outputs are written.
+    auto next_residual = [&]() -> uint32_t {
         ResidRow* my_rows = rows + (uint64_t)pix * a.M;
-        if (prim < 0) {
-            float4* q = reinterpret_cast<float4*>(recs + pix);
-            q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-            base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
-            base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (uint32_t j = 0; j < a.M; ++j) {
-                my_rows[j].wi = make_float4(0.f, 0.f, 1.f, 0.f);
-                my_rows[j].w = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
-            if (count) count[pix] = 0;
-            continue;
-        }
-        const Hit h = hit_info(tr.prims[prim], o, d, t);
-        const Prim* Pp = gp + prim;
-        const uint32_t pflags = __ldg(&Pp->flags);
-        const uint32_t mat = pflags & 3u;
-        write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (mat << 1));
-        float3 le = make_float3(0.f, 0.f, 0.f);
-        if (h.front || (pflags & EMIT_TWO_SIDED))
-            le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
-        const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
-        const float rough = __ldg(&Pp->roughness);
-        const V3 wo = sneg(d);
-
-        float3 wl = make_float3(0.f, 0.f, 0.f);
-        uint32_t nvalid = 0;
-        for (uint32_t j = 0; j < a.M; ++j) {
-            const BsdfSample s = sample_bsdf(h.n, wo, alb, rough, mat, a.k0, a.k1, pix, j, PURPOSE_RESID_DIR);
+        for (; j < a.M; ++j) {
+            const BsdfSample s = sample_bsdf(sn, swo, salb, srough, smat, a.k0, a.k1, pix, j, PURPOSE_RESID_DIR);
             sig = sig_mix(sig, s.word);
             my_rows[j].wi = make_float4(s.wi.x, s.wi.y, s.wi.z, s.valid ? 1.f : 0.f);
             my_rows[j].w = make_float4(s.w.x, s.w.y, s.w.z, 0.f);
-            if (!s.valid) continue;
-            const float3 L = trace_path(tr, gp, h.p, s.wi, a.k0, a.k1, pix, j, a.D, sig);
-            wl.x += s.w.x * L.x;
-            wl.y += s.w.y * L.y;
-            wl.z += s.w.z * L.z;
-            ++nvalid;
+            if (s.valid) {
+                o = sp;
+                d = s.wi;
+                sw = s.w;
+                beta = make_float3(1.f, 1.f, 1.f);
+                L = make_float3(0.f, 0.f, 0.f);
+                seg = 1;
+                return kResidRay;
+            }
         }
+        float3 w = wl;
         if (a.M) {
             const float inv = 1.0f / (float)a.M;
-            wl.x *= inv;
-            wl.y *= inv;
-            wl.z *= inv;
+            w.x *= inv;
+            w.y *= inv;
+            w.z *= inv;
         }
         base[pix].le = make_float4(le.x, le.y, le.z, 0.f);
-        base[pix].wl = make_float4(wl.x, wl.y, wl.z, 0.f);
+        base[pix].wl = make_float4(w.x, w.y, w.z, 0.f);
         if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
         if (count) count[pix] = nvalid;
+        return kNeedPixel;
+    };
+
+    while (true) {
+        // lanes without a pixel take the next ones (warp-aggregated)
+        const bool need = stage == kNeedPixel;
+        const unsigned needm = __ballot_sync(0xffffffffu, need);
+        if (needm) {
+            const int leader = __ffs(needm) - 1;
+            unsigned long long first = 0;
+            if ((int)lane == leader) first = atomicAdd(work, (unsigned long long)__popc(needm));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            if (need) {
+                const uint64_t mine = first + (uint64_t)__popc(needm & ((1u << lane) - 1u));
+                if (mine < P) {
+                    pix = (uint32_t)mine;
+                    const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
+                    camera_ray(hd, a.W, a.H, pix % a.W, pix / a.W, u01(r.x), u01(r.y), o, d);
+                    stage = kCameraRay;
+                } else {
+                    stage = kNoMoreWork;
+                }
+            }
+        }
+        if (__all_sync(0xffffffffu, stage == kNoMoreWork)) break;
+
+        float t = 0.f;
+        int prim = -1;
+        if (stage == kCameraRay || stage == kResidRay) prim = tr.nearest(o, d, t);
+
+        if (stage == kCameraRay) {
+            sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+            if (prim < 0) {
+                float4* q = reinterpret_cast<float4*>(recs + pix);
+                q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
+                base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
+                ResidRow* my_rows = rows + (uint64_t)pix * a.M;
+                for (uint32_t jj = 0; jj < a.M; ++jj) {
+                    my_rows[jj].wi = make_float4(0.f, 0.f, 1.f, 0.f);
+                    my_rows[jj].w = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+                if (count) count[pix] = 0;
+                stage = kNeedPixel;
+            } else {
+                const Hit h = hit_info(tr.prims[prim], o, d, t);
+                const Prim* Pp = gp + prim;
+                const uint32_t pflags = __ldg(&Pp->flags);
+                smat = pflags & 3u;
+                write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (smat << 1));
+                le = make_float3(0.f, 0.f, 0.f);
+                if (h.front || (pflags & EMIT_TWO_SIDED))
+                    le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
+                salb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+                srough = __ldg(&Pp->roughness);
+                sp = h.p;
+                sn = h.n;
+                swo = sneg(d);
+                wl = make_float3(0.f, 0.f, 0.f);
+                nvalid = 0;
+                j = 0;
+                stage = next_residual();
+            }
+        } else if (stage == kResidRay) {
+            // one segment of residual path j (the loop body of trace_path)
+            sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+            bool end = prim < 0;
+            if (!end) {
+                const Hit h = hit_info(tr.prims[prim], o, d, t);
+                const Prim* Q = gp + prim;
+                const uint32_t flags = __ldg(&Q->flags);
+                if (h.front || (flags & EMIT_TWO_SIDED)) {
+                    L.x += beta.x * __ldg(&Q->emission[0]);
+                    L.y += beta.y * __ldg(&Q->emission[1]);
+                    L.z += beta.z * __ldg(&Q->emission[2]);
+                }
+                if (seg == a.D) {
+                    end = true;
+                } else {
+                    const U4 r = philox(a.k0, a.k1, pix, j, 0u, PURPOSE_RR + 16u * seg);
+                    const bool cont = u01(r.x) < kRRContinue;
+                    sig = sig_mix(sig, (uint32_t)cont);
+                    if (!cont) {
+                        end = true;
+                    } else {
+                        beta.x /= kRRContinue;
+                        beta.y /= kRRContinue;
+                        beta.z /= kRRContinue;
+                        const float3 alb =
+                            make_float3(__ldg(&Q->albedo[0]), __ldg(&Q->albedo[1]), __ldg(&Q->albedo[2]));
+                        const BsdfSample s = sample_bsdf(h.n, sneg(d), alb, __ldg(&Q->roughness), flags & 3u, a.k0,
+                                                         a.k1, pix, j, PURPOSE_BOUNCE + 16u * seg);
+                        sig = sig_mix(sig, s.word);
+                        if (!s.valid) {
+                            end = true;
+                        } else {
+                            beta.x *= s.w.x;
+                            beta.y *= s.w.y;
+                            beta.z *= s.w.z;
+                            o = h.p;
+                            d = s.wi;
+                            ++seg;
+                        }
+                    }
+                }
+            }
+            if (end) {
+                wl.x += sw.x * L.x;
+                wl.y += sw.y * L.y;
+                wl.z += sw.z * L.z;
+                ++nvalid;
+                ++j;
+                stage = next_residual();
+            }
+        }
     }
 }
 
@@ -257,7 +363,9 @@ cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const 
     uint32_t grid = 1;
     cudaError_t e = persistent_grid(k_primary_resid, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
-    k_primary_resid<<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count);
+    e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_primary_resid<<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter);
     return cudaGetLastError();
 }
 

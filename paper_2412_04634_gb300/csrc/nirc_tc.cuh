@@ -25,6 +25,12 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t
     return (row >> 3) * 1024u + (row & 7u) * 128u + ((((k >> 3) ^ (row & 7u)) & 7u) << 4) + (k & 7u) * 2u;
 }
 
+// Byte offset of 8-bit element (row, k) (k < 64) in the same layout: a row
+// keeps its 64 bytes in chunks 0-3 (16 elements each) of its 128-byte line.
+__host__ __device__ __forceinline__ uint32_t sw128_offset_b8(uint32_t row, uint32_t k) {
+    return (row >> 3) * 1024u + (row & 7u) * 128u + ((((k >> 4) ^ (row & 7u)) & 7u) << 4) + (k & 15u);
+}
+
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B, stride between
 // 8-row groups 1024 bytes.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -48,6 +54,19 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b,
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// kind::f8f6f4 with both operands E4M3 (type code 0 in the instruction
+// descriptor, so idesc_f16(0, M, N) describes it): K = 32 per instruction,
+// i.e. 32 bytes of each K-major row, the same byte step as a kind::f16 K = 16.
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
         :
         : "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
         : "memory");
@@ -167,6 +186,15 @@ __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
     asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
     return d;
 }
+// Four floats to E4M3 (round to nearest, saturating to +-448), element 0 in
+// the lowest byte.
+__device__ __forceinline__ uint32_t pack_e4m3x4(float x0, float x1, float x2, float x3) {
+    uint16_t lo, hi;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(lo) : "f"(x1), "f"(x0));
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(hi) : "f"(x3), "f"(x2));
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+
 __device__ __forceinline__ uint32_t pack_f16(float lo, float hi) {
     uint32_t d;
     asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));

@@ -120,3 +120,67 @@ def test_tc_mrse_matches_oracle(N, oracle):
     m_gpu = out.item()
     m_or = oracle.mrse(o["pixel"], ref.astype(np.float32).astype(np.float64))
     assert abs(m_gpu - m_or) <= 0.01 * m_or, (m_gpu, m_or)
+
+
+# FP8 E4M3 hidden layers (3 mantissa bits, per-layer scales): the decisions
+# stay bit-exact; the cache values carry E4M3 rounding through the hidden
+# layers, so their error is bounded loosely here and reported in the
+# precision sweep.
+FP8_P50, FP8_P99 = 0.05, 0.3
+
+
+@pytest.mark.parametrize("which", ["small", "hash"])
+def test_tc_fp8(N, oracle, which):
+    import torch
+    if which == "small":
+        cfg = scenes.config_small()
+        params = scenes.init_params(cfg, 1)
+        sc = scenes.cornell_scene(64, 64, seed=1)
+        W, H, Nc, D, fr = 64, 64, 8, 4, 2
+    else:
+        cfg = _hash_cfg()
+        params = scenes.init_params(cfg, 2)
+        params[cfg.n_mlp_params:] = np.random.default_rng(0).uniform(-0.5, 0.5, cfg.n_hash_params).astype(np.float32)
+        sc = scenes.cornell_scene(96, 54, seed=1, n_prims=256, glossy=True, moving_emitter=True, frame=7)
+        W, H, Nc, D, fr = 96, 54, 16, 5, 7
+    g = _run_frame(N, cfg, params, sc, W, H, Nc, 1, D, fr, 1, precision=N.NIRC_FP8_E4M3_TC, rows=True)
+    o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(W, H, Nc, 1, D, fr, 1), rows=True)
+    assert np.array_equal(g["sig"], o["sig"])
+    assert np.array_equal(g["count"], o["count"])
+    err = _row_errors(g, o)
+    print(which, "fp8 row error p50 %.4f p99 %.4f max %.4f" % (np.percentile(err, 50), np.percentile(err, 99),
+                                                                err.max()))
+    assert np.percentile(err, 50) <= FP8_P50 and np.percentile(err, 99) <= FP8_P99
+
+
+def test_tc_fp8_delayed_scaling_is_deterministic(N):
+    """The first FP8 frame calibrates the activation scales with one FP16
+    pass; each later frame scales with the amax the previous frame recorded.
+    Two caches taken through the same frames give identical images, and
+    frames after the first stay within FP8 rounding of each other."""
+    import torch
+    cfg = _hash_cfg()
+    params = scenes.init_params(cfg, 5)
+    params[cfg.n_mlp_params:] = np.random.default_rng(1).uniform(-0.5, 0.5, cfg.n_hash_params).astype(np.float32)
+    sc = scenes.cornell_scene(64, 48, seed=3, n_prims=64, glossy=True)
+    scd = N.scene_to_tensor(sc)
+    runs = []
+    for _ in range(2):
+        cache = N.Cache(cfg)
+        cache.set_params(params)
+        N.nirc_set_precision(cache.h, N.NIRC_FP8_E4M3_TC)
+        imgs, lcs = [], []
+        for f in range(3):
+            out = torch.empty((64 * 48, 4), device="cuda")
+            lc = torch.empty((64 * 48, 3), device="cuda")
+            N.nirc_estimate_frame(cache.h, scd, N.frame_desc(64, 48, 8, 1, 4, 1, 1, sc.n_prims), out, lc=lc)
+            imgs.append(out.cpu().numpy())
+            lcs.append(lc.cpu().numpy())
+        N.nirc_sync(cache.h)
+        runs.append((imgs, lcs))
+        cache.close()
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    lc1, lc2 = runs[0][1][1], runs[0][1][2]
+    scale = max(np.abs(lc1).max(), 1e-30)
+    assert np.abs(lc1 - lc2).max() <= 0.1 * scale
