@@ -76,6 +76,23 @@ def dist_info():
     return world, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Replicas only: every rank renders and trains its own independent
+    replica (scene, weights and Philox seed offset by the rank); no data
+    crosses ranks."""
+    return 1 + rank
+
+
+def max_over_ranks(x: float, dev) -> float:
+    """The slowest rank's time (the only cross-rank operation: timing)."""
+    import torch
+    if dist_info()[0] <= 1:
+        return x
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -251,11 +268,7 @@ class FrameRunner:
         timing = N.nirc_timing_read(self.cache.h)
         N.nirc_timing_enable(self.cache.h, False)
         step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
-        total_ms = evs[0].elapsed_time(evs[-1])
-        if world > 1:
-            t = torch.tensor([total_ms], device=self.dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), self.dev)
         return dict(total_ms=total_ms, step_ms=step_ms, timing=timing, clocks=clocks, mrse=float(self.mrse.item()))
 
     def e2e(self, ref, first, steps, frames, stream):
@@ -278,11 +291,7 @@ class FrameRunner:
             host_small[1:2].copy_(self.loss.double(), non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize(self.dev)
-        ms = e0.elapsed_time(e1)
-        if dist_info()[0] > 1:
-            t = torch.tensor([ms], device=self.dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), self.dev)
         return ms, int(frames[0].blob().nbytes), int(self.P * 16 + 8 + 4)
 
 
@@ -330,7 +339,7 @@ def run_ours(args):
         torch.distributed.barrier()
     from paper_2412_04634_gb300 import nirc as N
 
-    cfg, params, frames = build_workload(args, seed_offset=rank)
+    cfg, params, frames = build_workload(args, seed_offset=replica_seed(rank) - 1)
     stream = torch.cuda.current_stream(dev)
     props = torch.cuda.get_device_properties(dev)
     gpu_id = None
@@ -338,7 +347,7 @@ def run_ours(args):
         gpu_id = "GPU-" + str(props.uuid)
     except Exception:
         pass
-    seed = 1 + rank
+    seed = replica_seed(rank)
     first = args.warmup
     last_frame = (first + args.steps - 1) % 60
 

@@ -280,8 +280,9 @@ nirc_status nirc_query_bwd(nirc_handle* h, const nirc_record* d_records, const f
                            const float* d_grad_out, uint64_t n, float* d_grad_params, float* d_value, void* stream);
 
 /* Mean relative squared error over pixels and RGB (paper: MRSE),
- * mean (I - R)^2 / (R^2 + eps), accumulated in FP64; images are float4 per
- * pixel (alpha ignored); d_out = one device double. */
+ * mean (I - R)^2 / (R^2 + eps); each term in binary32, the sum accumulated
+ * in FP64; images are float4 per pixel (alpha ignored); d_out = one device
+ * double. */
 nirc_status nirc_frame_mrse(const float* d_img_rgba, const float* d_ref_rgba, uint64_t n_pixels, float eps,
                             double* d_out, void* stream);
 

@@ -25,6 +25,7 @@ struct __align__(16) BvhNode {
 
 struct Bvh {
     const BvhNode* nodes;
+    const float4* boxes;    // conservative primitive boxes (lo, hi per primitive)
     const uint32_t* large;  // primitives tested by brute force
     uint32_t n_large;
     uint32_t n_tree;        // leaves of the tree
@@ -131,6 +132,7 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
     const float cmin = scal[0], cinv = scal[1];
     Bvh out;
     out.nodes = nodes;
+    out.boxes = box;
     out.large = large;
     out.n_large = __float_as_uint(scal[2]);
     out.n_tree = __float_as_uint(scal[3]);
@@ -289,14 +291,16 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
                 float t0 = 0.f, t1 = 0.f;
                 bool h0, h1;
                 if (c0 & kLeafBit) {
-                    h0 = true;
+                    const uint32_t q = c0 & ~kLeafBit;
+                    h0 = q < n && box_entry(b.boxes[2 * q], b.boxes[2 * q + 1], o, inv, best, t0);
                 } else if (c0 + 1 < m) {
                     h0 = box_entry(b.nodes[c0].lo, b.nodes[c0].hi, o, inv, best, t0);
                 } else {
                     h0 = false;
                 }
                 if (c1 & kLeafBit) {
-                    h1 = true;
+                    const uint32_t q = c1 & ~kLeafBit;
+                    h1 = q < n && box_entry(b.boxes[2 * q], b.boxes[2 * q + 1], o, inv, best, t1);
                 } else if (c1 + 1 < m) {
                     h1 = box_entry(b.nodes[c1].lo, b.nodes[c1].hi, o, inv, best, t1);
                 } else {

@@ -8,7 +8,8 @@
 //   paragraph).  Lanes regenerate work: one ray per busy lane per iteration,
 //   new pixels from a work counter as old ones finish.
 // k_gen_train: the separate training pass (section "Cache application"):
-//   T paths from uniformly drawn pixels, one record per path.
+//   T paths from uniformly drawn pixels, one record per path, organised the
+//   same way.
 //
 // Both kernels are persistent: each CTA stages the primitives' geometry in
 // shared memory and, for scenes of more than 16 primitives, builds its own
@@ -48,7 +49,7 @@ __device__ __forceinline__ Tracer setup_scene(const SceneHeader* __restrict__ hd
     Tracer tr;
     tr.prims = sp;
     tr.n = n_prims;
-    tr.tree = Bvh{nullptr, nullptr, 0u, 0u, 0u};
+    tr.tree = Bvh{nullptr, nullptr, nullptr, 0u, 0u, 0u};
     tr.bvh = n_prims >= kBvhMinPrims;
     if (tr.bvh) {
         tr.tree = bvh_build(sp, n_prims, smem + (size_t)n_prims * sizeof(PrimGeom));
@@ -57,45 +58,56 @@ __device__ __forceinline__ Tracer setup_scene(const SceneHeader* __restrict__ hd
     return tr;
 }
 
-// Incident radiance along (o, d) from the path's vertices.
-__device__ __forceinline__ float3 trace_path(const Tracer& tr, const Prim* __restrict__ gp, V3 o, V3 d, uint32_t k0,
-                                             uint32_t k1, uint32_t c0, uint32_t c1, uint32_t max_depth,
-                                             uint64_t& sig) {
-    float3 L = make_float3(0.f, 0.f, 0.f);
-    float3 beta = make_float3(1.f, 1.f, 1.f);
-    for (uint32_t seg = 1; seg <= max_depth; ++seg) {
-        float t;
-        const int prim = tr.nearest(o, d, t);
-        sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
-        if (prim < 0) break;
-        const Hit h = hit_info(tr.prims[prim], o, d, t);
-        const Prim* P = gp + prim;
-        const uint32_t flags = __ldg(&P->flags);
-        if (h.front || (flags & EMIT_TWO_SIDED)) {
-            L.x += beta.x * __ldg(&P->emission[0]);
-            L.y += beta.y * __ldg(&P->emission[1]);
-            L.z += beta.z * __ldg(&P->emission[2]);
-        }
-        if (seg == max_depth) break;
-        const U4 r = philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg);
-        const bool cont = u01(r.x) < kRRContinue;
-        sig = sig_mix(sig, (uint32_t)cont);
-        if (!cont) break;
-        beta.x /= kRRContinue;
-        beta.y /= kRRContinue;
-        beta.z /= kRRContinue;
-        const float3 alb = make_float3(__ldg(&P->albedo[0]), __ldg(&P->albedo[1]), __ldg(&P->albedo[2]));
-        const BsdfSample s = sample_bsdf(h.n, sneg(d), alb, __ldg(&P->roughness), flags & 3u, k0, k1, c0, c1,
-                                         PURPOSE_BOUNCE + 16u * seg);
-        sig = sig_mix(sig, s.word);
-        if (!s.valid) break;
-        beta.x *= s.w.x;
-        beta.y *= s.w.y;
-        beta.z *= s.w.z;
-        o = h.p;
-        d = s.wi;
+// One segment of a path (residual or training) after its ray was traced:
+// emission of the hit, then Russian roulette and the next BSDF direction.
+// Counters (c0, c1) identify the path, `seg` its segment (1-based).  Returns
+// true when the path ends; otherwise (o, d) is the next ray and seg + 1.
+__device__ __forceinline__ bool path_segment(const Tracer& tr, const Prim* __restrict__ gp, int prim, float t, V3& o,
+                                             V3& d, float3& beta, float3& L, uint32_t& seg, uint32_t max_depth,
+                                             uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint64_t& sig) {
+    sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+    if (prim < 0) return true;
+    const Hit h = hit_info(tr.prims[prim], o, d, t);
+    const Prim* Q = gp + prim;
+    const uint32_t flags = __ldg(&Q->flags);
+    if (h.front || (flags & EMIT_TWO_SIDED)) {
+        L.x += beta.x * __ldg(&Q->emission[0]);
+        L.y += beta.y * __ldg(&Q->emission[1]);
+        L.z += beta.z * __ldg(&Q->emission[2]);
     }
-    return L;
+    if (seg == max_depth) return true;
+    const U4 r = philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg);
+    const bool cont = u01(r.x) < kRRContinue;
+    sig = sig_mix(sig, (uint32_t)cont);
+    if (!cont) return true;
+    beta.x /= kRRContinue;
+    beta.y /= kRRContinue;
+    beta.z /= kRRContinue;
+    const float3 alb = make_float3(__ldg(&Q->albedo[0]), __ldg(&Q->albedo[1]), __ldg(&Q->albedo[2]));
+    const BsdfSample s =
+        sample_bsdf(h.n, sneg(d), alb, __ldg(&Q->roughness), flags & 3u, k0, k1, c0, c1, PURPOSE_BOUNCE + 16u * seg);
+    sig = sig_mix(sig, s.word);
+    if (!s.valid) return true;
+    beta.x *= s.w.x;
+    beta.y *= s.w.y;
+    beta.z *= s.w.z;
+    o = h.p;
+    d = s.wi;
+    ++seg;
+    return false;
+}
+
+// Take `need` lanes' next work items from the counter (one atomic per warp);
+// returns the lane's item (or a value >= limit when none is left).
+__device__ __forceinline__ uint64_t fetch_work(unsigned long long* work, bool need) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned needm = __ballot_sync(0xffffffffu, need);
+    if (!needm) return ~0ull;
+    const int leader = __ffs(needm) - 1;
+    unsigned long long first = 0;
+    if ((int)lane == leader) first = atomicAdd(work, (unsigned long long)__popc(needm));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    return first + (uint64_t)__popc(needm & ((1u << lane) - 1u));
 }
 
 __device__ __forceinline__ void write_record(nirc_record* dst, const Hit& h, V3 d, const Prim* P, uint32_t prim,
@@ -129,7 +141,6 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
     const Tracer tr = setup_scene(hd_g, gp, a.n_prims, smem_raw, &hd);
 
     const uint64_t P = (uint64_t)a.W * a.H;
-    const uint32_t lane = threadIdx.x & 31u;
     uint32_t stage = kNeedPixel;
     uint32_t pix = 0, j = 0, seg = 0, nvalid = 0;
     V3 o{0.f, 0.f, 0.f}, d{0.f, 0.f, 1.f};
@@ -175,22 +186,15 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
     while (true) {
         // lanes without a pixel take the next ones (warp-aggregated)
         const bool need = stage == kNeedPixel;
-        const unsigned needm = __ballot_sync(0xffffffffu, need);
-        if (needm) {
-            const int leader = __ffs(needm) - 1;
-            unsigned long long first = 0;
-            if ((int)lane == leader) first = atomicAdd(work, (unsigned long long)__popc(needm));
-            first = __shfl_sync(0xffffffffu, first, leader);
-            if (need) {
-                const uint64_t mine = first + (uint64_t)__popc(needm & ((1u << lane) - 1u));
-                if (mine < P) {
-                    pix = (uint32_t)mine;
-                    const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
-                    camera_ray(hd, a.W, a.H, pix % a.W, pix / a.W, u01(r.x), u01(r.y), o, d);
-                    stage = kCameraRay;
-                } else {
-                    stage = kNoMoreWork;
-                }
+        const uint64_t mine = fetch_work(work, need);
+        if (need) {
+            if (mine < P) {
+                pix = (uint32_t)mine;
+                const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
+                camera_ray(hd, a.W, a.H, pix % a.W, pix / a.W, u01(r.x), u01(r.y), o, d);
+                stage = kCameraRay;
+            } else {
+                stage = kNoMoreWork;
             }
         }
         if (__all_sync(0xffffffffu, stage == kNoMoreWork)) break;
@@ -234,48 +238,7 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
                 stage = next_residual();
             }
         } else if (stage == kResidRay) {
-            // one segment of residual path j (the loop body of trace_path)
-            sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
-            bool end = prim < 0;
-            if (!end) {
-                const Hit h = hit_info(tr.prims[prim], o, d, t);
-                const Prim* Q = gp + prim;
-                const uint32_t flags = __ldg(&Q->flags);
-                if (h.front || (flags & EMIT_TWO_SIDED)) {
-                    L.x += beta.x * __ldg(&Q->emission[0]);
-                    L.y += beta.y * __ldg(&Q->emission[1]);
-                    L.z += beta.z * __ldg(&Q->emission[2]);
-                }
-                if (seg == a.D) {
-                    end = true;
-                } else {
-                    const U4 r = philox(a.k0, a.k1, pix, j, 0u, PURPOSE_RR + 16u * seg);
-                    const bool cont = u01(r.x) < kRRContinue;
-                    sig = sig_mix(sig, (uint32_t)cont);
-                    if (!cont) {
-                        end = true;
-                    } else {
-                        beta.x /= kRRContinue;
-                        beta.y /= kRRContinue;
-                        beta.z /= kRRContinue;
-                        const float3 alb =
-                            make_float3(__ldg(&Q->albedo[0]), __ldg(&Q->albedo[1]), __ldg(&Q->albedo[2]));
-                        const BsdfSample s = sample_bsdf(h.n, sneg(d), alb, __ldg(&Q->roughness), flags & 3u, a.k0,
-                                                         a.k1, pix, j, PURPOSE_BOUNCE + 16u * seg);
-                        sig = sig_mix(sig, s.word);
-                        if (!s.valid) {
-                            end = true;
-                        } else {
-                            beta.x *= s.w.x;
-                            beta.y *= s.w.y;
-                            beta.z *= s.w.z;
-                            o = h.p;
-                            d = s.wi;
-                            ++seg;
-                        }
-                    }
-                }
-            }
+            const bool end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig);
             if (end) {
                 wl.x += sw.x * L.x;
                 wl.y += sw.y * L.y;
@@ -288,48 +251,86 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
     }
 }
 
+// Training paths, organised like k_primary_resid: per path index the pixel
+// pick, camera ray, record and first direction, then the path's segments;
+// one ray per busy lane per iteration.
 __global__ void __launch_bounds__(kPtThreads) k_gen_train(const SceneHeader* __restrict__ hd_g,
                                                           const Prim* __restrict__ gp, uint32_t n_prims, uint32_t W,
                                                           uint32_t H, uint64_t T, uint32_t k0, uint32_t k1,
                                                           uint32_t max_depth, nirc_record* __restrict__ recs,
-                                                          float* __restrict__ dirs, float* __restrict__ targets) {
+                                                          float* __restrict__ dirs, float* __restrict__ targets,
+                                                          unsigned long long* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
     const Tracer tr = setup_scene(hd_g, gp, n_prims, smem_raw, &hd);
     const uint32_t P = W * H;
-    for (uint64_t ti = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; ti < T; ti += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t tr_idx = (uint32_t)ti;
-        const U4 r = philox(k0, k1, tr_idx, 0u, 0u, PURPOSE_TRAIN_PICK);
-        const uint32_t pix = __umulhi(r.x, P);
-        V3 o, d;
-        camera_ray(hd, W, H, pix % W, pix / W, u01(r.y), u01(r.z), o, d);
-        float t;
-        const int prim = tr.nearest(o, d, t);
-        float* dir = dirs + 3 * ti;
-        float* tg = targets + 3 * ti;
-        dir[0] = dir[1] = dir[2] = 0.f;
-        tg[0] = tg[1] = tg[2] = 0.f;
-        if (prim < 0) {
-            float4* q = reinterpret_cast<float4*>(recs + ti);
-            q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
+    uint32_t stage = kNeedPixel;
+    uint32_t ti = 0, seg = 0;
+    V3 o{0.f, 0.f, 0.f}, d{0.f, 0.f, 1.f};
+    float3 beta = make_float3(0.f, 0.f, 0.f), L = beta;
+    uint64_t sig = 0;
+    while (true) {
+        const bool need = stage == kNeedPixel;
+        const uint64_t mine = fetch_work(work, need);
+        if (need) {
+            if (mine < T) {
+                ti = (uint32_t)mine;
+                const U4 r = philox(k0, k1, ti, 0u, 0u, PURPOSE_TRAIN_PICK);
+                const uint32_t pix = __umulhi(r.x, P);
+                camera_ray(hd, W, H, pix % W, pix / W, u01(r.y), u01(r.z), o, d);
+                stage = kCameraRay;
+            } else {
+                stage = kNoMoreWork;
+            }
         }
-        const Hit h = hit_info(tr.prims[prim], o, d, t);
-        const Prim* Pp = gp + prim;
-        const uint32_t mat = __ldg(&Pp->flags) & 3u;
-        const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
-        const BsdfSample s =
-            sample_bsdf(h.n, sneg(d), alb, __ldg(&Pp->roughness), mat, k0, k1, tr_idx, 0u, PURPOSE_RESID_DIR);
-        write_record(recs + ti, h, d, Pp, (uint32_t)prim, (s.valid ? 1u : 0u) | (mat << 1));
-        if (!s.valid) continue;
-        uint64_t sig = 0;
-        const float3 L = trace_path(tr, gp, h.p, s.wi, k0, k1, tr_idx, 0u, max_depth, sig);
-        dir[0] = s.wi.x;
-        dir[1] = s.wi.y;
-        dir[2] = s.wi.z;
-        tg[0] = L.x;
-        tg[1] = L.y;
-        tg[2] = L.z;
+        if (__all_sync(0xffffffffu, stage == kNoMoreWork)) break;
+
+        float t = 0.f;
+        int prim = -1;
+        if (stage == kCameraRay || stage == kResidRay) prim = tr.nearest(o, d, t);
+
+        if (stage == kCameraRay) {
+            float* dir = dirs + 3 * (uint64_t)ti;
+            float* tg = targets + 3 * (uint64_t)ti;
+            if (prim < 0) {
+                float4* q = reinterpret_cast<float4*>(recs + ti);
+                q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                dir[0] = dir[1] = dir[2] = 0.f;
+                tg[0] = tg[1] = tg[2] = 0.f;
+                stage = kNeedPixel;
+            } else {
+                const Hit h = hit_info(tr.prims[prim], o, d, t);
+                const Prim* Pp = gp + prim;
+                const uint32_t mat = __ldg(&Pp->flags) & 3u;
+                const float3 alb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+                const BsdfSample s =
+                    sample_bsdf(h.n, sneg(d), alb, __ldg(&Pp->roughness), mat, k0, k1, ti, 0u, PURPOSE_RESID_DIR);
+                write_record(recs + ti, h, d, Pp, (uint32_t)prim, (s.valid ? 1u : 0u) | (mat << 1));
+                if (!s.valid) {
+                    dir[0] = dir[1] = dir[2] = 0.f;
+                    tg[0] = tg[1] = tg[2] = 0.f;
+                    stage = kNeedPixel;
+                } else {
+                    dir[0] = s.wi.x;
+                    dir[1] = s.wi.y;
+                    dir[2] = s.wi.z;
+                    o = h.p;
+                    d = s.wi;
+                    beta = make_float3(1.f, 1.f, 1.f);
+                    L = make_float3(0.f, 0.f, 0.f);
+                    seg = 1;
+                    stage = kResidRay;
+                }
+            }
+        } else if (stage == kResidRay) {
+            if (path_segment(tr, gp, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig)) {
+                float* tg = targets + 3 * (uint64_t)ti;
+                tg[0] = L.x;
+                tg[1] = L.y;
+                tg[2] = L.z;
+                stage = kNeedPixel;
+            }
+        }
     }
 }
 
@@ -378,8 +379,10 @@ cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n
     uint32_t grid = 1;
     cudaError_t e = persistent_grid(k_gen_train, smem, T, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h->work_counter + 1, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
     k_gen_train<<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
-                                                max_depth, recs, dirs, targets);
+                                                max_depth, recs, dirs, targets, h->work_counter + 1);
     return cudaGetLastError();
 }
 
