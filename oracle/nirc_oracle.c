@@ -18,6 +18,14 @@
  * (compile with -ffp-contract=off, no fast-math), the precision the GPU path
  * takes these decisions in, so both sides make the same decisions.
  *
+ * Light modes (eq. Lsplit): mode 0 caches the full incident radiance and
+ * traces pure BSDF paths; mode 1 splits L_i = L_ind + L_nee, estimates the
+ * direct part by next-event estimation on rectangular emitters combined
+ * with BSDF sampling by the power heuristic (at the shading point the M
+ * residual directions are the BSDF technique, along a path the continuation
+ * direction), and the cache, the residual paths and the training targets
+ * carry L_ind (the emission of a path's first hit belongs to L_nee).
+ *
  * Parity pins (tests/test_oracle_*.py): Philox against a library
  * implementation and its published known answer; the white-furnace closed
  * form (constant cache on a Lambertian surface gives rho*L per sample); the
@@ -101,7 +109,7 @@ typedef struct {
     uint32_t frame;
     uint64_t seed;
     uint32_t cache_mode; /* 0 network, 1 zero, 2 constant */
-    uint32_t pad;
+    uint32_t light_mode; /* 0 cache = full L_i, 1 cache = L_ind with NEE + MIS (eq. Lsplit) */
     double cache_const[3];
 } o_frame;
 
@@ -117,7 +125,8 @@ enum {
     PURPOSE_RESID_DIR = 3,
     PURPOSE_BOUNCE = 4, /* + 16 * segment */
     PURPOSE_RR = 5,     /* + 16 * segment */
-    PURPOSE_TRAIN_PICK = 6
+    PURPOSE_TRAIN_PICK = 6,
+    PURPOSE_LIGHT = 7   /* + 16 * segment (0: the shading point) */
 };
 
 static const float T_MIN = 1e-4f;
@@ -731,6 +740,203 @@ static void trace_path(const uint8_t* blob, const float o_in[3], const float d_i
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Next-event estimation with multiple importance sampling (light mode 1)   */
+/* ------------------------------------------------------------------------ */
+
+#define MAX_LIGHTS 1024
+
+typedef struct {
+    uint32_t n;
+    uint32_t idx[MAX_LIGHTS]; /* emitting rectangles in primitive order */
+} o_lights;
+
+static int is_rect_emitter(const o_prim* p)
+{
+    return p->kind == KIND_RECT && (p->emission[0] > 0.0f || p->emission[1] > 0.0f || p->emission[2] > 0.0f);
+}
+
+static void collect_lights(const uint8_t* blob, o_lights* L)
+{
+    const o_header* hd = (const o_header*)blob;
+    const o_prim* prims = scene_prims(blob);
+    L->n = 0;
+    for (uint32_t i = 0; i < hd->n_prims && L->n < MAX_LIGHTS; i++)
+        if (is_rect_emitter(&prims[i])) L->idx[L->n++] = i;
+}
+
+static double rect_area(const o_prim* p)
+{
+    double u[3] = {p->u[0], p->u[1], p->u[2]}, v[3] = {p->v[0], p->v[1], p->v[2]};
+    double c[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    return sqrt(dot3d(c, c));
+}
+
+/* f_r cos(theta_i) and the BSDF sampling density p(wi) (solid angle) of the
+ * material at rec for an arbitrary direction wi; both 0 below the surface. */
+static void bsdf_eval(const o_record* rec, const float wif[3], double fcos[3], double* pdf)
+{
+    uint32_t mat = (rec->flags >> 1) & 3u;
+    double n[3] = {rec->n[0], rec->n[1], rec->n[2]};
+    double wi[3] = {wif[0], wif[1], wif[2]};
+    double ci = dot3d(n, wi);
+    fcos[0] = fcos[1] = fcos[2] = 0.0;
+    *pdf = 0.0;
+    if (mat == MAT_BLACK || !(ci > 0.0)) return;
+    if (mat == MAT_LAMBERT) {
+        for (int c = 0; c < 3; c++) fcos[c] = (double)rec->albedo[c] / O_PI * ci;
+        *pdf = ci / O_PI;
+        return;
+    }
+    double wo[3] = {rec->wo[0], rec->wo[1], rec->wo[2]};
+    double alpha = (double)(rec->roughness * rec->roughness);
+    double a2 = alpha * alpha;
+    double co = dot3d(n, wo);
+    double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
+    double hl = sqrt(dot3d(h, h));
+    for (int k = 0; k < 3; k++) h[k] /= hl;
+    double ch = dot3d(n, h);
+    double oh = dot3d(wo, h);
+    if (oh < 0.0) oh = 0.0;
+    if (oh > 1.0) oh = 1.0;
+    double dd = ch * ch * (a2 - 1.0) + 1.0;
+    double D = a2 / (O_PI * dd * dd);
+    double lam_o = sqrt(a2 + (1.0 - a2) * co * co);
+    double lam_i = sqrt(a2 + (1.0 - a2) * ci * ci);
+    double G2 = 2.0 * ci * co / (co * lam_i + ci * lam_o);
+    double G1o = 2.0 * co / (co + lam_o);
+    double F = F0_SPEC + (1.0 - F0_SPEC) * pow(1.0 - oh, 5.0);
+    double fs = F * D * G2 / (4.0 * ci * co);
+    for (int c = 0; c < 3; c++) fcos[c] = ((double)rec->albedo[c] / O_PI + fs) * ci;
+    *pdf = 0.5 * ci / O_PI + 0.5 * G1o * D / (4.0 * co);
+}
+
+/* Solid-angle density of sampling direction d toward a point at distance t
+ * on emitting rectangle e by the light technique (uniform emitter, uniform
+ * point). */
+static double light_pdf(const o_prim* e, const float d[3], double t, uint32_t n_lights)
+{
+    double cl = fabs((double)e->n[0] * d[0] + (double)e->n[1] * d[1] + (double)e->n[2] * d[2]);
+    return t * t / (cl * rect_area(e) * (double)n_lights);
+}
+
+/* Power-heuristic weight of technique a (n_a samples, density pa) against b. */
+static double power_weight(double na_pa, double nb_pb)
+{
+    double a = na_pa * na_pa, b = nb_pb * nb_pb;
+    return a + b > 0.0 ? a / (a + b) : 0.0;
+}
+
+/* One light sample at shading record rec: emitter k uniform among the
+ * rectangles (word 0), point a + u1 U + u2 V (words 1, 2), shadow ray,
+ * contribution f cos L_e cos_l / (dist^2 pdf_area), weighted against n_b BSDF
+ * samples by the power heuristic.  Adds into out; returns the decision word
+ * (emitter | geometry ok << 16 | visible << 17) for the signature. */
+static uint32_t nee_sample(const uint8_t* blob, const o_lights* lights, const o_record* rec, uint32_t n_b,
+                           uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3, double out[3])
+{
+    const o_header* hd = (const o_header*)blob;
+    const o_prim* prims = scene_prims(blob);
+    if (lights->n == 0 || ((rec->flags >> 1) & 3u) == MAT_BLACK) return 0;
+    uint32_t r[4];
+    philox(k0, k1, c0, c1, 0u, c3, r);
+    uint32_t e = (uint32_t)(((uint64_t)r[0] * lights->n) >> 32);
+    uint32_t li = lights->idx[e];
+    const o_prim* L = &prims[li];
+    float u1 = u01(r[1]), u2 = u01(r[2]);
+    float pt[3], v[3], w[3];
+    for (int k = 0; k < 3; k++) {
+        pt[k] = (L->a[k] + u1 * L->u[k]) + u2 * L->v[k];
+        v[k] = pt[k] - rec->p[k];
+    }
+    float dist2 = dot3f(v, v);
+    float dist = sqrtf(dist2);
+    w[0] = v[0];
+    w[1] = v[1];
+    w[2] = v[2];
+    normalize3f(w);
+    float cx = dot3f(rec->n, w);
+    float cl = -dot3f(L->n, w);
+    int ok = cx > 0.0f && (cl > 0.0f || ((L->flags & EMIT_TWO_SIDED) && cl < 0.0f));
+    uint32_t word = e | ((uint32_t)ok << 16);
+    if (!ok) return word;
+    float t;
+    int hit = trace_nearest(prims, hd->n_prims, rec->p, w, &t);
+    int visible = hit == (int)li && fabsf(t - dist) <= 1e-3f * dist;
+    word |= (uint32_t)visible << 17;
+    if (!visible) return word;
+    double fcos[3], pb;
+    bsdf_eval(rec, w, fcos, &pb);
+    double pl = light_pdf(L, w, (double)dist, lights->n);
+    double wl = power_weight(pl, (double)n_b * pb);
+    for (int c = 0; c < 3; c++) out[c] += fcos[c] * (double)L->emission[c] * wl / pl;
+    return word;
+}
+
+/* L_ind(x, d): the path from o along d, NEE at every vertex (MIS against the
+ * continuation, except at the last vertex, which has none), emission found
+ * by a continuation weighted by the power heuristic.  The emission of the
+ * first hit is not part of L_ind; it is returned in first_emit, weighted for
+ * the shading point's MIS (n_b0 BSDF samples of density pb0 there). */
+static void trace_path_nee(const uint8_t* blob, const o_lights* lights, const float o_in[3], const float d_in[3],
+                           uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t max_depth, uint32_t n_b0,
+                           double pb0, double L[3], double first_emit[3], uint64_t* sig)
+{
+    const o_header* hd = (const o_header*)blob;
+    const o_prim* prims = scene_prims(blob);
+    float o[3] = {o_in[0], o_in[1], o_in[2]};
+    float d[3] = {d_in[0], d_in[1], d_in[2]};
+    double beta[3] = {1.0, 1.0, 1.0};
+    double pb_prev = pb0;
+    L[0] = L[1] = L[2] = 0.0;
+    first_emit[0] = first_emit[1] = first_emit[2] = 0.0;
+    for (uint32_t seg = 1; seg <= max_depth; seg++) {
+        float t;
+        int prim = trace_nearest(prims, hd->n_prims, o, d, &t);
+        *sig = sig_mix(*sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+        if (prim < 0) break;
+        o_hit h;
+        hit_info(&prims[prim], o, d, t, &h);
+        double le[3];
+        emitted(&prims[prim], h.front, le);
+        if (le[0] > 0.0 || le[1] > 0.0 || le[2] > 0.0) {
+            uint32_t nb = seg == 1 ? n_b0 : 1u;
+            double wb = 1.0;
+            if (is_rect_emitter(&prims[prim]) && lights->n)
+                wb = power_weight((double)nb * pb_prev, light_pdf(&prims[prim], d, (double)t, lights->n));
+            if (seg == 1) {
+                for (int c = 0; c < 3; c++) first_emit[c] = le[c] * wb;
+            } else {
+                for (int c = 0; c < 3; c++) L[c] += beta[c] * le[c] * wb;
+            }
+        }
+        o_record rec;
+        make_record(&prims[prim], (uint32_t)prim, &h, d, &rec);
+        double dl[3] = {0.0, 0.0, 0.0};
+        *sig = sig_mix(*sig, nee_sample(blob, lights, &rec, seg < max_depth ? 1u : 0u, k0, k1, c0, c1,
+                                        PURPOSE_LIGHT + 16u * seg, dl));
+        for (int c = 0; c < 3; c++) L[c] += beta[c] * dl[c];
+        if (seg == max_depth) break;
+        uint32_t r[4];
+        philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg, r);
+        int cont = u01(r[0]) < RR_CONTINUE;
+        *sig = sig_mix(*sig, (uint32_t)cont);
+        if (!cont) break;
+        for (int c = 0; c < 3; c++) beta[c] /= (double)RR_CONTINUE;
+        o_sample s;
+        sample_bsdf(&rec, k0, k1, c0, c1, PURPOSE_BOUNCE + 16u * seg, &s);
+        *sig = sig_mix(*sig, sample_word(&s));
+        if (!s.valid) break;
+        for (int c = 0; c < 3; c++) beta[c] *= s.w[c];
+        double fc[3];
+        bsdf_eval(&rec, s.wi, fc, &pb_prev);
+        for (int k = 0; k < 3; k++) {
+            o[k] = h.p[k];
+            d[k] = s.wi[k];
+        }
+    }
+}
+
 /* Camera ray through pixel (px, py) with jitter (jx, jy). */
 static void camera_ray(const o_header* hd, uint32_t W, uint32_t H, uint32_t px, uint32_t py, float jx, float jy,
                        float o[3], float d[3])
@@ -765,8 +971,8 @@ static void cache_value(const o_cfg* c, const double* params, const o_frame* fd,
 }
 
 static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
-                           uint32_t pix, double out[3], double lc_out[3], double lr_out[3], uint64_t sig[2],
-                           uint32_t* count, double* row_n)
+                           const o_lights* lights, uint32_t pix, double out[3], double lc_out[3], double lr_out[3],
+                           uint64_t sig[2], uint32_t* count, double* row_n)
 {
     /* row_n (optional): cache value of each of the N + M rows, 0 for rows
      * whose sample is invalid or whose pixel has no camera hit */
@@ -792,6 +998,12 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
         emitted(&prims[prim], h.front, Le);
         o_record rec;
         make_record(&prims[prim], (uint32_t)prim, &h, d, &rec);
+        if (lights) {
+            /* direct light at x: one light sample against the M residual directions */
+            double dl[3] = {0.0, 0.0, 0.0};
+            sp = sig_mix(sp, nee_sample(blob, lights, &rec, fd->n_resid, k0, k1, pix, 0u, PURPOSE_LIGHT, dl));
+            for (int k = 0; k < 3; k++) Le[k] += dl[k];
+        }
 
         for (uint32_t i = 0; i < fd->n_cache; i++) {
             o_sample s;
@@ -813,7 +1025,15 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             sp = sig_mix(sp, sample_word(&s));
             if (!s.valid) continue;
             double Li[3], nv[3];
-            trace_path(blob, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, Li, &sp);
+            if (lights) {
+                double fc[3], pb, e1[3];
+                bsdf_eval(&rec, s.wi, fc, &pb);
+                trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, fd->n_resid, pb, Li, e1,
+                               &sp);
+                for (int k = 0; k < 3; k++) Le[k] += s.w[k] * e1[k] / (double)fd->n_resid;
+            } else {
+                trace_path(blob, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, Li, &sp);
+            }
             cache_value(c, params, fd, &rec, s.wi, nv);
             for (int k = 0; k < 3; k++) Lr[k] += s.w[k] * (Li[k] - nv[k]);
             if (row_n)
@@ -841,12 +1061,19 @@ void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* bl
                          uint32_t* count, double* row_n)
 {
     const uint64_t S = (uint64_t)fd->n_cache + fd->n_resid;
+    o_lights* lights = NULL;
+    if (fd->light_mode == 1) {
+        lights = (o_lights*)malloc(sizeof(o_lights));
+        collect_lights(blob, lights);
+    }
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < (int64_t)n; i++) {
         uint32_t pix = pixels ? pixels[i] : (uint32_t)i;
-        estimate_pixel(c, params, blob, fd, pix, out + 3 * i, lc ? lc + 3 * i : NULL, lr ? lr + 3 * i : NULL,
-                       sig ? sig + 2 * i : NULL, count ? count + i : NULL, row_n ? row_n + 3 * S * i : NULL);
+        estimate_pixel(c, params, blob, fd, lights, pix, out + 3 * i, lc ? lc + 3 * i : NULL,
+                       lr ? lr + 3 * i : NULL, sig ? sig + 2 * i : NULL, count ? count + i : NULL,
+                       row_n ? row_n + 3 * S * i : NULL);
     }
+    free(lights);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -855,12 +1082,18 @@ void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* bl
 /* ------------------------------------------------------------------------ */
 
 void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint32_t frame, uint64_t seed,
-                   uint32_t max_depth, o_record* recs, float* dirs, double* targets, uint64_t* sig)
+                   uint32_t max_depth, uint32_t light_mode, o_record* recs, float* dirs, double* targets,
+                   uint64_t* sig)
 {
     const o_header* hd = (const o_header*)blob;
     const o_prim* prims = scene_prims(blob);
     uint32_t k0 = (uint32_t)seed, k1 = frame ^ 0x80000000u;
     uint64_t P = (uint64_t)W * H;
+    o_lights* lights = NULL;
+    if (light_mode == 1) {
+        lights = (o_lights*)malloc(sizeof(o_lights));
+        collect_lights(blob, lights);
+    }
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t ti = 0; ti < (int64_t)T; ti++) {
         uint32_t tr = (uint32_t)ti;
@@ -888,7 +1121,13 @@ void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint
             sample_bsdf(&rec, k0, k1, tr, 0u, PURPOSE_RESID_DIR, &s);
             sg = sig_mix(sg, sample_word(&s));
             if (s.valid) {
-                trace_path(blob, rec.p, s.wi, k0, k1, tr, 0u, max_depth, tg, &sg);
+                if (lights) {
+                    /* target = L_ind: the first hit's emission is direct light */
+                    double e1[3];
+                    trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, tr, 0u, max_depth, 0u, 0.0, tg, e1, &sg);
+                } else {
+                    trace_path(blob, rec.p, s.wi, k0, k1, tr, 0u, max_depth, tg, &sg);
+                }
                 for (int k = 0; k < 3; k++) dir[k] = s.wi[k];
             } else {
                 rec.flags &= ~1u; /* no usable direction: excluded from the loss */
@@ -897,6 +1136,7 @@ void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint
         recs[ti] = rec;
         if (sig) sig[ti] = sg;
     }
+    free(lights);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1114,6 +1354,22 @@ void orc_trace_path(const uint8_t* blob, const float o[3], const float d[3], uin
 {
     uint64_t sg = SIG_INIT;
     trace_path(blob, o, d, k0, k1, c0, c1, max_depth, L, &sg);
+}
+
+/* One NEE sample at a shading record (light mode 1 machinery, for the
+ * pins): adds the weighted contribution into out, returns the decision
+ * word. */
+uint32_t orc_nee_sample(const uint8_t* blob, const o_record* rec, uint32_t n_b, uint32_t k0, uint32_t k1, uint32_t c0,
+                        uint32_t c1, uint32_t c3, double out[3])
+{
+    o_lights lights;
+    collect_lights(blob, &lights);
+    return nee_sample(blob, &lights, rec, n_b, k0, k1, c0, c1, c3, out);
+}
+
+void orc_bsdf_eval(const o_record* rec, const float wi[3], double fcos[3], double* pdf)
+{
+    bsdf_eval(rec, wi, fcos, pdf);
 }
 
 int orc_num_threads(void)

@@ -34,7 +34,7 @@ class OFrame(ctypes.Structure):
         ("n_cache", ctypes.c_uint32), ("n_resid", ctypes.c_uint32),
         ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("cache_mode", ctypes.c_uint32),
-        ("pad", ctypes.c_uint32), ("cache_const", ctypes.c_double * 3),
+        ("light_mode", ctypes.c_uint32), ("cache_const", ctypes.c_double * 3),
     ]
 
 
@@ -55,7 +55,10 @@ def lib():
         L.orc_mlp.argtypes = [P, P, P, P]
         L.orc_query.argtypes = [P, P, P, P, u64, P]
         L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P, P]
-        L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, P, P, P, P]
+        L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, u32, P, P, P, P]
+        L.orc_nee_sample.argtypes = [P, P, u32, u32, u32, u32, u32, u32, P]
+        L.orc_nee_sample.restype = u32
+        L.orc_bsdf_eval.argtypes = [P, P, P, P]
         L.orc_train_loss_grad.argtypes = [P, P, P, P, P, u64, P, P]
         L.orc_train_loss_grad.restype = f64
         L.orc_query_grad.argtypes = [P, P, P, P, P, u64, P]
@@ -85,8 +88,8 @@ def ocfg(cfg) -> OCfg:
 
 
 def oframe(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode=0,
-           cache_const=(0.0, 0.0, 0.0)) -> OFrame:
-    f = OFrame(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode, 0)
+           cache_const=(0.0, 0.0, 0.0), light_mode=0) -> OFrame:
+    f = OFrame(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode, light_mode)
     for k in range(3):
         f.cache_const[k] = float(cache_const[k])
     return f
@@ -185,15 +188,35 @@ def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None, rows=False):
     return res
 
 
-def gen_train(scene_blob, width, height, T, frame, seed, max_depth, record_dtype):
+def gen_train(scene_blob, width, height, T, frame, seed, max_depth, record_dtype, light_mode=0):
     blob = np.ascontiguousarray(scene_blob, np.uint8)
     recs = np.zeros(T, record_dtype)
     dirs = np.zeros((T, 3), np.float32)
     tg = np.zeros((T, 3), np.float64)
     sig = np.zeros(T, np.uint64)
-    lib().orc_gen_train(_ptr(blob), width, height, T, frame, seed, max_depth,
+    lib().orc_gen_train(_ptr(blob), width, height, T, frame, seed, max_depth, light_mode,
                         _ptr(recs), _ptr(dirs), _ptr(tg), _ptr(sig))
     return recs, dirs, tg, sig
+
+
+def nee_sample(scene_blob, rec, n_b, key, ctr013):
+    """One light sample at a record (light mode 1): (contribution f64 (3,), decision word)."""
+    blob = np.ascontiguousarray(scene_blob, np.uint8)
+    r = np.ascontiguousarray(rec)
+    out = np.zeros(3, np.float64)
+    word = lib().orc_nee_sample(_ptr(blob), _ptr(r), n_b, key[0], key[1], ctr013[0], ctr013[1], ctr013[2],
+                                _ptr(out))
+    return out, int(word)
+
+
+def bsdf_eval(rec, wi):
+    """(f_r cos, sampling density) of the record's material for direction wi."""
+    r = np.ascontiguousarray(rec)
+    w = np.ascontiguousarray(wi, np.float32)
+    fc = np.zeros(3, np.float64)
+    pdf = np.zeros(1, np.float64)
+    lib().orc_bsdf_eval(_ptr(r), _ptr(w), _ptr(fc), _ptr(pdf))
+    return fc, float(pdf[0])
 
 
 def loss_grad(cfg, params, recs, dirs, targets, den_fixed=None):

@@ -253,6 +253,24 @@ def scene_at_frame(scene: Scene, frame: int) -> Scene:
     return out
 
 
+def floor_light_scene(width: int, height: int, rho: float = 0.5, emission: float = 4.0,
+                      glossy: bool = False, roughness: float = 0.3) -> Scene:
+    """A unit floor (y = 0, normal +y, albedo ``rho``) under a 0.3 x 0.3
+    emitter at height 0.5 facing -y; the camera looks at the floor from
+    above.  Direct light on the floor has a closed form (the irradiance of a
+    polygonal emitter)."""
+    prims = np.zeros(2, PRIM_DTYPE)
+    mat = MAT_GGX if glossy else MAT_LAMBERT
+    _fill_rect(prims[0], (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (rho,) * 3, roughness, mat)
+    _fill_rect(prims[1], (0.35, 0.5, 0.35), (0.3, 0.0, 0.0), (0.0, 0.0, 0.3), (0.0,) * 3, 1.0, MAT_BLACK,
+               emission=(emission,) * 3)
+    origin, top_left, horizontal, vertical = _camera((0.5, 0.9, 0.5), 60.0, width, height)
+    # look down (-y): rotate the +z camera frame about x
+    top_left = origin + np.array([top_left[0] - origin[0], -1.0, -(top_left[1] - origin[1])])
+    vertical = np.array([0.0, 0.0, -vertical[1]])
+    return Scene(_header(2, (origin, top_left, horizontal, vertical)), prims, width, height)
+
+
 def furnace_scene(width: int, height: int, rho: float = 0.5, emission: float = 1.0) -> Scene:
     """White-furnace scene: the camera sits at the centre of a sphere whose
     inner surface is Lambertian with albedo ``rho`` and emits ``emission``

@@ -687,3 +687,99 @@ def test_mrse_closed_forms(oracle):
     assert abs(oracle.mrse(img, ref, 1e-2) - np.mean(ref ** 2 / (ref ** 2 + 1e-2))) < 1e-14
     zero = np.zeros((10, 3))
     assert abs(oracle.mrse(zero + 0.1, zero, 1e-2) - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Light mode 1: L_i = L_ind + L_nee (eq. Lsplit), NEE + MIS
+# ---------------------------------------------------------------------------
+
+def _polygon_irradiance(x, n, verts):
+    """Irradiance at x (normal n) from a unit-radiance polygon: Lambert's
+    formula, 1/2 sum_i angle(r_i, r_i+1) (n . unit(r_i x r_i+1))."""
+    r = [np.asarray(v, np.float64) - x for v in verts]
+    r = [v / np.linalg.norm(v) for v in r]
+    total = 0.0
+    for i in range(len(r)):
+        a, b = r[i], r[(i + 1) % len(r)]
+        c = np.cross(a, b)
+        total += 0.5 * math.acos(np.clip(np.dot(a, b), -1, 1)) * np.dot(n, c / np.linalg.norm(c))
+    return abs(total)
+
+
+@pytest.mark.parametrize("x", [(0.5, 0.0, 0.5), (0.1, 0.0, 0.8), (0.9, 0.0, 0.2)])
+def test_nee_light_sampling_matches_polygon_irradiance(oracle, x):
+    """Pure light sampling (no BSDF technique) at a Lambertian floor point
+    averages to rho / pi * L_e * E, E from the closed form."""
+    rho, Le = 0.5, 4.0
+    sc = scenes.floor_light_scene(8, 8, rho=rho, emission=Le)
+    rec = _lambert_record(n=(0.0, 1.0, 0.0), albedo=(rho,) * 3, p=x)
+    n = 40000
+    vals = np.empty(n)
+    words = set()
+    for i in range(n):
+        out, word = oracle.nee_sample(sc.blob(), rec, 0, (1, 2), (i, 0, 7))
+        vals[i] = out[0]
+        words.add(word >> 16)
+    verts = [(0.35, 0.5, 0.35), (0.65, 0.5, 0.35), (0.65, 0.5, 0.65), (0.35, 0.5, 0.65)]
+    expect = rho / math.pi * Le * _polygon_irradiance(np.asarray(x, np.float64), np.array([0.0, 1.0, 0.0]), verts)
+    se = vals.std() / math.sqrt(n)
+    assert abs(vals.mean() - expect) < 4 * se + 1e-12, (vals.mean(), expect, se)
+    assert words == {3}  # every sample sees the emitter from its front side, unoccluded
+
+
+def test_bsdf_density_matches_sampler(oracle):
+    """E[1 / p(w)] over the sampler's valid directions is the solid angle of
+    the upper hemisphere, 2 pi, for the density used in the MIS weights, and
+    f cos / p equals the sample weight."""
+    for mat, rough in ((scenes.MAT_LAMBERT, 1.0), (scenes.MAT_GGX, 0.3), (scenes.MAT_GGX, 0.8)):
+        nn = np.array([0.2, 0.9, 0.1])
+        wo = np.array([0.6, 0.7, -0.39])
+        rec = _lambert_record(n=nn, material=mat, roughness=rough, wo=wo / np.linalg.norm(wo))
+        n = 20000
+        inv = np.zeros(n)
+        for i in range(n):
+            wi, w, valid, _, _ = oracle.sample_bsdf(rec, (3, 4), (i, 0, 2))
+            if not valid:
+                continue
+            fc, pdf = oracle.bsdf_eval(rec, wi)
+            inv[i] = 1.0 / pdf
+            assert np.allclose(fc / pdf, w, rtol=1e-9)
+        se = inv.std() / math.sqrt(n)
+        assert abs(inv.mean() - 2 * math.pi) < 4 * se, (mat, rough, inv.mean(), se)
+
+
+@pytest.mark.parametrize("glossy", [False, True])
+def test_nee_estimator_has_path_tracing_expectation(oracle, glossy):
+    """With a zero cache, the NEE + MIS estimator at depth D and plain BSDF
+    path tracing at depth D + 1 both estimate the same truncated integral
+    (light paths of up to D + 1 bounces): their image means agree within 4
+    standard errors; the NEE image is far less noisy."""
+    W = H = 16
+    sc = scenes.cornell_scene(W, H, seed=3, n_prims=12, glossy=glossy)
+    cfg = scenes.config_small()
+    D = 3
+    means = {0: [], 1: []}
+    for f in range(48):
+        for mode, depth in ((0, D + 1), (1, D)):
+            o = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(W, H, 0, 2, depth, f, 5, cache_mode=1,
+                                                                    light_mode=mode))
+            means[mode].append(o["pixel"].mean(axis=0))
+    a = np.array(means[0])
+    b = np.array(means[1])
+    diff = a.mean(0) - b.mean(0)
+    se = np.sqrt(a.var(0) / len(a) + b.var(0) / len(b))
+    assert np.all(np.abs(diff) < 4 * se), (diff, se)
+    assert b.std(0).mean() < a.std(0).mean()
+
+
+def test_nee_training_targets_exclude_first_emission(oracle):
+    """In light mode 1 a training target is L_ind: records whose direction
+    hits the emitter first get no credit for its emission, and targets are
+    non-zero far more often than with pure BSDF paths."""
+    sc = scenes.cornell_scene(32, 32, seed=1)
+    T = 4000
+    _, _, tg0, _ = oracle.gen_train(sc.blob(), 32, 32, T, 0, 1, 4, scenes.RECORD_DTYPE)
+    _, _, tg1, _ = oracle.gen_train(sc.blob(), 32, 32, T, 0, 1, 4, scenes.RECORD_DTYPE, light_mode=1)
+    nz0 = (tg0.max(1) > 0).mean()
+    nz1 = (tg1.max(1) > 0).mean()
+    assert nz1 > 10 * nz0 and nz1 > 0.3, (nz0, nz1)
