@@ -62,6 +62,8 @@ def parse_args():
                     help="frame: the 1080p frame step (default); train: the training step alone on "
                          "2^16 / 2^18 / 2^20 samples of the analytic radiance field; serve: the frame-request "
                          "server on a Poisson stream of mixed-resolution requests over 8 resident scenes")
+    ap.add_argument("--light-mode", type=int, choices=[0, 1], default=0,
+                    help="1: the cache carries L_ind, direct light by NEE + MIS (frame and serve workloads)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-low-budget-gb", type=float, default=1.0)
@@ -236,10 +238,11 @@ class FrameRunner:
         N, a = self.N, self.args
         sc = self.scene_dev[f % 60] if scene is None else scene
         h = self.cache.h
-        d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims)
+        d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
+                         light_mode=a.light_mode)
         N.nirc_estimate_frame(h, sc, d, self.img)
         N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs, self.dirs,
-                         self.tgts)
+                         self.tgts, light_mode=a.light_mode)
         N.nirc_train_step(h, self.recs, self.dirs, self.tgts, self.loss)
         N.nirc_frame_mrse(self.img, ref, self.mrse)
 
@@ -406,6 +409,7 @@ def run_ours(args):
                                  "fp8": "fp8_e4m3_tc (hidden layers)"}[args.precision],
                    "frames": f"{first}..{first + args.steps - 1} (mod 60)",
                    "l2": "no flush: per-frame working set (~0.6 GB of records, rows, images, tables) > 129 MB L2",
+                   "light_mode": args.light_mode,
                    "parallelism": f"replicas x{world}"},
         "p50_ms": float(np.percentile(res["step_ms"], 50)), "p99_ms": float(np.percentile(res["step_ms"], 99)),
         "frame_mrse": res["mrse"], "mrse_reference": f"{ref_spp} spp path tracing, depth 16, frame {last_frame}",
@@ -637,7 +641,7 @@ def serve_requests(n, n_scenes, seed):
     return out
 
 
-def _serve_run(N, srv, reqs, arrivals):
+def _serve_run(N, srv, reqs, arrivals, light_mode=0):
     """Submit reqs[i] at server time arrivals[i] (seconds after the start);
     returns per-request (latency, batch size) and the makespan."""
     import torch
@@ -648,7 +652,7 @@ def _serve_run(N, srv, reqs, arrivals):
     while len(lat) < n:
         now = srv.clock() - t0
         while i < n and arrivals[i] <= now:
-            srv.submit(*reqs[i])
+            srv.submit(*reqs[i], light_mode=light_mode)
             i += 1
         for c in srv.poll(wait=False):
             if c.status != 0:
@@ -712,9 +716,10 @@ def run_serve_bench(args):
     # warm-up: every scene, every size once (graph instantiation, first-touch)
     warm = serve_requests(32, n_scenes, seed=99)
     warm = [(10_000 + r[0],) + r[1:] for r in warm]
-    _serve_run(N, srv, warm, [0.0] * len(warm))
+    lm = args.light_mode
+    _serve_run(N, srv, warm, [0.0] * len(warm), lm)
     reqs = serve_requests(n, n_scenes, seed=5)
-    lat, bs, mk = _serve_run(N, srv, reqs, [0.0] * n)
+    lat, bs, mk = _serve_run(N, srv, reqs, [0.0] * n, lm)
     sat = _serve_summary(lat, bs, mk, reqs)
     results["saturated (all at t=0)"] = sat
     rng = np.random.default_rng(17)
@@ -722,7 +727,7 @@ def run_serve_bench(args):
         rate = frac * sat["frames_per_s"]
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
         reqs = [(r[0] + int(frac * 10) * 100_000,) + r[1:] for r in serve_requests(n, n_scenes, seed=6)]
-        lat, bs, mk = _serve_run(N, srv, reqs, arrivals)
+        lat, bs, mk = _serve_run(N, srv, reqs, arrivals, lm)
         results[f"poisson {frac:.1f}x"] = dict(_serve_summary(lat, bs, mk, reqs), offered_per_s=rate)
     st = srv.stats()
     srv.close()
@@ -731,7 +736,7 @@ def run_serve_bench(args):
     rate = 0.8 * sat["frames_per_s"]
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
     reqs = [(r[0] + 900_000,) + r[1:] for r in serve_requests(n, n_scenes, seed=7)]
-    lat, bs, mk = _serve_run(N, srv, reqs, arrivals)
+    lat, bs, mk = _serve_run(N, srv, reqs, arrivals, lm)
     st_low = srv.stats()
     results[f"poisson 0.8x, {args.serve_low_budget_gb:g} GB budget"] = dict(
         _serve_summary(lat, bs, mk, reqs), offered_per_s=rate, arena_peak_gb=st_low["arena_peak_bytes"] / 2**30)
@@ -751,7 +756,7 @@ def run_serve_bench(args):
                                f"256^2/512^2/1280x720/1920x1080, N uniform in 4/8/16/32, M=1, depth 5; one training "
                                f"pass ({T} paths) + Adam step per served frame",
                    "budget_gb": args.serve_budget_gb, "slots": 8, "max_batches": 2, "graphs": True,
-                   "deterministic_training": bool(args.serve_deterministic),
+                   "deterministic_training": bool(args.serve_deterministic), "light_mode": args.light_mode,
                    "latency": "server clock from submission to the completion of the request's batch on the device"},
         "runs": results,
         "server_stats": {k: st[k] for k in ("batches", "graph_instantiations", "graph_updates", "max_batch_seen",

@@ -129,7 +129,17 @@ typedef struct nirc_frame_desc {
     uint32_t cache_mode;     /* 0 network, 1 zero cache (n = 0: plain path
                                 tracing), 2 constant cache n = cache_const */
     float cache_const[3];
-    uint32_t pad;
+    uint32_t light_mode;     /* 0: the cache and the residual paths carry the
+                                full incident radiance, pure BSDF paths.
+                                1: L_i = L_ind + L_nee (eq. Lsplit): direct
+                                light by next-event estimation on emitting
+                                rectangles (one light sample at the shading
+                                point and at every path vertex) combined with
+                                BSDF sampling by the power heuristic (the M
+                                residual directions are the BSDF technique at
+                                the shading point); cache, residual paths and
+                                training targets carry L_ind.  Spherical
+                                emitters are reached by BSDF sampling only. */
 } nirc_frame_desc;
 
 #define NIRC_MAX_PRIMS 1024u
@@ -230,10 +240,13 @@ nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d_scene, con
  * incident radiance as target.  Records whose path has no usable direction
  * get flags bit 0 cleared (excluded from the loss).  Philox key word 1 is
  * frame ^ 0x80000000 so training draws never repeat rendering draws.
- * d_records = T x 64 B, d_dirs = T x 3, d_targets = T x 3. */
+ * light_mode as in nirc_frame_desc (1: targets are L_ind estimates with NEE
+ * + MIS along the path).  d_records = T x 64 B, d_dirs = T x 3,
+ * d_targets = T x 3. */
 nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width,
                            uint32_t height, uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth,
-                           nirc_record* d_records, float* d_dirs, float* d_targets, void* stream);
+                           uint32_t light_mode, nirc_record* d_records, float* d_dirs, float* d_targets,
+                           void* stream);
 
 /* One Adam step on the relative L2 loss of eq. 12 with p_r = 1:
  *   L = 1/(3n) sum_t sum_rgb valid_t (f - n)^2 / (sg(n)^2 + loss_eps)

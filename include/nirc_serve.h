@@ -70,7 +70,7 @@ typedef struct nirc_request {
     uint32_t n_cache, n_resid;   /* N (0..1024), M (0..64) */
     uint32_t max_depth;          /* 1..64 */
     uint32_t frame;              /* frame index: Philox key word 1 and scene key frame (mod n_frames) */
-    uint32_t pad;
+    uint32_t light_mode;         /* as in nirc_frame_desc (frame and training pass) */
 } nirc_request;
 
 typedef struct nirc_completion {

@@ -397,6 +397,20 @@ static double dot3d(const double a[3], const double b[3])
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+/* GGX denominator dd = 1 - cos^2 (1 - a2) = sin^2 + a2 cos^2 of the angle
+ * between n and h, from the cross and dot products normalised by the
+ * vectors' lengths: no cancellation near the specular peak and no
+ * dependence on the binary32 rounding of the stored unit normal (which
+ * would move 1 - cos^2 by ~1e-7, a large relative change of dd at small
+ * roughness). */
+static double ggx_dd(const double n[3], const double h[3], double a2)
+{
+    double c[3] = {n[1] * h[2] - n[2] * h[1], n[2] * h[0] - n[0] * h[2], n[0] * h[1] - n[1] * h[0]};
+    double nh = dot3d(n, h);
+    double norm = dot3d(n, n) * dot3d(h, h);
+    return (dot3d(c, c) + a2 * nh * nh) / norm;
+}
+
 /* f_r(x, wi, wo) cos(theta_i) / p(wi) of the Lambertian + GGX material with
  * the one-sample mixture (1/2 cosine, 1/2 GGX visible normals), FP64. */
 static void ggx_mix_weight(const o_record* rec, const float wif[3], double w[3])
@@ -410,11 +424,10 @@ static void ggx_mix_weight(const o_record* rec, const float wif[3], double w[3])
     double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
     double hl = sqrt(dot3d(h, h));
     for (int k = 0; k < 3; k++) h[k] /= hl;
-    double ch = dot3d(n, h);
     double oh = dot3d(wo, h);
     if (oh < 0.0) oh = 0.0;
     if (oh > 1.0) oh = 1.0;
-    double dd = ch * ch * (a2 - 1.0) + 1.0;
+    double dd = ggx_dd(n, h, a2);
     double D = a2 / (O_PI * dd * dd);
     double lam_o = sqrt(a2 + (1.0 - a2) * co * co);
     double lam_i = sqrt(a2 + (1.0 - a2) * ci * ci);
@@ -795,11 +808,10 @@ static void bsdf_eval(const o_record* rec, const float wif[3], double fcos[3], d
     double h[3] = {wo[0] + wi[0], wo[1] + wi[1], wo[2] + wi[2]};
     double hl = sqrt(dot3d(h, h));
     for (int k = 0; k < 3; k++) h[k] /= hl;
-    double ch = dot3d(n, h);
     double oh = dot3d(wo, h);
     if (oh < 0.0) oh = 0.0;
     if (oh > 1.0) oh = 1.0;
-    double dd = ch * ch * (a2 - 1.0) + 1.0;
+    double dd = ggx_dd(n, h, a2);
     double D = a2 / (O_PI * dd * dd);
     double lam_o = sqrt(a2 + (1.0 - a2) * co * co);
     double lam_i = sqrt(a2 + (1.0 - a2) * ci * ci);

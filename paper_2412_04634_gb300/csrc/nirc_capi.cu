@@ -172,8 +172,9 @@ nirc_status check_frame_args(const char* who, const void* scene, const nirc_fram
         return NIRC_ERR_INVALID;
     }
     if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
-        fd.max_depth > 64 || fd.cache_mode > 2 || P > 0xFFFFFFFFull) {
-        set_error("%s: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64)", who, NIRC_MAX_PRIMS);
+        fd.max_depth > 64 || fd.cache_mode > 2 || fd.light_mode > 1 || P > 0xFFFFFFFFull) {
+        set_error("%s: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64, light_mode 0..1)", who,
+                  NIRC_MAX_PRIMS);
         return NIRC_ERR_INVALID;
     }
     if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
@@ -500,8 +501,8 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
 }
 
 nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width, uint32_t height,
-                           uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* d_records,
-                           float* d_dirs, float* d_targets, void* stream) {
+                           uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, uint32_t light_mode,
+                           nirc_record* d_records, float* d_dirs, float* d_targets, void* stream) {
     if (!h) {
         set_error("nirc_gen_train: handle is NULL");
         return NIRC_ERR_INVALID;
@@ -512,14 +513,15 @@ nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims
         return NIRC_ERR_INVALID;
     }
     if (n_prims < 1 || n_prims > NIRC_MAX_PRIMS || width == 0 || height == 0 ||
-        (uint64_t)width * height > 0xFFFFFFFFull || max_depth < 1 || max_depth > 64 || T > 0xFFFFFFFFull) {
+        (uint64_t)width * height > 0xFFFFFFFFull || max_depth < 1 || max_depth > 64 || T > 0xFFFFFFFFull ||
+        light_mode > 1) {
         set_error("nirc_gen_train: argument out of range");
         return NIRC_ERR_INVALID;
     }
     cudaStream_t st = (cudaStream_t)stream;
     timer_begin(h, NIRC_K_TRAIN_RECORDS, st);
-    cudaError_t e = launch_gen_train(h, d_scene, n_prims, width, height, T, frame, seed, max_depth, d_records, d_dirs,
-                                     d_targets, st);
+    cudaError_t e = launch_gen_train(h, d_scene, n_prims, width, height, T, frame, seed, max_depth, light_mode,
+                                     d_records, d_dirs, d_targets, st);
     timer_end(h, NIRC_K_TRAIN_RECORDS, st);
     return cuda_status(e, "nirc_gen_train");
 }

@@ -69,7 +69,8 @@ enum : uint32_t {
     PURPOSE_RESID_DIR = 3,
     PURPOSE_BOUNCE = 4,  // + 16 * segment
     PURPOSE_RR = 5,      // + 16 * segment
-    PURPOSE_TRAIN_PICK = 6
+    PURPOSE_TRAIN_PICK = 6,
+    PURPOSE_LIGHT = 7    // + 16 * segment (0: the shading point), light mode 1
 };
 
 constexpr float kTMin = 1e-4f;
@@ -333,19 +334,34 @@ __device__ __forceinline__ V3 ggx_vndf_reflect(V3 wo, V3 t, V3 b, V3 n, float al
 
 // f_r cos / p of the Lambertian + GGX material under the 1/2 cosine + 1/2
 // visible-normal mixture (FP32, continuous).
+// a d - b c with one rounding error (Kahan's FMA algorithm).
+__device__ __forceinline__ float det2(float a, float b, float c, float d) {
+    const float w = b * c;
+    const float e = __fmaf_rn(-b, c, w);
+    const float f = __fmaf_rn(a, d, -w);
+    return f + e;
+}
+
+// GGX denominator dd = sin^2 + a2 cos^2 of the angle between n and the
+// (unnormalised) half vector s = wo + wi, from the cross and dot products
+// normalised by the lengths: no cancellation near the specular peak, where
+// 1 - cos^2 (1 - a2) in FP32 loses all accuracy at small roughness.
+__device__ __forceinline__ float ggx_dd(V3 n, float sx, float sy, float sz, float a2) {
+    const float cx = det2(n.y, n.z, sy, sz), cy = det2(n.z, n.x, sz, sx), cz = det2(n.x, n.y, sx, sy);
+    const float ns = n.x * sx + n.y * sy + n.z * sz;
+    const float norm = (n.x * n.x + n.y * n.y + n.z * n.z) * (sx * sx + sy * sy + sz * sz);
+    return __fdividef(cx * cx + cy * cy + cz * cz + a2 * ns * ns, norm);
+}
+
 __device__ __forceinline__ float3 ggx_mix_weight(V3 n, V3 wo, V3 wi, float3 albedo, float rough) {
     const float alpha = __fmul_rn(rough, rough);
     const float a2 = alpha * alpha;
     const float ci = n.x * wi.x + n.y * wi.y + n.z * wi.z;
     const float co = n.x * wo.x + n.y * wo.y + n.z * wo.z;
-    float hx = wo.x + wi.x, hy = wo.y + wi.y, hz = wo.z + wi.z;
-    const float hinv = rsqrtf(hx * hx + hy * hy + hz * hz);
-    hx *= hinv;
-    hy *= hinv;
-    hz *= hinv;
-    const float ch = n.x * hx + n.y * hy + n.z * hz;
-    const float oh = fminf(fmaxf(wo.x * hx + wo.y * hy + wo.z * hz, 0.0f), 1.0f);
-    const float dd = ch * ch * (a2 - 1.0f) + 1.0f;
+    const float sx = wo.x + wi.x, sy = wo.y + wi.y, sz = wo.z + wi.z;
+    const float hinv = rsqrtf(sx * sx + sy * sy + sz * sz);
+    const float oh = fminf(fmaxf((wo.x * sx + wo.y * sy + wo.z * sz) * hinv, 0.0f), 1.0f);
+    const float dd = ggx_dd(n, sx, sy, sz, a2);
     const float D = __fdividef(a2, kPi * dd * dd);
     const float lam_o = sqrtf(a2 + (1.0f - a2) * co * co);
     const float lam_i = sqrtf(a2 + (1.0f - a2) * ci * ci);
@@ -359,6 +375,67 @@ __device__ __forceinline__ float3 ggx_mix_weight(V3 n, V3 wo, V3 wi, float3 albe
     const float pdf = 0.5f * ci * kInvPi + 0.5f * pdf_s;
     const float k = __fdividef(ci, pdf);
     return make_float3((albedo.x * kInvPi + fs) * k, (albedo.y * kInvPi + fs) * k, (albedo.z * kInvPi + fs) * k);
+}
+
+// a . b as if accumulated in twice the precision, then rounded (compensated
+// dot product of Ogita, Rump and Oishi 2005: error-free products by FMA,
+// error-free sums by TwoSum).  Used for cosines that cancel (grazing light
+// samples), where a plain FP32 dot loses most of its relative accuracy.
+__device__ __forceinline__ float dot_acc(V3 a, V3 b) {
+    float s = __fmul_rn(a.x, b.x);
+    float c = __fmaf_rn(a.x, b.x, -s);
+    const float qa[2] = {a.y, a.z}, qb[2] = {b.y, b.z};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float p = __fmul_rn(qa[k], qb[k]);
+        const float pe = __fmaf_rn(qa[k], qb[k], -p);
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(pe, se));
+    }
+    return __fadd_rn(s, c);
+}
+
+// f_r cos(theta_i) and the sampling density p(wi) (solid angle) of the
+// material for an arbitrary direction (next-event estimation and MIS); both
+// 0 below the surface.  Same formulas as ggx_mix_weight, which is their
+// ratio for sampled directions; the cosines by the compensated dot.
+struct BsdfEval {
+    float3 fcos;
+    float pdf;
+};
+
+__device__ __forceinline__ BsdfEval bsdf_eval(V3 n, V3 wo, V3 wi, float3 albedo, float rough, uint32_t mat) {
+    BsdfEval r;
+    r.fcos = make_float3(0.f, 0.f, 0.f);
+    r.pdf = 0.f;
+    const float ci = dot_acc(n, wi);
+    if (mat == MAT_BLACK || !(ci > 0.f)) return r;
+    if (mat == MAT_LAMBERT) {
+        const float k = ci * kInvPi;
+        r.fcos = make_float3(albedo.x * k, albedo.y * k, albedo.z * k);
+        r.pdf = k;
+        return r;
+    }
+    const float alpha = __fmul_rn(rough, rough);
+    const float a2 = alpha * alpha;
+    const float co = dot_acc(n, wo);
+    const float sx = wo.x + wi.x, sy = wo.y + wi.y, sz = wo.z + wi.z;
+    const float hinv = rsqrtf(sx * sx + sy * sy + sz * sz);
+    const float oh = fminf(fmaxf((wo.x * sx + wo.y * sy + wo.z * sz) * hinv, 0.0f), 1.0f);
+    const float dd = ggx_dd(n, sx, sy, sz, a2);
+    const float D = __fdividef(a2, kPi * dd * dd);
+    const float lam_o = sqrtf(a2 + (1.0f - a2) * co * co);
+    const float lam_i = sqrtf(a2 + (1.0f - a2) * ci * ci);
+    const float m = 1.0f - oh;
+    const float m2 = m * m;
+    const float F = kF0 + (1.0f - kF0) * (m2 * m2 * m);
+    const float fs = __fdividef(F * D, 2.0f * (co * lam_i + ci * lam_o));
+    r.fcos = make_float3((albedo.x * kInvPi + fs) * ci, (albedo.y * kInvPi + fs) * ci, (albedo.z * kInvPi + fs) * ci);
+    r.pdf = 0.5f * ci * kInvPi + 0.5f * __fdividef(D, 2.0f * (co + lam_o));
+    return r;
 }
 
 struct BsdfSample {

@@ -116,8 +116,8 @@ cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const 
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig,
                                  uint32_t* count, cudaStream_t st);
 cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
-                             uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* recs,
-                             float* dirs, float* targets, cudaStream_t st);
+                             uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, uint32_t light_mode,
+                             nirc_record* recs, float* dirs, float* targets, cudaStream_t st);
 
 // nirc_cache_simt.cu
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,

@@ -14,6 +14,16 @@
 // Both kernels are persistent: each CTA stages the primitives' geometry in
 // shared memory and, for scenes of more than 16 primitives, builds its own
 // bounding-volume hierarchy there once, then loops over pixels (paths).
+//
+// Light mode 1 (template kNee; eq. Lsplit): L_i = L_ind + L_nee.  At the
+// shading point one light sample (uniform emitting rectangle, uniform point,
+// shadow ray) is combined by the power heuristic with the M residual
+// directions as the BSDF technique, whose first-hit emission joins the
+// direct part; along paths every vertex takes a light sample against the
+// continuation direction, and emission reached by a continuation is
+// weighted the same way.  The residual paths and the training targets then
+// carry L_ind, which is what the cache learns.  Shadow-ray decisions are
+// strict binary32, like every other decision.
 #include "nirc_bvh.cuh"
 #include "nirc_internal.h"
 
@@ -27,6 +37,12 @@ struct FrameArgs {
     uint32_t k0, k1;
 };
 
+// Emitting rectangles in primitive order (the light technique's choices).
+struct Lights {
+    const uint16_t* idx;
+    uint32_t n;
+};
+
 // Nearest-hit queries over the CTA's primitives (brute force or hierarchy).
 struct Tracer {
     const PrimGeom* prims;
@@ -37,6 +53,12 @@ struct Tracer {
         return bvh ? bvh_nearest(tree, prims, n, o, d, t) : trace_nearest(prims, n, o, d, t);
     }
 };
+
+// Shared bytes of the staged geometry and hierarchy (the light list follows, 16-byte aligned).
+__host__ __device__ __forceinline__ size_t pt_geom_bytes(uint32_t n_prims) {
+    const size_t b = (size_t)n_prims * sizeof(PrimGeom) + (n_prims >= kBvhMinPrims ? bvh_smem_bytes(n_prims) : 0);
+    return (b + 15) & ~(size_t)15;
+}
 
 // Stage the scene header and primitive geometry, build the hierarchy.
 __device__ __forceinline__ Tracer setup_scene(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
@@ -56,6 +78,144 @@ __device__ __forceinline__ Tracer setup_scene(const SceneHeader* __restrict__ hd
         __syncthreads();
     }
     return tr;
+}
+
+__device__ __forceinline__ bool rect_emitter(const Prim* __restrict__ Q) {
+    return __ldg(&Q->kind) == KIND_RECT &&
+           (__ldg(&Q->emission[0]) > 0.f || __ldg(&Q->emission[1]) > 0.f || __ldg(&Q->emission[2]) > 0.f);
+}
+
+// Thread 0 lists the emitting rectangles in primitive order (the order the
+// light choice indexes); every thread of the CTA calls it.
+__device__ __forceinline__ Lights collect_lights(const Prim* __restrict__ gp, uint32_t n_prims, uint16_t* s_idx,
+                                                 uint32_t* s_n) {
+    if (threadIdx.x == 0) {
+        uint32_t k = 0;
+        for (uint32_t i = 0; i < n_prims; ++i)
+            if (rect_emitter(gp + i)) s_idx[k++] = (uint16_t)i;
+        *s_n = k;
+    }
+    __syncthreads();
+    return Lights{s_idx, *s_n};
+}
+
+__device__ __forceinline__ float rect_area(const PrimGeom& g) {
+    const float cx = g.u_iuu.y * g.v_ivv.z - g.u_iuu.z * g.v_ivv.y;
+    const float cy = g.u_iuu.z * g.v_ivv.x - g.u_iuu.x * g.v_ivv.z;
+    const float cz = g.u_iuu.x * g.v_ivv.y - g.u_iuu.y * g.v_ivv.x;
+    return sqrtf(cx * cx + cy * cy + cz * cz);
+}
+
+// Solid-angle density of the light technique for direction d toward a point
+// at distance t on emitting rectangle g.
+__device__ __forceinline__ float light_pdf(const PrimGeom& g, V3 d, float t, uint32_t n_lights) {
+    const float cl = fabsf(dot_acc(V3{g.n_kind.x, g.n_kind.y, g.n_kind.z}, d));
+    return t * t / (cl * rect_area(g) * (float)n_lights);
+}
+
+__device__ __forceinline__ float power_weight(float na_pa, float nb_pb) {
+    const float a = na_pa * na_pa, b = nb_pb * nb_pb;
+    return a + b > 0.f ? a / (a + b) : 0.f;
+}
+
+// One light sample at a shading point (p, n, wo, material), MIS against n_b
+// BSDF samples; adds into out and returns the decision word
+// (emitter | geometry ok << 16 | visible << 17).
+__device__ __forceinline__ uint32_t nee_sample(const Tracer& tr, const Prim* __restrict__ gp, const Lights& lt, V3 p,
+                                               V3 n, V3 wo, float3 alb, float rough, uint32_t mat, uint32_t n_b,
+                                               uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t c3,
+                                               float3& out) {
+    if (lt.n == 0 || mat == MAT_BLACK) return 0u;
+    const U4 r = philox(k0, k1, c0, c1, 0u, c3);
+    const uint32_t e = __umulhi(r.x, lt.n);
+    const uint32_t li = lt.idx[e];
+    const PrimGeom& g = tr.prims[li];
+    const float u1 = u01(r.y), u2 = u01(r.z);
+    const V3 pt{__fadd_rn(__fadd_rn(g.a_r.x, __fmul_rn(u1, g.u_iuu.x)), __fmul_rn(u2, g.v_ivv.x)),
+                __fadd_rn(__fadd_rn(g.a_r.y, __fmul_rn(u1, g.u_iuu.y)), __fmul_rn(u2, g.v_ivv.y)),
+                __fadd_rn(__fadd_rn(g.a_r.z, __fmul_rn(u1, g.u_iuu.z)), __fmul_rn(u2, g.v_ivv.z))};
+    const V3 v = ssub(pt, p);
+    const float dist2 = sdot(v, v);
+    const float dist = __fsqrt_rn(dist2);
+    const V3 w = snormalize(v);
+    const float cx = sdot(n, w);
+    const float cl = -sdot(V3{g.n_kind.x, g.n_kind.y, g.n_kind.z}, w);
+    const Prim* L = gp + li;
+    const bool ok = cx > 0.f && (cl > 0.f || ((__ldg(&L->flags) & EMIT_TWO_SIDED) && cl < 0.f));
+    uint32_t word = e | ((uint32_t)ok << 16);
+    if (!ok) return word;
+    float t;
+    const int hit = tr.nearest(p, w, t);
+    const bool visible = hit == (int)li && fabsf(__fsub_rn(t, dist)) <= __fmul_rn(1e-3f, dist);
+    word |= (uint32_t)visible << 17;
+    if (!visible) return word;
+    const BsdfEval be = bsdf_eval(n, wo, w, alb, rough, mat);
+    const float pl = light_pdf(g, w, dist, lt.n);
+    const float k = power_weight(pl, (float)n_b * be.pdf) / pl;
+    out.x += be.fcos.x * __ldg(&L->emission[0]) * k;
+    out.y += be.fcos.y * __ldg(&L->emission[1]) * k;
+    out.z += be.fcos.z * __ldg(&L->emission[2]) * k;
+    return word;
+}
+
+// One segment of an L_ind path (light mode 1) after its ray was traced:
+// emission found by the continuation (MIS weighted; the first hit's goes to
+// first_emit, weighted against nb0 BSDF samples of density pb at the
+// shading point), a light sample at the vertex, Russian roulette, the next
+// direction and its density.  Returns true when the path ends.
+__device__ __forceinline__ bool path_segment_nee(const Tracer& tr, const Prim* __restrict__ gp, const Lights& lt,
+                                                 int prim, float t, V3& o, V3& d, float3& beta, float3& L,
+                                                 uint32_t& seg, uint32_t max_depth, uint32_t k0, uint32_t k1,
+                                                 uint32_t c0, uint32_t c1, uint64_t& sig, float& pb, uint32_t nb0,
+                                                 float3& first_emit) {
+    sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+    if (prim < 0) return true;
+    const Hit h = hit_info(tr.prims[prim], o, d, t);
+    const Prim* Q = gp + prim;
+    const uint32_t flags = __ldg(&Q->flags);
+    if (h.front || (flags & EMIT_TWO_SIDED)) {
+        const float3 le = make_float3(__ldg(&Q->emission[0]), __ldg(&Q->emission[1]), __ldg(&Q->emission[2]));
+        if (le.x > 0.f || le.y > 0.f || le.z > 0.f) {
+            float wb = 1.f;
+            if (__ldg(&Q->kind) == KIND_RECT && lt.n)
+                wb = power_weight((float)(seg == 1 ? nb0 : 1u) * pb, light_pdf(tr.prims[prim], d, t, lt.n));
+            if (seg == 1) {
+                first_emit = make_float3(le.x * wb, le.y * wb, le.z * wb);
+            } else {
+                L.x += beta.x * le.x * wb;
+                L.y += beta.y * le.y * wb;
+                L.z += beta.z * le.z * wb;
+            }
+        }
+    }
+    const float3 alb = make_float3(__ldg(&Q->albedo[0]), __ldg(&Q->albedo[1]), __ldg(&Q->albedo[2]));
+    const float rough = __ldg(&Q->roughness);
+    const V3 wo = sneg(d);
+    float3 dl = make_float3(0.f, 0.f, 0.f);
+    sig = sig_mix(sig, nee_sample(tr, gp, lt, h.p, h.n, wo, alb, rough, flags & 3u, seg < max_depth ? 1u : 0u, k0,
+                                  k1, c0, c1, PURPOSE_LIGHT + 16u * seg, dl));
+    L.x += beta.x * dl.x;
+    L.y += beta.y * dl.y;
+    L.z += beta.z * dl.z;
+    if (seg == max_depth) return true;
+    const U4 r = philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg);
+    const bool cont = u01(r.x) < kRRContinue;
+    sig = sig_mix(sig, (uint32_t)cont);
+    if (!cont) return true;
+    beta.x /= kRRContinue;
+    beta.y /= kRRContinue;
+    beta.z /= kRRContinue;
+    const BsdfSample s = sample_bsdf(h.n, wo, alb, rough, flags & 3u, k0, k1, c0, c1, PURPOSE_BOUNCE + 16u * seg);
+    sig = sig_mix(sig, s.word);
+    if (!s.valid) return true;
+    beta.x *= s.w.x;
+    beta.y *= s.w.y;
+    beta.z *= s.w.z;
+    pb = bsdf_eval(h.n, wo, s.wi, alb, rough, flags & 3u).pdf;
+    o = h.p;
+    d = s.wi;
+    ++seg;
+    return false;
 }
 
 // One segment of a path (residual or training) after its ray was traced:
@@ -128,7 +288,8 @@ enum : uint32_t { kNeedPixel = 0, kCameraRay = 1, kResidRay = 2, kNoMoreWork = 3
 // per-lane state machine so that every iteration traces one ray per busy
 // lane: a lane whose pixel is done takes the next pixel from a work counter
 // (one atomic per warp), so lanes do not idle while others finish long paths.
-__global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader* __restrict__ hd_g,
+template <bool kNee>
+__global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(const SceneHeader* __restrict__ hd_g,
                                                               const Prim* __restrict__ gp, FrameArgs a,
                                                               nirc_record* __restrict__ recs,
                                                               PixelBase* __restrict__ base,
@@ -138,7 +299,12 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
                                                               unsigned long long* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
+    __shared__ uint32_t s_nlights;
     const Tracer tr = setup_scene(hd_g, gp, a.n_prims, smem_raw, &hd);
+    Lights lt{nullptr, 0u};
+    if constexpr (kNee)
+        lt = collect_lights(gp, a.n_prims, reinterpret_cast<uint16_t*>(smem_raw + pt_geom_bytes(a.n_prims)),
+                            &s_nlights);
 
     const uint64_t P = (uint64_t)a.W * a.H;
     uint32_t stage = kNeedPixel;
@@ -149,6 +315,8 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
     float srough = 1.f;
     uint32_t smat = 0;
     uint64_t sig = kSigInit;
+    float pb = 0.f;                                  // light mode 1: density of the current direction
+    float3 first_emit = make_float3(0.f, 0.f, 0.f);  // light mode 1: first hit's weighted emission
 
     // Next residual sample of the current pixel: the first valid one becomes
     // the ray in flight; with none left the pixel's outputs are written.
@@ -166,6 +334,10 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
                 beta = make_float3(1.f, 1.f, 1.f);
                 L = make_float3(0.f, 0.f, 0.f);
                 seg = 1;
+                if constexpr (kNee) {
+                    pb = bsdf_eval(sn, swo, s.wi, salb, srough, smat).pdf;
+                    first_emit = make_float3(0.f, 0.f, 0.f);
+                }
                 return kResidRay;
             }
         }
@@ -235,11 +407,27 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
                 wl = make_float3(0.f, 0.f, 0.f);
                 nvalid = 0;
                 j = 0;
+                if constexpr (kNee) {
+                    // direct light at the shading point: one light sample against the M residual directions
+                    sig = sig_mix(sig, nee_sample(tr, gp, lt, sp, sn, swo, salb, srough, smat, a.M, a.k0, a.k1, pix,
+                                                  0u, PURPOSE_LIGHT, le));
+                }
                 stage = next_residual();
             }
         } else if (stage == kResidRay) {
-            const bool end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig);
+            bool end;
+            if constexpr (kNee)
+                end = path_segment_nee(tr, gp, lt, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig, pb, a.M,
+                                       first_emit);
+            else
+                end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig);
             if (end) {
+                if constexpr (kNee) {
+                    const float inv = 1.0f / (float)a.M;
+                    le.x += sw.x * first_emit.x * inv;
+                    le.y += sw.y * first_emit.y * inv;
+                    le.z += sw.z * first_emit.z * inv;
+                }
                 wl.x += sw.x * L.x;
                 wl.y += sw.y * L.y;
                 wl.z += sw.z * L.z;
@@ -254,7 +442,8 @@ __global__ void __launch_bounds__(kPtThreads) k_primary_resid(const SceneHeader*
 // Training paths, organised like k_primary_resid: per path index the pixel
 // pick, camera ray, record and first direction, then the path's segments;
 // one ray per busy lane per iteration.
-__global__ void __launch_bounds__(kPtThreads) k_gen_train(const SceneHeader* __restrict__ hd_g,
+template <bool kNee>
+__global__ void __launch_bounds__(kPtThreads, 4) k_gen_train(const SceneHeader* __restrict__ hd_g,
                                                           const Prim* __restrict__ gp, uint32_t n_prims, uint32_t W,
                                                           uint32_t H, uint64_t T, uint32_t k0, uint32_t k1,
                                                           uint32_t max_depth, nirc_record* __restrict__ recs,
@@ -262,7 +451,13 @@ __global__ void __launch_bounds__(kPtThreads) k_gen_train(const SceneHeader* __r
                                                           unsigned long long* __restrict__ work) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
+    __shared__ uint32_t s_nlights;
     const Tracer tr = setup_scene(hd_g, gp, n_prims, smem_raw, &hd);
+    Lights lt{nullptr, 0u};
+    if constexpr (kNee)
+        lt = collect_lights(gp, n_prims, reinterpret_cast<uint16_t*>(smem_raw + pt_geom_bytes(n_prims)), &s_nlights);
+    float pb = 0.f;
+    float3 first_emit = make_float3(0.f, 0.f, 0.f);
     const uint32_t P = W * H;
     uint32_t stage = kNeedPixel;
     uint32_t ti = 0, seg = 0;
@@ -323,7 +518,13 @@ __global__ void __launch_bounds__(kPtThreads) k_gen_train(const SceneHeader* __r
                 }
             }
         } else if (stage == kResidRay) {
-            if (path_segment(tr, gp, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig)) {
+            bool end;
+            if constexpr (kNee)  // target = L_ind: the first hit's emission is direct light (discarded)
+                end = path_segment_nee(tr, gp, lt, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig, pb, 0u,
+                                       first_emit);
+            else
+                end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig);
+            if (end) {
                 float* tg = targets + 3 * (uint64_t)ti;
                 tg[0] = L.x;
                 tg[1] = L.y;
@@ -335,7 +536,8 @@ __global__ void __launch_bounds__(kPtThreads) k_gen_train(const SceneHeader* __r
 }
 
 static size_t pt_smem(uint32_t n_prims) {
-    return (size_t)n_prims * sizeof(PrimGeom) + (n_prims >= kBvhMinPrims ? bvh_smem_bytes(n_prims) : 0);
+    // geometry | hierarchy | light list (2 bytes per primitive)
+    return pt_geom_bytes(n_prims) + (size_t)n_prims * 2 + 16;
 }
 
 template <typename K>
@@ -353,37 +555,56 @@ static cudaError_t persistent_grid(K kernel, size_t smem, uint64_t work, int num
     return cudaSuccess;
 }
 
+template <bool kNee>
+static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeader* hd, const Prim* gp,
+                                          const FrameArgs& a, uint64_t P, nirc_record* recs, PixelBase* base,
+                                          ResidRow* rows, uint64_t* sig, uint32_t* count, cudaStream_t st) {
+    const size_t smem = pt_smem(a.n_prims);
+    uint32_t grid = 1;
+    cudaError_t e = persistent_grid(k_primary_resid<kNee>, smem, P, h->num_sms, &grid);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_primary_resid<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig, uint32_t* count,
                                  cudaStream_t st) {
     FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
     const uint64_t P = (uint64_t)fd.width * fd.height;
-    const size_t smem = pt_smem(fd.n_prims);
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
+    if (fd.light_mode == 1)
+        return launch_primary_resid_t<true>(h, hd, gp, a, P, recs, base, rows, sig, count, st);
+    return launch_primary_resid_t<false>(h, hd, gp, a, P, recs, base, rows, sig, count, st);
+}
+
+template <bool kNee>
+static cudaError_t launch_gen_train_t(const nirc_handle* h, const SceneHeader* hd, const Prim* gp, uint32_t n_prims,
+                                      uint32_t W, uint32_t H, uint64_t T, uint32_t frame, uint64_t seed,
+                                      uint32_t max_depth, nirc_record* recs, float* dirs, float* targets,
+                                      cudaStream_t st) {
+    const size_t smem = pt_smem(n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_primary_resid, smem, P, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_gen_train<kNee>, smem, T, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
+    e = cudaMemsetAsync(h->work_counter + 1, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_primary_resid<<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter);
+    k_gen_train<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
+                                                      max_depth, recs, dirs, targets, h->work_counter + 1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
-                             uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, nirc_record* recs,
-                             float* dirs, float* targets, cudaStream_t st) {
-    const size_t smem = pt_smem(n_prims);
+                             uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, uint32_t light_mode,
+                             nirc_record* recs, float* dirs, float* targets, cudaStream_t st) {
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
-    uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_gen_train, smem, T, h->num_sms, &grid);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(h->work_counter + 1, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    k_gen_train<<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
-                                                max_depth, recs, dirs, targets, h->work_counter + 1);
-    return cudaGetLastError();
+    if (light_mode == 1)
+        return launch_gen_train_t<true>(h, hd, gp, n_prims, W, H, T, frame, seed, max_depth, recs, dirs, targets, st);
+    return launch_gen_train_t<false>(h, hd, gp, n_prims, W, H, T, frame, seed, max_depth, recs, dirs, targets, st);
 }
 
 }  // namespace nirc

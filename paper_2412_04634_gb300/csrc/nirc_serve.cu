@@ -168,6 +168,7 @@ nirc_status nirc_server::enqueue_request(Req* q, cudaStream_t st) {
     fd.seed = sc.seed;
     fd.n_prims = sc.n_prims;
     fd.cache_mode = 0;
+    fd.light_mode = q->r.light_mode;
     const void* blob = sc.frames + (uint64_t)(q->r.frame % sc.n_frames) * sc.stride;
     float* img = reinterpret_cast<float*>(arena_base + q->img_off);
     void* scratch = arena_base + q->scr_off;
@@ -181,7 +182,7 @@ nirc_status nirc_server::enqueue_request(Req* q, cudaStream_t st) {
     nirc_status s = enqueue_frame("nirc_server", sc.h, blob, fd, img, nullptr, scratch, st);
     if (s != NIRC_OK || cfg.train_samples == 0) return s;
     cudaError_t e = launch_gen_train(sc.h, blob, sc.n_prims, fd.width, fd.height, cfg.train_samples, fd.frame,
-                                     sc.seed, fd.max_depth, sc.trecs, sc.tdirs, sc.ttgts, st);
+                                     sc.seed, fd.max_depth, fd.light_mode, sc.trecs, sc.tdirs, sc.ttgts, st);
     if (e == cudaSuccess) e = launch_train_step(sc.h, sc.trecs, sc.tdirs, sc.ttgts, cfg.train_samples, nullptr, st);
     return cuda_status(e, "nirc_server (training)");
 }
@@ -506,8 +507,9 @@ nirc_status nirc_server_submit(nirc_server* s, const nirc_request* req) {
     }
     const nirc_request& r = *req;
     if (r.width < 1 || r.width > 8192 || r.height < 1 || r.height > 8192 || r.n_cache > 1024 || r.n_resid > 64 ||
-        r.max_depth < 1 || r.max_depth > 64) {
-        set_error("nirc_server_submit: size out of range (W, H 1..8192, N <= 1024, M <= 64, depth 1..64)");
+        r.max_depth < 1 || r.max_depth > 64 || r.light_mode > 1) {
+        set_error("nirc_server_submit: size out of range (W, H 1..8192, N <= 1024, M <= 64, depth 1..64, "
+                  "light_mode 0..1)");
         return NIRC_ERR_INVALID;
     }
     Req* q = new (std::nothrow) Req();

@@ -48,7 +48,7 @@ class nirc_frame_desc(ctypes.Structure):
         ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("n_prims", ctypes.c_uint32),
         ("cache_mode", ctypes.c_uint32), ("cache_const", ctypes.c_float * 3),
-        ("pad", ctypes.c_uint32),
+        ("light_mode", ctypes.c_uint32),
     ]
 
 
@@ -72,7 +72,7 @@ class nirc_server_config(ctypes.Structure):
 class nirc_request(ctypes.Structure):
     _fields_ = [("id", ctypes.c_uint64), ("scene", ctypes.c_uint32), ("width", ctypes.c_uint32),
                 ("height", ctypes.c_uint32), ("n_cache", ctypes.c_uint32), ("n_resid", ctypes.c_uint32),
-                ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32), ("light_mode", ctypes.c_uint32)]
 
 
 class nirc_completion(ctypes.Structure):
@@ -110,7 +110,7 @@ def _load():
         "nirc_query": ([P, P, P, u64, P, P], st),
         "nirc_estimate_frame": ([P, P, P, P, P, P], st),
         "nirc_estimate_frame_noalloc": ([P, P, P, P, P, P], st),
-        "nirc_gen_train": ([P, P, u32, u32, u32, u64, u32, u64, u32, P, P, P, P], st),
+        "nirc_gen_train": ([P, P, u32, u32, u32, u64, u32, u64, u32, u32, P, P, P, P], st),
         "nirc_train_step": ([P, P, P, P, u64, P, P], st),
         "nirc_frame_mrse": ([P, P, u64, ctypes.c_float, P, P], st),
         "nirc_timing_enable": ([P, i32], st),
@@ -172,10 +172,11 @@ def make_config(cfg: scenes.NetConfig, precision: int = NIRC_FP32_SIMT) -> nirc_
 
 
 def frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode=0,
-               cache_const=(0.0, 0.0, 0.0)) -> nirc_frame_desc:
+               cache_const=(0.0, 0.0, 0.0), light_mode=0) -> nirc_frame_desc:
     d = nirc_frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode)
     for k in range(3):
         d.cache_const[k] = float(cache_const[k])
+    d.light_mode = light_mode
     return d
 
 
@@ -262,8 +263,8 @@ def nirc_estimate_frame_noalloc(h, scene: torch.Tensor, desc: nirc_frame_desc, o
 
 
 def nirc_gen_train(h, scene: torch.Tensor, n_prims, width, height, T, frame, seed, max_depth,
-                   records: torch.Tensor, dirs: torch.Tensor, targets: torch.Tensor, stream=None):
-    _check(_lib.nirc_gen_train(h, _ptr(scene), n_prims, width, height, T, frame, seed, max_depth,
+                   records: torch.Tensor, dirs: torch.Tensor, targets: torch.Tensor, stream=None, light_mode=0):
+    _check(_lib.nirc_gen_train(h, _ptr(scene), n_prims, width, height, T, frame, seed, max_depth, light_mode,
                                _ptr(records), _ptr(dirs), _ptr(targets), _stream(stream)))
 
 
@@ -453,8 +454,9 @@ class Server:
         self._keep.append((cache, dev))
         return nirc_server_add_scene(self.h, cache.h, dev, len(blobs), stride, frames[0].n_prims, seed)
 
-    def submit(self, rid, scene, width, height, n_cache, n_resid, max_depth, frame):
-        nirc_server_submit(self.h, nirc_request(rid, scene, width, height, n_cache, n_resid, max_depth, frame, 0))
+    def submit(self, rid, scene, width, height, n_cache, n_resid, max_depth, frame, light_mode=0):
+        nirc_server_submit(self.h, nirc_request(rid, scene, width, height, n_cache, n_resid, max_depth, frame,
+                                                light_mode))
 
     def poll(self, wait=False, max_n=64):
         return nirc_server_poll(self.h, max_n, wait)

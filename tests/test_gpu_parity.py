@@ -42,7 +42,7 @@ def _hash_cfg():
 
 
 def _run_frame(N, cfg, params, scene, W, H, Nc, M, D, frame, seed, cache_mode=0, cache_const=(0, 0, 0),
-               precision=0, rows=False):
+               precision=0, rows=False, light_mode=0):
     import torch
     cache = N.Cache(cfg)
     if params is not None:
@@ -57,7 +57,7 @@ def _run_frame(N, cfg, params, scene, W, H, Nc, M, D, frame, seed, cache_mode=0,
     sig = torch.empty((P, 2), device="cuda", dtype=torch.int64)
     cnt = torch.empty(P, device="cuda", dtype=torch.int32)
     row_n = torch.full((P, Nc + M, 3), -1.0, device="cuda") if rows else None
-    desc = N.frame_desc(W, H, Nc, M, D, frame, seed, scene.n_prims, cache_mode, cache_const)
+    desc = N.frame_desc(W, H, Nc, M, D, frame, seed, scene.n_prims, cache_mode, cache_const, light_mode=light_mode)
     N.nirc_estimate_frame(cache.h, sc, desc, out, lc, lr, sig, cnt, row_n)
     N.nirc_sync(cache.h)
     torch.cuda.synchronize()
