@@ -298,6 +298,33 @@ class FrameRunner:
         return ms, int(frames[0].blob().nbytes), int(self.P * 16 + 8 + 4)
 
 
+def recorded_traffic(args, precision):
+    """DRAM bytes per launch of the cache kernel from the committed ncu
+    record, or None when the record is for another workload or precision,
+    or the kernel's sources have changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"k_cache_tc_{precision}_1080p.traffic.txt")
+    if not os.path.exists(path) or (args.width, args.height, args.n_cache, args.n_resid) != (1920, 1080, 16, 1):
+        return None
+    rec, srcs = {}, []
+    for line in open(path):
+        if line.startswith("# valid while these sources hash"):
+            srcs = line.split(":", 1)[1].split()
+        elif ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            rec[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    try:
+        for sp in srcs:
+            with open(os.path.join(ROOT, sp), "rb") as f:
+                h.update(f.read())
+    except OSError:
+        return None
+    if not srcs or h.hexdigest() != rec.get("sources_sha256"):
+        return None
+    return int(rec["dram_bytes_per_launch"])
+
+
 def _roofline(args, cfg, props, kernel_ms, dominant, sm_max):
     fl_frame, per_row, per_pixel = flops_per_frame(cfg, args)
     P = args.width * args.height
@@ -318,9 +345,14 @@ def _roofline(args, cfg, props, kernel_ms, dominant, sm_max):
             f16 = fl_frame - f8
             peak = peak * fl_frame / (f8 / 2.0 + f16)
             src += " x nominal E4M3/BF16 ratio 2 on the hidden-layer share of the FLOPs"
+        traffic = recorded_traffic(args, args.precision) if args.light_mode == 0 else None
         roof = {"kernel": f"k_cache_tc<{args.precision}>", "bound": "tensor", "achieved": round(achieved, 3),
-                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": src}
+        if traffic is not None:
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                                      f"profiles/k_cache_tc_{args.precision}_1080p.traffic.txt (sources unchanged since)")
+            roof["traffic_vs_algorithmic"] = round(traffic / (args.width * args.height * (64 + 32 + 32 + 16)), 3)
     roof["algorithmic"] = algorithmic
     roof["launch_ms"] = round(avg_ms, 4)
     roof["dominant_kernel"] = dominant

@@ -349,8 +349,10 @@ def config_small() -> NetConfig:
 
 def config_1080p() -> NetConfig:
     """1080p workload: 16-level hash grid (2 features, 2^19 entries, base 16,
-    growth 1.5), width 64 with 4 hidden layers, Adam lr 1e-2."""
-    return NetConfig(pos_encoding=POS_HASHGRID, hidden_layers=4, lr=1e-2)
+    growth 1.5), width 64 with 4 hidden layers, Adam lr 1e-3 (with 1e-2 the
+    exp output and Adam's normalised first steps overshoot and the cache
+    sinks towards 0 within a few dozen frames on this workload)."""
+    return NetConfig(pos_encoding=POS_HASHGRID, hidden_layers=4, lr=1e-3)
 
 
 def init_params(cfg: NetConfig, seed: int = 1) -> np.ndarray:

@@ -36,14 +36,15 @@ def _mrse(img, ref, eps=1e-2):
     return float(np.mean((img - ref) ** 2 / (ref ** 2 + eps)))
 
 
-@pytest.fixture(scope="module", params=["trained30", "init"])
+@pytest.fixture(scope="module", params=["trained30", "init", "trained30_nee"])
 def trained(N, request):
     """Cache weights after 30 training frames (or the initial weights) and
     the frame-30 scene.  With BSDF-sampled training paths and the small
     emitter, almost every training target is 0 and the trained cache sinks
     towards 0 in most of the scene (the oracle does the same), so the
     initial weights are swept as well to show the arithmetic on a network
-    whose outputs are O(1)."""
+    whose outputs are O(1), and light mode 1 (the cache learns L_ind, direct
+    light by NEE + MIS), whose training targets are mostly non-zero."""
     import torch
     cfg = scenes.config_1080p()
     base = scenes.cornell_scene(W, H, seed=1, n_prims=256, glossy=True, moving_emitter=True)
@@ -55,9 +56,10 @@ def trained(N, request):
     recs = torch.empty((T_TRAIN, 16), device="cuda")
     dirs = torch.empty((T_TRAIN, 3), device="cuda")
     tgts = torch.empty((T_TRAIN, 3), device="cuda")
-    for f in range(FRAMES if request.param == "trained30" else 0):
+    lm = 1 if request.param.endswith("_nee") else 0
+    for f in range(FRAMES if request.param.startswith("trained30") else 0):
         sc = N.scene_to_tensor(scenes.scene_at_frame(base, f))
-        N.nirc_gen_train(cache.h, sc, base.n_prims, W, H, T_TRAIN, f, 1, 5, recs, dirs, tgts)
+        N.nirc_gen_train(cache.h, sc, base.n_prims, W, H, T_TRAIN, f, 1, 5, recs, dirs, tgts, light_mode=lm)
         N.nirc_train_step(cache.h, recs, dirs, tgts)
     torch.cuda.synchronize()
     params = cache.get_params().numpy()
@@ -72,17 +74,18 @@ def trained(N, request):
         ref += tmp
     ref /= 16
     torch.cuda.synchronize()
-    yield cfg, params, scene, sc, ref.cpu().numpy(), cache, request.param
+    yield cfg, params, scene, sc, ref.cpu().numpy(), cache, request.param, lm
     cache.close()
 
 
-def _gpu_frame(N, cache, sc, scene, Nc, precision, pix):
+def _gpu_frame(N, cache, sc, scene, Nc, precision, pix, lm):
     import torch
     N.nirc_set_precision(cache.h, precision)
     S = Nc + 1
     out = torch.empty((W * H, 4), device="cuda")
     row_n = torch.empty((W * H, S, 3), device="cuda")
-    N.nirc_estimate_frame(cache.h, sc, N.frame_desc(W, H, Nc, 1, 5, FRAMES, 1, scene.n_prims), out, row_n=row_n)
+    N.nirc_estimate_frame(cache.h, sc, N.frame_desc(W, H, Nc, 1, 5, FRAMES, 1, scene.n_prims, light_mode=lm), out,
+                          row_n=row_n)
     idx = torch.from_numpy(pix.astype(np.int64)).cuda()
     sub_rows = row_n[idx].cpu().numpy().astype(np.float64)
     img = out.cpu().numpy()
@@ -91,7 +94,7 @@ def _gpu_frame(N, cache, sc, scene, Nc, precision, pix):
 
 
 def test_precision_sweep(N, oracle, trained):
-    cfg, params, scene, sc, ref, cache, state = trained
+    cfg, params, scene, sc, ref, cache, state, lm = trained
     precisions = {"fp32_simt": N.NIRC_FP32_SIMT, "fp16_tc": N.NIRC_FP16_TC, "bf16_tc": N.NIRC_BF16_TC,
                   "fp8_tc": N.NIRC_FP8_E4M3_TC}
     rng = np.random.default_rng(30)
@@ -99,10 +102,11 @@ def test_precision_sweep(N, oracle, trained):
     for Nc in NS:
         S = Nc + 1
         pix = np.sort(rng.choice(W * H, (ROWS + S - 1) // S, replace=False)).astype(np.uint32)
-        o = oracle.estimate(cfg, params, scene.blob(), oracle.oframe(W, H, Nc, 1, 5, FRAMES, 1), pixels=pix, rows=True)
+        o = oracle.estimate(cfg, params, scene.blob(), oracle.oframe(W, H, Nc, 1, 5, FRAMES, 1, light_mode=lm),
+                            pixels=pix, rows=True)
         m_or = _mrse(o["pixel"], ref[pix])
         for name, code in precisions.items():
-            img, rows = _gpu_frame(N, cache, sc, scene, Nc, code, pix)
+            img, rows = _gpu_frame(N, cache, sc, scene, Nc, code, pix, lm)
             # rows of invalid samples are 0 on both sides; a valid row's n is
             # exp(z) > 0 in FP64 but can underflow to 0 in FP32 for z < -87,
             # so errors are taken against a floor of 1e-3 x the mean value
@@ -111,7 +115,7 @@ def test_precision_sweep(N, oracle, trained):
             floor = 1e-3 * o["row_n"][valid].mean()
             err = np.abs(rows[valid] - o["row_n"][valid]) / np.maximum(o["row_n"][valid], floor)
             m_gpu = _mrse(img[pix], ref[pix])
-            rec = {"weights": state, "precision": name, "N": Nc, "rows": int(valid.sum() // 3), "row_err_max": float(err.max()),
+            rec = {"weights": state, "light_mode": lm, "precision": name, "N": Nc, "rows": int(valid.sum() // 3), "row_err_max": float(err.max()),
                    "row_err_p99": float(np.percentile(err, 99)), "mrse_gpu": m_gpu, "mrse_oracle": m_or,
                    "mrse_rel_diff": abs(m_gpu - m_or) / m_or, "mrse_gpu_full_frame": _mrse(img, ref),
                    "rows_below_floor": int(np.sum(o["row_n"][valid] < floor)),
