@@ -187,6 +187,20 @@ nirc_status nirc_load_params(nirc_handle* h, const float* params, int on_device,
 nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* stream);
 /* Copy out the gradient of the last nirc_train_step (same layout). */
 nirc_status nirc_get_grads(nirc_handle* h, float* out, int on_device, void* stream);
+/* Checkpoint / resume of a cache: nirc_state_bytes() bytes of host memory
+ * hold a header (magic "NIRCSTAT", format version, the nirc_config, the
+ * Adam step count) followed by the FP32 master parameters, Adam m and v in
+ * the nirc_param_count() layout.  nirc_save_state synchronises `stream`
+ * and writes `host_buf`; nirc_load_state reads it back (the handle must
+ * have the same configuration apart from precision and learning-rate
+ * fields: NIRC_ERR_INVALID otherwise, handle unchanged), restores weights,
+ * moments and step exactly and refreshes the low-precision copies.
+ * Training after a load continues bit for bit as it would have without the
+ * save (deterministic mode). */
+uint64_t nirc_state_bytes(const nirc_handle* h);
+nirc_status nirc_save_state(nirc_handle* h, void* host_buf, uint64_t bytes, void* stream);
+nirc_status nirc_load_state(nirc_handle* h, const void* host_buf, uint64_t bytes, void* stream);
+
 /* Select the layer arithmetic for later calls (nirc_precision).  The
  * tensor-core modes apply to the cache integral of nirc_estimate_frame when
  * the network is used (cache_mode 0) and N + M >= 4; other work (queries,

@@ -261,27 +261,29 @@ __device__ __forceinline__ void octaves(float s, float c, float* e) {
     }
 }
 
-// Direction features of w without transcendentals: with theta = acos(w_z) and
+// Direction features of w without transcendentals (hardware rsqrt and fast
+// divide: the features are continuous network inputs): with theta = acos(w_z) and
 // phi' = atan2(w_y, w_x) mapped to [0, 2 pi), pi theta_hat = theta and
 // pi phi_hat = phi' / 2, so sin/cos follow from w_z and from the half-angle
 // identities in forms free of cancellation.
 __device__ __forceinline__ void dir_features_fast(V3 w, float* e) {
     const float c = fminf(fmaxf(w.z, -1.f), 1.f);
-    const float s = sqrtf(fmaxf((1.f - c) * (1.f + c), 0.f));
+    const float s = fast_sqrt((1.f - c) * (1.f + c));
     octaves(s, c, e);
     const float r2 = w.x * w.x + w.y * w.y;
     float sp = 0.f, cp = 1.f;
     if (r2 > 0.f) {
-        const float r = sqrtf(r2);
-        const float ir = 0.5f / r;
+        const float rr = rsqrtf(r2);
+        const float r = r2 * rr;
+        const float ir = 0.5f * rr;
         if (w.x >= 0.f) {
             const float a = r + w.x;
-            cp = sqrtf(a * ir);
-            sp = sqrtf(w.y * w.y * ir / a);
+            cp = fast_sqrt(a * ir);
+            sp = fast_sqrt(__fdividef(w.y * w.y * ir, a));
         } else {
             const float a = r - w.x;
-            sp = sqrtf(a * ir);
-            cp = sqrtf(w.y * w.y * ir / a);
+            sp = fast_sqrt(a * ir);
+            cp = fast_sqrt(__fdividef(w.y * w.y * ir, a));
         }
         const bool upper = (w.y > 0.f) || (w.y == 0.f && w.x >= 0.f);
         if (!upper) cp = -cp;

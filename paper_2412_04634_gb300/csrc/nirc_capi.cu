@@ -432,6 +432,85 @@ static nirc_status copy_out(const nirc_handle* h, const float* src, float* out, 
     return cuda_status(e, what);
 }
 
+namespace {
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t step;
+    nirc_config cfg;
+    uint64_t n_params;
+    uint64_t pad;
+};
+constexpr uint32_t kStateVersion = 1;
+
+bool same_shape(const nirc_config& a, const nirc_config& b) {
+    return a.pos_encoding == b.pos_encoding && a.hash_levels == b.hash_levels &&
+           a.feats_per_level == b.feats_per_level && a.log2_table == b.log2_table && a.base_res == b.base_res &&
+           a.growth == b.growth && a.freq_octaves == b.freq_octaves && a.width == b.width &&
+           a.hidden_layers == b.hidden_layers;
+}
+}  // namespace
+
+uint64_t nirc_state_bytes(const nirc_handle* h) {
+    if (!h) return 0;
+    return sizeof(StateHeader) + 3ull * (h->shape.n_mlp + h->shape.n_hash) * sizeof(float);
+}
+
+nirc_status nirc_save_state(nirc_handle* h, void* host_buf, uint64_t bytes, void* stream) {
+    if (!h || !host_buf || bytes < nirc_state_bytes(h)) {
+        set_error("nirc_save_state: NULL argument or buffer smaller than nirc_state_bytes()");
+        return NIRC_ERR_INVALID;
+    }
+    StateHeader hd{};
+    memcpy(hd.magic, "NIRCSTAT", 8);
+    hd.version = kStateVersion;
+    hd.step = h->step;
+    hd.cfg = h->cfg;
+    hd.n_params = h->shape.n_mlp + h->shape.n_hash;
+    char* out = static_cast<char*>(host_buf);
+    memcpy(out, &hd, sizeof(hd));
+    float* body = reinterpret_cast<float*>(out + sizeof(hd));
+    nirc_status st = copy_out(h, h->params, body, 0, stream, "nirc_save_state");
+    if (st == NIRC_OK) st = copy_out(h, h->adam_m, body + hd.n_params, 0, stream, "nirc_save_state");
+    if (st == NIRC_OK) st = copy_out(h, h->adam_v, body + 2 * hd.n_params, 0, stream, "nirc_save_state");
+    return st;
+}
+
+nirc_status nirc_load_state(nirc_handle* h, const void* host_buf, uint64_t bytes, void* stream) {
+    if (!h || !host_buf || bytes < sizeof(StateHeader)) {
+        set_error("nirc_load_state: NULL argument or truncated buffer");
+        return NIRC_ERR_INVALID;
+    }
+    StateHeader hd;
+    memcpy(&hd, host_buf, sizeof(hd));
+    const uint64_t np = h->shape.n_mlp + h->shape.n_hash;
+    if (memcmp(hd.magic, "NIRCSTAT", 8) != 0 || hd.version != kStateVersion || hd.n_params != np ||
+        !same_shape(hd.cfg, h->cfg) || bytes < nirc_state_bytes(h)) {
+        set_error("nirc_load_state: not a state of this configuration (magic, version, shape or size differ)");
+        return NIRC_ERR_INVALID;
+    }
+    const float* body = reinterpret_cast<const float*>(static_cast<const char*>(host_buf) + sizeof(hd));
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t mlp_b = h->shape.n_mlp * sizeof(float), hash_b = h->shape.n_hash * sizeof(float);
+    float* dst[3] = {h->params, h->adam_m, h->adam_v};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        e = cudaMemsetAsync(dst[k], 0, h->shape.n_dev * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst[k], body + k * np, mlp_b, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && hash_b)
+            e = cudaMemcpyAsync(dst[k] + h->shape.hash_off, body + k * np + h->shape.n_mlp, hash_b,
+                                cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = launch_repack_simt(h, st);
+    if (e == cudaSuccess) e = launch_hash_to_half(h, st);
+    if (e == cudaSuccess) e = launch_repack_tc(h, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host buffer may be freed on return
+    if (e != cudaSuccess) return cuda_status(e, "nirc_load_state");
+    h->step = hd.step;
+    h->fp8_calibrated = false;
+    return NIRC_OK;
+}
+
 nirc_status nirc_get_params(nirc_handle* h, float* out, int on_device, void* stream) {
     if (!h || !out) {
         set_error("nirc_get_params: NULL argument");

@@ -334,6 +334,10 @@ __device__ __forceinline__ V3 ggx_vndf_reflect(V3 wo, V3 t, V3 b, V3 n, float al
 
 // f_r cos / p of the Lambertian + GGX material under the 1/2 cosine + 1/2
 // visible-normal mixture (FP32, continuous).
+// sqrt(x) for x >= 0 from the hardware reciprocal square root (a few ulp;
+// for continuous quantities only, never for a decision).
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
 // a d - b c with one rounding error (Kahan's FMA algorithm).
 __device__ __forceinline__ float det2(float a, float b, float c, float d) {
     const float w = b * c;
@@ -363,8 +367,8 @@ __device__ __forceinline__ float3 ggx_mix_weight(V3 n, V3 wo, V3 wi, float3 albe
     const float oh = fminf(fmaxf((wo.x * sx + wo.y * sy + wo.z * sz) * hinv, 0.0f), 1.0f);
     const float dd = ggx_dd(n, sx, sy, sz, a2);
     const float D = __fdividef(a2, kPi * dd * dd);
-    const float lam_o = sqrtf(a2 + (1.0f - a2) * co * co);
-    const float lam_i = sqrtf(a2 + (1.0f - a2) * ci * ci);
+    const float lam_o = fast_sqrt(a2 + (1.0f - a2) * co * co);
+    const float lam_i = fast_sqrt(a2 + (1.0f - a2) * ci * ci);
     const float m = 1.0f - oh;
     const float m2 = m * m;
     const float F = kF0 + (1.0f - kF0) * (m2 * m2 * m);
@@ -427,8 +431,8 @@ __device__ __forceinline__ BsdfEval bsdf_eval(V3 n, V3 wo, V3 wi, float3 albedo,
     const float oh = fminf(fmaxf((wo.x * sx + wo.y * sy + wo.z * sz) * hinv, 0.0f), 1.0f);
     const float dd = ggx_dd(n, sx, sy, sz, a2);
     const float D = __fdividef(a2, kPi * dd * dd);
-    const float lam_o = sqrtf(a2 + (1.0f - a2) * co * co);
-    const float lam_i = sqrtf(a2 + (1.0f - a2) * ci * ci);
+    const float lam_o = fast_sqrt(a2 + (1.0f - a2) * co * co);
+    const float lam_i = fast_sqrt(a2 + (1.0f - a2) * ci * ci);
     const float m = 1.0f - oh;
     const float m2 = m * m;
     const float F = kF0 + (1.0f - kF0) * (m2 * m2 * m);

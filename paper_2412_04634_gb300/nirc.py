@@ -106,6 +106,9 @@ def _load():
         "nirc_get_params": ([P, P, i32, P], st),
         "nirc_get_grads": ([P, P, i32, P], st),
         "nirc_set_precision": ([P, u32], st),
+        "nirc_state_bytes": ([P], u64),
+        "nirc_save_state": ([P, P, u64, P], st),
+        "nirc_load_state": ([P, P, u64, P], st),
         "nirc_sync": ([P, P], st),
         "nirc_query": ([P, P, P, u64, P, P], st),
         "nirc_estimate_frame": ([P, P, P, P, P, P], st),
@@ -229,6 +232,23 @@ def nirc_get_params(h, out: torch.Tensor, stream=None):
 
 def nirc_get_grads(h, out: torch.Tensor, stream=None):
     _check(_lib.nirc_get_grads(h, _ptr(out), 1 if out.is_cuda else 0, _stream(stream)))
+
+
+def nirc_state_bytes(h) -> int:
+    return int(_lib.nirc_state_bytes(h))
+
+
+def nirc_save_state(h, stream=None) -> bytearray:
+    """The cache's weights, Adam moments, step and configuration as bytes."""
+    n = nirc_state_bytes(h)
+    buf = (ctypes.c_char * n)()
+    _check(_lib.nirc_save_state(h, buf, n, _stream(stream)))
+    return bytearray(buf)
+
+
+def nirc_load_state(h, state: bytes, stream=None):
+    buf = (ctypes.c_char * len(state)).from_buffer_copy(bytes(state))
+    _check(_lib.nirc_load_state(h, buf, len(state), _stream(stream)))
 
 
 def nirc_set_precision(h, precision: int):

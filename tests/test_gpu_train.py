@@ -266,3 +266,38 @@ def test_deterministic_query_bwd(N, oracle):
     _, g_or = oracle.query_grad(cfg, params, recs, dirs, gout.astype(np.float64))
     _assert_grad_close(cfg, g1.cpu().numpy().astype(np.float64), g_or)
     cache.close()
+
+
+def test_save_load_state_resumes_training_exactly(N):
+    """Checkpoint after two deterministic steps, take two more; a fresh cache
+    loaded from the checkpoint takes the same two steps to the same bits.
+    A state of another configuration is refused."""
+    import torch
+    cfg = _hash_cfg(levels=8, log2_table=12, hidden=3)
+    params = scenes.init_params(cfg, 91)
+    batches = []
+    for k in range(4):
+        r, d, t = scenes.training_batch(2000, seed=100 + k)
+        batches.append((N.records_to_tensor(r), torch.from_numpy(d).cuda(), torch.from_numpy(t).cuda()))
+    a = N.Cache(cfg)
+    a.set_params(params)
+    N.nirc_set_deterministic(a.h, True)
+    for rt, dt, tt in batches[:2]:
+        N.nirc_train_step(a.h, rt, dt, tt)
+    state = N.nirc_save_state(a.h)
+    for rt, dt, tt in batches[2:]:
+        N.nirc_train_step(a.h, rt, dt, tt)
+    torch.cuda.synchronize()
+    b = N.Cache(cfg)
+    N.nirc_set_deterministic(b.h, True)
+    N.nirc_load_state(b.h, state)
+    for rt, dt, tt in batches[2:]:
+        N.nirc_train_step(b.h, rt, dt, tt)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.get_params().numpy(), b.get_params().numpy())
+    other = N.Cache(_hash_cfg(levels=8, log2_table=12, hidden=2))
+    with pytest.raises(N.NircError) as ei:
+        N.nirc_load_state(other.h, state)
+    assert ei.value.status == N.NIRC_ERR_INVALID
+    for c in (a, b, other):
+        c.close()
