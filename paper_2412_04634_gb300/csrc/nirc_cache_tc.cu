@@ -202,13 +202,20 @@ __device__ __forceinline__ void epilogue(uint32_t taddr, const float* __restrict
         tc::tmem_wait_ld();
         float x[32];
         if (bias) {
-            const float2* b2 = reinterpret_cast<const float2*>(bias + 32u * half);
+            const float4* b4 = reinterpret_cast<const float4*>(bias + 32u * half);  // 128-bit broadcast loads
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float2 acc = make_float2(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
-                const float2 y = kMul ? __ffma2_rn(acc, make_float2(mul, mul), b2[i]) : __fadd2_rn(acc, b2[i]);
-                x[2 * i] = y.x;
-                x[2 * i + 1] = y.y;
+            for (int i = 0; i < 8; ++i) {
+                const float4 bb = b4[i];
+                const float2 a0 = make_float2(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]));
+                const float2 a1 = make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]));
+                const float2 y0 = kMul ? __ffma2_rn(a0, make_float2(mul, mul), make_float2(bb.x, bb.y))
+                                       : __fadd2_rn(a0, make_float2(bb.x, bb.y));
+                const float2 y1 = kMul ? __ffma2_rn(a1, make_float2(mul, mul), make_float2(bb.z, bb.w))
+                                       : __fadd2_rn(a1, make_float2(bb.z, bb.w));
+                x[4 * i] = y0.x;
+                x[4 * i + 1] = y0.y;
+                x[4 * i + 2] = y1.x;
+                x[4 * i + 3] = y1.y;
             }
         } else {
 #pragma unroll
@@ -493,12 +500,12 @@ __global__ void __launch_bounds__(640, 1)
             bool ok = false;
             uint32_t word = 0;
             {
+                // all four words of the record at once (one L1 round trip)
                 const float4* rq = reinterpret_cast<const float4*>(recs + p0 + pl);
-                const float4 q3 = __ldg(rq + 3);
+                const float4 q0 = __ldg(rq), q1 = __ldg(rq + 1), q2 = __ldg(rq + 2), q3 = __ldg(rq + 3);
                 const uint32_t flags = __float_as_uint(q3.z);
                 if (rin && (flags & 1u)) {
                     if (s < a.N) {
-                        const float4 q0 = __ldg(rq), q1 = __ldg(rq + 1), q2 = __ldg(rq + 2);
                         const BsdfSample bs =
                             sample_bsdf(V3{q0.w, q1.x, q1.y}, V3{q1.z, q1.w, q2.x}, make_float3(q2.y, q2.z, q2.w),
                                         q3.x, (flags >> 1) & 3u, a.k0, a.k1, p0 + pl, s, PURPOSE_CACHE_DIR);
