@@ -17,9 +17,12 @@
 //                (few cells, many samples per cell) lanes of a warp that hit
 //                the same entry are combined first (__match_any_sync) and
 //                only the group leader issues the atomic
-//  k_grad_w      per layer: dW = delta x^T and db = sum delta, 4x4 register
-//                tiles over 32-sample chunks staged in shared memory,
-//                split over blocks and combined with float atomics
+//  dW, db        per layer: dW = delta x^T and db = delta 1, a plain GEMM
+//                and GEMV over the samples: k_grad_w (4x4 register tiles
+//                over 32-sample chunks staged in shared memory, combined by
+//                float atomics, or in deterministic mode by block partials
+//                summed in a fixed order); passes of >= 2^18 samples in the
+//                default mode use cuBLAS (FP32 math), faster at that length
 //  k_adam        dense bias-corrected Adam over every parameter (untouched
 //                hash entries have g = 0), FP32 master weights and moments,
 //                FP16 copy of the hash table refreshed in the same pass
@@ -42,6 +45,8 @@
 // that chunk's backward and weight gradients).  Recomputation trades one
 // extra forward for O(chunk) instead of O(n) activation memory; a chunk of
 // 2^15 samples keeps the activation buffer (~78 MB) inside the 129 MB L2.
+#include <cublas_v2.h>
+
 #include <cmath>
 
 #include "nirc_internal.h"
@@ -90,10 +95,12 @@ struct DetPtrs {
 };
 
 static uint64_t max_grad_blocks(const nirc_handle* h) { return 2ull * (uint64_t)h->num_sms + 1; }
+// Forward / backward grids: at most two 128-thread blocks per SM.
+static uint64_t max_train_blocks(const nirc_handle* h) { return 2ull * (uint64_t)h->num_sms; }
 
 static uint64_t det_floats(const nirc_handle* h, uint64_t n) {
     const NetShape& s = h->shape;
-    return round64(2ull * s.levels * n) + 64 + round64((uint64_t)h->num_sms) + round64(max_grad_blocks(h) * s.n_mlp) +
+    return round64(2ull * s.levels * n) + 64 + round64(max_train_blocks(h)) + round64(max_grad_blocks(h) * s.n_mlp) +
            2 * round64(s.n_hash);
 }
 
@@ -101,7 +108,46 @@ size_t train_scratch_bytes(const nirc_handle* h, uint64_t n) {
     const uint64_t c = chunk_of(h, n);
     uint64_t f = round64(3 * n + c * act_floats_per_sample(h->shape));
     if (h->deterministic) f += det_floats(h, n);
+    else f += round64(c);  // a vector of ones (bias gradients as a GEMV)
     return (size_t)f * sizeof(float) + 256;
+}
+
+constexpr size_t kBlasWorkspace = 32u << 20;
+// Below this many samples per pass the hand-written k_grad_w is faster than
+// the library GEMM for these skinny shapes (64 x 72 outputs, K = samples).
+constexpr uint64_t kBlasMinSamples = 1ull << 18;
+
+cudaError_t prepare_blas(nirc_handle* h) {
+    if (h->blas) return cudaSuccess;
+    cublasHandle_t b = nullptr;
+    if (cublasCreate(&b) != CUBLAS_STATUS_SUCCESS) return cudaErrorNotSupported;
+    cudaError_t e = cudaMalloc(&h->blas_ws, kBlasWorkspace);
+    if (e != cudaSuccess) {
+        h->blas_ws = nullptr;
+        cublasDestroy(b);
+        return e;
+    }
+    if (cublasSetWorkspace(b, h->blas_ws, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetMathMode(b, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) {
+        cublasDestroy(b);
+        cudaFree(h->blas_ws);
+        h->blas_ws = nullptr;
+        return cudaErrorNotSupported;
+    }
+    h->blas = b;
+    return cudaSuccess;
+}
+
+void release_blas(nirc_handle* h) {
+    if (h->blas) cublasDestroy(static_cast<cublasHandle_t>(h->blas));
+    cudaFree(h->blas_ws);
+    h->blas = nullptr;
+    h->blas_ws = nullptr;
+}
+
+__global__ void k_fill(float* __restrict__ p, uint64_t n, float v) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 static TrainPtrs carve(void* base, const NetShape& s, uint64_t n, uint64_t chunk) {
@@ -125,7 +171,7 @@ static DetPtrs carve_det(const nirc_handle* h, void* base, uint64_t n, uint64_t 
     d.lvl_max = reinterpret_cast<unsigned*>(f);
     f += 64;
     d.loss_part = f;
-    f += round64((uint64_t)h->num_sms);
+    f += round64(max_train_blocks(h));
     d.gw_part = f;
     f += round64(max_grad_blocks(h) * s.n_mlp);
     d.acc = reinterpret_cast<unsigned long long*>(f);
@@ -141,7 +187,7 @@ __device__ __forceinline__ float fixed_scale(float m, uint64_t n) {
     return ldexpf(1.f, min(61 - e, 100));
 }
 
-__global__ void __launch_bounds__(kTrainThreads, 1)
+__global__ void __launch_bounds__(kTrainThreads, 2)
     k_train_fwd(NetShape s, GridParams g, float z_clamp, float loss_eps, float scale, const float* __restrict__ packed,
                 const float* __restrict__ table, const nirc_record* __restrict__ recs, const float* __restrict__ dirs,
                 const float* __restrict__ targets, uint64_t n, TrainPtrs tp, int store, int kind,
@@ -290,7 +336,7 @@ __device__ __forceinline__ float dot64(const float* __restrict__ wrow, const flo
     return (s0 + s1) + (s2 + s3);
 }
 
-__global__ void __launch_bounds__(kTrainThreads, 1)
+__global__ void __launch_bounds__(kTrainThreads, 2)
     k_train_bwd(NetShape s, GridParams g, const float* __restrict__ packed, const nirc_record* __restrict__ recs,
                 uint64_t n, TrainPtrs tp, int all_records, float* __restrict__ grad_table, float* __restrict__ de_out,
                 uint64_t de_ld, unsigned* __restrict__ lvl_max) {
@@ -527,7 +573,16 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     const bool det_hash = det && s.hashgrid;
     DetPtrs dp{};
     if (det) dp = carve_det(h, h->train_scratch, n, chunk);
+    float* ones = det ? nullptr
+                      : reinterpret_cast<float*>(h->train_scratch) + round64(3 * n + chunk * act_floats_per_sample(s));
     cudaError_t e;
+    if (!det) {
+        if ((e = prepare_blas(h)) != cudaSuccess) return e;
+        if (cublasSetStream(static_cast<cublasHandle_t>(h->blas), st) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorNotSupported;
+        k_fill<<<(uint32_t)((chunk + 255) / 256 < 1024 ? (chunk + 255) / 256 : 1024), 256, 0, st>>>(ones, chunk, 1.f);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if ((e = cudaMemsetAsync(h->grad, 0, s.n_dev * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
     if (det_hash) {
@@ -542,9 +597,9 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         return e;
     const float scale = 1.0f / (3.0f * (float)n);
     const float* table = h->params + s.hash_off;
-    auto blocks_for = [&](uint64_t m) {
+    auto blocks_for = [&](uint64_t m) {  // two 128-thread blocks per SM fit (shared memory and registers)
         uint64_t b = (m + kTrainThreads - 1) / kTrainThreads;
-        return (uint32_t)(b > (uint64_t)h->num_sms ? h->num_sms : b);
+        return (uint32_t)(b > max_train_blocks(h) ? max_train_blocks(h) : b);
     };
     // full-batch forward: loss and dL/dz, activations only when stored
     timer_begin(h, NIRC_K_TRAIN_FWD, st);
@@ -601,11 +656,28 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         if (gx > n_chunks) gx = n_chunks;
         if (gx < 1) gx = 1;
         timer_begin(h, NIRC_K_TRAIN_GRADW, st);
-        if (det) k_grad_w<true><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
-        else k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
-        if (det && (e = cudaGetLastError()) == cudaSuccess) {
-            // chunks add their block partials into grad in chunk order
-            k_sum_rows<<<(uint32_t)((s.n_mlp + 255) / 256), 256, 0, st>>>(dp.gw_part, gx, s.n_mlp, h->grad, 1);
+        if (!det && m < kBlasMinSamples) {
+            k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+        } else if (det) {
+            k_grad_w<true><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+            if ((e = cudaGetLastError()) == cudaSuccess) {
+                // chunks add their block partials into grad in chunk order
+                k_sum_rows<<<(uint32_t)((s.n_mlp + 255) / 256), 256, 0, st>>>(dp.gw_part, gx, s.n_mlp, h->grad, 1);
+            }
+        } else {
+            // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t]
+            cublasHandle_t bh = static_cast<cublasHandle_t>(h->blas);
+            const float one = 1.f;
+            for (uint32_t l = 0; l <= s.hidden; ++l) {
+                const GradJob& J = jobs.j[l];
+                if (cublasSgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)J.in, (int)J.out, (int)m, &one, J.x, (int)J.ld_x,
+                                J.dl, (int)J.ld_dl, &one, J.gw, (int)J.in) != CUBLAS_STATUS_SUCCESS ||
+                    cublasSgemv(bh, CUBLAS_OP_T, (int)m, (int)J.out, &one, J.dl, (int)J.ld_dl, ones, 1, &one,
+                                J.gw + (uint64_t)J.out * J.in, 1) != CUBLAS_STATUS_SUCCESS) {
+                    timer_end(h, NIRC_K_TRAIN_GRADW, st);
+                    return cudaErrorNotSupported;
+                }
+            }
         }
         timer_end(h, NIRC_K_TRAIN_GRADW, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
