@@ -96,6 +96,8 @@ typedef struct {
     int32_t freq_octaves;
     int32_t width;
     int32_t hidden_layers;
+    int32_t input_encoding; /* 0 frequency encodings of w and n, 1 the paper's (spherical harmonics + phi) */
+    int32_t pad0;
     double growth;
     double z_clamp;
     double loss_eps;
@@ -505,9 +507,23 @@ static int n_pos_features(const o_cfg* c)
     return c->pos_encoding == 1 ? c->hash_levels * c->feats_per_level : 3 * 2 * c->freq_octaves;
 }
 
+#define SH_COEFFS 25   /* real spherical harmonics of degree l = 0..4 */
+#define BLOB_BINS 4    /* one-blob bins of each phi scalar */
+#define PHI_FEATURES (3 + 2 * BLOB_BINS + BLOB_BINS)
+
+static int n_dir_features(const o_cfg* c)
+{
+    return c->input_encoding == 1 ? SH_COEFFS : 2 * 2 * c->freq_octaves;
+}
+
+static int n_surface_features(const o_cfg* c)
+{
+    return c->input_encoding == 1 ? PHI_FEATURES : 3 * 2 * c->freq_octaves;
+}
+
 static int n_inputs(const o_cfg* c)
 {
-    return n_pos_features(c) + 2 * 2 * c->freq_octaves + 3 * 2 * c->freq_octaves;
+    return n_pos_features(c) + n_dir_features(c) + n_surface_features(c);
 }
 
 /* sin(2^k pi v), cos(2^k pi v), k = 0..octaves-1 */
@@ -519,6 +535,94 @@ static int freq_encode(double v, int octaves, double* e)
         e[2 * k + 1] = cos(arg);
     }
     return 2 * octaves;
+}
+
+/* theta_hat = theta / pi and phi_hat = phi / (2 pi) in [0, 1) of a unit
+ * vector (polar angle from +z, azimuth from +x towards +y). */
+static void unit_angles(const float w[3], double* theta_hat, double* phi_hat)
+{
+    double wz = (double)w[2];
+    if (wz > 1.0) wz = 1.0;
+    if (wz < -1.0) wz = -1.0;
+    *theta_hat = acos(wz) / O_PI;
+    double ph = atan2((double)w[1], (double)w[0]) / (2.0 * O_PI);
+    if (ph < 0.0) ph += 1.0;
+    *phi_hat = ph;
+}
+
+static double factorial(int n)
+{
+    double f = 1.0;
+    for (int i = 2; i <= n; i++) f *= i;
+    return f;
+}
+
+/* Real spherical harmonics Y_l^m, l = 0..4, of the direction of w (paper,
+ * section "Neural Network Architecture": spherical-harmonics coefficients of
+ * w_i, 25 values per request), orthonormal on the unit sphere, stored at
+ * index l*l + l + m:
+ *   Y_l^0  = K_l^0 P_l^0(cos t)
+ *   Y_l^m  = sqrt(2) K_l^m P_l^m(cos t) cos(m p)   (m > 0)
+ *   Y_l^-m = sqrt(2) K_l^m P_l^m(cos t) sin(m p)   (m > 0)
+ * with K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), (t, p) the polar angle and
+ * azimuth of w, and P_l^m the associated Legendre functions without the
+ * Condon-Shortley phase, from the textbook recurrences
+ *   P_m^m = (2m-1)!! sin^m t,  P_{m+1}^m = (2m+1) cos t P_m^m,
+ *   (l-m) P_l^m = (2l-1) cos t P_{l-1}^m - (l+m-1) P_{l-2}^m. */
+void orc_sh_basis(const float w[3], double* e)
+{
+    double x = w[0], y = w[1], z = w[2];
+    double r = sqrt(x * x + y * y + z * z);
+    double ct = z / r, st = sqrt(x * x + y * y) / r;
+    double ph = atan2(y, x);
+    double P[5][5];
+    for (int m = 0; m <= 4; m++) {
+        double pmm = 1.0;
+        for (int i = 1; i <= m; i++) pmm *= (2.0 * i - 1.0) * st;
+        P[m][m] = pmm;
+        if (m + 1 <= 4) P[m + 1][m] = (2.0 * m + 1.0) * ct * pmm;
+        for (int l = m + 2; l <= 4; l++)
+            P[l][m] = ((2.0 * l - 1.0) * ct * P[l - 1][m] - (l + m - 1.0) * P[l - 2][m]) / (l - m);
+    }
+    for (int l = 0; l <= 4; l++) {
+        for (int m = 0; m <= l; m++) {
+            double K = sqrt((2.0 * l + 1.0) / (4.0 * O_PI) * factorial(l - m) / factorial(l + m));
+            if (m == 0) {
+                e[l * l + l] = K * P[l][0];
+            } else {
+                e[l * l + l + m] = sqrt(2.0) * K * P[l][m] * cos(m * ph);
+                e[l * l + l - m] = sqrt(2.0) * K * P[l][m] * sin(m * ph);
+            }
+        }
+    }
+}
+
+/* One-blob encoding of s in [0, 1] into k bins (Mueller et al. 2019, the
+ * encoding NRC gives these inputs): a Gaussian kernel of standard deviation
+ * 1/k centred at s, integrated over each bin [i/k, (i+1)/k):
+ *   e_i = G((i+1)/k - s) - G(i/k - s),  G(u) = (1 + erf(u k / sqrt 2)) / 2,
+ * with no wrap-around at the ends. */
+void orc_one_blob(double s, int k, double* e)
+{
+    double scale = k / sqrt(2.0);
+    for (int i = 0; i < k; i++) {
+        double lo = (double)i / k - s, hi = (double)(i + 1) / k - s;
+        e[i] = 0.5 * (erf(hi * scale) - erf(lo * scale));
+    }
+}
+
+/* The per-surface inputs phi of the paper's encoding (paper: shading normal,
+ * albedo and roughness fed with NRC's encodings): albedo as is (3), the
+ * normal's (theta_hat, phi_hat) one-blob encoded (2 x 4) and the roughness
+ * one-blob encoded (4). */
+static void phi_encode(const o_record* rec, double* e)
+{
+    for (int k = 0; k < 3; k++) e[k] = (double)rec->albedo[k];
+    double th, ph;
+    unit_angles(rec->n, &th, &ph);
+    orc_one_blob(th, BLOB_BINS, e + 3);
+    orc_one_blob(ph, BLOB_BINS, e + 3 + BLOB_BINS);
+    orc_one_blob((double)rec->roughness, BLOB_BINS, e + 3 + 2 * BLOB_BINS);
 }
 
 static uint32_t grid_resolution(const o_cfg* c, int level)
@@ -565,12 +669,16 @@ void orc_hash_level(const o_cfg* c, int level, const float x[3], uint32_t idx[8]
     }
 }
 
-/* Network input for shading point (p, n) and incident direction w:
- * [position features][theta_hat, phi_hat features][normal features]. */
-static void encode(const o_cfg* c, const double* hash_table, const float p[3], const float n[3],
-                   const float w[3], double* e)
+/* Network input for the shading record rec and incident direction w:
+ * [position features][direction features][surface features].
+ * input_encoding 0: direction = frequency encoding of (theta_hat, phi_hat),
+ *   surface = frequency encoding of the normal's three components;
+ * input_encoding 1 (the paper's): direction = the 25 spherical-harmonics
+ *   values of w, surface = phi (albedo, normal and roughness). */
+static void encode(const o_cfg* c, const double* hash_table, const o_record* rec, const float w[3], double* e)
 {
     int k = 0;
+    const float* p = rec->p;
     if (c->pos_encoding == 1) {
         uint64_t T = 1ull << c->log2_table;
         int F = c->feats_per_level;
@@ -588,15 +696,16 @@ static void encode(const o_cfg* c, const double* hash_table, const float p[3], c
     } else {
         for (int d = 0; d < 3; d++) k += freq_encode((double)p[d], c->freq_octaves, e + k);
     }
-    double wz = (double)w[2];
-    if (wz > 1.0) wz = 1.0;
-    if (wz < -1.0) wz = -1.0;
-    double theta_hat = acos(wz) / O_PI;
-    double phi_hat = atan2((double)w[1], (double)w[0]) / (2.0 * O_PI);
-    if (phi_hat < 0.0) phi_hat += 1.0;
+    if (c->input_encoding == 1) {
+        orc_sh_basis(w, e + k);
+        phi_encode(rec, e + k + SH_COEFFS);
+        return;
+    }
+    double theta_hat, phi_hat;
+    unit_angles(w, &theta_hat, &phi_hat);
     k += freq_encode(theta_hat, c->freq_octaves, e + k);
     k += freq_encode(phi_hat, c->freq_octaves, e + k);
-    for (int d = 0; d < 3; d++) k += freq_encode((double)n[d], c->freq_octaves, e + k);
+    for (int d = 0; d < 3; d++) k += freq_encode((double)rec->n[d], c->freq_octaves, e + k);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -664,14 +773,14 @@ static void cache_eval(const o_cfg* c, const double* params, const o_record* rec
     double e[1024];
     double z[3];
     const double* hash = params + mlp_param_count(c);
-    encode(c, hash, rec->p, rec->n, w, e);
+    encode(c, hash, rec, w, e);
     mlp_forward(c, params, e, NULL, NULL, z);
     for (int k = 0; k < 3; k++) nval[k] = exp(z[k] < c->z_clamp ? z[k] : c->z_clamp);
 }
 
 void orc_encode(const o_cfg* c, const double* params, const o_record* rec, const float w[3], double* e)
 {
-    encode(c, params + mlp_param_count(c), rec->p, rec->n, w, e);
+    encode(c, params + mlp_param_count(c), rec, w, e);
 }
 
 void orc_mlp(const o_cfg* c, const double* params, const double* e, double z[3])
@@ -1204,7 +1313,7 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
         for (int64_t t = 0; t < (int64_t)T; t++) {
             if (!gout && !(recs[t].flags & 1u)) continue;
             double z[3];
-            encode(c, hash, recs[t].p, recs[t].n, dirs + 3 * t, e);
+            encode(c, hash, &recs[t], dirs + 3 * t, e);
             mlp_forward(c, params, e, pre, act, z);
             double dz[3];
             double lt = 0.0;

@@ -23,6 +23,7 @@ class OCfg(ctypes.Structure):
         ("feats_per_level", ctypes.c_int32), ("log2_table", ctypes.c_int32),
         ("base_res", ctypes.c_int32), ("freq_octaves", ctypes.c_int32),
         ("width", ctypes.c_int32), ("hidden_layers", ctypes.c_int32),
+        ("input_encoding", ctypes.c_int32), ("pad0", ctypes.c_int32),
         ("growth", ctypes.c_double), ("z_clamp", ctypes.c_double),
         ("loss_eps", ctypes.c_double),
     ]
@@ -53,6 +54,8 @@ def lib():
         L.orc_hash_level.argtypes = [P, i32, P, P, P]
         L.orc_encode.argtypes = [P, P, P, P, P]
         L.orc_mlp.argtypes = [P, P, P, P]
+        L.orc_sh_basis.argtypes = [P, P]
+        L.orc_one_blob.argtypes = [f64, i32, P]
         L.orc_query.argtypes = [P, P, P, P, u64, P]
         L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P, P]
         L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, u32, P, P, P, P]
@@ -84,7 +87,7 @@ def _ptr(a: np.ndarray):
 def ocfg(cfg) -> OCfg:
     return OCfg(cfg.pos_encoding, cfg.hash_levels, cfg.feats_per_level, cfg.log2_table,
                 cfg.base_res, cfg.freq_octaves, cfg.width, cfg.hidden_layers,
-                float(cfg.growth), float(cfg.z_clamp), float(cfg.loss_eps))
+                int(getattr(cfg, "input_encoding", 0)), 0, float(cfg.growth), float(cfg.z_clamp), float(cfg.loss_eps))
 
 
 def oframe(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode=0,
@@ -136,6 +139,20 @@ def encode(cfg, params, rec, w) -> np.ndarray:
     wf = np.ascontiguousarray(w, np.float32)
     e = np.zeros(cfg.n_inputs, np.float64)
     lib().orc_encode(ctypes.byref(c), _ptr(p), _ptr(r), _ptr(wf), _ptr(e))
+    return e
+
+
+def sh_basis(w) -> np.ndarray:
+    """The 25 real spherical harmonics (l <= 4, index l*l + l + m) of w."""
+    wf = np.ascontiguousarray(w, np.float32)
+    e = np.zeros(25, np.float64)
+    lib().orc_sh_basis(_ptr(wf), _ptr(e))
+    return e
+
+
+def one_blob(s: float, k: int = 4) -> np.ndarray:
+    e = np.zeros(k, np.float64)
+    lib().orc_one_blob(float(s), int(k), _ptr(e))
     return e
 
 

@@ -287,6 +287,7 @@ def furnace_scene(width: int, height: int, rho: float = 0.5, emission: float = 1
 # ---------------------------------------------------------------------------
 
 POS_FREQ, POS_HASHGRID = 0, 1
+INPUT_FREQ, INPUT_SH = 0, 1  # network input: frequency encodings, or the paper's SH + phi
 
 
 @dataclasses.dataclass
@@ -301,6 +302,7 @@ class NetConfig:
     freq_octaves: int = 4
     width: int = 64
     hidden_layers: int = 3
+    input_encoding: int = INPUT_FREQ
     lr: float = 1e-3
     beta1: float = 0.9
     beta2: float = 0.99
@@ -315,9 +317,19 @@ class NetConfig:
         return 3 * 2 * self.freq_octaves
 
     @property
+    def n_dir_features(self) -> int:
+        return 25 if self.input_encoding == INPUT_SH else 2 * 2 * self.freq_octaves
+
+    @property
+    def n_surface_features(self) -> int:
+        return 3 + 4 + 4 + 4 if self.input_encoding == INPUT_SH else 3 * 2 * self.freq_octaves
+
+    @property
     def n_inputs(self) -> int:
-        """Position features + direction (theta, phi) + normal features."""
-        return self.n_pos_features + 2 * 2 * self.freq_octaves + 3 * 2 * self.freq_octaves
+        """Position + direction + per-surface features: frequency encodings of
+        (theta, phi) and of the normal, or (INPUT_SH) spherical harmonics of
+        the direction and albedo / one-blob normal / one-blob roughness."""
+        return self.n_pos_features + self.n_dir_features + self.n_surface_features
 
     def layer_shapes(self):
         """(fan_out, fan_in) of each weight matrix, input layer first."""
@@ -353,6 +365,14 @@ def config_1080p() -> NetConfig:
     exp output and Adam's normalised first steps overshoot and the cache
     sinks towards 0 within a few dozen frames on this workload)."""
     return NetConfig(pos_encoding=POS_HASHGRID, hidden_layers=4, lr=1e-3)
+
+
+def config_paper_1080p() -> NetConfig:
+    """The paper's network input on the 1080p workload: 12-level hash grid
+    (2 features), spherical harmonics of degree <= 4 of the direction (25)
+    and albedo + one-blob normal + one-blob roughness (15), 64 inputs; width
+    64 with 4 hidden layers, Adam lr 1e-3."""
+    return NetConfig(pos_encoding=POS_HASHGRID, hash_levels=12, hidden_layers=4, input_encoding=INPUT_SH, lr=1e-3)
 
 
 def init_params(cfg: NetConfig, seed: int = 1) -> np.ndarray:
@@ -414,9 +434,11 @@ def analytic_field(x: np.ndarray, w: np.ndarray, fp) -> np.ndarray:
 
 
 def training_batch(n: int, seed: int = 3, field_seed: int = 7):
-    """Seeded training batch: records with x ~ U[0,1]^3 and normal uniform on
-    the sphere, directions uniform on the sphere, targets from the analytic
-    field.  Returns (records[RECORD_DTYPE], dirs f32 (n,3), targets f32 (n,3))."""
+    """Seeded training batch: records with x ~ U[0,1]^3, normal uniform on
+    the sphere, albedo ~ U[0.2,0.8]^3 and roughness ~ U[0.05,1] (the scene
+    family's materials), directions uniform on the sphere, targets from the
+    analytic field (of x and the direction only).  Returns
+    (records[RECORD_DTYPE], dirs f32 (n,3), targets f32 (n,3))."""
     rng = np.random.default_rng(seed)
     x = rng.uniform(0.0, 1.0, (n, 3))
     nrm = _unit_sphere(rng, n)
@@ -425,8 +447,8 @@ def training_batch(n: int, seed: int = 3, field_seed: int = 7):
     rec["p"] = x
     rec["n"] = nrm
     rec["wo"] = nrm
-    rec["albedo"] = 0.5
-    rec["roughness"] = 1.0
+    rec["albedo"] = rng.uniform(0.2, 0.8, (n, 3))
+    rec["roughness"] = rng.uniform(0.05, 1.0, n)
     rec["prim"] = 0
     rec["flags"] = 1 | (MAT_LAMBERT << 1)
     tgt = analytic_field(x, w, analytic_field_params(field_seed))

@@ -5,6 +5,7 @@ known answer, a closed form, an invariant of the method or a statistical
 expectation, chosen so that a dropped term, a wrong sign or index, or a
 transposed operand in that part fails here.
 """
+import dataclasses
 import math
 import os
 import subprocess
@@ -329,6 +330,113 @@ def test_trilinear_partition_of_unity_and_affine_reproduction(oracle):
         assert abs(e[1] - ps[1]) < 1e-9
 
 
+def _scipy_real_sh(w):
+    """Real spherical harmonics (l <= 4, index l*l + l + m, no Condon-Shortley
+    phase) from scipy's complex Y_l^m: for m > 0 the cosine and sine parts
+    are sqrt(2) (-1)^m Re / Im of Y_l^m (the (-1)^m removes scipy's phase)."""
+    ss = pytest.importorskip("scipy.special")
+    w = np.asarray(w, np.float64)
+    w = w / np.linalg.norm(w)
+    theta = math.acos(max(-1.0, min(1.0, w[2])))
+    phi = math.atan2(w[1], w[0])
+    out = np.zeros(25)
+    for l in range(5):
+        out[l * l + l] = ss.sph_harm_y(l, 0, theta, phi).real
+        for m in range(1, l + 1):
+            y = ss.sph_harm_y(l, m, theta, phi) * math.sqrt(2.0) * (-1) ** m
+            out[l * l + l + m] = y.real
+            out[l * l + l - m] = y.imag
+    return out
+
+
+def test_spherical_harmonics_match_library(oracle):
+    """The oracle's real SH basis (degree <= 4, 25 values: the paper's
+    direction input) against scipy's complex spherical harmonics."""
+    rng = np.random.default_rng(41)
+    dirs = rng.normal(size=(200, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    dirs = np.concatenate([dirs, np.eye(3), -np.eye(3)]).astype(np.float32)
+    for w in dirs:
+        assert np.allclose(oracle.sh_basis(w), _scipy_real_sh(w.astype(np.float64)), rtol=0, atol=1e-12), w
+
+
+def test_spherical_harmonics_closed_forms_and_orthonormality(oracle):
+    """Y_0^0 = 1/(2 sqrt(pi)), (Y_1^-1, Y_1^0, Y_1^1) = sqrt(3/(4 pi)) (y, z, x),
+    Y_2^-2 = sqrt(15/(4 pi)) x y; and the 25 functions are orthonormal on the
+    sphere (Gauss-Legendre in cos t x uniform azimuth, exact for these
+    degrees up to the float32 rounding of the nodes)."""
+    w = np.array([0.48, -0.6, 0.64], np.float32)
+    e = oracle.sh_basis(w)
+    x, y, z = (float(v) / float(np.linalg.norm(w.astype(np.float64))) for v in w)
+    assert abs(e[0] - 0.5 / math.sqrt(math.pi)) < 1e-15
+    assert np.allclose(e[1:4], math.sqrt(3 / (4 * math.pi)) * np.array([y, z, x]), atol=1e-14)
+    assert abs(e[4] - math.sqrt(15 / (4 * math.pi)) * x * y) < 1e-14
+    assert abs(e[6] - math.sqrt(5 / (16 * math.pi)) * (3 * z * z - 1)) < 1e-14
+    ct, wt = np.polynomial.legendre.leggauss(12)
+    n_az = 16
+    G = np.zeros((25, 25))
+    for c, wq in zip(ct, wt):
+        s_ = math.sqrt(1 - c * c)
+        for j in range(n_az):
+            a = 2 * math.pi * j / n_az
+            v = oracle.sh_basis(np.array([s_ * math.cos(a), s_ * math.sin(a), c], np.float32))
+            G += np.outer(v, v) * wq * (2 * math.pi / n_az)
+    assert np.allclose(G, np.eye(25), atol=2e-6), np.abs(G - np.eye(25)).max()
+
+
+def test_one_blob_matches_gaussian_bin_masses(oracle):
+    """One-blob (k = 4): the mass of a Gaussian of standard deviation 1/4
+    centred at s in each quarter of [0, 1], from scipy's normal CDF; the
+    encoding mirrors under s -> 1 - s and its bins sum to the mass of [0, 1]."""
+    norm = pytest.importorskip("scipy.stats").norm
+    for s_ in [0.0, 0.1, 0.25, 0.5, 0.77, 1.0]:
+        e = oracle.one_blob(s_, 4)
+        edges = np.arange(5) / 4.0
+        ref = np.diff(norm.cdf(edges, loc=s_, scale=0.25))
+        assert np.allclose(e, ref, atol=1e-15), (s_, e, ref)
+        assert np.allclose(oracle.one_blob(1.0 - s_, 4), e[::-1], atol=1e-15)
+        assert abs(e.sum() - (norm.cdf(1, s_, 0.25) - norm.cdf(0, s_, 0.25))) < 1e-14
+
+
+def test_paper_input_layout(oracle):
+    """The paper's network input: 12 hash levels x 2 features (24), 25
+    spherical-harmonics values of w and 15 per-surface values phi =
+    [albedo (3), one-blob theta_hat and phi_hat of the normal (2 x 4),
+    one-blob roughness (4)], 64 inputs in all; checked piece by piece against
+    the library SH, the normal CDF and the stored albedo."""
+    norm = pytest.importorskip("scipy.stats").norm
+    cfg = scenes.config_paper_1080p()
+    assert (cfg.n_pos_features, cfg.n_dir_features, cfg.n_surface_features, cfg.n_inputs) == (24, 25, 15, 64)
+    cfg_small = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=12, log2_table=10,
+                                 input_encoding=scenes.INPUT_SH)
+    params = scenes.init_params(cfg_small, 3)
+    rng = np.random.default_rng(43)
+    params[cfg_small.n_mlp_params:] = rng.uniform(-1, 1, cfg_small.n_hash_params)
+    cfg_freq = dataclasses.replace(cfg_small, input_encoding=scenes.INPUT_FREQ)
+    pf = np.concatenate([scenes.init_params(cfg_freq, 3)[:cfg_freq.n_mlp_params], params[cfg_small.n_mlp_params:]])
+
+    def blob(v):
+        return np.diff(norm.cdf(np.arange(5) / 4.0, loc=v, scale=0.25))
+
+    for i in range(20):
+        nrm = rng.normal(size=3)
+        rec = _lambert_record(n=nrm, albedo=rng.uniform(0.2, 0.8, 3), roughness=rng.uniform(0.05, 1), p=rng.uniform(0, 1, 3))
+        w = rng.normal(size=3)
+        w = (w / np.linalg.norm(w)).astype(np.float32)
+        e = oracle.encode(cfg_small, params, rec, w)
+        assert e.shape == (64,)
+        # position features are the hash-grid features of the frequency layout
+        assert np.array_equal(e[:24], oracle.encode(cfg_freq, pf, rec, w)[:24])
+        assert np.allclose(e[24:49], _scipy_real_sh(w.astype(np.float64)), atol=1e-12)
+        n32 = rec["n"][0].astype(np.float64)
+        th = math.acos(max(-1.0, min(1.0, n32[2]))) / math.pi
+        ph = math.atan2(n32[1], n32[0]) / (2 * math.pi) % 1.0
+        assert np.array_equal(e[49:52], rec["albedo"][0].astype(np.float64))
+        assert np.allclose(e[52:56], blob(th), atol=1e-14)
+        assert np.allclose(e[56:60], blob(ph), atol=1e-14)
+        assert np.allclose(e[60:64], blob(float(rec["roughness"][0])), atol=1e-14)
+
+
 # ---------------------------------------------------------------------------
 # Network
 # ---------------------------------------------------------------------------
@@ -580,6 +688,25 @@ def test_gradients_finite_differences_1024_samples(oracle):
     touched = np.nonzero(g[cfg.n_mlp_params:])[0] + cfg.n_mlp_params
     idx = np.concatenate([rng.choice(touched, 30, replace=False), rng.choice(cfg.n_mlp_params, 30, replace=False),
                           np.arange(cfg.n_mlp_params - 3, cfg.n_mlp_params)])
+    _fd_check(oracle, cfg, params, recs, dirs, tg.astype(np.float64), idx)
+
+
+def test_gradients_finite_differences_paper_input(oracle):
+    """The training gradient with the paper's input (12-level hash grid, SH
+    of the direction, phi) against FP64 central differences."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=12, log2_table=10, hidden_layers=3,
+                           base_res=4, growth=1.5, input_encoding=scenes.INPUT_SH)
+    params = scenes.init_params(cfg, 31).astype(np.float64)
+    rng = np.random.default_rng(32)
+    params[:cfg.n_mlp_params] += rng.normal(0, 0.02, cfg.n_mlp_params)
+    params[cfg.n_mlp_params:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params)
+    recs, dirs, tg = scenes.training_batch(128, seed=33)
+    _, g = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    touched = np.nonzero(g[cfg.n_mlp_params:])[0] + cfg.n_mlp_params
+    # input-layer weights of every segment: position, SH and phi columns
+    w0 = [o * 64 + i for o in (0, 17, 63) for i in (0, 23, 24, 40, 48, 49, 55, 63)]
+    idx = np.concatenate([rng.choice(touched, 30, replace=False), rng.choice(cfg.n_mlp_params, 30, replace=False),
+                          np.array(w0)])
     _fd_check(oracle, cfg, params, recs, dirs, tg.astype(np.float64), idx)
 
 
