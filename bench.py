@@ -37,6 +37,13 @@ from paper_2412_04634_gb300 import scenes  # noqa: E402
 
 METRIC = "NIRC queries/s & 1080p ms/frame, FP16 TC vs FP32 at equal MRSE; p50/p99"
 WORKLOAD = "1080p dynamic Cornell family (256 prims, GGX), hash-grid NIRC 16x2 T=2^19, MLP 64x4, N=16 M=1 depth 5, 65536 train samples/frame"
+WORKLOAD_SH = ("1080p dynamic Cornell family (256 prims, GGX), the paper's NIRC input: hash grid 12x2 T=2^19 + "
+               "spherical harmonics l<=4 (25) + albedo/one-blob normal/one-blob roughness (15), MLP 64x4, N=16 M=1 "
+               "depth 5, 65536 train samples/frame")
+
+
+def workload_name(args):
+    return WORKLOAD_SH if getattr(args, "input", "freq") == "sh" else WORKLOAD
 
 
 def parse_args():
@@ -62,6 +69,10 @@ def parse_args():
                     help="frame: the 1080p frame step (default); train: the training step alone on "
                          "2^16 / 2^18 / 2^20 samples of the analytic radiance field; serve: the frame-request "
                          "server on a Poisson stream of mixed-resolution requests over 8 resident scenes")
+    ap.add_argument("--input", choices=["freq", "sh"], default="freq",
+                    help="network input of the frame workload: frequency encodings of direction and normal with "
+                         "the 16-level hash grid (default), or the paper's (12-level hash grid, spherical "
+                         "harmonics, albedo / one-blob normal and roughness)")
     ap.add_argument("--light-mode", type=int, choices=[0, 1], default=0,
                     help="1: the cache carries L_ind, direct light by NEE + MIS (frame and serve workloads)")
     ap.add_argument("--serve-requests", type=int, default=256)
@@ -154,7 +165,7 @@ def build_workload(args, seed_offset=0):
     W, H = args.width, args.height
     base = scenes.cornell_scene(W, H, seed=1 + seed_offset, n_prims=args.prims, glossy=True, moving_emitter=True)
     frames = [scenes.scene_at_frame(base, f) for f in range(60)]
-    cfg = scenes.config_1080p()
+    cfg = scenes.config_paper_1080p() if args.input == "sh" else scenes.config_1080p()
     params = scenes.init_params(cfg, 1 + seed_offset)
     return cfg, params, frames
 
@@ -167,8 +178,8 @@ def flops_per_frame(cfg, args):
     """Algorithmic FLOPs of the cache integral: per row the direction part of
     layer 0, the hidden layers and the output layer; per pixel the shared
     per-surface part of layer 0."""
-    per_row = 2 * (16 * 64 + (cfg.hidden_layers - 1) * 64 * 64 + 64 * 3)
-    n_pix_features = cfg.n_pos_features + 24
+    per_row = 2 * (cfg.n_dir_features * 64 + (cfg.hidden_layers - 1) * 64 * 64 + 64 * 3)
+    n_pix_features = cfg.n_pos_features + cfg.n_surface_features
     per_pixel = 2 * n_pix_features * 64
     return rows_per_frame(args) * per_row + args.width * args.height * per_pixel, per_row, per_pixel
 
@@ -304,7 +315,8 @@ def recorded_traffic(args, precision):
     or the kernel's sources have changed since the counters were taken."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"k_cache_tc_{precision}_1080p.traffic.txt")
-    if not os.path.exists(path) or (args.width, args.height, args.n_cache, args.n_resid) != (1920, 1080, 16, 1):
+    if not os.path.exists(path) or (args.width, args.height, args.n_cache, args.n_resid) != (1920, 1080, 16, 1) \
+            or args.input != "freq":
         return None
     rec, srcs = {}, []
     for line in open(path):
@@ -434,7 +446,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16", "bf16": "bf16", "fp8": "e4m3+f16"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": args.width, "height": args.height, "n_cache": args.n_cache,
+        "config": {"workload": workload_name(args), "width": args.width, "height": args.height, "n_cache": args.n_cache,
                    "n_resid": args.n_resid, "max_depth": args.depth, "prims": run.n_prims,
                    "train_samples": args.train,
                    "precision": {"fp32": "fp32_simt", "fp16": "fp16_tc", "bf16": "bf16_tc",
@@ -544,7 +556,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "width": args.width, "height": args.height, "n_cache": args.n_cache,
+        "config": {"workload": workload_name(args), "width": args.width, "height": args.height, "n_cache": args.n_cache,
                    "n_resid": args.n_resid, "max_depth": args.depth, "train_samples": args.train,
                    "sample_pixels_per_step": n},
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": O.num_threads(), "kind": "oracle",

@@ -69,11 +69,31 @@ typedef enum nirc_pos_encoding {
                               "Neural Network Architecture", first bullet) */
 } nirc_pos_encoding;
 
+typedef enum nirc_input_encoding {
+    NIRC_INPUT_FREQ = 0,  /* direction (theta/pi, phi/2pi) and normal by
+                             frequency features (the 64x64 and 1080p workloads) */
+    NIRC_INPUT_SH = 1     /* the paper's input (section "Neural Network
+                             Architecture", encoding bullets and the system
+                             figure's 24 + 25 + 15 inputs): direction by the 25
+                             real spherical harmonics of degree <= 4, and
+                             phi = albedo (3), one-blob normal angles (2 x 4)
+                             and one-blob roughness (4) */
+} nirc_input_encoding;
+
 /* Cache hyper-parameters.  Network input, in order: position features
- * (3 dims x 2 x freq_octaves, or hash_levels x feats_per_level), the
- * incident direction as (theta/pi, phi/2pi) with 2 x 2 x freq_octaves
- * features, and the shading normal with 3 x 2 x freq_octaves features.
- * Frequency features of a scalar v are sin(2^k pi v), cos(2^k pi v).
+ * (3 dims x 2 x freq_octaves, or hash_levels x feats_per_level), then
+ * direction and per-surface features by `input_encoding`:
+ *  NIRC_INPUT_FREQ: the incident direction as (theta/pi, phi/2pi) with
+ *   2 x 2 x freq_octaves features, and the shading normal with
+ *   3 x 2 x freq_octaves features.  Frequency features of a scalar v are
+ *   sin(2^k pi v), cos(2^k pi v).
+ *  NIRC_INPUT_SH: Y_l^m(w), l = 0..4, at index l*l + l + m (orthonormal
+ *   real harmonics: sqrt(2) K_l^m P_l^m(cos t) cos(m p) for m > 0, sin(|m| p)
+ *   for m < 0, no Condon-Shortley phase); then albedo, the one-blob
+ *   encodings of the normal's theta/pi and phi/2pi and of the roughness, each
+ *   4 bins holding the mass of a Gaussian of standard deviation 1/4 centred
+ *   at the value over [i/4, (i+1)/4) (no wrap-around).  Needs
+ *   position features + 15 <= 64.
  * Hidden layers: `hidden_layers` ReLU layers of `width` (only 64 is
  * supported), output 3 logits z, cache value n = exp(min(z, z_clamp)). */
 typedef struct nirc_config {
@@ -92,6 +112,7 @@ typedef struct nirc_config {
     float adam_eps;            /* e.g. 1e-15 */
     float loss_eps;            /* eps of eq. 12, e.g. 0.01 */
     float z_clamp;             /* e.g. 15 */
+    uint32_t input_encoding;   /* nirc_input_encoding */
 } nirc_config;
 
 /* Shading record: one surface point (paper: "surface parameter buffer",

@@ -38,18 +38,17 @@ __device__ __forceinline__ void surface_product(const NetShape& s, const float* 
 }
 
 // One row: direction features -> layer 0 (with h_pix) -> hidden -> logits.
+template <bool kSh>
 __device__ __forceinline__ float3 row_mlp(const NetShape& s, const float* __restrict__ sw, float* act, int stride,
                                           const float2 (&hpix)[32], V3 wi, float z_clamp) {
-    float th, ph;
-    dir_angles(wi, th, ph);
-    float e[16];
-    freq4_accurate(th, e);
-    freq4_accurate(ph, e + 8);
+    constexpr int nd = dir_features<kSh>();
+    float e[nd];
+    dir_encode<kSh>(wi, e);
     float2 acc[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = hpix[q];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) fma_row(acc, sw + s.off_wdir + i * kWidth, e[i]);
+    for (int i = 0; i < nd; ++i) fma_row(acc, sw + s.off_wdir + i * kWidth, e[i]);
     for (uint32_t l = 1; l < s.hidden; ++l) {
         store_relu(acc, act, stride);
         const float* Wl = sw + s.off_hidden + (l - 1) * (kWidth * kWidth + kWidth);
@@ -75,6 +74,7 @@ __device__ __forceinline__ float3 row_mlp(const NetShape& s, const float* __rest
                        expf(fminf(z23.x, z_clamp)));
 }
 
+template <bool kSh>
 __global__ void __launch_bounds__(kSimtThreads, 1)
     k_cache_simt(CacheArgs a, const float* __restrict__ packed, const float* __restrict__ table,
                  const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
 
         float2 hpix[32];
         if (network && __any_sync(0xffffffffu, valid)) {
-            encode_surface(a.s, a.g, table, p, n, act, stride);
+            encode_surface(a.s, a.g, table, p, n, alb, rough, act, stride);
             surface_product(a.s, sw, act, stride, hpix);
         }
         Kahan3 lc, sub;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
             }
             float3 nv = make_float3(0.f, 0.f, 0.f);
             if (network) {
-                if (__any_sync(0xffffffffu, ok)) nv = row_mlp(a.s, sw, act, stride, hpix, wi, a.z_clamp);
+                if (__any_sync(0xffffffffu, ok)) nv = row_mlp<kSh>(a.s, sw, act, stride, hpix, wi, a.z_clamp);
             } else if (a.cache_mode == 2) {
                 nv = make_float3(a.cc0, a.cc1, a.cc2);
             }
@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
     }
 }
 
+template <bool kSh>
 __global__ void __launch_bounds__(kSimtThreads, 1)
     k_query_simt(NetShape s, GridParams g, float z_clamp, const float* __restrict__ packed,
                  const float* __restrict__ table, const nirc_record* __restrict__ recs, const float* __restrict__ dirs,
@@ -200,13 +201,13 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
     for (uint64_t i = (uint64_t)blockIdx.x * kSimtThreads + threadIdx.x; i < n_rows;
          i += (uint64_t)gridDim.x * kSimtThreads) {
         const float4* rq = reinterpret_cast<const float4*>(recs + i);
-        const float4 r0 = __ldg(rq), r1 = __ldg(rq + 1);
+        const float4 r0 = __ldg(rq), r1 = __ldg(rq + 1), r2 = __ldg(rq + 2), r3 = __ldg(rq + 3);
         const V3 p{r0.x, r0.y, r0.z}, n{r0.w, r1.x, r1.y};
         const V3 wi{__ldg(dirs + 3 * i), __ldg(dirs + 3 * i + 1), __ldg(dirs + 3 * i + 2)};
-        encode_surface(s, g, table, p, n, act, stride);
+        encode_surface(s, g, table, p, n, make_float3(r2.y, r2.z, r2.w), r3.x, act, stride);
         float2 hpix[32];
         surface_product(s, sw, act, stride, hpix);
-        const float3 nv = row_mlp(s, sw, act, stride, hpix, wi, z_clamp);
+        const float3 nv = row_mlp<kSh>(s, sw, act, stride, hpix, wi, z_clamp);
         out[3 * i] = nv.x;
         out[3 * i + 1] = nv.y;
         out[3 * i + 2] = nv.z;
@@ -221,7 +222,7 @@ __global__ void k_repack_simt(NetShape s, const float* __restrict__ params, floa
     float v = 0.f;
     if (idx < s.off_wdir) {
         const uint32_t k = idx / kWidth, o = idx % kWidth;
-        const uint32_t col = k < s.n_pos ? k : k + kDirFeatures;
+        const uint32_t col = k < s.n_pos ? k : k + s.n_dir;
         v = params[o * n_in + col];
     } else if (idx < s.off_b0) {
         const uint32_t k = (idx - s.off_wdir) / kWidth, o = (idx - s.off_wdir) % kWidth;
@@ -274,28 +275,29 @@ cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, c
     a.s = h->shape;
     a.g = h->grid;
     const size_t smem = simt_smem(h->shape);
-    cudaError_t e = cudaFuncSetAttribute(k_cache_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = h->shape.sh ? k_cache_simt<true> : k_cache_simt<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const uint64_t P = (uint64_t)fd.width * fd.height;
     uint64_t blocks = (P + kSimtThreads - 1) / kSimtThreads;
     if (blocks > 2ull * h->num_sms) blocks = 2ull * h->num_sms;
     const float* table = h->params + h->shape.hash_off;
-    k_cache_simt<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(a, h->packed, table, recs, base, rows,
-                                                               reinterpret_cast<float4*>(out_rgba), lc, lr, sig,
-                                                               count, row_n);
+    kern<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(a, h->packed, table, recs, base, rows,
+                                                       reinterpret_cast<float4*>(out_rgba), lc, lr, sig, count, row_n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, const float* dirs, uint64_t n, float* out,
                               cudaStream_t st) {
     const size_t smem = simt_smem(h->shape);
-    cudaError_t e = cudaFuncSetAttribute(k_query_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = h->shape.sh ? k_query_simt<true> : k_query_simt<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     uint64_t blocks = (n + kSimtThreads - 1) / kSimtThreads;
     if (blocks > 2ull * h->num_sms) blocks = 2ull * h->num_sms;
     const float* table = h->params + h->shape.hash_off;
-    k_query_simt<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(h->shape, h->grid, h->cfg.z_clamp, h->packed, table,
-                                                               recs, dirs, n, out);
+    kern<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(h->shape, h->grid, h->cfg.z_clamp, h->packed, table, recs, dirs,
+                                                       n, out);
     return cudaGetLastError();
 }
 

@@ -28,6 +28,13 @@
 //                carrying a pixel that straddles two tiles, and writes the
 //                pixel (eq. L_mlmc = L_e + L_c + L_r).
 //
+// The paper's input (NIRC_INPUT_SH): the pixel stage encodes [position |
+// albedo, one-blob normal and roughness]; H is stored pixel-major (row t =
+// pixel t's h_pix in 16 bits, the A-tile swizzle); a row writes the 25
+// spherical harmonics of its direction (K = 32, two MMAs against the SH
+// columns of layer 0) and the layer-0 epilogue adds its pixel's H row.  Any
+// S >= 1 works (no one-hot window).
+//
 // FP8 (E4M3) mode: the hidden 64x64 layers run as kind::f8f6f4 MMAs (K = 32,
 // two per layer) on E4M3 weights and activations with per-layer scales:
 // weights W / s_w with s_w = amax|W| / 448 (taken when the weights are
@@ -107,13 +114,13 @@ __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_
         uint32_t n = r / 64, k = r % 64;
         float v = 0.f;
         uint32_t off;
-        if (m == 0) {  // surface columns of layer 0: [pos][nrm] -> master columns [pos][dir][nrm]
+        if (m == 0) {  // surface columns of layer 0: [pos][surf] -> master columns [pos][dir][surf]
             off = tcimg::off_w0pix();
             if (k < s.n_pos) v = params[n * n_in + k];
-            else if (k < s.n_pix) v = params[n * n_in + k + kDirFeatures];
+            else if (k < s.n_pix) v = params[n * n_in + k + s.n_dir];
         } else if (m == 1) {  // direction columns of layer 0
             off = tcimg::off_w0dir();
-            if (k < kDirFeatures) v = params[n * n_in + s.n_pos + k];
+            if (k < s.n_dir) v = params[n * n_in + s.n_pos + k];
         } else if (m < 2 + (H - 1)) {
             const uint32_t l = m - 2;  // hidden layer l + 1
             off = tcimg::off_wh(l);
@@ -187,13 +194,16 @@ __device__ __forceinline__ void sts_chunk8(uint32_t tile, uint32_t r, uint32_t c
 
 // Epilogue of one layer for row r: 64 accumulators from TMEM (two halves of
 // 32 columns), times `mul` (kMul: the FP8 scales s_w s_a of the layer),
-// + bias (none for layer 0, whose h_pix holds b0), ReLU, then either 16-bit
+// + bias (none for layer 0 of the frequency input, whose h_pix holds b0;
+// kHrow: layer 0 of the paper's input adds row `pr` of the pixel-major
+// 16-bit tile at `hrow`, h_pix of the row's pixel), ReLU, then either 16-bit
 // rounding into the next A tile (chunks 0-7) or, kF8Out, scaling by 1/s_a of
 // the next layer and E4M3 rounding (chunks 0-3).  kRec: the warp's amax of
 // the ReLU outputs goes into the shared word at s_amax (atomicMax on bits).
-template <uint32_t AB16, bool kF8Out, bool kMul, bool kRec>
+template <uint32_t AB16, bool kF8Out, bool kMul, bool kRec, bool kHrow = false>
 __device__ __forceinline__ void epilogue(uint32_t taddr, const float* __restrict__ bias, float mul, float inv_sa,
-                                         uint32_t tile, uint32_t r, uint32_t* s_amax) {
+                                         uint32_t tile, uint32_t r, uint32_t* s_amax, uint32_t hrow = 0,
+                                         uint32_t pr = 0) {
     float mx = 0.f;
 #pragma unroll
     for (uint32_t half = 0; half < 2; ++half) {
@@ -201,7 +211,22 @@ __device__ __forceinline__ void epilogue(uint32_t taddr, const float* __restrict
         tc::tmem_ld32(taddr + 32u * half, v);
         tc::tmem_wait_ld();
         float x[32];
-        if (bias) {
+        if constexpr (kHrow) {
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                const uint32_t c = 4u * half + q;
+                const uint4 hv = tc::lds128(hrow + (pr >> 3) * 1024u + (pr & 7u) * 128u + (((c ^ pr) & 7u) << 4));
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 hh = tc::unpack2<AB16>(hw[j]);
+                    const float2 a2 = make_float2(__uint_as_float(v[8 * q + 2 * j]), __uint_as_float(v[8 * q + 2 * j + 1]));
+                    const float2 y = kMul ? __ffma2_rn(a2, make_float2(mul, mul), hh) : __fadd2_rn(a2, hh);
+                    x[8 * q + 2 * j] = y.x;
+                    x[8 * q + 2 * j + 1] = y.y;
+                }
+            }
+        } else if (bias) {
             const float4* b4 = reinterpret_cast<const float4*>(bias + 32u * half);  // 128-bit broadcast loads
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -300,7 +325,7 @@ __device__ __forceinline__ void dir_features_fast(V3 w, float* e) {
 
 // AB: 0 FP16, 1 BF16, 2 FP8 hidden layers (FP16 elsewhere).  kAmax: record
 // the amax of every hidden layer's input activations into amax[8 + l].
-template <uint32_t AB, bool kAmax>
+template <uint32_t AB, bool kAmax, bool kSh>
 __global__ void __launch_bounds__(640, 1)
     k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
                const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
@@ -414,11 +439,15 @@ __global__ void __launch_bounds__(640, 1)
         const uint32_t npix = min(128u, a.P - p0);
         // ------------------------------------------------ pixel stage
         {
-            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+            float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
             if (t < npix) {
                 const float4* rq = reinterpret_cast<const float4*>(recs + p0 + t);
                 r0 = __ldg(rq);
                 r1 = __ldg(rq + 1);
+                if constexpr (kSh) {
+                    r2 = __ldg(rq + 2);
+                    r3 = __ldg(rq + 3);
+                }
             }
             const V3 p{r0.x, r0.y, r0.z}, n{r0.w, r1.x, r1.y};
             float f[8];
@@ -453,18 +482,41 @@ __global__ void __launch_bounds__(640, 1)
                 freq4(p.z, f);
                 sts_chunk8<AB16>(tA, t, c++, f);
             }
-            freq4(n.x, f);
-            sts_chunk8<AB16>(tA, t, c++, f);
-            freq4(n.y, f);
-            sts_chunk8<AB16>(tA, t, c++, f);
-            freq4(n.z, f);
-            sts_chunk8<AB16>(tA, t, c++, f);
+            if constexpr (kSh) {
+                float ph[16];
+                phi_features(n, make_float3(r2.y, r2.z, r2.w), r3.x, ph);
+                ph[15] = 0.f;
+                sts_chunk8<AB16>(tA, t, c++, ph);
+                sts_chunk8<AB16>(tA, t, c++, ph + 8);
+            } else {
+                freq4(n.x, f);
+                sts_chunk8<AB16>(tA, t, c++, f);
+                freq4(n.y, f);
+                sts_chunk8<AB16>(tA, t, c++, f);
+                freq4(n.z, f);
+                sts_chunk8<AB16>(tA, t, c++, f);
+            }
             for (; c < 8; ++c) sts_chunk(tA, t, c, 0u, 0u, 0u, 0u);
         }
         sync_wg();
         issue_k64(tA, w0pix, id64);
         wait_mma();
-        {
+        if constexpr (kSh) {
+            // H pixel-major: row t = h_pix of pixel t = accumulator + b0, 16-bit
+#pragma unroll
+            for (uint32_t half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                tc::tmem_ld32(tmem_row + 32u * half, v);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (uint32_t q = 0; q < 4; ++q) {
+                    float y[8];
+#pragma unroll
+                    for (uint32_t j = 0; j < 8; ++j) y[j] = __uint_as_float(v[8 * q + j]) + bias[32 * half + 8 * q + j];
+                    sts_chunk8<AB16>(tH, t, 4 * half + q, y);
+                }
+            }
+        } else {
             // H operand: element (n = output unit, k = pixel t), h = accumulator + b0
             const uint32_t hk = tH + (t >> 6) * 8192u;
 #pragma unroll
@@ -522,7 +574,15 @@ __global__ void __launch_bounds__(640, 1)
                     }
                 }
             }
-            {
+            if constexpr (kSh) {
+                // columns 0..31: the 25 spherical harmonics, zero padded (layer 0 reads K = 32)
+                float e[32];
+                sh_basis25(wi, e);
+#pragma unroll
+                for (int i = 25; i < 32; ++i) e[i] = 0.f;
+#pragma unroll
+                for (uint32_t c = 0; c < 4; ++c) sts_chunk8<AB16>(tA, t, c, e + 8 * c);
+            } else {
                 float e[16];
                 dir_features_fast(wi, e);
                 sts_chunk8<AB16>(tA, t, 0u, e);
@@ -543,10 +603,14 @@ __global__ void __launch_bounds__(640, 1)
             if (t == 0 && !*abort_flag) {
                 tc::fence_after_sync();
                 tc::mma_f16(tmem, tc::sdesc(tA), tc::sdesc(w0dir), id64, 0);
-                for (uint32_t qq = 1; qq <= n_oh; ++qq) {
-                    const uint32_t kk = kb + 16u * (qq - 1);
-                    tc::mma_f16(tmem, tc::sdesc(tA + 32u * qq), tc::sdesc(tH + (kk >> 6) * 8192u + (kk & 63u) * 2u),
-                                id64, 1);
+                if constexpr (kSh) {
+                    tc::mma_f16(tmem, tc::sdesc(tA + 32u), tc::sdesc(w0dir + 32u), id64, 1);
+                } else {
+                    for (uint32_t qq = 1; qq <= n_oh; ++qq) {
+                        const uint32_t kk = kb + 16u * (qq - 1);
+                        tc::mma_f16(tmem, tc::sdesc(tA + 32u * qq),
+                                    tc::sdesc(tH + (kk >> 6) * 8192u + (kk & 63u) * 2u), id64, 1);
+                    }
                 }
                 tc::mma_commit(mbar);
             }
@@ -555,7 +619,18 @@ __global__ void __launch_bounds__(640, 1)
                 // epilogue of layer l (l = 0: h_pix already holds b0), then the MMAs of layer l + 1
                 const float* bl = l == 0 ? nullptr : bias + 64 + (l - 1) * 64;
                 const bool next_hidden = l + 1 < a.s.hidden;
-                if constexpr (kF8) {
+                if (kSh && l == 0) {
+                    // layer 0 of the paper's input: + h_pix of the row's pixel (H row pl)
+                    if constexpr (kF8) {
+                        if (next_hidden) epilogue<0, true, false, true, true>(tmem_row, nullptr, 1.f, s_inv[0], tA, t, s_amax, tH, pl);
+                        else epilogue<0, false, false, false, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, nullptr, tH, pl);
+                    } else if constexpr (kAmax) {
+                        if (next_hidden) epilogue<AB16, false, false, true, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, s_amax, tH, pl);
+                        else epilogue<AB16, false, false, false, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, nullptr, tH, pl);
+                    } else {
+                        epilogue<AB16, false, false, false, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, nullptr, tH, pl);
+                    }
+                } else if constexpr (kF8) {
                     const float mul = l == 0 ? 1.f : s_mul[l - 1];
                     if (next_hidden) epilogue<0, true, true, true>(tmem_row, bl, mul, s_inv[l], tA, t, s_amax + l);
                     else epilogue<0, false, true, false>(tmem_row, bl, mul, 1.f, tA, t, nullptr);
@@ -734,21 +809,35 @@ cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
 bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd) {
     return (h->cfg.precision == NIRC_FP16_TC || h->cfg.precision == NIRC_BF16_TC ||
             h->cfg.precision == NIRC_FP8_E4M3_TC) &&
-           fd.cache_mode == 0 && fd.n_cache + fd.n_resid >= 4 && h->packed_tc != nullptr &&
+           fd.cache_mode == 0 && fd.n_cache + fd.n_resid >= (h->shape.sh ? 1u : 4u) && h->packed_tc != nullptr &&
            (h->shape.n_pos == 24 || h->shape.n_pos == 32);
 }
 
+template <uint32_t AB, bool kAmax, bool kSh>
+static cudaError_t launch_tc_kernel(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
+                                      const void* img, const __half2* hash, const nirc_record* recs,
+                                      const PixelBase* base, const ResidRow* rows, float* out, float* lc, float* lr,
+                                      uint64_t* sig, uint32_t* count, float* row_n, int* err, uint32_t* amax) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_cache_tc<AB, kAmax, kSh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_cache_tc<AB, kAmax, kSh><<<grid, threads, smem, st>>>(a, reinterpret_cast<const uint8_t*>(img), hash, recs, base, rows,
+                                                      reinterpret_cast<float4*>(out), lc, lr, sig, count, row_n, err,
+                                                      amax);
+    return cudaGetLastError();
+}
+
+// The instance for the network input of a.s (frequency or the paper's).
 template <uint32_t AB, bool kAmax>
 static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
                                       const void* img, const __half2* hash, const nirc_record* recs,
                                       const PixelBase* base, const ResidRow* rows, float* out, float* lc, float* lr,
                                       uint64_t* sig, uint32_t* count, float* row_n, int* err, uint32_t* amax) {
-    cudaError_t e = cudaFuncSetAttribute(k_cache_tc<AB, kAmax>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_cache_tc<AB, kAmax><<<grid, threads, smem, st>>>(a, reinterpret_cast<const uint8_t*>(img), hash, recs, base, rows,
-                                                      reinterpret_cast<float4*>(out), lc, lr, sig, count, row_n, err,
-                                                      amax);
-    return cudaGetLastError();
+    if (a.s.sh)
+        return launch_tc_kernel<AB, kAmax, true>(grid, threads, smem, st, a, img, hash, recs, base, rows, out, lc, lr,
+                                                 sig, count, row_n, err, amax);
+    return launch_tc_kernel<AB, kAmax, false>(grid, threads, smem, st, a, img, hash, recs, base, rows, out, lc, lr, sig,
+                                              count, row_n, err, amax);
 }
 
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,

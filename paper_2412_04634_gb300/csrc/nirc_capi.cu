@@ -34,8 +34,11 @@ NetShape make_shape(const nirc_config& cfg) {
     s.levels = s.hashgrid ? cfg.hash_levels : 0;
     s.log2_table = cfg.log2_table;
     s.n_pos = s.hashgrid ? cfg.hash_levels * cfg.feats_per_level : 3 * 2 * cfg.freq_octaves;
-    s.n_in = s.n_pos + kDirFeatures + kNrmFeatures;
-    s.n_pix = s.n_pos + kNrmFeatures;
+    s.sh = cfg.input_encoding == NIRC_INPUT_SH ? 1u : 0u;
+    s.n_dir = s.sh ? kShFeatures : kDirFeatures;
+    s.n_surf = s.sh ? kPhiFeatures : kNrmFeatures;
+    s.n_in = s.n_pos + s.n_dir + s.n_surf;
+    s.n_pix = s.n_pos + s.n_surf;
     s.hidden = cfg.hidden_layers;
     s.n_mlp = (uint64_t)kWidth * s.n_in + kWidth + (uint64_t)(s.hidden - 1) * (kWidth * kWidth + kWidth) +
               3ull * kWidth + 3;
@@ -44,7 +47,7 @@ NetShape make_shape(const nirc_config& cfg) {
     s.n_dev = s.hash_off + s.n_hash;
     s.off_wpix = 0;
     s.off_wdir = s.n_pix * kWidth;
-    s.off_b0 = s.off_wdir + kDirFeatures * kWidth;
+    s.off_b0 = s.off_wdir + s.n_dir * kWidth;
     s.off_hidden = s.off_b0 + kWidth;
     s.off_out = s.off_hidden + (s.hidden - 1) * (kWidth * kWidth + kWidth);
     s.packed_floats = s.off_out + 4 * kWidth + 4;
@@ -92,13 +95,20 @@ static nirc_status check_config(const nirc_config* c) {
             set_error("hash grid configuration unsupported (2 features, 1..16 levels, log2_table 4..24)");
             return NIRC_ERR_UNSUPPORTED;
         }
-        if (c->hash_levels * 2 + kNrmFeatures > kWidth) {
-            set_error("too many per-surface features");
-            return NIRC_ERR_UNSUPPORTED;
-        }
     } else if (c->pos_encoding != NIRC_POS_FREQ) {
         set_error("pos_encoding %u unknown", c->pos_encoding);
         return NIRC_ERR_INVALID;
+    }
+    if (c->input_encoding > NIRC_INPUT_SH) {
+        set_error("input_encoding %u unknown", c->input_encoding);
+        return NIRC_ERR_INVALID;
+    }
+    {
+        const uint32_t n_pos = c->pos_encoding == NIRC_POS_HASHGRID ? c->hash_levels * 2 : 24;
+        if (n_pos + (c->input_encoding == NIRC_INPUT_SH ? kPhiFeatures : kNrmFeatures) > kWidth) {
+            set_error("too many per-surface features (position + surface features must fit in 64)");
+            return NIRC_ERR_UNSUPPORTED;
+        }
     }
     if (c->precision > NIRC_FP8_E4M3_TC) {
         set_error("precision %u unknown", c->precision);
@@ -444,13 +454,13 @@ struct StateHeader {
     uint64_t n_params;
     uint64_t pad;
 };
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 
 bool same_shape(const nirc_config& a, const nirc_config& b) {
     return a.pos_encoding == b.pos_encoding && a.hash_levels == b.hash_levels &&
            a.feats_per_level == b.feats_per_level && a.log2_table == b.log2_table && a.base_res == b.base_res &&
            a.growth == b.growth && a.freq_octaves == b.freq_octaves && a.width == b.width &&
-           a.hidden_layers == b.hidden_layers;
+           a.hidden_layers == b.hidden_layers && a.input_encoding == b.input_encoding;
 }
 }  // namespace
 

@@ -521,6 +521,82 @@ __device__ __forceinline__ void dir_angles(V3 w, float& th, float& ph) {
     ph = p;
 }
 
+// Real spherical harmonics Y_l^m, l = 0..4, of the unit vector w, at index
+// l*l + l + m (the paper's direction input, 25 values).  With D_lm the m-th
+// derivative of the Legendre polynomial P_l and c_m + i s_m = (x + i y)^m
+// (= sin^m t e^{i m p} on the unit sphere):
+//   Y_l^0 = A_l0 D_l0(z),  Y_l^m = A_lm D_lm(z) c_m,  Y_l^-m = A_lm D_lm(z) s_m,
+// A_l0 = K_l^0, A_lm = sqrt(2) K_l^m, K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!)
+// (orthonormal, no Condon-Shortley phase).
+__device__ __forceinline__ void sh_basis25(V3 w, float* e) {
+    constexpr float A00 = 0.28209479177387814f, A10 = 0.4886025119029199f, A11 = 0.48860251190292f;
+    constexpr float A20 = 0.6307831305050401f, A21 = 0.36418281019735976f, A22 = 0.18209140509867988f;
+    constexpr float A30 = 0.7463526651802308f, A31 = 0.3046971996429772f, A32 = 0.09635371475468515f,
+                    A33 = 0.03933623932844291f;
+    constexpr float A40 = 0.8462843753216345f, A41 = 0.2676186174229157f, A42 = 0.063078313050504f,
+                    A43 = 0.016858388283618388f, A44 = 0.005960340337611203f;
+    const float x = w.x, y = w.y, z = w.z, z2 = z * z;
+    const float c2 = x * x - y * y, s2 = 2.f * x * y;
+    const float c3 = x * c2 - y * s2, s3 = x * s2 + y * c2;
+    const float c4 = x * c3 - y * s3, s4 = x * s3 + y * c3;
+    // A_lm D_lm(z): P_2 = (3z^2 - 1)/2, P_3 = (5z^3 - 3z)/2, P_4 = (35z^4 - 30z^2 + 3)/8 and derivatives
+    const float b20 = A20 * (1.5f * z2 - 0.5f), b21 = A21 * 3.f * z, b22 = A22 * 3.f;
+    const float b30 = A30 * z * (2.5f * z2 - 1.5f), b31 = A31 * (7.5f * z2 - 1.5f), b32 = A32 * 15.f * z,
+                b33 = A33 * 15.f;
+    const float b40 = A40 * ((4.375f * z2 - 3.75f) * z2 + 0.375f), b41 = A41 * z * (17.5f * z2 - 7.5f),
+                b42 = A42 * (52.5f * z2 - 7.5f), b43 = A43 * 105.f * z, b44 = A44 * 105.f;
+    e[0] = A00;
+    e[1] = A11 * y;
+    e[2] = A10 * z;
+    e[3] = A11 * x;
+    e[4] = b22 * s2;
+    e[5] = b21 * y;
+    e[6] = b20;
+    e[7] = b21 * x;
+    e[8] = b22 * c2;
+    e[9] = b33 * s3;
+    e[10] = b32 * s2;
+    e[11] = b31 * y;
+    e[12] = b30;
+    e[13] = b31 * x;
+    e[14] = b32 * c2;
+    e[15] = b33 * c3;
+    e[16] = b44 * s4;
+    e[17] = b43 * s3;
+    e[18] = b42 * s2;
+    e[19] = b41 * y;
+    e[20] = b40;
+    e[21] = b41 * x;
+    e[22] = b42 * c2;
+    e[23] = b43 * c3;
+    e[24] = b44 * c4;
+}
+
+// One-blob encoding of s into 4 bins (Mueller et al. 2019): the mass of a
+// Gaussian of standard deviation 1/4 centred at s over [i/4, (i+1)/4),
+// e_i = (erf((i+1)/4 - s) 4/sqrt 2) - erf((i/4 - s) 4/sqrt 2)) / 2, no wrap-around.
+__device__ __forceinline__ void one_blob4(float s, float* e) {
+    constexpr float k = 2.8284271247461903f;  // 4 / sqrt(2)
+    float g[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = erff((0.25f * (float)i - s) * k);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) e[i] = 0.5f * (g[i + 1] - g[i]);
+}
+
+// The paper's per-surface inputs phi (15): albedo, one-blob of the normal's
+// (theta/pi, phi/2pi), one-blob of the roughness.
+__device__ __forceinline__ void phi_features(V3 n, float3 alb, float rough, float* e) {
+    e[0] = alb.x;
+    e[1] = alb.y;
+    e[2] = alb.z;
+    float th, ph;
+    dir_angles(n, th, ph);
+    one_blob4(th, e + 3);
+    one_blob4(ph, e + 7);
+    one_blob4(rough, e + 11);
+}
+
 // Hash-grid level description (precomputed on the host).
 struct GridLevel {
     uint32_t res;    // floor(base * growth^l)

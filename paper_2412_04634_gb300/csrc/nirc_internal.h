@@ -18,6 +18,8 @@ constexpr uint32_t kMaxHidden = 8;
 constexpr uint32_t kMaxLevels = 16;
 constexpr uint32_t kDirFeatures = 16;  // (theta, phi) x 4 octaves x (sin, cos)
 constexpr uint32_t kNrmFeatures = 24;  // normal (3) x 4 octaves x (sin, cos)
+constexpr uint32_t kShFeatures = 25;   // real spherical harmonics, degree <= 4
+constexpr uint32_t kPhiFeatures = 15;  // albedo (3), one-blob normal angles (8), one-blob roughness (4)
 
 // Per-pixel data the path-tracing kernel hands to the cache kernel.
 struct __align__(16) PixelBase {
@@ -34,8 +36,11 @@ struct __align__(16) ResidRow {
 // Network shape derived from a config.
 struct NetShape {
     uint32_t n_pos;     // position features
-    uint32_t n_in;      // network inputs = n_pos + 16 + 24
-    uint32_t n_pix;     // per-pixel features = n_pos + 24
+    uint32_t n_dir;     // direction features: 16 (frequency) or 25 (spherical harmonics)
+    uint32_t n_surf;    // per-surface features after the position: 24 (normal frequency) or 15 (phi)
+    uint32_t sh;        // 1 = the paper's input (spherical harmonics + phi)
+    uint32_t n_in;      // network inputs = n_pos + n_dir + n_surf, in the order [pos][dir][surf]
+    uint32_t n_pix;     // per-pixel features = n_pos + n_surf
     uint32_t hidden;    // hidden layers (>= 1)
     uint64_t n_mlp;     // MLP parameters in the master vector
     uint64_t n_hash;    // hash-table parameters

@@ -36,9 +36,10 @@ __device__ __forceinline__ void store_relu(const float2 (&acc)[32], float* act, 
     }
 }
 
-// Per-surface features [position (n_pos)][normal (24)] into act[k * stride].
+// Per-surface features [position (n_pos)][normal frequency (24) or phi (15)]
+// into act[k * stride].
 __device__ __forceinline__ void encode_surface(const NetShape& s, const GridParams& g, const float* __restrict__ table,
-                                               V3 p, V3 n, float* act, int stride) {
+                                               V3 p, V3 n, float3 alb, float rough, float* act, int stride) {
     float e[8];
     uint32_t k = 0;
     if (s.hashgrid) {
@@ -66,12 +67,37 @@ __device__ __forceinline__ void encode_surface(const NetShape& s, const GridPara
             for (int q = 0; q < 8; ++q) act[(k++) * stride] = e[q];
         }
     }
+    if (s.sh) {
+        float f[kPhiFeatures];
+        phi_features(n, alb, rough, f);
+#pragma unroll
+        for (int q = 0; q < (int)kPhiFeatures; ++q) act[(k++) * stride] = f[q];
+        return;
+    }
     const float nv[3] = {n.x, n.y, n.z};
     for (int d = 0; d < 3; ++d) {
         freq4_accurate(nv[d], e);
 #pragma unroll
         for (int q = 0; q < 8; ++q) act[(k++) * stride] = e[q];
     }
+}
+
+// Direction features of a row: frequency features of (theta/pi, phi/2pi)
+// (16) or the spherical harmonics (25).
+template <bool kSh>
+__device__ __forceinline__ void dir_encode(V3 wi, float* e) {
+    if constexpr (kSh) {
+        sh_basis25(wi, e);
+    } else {
+        float th, ph;
+        dir_angles(wi, th, ph);
+        freq4_accurate(th, e);
+        freq4_accurate(ph, e + 8);
+    }
+}
+template <bool kSh>
+constexpr int dir_features() {
+    return kSh ? (int)kShFeatures : (int)kDirFeatures;
 }
 
 __device__ __forceinline__ void stage_weights(float* sw, const float* __restrict__ packed, uint32_t n_floats) {

@@ -212,6 +212,20 @@ __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, ui
 __device__ __forceinline__ void sts16(uint32_t addr, uint16_t v) {
     asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr), "h"(v) : "memory");
 }
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+// Two packed 16-bit values (low half first) to FP32: bf16 by a shift, f16 by cvt.
+template <uint32_t kBf16>
+__device__ __forceinline__ float2 unpack2(uint32_t u) {
+    if constexpr (kBf16) return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+    return __half22float2(*reinterpret_cast<const __half2*>(&u));
+}
 
 }  // namespace tc
 }  // namespace nirc

@@ -187,6 +187,7 @@ __device__ __forceinline__ float fixed_scale(float m, uint64_t n) {
     return ldexpf(1.f, min(61 - e, 100));
 }
 
+template <bool kSh>
 __global__ void __launch_bounds__(kTrainThreads, 2)
     k_train_fwd(NetShape s, GridParams g, float z_clamp, float loss_eps, float scale, const float* __restrict__ packed,
                 const float* __restrict__ table, const nirc_record* __restrict__ recs, const float* __restrict__ dirs,
@@ -205,31 +206,30 @@ __global__ void __launch_bounds__(kTrainThreads, 2)
         const bool in_range = first + threadIdx.x < n;
         const uint64_t t = in_range ? first + threadIdx.x : 0;
         const float4* rq = reinterpret_cast<const float4*>(recs + t);
-        const float4 r0 = __ldg(rq), r1 = __ldg(rq + 1), r3 = __ldg(rq + 3);
+        const float4 r0 = __ldg(rq), r1 = __ldg(rq + 1), r2 = __ldg(rq + 2), r3 = __ldg(rq + 3);
         const bool valid = in_range && (kind == kLossUpstream || (__float_as_uint(r3.z) & 1u));
         const bool keep = in_range && store;
         const V3 p{r0.x, r0.y, r0.z}, nn{r0.w, r1.x, r1.y};
         const V3 wi{__ldg(dirs + 3 * t), __ldg(dirs + 3 * t + 1), __ldg(dirs + 3 * t + 2)};
-        encode_surface(s, g, table, p, nn, act, stride);  // [pos][nrm]
-        float th, ph, edir[16];
-        dir_angles(wi, th, ph);
-        freq4_accurate(th, edir);
-        freq4_accurate(ph, edir + 8);
-        // network input in parameter order [pos][dir][nrm]
+        encode_surface(s, g, table, p, nn, make_float3(r2.y, r2.z, r2.w), r3.x, act, stride);  // [pos][surf]
+        constexpr int nd = dir_features<kSh>();
+        float edir[nd];
+        dir_encode<kSh>(wi, edir);
+        // network input in parameter order [pos][dir][surf]
         if (keep) {
             const uint64_t ld = tp.ld;
             for (uint32_t k = 0; k < s.n_pos; ++k) tp.e[(uint64_t)k * ld + t] = act[k * stride];
 #pragma unroll
-            for (uint32_t k = 0; k < 16; ++k) tp.e[(uint64_t)(s.n_pos + k) * ld + t] = edir[k];
-            for (uint32_t k = 0; k < kNrmFeatures; ++k)
-                tp.e[(uint64_t)(s.n_pos + 16 + k) * ld + t] = act[(s.n_pos + k) * stride];
+            for (uint32_t k = 0; k < (uint32_t)nd; ++k) tp.e[(uint64_t)(s.n_pos + k) * ld + t] = edir[k];
+            for (uint32_t k = 0; k < s.n_surf; ++k)
+                tp.e[(uint64_t)(s.n_pos + nd + k) * ld + t] = act[(s.n_pos + k) * stride];
         }
 
         float2 acc[32];
         load_bias(acc, sw + s.off_b0);
         for (uint32_t i = 0; i < s.n_pix; ++i) fma_row(acc, sw + s.off_wpix + i * kWidth, act[i * stride]);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) fma_row(acc, sw + s.off_wdir + i * kWidth, edir[i]);
+        for (int i = 0; i < nd; ++i) fma_row(acc, sw + s.off_wdir + i * kWidth, edir[i]);
         for (uint32_t l = 0; l < s.hidden; ++l) {
             float* ag = tp.act + ((uint64_t)l * kWidth) * tp.ld + t;
 #pragma unroll
@@ -591,7 +591,8 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     }
     const size_t smem_f = (size_t)s.packed_floats * 4 + (size_t)kTrainThreads * kWidth * 4;
     const size_t smem_b = (size_t)s.packed_floats * 4;
-    if ((e = cudaFuncSetAttribute(k_train_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f)) != cudaSuccess)
+    auto fwd = s.sh ? k_train_fwd<true> : k_train_fwd<false>;
+    if ((e = cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(k_train_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b)) != cudaSuccess)
         return e;
@@ -604,10 +605,9 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     // full-batch forward: loss and dL/dz, activations only when stored
     timer_begin(h, NIRC_K_TRAIN_FWD, st);
     const uint32_t fwd_blocks = blocks_for(n);
-    k_train_fwd<<<fwd_blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
-                                                          h->packed, table, recs, dirs, targets, n, tp,
-                                                          store ? 1 : 0, kind, h->loss_accum,
-                                                          det ? dp.loss_part : nullptr);
+    fwd<<<fwd_blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale, h->packed,
+                                                  table, recs, dirs, targets, n, tp, store ? 1 : 0, kind,
+                                                  h->loss_accum, det ? dp.loss_part : nullptr);
     timer_end(h, NIRC_K_TRAIN_FWD, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (det) {
@@ -620,10 +620,9 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         tc.dz = tp.dz + c0;
         if (!store) {
             timer_begin(h, NIRC_K_TRAIN_FWD, st);
-            k_train_fwd<<<blocks_for(m), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps,
-                                                                     scale, h->packed, table, recs + c0,
-                                                                     dirs + 3 * c0, targets + 3 * c0, m, tc, 1,
-                                                                     kLossNone, nullptr, nullptr);
+            fwd<<<blocks_for(m), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
+                                                             h->packed, table, recs + c0, dirs + 3 * c0,
+                                                             targets + 3 * c0, m, tc, 1, kLossNone, nullptr, nullptr);
             timer_end(h, NIRC_K_TRAIN_FWD, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }

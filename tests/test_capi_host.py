@@ -39,9 +39,10 @@ def test_exports_every_declared_symbol(N):
     assert not missing, missing
 
 
-@pytest.mark.parametrize("cfg", [scenes.config_small(), scenes.config_1080p(),
+@pytest.mark.parametrize("cfg", [scenes.config_small(), scenes.config_1080p(), scenes.config_paper_1080p(),
                                  scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=8, log2_table=12,
-                                                  hidden_layers=2)])
+                                                  hidden_layers=2),
+                                 scenes.NetConfig(input_encoding=scenes.INPUT_SH, hidden_layers=2)])
 def test_param_count_matches_layout(N, cfg):
     assert N.nirc_param_count(N.make_config(cfg)) == cfg.n_params
 
@@ -55,6 +56,12 @@ def test_bad_arguments_return_status(N):
     assert N.lib().nirc_create(ctypes.byref(bad), ctypes.byref(h)) == N.NIRC_ERR_UNSUPPORTED
     bad = N.make_config(scenes.NetConfig(pos_encoding=7))
     assert N.lib().nirc_create(ctypes.byref(bad), ctypes.byref(h)) == N.NIRC_ERR_INVALID
+    bad = N.make_config(scenes.NetConfig(input_encoding=2))
+    assert N.lib().nirc_create(ctypes.byref(bad), ctypes.byref(h)) == N.NIRC_ERR_INVALID
+    assert b"input_encoding" in N.lib().nirc_last_error()
+    # more than 16 hash levels
+    bad = N.make_config(scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=24, input_encoding=1))
+    assert N.lib().nirc_create(ctypes.byref(bad), ctypes.byref(h)) == N.NIRC_ERR_UNSUPPORTED
     assert N.lib().nirc_create(None, ctypes.byref(h)) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_query(None, None, None, 5, None, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_train_step(None, None, None, None, 5, None, None) == N.NIRC_ERR_INVALID
@@ -87,5 +94,6 @@ def test_struct_layouts(N):
     assert ctypes.sizeof(N.nirc_completion) == 48
     assert ctypes.sizeof(N.nirc_server_config) == 24
     assert ctypes.sizeof(N.nirc_frame_desc) == 56
+    assert ctypes.sizeof(N.nirc_config) == 68
     assert scenes.RECORD_DTYPE.itemsize == 64
     assert scenes.PRIM_DTYPE.itemsize == 96 and scenes.HEADER_DTYPE.itemsize == 96
