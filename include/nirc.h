@@ -224,7 +224,8 @@ nirc_status nirc_load_state(nirc_handle* h, const void* host_buf, uint64_t bytes
 
 /* Select the layer arithmetic for later calls (nirc_precision).  The
  * tensor-core modes apply to the cache integral of nirc_estimate_frame when
- * the network is used (cache_mode 0) and N + M >= 4; other work (queries,
+ * the network is used (cache_mode 0) and N + M >= 4 (N + M >= 1 with
+ * NIRC_INPUT_SH); other work (queries,
  * training, the other cache modes) runs the FP32 kernels.  Synchronises the
  * legacy default stream. */
 nirc_status nirc_set_precision(nirc_handle* h, uint32_t precision);
