@@ -112,6 +112,8 @@ typedef struct {
     uint64_t seed;
     uint32_t cache_mode; /* 0 network, 1 zero, 2 constant */
     uint32_t light_mode; /* 0 cache = full L_i, 1 cache = L_ind with NEE + MIS (eq. Lsplit) */
+    uint32_t estimator;  /* 0 two-level (eq. L_mlmc), 1 biased with the Balanced Termination Heuristic */
+    uint32_t pad2;
     double cache_const[3];
 } o_frame;
 
@@ -128,7 +130,9 @@ enum {
     PURPOSE_BOUNCE = 4, /* + 16 * segment */
     PURPOSE_RR = 5,     /* + 16 * segment */
     PURPOSE_TRAIN_PICK = 6,
-    PURPOSE_LIGHT = 7   /* + 16 * segment (0: the shading point) */
+    PURPOSE_LIGHT = 7,  /* + 16 * segment (0: the shading point) */
+    PURPOSE_BTH_DIR = 8, /* + 16 * vertex: the scattering direction sampled at a biased path's vertex */
+    PURPOSE_BTH_XI = 9   /* + 16 * vertex: the termination test's uniform */
 };
 
 static const float T_MIN = 1e-4f;
@@ -1175,6 +1179,226 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
     if (count) *count = active;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Path termination (paper: section "Path Termination Heuristics")          */
+/* ------------------------------------------------------------------------ */
+
+/* Density of the BSDF sampler at wi (the p of the termination tests) in
+ * strict binary32, fixed operation order: it decides whether a path goes on,
+ * so both implementations compute it identically.  Lambertian: cos/pi;
+ * Lambertian + GGX: the one-sample mixture 1/2 cos/pi + 1/2 G1(wo) D / (4
+ * cos_o), D = a2 / (pi dd^2), dd = |n x h|^2 + a2 (n.h)^2, a = roughness^2. */
+static float sampler_pdf32(const o_record* rec, const float wi[3])
+{
+    const float inv_pi = (float)(1.0 / O_PI);
+    uint32_t mat = (rec->flags >> 1) & 3u;
+    float ci = dot3f(rec->n, wi);
+    if (mat == MAT_BLACK || !(ci > 0.0f)) return 0.0f;
+    if (mat == MAT_LAMBERT) return ci * inv_pi;
+    const float* n = rec->n;
+    float co = dot3f(n, rec->wo);
+    float h[3] = {rec->wo[0] + wi[0], rec->wo[1] + wi[1], rec->wo[2] + wi[2]};
+    normalize3f(h);
+    float a = rec->roughness * rec->roughness;
+    float a2 = a * a;
+    float cnh = dot3f(n, h);
+    float cx[3] = {n[1] * h[2] - n[2] * h[1], n[2] * h[0] - n[0] * h[2], n[0] * h[1] - n[1] * h[0]};
+    float dd = dot3f(cx, cx) + a2 * (cnh * cnh);
+    float D = a2 / (((float)O_PI * dd) * dd);
+    float lam_o = sqrtf(a2 + (1.0f - a2) * (co * co));
+    float g1 = (2.0f * co) / (co + lam_o);
+    return 0.5f * (ci * inv_pi) + 0.5f * ((g1 * D) / (4.0f * co));
+}
+
+/* Balanced Termination Heuristic: continuation probability
+ * P_s = p / (p + N_c / pi) of a path whose sampled direction has density p,
+ * N_c neural samples (binary32). */
+static float bth_continue_prob(float p, uint32_t n_c)
+{
+    return p / (p + (float)n_c * (float)(1.0 / O_PI));
+}
+
+/* Spread-angle footprint term of one segment of length t arriving at a
+ * vertex at cosine cos_in, sampled with density p at the previous vertex
+ * (NRC's heuristic, which the paper uses for vertices after the first):
+ *   a(x_1 .. x_n) = (sum_{i=2..n} sqrt(|x_{i-1} - x_i|^2 / (p cos_i)))^2,
+ *   a_0 = |x_0 - x_1|^2 / (4 pi cos_1),  stop when a > c a_0, c = 0.01. */
+static float spread_term(float t, float p, float cos_in)
+{
+    return sqrtf((t * t) / (p * cos_in));
+}
+
+/* The camera path of the biased estimator (paper: "Biased and unbiased
+ * variants" and the termination criteria of section "Path Termination
+ * Heuristics"): from vertex x_i the path continues with the BSDF-sampled
+ * direction w_i while xi_i <= P_s(w_i) and, for i > 1, the footprint
+ * a(x_1..x_i) stays within c a_0; it stops there otherwise, or at vertex
+ * max_depth.  Emission found along the path is added to le with the path
+ * throughput; in light mode 1 every vertex takes a light sample (NEE) and
+ * w_i is the BSDF technique of the power heuristic (one sample), traced at
+ * the stopping vertex too, for its emission only.  No Russian roulette: the
+ * termination tests and the depth cap end the path.  Returns the index of
+ * the stopping vertex (its record in term, the throughput up to it in beta)
+ * or 0 when the path left the scene first. */
+static uint32_t bth_path(const uint8_t* blob, const o_frame* fd, const o_lights* lights, uint32_t pix,
+                         o_record* term, double beta[3], double Le[3], uint64_t* sig)
+{
+    const o_header* hd = (const o_header*)blob;
+    const o_prim* prims = scene_prims(blob);
+    uint32_t k0 = (uint32_t)fd->seed, k1 = fd->frame;
+    uint32_t px = pix % fd->width, py = pix / fd->width;
+    uint64_t sp = SIG_INIT;
+    uint32_t stop_at = 0;
+    for (int k = 0; k < 3; k++) {
+        Le[k] = 0.0;
+        beta[k] = 1.0;
+    }
+    memset(term, 0, sizeof(*term));
+
+    uint32_t r[4];
+    philox(k0, k1, pix, 0u, 0u, PURPOSE_CAMERA, r);
+    float o[3], d[3];
+    camera_ray(hd, fd->width, fd->height, px, py, u01(r[0]), u01(r[1]), o, d);
+    float t;
+    int prim = trace_nearest(prims, hd->n_prims, o, d, &t);
+    sp = sig_mix(sp, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+    if (prim >= 0) {
+        o_hit h;
+        hit_info(&prims[prim], o, d, t, &h);
+        emitted(&prims[prim], h.front, Le);
+        const float c_a0 = 0.01f * ((t * t) / ((4.0f * (float)O_PI) * fabsf(dot3f(h.n, d))));
+        float spread = 0.0f;
+        for (uint32_t i = 1;; i++) {
+            o_record rec;
+            make_record(&prims[prim], (uint32_t)prim, &h, d, &rec);
+            if (lights) {
+                double dl[3] = {0.0, 0.0, 0.0};
+                sp = sig_mix(sp, nee_sample(blob, lights, &rec, 1u, k0, k1, pix, 0u, PURPOSE_LIGHT + 16u * i, dl));
+                for (int k = 0; k < 3; k++) Le[k] += beta[k] * dl[k];
+            }
+            o_sample s;
+            sample_bsdf(&rec, k0, k1, pix, 0u, PURPOSE_BTH_DIR + 16u * i, &s);
+            sp = sig_mix(sp, sample_word(&s));
+            float p = s.valid ? sampler_pdf32(&rec, s.wi) : 0.0f;
+            philox(k0, k1, pix, 0u, 0u, PURPOSE_BTH_XI + 16u * i, r);
+            uint32_t stop = (uint32_t)(u01(r[0]) > bth_continue_prob(p, fd->n_cache));
+            if (i > 1 && spread * spread > c_a0) stop |= 2u;
+            if (i == fd->max_depth) stop |= 4u;
+            sp = sig_mix(sp, stop);
+            if (stop) {
+                *term = rec;
+                stop_at = i;
+                if (lights && s.valid) {
+                    /* the BSDF technique of the direct light at the stopping vertex */
+                    int q = trace_nearest(prims, hd->n_prims, rec.p, s.wi, &t);
+                    sp = sig_mix(sp, q < 0 ? 0xFFFFFFFFu : (uint32_t)q);
+                    if (q >= 0) {
+                        o_hit hq;
+                        hit_info(&prims[q], rec.p, s.wi, t, &hq);
+                        double le[3];
+                        emitted(&prims[q], hq.front, le);
+                        double wb = 1.0;
+                        if (is_rect_emitter(&prims[q]) && lights->n) {
+                            double fc[3], pb;
+                            bsdf_eval(&rec, s.wi, fc, &pb);
+                            wb = power_weight(pb, light_pdf(&prims[q], s.wi, (double)t, lights->n));
+                        }
+                        for (int k = 0; k < 3; k++) Le[k] += beta[k] * s.w[k] * le[k] * wb;
+                    }
+                }
+                break;
+            }
+            /* continue along w_i */
+            double pb = 0.0;
+            if (lights) {
+                double fc[3];
+                bsdf_eval(&rec, s.wi, fc, &pb);
+            }
+            for (int k = 0; k < 3; k++) beta[k] *= s.w[k];
+            for (int k = 0; k < 3; k++) {
+                o[k] = rec.p[k];
+                d[k] = s.wi[k];
+            }
+            prim = trace_nearest(prims, hd->n_prims, o, d, &t);
+            sp = sig_mix(sp, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+            if (prim < 0) break;
+            hit_info(&prims[prim], o, d, t, &h);
+            double le[3];
+            emitted(&prims[prim], h.front, le);
+            double wb = 1.0;
+            if (lights && is_rect_emitter(&prims[prim]) && lights->n)
+                wb = power_weight(pb, light_pdf(&prims[prim], d, (double)t, lights->n));
+            for (int k = 0; k < 3; k++) Le[k] += beta[k] * le[k] * wb;
+            spread = spread + spread_term(t, p, fabsf(dot3f(h.n, d)));
+        }
+    }
+    *sig = sp;
+    return stop_at;
+}
+
+/* The biased estimator per pixel: the camera path above, then N_c cache
+ * samples at its stopping vertex (eq. L_c) times the path throughput; no
+ * residual level. */
+static void estimate_pixel_bth(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
+                               const o_lights* lights, uint32_t pix, double out[3], double lc_out[3],
+                               double lr_out[3], uint64_t sig[2], uint32_t* count, double* row_n)
+{
+    if (row_n) memset(row_n, 0, 3 * sizeof(double) * fd->n_cache);
+    uint32_t k0 = (uint32_t)fd->seed, k1 = fd->frame;
+    uint64_t sp, sc = SIG_INIT;
+    uint32_t active = 0;
+    double Le[3], beta[3], Lc[3] = {0, 0, 0};
+    o_record term;
+    uint32_t at = bth_path(blob, fd, lights, pix, &term, beta, Le, &sp);
+    if (at) {
+        for (uint32_t i = 0; i < fd->n_cache; i++) {
+            o_sample s;
+            sample_bsdf(&term, k0, k1, pix, i, PURPOSE_CACHE_DIR, &s);
+            sc = sig_mix(sc, sample_word(&s));
+            if (!s.valid) continue;
+            double nv[3];
+            cache_value(c, params, fd, &term, s.wi, nv);
+            for (int k = 0; k < 3; k++) Lc[k] += s.w[k] * nv[k];
+            if (row_n)
+                for (int k = 0; k < 3; k++) row_n[3 * i + k] = nv[k];
+            active++;
+        }
+        if (fd->n_cache)
+            for (int k = 0; k < 3; k++) Lc[k] *= beta[k] / (double)fd->n_cache;
+    }
+    for (int k = 0; k < 3; k++) {
+        out[k] = Le[k] + Lc[k];
+        if (lc_out) lc_out[k] = Lc[k];
+        if (lr_out) lr_out[k] = 0.0;
+    }
+    if (sig) {
+        sig[0] = sp;
+        sig[1] = sc;
+    }
+    if (count) *count = active;
+}
+
+/* The camera path of the biased estimator for one pixel (test access):
+ * returns the stopping vertex (0: none) with its record, the throughput up
+ * to it and the radiance collected on the way. */
+uint32_t orc_bth_path(const uint8_t* blob, const o_frame* fd, uint32_t pix, o_record* term, double beta[3],
+                      double le[3], uint64_t* sig)
+{
+    o_lights* lights = NULL;
+    if (fd->light_mode == 1) {
+        lights = (o_lights*)malloc(sizeof(o_lights));
+        collect_lights(blob, lights);
+    }
+    uint32_t at = bth_path(blob, fd, lights, pix, term, beta, le, sig);
+    free(lights);
+    return at;
+}
+
+float orc_sampler_pdf32(const o_record* rec, const float wi[3])
+{
+    return sampler_pdf32(rec, wi);
+}
+
 /* Estimate the listed pixels (all W*H when pixels == NULL).  Outputs are
  * indexed by position in the list; optional outputs may be NULL. */
 void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
@@ -1190,9 +1414,14 @@ void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* bl
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t i = 0; i < (int64_t)n; i++) {
         uint32_t pix = pixels ? pixels[i] : (uint32_t)i;
-        estimate_pixel(c, params, blob, fd, lights, pix, out + 3 * i, lc ? lc + 3 * i : NULL,
-                       lr ? lr + 3 * i : NULL, sig ? sig + 2 * i : NULL, count ? count + i : NULL,
-                       row_n ? row_n + 3 * S * i : NULL);
+        if (fd->estimator == 1)
+            estimate_pixel_bth(c, params, blob, fd, lights, pix, out + 3 * i, lc ? lc + 3 * i : NULL,
+                               lr ? lr + 3 * i : NULL, sig ? sig + 2 * i : NULL, count ? count + i : NULL,
+                               row_n ? row_n + 3 * S * i : NULL);
+        else
+            estimate_pixel(c, params, blob, fd, lights, pix, out + 3 * i, lc ? lc + 3 * i : NULL,
+                           lr ? lr + 3 * i : NULL, sig ? sig + 2 * i : NULL, count ? count + i : NULL,
+                           row_n ? row_n + 3 * S * i : NULL);
     }
     free(lights);
 }

@@ -35,7 +35,8 @@ class OFrame(ctypes.Structure):
         ("n_cache", ctypes.c_uint32), ("n_resid", ctypes.c_uint32),
         ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("cache_mode", ctypes.c_uint32),
-        ("light_mode", ctypes.c_uint32), ("cache_const", ctypes.c_double * 3),
+        ("light_mode", ctypes.c_uint32), ("estimator", ctypes.c_uint32), ("pad2", ctypes.c_uint32),
+        ("cache_const", ctypes.c_double * 3),
     ]
 
 
@@ -62,6 +63,10 @@ def lib():
         L.orc_nee_sample.argtypes = [P, P, u32, u32, u32, u32, u32, u32, P]
         L.orc_nee_sample.restype = u32
         L.orc_bsdf_eval.argtypes = [P, P, P, P]
+        L.orc_bth_path.argtypes = [P, P, u32, P, P, P, P]
+        L.orc_bth_path.restype = u32
+        L.orc_sampler_pdf32.argtypes = [P, P]
+        L.orc_sampler_pdf32.restype = ctypes.c_float
         L.orc_train_loss_grad.argtypes = [P, P, P, P, P, u64, P, P]
         L.orc_train_loss_grad.restype = f64
         L.orc_query_grad.argtypes = [P, P, P, P, P, u64, P]
@@ -91,8 +96,8 @@ def ocfg(cfg) -> OCfg:
 
 
 def oframe(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode=0,
-           cache_const=(0.0, 0.0, 0.0), light_mode=0) -> OFrame:
-    f = OFrame(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode, light_mode)
+           cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0) -> OFrame:
+    f = OFrame(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode, light_mode, estimator)
     for k in range(3):
         f.cache_const[k] = float(cache_const[k])
     return f
@@ -203,6 +208,24 @@ def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None, rows=False):
     if rows:
         res["row_n"] = row_n
     return res
+
+
+def bth_path(scene_blob, frame: OFrame, pix: int, record_dtype):
+    """The biased estimator's camera path of one pixel: (stopping vertex or
+    0, its record, throughput, collected radiance, path signature)."""
+    blob = np.ascontiguousarray(scene_blob, np.uint8)
+    rec = np.zeros(1, record_dtype)
+    beta = np.zeros(3, np.float64)
+    le = np.zeros(3, np.float64)
+    sig = np.zeros(1, np.uint64)
+    at = lib().orc_bth_path(_ptr(blob), ctypes.byref(frame), int(pix), _ptr(rec), _ptr(beta), _ptr(le), _ptr(sig))
+    return int(at), rec, beta, le, int(sig[0])
+
+
+def sampler_pdf32(rec, wi) -> float:
+    r = np.ascontiguousarray(rec)
+    w = np.ascontiguousarray(wi, np.float32)
+    return float(lib().orc_sampler_pdf32(_ptr(r), _ptr(w)))
 
 
 def gen_train(scene_blob, width, height, T, frame, seed, max_depth, record_dtype, light_mode=0):

@@ -910,3 +910,139 @@ def test_nee_training_targets_exclude_first_emission(oracle):
     nz0 = (tg0.max(1) > 0).mean()
     nz1 = (tg1.max(1) > 0).mean()
     assert nz1 > 10 * nz0 and nz1 > 0.3, (nz0, nz1)
+
+
+# ---------------------------------------------------------------------------
+# Biased estimator with the Balanced Termination Heuristic
+# ---------------------------------------------------------------------------
+
+def _cube_furnace(rho, Le, W=32, H=32):
+    """Camera at the centre of the unit cube; six Lambertian walls of albedo
+    rho emitting Le on both sides."""
+    prims = np.zeros(6, scenes.PRIM_DTYPE)
+    faces = [((0, 0, 0), (1, 0, 0), (0, 1, 0)), ((0, 0, 1), (1, 0, 0), (0, 1, 0)),
+             ((0, 0, 0), (0, 1, 0), (0, 0, 1)), ((1, 0, 0), (0, 1, 0), (0, 0, 1)),
+             ((0, 0, 0), (0, 0, 1), (1, 0, 0)), ((0, 1, 0), (0, 0, 1), (1, 0, 0))]
+    for k, (a, u, v) in enumerate(faces):
+        scenes._fill_rect(prims[k], a, u, v, (rho,) * 3, 1.0, scenes.MAT_LAMBERT, emission=(Le,) * 3,
+                          flags_extra=scenes.EMIT_TWO_SIDED)
+    cam = scenes._camera((0.5, 0.5, 0.5), 60.0, W, H)
+    return scenes.Scene(scenes._header(6, cam), prims, W, H)
+
+
+@pytest.mark.parametrize("light_mode", [0, 1])
+@pytest.mark.parametrize("n_c", [1, 4, 16])
+def test_bth_furnace_exact(oracle, light_mode, n_c):
+    """Inside an emitting Lambertian sphere (L_e, rho) the incident radiance
+    is L_e / (1 - rho) everywhere (L_ind = rho L_e / (1 - rho)).  With that
+    cache the biased estimator is exact at whatever vertex each path stops:
+    L_e sum_{k<t} rho^k + rho^t n = L_e / (1 - rho) (light mode 1: the
+    stopping vertex's BSDF ray adds rho^t L_e and the cache holds L_ind)."""
+    rho = float(np.float32(0.6))
+    Le = 1.0
+    sc = scenes.furnace_scene(48, 48, rho=rho, emission=Le)
+    L = Le / (1 - rho)
+    n = L if light_mode == 0 else rho * L
+    cfg = scenes.config_small()
+    fd = oracle.oframe(48, 48, n_c, 0, 6, 2, 7, cache_mode=2, cache_const=(n, n, n), light_mode=light_mode,
+                       estimator=1)
+    r = oracle.estimate(cfg, None, sc.blob(), fd)
+    assert np.all(r["count"] == n_c)
+    assert np.allclose(r["pixel"], L, rtol=1e-12, atol=0), np.abs(r["pixel"] - L).max()
+    # and the paths do stop at different vertices (at the first by the BTH
+    # test, at the second at the latest: seen from the centre, a_0 is small
+    # and the footprint of any chord exceeds c a_0)
+    fdp = oracle.oframe(48, 48, n_c, 0, 6, 2, 7, light_mode=light_mode, estimator=1)
+    stops = [oracle.bth_path(sc.blob(), fdp, p, scenes.RECORD_DTYPE)[0] for p in range(0, 48 * 48, 7)]
+    assert set(stops) == {1, 2}, set(stops)
+
+
+def test_bth_cube_furnace_with_nee_expectation(oracle):
+    """Light mode 1 in a cube of emitting rectangles: light samples and the
+    BSDF rays are combined by the power heuristic; with the exact L_ind cache
+    the expectation is L_e / (1 - rho)."""
+    rho, Le = float(np.float32(0.5)), 1.0
+    sc = _cube_furnace(rho, Le, 64, 64)
+    L = Le / (1 - rho)
+    cfg = scenes.config_small()
+    vals = []
+    for frame in range(3):
+        fd = oracle.oframe(64, 64, 4, 0, 6, frame, 3, cache_mode=2, cache_const=(rho * L,) * 3, light_mode=1,
+                           estimator=1)
+        vals.append(oracle.estimate(cfg, None, sc.blob(), fd)["pixel"][:, 0])
+    v = np.concatenate(vals)
+    se = v.std() / math.sqrt(v.size)
+    assert se > 0
+    assert abs(v.mean() - L) < 4 * se, (v.mean(), L, se)
+
+
+def _plane_scene(W=128, H=128):
+    """One large Lambertian rectangle (z = 0, facing +z) seen straight down
+    by the camera at height 1: every path that leaves it escapes."""
+    prims = np.zeros(1, scenes.PRIM_DTYPE)
+    scenes._fill_rect(prims[0], (-50.0, -50.0, 0.0), (100.0, 0.0, 0.0), (0.0, 100.0, 0.0), (0.5,) * 3, 1.0,
+                      scenes.MAT_LAMBERT)
+    origin = np.array([0.0, 0.0, 1.0])
+    cam = (origin, origin + np.array([-0.2, 0.2, -1.0]), np.array([0.4, 0.0, 0.0]), np.array([0.0, -0.4, 0.0]))
+    return scenes.Scene(scenes._header(1, cam), prims, W, H)
+
+
+@pytest.mark.parametrize("n_c", [1, 4])
+def test_bth_first_vertex_stop_probability(oracle, n_c):
+    """P_s = p / (p + N_c / pi) with the cosine density p = cos / pi: a path
+    stops at its first vertex with probability
+    E[N_c / (cos + N_c)] = 2 N_c (1 - N_c ln(1 + 1 / N_c)) (closed form of
+    the integral over the cosine-weighted hemisphere); on an open plane the
+    continuing paths escape, so the stopping fraction is the fraction of
+    pixels with cache samples."""
+    sc = _plane_scene()
+    cfg = scenes.config_small()
+    fd = oracle.oframe(128, 128, n_c, 0, 4, 0, 11, cache_mode=1, estimator=1)
+    r = oracle.estimate(cfg, None, sc.blob(), fd)
+    frac = float(np.mean(r["count"] > 0))
+    expect = 2 * n_c * (1 - n_c * math.log(1 + 1 / n_c))
+    sd = math.sqrt(expect * (1 - expect) / r["count"].size)
+    assert abs(frac - expect) < 4 * sd, (frac, expect, sd)
+    assert set(np.unique(r["count"])) <= {0, n_c}
+
+
+def test_bth_spread_heuristic_stop_probability(oracle):
+    """Vertices after the first also stop when the footprint
+    a = (sum_i sqrt(|x_{i-1} - x_i|^2 / (p cos_i)))^2 exceeds c a_0,
+    a_0 = |x_0 - x_1|^2 / (4 pi cos_1), c = 0.01.  Between two parallel
+    Lambertian planes a distance 1 apart, with N_c = 0 (P_s = 1: only the
+    footprint test stops a path), a path seen at grazing angle cos_1 from
+    distance D_1 reaches the second plane with a = pi / cos^4(theta), so it
+    stops there iff cos^4(theta) < K = pi / (c a_0); under cosine sampling
+    that has probability min(1, sqrt(K))."""
+    prims = np.zeros(2, scenes.PRIM_DTYPE)
+    scenes._fill_rect(prims[0], (-10.0, -100.0, 0.0), (0.0, 200.0, 0.0), (200.0, 0.0, 0.0), (0.5,) * 3, 1.0,
+                      scenes.MAT_LAMBERT)
+    scenes._fill_rect(prims[1], (-10.0, -100.0, 1.0), (200.0, 0.0, 0.0), (0.0, 200.0, 0.0), (0.5,) * 3, 1.0,
+                      scenes.MAT_LAMBERT)
+    W = H = 48
+    origin = np.array([0.0, 0.0, 0.5])
+    top_left, horiz, vert = origin + np.array([1.0, -0.01, 0.04]), np.array([0.0, 0.02, 0.0]), np.array([0, 0, -0.03])
+    sc = scenes.Scene(scenes._header(2, (origin, top_left, horiz, vert)), prims, W, H)
+    fd = oracle.oframe(W, H, 0, 0, 4, 0, 5, estimator=1)
+    stops, expect = [], []
+    for pix in range(W * H):
+        at = oracle.bth_path(sc.blob(), fd, pix, scenes.RECORD_DTYPE)[0]
+        stops.append(at)
+        # the camera ray of this pixel (Philox jitter, purpose 1)
+        r = oracle.philox([pix, 0, 0, 1], [5, 0])
+        jx, jy = [((int(v) >> 8) * 2.0 ** -24) for v in r[:2]]
+        d = top_left + ((pix % W + jx) / W) * horiz + ((pix // W + jy) / H) * vert - origin
+        d = d / np.linalg.norm(d)
+        d1 = 0.5 / d[2]
+        cos1 = d[2]
+        a0 = d1 * d1 / (4 * math.pi * cos1)
+        K = math.pi / (0.01 * a0)
+        expect.append(min(1.0, math.sqrt(K)))
+    stops = np.array(stops)
+    expect = np.array(expect)
+    assert set(np.unique(stops)) <= {2, 3, 4}
+    n2 = float(np.sum(stops == 2))
+    mu, var = expect.sum(), float(np.sum(expect * (1 - expect)))
+    assert 0.2 * stops.size < mu < 0.8 * stops.size  # a non-trivial regime
+    assert abs(n2 - mu) < 4 * math.sqrt(var), (n2, mu, math.sqrt(var))
