@@ -165,7 +165,7 @@ def build_workload(args, seed_offset=0):
     W, H = args.width, args.height
     base = scenes.cornell_scene(W, H, seed=1 + seed_offset, n_prims=args.prims, glossy=True, moving_emitter=True)
     frames = [scenes.scene_at_frame(base, f) for f in range(60)]
-    cfg = scenes.config_paper_1080p() if args.input == "sh" else scenes.config_1080p()
+    cfg = scenes.config_paper_1080p() if getattr(args, "input", "freq") == "sh" else scenes.config_1080p()
     params = scenes.init_params(cfg, 1 + seed_offset)
     return cfg, params, frames
 
