@@ -161,7 +161,32 @@ typedef struct nirc_frame_desc {
                                 the shading point); cache, residual paths and
                                 training targets carry L_ind.  Spherical
                                 emitters are reached by BSDF sampling only. */
+    uint32_t estimator;      /* nirc_estimator */
+    uint32_t reserved;       /* 0 */
 } nirc_frame_desc;
+
+/* Estimator of nirc_frame_desc.estimator.
+ * NIRC_EST_TWO_LEVEL: eq. L_mlmc at the first camera hit (N cache samples,
+ *   M residual paths): unbiased.
+ * NIRC_EST_BIASED_BTH: the paper's biased variant (section "Path
+ *   Termination Heuristics", paragraph "Biased and unbiased variants"): the
+ *   camera path continues from vertex x_i with its BSDF-sampled direction
+ *   w_i (Philox purpose 8 + 16 i) unless xi_i (purpose 9 + 16 i) > P_s =
+ *   p / (p + N / pi), p the sampler's density of w_i (Balanced Termination
+ *   Heuristic), or, for i > 1, NRC's footprint
+ *   a = (sum_k sqrt(|x_{k-1} - x_k|^2 / (p_{k-1} cos_k)))^2 exceeds
+ *   0.01 |x_0 - x_1|^2 / (4 pi cos_1), or i = max_depth.  At the stopping
+ *   vertex N cache samples complete the outgoing radiance, times the path
+ *   throughput; emission found along the path is added; light mode 1 adds a
+ *   light sample at every vertex and uses w_i as the BSDF technique (one
+ *   sample, traced at the stopping vertex for its emission only).  No
+ *   Russian roulette, no residual level: requires n_resid = 0.  The
+ *   decisions (p, P_s, the footprint) are strict binary32.  lc = throughput
+ *   x cache level at the stopping vertex, lr = 0. */
+typedef enum nirc_estimator {
+    NIRC_EST_TWO_LEVEL = 0,
+    NIRC_EST_BIASED_BTH = 1
+} nirc_estimator;
 
 #define NIRC_MAX_PRIMS 1024u
 

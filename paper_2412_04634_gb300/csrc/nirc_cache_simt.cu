@@ -78,8 +78,9 @@ template <bool kSh>
 __global__ void __launch_bounds__(kSimtThreads, 1)
     k_cache_simt(CacheArgs a, const float* __restrict__ packed, const float* __restrict__ table,
                  const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
-                 const ResidRow* __restrict__ rows, float4* __restrict__ out, float* __restrict__ lc_out,
-                 float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
+                 const ResidRow* __restrict__ rows, const float4* __restrict__ beta, float4* __restrict__ out,
+                 float* __restrict__ lc_out, float* __restrict__ lr_out, uint64_t* __restrict__ sig_out,
+                 uint32_t* __restrict__ count,
                  float* __restrict__ row_n) {
     extern __shared__ __align__(16) float smem[];
     float* sw = smem;
@@ -164,6 +165,10 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
         if (a.N) {
             const float inv = 1.0f / (float)a.N;
             Lc = make_float3(lc.s.x * inv, lc.s.y * inv, lc.s.z * inv);
+            if (beta) {  // biased estimator: the cache level at the stopping vertex times the path throughput
+                const float4 bt = beta[pix];
+                Lc = make_float3(Lc.x * bt.x, Lc.y * bt.y, Lc.z * bt.z);
+            }
         }
         if (a.M) {
             const float inv = 1.0f / (float)a.M;
@@ -258,8 +263,8 @@ static size_t simt_smem(const NetShape& s) {
 }
 
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
-                              const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
-                              uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st) {
+                              const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
+                              float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st) {
     CacheArgs a;
     a.W = fd.width;
     a.H = fd.height;
@@ -282,7 +287,7 @@ cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, c
     uint64_t blocks = (P + kSimtThreads - 1) / kSimtThreads;
     if (blocks > 2ull * h->num_sms) blocks = 2ull * h->num_sms;
     const float* table = h->params + h->shape.hash_off;
-    kern<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(a, h->packed, table, recs, base, rows,
+    kern<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(a, h->packed, table, recs, base, rows, beta,
                                                        reinterpret_cast<float4*>(out_rgba), lc, lr, sig, count, row_n);
     return cudaGetLastError();
 }

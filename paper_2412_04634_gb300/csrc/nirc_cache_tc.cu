@@ -329,7 +329,8 @@ template <uint32_t AB, bool kAmax, bool kSh>
 __global__ void __launch_bounds__(640, 1)
     k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
                const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
-               const ResidRow* __restrict__ rows, float4* __restrict__ out, float* __restrict__ lc_out,
+               const ResidRow* __restrict__ rows, const float4* __restrict__ beta, float4* __restrict__ out,
+               float* __restrict__ lc_out,
                float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
                float* __restrict__ row_n, int* __restrict__ err, uint32_t* __restrict__ amax) {
     constexpr uint32_t AB16 = AB == 1 ? 1u : 0u;  // type of the 16-bit layers
@@ -749,6 +750,12 @@ __global__ void __launch_bounds__(640, 1)
                         const float inv = 1.0f / (float)a.N;
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc) Lc[cc] = acc[cc] * inv;
+                        if (beta) {  // biased estimator: times the path throughput to the stopping vertex
+                            const float4 bt = beta[gp];
+                            Lc[0] *= bt.x;
+                            Lc[1] *= bt.y;
+                            Lc[2] *= bt.z;
+                        }
                     }
                     if (a.M) {
                         const float inv = 1.0f / (float)a.M;
@@ -816,14 +823,15 @@ bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd) {
 template <uint32_t AB, bool kAmax, bool kSh>
 static cudaError_t launch_tc_kernel(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
                                       const void* img, const __half2* hash, const nirc_record* recs,
-                                      const PixelBase* base, const ResidRow* rows, float* out, float* lc, float* lr,
-                                      uint64_t* sig, uint32_t* count, float* row_n, int* err, uint32_t* amax) {
+                                      const PixelBase* base, const ResidRow* rows, const float4* beta, float* out,
+                                      float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
+                                      uint32_t* amax) {
     cudaError_t e =
         cudaFuncSetAttribute(k_cache_tc<AB, kAmax, kSh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_cache_tc<AB, kAmax, kSh><<<grid, threads, smem, st>>>(a, reinterpret_cast<const uint8_t*>(img), hash, recs, base, rows,
-                                                      reinterpret_cast<float4*>(out), lc, lr, sig, count, row_n, err,
-                                                      amax);
+    k_cache_tc<AB, kAmax, kSh><<<grid, threads, smem, st>>>(a, reinterpret_cast<const uint8_t*>(img), hash, recs, base,
+                                                            rows, beta, reinterpret_cast<float4*>(out), lc, lr, sig,
+                                                            count, row_n, err, amax);
     return cudaGetLastError();
 }
 
@@ -831,18 +839,20 @@ static cudaError_t launch_tc_kernel(uint32_t grid, uint32_t threads, size_t smem
 template <uint32_t AB, bool kAmax>
 static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
                                       const void* img, const __half2* hash, const nirc_record* recs,
-                                      const PixelBase* base, const ResidRow* rows, float* out, float* lc, float* lr,
-                                      uint64_t* sig, uint32_t* count, float* row_n, int* err, uint32_t* amax) {
+                                      const PixelBase* base, const ResidRow* rows, const float4* beta, float* out,
+                                      float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
+                                      uint32_t* amax) {
     if (a.s.sh)
-        return launch_tc_kernel<AB, kAmax, true>(grid, threads, smem, st, a, img, hash, recs, base, rows, out, lc, lr,
-                                                 sig, count, row_n, err, amax);
-    return launch_tc_kernel<AB, kAmax, false>(grid, threads, smem, st, a, img, hash, recs, base, rows, out, lc, lr, sig,
-                                              count, row_n, err, amax);
+        return launch_tc_kernel<AB, kAmax, true>(grid, threads, smem, st, a, img, hash, recs, base, rows, beta, out, lc,
+                                                 lr, sig, count, row_n, err, amax);
+    return launch_tc_kernel<AB, kAmax, false>(grid, threads, smem, st, a, img, hash, recs, base, rows, beta, out, lc,
+                                              lr, sig, count, row_n, err, amax);
 }
 
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
-                            const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
-                            uint64_t* sig, uint32_t* count, float* row_n, int* err, cudaStream_t st) {
+                            const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
+                            float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
+                            cudaStream_t st) {
     TcArgs a;
     a.W = fd.width;
     a.H = fd.height;
@@ -868,24 +878,24 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     const __half2* hash = reinterpret_cast<const __half2*>(h->hash16);
     const uint32_t threads = n_wg * 128;
     if (h->cfg.precision == NIRC_BF16_TC)
-        return launch_tc_instance<1, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, out_rgba,
+        return launch_tc_instance<1, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba,
                                             lc, lr, sig, count, row_n, err, nullptr);
     if (h->cfg.precision != NIRC_FP8_E4M3_TC)
-        return launch_tc_instance<0, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, out_rgba,
+        return launch_tc_instance<0, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba,
                                             lc, lr, sig, count, row_n, err, nullptr);
     cudaError_t e = cudaSuccess;
     uint32_t* amax = h->fp8_amax;
     const uint32_t n_slots = h->shape.hidden - 1;
     if (!h->fp8_calibrated) {
         // one FP16 launch records the activation amax (its image is overwritten below)
-        e = launch_tc_instance<0, true>(grid, threads, smem, st, a, h->packed_tc16, hash, recs, base, rows, out_rgba,
+        e = launch_tc_instance<0, true>(grid, threads, smem, st, a, h->packed_tc16, hash, recs, base, rows, beta, out_rgba,
                                         nullptr, nullptr, nullptr, nullptr, nullptr, err, amax);
         if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const_cast<nirc_handle*>(h)->fp8_calibrated = true;
     }
-    e = launch_tc_instance<2, true>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, out_rgba, lc, lr,
+    e = launch_tc_instance<2, true>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba, lc, lr,
                                     sig, count, row_n, err, amax);
     if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
     return e == cudaSuccess ? cudaGetLastError() : e;

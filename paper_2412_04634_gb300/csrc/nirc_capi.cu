@@ -170,8 +170,10 @@ void timer_end(const nirc_handle* hc, int cls, cudaStream_t st) {
 
 static size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
-size_t frame_scratch_bytes(uint64_t P, uint32_t M) {
-    return round256(P * sizeof(nirc_record)) + round256(P * sizeof(PixelBase)) + round256(P * M * sizeof(ResidRow));
+size_t frame_scratch_bytes(uint64_t P, uint32_t M, uint32_t estimator) {
+    // records | per-pixel bases | residual rows (two-level) or path throughputs (biased)
+    const size_t third = estimator == NIRC_EST_BIASED_BTH ? P * sizeof(float4) : P * M * sizeof(ResidRow);
+    return round256(P * sizeof(nirc_record)) + round256(P * sizeof(PixelBase)) + round256(third);
 }
 
 nirc_status check_frame_args(const char* who, const void* scene, const nirc_frame_desc& fd, const float* out,
@@ -182,9 +184,11 @@ nirc_status check_frame_args(const char* who, const void* scene, const nirc_fram
         return NIRC_ERR_INVALID;
     }
     if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
-        fd.max_depth > 64 || fd.cache_mode > 2 || fd.light_mode > 1 || P > 0xFFFFFFFFull) {
-        set_error("%s: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64, light_mode 0..1)", who,
-                  NIRC_MAX_PRIMS);
+        fd.max_depth > 64 || fd.cache_mode > 2 || fd.light_mode > 1 || P > 0xFFFFFFFFull ||
+        fd.estimator > NIRC_EST_BIASED_BTH || (fd.estimator == NIRC_EST_BIASED_BTH && fd.n_resid != 0)) {
+        set_error("%s: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64, light_mode 0..1, "
+                  "estimator 0..1, M = 0 for the biased estimator)",
+                  who, NIRC_MAX_PRIMS);
         return NIRC_ERR_INVALID;
     }
     if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
@@ -206,11 +210,14 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
     // the cache kernel reads, so no part of the scratch has to start at zero.
     nirc_record* recs = reinterpret_cast<nirc_record*>(sp);
     PixelBase* base = reinterpret_cast<PixelBase*>(sp + rec_bytes);
-    ResidRow* rows = reinterpret_cast<ResidRow*>(sp + rec_bytes + base_bytes);
+    const bool biased = fd.estimator == NIRC_EST_BIASED_BTH;
+    ResidRow* rows = biased ? nullptr : reinterpret_cast<ResidRow*>(sp + rec_bytes + base_bytes);
+    float4* beta = biased ? reinterpret_cast<float4*>(sp + rec_bytes + base_bytes) : nullptr;
     uint64_t* sig = aux ? aux->sig : nullptr;
     uint32_t* count = aux ? aux->count : nullptr;
     timer_begin(h, NIRC_K_PATH_TRACE, st);
-    cudaError_t e = launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st);
+    cudaError_t e = biased ? launch_primary_bth(h, scene, fd, recs, base, beta, sig, count, st)
+                           : launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st);
     timer_end(h, NIRC_K_PATH_TRACE, st);
     if (e != cudaSuccess) {
         set_error("%s (path tracing): %s", who, cudaGetErrorString(e));
@@ -219,10 +226,10 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
     timer_begin(h, NIRC_K_CACHE, st);
     const bool tc = tc_supported(h, fd);
     if (tc) {
-        e = launch_cache_tc(h, fd, recs, base, rows, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig, count,
-                            aux ? aux->row_n : nullptr, h->dev_err, st);
+        e = launch_cache_tc(h, fd, recs, base, rows, beta, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
+                            count, aux ? aux->row_n : nullptr, h->dev_err, st);
     } else {
-        e = launch_cache_simt(h, fd, recs, base, rows, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
+        e = launch_cache_simt(h, fd, recs, base, rows, beta, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
                               count, aux ? aux->row_n : nullptr, st);
     }
     timer_end(h, NIRC_K_CACHE, st);
@@ -587,7 +594,7 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
     if (P == 0) return NIRC_OK;
     nirc_status s = check_frame_args("nirc_estimate_frame", d_scene, fd, d_out_rgba, aux);
     if (s != NIRC_OK) return s;
-    s = ensure(&h->scratch, &h->scratch_bytes, frame_scratch_bytes(P, fd.n_resid), "frame");
+    s = ensure(&h->scratch, &h->scratch_bytes, frame_scratch_bytes(P, fd.n_resid, fd.estimator), "frame");
     if (s != NIRC_OK) return s;
     return enqueue_frame("nirc_estimate_frame", h, d_scene, fd, d_out_rgba, aux, h->scratch, (cudaStream_t)stream);
 }

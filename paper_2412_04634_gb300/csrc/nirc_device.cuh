@@ -70,7 +70,9 @@ enum : uint32_t {
     PURPOSE_BOUNCE = 4,  // + 16 * segment
     PURPOSE_RR = 5,      // + 16 * segment
     PURPOSE_TRAIN_PICK = 6,
-    PURPOSE_LIGHT = 7    // + 16 * segment (0: the shading point), light mode 1
+    PURPOSE_LIGHT = 7,   // + 16 * segment (0: the shading point), light mode 1
+    PURPOSE_BTH_DIR = 8, // + 16 * vertex: biased estimator, direction sampled at a camera-path vertex
+    PURPOSE_BTH_XI = 9   // + 16 * vertex: biased estimator, the termination test's uniform
 };
 
 constexpr float kTMin = 1e-4f;

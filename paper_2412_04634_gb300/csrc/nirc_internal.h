@@ -122,14 +122,17 @@ GridParams make_grid(const nirc_config& cfg);
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig,
                                  uint32_t* count, cudaStream_t st);
+cudaError_t launch_primary_bth(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd, nirc_record* recs,
+                               PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st);
 cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
                              uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, uint32_t light_mode,
                              nirc_record* recs, float* dirs, float* targets, cudaStream_t st);
 
 // nirc_cache_simt.cu
+// beta (biased estimator, else NULL): per-pixel path throughput applied to the cache level
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
-                              const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
-                              uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st);
+                              const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
+                              float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st);
 cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, const float* dirs, uint64_t n,
                               float* out, cudaStream_t st);
 cudaError_t launch_repack_simt(const nirc_handle* h, cudaStream_t st);
@@ -139,8 +142,9 @@ size_t tc_image_bytes(uint32_t hidden);
 cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st);
 bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd);
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
-                            const PixelBase* base, const ResidRow* rows, float* out_rgba, float* lc, float* lr,
-                            uint64_t* sig, uint32_t* count, float* row_n, int* err, cudaStream_t st);
+                            const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
+                            float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
+                            cudaStream_t st);
 
 // nirc_train.cu
 size_t train_scratch_bytes(const nirc_handle* h, uint64_t n);
@@ -155,7 +159,7 @@ cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st);
 // nirc_capi.cu: shared by the public frame entry points and the server.
 // Frame scratch = records | per-pixel bases | residual rows, each part
 // rounded up to 256 bytes.
-size_t frame_scratch_bytes(uint64_t P, uint32_t M);
+size_t frame_scratch_bytes(uint64_t P, uint32_t M, uint32_t estimator);
 // Argument checks of a frame call (message prefixed with `who`).
 nirc_status check_frame_args(const char* who, const void* scene, const nirc_frame_desc& fd, const float* out,
                              const nirc_frame_aux* aux);

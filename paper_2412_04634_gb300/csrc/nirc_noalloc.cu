@@ -68,7 +68,7 @@ extern "C" nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d
     if (P == 0) return NIRC_OK;
     nirc_status st = check_frame_args("nirc_estimate_frame_noalloc", d_scene, fd, d_out_rgba, aux);
     if (st != NIRC_OK) return st;
-    const size_t need = frame_scratch_bytes(P, fd.n_resid);
+    const size_t need = frame_scratch_bytes(P, fd.n_resid, fd.estimator);
     if (need > kNoAllocScratchBytes) {
         set_error("nirc_estimate_frame_noalloc: frame needs %zu bytes of scratch (W*H*(96 + 32*M) rounded), more than "
                   "the fixed %zu-byte area; use nirc_estimate_frame or a smaller tile",

@@ -11,7 +11,10 @@
 //   T paths from uniformly drawn pixels, one record per path, organised the
 //   same way.
 //
-// Both kernels are persistent: each CTA stages the primitives' geometry in
+// k_primary_bth: the biased estimator's camera path (Balanced Termination
+//   Heuristic), see below.
+//
+// The kernels are persistent: each CTA stages the primitives' geometry in
 // shared memory and, for scenes of more than 16 primitives, builds its own
 // bounding-volume hierarchy there once, then loops over pixels (paths).
 //
@@ -439,6 +442,179 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// Biased estimator: path termination (Balanced Termination Heuristic and
+// NRC's footprint test).  These quantities decide whether a path goes on,
+// so they are strict binary32 in a fixed operation order.
+// ---------------------------------------------------------------------------
+
+// Density of the BSDF sampler at wi: cos/pi (Lambertian), or the one-sample
+// mixture 1/2 cos/pi + 1/2 G1(wo) D / (4 cos_o) with D = a2 / (pi dd^2),
+// dd = |n x h|^2 + a2 (n.h)^2, a = roughness^2.
+__device__ __forceinline__ float sampler_pdf32(V3 n, V3 wo, V3 wi, float rough, uint32_t mat) {
+    const float ci = sdot(n, wi);
+    if (mat == MAT_BLACK || !(ci > 0.f)) return 0.f;
+    if (mat == MAT_LAMBERT) return __fmul_rn(ci, kInvPi);
+    const float co = sdot(n, wo);
+    const V3 h = snormalize(V3{__fadd_rn(wo.x, wi.x), __fadd_rn(wo.y, wi.y), __fadd_rn(wo.z, wi.z)});
+    const float a = __fmul_rn(rough, rough), a2 = __fmul_rn(a, a);
+    const float cnh = sdot(n, h);
+    const V3 cx{__fsub_rn(__fmul_rn(n.y, h.z), __fmul_rn(n.z, h.y)), __fsub_rn(__fmul_rn(n.z, h.x), __fmul_rn(n.x, h.z)),
+                __fsub_rn(__fmul_rn(n.x, h.y), __fmul_rn(n.y, h.x))};
+    const float dd = __fadd_rn(sdot(cx, cx), __fmul_rn(a2, __fmul_rn(cnh, cnh)));
+    const float D = __fdiv_rn(a2, __fmul_rn(__fmul_rn(kPi, dd), dd));
+    const float lam = __fsqrt_rn(__fadd_rn(a2, __fmul_rn(__fsub_rn(1.f, a2), __fmul_rn(co, co))));
+    const float g1 = __fdiv_rn(__fmul_rn(2.f, co), __fadd_rn(co, lam));
+    return __fadd_rn(__fmul_rn(0.5f, __fmul_rn(ci, kInvPi)),
+                     __fmul_rn(0.5f, __fdiv_rn(__fmul_rn(g1, D), __fmul_rn(4.f, co))));
+}
+
+// Balanced Termination Heuristic: continuation probability p / (p + N_c / pi).
+__device__ __forceinline__ float bth_continue_prob(float p, uint32_t n_c) {
+    return __fdiv_rn(p, __fadd_rn(p, __fmul_rn((float)n_c, kInvPi)));
+}
+
+// Footprint term sqrt(t^2 / (p cos_in)) of one segment (NRC's spread heuristic).
+__device__ __forceinline__ float spread_term(float t, float p, float cos_in) {
+    return __fsqrt_rn(__fdiv_rn(__fmul_rn(t, t), __fmul_rn(p, cos_in)));
+}
+
+// Emission of primitive q seen along d at distance t from a vertex whose
+// BSDF technique sampled d with density pb (light mode 1: power heuristic
+// against the light technique for emitting rectangles).
+template <bool kNee>
+__device__ __forceinline__ float3 weighted_emission(const Tracer& tr, const Prim* __restrict__ gp, const Lights& lt,
+                                                    int q, bool front, V3 d, float t, float pb) {
+    const Prim* Q = gp + q;
+    if (!(front || (__ldg(&Q->flags) & EMIT_TWO_SIDED))) return make_float3(0.f, 0.f, 0.f);
+    const float3 le = make_float3(__ldg(&Q->emission[0]), __ldg(&Q->emission[1]), __ldg(&Q->emission[2]));
+    if (!(le.x > 0.f || le.y > 0.f || le.z > 0.f)) return make_float3(0.f, 0.f, 0.f);
+    float wb = 1.f;
+    if constexpr (kNee) {
+        if (__ldg(&Q->kind) == KIND_RECT && lt.n) wb = power_weight(pb, light_pdf(tr.prims[q], d, t, lt.n));
+    }
+    return make_float3(le.x * wb, le.y * wb, le.z * wb);
+}
+
+// Per pixel, the camera path of the biased estimator: from vertex x_i it
+// continues along the BSDF-sampled w_i unless xi_i > P_s(w_i), or (i > 1)
+// the footprint a exceeds 0.01 a_0, or i = max_depth.  Emission found along
+// the path (and in light mode 1 a light sample at every vertex, with w_i as
+// the one-sample BSDF technique, traced at the stopping vertex for its
+// emission) goes into base.le; the stopping vertex's record and the
+// throughput up to it are what the cache kernel completes.  One pixel per
+// lane, pixels from the work counter.
+template <bool kNee>
+__global__ void __launch_bounds__(kPtThreads, 4) k_primary_bth(const SceneHeader* __restrict__ hd_g,
+                                                                const Prim* __restrict__ gp, FrameArgs a,
+                                                                nirc_record* __restrict__ recs,
+                                                                PixelBase* __restrict__ base,
+                                                                float4* __restrict__ beta_out,
+                                                                uint64_t* __restrict__ sig_out,
+                                                                uint32_t* __restrict__ count,
+                                                                unsigned long long* __restrict__ work) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SceneHeader hd;
+    __shared__ uint32_t s_nlights;
+    const Tracer tr = setup_scene(hd_g, gp, a.n_prims, smem_raw, &hd);
+    Lights lt{nullptr, 0u};
+    if constexpr (kNee)
+        lt = collect_lights(gp, a.n_prims, reinterpret_cast<uint16_t*>(smem_raw + pt_geom_bytes(a.n_prims)),
+                            &s_nlights);
+    const uint64_t P = (uint64_t)a.W * a.H;
+    while (true) {
+        const uint64_t mine = fetch_work(work, true);
+        if (__all_sync(0xffffffffu, mine >= P)) break;
+        if (mine >= P) continue;
+        const uint32_t pix = (uint32_t)mine;
+        uint64_t sig = kSigInit;
+        float3 le = make_float3(0.f, 0.f, 0.f), beta = make_float3(1.f, 1.f, 1.f);
+        uint32_t stop_at = 0;
+        const U4 rc = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
+        V3 o, d;
+        camera_ray(hd, a.W, a.H, pix % a.W, pix / a.W, u01(rc.x), u01(rc.y), o, d);
+        float t = 0.f;
+        int prim = tr.nearest(o, d, t);
+        sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+        if (prim >= 0) {
+            Hit h = hit_info(tr.prims[prim], o, d, t);
+            le = weighted_emission<false>(tr, gp, lt, prim, h.front, d, t, 0.f);
+            const float c_a0 =
+                __fmul_rn(0.01f, __fdiv_rn(__fmul_rn(t, t), __fmul_rn(__fmul_rn(4.f, kPi), fabsf(sdot(h.n, d)))));
+            float spread = 0.f;
+            for (uint32_t i = 1;; ++i) {
+                const Prim* Q = gp + prim;
+                const uint32_t mat = __ldg(&Q->flags) & 3u;
+                const float3 alb = make_float3(__ldg(&Q->albedo[0]), __ldg(&Q->albedo[1]), __ldg(&Q->albedo[2]));
+                const float rough = __ldg(&Q->roughness);
+                const V3 wo = sneg(d);
+                if constexpr (kNee) {
+                    float3 dl = make_float3(0.f, 0.f, 0.f);
+                    sig = sig_mix(sig, nee_sample(tr, gp, lt, h.p, h.n, wo, alb, rough, mat, 1u, a.k0, a.k1, pix, 0u,
+                                                  PURPOSE_LIGHT + 16u * i, dl));
+                    le.x += beta.x * dl.x;
+                    le.y += beta.y * dl.y;
+                    le.z += beta.z * dl.z;
+                }
+                const BsdfSample s =
+                    sample_bsdf(h.n, wo, alb, rough, mat, a.k0, a.k1, pix, 0u, PURPOSE_BTH_DIR + 16u * i);
+                sig = sig_mix(sig, s.word);
+                const float p = s.valid ? sampler_pdf32(h.n, wo, s.wi, rough, mat) : 0.f;
+                const U4 rx = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_BTH_XI + 16u * i);
+                uint32_t stop = u01(rx.x) > bth_continue_prob(p, a.N) ? 1u : 0u;
+                if (i > 1 && __fmul_rn(spread, spread) > c_a0) stop |= 2u;
+                if (i == a.D) stop |= 4u;
+                sig = sig_mix(sig, stop);
+                if (stop) {
+                    write_record(recs + pix, h, d, Q, (uint32_t)prim, 1u | (mat << 1));
+                    stop_at = i;
+                    if constexpr (kNee) {
+                        if (s.valid) {  // the BSDF technique of the direct light at the stopping vertex
+                            float tq = 0.f;
+                            const int q = tr.nearest(h.p, s.wi, tq);
+                            sig = sig_mix(sig, q < 0 ? 0xFFFFFFFFu : (uint32_t)q);
+                            if (q >= 0) {
+                                const Hit hq = hit_info(tr.prims[q], h.p, s.wi, tq);
+                                const float pb = bsdf_eval(h.n, wo, s.wi, alb, rough, mat).pdf;
+                                const float3 e = weighted_emission<true>(tr, gp, lt, q, hq.front, s.wi, tq, pb);
+                                le.x += beta.x * s.w.x * e.x;
+                                le.y += beta.y * s.w.y * e.y;
+                                le.z += beta.z * s.w.z * e.z;
+                            }
+                        }
+                    }
+                    break;
+                }
+                float pb = 0.f;
+                if constexpr (kNee) pb = bsdf_eval(h.n, wo, s.wi, alb, rough, mat).pdf;
+                beta.x *= s.w.x;
+                beta.y *= s.w.y;
+                beta.z *= s.w.z;
+                o = h.p;
+                d = s.wi;
+                prim = tr.nearest(o, d, t);
+                sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+                if (prim < 0) break;
+                h = hit_info(tr.prims[prim], o, d, t);
+                const float3 e = weighted_emission<kNee>(tr, gp, lt, prim, h.front, d, t, pb);
+                le.x += beta.x * e.x;
+                le.y += beta.y * e.y;
+                le.z += beta.z * e.z;
+                spread = __fadd_rn(spread, spread_term(t, p, fabsf(sdot(h.n, d))));
+            }
+        }
+        if (!stop_at) {
+            float4* q = reinterpret_cast<float4*>(recs + pix);
+            q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        base[pix].le = make_float4(le.x, le.y, le.z, 0.f);
+        base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
+        beta_out[pix] = make_float4(beta.x, beta.y, beta.z, 0.f);
+        if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+        if (count) count[pix] = 0;
+    }
+}
+
 // Training paths, organised like k_primary_resid: per path index the pixel
 // pick, camera ray, record and first direction, then the path's segments;
 // one ray per busy lane per iteration.
@@ -579,6 +755,30 @@ cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const 
     if (fd.light_mode == 1)
         return launch_primary_resid_t<true>(h, hd, gp, a, P, recs, base, rows, sig, count, st);
     return launch_primary_resid_t<false>(h, hd, gp, a, P, recs, base, rows, sig, count, st);
+}
+
+template <bool kNee>
+static cudaError_t launch_primary_bth_t(const nirc_handle* h, const SceneHeader* hd, const Prim* gp,
+                                        const FrameArgs& a, uint64_t P, nirc_record* recs, PixelBase* base,
+                                        float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st) {
+    const size_t smem = pt_smem(a.n_prims);
+    uint32_t grid = 1;
+    cudaError_t e = persistent_grid(k_primary_bth<kNee>, smem, P, h->num_sms, &grid);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_primary_bth<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, beta, sig, count, h->work_counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primary_bth(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd, nirc_record* recs,
+                               PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st) {
+    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
+    const uint64_t P = (uint64_t)fd.width * fd.height;
+    const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
+    const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
+    if (fd.light_mode == 1) return launch_primary_bth_t<true>(h, hd, gp, a, P, recs, base, beta, sig, count, st);
+    return launch_primary_bth_t<false>(h, hd, gp, a, P, recs, base, beta, sig, count, st);
 }
 
 template <bool kNee>

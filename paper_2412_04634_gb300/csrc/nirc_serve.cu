@@ -521,7 +521,7 @@ nirc_status nirc_server_submit(nirc_server* s, const nirc_request* req) {
     q->r = r;
     const uint64_t P = (uint64_t)r.width * r.height;
     q->img_bytes = granule(P * 16);
-    q->scr_bytes = granule(frame_scratch_bytes(P, r.n_resid));
+    q->scr_bytes = granule(frame_scratch_bytes(P, r.n_resid, NIRC_EST_TWO_LEVEL));
     std::lock_guard<std::mutex> lk(s->mu);
     if (r.scene >= s->scenes.size()) {
         delete q;
