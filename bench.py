@@ -43,7 +43,14 @@ WORKLOAD_SH = ("1080p dynamic Cornell family (256 prims, GGX), the paper's NIRC 
 
 
 def workload_name(args):
-    return WORKLOAD_SH if getattr(args, "input", "freq") == "sh" else WORKLOAD
+    name = WORKLOAD_SH if getattr(args, "input", "freq") == "sh" else WORKLOAD
+    if getattr(args, "estimator", "two_level") == "bth":
+        name += "; biased estimator (Balanced Termination Heuristic, N cache samples at the stopping vertex, M=0)"
+    return name
+
+
+def estimator_code(args):
+    return 1 if getattr(args, "estimator", "two_level") == "bth" else 0
 
 
 def parse_args():
@@ -73,6 +80,9 @@ def parse_args():
                     help="network input of the frame workload: frequency encodings of direction and normal with "
                          "the 16-level hash grid (default), or the paper's (12-level hash grid, spherical "
                          "harmonics, albedo / one-blob normal and roughness)")
+    ap.add_argument("--estimator", choices=["two_level", "bth"], default="two_level",
+                    help="two_level: eq. L_mlmc at the first hit (default); bth: the biased variant with the "
+                         "Balanced Termination Heuristic (N cache samples at the stopping vertex, M forced to 0)")
     ap.add_argument("--light-mode", type=int, choices=[0, 1], default=0,
                     help="1: the cache carries L_ind, direct light by NEE + MIS (frame and serve workloads)")
     ap.add_argument("--serve-requests", type=int, default=256)
@@ -250,7 +260,7 @@ class FrameRunner:
         sc = self.scene_dev[f % 60] if scene is None else scene
         h = self.cache.h
         d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
-                         light_mode=a.light_mode)
+                         light_mode=a.light_mode, estimator=estimator_code(a))
         N.nirc_estimate_frame(h, sc, d, self.img)
         N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs, self.dirs,
                          self.tgts, light_mode=a.light_mode)
@@ -453,7 +463,7 @@ def run_ours(args):
                                  "fp8": "fp8_e4m3_tc (hidden layers)"}[args.precision],
                    "frames": f"{first}..{first + args.steps - 1} (mod 60)",
                    "l2": "no flush: per-frame working set (~0.6 GB of records, rows, images, tables) > 129 MB L2",
-                   "light_mode": args.light_mode,
+                   "light_mode": args.light_mode, "estimator": args.estimator, "input": args.input,
                    "parallelism": f"replicas x{world}"},
         "p50_ms": float(np.percentile(res["step_ms"], 50)), "p99_ms": float(np.percentile(res["step_ms"], 99)),
         "frame_mrse": res["mrse"], "mrse_reference": f"{ref_spp} spp path tracing, depth 16, frame {last_frame}",
@@ -476,9 +486,11 @@ def oracle_step(O, cfg, params64, m, v, blob, args, frame, pix, T_s, seed):
     """One bounded sample of the frame step on the oracle: the listed pixels'
     two-level estimates, T_s training paths, loss + gradient, Adam, MRSE."""
     W, H = args.width, args.height
-    fd = O.oframe(W, H, args.n_cache, args.n_resid, args.depth, frame, seed)
+    fd = O.oframe(W, H, args.n_cache, args.n_resid, args.depth, frame, seed, light_mode=args.light_mode,
+                  estimator=estimator_code(args))
     est = O.estimate(cfg, params64, blob, fd, pixels=pix)
-    recs, dirs, tg, _ = O.gen_train(blob, W, H, T_s, frame, seed, args.depth, scenes.RECORD_DTYPE)
+    recs, dirs, tg, _ = O.gen_train(blob, W, H, T_s, frame, seed, args.depth, scenes.RECORD_DTYPE,
+                                    light_mode=args.light_mode)
     loss, g = O.loss_grad(cfg, params64, recs, dirs, tg)
     O.adam_step(params64, m, v, g, 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps)
     O.mrse(est["pixel"], est["pixel"])
@@ -812,6 +824,8 @@ def run_serve_bench(args):
 
 def main():
     args = parse_args()
+    if args.estimator == "bth":
+        args.n_resid = 0  # the biased estimator has no residual level
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "train":
