@@ -112,8 +112,10 @@ typedef struct {
     uint64_t seed;
     uint32_t cache_mode; /* 0 network, 1 zero, 2 constant */
     uint32_t light_mode; /* 0 cache = full L_i, 1 cache = L_ind with NEE + MIS (eq. Lsplit) */
-    uint32_t estimator;  /* 0 two-level (eq. L_mlmc), 1 biased with the Balanced Termination Heuristic */
-    uint32_t pad2;
+    uint32_t estimator;  /* 0 two-level (eq. L_mlmc), 1 biased with the Balanced Termination Heuristic,
+                            2 two-level at the first three vertices of each path */
+    uint32_t n_cache2;   /* estimator 2: cache samples at the second and third vertex */
+    uint32_t n_cache3;
     double cache_const[3];
 } o_frame;
 
@@ -132,7 +134,8 @@ enum {
     PURPOSE_TRAIN_PICK = 6,
     PURPOSE_LIGHT = 7,  /* + 16 * segment (0: the shading point) */
     PURPOSE_BTH_DIR = 8, /* + 16 * vertex: the scattering direction sampled at a biased path's vertex */
-    PURPOSE_BTH_XI = 9   /* + 16 * vertex: the termination test's uniform */
+    PURPOSE_BTH_XI = 9,  /* + 16 * vertex: the termination test's uniform */
+    PURPOSE_VCACHE = 10  /* + 16 * vertex (2, 3): cache samples at later vertices of a residual path */
 };
 
 static const float T_MIN = 1e-4f;
@@ -823,11 +826,66 @@ static void make_record(const o_prim* pr, uint32_t prim, const o_hit* h, const f
     rec->flags = 1u | ((pr->flags & 3u) << 1);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Two-level estimation at later path vertices (estimator 2; paper:        */
+/* "Biased and unbiased variants": NIRC at the first three vertices, and   */
+/* the redistribution of neural samples between vertices)                   */
+/* ------------------------------------------------------------------------ */
+
+/* The residual path j of pixel pix reaches vertex x_k (k = 2, 3; x_1 is the
+ * shading point) with throughput beta_k.  Its incident radiance there is
+ * estimated by the same two levels (eq. L_mlmc applied recursively): the
+ * path-traced continuation minus the cache's value for the continuation
+ * direction w_k, plus N_k cache samples.  Along the path this adds
+ *   beta_k C_k - beta_{k+1} n(x_k, w_k),  C_k = 1/N_k sum_i (f cos / p)_i n(x_k, w_i),
+ * the second term only when the path continues (beta_{k+1} includes the
+ * continuation weight and the Russian-roulette factor).  Both terms have
+ * the same expectation, so the correction has mean zero for any cache. */
+typedef struct {
+    const o_cfg* c;
+    const double* params;
+    const o_frame* fd;
+    uint32_t pix, j;
+    double L[3]; /* sum of the corrections along the path */
+} o_mv;
+
+static void cache_value(const o_cfg* c, const double* params, const o_frame* fd, const o_record* rec,
+                        const float w[3], double nval[3]);
+
+/* beta_k C_k at vertex k: N_k directions from purpose 10 + 16 k, counter (pix, j << 16 | i). */
+static void mv_vertex(o_mv* mv, const o_record* rec, uint32_t k, const double beta[3])
+{
+    uint32_t nk = k == 2 ? mv->fd->n_cache2 : mv->fd->n_cache3;
+    if (nk == 0) return;
+    uint32_t k0 = (uint32_t)mv->fd->seed, k1 = mv->fd->frame;
+    double C[3] = {0.0, 0.0, 0.0};
+    for (uint32_t i = 0; i < nk; i++) {
+        o_sample s;
+        sample_bsdf(rec, k0, k1, mv->pix, (mv->j << 16) | i, PURPOSE_VCACHE + 16u * k, &s);
+        if (!s.valid) continue;
+        double nv[3];
+        cache_value(mv->c, mv->params, mv->fd, rec, s.wi, nv);
+        for (int q = 0; q < 3; q++) C[q] += s.w[q] * nv[q];
+    }
+    for (int q = 0; q < 3; q++) mv->L[q] += beta[q] * C[q] / (double)nk;
+}
+
+/* - beta_{k+1} n(x_k, w_k) for the continuation direction (vertices with N_k = 0
+ * use no cache at all). */
+static void mv_continue(o_mv* mv, const o_record* rec, uint32_t k, const float wi[3], const double beta_next[3])
+{
+    if ((k == 2 ? mv->fd->n_cache2 : mv->fd->n_cache3) == 0) return;
+    double nv[3];
+    cache_value(mv->c, mv->params, mv->fd, rec, wi, nv);
+    for (int q = 0; q < 3; q++) mv->L[q] -= beta_next[q] * nv[q];
+}
+
 /* Incident radiance along (o, d): emission at each vertex, BSDF-sampled
  * continuation, Russian roulette (continue with probability 0.9) before each
- * continuation, at most max_depth segments. */
+ * continuation, at most max_depth segments.  With mv, the two-level terms at
+ * the path's vertices 2 and 3 (segments 1 and 2) go into mv->L. */
 static void trace_path(const uint8_t* blob, const float o_in[3], const float d_in[3], uint32_t k0, uint32_t k1,
-                       uint32_t c0, uint32_t c1, uint32_t max_depth, double L[3], uint64_t* sig)
+                       uint32_t c0, uint32_t c1, uint32_t max_depth, double L[3], uint64_t* sig, o_mv* mv)
 {
     const o_header* hd = (const o_header*)blob;
     const o_prim* prims = scene_prims(blob);
@@ -845,6 +903,10 @@ static void trace_path(const uint8_t* blob, const float o_in[3], const float d_i
         double le[3];
         emitted(&prims[prim], h.front, le);
         for (int c = 0; c < 3; c++) L[c] += beta[c] * le[c];
+        o_record rec;
+        make_record(&prims[prim], (uint32_t)prim, &h, d, &rec);
+        const int mv_here = mv && seg <= 2u;
+        if (mv_here) mv_vertex(mv, &rec, seg + 1u, beta);
         if (seg == max_depth) break;
         uint32_t r[4];
         philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg, r);
@@ -852,13 +914,12 @@ static void trace_path(const uint8_t* blob, const float o_in[3], const float d_i
         *sig = sig_mix(*sig, (uint32_t)cont);
         if (!cont) break;
         for (int c = 0; c < 3; c++) beta[c] /= (double)RR_CONTINUE;
-        o_record rec;
-        make_record(&prims[prim], (uint32_t)prim, &h, d, &rec);
         o_sample s;
         sample_bsdf(&rec, k0, k1, c0, c1, PURPOSE_BOUNCE + 16u * seg, &s);
         *sig = sig_mix(*sig, sample_word(&s));
         if (!s.valid) break;
         for (int c = 0; c < 3; c++) beta[c] *= s.w[c];
+        if (mv_here) mv_continue(mv, &rec, seg + 1u, s.wi, beta);
         for (int k = 0; k < 3; k++) {
             o[k] = h.p[k];
             d[k] = s.wi[k];
@@ -1005,7 +1066,7 @@ static uint32_t nee_sample(const uint8_t* blob, const o_lights* lights, const o_
  * the shading point's MIS (n_b0 BSDF samples of density pb0 there). */
 static void trace_path_nee(const uint8_t* blob, const o_lights* lights, const float o_in[3], const float d_in[3],
                            uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint32_t max_depth, uint32_t n_b0,
-                           double pb0, double L[3], double first_emit[3], uint64_t* sig)
+                           double pb0, double L[3], double first_emit[3], uint64_t* sig, o_mv* mv)
 {
     const o_header* hd = (const o_header*)blob;
     const o_prim* prims = scene_prims(blob);
@@ -1041,6 +1102,8 @@ static void trace_path_nee(const uint8_t* blob, const o_lights* lights, const fl
         *sig = sig_mix(*sig, nee_sample(blob, lights, &rec, seg < max_depth ? 1u : 0u, k0, k1, c0, c1,
                                         PURPOSE_LIGHT + 16u * seg, dl));
         for (int c = 0; c < 3; c++) L[c] += beta[c] * dl[c];
+        const int mv_here = mv && seg <= 2u;
+        if (mv_here) mv_vertex(mv, &rec, seg + 1u, beta);
         if (seg == max_depth) break;
         uint32_t r[4];
         philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg, r);
@@ -1053,6 +1116,7 @@ static void trace_path_nee(const uint8_t* blob, const o_lights* lights, const fl
         *sig = sig_mix(*sig, sample_word(&s));
         if (!s.valid) break;
         for (int c = 0; c < 3; c++) beta[c] *= s.w[c];
+        if (mv_here) mv_continue(mv, &rec, seg + 1u, s.wi, beta);
         double fc[3];
         bsdf_eval(&rec, s.wi, fc, &pb_prev);
         for (int k = 0; k < 3; k++) {
@@ -1150,17 +1214,21 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             sp = sig_mix(sp, sample_word(&s));
             if (!s.valid) continue;
             double Li[3], nv[3];
+            o_mv mv = {c, params, fd, pix, j, {0.0, 0.0, 0.0}};
+            o_mv* mvp = fd->estimator == 2 ? &mv : NULL;
             if (lights) {
                 double fc[3], pb, e1[3];
                 bsdf_eval(&rec, s.wi, fc, &pb);
                 trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, fd->n_resid, pb, Li, e1,
-                               &sp);
+                               &sp, mvp);
                 for (int k = 0; k < 3; k++) Le[k] += s.w[k] * e1[k] / (double)fd->n_resid;
             } else {
-                trace_path(blob, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, Li, &sp);
+                trace_path(blob, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, Li, &sp, mvp);
             }
             cache_value(c, params, fd, &rec, s.wi, nv);
-            for (int k = 0; k < 3; k++) Lr[k] += s.w[k] * (Li[k] - nv[k]);
+            /* with N = 0 there is no cache level, and nothing is subtracted */
+            const double use = fd->n_cache ? 1.0 : 0.0;
+            for (int k = 0; k < 3; k++) Lr[k] += s.w[k] * (Li[k] - use * nv[k] + mv.L[k]);
             if (row_n)
                 for (int k = 0; k < 3; k++) row_n[3 * (fd->n_cache + j) + k] = nv[k];
             active++;
@@ -1474,9 +1542,9 @@ void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint
                 if (lights) {
                     /* target = L_ind: the first hit's emission is direct light */
                     double e1[3];
-                    trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, tr, 0u, max_depth, 0u, 0.0, tg, e1, &sg);
+                    trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, tr, 0u, max_depth, 0u, 0.0, tg, e1, &sg, NULL);
                 } else {
-                    trace_path(blob, rec.p, s.wi, k0, k1, tr, 0u, max_depth, tg, &sg);
+                    trace_path(blob, rec.p, s.wi, k0, k1, tr, 0u, max_depth, tg, &sg, NULL);
                 }
                 for (int k = 0; k < 3; k++) dir[k] = s.wi[k];
             } else {
@@ -1703,7 +1771,7 @@ void orc_trace_path(const uint8_t* blob, const float o[3], const float d[3], uin
                     uint32_t c1, uint32_t max_depth, double L[3])
 {
     uint64_t sg = SIG_INIT;
-    trace_path(blob, o, d, k0, k1, c0, c1, max_depth, L, &sg);
+    trace_path(blob, o, d, k0, k1, c0, c1, max_depth, L, &sg, NULL);
 }
 
 /* One NEE sample at a shading record (light mode 1 machinery, for the

@@ -35,8 +35,8 @@ class OFrame(ctypes.Structure):
         ("n_cache", ctypes.c_uint32), ("n_resid", ctypes.c_uint32),
         ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("cache_mode", ctypes.c_uint32),
-        ("light_mode", ctypes.c_uint32), ("estimator", ctypes.c_uint32), ("pad2", ctypes.c_uint32),
-        ("cache_const", ctypes.c_double * 3),
+        ("light_mode", ctypes.c_uint32), ("estimator", ctypes.c_uint32), ("n_cache2", ctypes.c_uint32),
+        ("n_cache3", ctypes.c_uint32), ("cache_const", ctypes.c_double * 3),
     ]
 
 
@@ -96,8 +96,9 @@ def ocfg(cfg) -> OCfg:
 
 
 def oframe(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode=0,
-           cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0) -> OFrame:
-    f = OFrame(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode, light_mode, estimator)
+           cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0, n_cache2=0, n_cache3=0) -> OFrame:
+    f = OFrame(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode, light_mode, estimator, n_cache2,
+               n_cache3)
     for k in range(3):
         f.cache_const[k] = float(cache_const[k])
     return f

@@ -1046,3 +1046,64 @@ def test_bth_spread_heuristic_stop_probability(oracle):
     mu, var = expect.sum(), float(np.sum(expect * (1 - expect)))
     assert 0.2 * stops.size < mu < 0.8 * stops.size  # a non-trivial regime
     assert abs(n2 - mu) < 4 * math.sqrt(var), (n2, mu, math.sqrt(var))
+
+
+# ---------------------------------------------------------------------------
+# Two-level estimation at the first three vertices (estimator 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("D,M,N1,N2,N3", [(1, 1, 4, 3, 5), (2, 1, 1, 7, 2), (1, 3, 5, 4, 0), (2, 2, 0, 6, 6)])
+def test_multivertex_furnace_exact(oracle, D, M, N1, N2, N3):
+    """Emitting Lambertian sphere, exact cache L = L_e / (1 - rho): at each of
+    the vertices 2 and 3 the cache samples give beta rho L and the
+    continuation subtracts beta' n = beta' L while the path adds beta' L_e
+    at the next vertex, so with at most two path segments after the shading
+    point (no uncached tail) every pixel is L exactly, whatever Russian
+    roulette decides (the continuation's 1/q is in beta')."""
+    rho = float(np.float32(0.6))
+    Le = 1.0
+    L = Le / (1 - rho)
+    sc = scenes.furnace_scene(32, 32, rho=rho, emission=Le)
+    fd = oracle.oframe(32, 32, N1, M, D, 1, 3, cache_mode=2, cache_const=(L, L, L), estimator=2, n_cache2=N2,
+                       n_cache3=N3)
+    r = oracle.estimate(scenes.config_small(), None, sc.blob(), fd)
+    assert np.allclose(r["pixel"], L, rtol=1e-12, atol=0), np.abs(r["pixel"] - L).max()
+    # the same frame with the two-level estimator is not exact (its residual
+    # path is truncated without the later cache terms)
+    fd0 = oracle.oframe(32, 32, N1, M, D, 1, 3, cache_mode=2, cache_const=(L, L, L))
+    assert np.abs(oracle.estimate(scenes.config_small(), None, sc.blob(), fd0)["pixel"] - L).max() > 0.1
+
+
+def test_multivertex_zero_cache_is_two_level(oracle):
+    """n = 0: the later-vertex terms vanish and the estimate is the
+    two-level one, pixel for pixel, decisions included."""
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(24, 24, seed=5, n_prims=32, glossy=True)
+    a = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(24, 24, 4, 2, 5, 1, 2, cache_mode=1))
+    b = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(24, 24, 4, 2, 5, 1, 2, cache_mode=1, estimator=2,
+                                                             n_cache2=5, n_cache3=3))
+    assert np.array_equal(a["pixel"], b["pixel"]) and np.array_equal(a["sig"], b["sig"])
+
+
+@pytest.mark.parametrize("light_mode", [0, 1])
+def test_multivertex_correction_has_zero_mean(oracle, light_mode):
+    """For any cache (here an untrained network) the later-vertex terms
+    beta_k C_k - beta_{k+1} n(x_k, w_k) have mean zero: on the same residual
+    paths (same seeds) the estimates with and without them differ by a
+    zero-mean quantity (paired test over pixels and frames)."""
+    cfg = scenes.config_small()
+    params = scenes.init_params(cfg, 8)
+    params[:cfg.n_mlp_params] += np.random.default_rng(8).normal(0, 0.05, cfg.n_mlp_params).astype(np.float32)
+    sc = scenes.cornell_scene(24, 24, seed=6, n_prims=8, glossy=True)
+    diffs = []
+    for frame in range(6):
+        kw = dict(light_mode=light_mode)
+        a = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(24, 24, 2, 1, 6, frame, 4, **kw))
+        b = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(24, 24, 2, 1, 6, frame, 4, estimator=2,
+                                                                  n_cache2=2, n_cache3=2, **kw))
+        assert np.array_equal(a["sig"], b["sig"])
+        diffs.append((b["pixel"] - a["pixel"]).ravel())
+    d = np.concatenate(diffs)
+    se = d.std() / math.sqrt(d.size)
+    assert se > 0 and np.abs(d).max() > 10 * se  # the terms are there
+    assert abs(d.mean()) < 4 * se, (d.mean(), se)
