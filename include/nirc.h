@@ -162,12 +162,28 @@ typedef struct nirc_frame_desc {
                                 training targets carry L_ind.  Spherical
                                 emitters are reached by BSDF sampling only. */
     uint32_t estimator;      /* nirc_estimator */
+    uint32_t n_cache2;       /* NIRC_EST_MULTI_VERTEX: cache samples at the */
+    uint32_t n_cache3;       /* second and third vertex (0..1024) */
     uint32_t reserved;       /* 0 */
 } nirc_frame_desc;
 
 /* Estimator of nirc_frame_desc.estimator.
  * NIRC_EST_TWO_LEVEL: eq. L_mlmc at the first camera hit (N cache samples,
- *   M residual paths): unbiased.
+ *   M residual paths): unbiased.  With N = 0 there is no cache level and no
+ *   cache value is subtracted (plain path tracing).
+ * NIRC_EST_MULTI_VERTEX: the paper's unbiased variant ("Biased and unbiased
+ *   variants": NIRC at the first three vertices, the neural samples
+ *   redistributed between them): the same at the shading point x_1, and
+ *   along each residual path at its vertices x_2 and x_3 the path's
+ *   incident-radiance estimate gains beta_k C_k - beta_{k+1} n(x_k, w_k):
+ *   C_k = 1/N_k sum_i (f cos / p)_i n(x_k, w_i) over N_k = n_cache2 /
+ *   n_cache3 BSDF-sampled directions (Philox purpose 10 + 16 k, counter
+ *   (pixel, j << 16 | i) for residual path j), minus the cache value of the
+ *   path's continuation direction w_k (only when it continues; beta_{k+1}
+ *   includes the continuation weight and Russian roulette), beta_k the
+ *   path's throughput to x_k times w_j / M.  Zero mean for any cache;
+ *   vertices with N_k = 0 use no cache.  The terms count in lr; count,
+ *   sig[1] and row_n describe x_1's cache samples.
  * NIRC_EST_BIASED_BTH: the paper's biased variant (section "Path
  *   Termination Heuristics", paragraph "Biased and unbiased variants"): the
  *   camera path continues from vertex x_i with its BSDF-sampled direction
@@ -185,7 +201,8 @@ typedef struct nirc_frame_desc {
  *   x cache level at the stopping vertex, lr = 0. */
 typedef enum nirc_estimator {
     NIRC_EST_TWO_LEVEL = 0,
-    NIRC_EST_BIASED_BTH = 1
+    NIRC_EST_BIASED_BTH = 1,
+    NIRC_EST_MULTI_VERTEX = 2
 } nirc_estimator;
 
 #define NIRC_MAX_PRIMS 1024u

@@ -23,6 +23,7 @@ constexpr int kSimtThreads = 128;
 
 struct CacheArgs {
     uint32_t W, H, N, M, k0, k1;
+    uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
     uint32_t cache_mode;
     float cc0, cc1, cc2;
     float z_clamp;
@@ -121,7 +122,8 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
             if (r < a.N) {
                 BsdfSample bs;
                 if (valid) {
-                    bs = sample_bsdf(n, wo, alb, rough, mat, a.k0, a.k1, pix, r, PURPOSE_CACHE_DIR);
+                    bs = sample_bsdf(n, wo, alb, rough, mat, a.k0, a.k1, pix / a.unit_div,
+                                     ((pix % a.unit_div) << 16) | r, a.purpose);
                     sig = sig_mix(sig, bs.word);
                 } else {
                     bs.valid = false;
@@ -160,21 +162,27 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
             }
         }
         if (!in_range) continue;
-        const PixelBase b = base[pix];
+        PixelBase b;
+        if (base) {
+            b = base[pix];
+        } else {
+            b.le = b.wl = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         float3 Lc = make_float3(0.f, 0.f, 0.f), Lr = make_float3(b.wl.x, b.wl.y, b.wl.z);
         if (a.N) {
             const float inv = 1.0f / (float)a.N;
             Lc = make_float3(lc.s.x * inv, lc.s.y * inv, lc.s.z * inv);
-            if (beta) {  // biased estimator: the cache level at the stopping vertex times the path throughput
-                const float4 bt = beta[pix];
-                Lc = make_float3(Lc.x * bt.x, Lc.y * bt.y, Lc.z * bt.z);
-            }
         }
-        if (a.M) {
+        if (a.M && a.N) {  // without a cache level nothing is subtracted
             const float inv = 1.0f / (float)a.M;
             Lr.x -= sub.s.x * inv;
             Lr.y -= sub.s.y * inv;
             Lr.z -= sub.s.z * inv;
+        }
+        if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
+            const float4 bt = beta[pix];
+            Lc = make_float3(Lc.x * bt.x, Lc.y * bt.y, Lc.z * bt.z);
+            Lr = make_float3(Lr.x * bt.x, Lr.y * bt.y, Lr.z * bt.z);
         }
         out[pix] = make_float4(b.le.x + Lc.x + Lr.x, b.le.y + Lc.y + Lr.y, b.le.z + Lc.z + Lr.z, 1.f);
         if (lc_out) {
@@ -264,8 +272,11 @@ static size_t simt_smem(const NetShape& s) {
 
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                               const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
-                              float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st) {
+                              float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st,
+                              CachePass pass) {
     CacheArgs a;
+    a.unit_div = pass.unit_div;
+    a.purpose = pass.purpose;
     a.W = fd.width;
     a.H = fd.height;
     a.N = fd.n_cache;

@@ -160,6 +160,7 @@ __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_
 
 struct TcArgs {
     uint32_t W, H, N, M, k0, k1;
+    uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
     uint32_t S, P, n_blocks;
     float z_clamp;
     uint32_t img_bytes;
@@ -561,7 +562,8 @@ __global__ void __launch_bounds__(640, 1)
                     if (s < a.N) {
                         const BsdfSample bs =
                             sample_bsdf(V3{q0.w, q1.x, q1.y}, V3{q1.z, q1.w, q2.x}, make_float3(q2.y, q2.z, q2.w),
-                                        q3.x, (flags >> 1) & 3u, a.k0, a.k1, p0 + pl, s, PURPOSE_CACHE_DIR);
+                                        q3.x, (flags >> 1) & 3u, a.k0, a.k1, (p0 + pl) / a.unit_div,
+                                        (((p0 + pl) % a.unit_div) << 16) | s, a.purpose);
                         wi = bs.wi;
                         w = bs.w;
                         ok = bs.valid;
@@ -744,23 +746,31 @@ __global__ void __launch_bounds__(640, 1)
                     if (sig_out) s_sigc[(jt + 1u) & 1u] = sig;
                 } else {
                     const uint32_t gp = p0 + q;
-                    const PixelBase b = base[gp];
+                    PixelBase b;
+                    if (base) {
+                        b = base[gp];
+                    } else {
+                        b.le = b.wl = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                     float Lc[3] = {0.f, 0.f, 0.f}, Lr[3] = {b.wl.x, b.wl.y, b.wl.z};
                     if (a.N) {
                         const float inv = 1.0f / (float)a.N;
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc) Lc[cc] = acc[cc] * inv;
-                        if (beta) {  // biased estimator: times the path throughput to the stopping vertex
-                            const float4 bt = beta[gp];
-                            Lc[0] *= bt.x;
-                            Lc[1] *= bt.y;
-                            Lc[2] *= bt.z;
-                        }
                     }
-                    if (a.M) {
+                    if (a.M && a.N) {  // without a cache level nothing is subtracted
                         const float inv = 1.0f / (float)a.M;
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc) Lr[cc] -= acc[3 + cc] * inv;
+                    }
+                    if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
+                        const float4 bt = beta[gp];
+                        const float bb[3] = {bt.x, bt.y, bt.z};
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            Lc[cc] *= bb[cc];
+                            Lr[cc] *= bb[cc];
+                        }
                     }
                     out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
                     if (lc_out) {
@@ -852,8 +862,10 @@ static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t sm
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
-                            cudaStream_t st) {
+                            cudaStream_t st, CachePass pass) {
     TcArgs a;
+    a.unit_div = pass.unit_div;
+    a.purpose = pass.purpose;
     a.W = fd.width;
     a.H = fd.height;
     a.N = fd.n_cache;

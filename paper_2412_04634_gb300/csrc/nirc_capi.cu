@@ -170,10 +170,19 @@ void timer_end(const nirc_handle* hc, int cls, cudaStream_t st) {
 
 static size_t round256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
+// Later-vertex data of the multi-vertex estimator, per residual path (unit)
+// and vertex: record, throughput, continuation row; and per unit the two
+// vertex passes' outputs.
+static size_t mv_bytes(uint64_t PM) {
+    return round256(2 * PM * sizeof(nirc_record)) + round256(2 * PM * sizeof(float4)) +
+           round256(2 * PM * sizeof(ResidRow)) + 2 * round256(PM * sizeof(float4));
+}
+
 size_t frame_scratch_bytes(uint64_t P, uint32_t M, uint32_t estimator) {
-    // records | per-pixel bases | residual rows (two-level) or path throughputs (biased)
+    // records | per-pixel bases | residual rows (two-level) or path throughputs (biased) | later vertices
     const size_t third = estimator == NIRC_EST_BIASED_BTH ? P * sizeof(float4) : P * M * sizeof(ResidRow);
-    return round256(P * sizeof(nirc_record)) + round256(P * sizeof(PixelBase)) + round256(third);
+    return round256(P * sizeof(nirc_record)) + round256(P * sizeof(PixelBase)) + round256(third) +
+           (estimator == NIRC_EST_MULTI_VERTEX ? mv_bytes(P * M) : 0);
 }
 
 nirc_status check_frame_args(const char* who, const void* scene, const nirc_frame_desc& fd, const float* out,
@@ -185,9 +194,11 @@ nirc_status check_frame_args(const char* who, const void* scene, const nirc_fram
     }
     if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
         fd.max_depth > 64 || fd.cache_mode > 2 || fd.light_mode > 1 || P > 0xFFFFFFFFull ||
-        fd.estimator > NIRC_EST_BIASED_BTH || (fd.estimator == NIRC_EST_BIASED_BTH && fd.n_resid != 0)) {
-        set_error("%s: argument out of range (n_prims 1..%u, N <= 1024, M <= 64, depth 1..64, light_mode 0..1, "
-                  "estimator 0..1, M = 0 for the biased estimator)",
+        fd.estimator > NIRC_EST_MULTI_VERTEX || (fd.estimator == NIRC_EST_BIASED_BTH && fd.n_resid != 0) ||
+        (fd.estimator == NIRC_EST_MULTI_VERTEX &&
+         (fd.n_cache2 > 1024 || fd.n_cache3 > 1024 || P * fd.n_resid > 0xFFFFFFFFull))) {
+        set_error("%s: argument out of range (n_prims 1..%u, N, N2, N3 <= 1024, M <= 64, depth 1..64, "
+                  "light_mode 0..1, estimator 0..2, M = 0 for the biased estimator)",
                   who, NIRC_MAX_PRIMS);
         return NIRC_ERR_INVALID;
     }
@@ -215,9 +226,26 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
     float4* beta = biased ? reinterpret_cast<float4*>(sp + rec_bytes + base_bytes) : nullptr;
     uint64_t* sig = aux ? aux->sig : nullptr;
     uint32_t* count = aux ? aux->count : nullptr;
+    // multi-vertex estimator: later-vertex data after the residual rows
+    const bool multi = fd.estimator == NIRC_EST_MULTI_VERTEX && fd.n_resid > 0 && (fd.n_cache2 || fd.n_cache3);
+    const uint64_t PM = P * fd.n_resid;
+    nirc_record* mv_rec = nullptr;
+    float4 *mv_beta = nullptr, *mv_out = nullptr;
+    ResidRow* mv_row = nullptr;
+    if (multi) {
+        char* q = sp + rec_bytes + base_bytes + round256(PM * sizeof(ResidRow));
+        mv_rec = reinterpret_cast<nirc_record*>(q);
+        q += round256(2 * PM * sizeof(nirc_record));
+        mv_beta = reinterpret_cast<float4*>(q);
+        q += round256(2 * PM * sizeof(float4));
+        mv_row = reinterpret_cast<ResidRow*>(q);
+        q += round256(2 * PM * sizeof(ResidRow));
+        mv_out = reinterpret_cast<float4*>(q);  // [2][PM], each part round256
+    }
     timer_begin(h, NIRC_K_PATH_TRACE, st);
     cudaError_t e = biased ? launch_primary_bth(h, scene, fd, recs, base, beta, sig, count, st)
-                           : launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st);
+                           : launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st, mv_rec, mv_beta,
+                                                  mv_row);
     timer_end(h, NIRC_K_PATH_TRACE, st);
     if (e != cudaSuccess) {
         set_error("%s (path tracing): %s", who, cudaGetErrorString(e));
@@ -232,8 +260,42 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
         e = launch_cache_simt(h, fd, recs, base, rows, beta, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
                               count, aux ? aux->row_n : nullptr, st);
     }
+    bool tc_any = tc;
+    if (multi && e == cudaSuccess) {
+        // vertices 2 and 3 of every residual path: one cache pass each over the
+        // P M units (N_k cache rows + the continuation row), then the sums
+        const size_t part = round256(PM * sizeof(float4)) / sizeof(float4);
+        float4* outs[2] = {nullptr, nullptr};
+        for (uint32_t k = 2; k <= 3 && e == cudaSuccess; ++k) {
+            const uint32_t nk = k == 2 ? fd.n_cache2 : fd.n_cache3;
+            if (!nk) continue;
+            nirc_frame_desc dk = fd;
+            dk.width = (uint32_t)PM;
+            dk.height = 1;
+            dk.n_cache = nk;
+            dk.n_resid = 1;
+            dk.estimator = NIRC_EST_TWO_LEVEL;
+            const uint64_t off = (uint64_t)(k - 2) * PM;
+            float4* ok = mv_out + (k - 2) * part;
+            const CachePass pass{fd.n_resid, PURPOSE_VCACHE + 16u * k};
+            const bool tck = tc_supported(h, dk);
+            tc_any = tc_any || tck;
+            if (tck)
+                e = launch_cache_tc(h, dk, mv_rec + off, nullptr, mv_row + off, mv_beta + off,
+                                    reinterpret_cast<float*>(ok), nullptr, nullptr, nullptr, nullptr, nullptr,
+                                    h->dev_err, st, pass);
+            else
+                e = launch_cache_simt(h, dk, mv_rec + off, nullptr, mv_row + off, mv_beta + off,
+                                      reinterpret_cast<float*>(ok), nullptr, nullptr, nullptr, nullptr, nullptr, st,
+                                      pass);
+            outs[k - 2] = ok;
+        }
+        if (e == cudaSuccess)
+            e = launch_mv_accumulate(out, aux ? aux->lr : nullptr, outs[0], outs[1], P, fd.n_resid, st);
+    }
     timer_end(h, NIRC_K_CACHE, st);
-    if (e == cudaSuccess && tc) e = cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && tc_any)
+        e = cudaMemcpyAsync(h->host_err, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) {
         set_error("%s (cache integral): %s", who, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? NIRC_ERR_OOM : NIRC_ERR_CUDA;

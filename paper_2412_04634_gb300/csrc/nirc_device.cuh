@@ -72,7 +72,8 @@ enum : uint32_t {
     PURPOSE_TRAIN_PICK = 6,
     PURPOSE_LIGHT = 7,   // + 16 * segment (0: the shading point), light mode 1
     PURPOSE_BTH_DIR = 8, // + 16 * vertex: biased estimator, direction sampled at a camera-path vertex
-    PURPOSE_BTH_XI = 9   // + 16 * vertex: biased estimator, the termination test's uniform
+    PURPOSE_BTH_XI = 9,  // + 16 * vertex: biased estimator, the termination test's uniform
+    PURPOSE_VCACHE = 10  // + 16 * vertex (2, 3): multi-vertex estimator, cache samples along a residual path
 };
 
 constexpr float kTMin = 1e-4f;

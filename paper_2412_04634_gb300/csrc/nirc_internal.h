@@ -119,9 +119,15 @@ NetShape make_shape(const nirc_config& cfg);
 GridParams make_grid(const nirc_config& cfg);
 
 // nirc_pt.cu
+// mv_* (multi-vertex estimator, else NULL): [2][W H M] records, throughputs and continuation rows
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig,
-                                 uint32_t* count, cudaStream_t st);
+                                 uint32_t* count, cudaStream_t st, nirc_record* mv_rec = nullptr,
+                                 float4* mv_beta = nullptr, ResidRow* mv_row = nullptr);
+// Multi-vertex estimator: out (RGBA) and lr (RGB, may be NULL) of pixel p gain
+// sum over j of o2[p M + j] + o3[p M + j] (either may be NULL).
+cudaError_t launch_mv_accumulate(float* out_rgba, float* lr, const float4* o2, const float4* o3, uint64_t P,
+                                 uint32_t M, cudaStream_t st);
 cudaError_t launch_primary_bth(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd, nirc_record* recs,
                                PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st);
 cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
@@ -129,10 +135,21 @@ cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n
                              nirc_record* recs, float* dirs, float* targets, cudaStream_t st);
 
 // nirc_cache_simt.cu
-// beta (biased estimator, else NULL): per-pixel path throughput applied to the cache level
+// Which cache samples a launch of the cache integral draws: unit u's row i
+// takes Philox counter (u / unit_div, ((u % unit_div) << 16) | i) and
+// purpose `purpose`.  The shading-point pass: {1, PURPOSE_CACHE_DIR}; the
+// later-vertex passes of the multi-vertex estimator: {M, PURPOSE_VCACHE + 16 k}.
+struct CachePass {
+    uint32_t unit_div = 1;
+    uint32_t purpose = PURPOSE_CACHE_DIR;
+};
+
+// beta (biased and multi-vertex estimators, else NULL): per-unit throughput
+// applied to both levels; base NULL: zero emission and path-traced part.
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                               const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
-                              float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st);
+                              float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st,
+                              CachePass pass = CachePass{});
 cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, const float* dirs, uint64_t n,
                               float* out, cudaStream_t st);
 cudaError_t launch_repack_simt(const nirc_handle* h, cudaStream_t st);
@@ -144,7 +161,7 @@ bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd);
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
-                            cudaStream_t st);
+                            cudaStream_t st, CachePass pass = CachePass{});
 
 // nirc_train.cu
 size_t train_scratch_bytes(const nirc_handle* h, uint64_t n);

@@ -1,4 +1,6 @@
-// nirc_metrics.cu -- frame metric: mean relative squared error (paper:
+// nirc_metrics.cu -- per-pixel frame reductions: the later-vertex sums of
+// the multi-vertex estimator (k_mv_accumulate), and the frame metric: mean
+// relative squared error (paper:
 // MRSE, used for every equal-time comparison), mean over pixels and RGB of
 // (I - R)^2 / (R^2 + eps).  Each term is formed in binary32 (IEEE divide;
 // at most four roundings, ~2.4e-7 relative) and the frame-level sum is
@@ -33,6 +35,49 @@ __global__ void __launch_bounds__(kMrseThreads) k_mrse(const float4* __restrict_
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (threadIdx.x == 0) atomicAdd(out, v * scale);
     }
+}
+
+// Multi-vertex estimator: pixel p gains the later-vertex terms of its M
+// residual paths (units p M .. p M + M - 1), added in unit order.
+__global__ void k_mv_accumulate(float4* __restrict__ out, float* __restrict__ lr, const float4* __restrict__ o2,
+                                const float4* __restrict__ o3, uint64_t P, uint32_t M) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (uint64_t)gridDim.x * blockDim.x) {
+        float3 a = make_float3(0.f, 0.f, 0.f);
+        for (uint32_t j = 0; j < M; ++j) {
+            const uint64_t u = p * M + j;
+            if (o2) {
+                const float4 v = o2[u];
+                a.x += v.x;
+                a.y += v.y;
+                a.z += v.z;
+            }
+            if (o3) {
+                const float4 v = o3[u];
+                a.x += v.x;
+                a.y += v.y;
+                a.z += v.z;
+            }
+        }
+        float4 o = out[p];
+        out[p] = make_float4(o.x + a.x, o.y + a.y, o.z + a.z, o.w);
+        if (lr) {
+            lr[3 * p] += a.x;
+            lr[3 * p + 1] += a.y;
+            lr[3 * p + 2] += a.z;
+        }
+    }
+}
+
+cudaError_t launch_mv_accumulate(float* out_rgba, float* lr, const float4* o2, const float4* o3, uint64_t P,
+                                 uint32_t M, cudaStream_t st) {
+    if (P == 0 || (!o2 && !o3)) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint64_t blocks = (P + 255) / 256;
+    if (blocks > (uint64_t)sms * 8) blocks = (uint64_t)sms * 8;
+    k_mv_accumulate<<<(uint32_t)blocks, 256, 0, st>>>(reinterpret_cast<float4*>(out_rgba), lr, o2, o3, P, M);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_mrse(const float* img, const float* ref, uint64_t n, float eps, double* out, cudaStream_t st) {

@@ -13,6 +13,9 @@
 //
 // k_primary_bth: the biased estimator's camera path (Balanced Termination
 //   Heuristic), see below.
+// Multi-vertex estimator: k_primary_resid also hands the cache kernels the
+//   records, throughputs and continuation rows of each residual path's
+//   second and third vertex (MvOut).
 //
 // The kernels are persistent: each CTA stages the primitives' geometry in
 // shared memory and, for scenes of more than 16 primitives, builds its own
@@ -44,6 +47,17 @@ struct FrameArgs {
 struct Lights {
     const uint16_t* idx;
     uint32_t n;
+};
+
+// Multi-vertex estimator: per residual path (unit u = pixel * M + j) the
+// record of its vertices 2 and 3 ([k - 2][P M]), the throughput to each
+// (w_j / M included) and the continuation row (direction, weight w / q
+// relative to that throughput; w = 0 in .wi when the path stops there).
+struct MvOut {
+    nirc_record* rec;
+    float4* beta;
+    ResidRow* row;
+    uint64_t PM;
 };
 
 // Nearest-hit queries over the CTA's primitives (brute force or hierarchy).
@@ -161,6 +175,42 @@ __device__ __forceinline__ uint32_t nee_sample(const Tracer& tr, const Prim* __r
     return word;
 }
 
+__device__ __forceinline__ void write_record(nirc_record* dst, const Hit& h, V3 d, const Prim* P, uint32_t prim,
+                                             uint32_t flags) {
+    float4* q = reinterpret_cast<float4*>(dst);
+    q[0] = make_float4(h.p.x, h.p.y, h.p.z, h.n.x);
+    q[1] = make_float4(h.n.y, h.n.z, -d.x, -d.y);
+    q[2] = make_float4(-d.z, __ldg(&P->albedo[0]), __ldg(&P->albedo[1]), __ldg(&P->albedo[2]));
+    q[3] = make_float4(__ldg(&P->roughness), __uint_as_float(prim), __uint_as_float(flags), 0.f);
+}
+
+// Vertex k = seg + 1 (seg 1, 2) of a residual path: its record and throughput;
+// the continuation row is invalid until mv_continue_row sets it.
+__device__ __forceinline__ void mv_vertex(const MvOut* mv, uint32_t seg, uint64_t unit, const Hit& h, V3 d,
+                                          const Prim* Q, uint32_t prim, uint32_t flags, float3 pre, float3 beta) {
+    const uint64_t slot = (uint64_t)(seg - 1) * mv->PM + unit;
+    write_record(mv->rec + slot, h, d, Q, prim, 1u | ((flags & 3u) << 1));
+    mv->beta[slot] = make_float4(pre.x * beta.x, pre.y * beta.y, pre.z * beta.z, 0.f);
+    mv->row[slot].wi = make_float4(0.f, 0.f, 1.f, 0.f);
+    mv->row[slot].w = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void mv_continue_row(const MvOut* mv, uint32_t seg, uint64_t unit, V3 wi, float3 w) {
+    const uint64_t slot = (uint64_t)(seg - 1) * mv->PM + unit;
+    mv->row[slot].wi = make_float4(wi.x, wi.y, wi.z, 1.f);
+    mv->row[slot].w = make_float4(w.x / kRRContinue, w.y / kRRContinue, w.z / kRRContinue, 0.f);
+}
+// Both later vertices of a unit not reached (yet): zero records (flags 0).
+__device__ __forceinline__ void mv_clear(const MvOut* mv, uint64_t unit) {
+    for (uint32_t k = 0; k < 2; ++k) {
+        const uint64_t slot = (uint64_t)k * mv->PM + unit;
+        float4* q = reinterpret_cast<float4*>(mv->rec + slot);
+        q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mv->beta[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mv->row[slot].wi = make_float4(0.f, 0.f, 1.f, 0.f);
+        mv->row[slot].w = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // One segment of an L_ind path (light mode 1) after its ray was traced:
 // emission found by the continuation (MIS weighted; the first hit's goes to
 // first_emit, weighted against nb0 BSDF samples of density pb at the
@@ -170,7 +220,7 @@ __device__ __forceinline__ bool path_segment_nee(const Tracer& tr, const Prim* _
                                                  int prim, float t, V3& o, V3& d, float3& beta, float3& L,
                                                  uint32_t& seg, uint32_t max_depth, uint32_t k0, uint32_t k1,
                                                  uint32_t c0, uint32_t c1, uint64_t& sig, float& pb, uint32_t nb0,
-                                                 float3& first_emit) {
+                                                 float3& first_emit, const MvOut* mv, uint64_t unit, float3 pre) {
     sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
     if (prim < 0) return true;
     const Hit h = hit_info(tr.prims[prim], o, d, t);
@@ -200,6 +250,8 @@ __device__ __forceinline__ bool path_segment_nee(const Tracer& tr, const Prim* _
     L.x += beta.x * dl.x;
     L.y += beta.y * dl.y;
     L.z += beta.z * dl.z;
+    const bool mv_here = mv && seg <= 2u;
+    if (mv_here) mv_vertex(mv, seg, unit, h, d, Q, (uint32_t)prim, flags, pre, beta);
     if (seg == max_depth) return true;
     const U4 r = philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg);
     const bool cont = u01(r.x) < kRRContinue;
@@ -214,6 +266,7 @@ __device__ __forceinline__ bool path_segment_nee(const Tracer& tr, const Prim* _
     beta.x *= s.w.x;
     beta.y *= s.w.y;
     beta.z *= s.w.z;
+    if (mv_here) mv_continue_row(mv, seg, unit, s.wi, s.w);
     pb = bsdf_eval(h.n, wo, s.wi, alb, rough, flags & 3u).pdf;
     o = h.p;
     d = s.wi;
@@ -227,7 +280,9 @@ __device__ __forceinline__ bool path_segment_nee(const Tracer& tr, const Prim* _
 // true when the path ends; otherwise (o, d) is the next ray and seg + 1.
 __device__ __forceinline__ bool path_segment(const Tracer& tr, const Prim* __restrict__ gp, int prim, float t, V3& o,
                                              V3& d, float3& beta, float3& L, uint32_t& seg, uint32_t max_depth,
-                                             uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint64_t& sig) {
+                                             uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1, uint64_t& sig,
+                                             const MvOut* mv = nullptr, uint64_t unit = 0,
+                                             float3 pre = make_float3(0.f, 0.f, 0.f)) {
     sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
     if (prim < 0) return true;
     const Hit h = hit_info(tr.prims[prim], o, d, t);
@@ -238,6 +293,8 @@ __device__ __forceinline__ bool path_segment(const Tracer& tr, const Prim* __res
         L.y += beta.y * __ldg(&Q->emission[1]);
         L.z += beta.z * __ldg(&Q->emission[2]);
     }
+    const bool mv_here = mv && seg <= 2u;
+    if (mv_here) mv_vertex(mv, seg, unit, h, d, Q, (uint32_t)prim, flags, pre, beta);
     if (seg == max_depth) return true;
     const U4 r = philox(k0, k1, c0, c1, 0u, PURPOSE_RR + 16u * seg);
     const bool cont = u01(r.x) < kRRContinue;
@@ -254,6 +311,7 @@ __device__ __forceinline__ bool path_segment(const Tracer& tr, const Prim* __res
     beta.x *= s.w.x;
     beta.y *= s.w.y;
     beta.z *= s.w.z;
+    if (mv_here) mv_continue_row(mv, seg, unit, s.wi, s.w);
     o = h.p;
     d = s.wi;
     ++seg;
@@ -273,15 +331,6 @@ __device__ __forceinline__ uint64_t fetch_work(unsigned long long* work, bool ne
     return first + (uint64_t)__popc(needm & ((1u << lane) - 1u));
 }
 
-__device__ __forceinline__ void write_record(nirc_record* dst, const Hit& h, V3 d, const Prim* P, uint32_t prim,
-                                             uint32_t flags) {
-    float4* q = reinterpret_cast<float4*>(dst);
-    q[0] = make_float4(h.p.x, h.p.y, h.p.z, h.n.x);
-    q[1] = make_float4(h.n.y, h.n.z, -d.x, -d.y);
-    q[2] = make_float4(-d.z, __ldg(&P->albedo[0]), __ldg(&P->albedo[1]), __ldg(&P->albedo[2]));
-    q[3] = make_float4(__ldg(&P->roughness), __uint_as_float(prim), __uint_as_float(flags), 0.f);
-}
-
 // Lane state of k_primary_resid: which pixel, which ray is in flight.
 enum : uint32_t { kNeedPixel = 0, kCameraRay = 1, kResidRay = 2, kNoMoreWork = 3 };
 
@@ -299,7 +348,8 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
                                                               ResidRow* __restrict__ rows,
                                                               uint64_t* __restrict__ sig_out,
                                                               uint32_t* __restrict__ count,
-                                                              unsigned long long* __restrict__ work) {
+                                                              unsigned long long* __restrict__ work,
+                                                              MvOut mvo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
     __shared__ uint32_t s_nlights;
@@ -308,6 +358,8 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
     if constexpr (kNee)
         lt = collect_lights(gp, a.n_prims, reinterpret_cast<uint16_t*>(smem_raw + pt_geom_bytes(a.n_prims)),
                             &s_nlights);
+    const MvOut* mv = mvo.rec ? &mvo : nullptr;  // multi-vertex estimator: later-vertex data per residual path
+    const float invM = a.M ? 1.0f / (float)a.M : 0.f;
 
     const uint64_t P = (uint64_t)a.W * a.H;
     uint32_t stage = kNeedPixel;
@@ -326,6 +378,7 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
     auto next_residual = [&]() -> uint32_t {
         ResidRow* my_rows = rows + (uint64_t)pix * a.M;
         for (; j < a.M; ++j) {
+            if (mv) mv_clear(mv, (uint64_t)pix * a.M + j);
             const BsdfSample s = sample_bsdf(sn, swo, salb, srough, smat, a.k0, a.k1, pix, j, PURPOSE_RESID_DIR);
             sig = sig_mix(sig, s.word);
             my_rows[j].wi = make_float4(s.wi.x, s.wi.y, s.wi.z, s.valid ? 1.f : 0.f);
@@ -389,6 +442,7 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
                 for (uint32_t jj = 0; jj < a.M; ++jj) {
                     my_rows[jj].wi = make_float4(0.f, 0.f, 1.f, 0.f);
                     my_rows[jj].w = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (mv) mv_clear(mv, (uint64_t)pix * a.M + jj);
                 }
                 if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
                 if (count) count[pix] = 0;
@@ -421,9 +475,11 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
             bool end;
             if constexpr (kNee)
                 end = path_segment_nee(tr, gp, lt, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig, pb, a.M,
-                                       first_emit);
+                                       first_emit, mv, (uint64_t)pix * a.M + j,
+                                       make_float3(sw.x * invM, sw.y * invM, sw.z * invM));
             else
-                end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig);
+                end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig, mv,
+                                   (uint64_t)pix * a.M + j, make_float3(sw.x * invM, sw.y * invM, sw.z * invM));
             if (end) {
                 if constexpr (kNee) {
                     const float inv = 1.0f / (float)a.M;
@@ -697,7 +753,7 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_gen_train(const SceneHeader* 
             bool end;
             if constexpr (kNee)  // target = L_ind: the first hit's emission is direct light (discarded)
                 end = path_segment_nee(tr, gp, lt, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig, pb, 0u,
-                                       first_emit);
+                                       first_emit, nullptr, 0, make_float3(0.f, 0.f, 0.f));
             else
                 end = path_segment(tr, gp, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig);
             if (end) {
@@ -734,27 +790,30 @@ static cudaError_t persistent_grid(K kernel, size_t smem, uint64_t work, int num
 template <bool kNee>
 static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeader* hd, const Prim* gp,
                                           const FrameArgs& a, uint64_t P, nirc_record* recs, PixelBase* base,
-                                          ResidRow* rows, uint64_t* sig, uint32_t* count, cudaStream_t st) {
+                                          ResidRow* rows, uint64_t* sig, uint32_t* count, const MvOut& mv,
+                                          cudaStream_t st) {
     const size_t smem = pt_smem(a.n_prims);
     uint32_t grid = 1;
     cudaError_t e = persistent_grid(k_primary_resid<kNee>, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_primary_resid<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter);
+    k_primary_resid<kNee>
+        <<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
     return cudaGetLastError();
 }
 
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig, uint32_t* count,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, nirc_record* mv_rec, float4* mv_beta, ResidRow* mv_row) {
     FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
     const uint64_t P = (uint64_t)fd.width * fd.height;
+    const MvOut mv{mv_rec, mv_beta, mv_row, P * fd.n_resid};
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
     if (fd.light_mode == 1)
-        return launch_primary_resid_t<true>(h, hd, gp, a, P, recs, base, rows, sig, count, st);
-    return launch_primary_resid_t<false>(h, hd, gp, a, P, recs, base, rows, sig, count, st);
+        return launch_primary_resid_t<true>(h, hd, gp, a, P, recs, base, rows, sig, count, mv, st);
+    return launch_primary_resid_t<false>(h, hd, gp, a, P, recs, base, rows, sig, count, mv, st);
 }
 
 template <bool kNee>

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libnirc.so")
 NIRC_OK, NIRC_ERR_INVALID, NIRC_ERR_OOM, NIRC_ERR_BUDGET, NIRC_ERR_CUDA, NIRC_ERR_TIMEOUT, NIRC_ERR_UNSUPPORTED = range(7)
 NIRC_FP32_SIMT, NIRC_FP16_TC, NIRC_BF16_TC, NIRC_FP8_E4M3_TC = range(4)
 NIRC_INPUT_FREQ, NIRC_INPUT_SH = range(2)
-NIRC_EST_TWO_LEVEL, NIRC_EST_BIASED_BTH = range(2)
+NIRC_EST_TWO_LEVEL, NIRC_EST_BIASED_BTH, NIRC_EST_MULTI_VERTEX = range(3)
 NIRC_MAX_PRIMS = 1024
 
 
@@ -51,7 +51,8 @@ class nirc_frame_desc(ctypes.Structure):
         ("max_depth", ctypes.c_uint32), ("frame", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("n_prims", ctypes.c_uint32),
         ("cache_mode", ctypes.c_uint32), ("cache_const", ctypes.c_float * 3),
-        ("light_mode", ctypes.c_uint32), ("estimator", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("light_mode", ctypes.c_uint32), ("estimator", ctypes.c_uint32), ("n_cache2", ctypes.c_uint32),
+        ("n_cache3", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
     ]
 
 
@@ -179,12 +180,14 @@ def make_config(cfg: scenes.NetConfig, precision: int = NIRC_FP32_SIMT) -> nirc_
 
 
 def frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode=0,
-               cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0) -> nirc_frame_desc:
+               cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0, n_cache2=0, n_cache3=0) -> nirc_frame_desc:
     d = nirc_frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode)
     for k in range(3):
         d.cache_const[k] = float(cache_const[k])
     d.light_mode = light_mode
     d.estimator = estimator
+    d.n_cache2 = n_cache2
+    d.n_cache3 = n_cache3
     return d
 
 
