@@ -46,11 +46,21 @@ def workload_name(args):
     name = WORKLOAD_SH if getattr(args, "input", "freq") == "sh" else WORKLOAD
     if getattr(args, "estimator", "two_level") == "bth":
         name += "; biased estimator (Balanced Termination Heuristic, N cache samples at the stopping vertex, M=0)"
+    elif getattr(args, "estimator", "two_level") == "mv":
+        name += (f"; two levels at the first three vertices (N_c = {args.n_cache} / {args.n_cache2} / "
+                 f"{args.n_cache3})")
     return name
 
 
 def estimator_code(args):
-    return 1 if getattr(args, "estimator", "two_level") == "bth" else 0
+    return {"two_level": 0, "bth": 1, "mv": 2}[getattr(args, "estimator", "two_level")]
+
+
+def later_vertex_samples(args):
+    """(N_c^2, N_c^3) of the multi-vertex estimator, else (0, 0)."""
+    if estimator_code(args) != 2:
+        return 0, 0
+    return args.n_cache2, args.n_cache3
 
 
 def parse_args():
@@ -80,9 +90,13 @@ def parse_args():
                     help="network input of the frame workload: frequency encodings of direction and normal with "
                          "the 16-level hash grid (default), or the paper's (12-level hash grid, spherical "
                          "harmonics, albedo / one-blob normal and roughness)")
-    ap.add_argument("--estimator", choices=["two_level", "bth"], default="two_level",
+    ap.add_argument("--estimator", choices=["two_level", "bth", "mv"], default="two_level",
                     help="two_level: eq. L_mlmc at the first hit (default); bth: the biased variant with the "
-                         "Balanced Termination Heuristic (N cache samples at the stopping vertex, M forced to 0)")
+                         "Balanced Termination Heuristic (N cache samples at the stopping vertex, M forced to 0); "
+                         "mv: the unbiased variant with the two levels also at the second and third vertex of "
+                         "each residual path (--n-cache2 / --n-cache3 cache samples there)")
+    ap.add_argument("--n-cache2", type=int, default=5)
+    ap.add_argument("--n-cache3", type=int, default=4)
     ap.add_argument("--light-mode", type=int, choices=[0, 1], default=0,
                     help="1: the cache carries L_ind, direct light by NEE + MIS (frame and serve workloads)")
     ap.add_argument("--serve-requests", type=int, default=256)
@@ -181,7 +195,11 @@ def build_workload(args, seed_offset=0):
 
 
 def rows_per_frame(args):
-    return args.width * args.height * (args.n_cache + args.n_resid)
+    """Cache queries per frame: N + M rows per pixel, and with the
+    multi-vertex estimator N_k + 1 rows per residual path at vertices 2, 3."""
+    n2, n3 = later_vertex_samples(args)
+    per = args.n_cache + args.n_resid + args.n_resid * ((n2 + 1 if n2 else 0) + (n3 + 1 if n3 else 0))
+    return args.width * args.height * per
 
 
 def flops_per_frame(cfg, args):
@@ -191,7 +209,9 @@ def flops_per_frame(cfg, args):
     per_row = 2 * (cfg.n_dir_features * 64 + (cfg.hidden_layers - 1) * 64 * 64 + 64 * 3)
     n_pix_features = cfg.n_pos_features + cfg.n_surface_features
     per_pixel = 2 * n_pix_features * 64
-    return rows_per_frame(args) * per_row + args.width * args.height * per_pixel, per_row, per_pixel
+    n2, n3 = later_vertex_samples(args)
+    units = args.width * args.height * (1 + args.n_resid * ((1 if n2 else 0) + (1 if n3 else 0)))
+    return rows_per_frame(args) * per_row + units * per_pixel, per_row, per_pixel
 
 
 def fp32_alu_peak_tflops(num_sms, sm_mhz):
@@ -259,8 +279,9 @@ class FrameRunner:
         N, a = self.N, self.args
         sc = self.scene_dev[f % 60] if scene is None else scene
         h = self.cache.h
+        n2, n3 = later_vertex_samples(a)
         d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
-                         light_mode=a.light_mode, estimator=estimator_code(a))
+                         light_mode=a.light_mode, estimator=estimator_code(a), n_cache2=n2, n_cache3=n3)
         N.nirc_estimate_frame(h, sc, d, self.img)
         N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs, self.dirs,
                          self.tgts, light_mode=a.light_mode)
@@ -486,8 +507,9 @@ def oracle_step(O, cfg, params64, m, v, blob, args, frame, pix, T_s, seed):
     """One bounded sample of the frame step on the oracle: the listed pixels'
     two-level estimates, T_s training paths, loss + gradient, Adam, MRSE."""
     W, H = args.width, args.height
+    n2, n3 = later_vertex_samples(args)
     fd = O.oframe(W, H, args.n_cache, args.n_resid, args.depth, frame, seed, light_mode=args.light_mode,
-                  estimator=estimator_code(args))
+                  estimator=estimator_code(args), n_cache2=n2, n_cache3=n3)
     est = O.estimate(cfg, params64, blob, fd, pixels=pix)
     recs, dirs, tg, _ = O.gen_train(blob, W, H, T_s, frame, seed, args.depth, scenes.RECORD_DTYPE,
                                     light_mode=args.light_mode)
@@ -521,7 +543,7 @@ def _calibrate(O, cfg, p64, m, v, frames, args, budget_s):
 
 def cpu_baseline(args, budget_s):
     O, cfg, p64, m, v, frames = _oracle_setup(args)
-    S = args.n_cache + args.n_resid
+    S = rows_per_frame(args) // (args.width * args.height)
     n, _ = _calibrate(O, cfg, p64, m, v, frames, args, budget_s)
     P = args.width * args.height
     n = min(P, int(n * 2))
@@ -542,7 +564,7 @@ def run_reference(args):
     if rank != 0:
         return
     O, cfg, p64, m, v, frames = _oracle_setup(args)
-    S = args.n_cache + args.n_resid
+    S = rows_per_frame(args) // (args.width * args.height)
     per_step_budget = max(0.5, 150.0 / (args.steps + args.warmup))
     n, dt = _calibrate(O, cfg, p64, m, v, frames, args, per_step_budget * 4)
     n = max(64, int(n * per_step_budget / max(dt, 1e-3)))
