@@ -846,7 +846,8 @@ typedef struct {
     const double* params;
     const o_frame* fd;
     uint32_t pix, j;
-    double L[3]; /* sum of the corrections along the path */
+    double L[3];    /* sum of the corrections along the path */
+    double Labs[3]; /* sum of their absolute values (the rounding scale of the sum) */
 } o_mv;
 
 static void cache_value(const o_cfg* c, const double* params, const o_frame* fd, const o_record* rec,
@@ -867,7 +868,10 @@ static void mv_vertex(o_mv* mv, const o_record* rec, uint32_t k, const double be
         cache_value(mv->c, mv->params, mv->fd, rec, s.wi, nv);
         for (int q = 0; q < 3; q++) C[q] += s.w[q] * nv[q];
     }
-    for (int q = 0; q < 3; q++) mv->L[q] += beta[q] * C[q] / (double)nk;
+    for (int q = 0; q < 3; q++) {
+        mv->L[q] += beta[q] * C[q] / (double)nk;
+        mv->Labs[q] += fabs(beta[q] * C[q] / (double)nk);
+    }
 }
 
 /* - beta_{k+1} n(x_k, w_k) for the continuation direction (vertices with N_k = 0
@@ -877,7 +881,10 @@ static void mv_continue(o_mv* mv, const o_record* rec, uint32_t k, const float w
     if ((k == 2 ? mv->fd->n_cache2 : mv->fd->n_cache3) == 0) return;
     double nv[3];
     cache_value(mv->c, mv->params, mv->fd, rec, wi, nv);
-    for (int q = 0; q < 3; q++) mv->L[q] -= beta_next[q] * nv[q];
+    for (int q = 0; q < 3; q++) {
+        mv->L[q] -= beta_next[q] * nv[q];
+        mv->Labs[q] += fabs(beta_next[q] * nv[q]);
+    }
 }
 
 /* Incident radiance along (o, d): emission at each vertex, BSDF-sampled
@@ -1161,8 +1168,11 @@ static void cache_value(const o_cfg* c, const double* params, const o_frame* fd,
 
 static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
                            const o_lights* lights, uint32_t pix, double out[3], double lc_out[3], double lr_out[3],
-                           uint64_t sig[2], uint32_t* count, double* row_n)
+                           uint64_t sig[2], uint32_t* count, double* row_n, double lr_abs[3])
 {
+    /* lr_abs (optional): the sum of the absolute values of the terms that
+     * make up L_r, the scale of its rounding error (the terms cancel) */
+    double Labs[3] = {0.0, 0.0, 0.0};
     /* row_n (optional): cache value of each of the N + M rows, 0 for rows
      * whose sample is invalid or whose pixel has no camera hit */
     if (row_n) memset(row_n, 0, 3 * sizeof(double) * (fd->n_cache + fd->n_resid));
@@ -1214,7 +1224,7 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             sp = sig_mix(sp, sample_word(&s));
             if (!s.valid) continue;
             double Li[3], nv[3];
-            o_mv mv = {c, params, fd, pix, j, {0.0, 0.0, 0.0}};
+            o_mv mv = {c, params, fd, pix, j, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
             o_mv* mvp = fd->estimator == 2 ? &mv : NULL;
             if (lights) {
                 double fc[3], pb, e1[3];
@@ -1228,13 +1238,22 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             cache_value(c, params, fd, &rec, s.wi, nv);
             /* with N = 0 there is no cache level, and nothing is subtracted */
             const double use = fd->n_cache ? 1.0 : 0.0;
-            for (int k = 0; k < 3; k++) Lr[k] += s.w[k] * (Li[k] - use * nv[k] + mv.L[k]);
+            for (int k = 0; k < 3; k++) {
+                Lr[k] += s.w[k] * (Li[k] - use * nv[k] + mv.L[k]);
+                Labs[k] += fabs(s.w[k]) * (fabs(Li[k]) + use * fabs(nv[k]) + mv.Labs[k]);
+            }
             if (row_n)
                 for (int k = 0; k < 3; k++) row_n[3 * (fd->n_cache + j) + k] = nv[k];
             active++;
         }
-        if (fd->n_resid) for (int k = 0; k < 3; k++) Lr[k] /= (double)fd->n_resid;
+        if (fd->n_resid)
+            for (int k = 0; k < 3; k++) {
+                Lr[k] /= (double)fd->n_resid;
+                Labs[k] /= (double)fd->n_resid;
+            }
     }
+    if (lr_abs)
+        for (int k = 0; k < 3; k++) lr_abs[k] = Labs[k];
     for (int k = 0; k < 3; k++) {
         out[k] = Le[k] + Lc[k] + Lr[k];
         if (lc_out) lc_out[k] = Lc[k];
@@ -1409,8 +1428,9 @@ static uint32_t bth_path(const uint8_t* blob, const o_frame* fd, const o_lights*
  * residual level. */
 static void estimate_pixel_bth(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
                                const o_lights* lights, uint32_t pix, double out[3], double lc_out[3],
-                               double lr_out[3], uint64_t sig[2], uint32_t* count, double* row_n)
+                               double lr_out[3], uint64_t sig[2], uint32_t* count, double* row_n, double lr_abs[3])
 {
+    if (lr_abs) lr_abs[0] = lr_abs[1] = lr_abs[2] = 0.0;
     if (row_n) memset(row_n, 0, 3 * sizeof(double) * fd->n_cache);
     uint32_t k0 = (uint32_t)fd->seed, k1 = fd->frame;
     uint64_t sp, sc = SIG_INIT;
@@ -1471,7 +1491,7 @@ float orc_sampler_pdf32(const o_record* rec, const float wi[3])
  * indexed by position in the list; optional outputs may be NULL. */
 void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* blob, const o_frame* fd,
                          const uint32_t* pixels, uint64_t n, double* out, double* lc, double* lr, uint64_t* sig,
-                         uint32_t* count, double* row_n)
+                         uint32_t* count, double* row_n, double* lr_abs)
 {
     const uint64_t S = (uint64_t)fd->n_cache + fd->n_resid;
     o_lights* lights = NULL;
@@ -1485,11 +1505,11 @@ void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* bl
         if (fd->estimator == 1)
             estimate_pixel_bth(c, params, blob, fd, lights, pix, out + 3 * i, lc ? lc + 3 * i : NULL,
                                lr ? lr + 3 * i : NULL, sig ? sig + 2 * i : NULL, count ? count + i : NULL,
-                               row_n ? row_n + 3 * S * i : NULL);
+                               row_n ? row_n + 3 * S * i : NULL, lr_abs ? lr_abs + 3 * i : NULL);
         else
             estimate_pixel(c, params, blob, fd, lights, pix, out + 3 * i, lc ? lc + 3 * i : NULL,
                            lr ? lr + 3 * i : NULL, sig ? sig + 2 * i : NULL, count ? count + i : NULL,
-                           row_n ? row_n + 3 * S * i : NULL);
+                           row_n ? row_n + 3 * S * i : NULL, lr_abs ? lr_abs + 3 * i : NULL);
     }
     free(lights);
 }

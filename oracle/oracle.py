@@ -58,7 +58,7 @@ def lib():
         L.orc_sh_basis.argtypes = [P, P]
         L.orc_one_blob.argtypes = [f64, i32, P]
         L.orc_query.argtypes = [P, P, P, P, u64, P]
-        L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P, P]
+        L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P, P, P]
         L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, u32, P, P, P, P]
         L.orc_nee_sample.argtypes = [P, P, u32, u32, u32, u32, u32, u32, P]
         L.orc_nee_sample.restype = u32
@@ -185,7 +185,8 @@ def query(cfg, params, recs, dirs) -> np.ndarray:
 def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None, rows=False):
     """Two-level estimate of the listed pixels (all when None).
     Returns dict(pixel, lc, lr (n,3) f64; sig (n,2) u64; count (n,) u32;
-    with rows=True also row_n (n, N+M, 3) f64, the cache value of each row)."""
+    lr_abs (n,3) f64, the sum of the absolute values of L_r's terms; with
+    rows=True also row_n (n, N+M, 3) f64, the cache value of each row)."""
     c = ocfg(cfg)
     p = _params64(params) if params is not None else np.zeros(1, np.float64)
     blob = np.ascontiguousarray(scene_blob, np.uint8)
@@ -202,10 +203,11 @@ def estimate(cfg, params, scene_blob, frame: OFrame, pixels=None, rows=False):
     sig = np.zeros((n, 2), np.uint64)
     cnt = np.zeros(n, np.uint32)
     row_n = np.zeros((n, frame.n_cache + frame.n_resid, 3), np.float64) if rows else None
+    lr_abs = np.zeros((n, 3), np.float64)
     lib().orc_estimate_pixels(ctypes.byref(c), _ptr(p), _ptr(blob), ctypes.byref(frame), pix_ptr, n,
                               _ptr(out), _ptr(lc), _ptr(lr), _ptr(sig), _ptr(cnt),
-                              None if row_n is None else _ptr(row_n))
-    res = dict(pixel=out, lc=lc, lr=lr, sig=sig, count=cnt)
+                              None if row_n is None else _ptr(row_n), _ptr(lr_abs))
+    res = dict(pixel=out, lc=lc, lr=lr, sig=sig, count=cnt, lr_abs=lr_abs)
     if rows:
         res["row_n"] = row_n
     return res

@@ -74,14 +74,18 @@ def frame_errors(g, o):
     floored at 1e-3 of its mean) and of the pixel.  The pixel is L_e + L_c +
     L_r and the levels cancel by design (L_r subtracts the cache's
     prediction), so its error is measured against the largest of |pixel|,
-    |L_c| and |L_r|."""
+    |L_c|, |L_r| and the oracle's sum of the absolute values of L_r's terms
+    (the scale of the rounding error of a sum whose terms cancel)."""
     errs = {"lc": rel_err(g["lc"], o["lc"])}
     # L_r = 1/M sum w (L_i - n) cancels internally when the cache is close to
     # L_i: measure it against the cache term's size, which |L_c| estimates
     scale_r = np.maximum(np.abs(o["lr"]), np.abs(o["lc"]))
+    if "lr_abs" in o:  # the terms of L_r (later-vertex cache terms included) before they cancel
+        scale_r = np.maximum(scale_r, o["lr_abs"])
     scale_r = np.maximum(scale_r, 1e-3 * max(np.abs(o["lr"]).mean(), 1e-30))
     errs["lr"] = np.abs(np.asarray(g["lr"], np.float64) - o["lr"]) / scale_r
-    scale = np.maximum.reduce([np.abs(o["pixel"]), np.abs(o["lc"]), np.abs(o["lr"])])
+    scale = np.maximum.reduce([np.abs(o["pixel"]), np.abs(o["lc"]), np.abs(o["lr"])] +
+                              ([o["lr_abs"]] if "lr_abs" in o else []))
     scale = np.maximum(scale, 1e-3 * max(np.abs(o["pixel"]).mean(), 1e-30))
     errs["pixel"] = np.abs(np.asarray(g["pixel"], np.float64) - o["pixel"]) / scale
     return errs
