@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
         uint64_t sig = kSigInit;
         uint32_t nvalid = 0;
         const uint32_t S = a.N + a.M;
+        // Philox counter of cache sample r: (unit / unit_div, (unit % unit_div) << 16 | r)
+        const uint32_t sc0 = pix / a.unit_div, sc1 = (pix - sc0 * a.unit_div) << 16;
         for (uint32_t r = 0; r < S; ++r) {
             V3 wi;
             float3 w;
@@ -122,8 +124,7 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
             if (r < a.N) {
                 BsdfSample bs;
                 if (valid) {
-                    bs = sample_bsdf(n, wo, alb, rough, mat, a.k0, a.k1, pix / a.unit_div,
-                                     ((pix % a.unit_div) << 16) | r, a.purpose);
+                    bs = sample_bsdf(n, wo, alb, rough, mat, a.k0, a.k1, sc0, sc1 | r, a.purpose);
                     sig = sig_mix(sig, bs.word);
                 } else {
                     bs.valid = false;

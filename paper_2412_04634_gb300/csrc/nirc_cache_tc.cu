@@ -560,10 +560,13 @@ __global__ void __launch_bounds__(640, 1)
                 const uint32_t flags = __float_as_uint(q3.z);
                 if (rin && (flags & 1u)) {
                     if (s < a.N) {
+                        // Philox counter of the sample: (unit / unit_div, (unit % unit_div) << 16 | s)
+                        const uint32_t u = p0 + pl;
+                        const uint32_t c0 = a.unit_div == 1u ? u : u / a.unit_div;
+                        const uint32_t c1 = a.unit_div == 1u ? s : (((u - c0 * a.unit_div) << 16) | s);
                         const BsdfSample bs =
                             sample_bsdf(V3{q0.w, q1.x, q1.y}, V3{q1.z, q1.w, q2.x}, make_float3(q2.y, q2.z, q2.w),
-                                        q3.x, (flags >> 1) & 3u, a.k0, a.k1, (p0 + pl) / a.unit_div,
-                                        (((p0 + pl) % a.unit_div) << 16) | s, a.purpose);
+                                        q3.x, (flags >> 1) & 3u, a.k0, a.k1, c0, c1, a.purpose);
                         wi = bs.wi;
                         w = bs.w;
                         ok = bs.valid;
