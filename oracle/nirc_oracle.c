@@ -97,7 +97,7 @@ typedef struct {
     int32_t width;
     int32_t hidden_layers;
     int32_t input_encoding; /* 0 frequency encodings of w and n, 1 the paper's (spherical harmonics + phi) */
-    int32_t pad0;
+    int32_t output;         /* 0 radiance: n = exp(z), relative L2 loss; 1 visibility: V = sigmoid(z), L2 loss */
     double growth;
     double z_clamp;
     double loss_eps;
@@ -774,7 +774,16 @@ static void mlp_forward(const o_cfg* c, const double* params, const double* e, d
     }
 }
 
-/* Cache value n = exp(min(z, z_clamp)) per RGB channel. */
+/* Output activation: radiance n = exp(min(z, z_clamp)); visibility (the
+ * Neural Visibility Cache, paper section "Neural Visibility Cache": a
+ * sigmoid on the output neurons) V = 1 / (1 + exp(-z)). */
+static double output_act(const o_cfg* c, double z)
+{
+    if (c->output == 1) return 1.0 / (1.0 + exp(-z));
+    return exp(z < c->z_clamp ? z : c->z_clamp);
+}
+
+/* Cache value per RGB channel. */
 static void cache_eval(const o_cfg* c, const double* params, const o_record* rec, const float w[3], double nval[3])
 {
     double e[1024];
@@ -782,7 +791,7 @@ static void cache_eval(const o_cfg* c, const double* params, const o_record* rec
     const double* hash = params + mlp_param_count(c);
     encode(c, hash, rec, w, e);
     mlp_forward(c, params, e, NULL, NULL, z);
-    for (int k = 0; k < 3; k++) nval[k] = exp(z[k] < c->z_clamp ? z[k] : c->z_clamp);
+    for (int k = 0; k < 3; k++) nval[k] = output_act(c, z[k]);
 }
 
 void orc_encode(const o_cfg* c, const double* params, const o_record* rec, const float w[3], double* e)
@@ -1147,6 +1156,76 @@ static void camera_ray(const o_header* hd, uint32_t W, uint32_t H, uint32_t px, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Environment map (light mode 2): a cube map stored after the primitives   */
+/* ------------------------------------------------------------------------ */
+
+/* Face size S of the scene's cube map (header word reserved[0]; 0: none);
+ * its 6 S S texels (RGB + pad, float) follow the primitives, face-major,
+ * then row, then column. */
+static uint32_t env_size(const uint8_t* blob)
+{
+    return ((const o_header*)blob)->reserved[0];
+}
+
+/* Texel of direction d: the major axis picks the face (ties: x before y
+ * before z; face 0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z), the other two
+ * coordinates in axis order (a, b) over |major| map [-1, 1] to [0, S)
+ * (column from a, row from b, clamped to S - 1).  Strict binary32: it picks
+ * an integer. */
+static uint32_t env_texel(uint32_t S, const float d[3])
+{
+    float ax = fabsf(d[0]), ay = fabsf(d[1]), az = fabsf(d[2]);
+    uint32_t face;
+    float m, a, b;
+    if (ax >= ay && ax >= az) {
+        face = d[0] >= 0.0f ? 0u : 1u;
+        m = ax;
+        a = d[1];
+        b = d[2];
+    } else if (ay >= az) {
+        face = d[1] >= 0.0f ? 2u : 3u;
+        m = ay;
+        a = d[0];
+        b = d[2];
+    } else {
+        face = d[2] >= 0.0f ? 4u : 5u;
+        m = az;
+        a = d[0];
+        b = d[1];
+    }
+    float u = (a / m + 1.0f) * 0.5f, v = (b / m + 1.0f) * 0.5f;
+    uint32_t i = (uint32_t)floorf(u * (float)S), j = (uint32_t)floorf(v * (float)S);
+    if (i >= S) i = S - 1;
+    if (j >= S) j = S - 1;
+    return face * S * S + j * S + i;
+}
+
+/* L_env(d): the texel's radiance (nearest texel), 0 without a map. */
+static void env_radiance(const uint8_t* blob, const float d[3], double L[3])
+{
+    uint32_t S = env_size(blob);
+    L[0] = L[1] = L[2] = 0.0;
+    if (!S) return;
+    const o_header* hd = (const o_header*)blob;
+    const float* tex = (const float*)(blob + sizeof(o_header) + (size_t)hd->n_prims * sizeof(o_prim));
+    uint32_t t = env_texel(S, d);
+    for (int k = 0; k < 3; k++) L[k] = (double)tex[4 * (size_t)t + k];
+}
+
+/* A visibility cache's value times the environment's radiance. */
+static void env_factor(const uint8_t* blob, const float d[3], double nv[3])
+{
+    double L[3];
+    env_radiance(blob, d, L);
+    for (int k = 0; k < 3; k++) nv[k] *= L[k];
+}
+
+uint32_t orc_env_texel(uint32_t S, const float d[3])
+{
+    return env_texel(S, d);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Two-level estimator per pixel:                                           */
 /*   L_o = L_e + L_c + L_r                                (eq. L_mlmc)      */
 /*   L_c = 1/N_c sum_i n(x, w_i) f_r cos / p              (eq. L_c)         */
@@ -1173,6 +1252,8 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
     /* lr_abs (optional): the sum of the absolute values of the terms that
      * make up L_r, the scale of its rounding error (the terms cancel) */
     double Labs[3] = {0.0, 0.0, 0.0};
+    /* light mode 2 with a visibility cache: n = V(x, w) L_env(w) */
+    const int env = fd->light_mode == 2 && c->output == 1;
     /* row_n (optional): cache value of each of the N + M rows, 0 for rows
      * whose sample is invalid or whose pixel has no camera hit */
     if (row_n) memset(row_n, 0, 3 * sizeof(double) * (fd->n_cache + fd->n_resid));
@@ -1211,6 +1292,7 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             if (!s.valid) continue;
             double nv[3];
             cache_value(c, params, fd, &rec, s.wi, nv);
+            if (env) env_factor(blob, s.wi, nv);
             for (int k = 0; k < 3; k++) Lc[k] += s.w[k] * nv[k];
             if (row_n)
                 for (int k = 0; k < 3; k++) row_n[3 * i + k] = nv[k];
@@ -1226,7 +1308,17 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
             double Li[3], nv[3];
             o_mv mv = {c, params, fd, pix, j, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
             o_mv* mvp = fd->estimator == 2 ? &mv : NULL;
-            if (lights) {
+            if (fd->light_mode == 2) {
+                /* direct environment light: V(x, w_j) L_env(w_j), one ray */
+                float tv;
+                int q = trace_nearest(prims, hd->n_prims, rec.p, s.wi, &tv);
+                sp = sig_mix(sp, q < 0 ? 0xFFFFFFFFu : (uint32_t)q);
+                if (q < 0) {
+                    env_radiance(blob, s.wi, Li);
+                } else {
+                    Li[0] = Li[1] = Li[2] = 0.0;
+                }
+            } else if (lights) {
                 double fc[3], pb, e1[3];
                 bsdf_eval(&rec, s.wi, fc, &pb);
                 trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, fd->n_resid, pb, Li, e1,
@@ -1236,6 +1328,7 @@ static void estimate_pixel(const o_cfg* c, const double* params, const uint8_t* 
                 trace_path(blob, rec.p, s.wi, k0, k1, pix, j, fd->max_depth, Li, &sp, mvp);
             }
             cache_value(c, params, fd, &rec, s.wi, nv);
+            if (env) env_factor(blob, s.wi, nv);
             /* with N = 0 there is no cache level, and nothing is subtracted */
             const double use = fd->n_cache ? 1.0 : 0.0;
             for (int k = 0; k < 3; k++) {
@@ -1520,9 +1613,11 @@ void orc_estimate_pixels(const o_cfg* c, const double* params, const uint8_t* bl
 /* ------------------------------------------------------------------------ */
 
 void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint32_t frame, uint64_t seed,
-                   uint32_t max_depth, uint32_t light_mode, o_record* recs, float* dirs, double* targets,
-                   uint64_t* sig)
+                   uint32_t max_depth, uint32_t light_mode, uint32_t visibility, o_record* recs, float* dirs,
+                   double* targets, uint64_t* sig)
 {
+    /* light mode 2: the target is the direct environment light V L_env
+     * along the sampled direction, or V alone for a visibility cache */
     const o_header* hd = (const o_header*)blob;
     const o_prim* prims = scene_prims(blob);
     uint32_t k0 = (uint32_t)seed, k1 = frame ^ 0x80000000u;
@@ -1559,7 +1654,18 @@ void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint
             sample_bsdf(&rec, k0, k1, tr, 0u, PURPOSE_RESID_DIR, &s);
             sg = sig_mix(sg, sample_word(&s));
             if (s.valid) {
-                if (lights) {
+                if (light_mode == 2) {
+                    float tv;
+                    int q = trace_nearest(prims, hd->n_prims, rec.p, s.wi, &tv);
+                    sg = sig_mix(sg, q < 0 ? 0xFFFFFFFFu : (uint32_t)q);
+                    if (q < 0) {
+                        if (visibility) {
+                            tg[0] = tg[1] = tg[2] = 1.0;
+                        } else {
+                            env_radiance(blob, s.wi, tg);
+                        }
+                    }
+                } else if (lights) {
                     /* target = L_ind: the first hit's emission is direct light */
                     double e1[3];
                     trace_path_nee(blob, lights, rec.p, s.wi, k0, k1, tr, 0u, max_depth, 0u, 0.0, tg, e1, &sg, NULL);
@@ -1635,19 +1741,26 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
             double dz[3];
             double lt = 0.0;
             for (int k = 0; k < 3; k++) {
-                int clamped = !(z[k] <= c->z_clamp);
-                double nv = exp(clamped ? c->z_clamp : z[k]);
+                int vis = c->output == 1;
+                int clamped = !vis && !(z[k] <= c->z_clamp);
+                double nv = output_act(c, z[k]);
                 double dn;
                 if (gout) {
                     lt += gout[3 * t + k] * nv;
                     dn = gout[3 * t + k];
+                } else if (vis) {
+                    /* visibility: plain L2, (f - V)^2 */
+                    double f = targets[3 * t + k];
+                    lt += (f - nv) * (f - nv) * scale;
+                    dn = -2.0 * (f - nv) * scale;
                 } else {
                     double f = targets[3 * t + k];
                     double den = den_fixed ? den_fixed[3 * t + k] : nv * nv + c->loss_eps; /* sg(n)^2 + eps */
                     lt += (f - nv) * (f - nv) / den * scale;
                     dn = -2.0 * (f - nv) / den * scale;
                 }
-                dz[k] = clamped ? 0.0 : dn * nv;
+                /* dn/dz: exp' = n (0 above the clamp), sigmoid' = V (1 - V) */
+                dz[k] = vis ? dn * nv * (1.0 - nv) : (clamped ? 0.0 : dn * nv);
             }
             loss_part[t] = lt;
             /* Walk the layers backwards: delta = dL/d(pre-activation). */

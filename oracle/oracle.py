@@ -23,7 +23,7 @@ class OCfg(ctypes.Structure):
         ("feats_per_level", ctypes.c_int32), ("log2_table", ctypes.c_int32),
         ("base_res", ctypes.c_int32), ("freq_octaves", ctypes.c_int32),
         ("width", ctypes.c_int32), ("hidden_layers", ctypes.c_int32),
-        ("input_encoding", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("input_encoding", ctypes.c_int32), ("output", ctypes.c_int32),
         ("growth", ctypes.c_double), ("z_clamp", ctypes.c_double),
         ("loss_eps", ctypes.c_double),
     ]
@@ -59,7 +59,9 @@ def lib():
         L.orc_one_blob.argtypes = [f64, i32, P]
         L.orc_query.argtypes = [P, P, P, P, u64, P]
         L.orc_estimate_pixels.argtypes = [P, P, P, P, P, u64, P, P, P, P, P, P, P]
-        L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, u32, P, P, P, P]
+        L.orc_gen_train.argtypes = [P, u32, u32, u64, u32, u64, u32, u32, u32, P, P, P, P]
+        L.orc_env_texel.argtypes = [u32, P]
+        L.orc_env_texel.restype = u32
         L.orc_nee_sample.argtypes = [P, P, u32, u32, u32, u32, u32, u32, P]
         L.orc_nee_sample.restype = u32
         L.orc_bsdf_eval.argtypes = [P, P, P, P]
@@ -92,7 +94,7 @@ def _ptr(a: np.ndarray):
 def ocfg(cfg) -> OCfg:
     return OCfg(cfg.pos_encoding, cfg.hash_levels, cfg.feats_per_level, cfg.log2_table,
                 cfg.base_res, cfg.freq_octaves, cfg.width, cfg.hidden_layers,
-                int(getattr(cfg, "input_encoding", 0)), 0, float(cfg.growth), float(cfg.z_clamp), float(cfg.loss_eps))
+                int(getattr(cfg, "input_encoding", 0)), int(getattr(cfg, "output", 0)), float(cfg.growth), float(cfg.z_clamp), float(cfg.loss_eps))
 
 
 def oframe(width, height, n_cache, n_resid, max_depth, frame, seed, cache_mode=0,
@@ -231,15 +233,20 @@ def sampler_pdf32(rec, wi) -> float:
     return float(lib().orc_sampler_pdf32(_ptr(r), _ptr(w)))
 
 
-def gen_train(scene_blob, width, height, T, frame, seed, max_depth, record_dtype, light_mode=0):
+def gen_train(scene_blob, width, height, T, frame, seed, max_depth, record_dtype, light_mode=0, visibility=0):
     blob = np.ascontiguousarray(scene_blob, np.uint8)
     recs = np.zeros(T, record_dtype)
     dirs = np.zeros((T, 3), np.float32)
     tg = np.zeros((T, 3), np.float64)
     sig = np.zeros(T, np.uint64)
-    lib().orc_gen_train(_ptr(blob), width, height, T, frame, seed, max_depth, light_mode,
+    lib().orc_gen_train(_ptr(blob), width, height, T, frame, seed, max_depth, light_mode, int(visibility),
                         _ptr(recs), _ptr(dirs), _ptr(tg), _ptr(sig))
     return recs, dirs, tg, sig
+
+
+def env_texel(size: int, d) -> int:
+    dd = np.ascontiguousarray(d, np.float32)
+    return int(lib().orc_env_texel(int(size), _ptr(dd)))
 
 
 def nee_sample(scene_blob, rec, n_b, key, ctr013):

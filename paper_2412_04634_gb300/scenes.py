@@ -80,13 +80,14 @@ class Scene:
     height: int
     emitter_phase: float = 0.0
     moving_emitter: bool = False
+    env: np.ndarray | None = None  # cube-map texels, float32 (6 S S, 4); header reserved[0] = S
 
     def blob(self) -> np.ndarray:
-        """Header followed by primitives, as a uint8 array."""
-        return np.concatenate([
-            np.frombuffer(self.header.tobytes(), np.uint8),
-            np.frombuffer(self.prims.tobytes(), np.uint8),
-        ])
+        """Header, primitives and (if any) the environment cube map, as a uint8 array."""
+        parts = [np.frombuffer(self.header.tobytes(), np.uint8), np.frombuffer(self.prims.tobytes(), np.uint8)]
+        if self.env is not None:
+            parts.append(np.frombuffer(np.ascontiguousarray(self.env, np.float32).tobytes(), np.uint8))
+        return np.concatenate(parts)
 
     @property
     def n_prims(self) -> int:
@@ -250,6 +251,7 @@ def scene_at_frame(scene: Scene, frame: int) -> Scene:
     out = Scene(scene.header.copy(), prims, scene.width, scene.height)
     out.emitter_phase = scene.emitter_phase
     out.moving_emitter = scene.moving_emitter
+    out.env = scene.env
     return out
 
 
@@ -271,6 +273,94 @@ def floor_light_scene(width: int, height: int, rho: float = 0.5, emission: float
     return Scene(_header(2, (origin, top_left, horizontal, vertical)), prims, width, height)
 
 
+def cube_texel_dirs(S: int) -> np.ndarray:
+    """Unit direction through the centre of every cube-map texel, (6 S S, 3),
+    in the layout the scene blob uses: face 0 +x, 1 -x, 2 +y, 3 -y, 4 +z,
+    5 -z; on each face the other two axes in order (a, b), column from a,
+    row from b, each spanning [-1, 1]."""
+    c = (np.arange(S) + 0.5) / S * 2.0 - 1.0
+    b, a = np.meshgrid(c, c, indexing="ij")  # row b, column a
+    out = []
+    for face in range(6):
+        axis, sign = face // 2, (1.0 if face % 2 == 0 else -1.0)
+        d = np.zeros((S, S, 3))
+        others = [k for k in range(3) if k != axis]
+        d[..., axis] = sign
+        d[..., others[0]] = a
+        d[..., others[1]] = b
+        out.append(d.reshape(-1, 3))
+    d = np.concatenate(out)
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def sky_env(S: int = 64, seed: int = 1) -> np.ndarray:
+    """Procedural sky (up = +y): a blue gradient above the horizon, a dim
+    ground colour below, and a bright sun lobe in a seeded direction 20-70
+    degrees above the horizon.  float32 (6 S S, 4)."""
+    rng = np.random.default_rng(seed + 0x5C1)
+    d = cube_texel_dirs(S)
+    elev = math.radians(float(rng.uniform(20.0, 70.0)))
+    azim = float(rng.uniform(0.0, 2.0 * math.pi))
+    sun = np.array([math.cos(elev) * math.cos(azim), math.sin(elev), math.cos(elev) * math.sin(azim)])
+    up = np.clip(d[:, 1], -1.0, 1.0)
+    sky = np.where(up[:, None] > 0.0, np.array([0.35, 0.55, 1.0]) * (0.4 + 0.6 * up[:, None]),
+                   np.array([0.12, 0.1, 0.08]))
+    lobe = 30.0 * np.clip(d @ sun, 0.0, 1.0) ** 400
+    env = np.zeros((d.shape[0], 4), np.float32)
+    env[:, :3] = sky + lobe[:, None]
+    return env
+
+
+def uniform_env(S: int, radiance) -> np.ndarray:
+    env = np.zeros((6 * S * S, 4), np.float32)
+    env[:, :3] = radiance
+    return env
+
+
+def env_scene(width: int, height: int, seed: int = 1, n_prims: int = 64, env_size: int = 64,
+              glossy: bool = True) -> Scene:
+    """Outdoor scene under an environment map (the Neural Visibility Cache
+    workload): a large ground rectangle (y = 0, facing +y) and n_prims - 1
+    seeded spheres and rectangles standing on it in [0, 1] x [0, 0.5] x
+    [0, 1], under the procedural sky of ``sky_env``; the camera looks down
+    at the objects from the front."""
+    assert n_prims >= 1
+    rng = np.random.default_rng(seed + 0xE1)
+    prims = np.zeros(n_prims, PRIM_DTYPE)
+    mat = MAT_GGX if glossy else MAT_LAMBERT
+    _fill_rect(prims[0], (-20.0, 0.0, -20.0), (0.0, 0.0, 40.0), (40.0, 0.0, 0.0), rng.uniform(0.2, 0.8, 3),
+               float(rng.uniform(0.3, 1.0)) if glossy else 1.0, mat)
+    for i in range(1, n_prims):
+        alb = rng.uniform(0.2, 0.8, 3)
+        rough = float(rng.uniform(0.05, 1.0)) if glossy else 1.0
+        if i % 2:
+            r = float(rng.uniform(0.02, 0.08))
+            c = np.array([rng.uniform(0.0, 1.0), r + rng.uniform(0.0, 0.4), rng.uniform(0.0, 1.0)])
+            _fill_sphere(prims[i], c, r, alb, rough, mat)
+        else:
+            nrm = rng.normal(size=3)
+            nrm /= np.linalg.norm(nrm)
+            t = np.cross(nrm, [1.0, 0.0, 0.0] if abs(nrm[0]) < 0.9 else [0.0, 1.0, 0.0])
+            t /= np.linalg.norm(t)
+            b = np.cross(nrm, t)
+            lu, lv = rng.uniform(0.05, 0.2, 2)
+            centre = np.array([rng.uniform(0.0, 1.0), rng.uniform(0.1, 0.5), rng.uniform(0.0, 1.0)])
+            corner = centre - 0.5 * t * lu - 0.5 * b * lv
+            _fill_rect(prims[i], corner, t * lu, b * lv, alb, rough, mat)
+    origin, top_left, horizontal, vertical = _camera((0.5, 0.9, -0.9), 50.0, width, height)
+    # tilt the +z camera frame down by 35 degrees about x
+    ang = math.radians(35.0)
+    rot = np.array([[1.0, 0.0, 0.0], [0.0, math.cos(ang), -math.sin(ang)], [0.0, math.sin(ang), math.cos(ang)]])
+    top_left = origin + rot @ (top_left - origin)
+    horizontal = rot @ horizontal
+    vertical = rot @ vertical
+    hd = _header(n_prims, (origin, top_left, horizontal, vertical))
+    hd["reserved"][0] = env_size
+    sc = Scene(hd, prims, width, height)
+    sc.env = sky_env(env_size, seed)
+    return sc
+
+
 def furnace_scene(width: int, height: int, rho: float = 0.5, emission: float = 1.0) -> Scene:
     """White-furnace scene: the camera sits at the centre of a sphere whose
     inner surface is Lambertian with albedo ``rho`` and emits ``emission``
@@ -288,6 +378,7 @@ def furnace_scene(width: int, height: int, rho: float = 0.5, emission: float = 1
 
 POS_FREQ, POS_HASHGRID = 0, 1
 INPUT_FREQ, INPUT_SH = 0, 1  # network input: frequency encodings, or the paper's SH + phi
+OUT_RADIANCE, OUT_VISIBILITY = 0, 1  # cache output: exp radiance, or sigmoid visibility (NVC)
 
 
 @dataclasses.dataclass
@@ -303,6 +394,7 @@ class NetConfig:
     width: int = 64
     hidden_layers: int = 3
     input_encoding: int = INPUT_FREQ
+    output: int = OUT_RADIANCE
     lr: float = 1e-3
     beta1: float = 0.9
     beta2: float = 0.99

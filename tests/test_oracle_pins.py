@@ -1107,3 +1107,150 @@ def test_multivertex_correction_has_zero_mean(oracle, light_mode):
     se = d.std() / math.sqrt(d.size)
     assert se > 0 and np.abs(d).max() > 10 * se  # the terms are there
     assert abs(d.mean()) < 4 * se, (d.mean(), se)
+
+
+# ---------------------------------------------------------------------------
+# Environment light and the Neural Visibility Cache (light mode 2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("S", [1, 4, 16])
+def test_env_texel_lookup_matches_texel_centres(oracle, S):
+    """The oracle's cube-map lookup maps every texel-centre direction of the
+    input generator (written independently, in numpy) back to that texel;
+    axis directions land on the face centres; ties go to x before y before z."""
+    d = scenes.cube_texel_dirs(S).astype(np.float32)
+    assert [oracle.env_texel(S, x) for x in d] == list(range(6 * S * S))
+    h = S // 2
+    for face, v in enumerate(np.eye(3).repeat(2, axis=0) * np.array([1, -1] * 3)[:, None]):
+        assert oracle.env_texel(S, v.astype(np.float32)) == face * S * S + h * S + h
+    tie = np.array([1.0, 1.0, 0.0], np.float32) / np.float32(math.sqrt(2.0))
+    assert oracle.env_texel(S, tie) // (S * S) == 0
+
+
+def _ground(W=64, H=48, occluder=False, rho=0.5, L0=(0.7, 1.1, 1.6)):
+    """Lambertian ground (y = 0) under a uniform environment, optionally a
+    1 x 1 square occluder at height 0.5 over the origin; the camera sits below
+    the occluder's plane and looks down at the ground."""
+    prims = np.zeros(2 if occluder else 1, scenes.PRIM_DTYPE)
+    scenes._fill_rect(prims[0], (-30.0, 0.0, -30.0), (0.0, 0.0, 60.0), (60.0, 0.0, 0.0), (rho,) * 3, 1.0,
+                      scenes.MAT_LAMBERT)
+    if occluder:
+        scenes._fill_rect(prims[1], (-0.5, 0.5, -0.5), (1.0, 0.0, 0.0), (0.0, 0.0, 1.0), (0.5,) * 3, 1.0,
+                          scenes.MAT_LAMBERT)
+    origin = np.array([0.0, 0.25, -1.5])
+    fwd = np.array([0.0, -0.25, 1.5])
+    fwd /= np.linalg.norm(fwd)
+    right = np.array([1.0, 0.0, 0.0])
+    up = np.cross(right, fwd)
+    top_left = origin + fwd - 0.5 * right * 1.2 + 0.5 * up * 0.9
+    hd = scenes._header(len(prims), (origin, top_left, right * 1.2, -up * 0.9))
+    hd["reserved"][0] = 4
+    sc = scenes.Scene(hd, prims, W, H)
+    sc.env = scenes.uniform_env(4, L0)
+    return sc
+
+
+def test_env_open_ground_exact(oracle):
+    """Nothing occludes the sky of an open Lambertian ground: every residual
+    sample sees L_env, so with no cache level the pixel is rho L_env exactly;
+    a visibility cache V = c gives c rho L_env as cache level and
+    (1 - c) rho L_env as residual level (light mode 2)."""
+    rho, L0 = float(np.float32(0.5)), np.array([0.7, 1.1, 1.6], np.float32).astype(np.float64)
+    sc = _ground()
+    cfg = scenes.config_small()
+    r = oracle.estimate(cfg, None, sc.blob(), oracle.oframe(64, 48, 0, 3, 1, 0, 2, cache_mode=1, light_mode=2))
+    hit = r["count"] > 0
+    assert hit.mean() > 0.5
+    assert np.allclose(r["pixel"][hit], rho * L0, rtol=1e-12)
+    vis = dataclasses.replace(cfg, output=scenes.OUT_VISIBILITY)
+    fd = oracle.oframe(64, 48, 4, 2, 1, 0, 2, cache_mode=2, cache_const=(0.3, 0.3, 0.3), light_mode=2)
+    r = oracle.estimate(vis, None, sc.blob(), fd)
+    hit = r["count"] > 0
+    assert np.allclose(r["lc"][hit], 0.3 * rho * L0, rtol=1e-12)
+    assert np.allclose(r["lr"][hit], 0.7 * rho * L0, rtol=1e-12)
+
+
+def _corner_ff(a, b, c):
+    """Form factor from a differential area to a parallel a x b rectangle at
+    distance c with one corner straight above it (the catalogue closed form)."""
+    X, Y = a / c, b / c
+    return (X / math.sqrt(1 + X * X) * math.atan(Y / math.sqrt(1 + X * X)) +
+            Y / math.sqrt(1 + Y * Y) * math.atan(X / math.sqrt(1 + Y * Y))) / (2 * math.pi)
+
+
+def _rect_ff(px, pz, x0, x1, z0, z1, c):
+    def g(a, b):
+        return math.copysign(1.0, a) * math.copysign(1.0, b) * _corner_ff(abs(a), abs(b), c)
+    return g(x1 - px, z1 - pz) - g(x0 - px, z1 - pz) - g(x1 - px, z0 - pz) + g(x0 - px, z0 - pz)
+
+
+def test_env_visibility_expectation_under_occluder(oracle):
+    """Under a square occluder the fraction of cosine-distributed directions
+    that see the sky is 1 - F, F the form factor from the ground point to the
+    square (closed form): the mean of pixel / (rho L_env) over the ground
+    pixels matches the mean of 1 - F at their hit points."""
+    rho, L0 = float(np.float32(0.5)), 1.0
+    sc = _ground(occluder=True, L0=(L0, L0, L0))
+    cfg = scenes.config_small()
+    hd = sc.header
+    o = hd["cam_origin"][:3].astype(np.float64)
+    tl, hz, vt = (hd[k][:3].astype(np.float64) for k in ("cam_top_left", "cam_horizontal", "cam_vertical"))
+    vals, expect = [], []
+    for frame in range(4):
+        fd = oracle.oframe(64, 48, 0, 8, 1, frame, 6, cache_mode=1, light_mode=2)
+        r = oracle.estimate(cfg, None, sc.blob(), fd)
+        for pix in range(64 * 48):
+            rr = oracle.philox([pix, 0, 0, 1], [6, frame])
+            jx, jy = [((int(v) >> 8) * 2.0 ** -24) for v in rr[:2]]
+            d = tl + ((pix % 64 + jx) / 64) * hz + ((pix // 64 + jy) / 48) * vt - o
+            if d[1] >= 0:
+                continue
+            t = -o[1] / d[1]
+            p = o + t * d
+            if max(abs(p[0]), abs(p[2])) > 29.0:  # beyond the ground rectangle: the camera ray misses
+                continue
+            assert r["count"][pix] == 8
+            vals.append(r["pixel"][pix, 0] / (rho * L0))
+            expect.append(1.0 - _rect_ff(p[0], p[2], -0.5, 0.5, -0.5, 0.5, 0.5))
+    vals, expect = np.array(vals), np.array(expect)
+    assert expect.min() < 0.6 and expect.max() > 0.95  # pixels under and beside the occluder
+    se = vals.std() / math.sqrt(vals.size)
+    assert abs(vals.mean() - expect.mean()) < 4 * se, (vals.mean(), expect.mean(), se)
+
+
+def test_env_training_targets(oracle):
+    """Light mode 2 training records: visibility targets are 0 or 1 and 1
+    exactly where the radiance targets are the sky's texel radiance."""
+    sc = scenes.env_scene(48, 32, seed=3, n_prims=16, env_size=8)
+    blob = sc.blob()
+    r1, d1, tv, _ = oracle.gen_train(blob, 48, 32, 2000, 1, 4, 3, scenes.RECORD_DTYPE, light_mode=2, visibility=1)
+    r2, d2, tr, _ = oracle.gen_train(blob, 48, 32, 2000, 1, 4, 3, scenes.RECORD_DTYPE, light_mode=2, visibility=0)
+    assert np.array_equal(d1, d2)
+    assert set(np.unique(tv)) <= {0.0, 1.0} and 0.1 < tv[:, 0].mean() < 0.99
+    vis = tv[:, 0] == 1.0
+    env = sc.env.astype(np.float64)
+    for i in np.nonzero(vis)[0][:200]:
+        assert np.array_equal(tr[i], env[oracle.env_texel(8, d1[i]), :3])
+    assert np.all(tr[~vis] == 0)
+
+
+def test_visibility_gradients_match_finite_differences(oracle):
+    """Sigmoid output and plain L2 loss (the visibility cache) against FP64
+    central differences."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=6, log2_table=10, hidden_layers=3,
+                           base_res=4, growth=2.0, output=scenes.OUT_VISIBILITY)
+    params = scenes.init_params(cfg, 41).astype(np.float64)
+    rng = np.random.default_rng(42)
+    params[:cfg.n_mlp_params] += rng.normal(0, 0.05, cfg.n_mlp_params)
+    params[cfg.n_mlp_params:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params)
+    recs, dirs, _ = scenes.training_batch(96, seed=43)
+    tg = (rng.uniform(size=(96, 1)) < 0.6).astype(np.float64).repeat(3, axis=1)
+    _, g = oracle.loss_grad(cfg, params, recs, dirs, tg)
+    touched = np.nonzero(g[cfg.n_mlp_params:])[0] + cfg.n_mlp_params
+    idx = np.concatenate([rng.choice(touched, 30, replace=False), rng.choice(cfg.n_mlp_params, 40, replace=False),
+                          np.arange(cfg.n_mlp_params - 3, cfg.n_mlp_params)])
+    _fd_check(oracle, cfg, params, recs, dirs, tg, idx)
+    # and the loss value: mean (f - sigmoid(z))^2 over samples and channels
+    q = oracle.query(cfg, params, recs, dirs)
+    loss, _ = oracle.loss_grad(cfg, params, recs, dirs, tg)
+    assert abs(loss - np.mean((tg - q) ** 2)) < 1e-12
