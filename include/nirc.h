@@ -69,6 +69,13 @@ typedef enum nirc_pos_encoding {
                               "Neural Network Architecture", first bullet) */
 } nirc_pos_encoding;
 
+typedef enum nirc_output {
+    NIRC_OUT_RADIANCE = 0,   /* n = exp(min(z, z_clamp)), relative L2 loss (eq. 12) */
+    NIRC_OUT_VISIBILITY = 1  /* the Neural Visibility Cache: V = 1 / (1 + exp(-z))
+                                per channel (a sigmoid on the output neurons),
+                                loss mean (f - V)^2 over records and channels */
+} nirc_output;
+
 typedef enum nirc_input_encoding {
     NIRC_INPUT_FREQ = 0,  /* direction (theta/pi, phi/2pi) and normal by
                              frequency features (the 64x64 and 1080p workloads) */
@@ -113,6 +120,7 @@ typedef struct nirc_config {
     float loss_eps;            /* eps of eq. 12, e.g. 0.01 */
     float z_clamp;             /* e.g. 15 */
     uint32_t input_encoding;   /* nirc_input_encoding */
+    uint32_t output;           /* nirc_output */
 } nirc_config;
 
 /* Shading record: one surface point (paper: "surface parameter buffer",
@@ -138,7 +146,14 @@ typedef struct nirc_record {
  * f32 albedo[3], roughness, emission[3], u32 flags}; kind 0 sphere (centre
  * a), 1 rectangle (corner a, perpendicular edges u, v, unit normal n);
  * flags bits 0-1 material, bit 8 two-sided emission.  The blob must be
- * 16-byte aligned and hold at least n_prims primitives. */
+ * 16-byte aligned and hold at least n_prims primitives.  Environment map
+ * (light mode 2): header word reserved[0] = cube face size S (0: none) and
+ * 6 S S texels {f32 rgb[3], pad} after the primitives, face-major (0 +x,
+ * 1 -x, 2 +y, 3 -y, 4 +z, 5 -z), then row, then column; direction d picks
+ * the face of its largest |component| (ties: x, then y, then z) and, with
+ * (a, b) its other two components in axis order, column
+ * floor((a / |major| + 1) / 2 * S) and row floor((b / |major| + 1) / 2 * S)
+ * (clamped to S - 1), in binary32; L_env(d) is that texel (nearest). */
 typedef struct nirc_frame_desc {
     uint32_t width, height;  /* W, H; pixel index = y * W + x, row 0 at top */
     uint32_t n_cache;        /* N cache-level samples per pixel (0..1024) */
@@ -160,7 +175,17 @@ typedef struct nirc_frame_desc {
                                 residual directions are the BSDF technique at
                                 the shading point); cache, residual paths and
                                 training targets carry L_ind.  Spherical
-                                emitters are reached by BSDF sampling only. */
+                                emitters are reached by BSDF sampling only.
+                                2: direct environment light (section
+                                "Neural Visibility Cache"): the frame is
+                                L_e(x) + the two levels of
+                                f cos V(x, w) L_env(w): residual rows trace
+                                one ray (V = 1 when it leaves the scene), the
+                                cache value is V^(x, w) L_env(w) for a
+                                visibility cache (NIRC_OUT_VISIBILITY) or the
+                                network's radiance otherwise (the generic
+                                NIRC on the same task); two-level estimator
+                                only. */
     uint32_t estimator;      /* nirc_estimator */
     uint32_t n_cache2;       /* NIRC_EST_MULTI_VERTEX: cache samples at the */
     uint32_t n_cache3;       /* second and third vertex (0..1024) */
@@ -319,8 +344,9 @@ nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d_scene, con
  * get flags bit 0 cleared (excluded from the loss).  Philox key word 1 is
  * frame ^ 0x80000000 so training draws never repeat rendering draws.
  * light_mode as in nirc_frame_desc (1: targets are L_ind estimates with NEE
- * + MIS along the path).  d_records = T x 64 B, d_dirs = T x 3,
- * d_targets = T x 3. */
+ * + MIS along the path; 2: one ray, target V L_env along it, or V in all
+ * three channels for a visibility cache).  d_records = T x 64 B,
+ * d_dirs = T x 3, d_targets = T x 3. */
 nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width,
                            uint32_t height, uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth,
                            uint32_t light_mode, nirc_record* d_records, float* d_dirs, float* d_targets,

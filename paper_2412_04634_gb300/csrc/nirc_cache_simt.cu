@@ -24,6 +24,8 @@ constexpr int kSimtThreads = 128;
 struct CacheArgs {
     uint32_t W, H, N, M, k0, k1;
     uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
+    const SceneHeader* env_hd;   // light mode 2 with a visibility cache: cache values times L_env
+    uint32_t env_nprims;
     uint32_t cache_mode;
     float cc0, cc1, cc2;
     float z_clamp;
@@ -71,8 +73,8 @@ __device__ __forceinline__ float3 row_mlp(const NetShape& s, const float* __rest
         z01 = __ffma2_rn(make_float2(w1.x, w1.y), make_float2(a1, a1), z01);
         z23 = __ffma2_rn(make_float2(w1.z, w1.w), make_float2(a1, a1), z23);
     }
-    return make_float3(expf(fminf(z01.x, z_clamp)), expf(fminf(z01.y, z_clamp)),
-                       expf(fminf(z23.x, z_clamp)));
+    const bool vis = s.vis;
+    return make_float3(out_act(vis, z01.x, z_clamp), out_act(vis, z01.y, z_clamp), out_act(vis, z23.x, z_clamp));
 }
 
 template <bool kSh>
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
 
     const uint64_t P = (uint64_t)a.W * a.H;
     const bool network = a.cache_mode == 0;
+    const EnvMap env = env_from(a.env_hd, a.env_nprims);
     // Every lane of a block runs the same number of iterations (warp votes below).
     for (uint64_t first = (uint64_t)blockIdx.x * kSimtThreads; first < P; first += (uint64_t)gridDim.x * kSimtThreads) {
         const uint64_t pix64 = first + threadIdx.x;
@@ -146,6 +149,10 @@ __global__ void __launch_bounds__(kSimtThreads, 1)
                 if (__any_sync(0xffffffffu, ok)) nv = row_mlp<kSh>(a.s, sw, act, stride, hpix, wi, a.z_clamp);
             } else if (a.cache_mode == 2) {
                 nv = make_float3(a.cc0, a.cc1, a.cc2);
+            }
+            if (a.env_hd && ok) {  // visibility cache: n = V L_env(w)
+                const float3 le = env_radiance(env, wi);
+                nv = make_float3(nv.x * le.x, nv.y * le.y, nv.z * le.z);
             }
             if (row_n && in_range) {
                 float* rn = row_n + 3 * ((uint64_t)pix * S + r);
@@ -274,10 +281,12 @@ static size_t simt_smem(const NetShape& s) {
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                               const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                               float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st,
-                              CachePass pass) {
+                              CachePass pass, EnvSource env) {
     CacheArgs a;
     a.unit_div = pass.unit_div;
     a.purpose = pass.purpose;
+    a.env_hd = reinterpret_cast<const SceneHeader*>(env.scene);
+    a.env_nprims = env.n_prims;
     a.W = fd.width;
     a.H = fd.height;
     a.N = fd.n_cache;

@@ -161,6 +161,8 @@ __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_
 struct TcArgs {
     uint32_t W, H, N, M, k0, k1;
     uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
+    const SceneHeader* env_hd;   // light mode 2 with a visibility cache: cache values times L_env
+    uint32_t env_nprims;
     uint32_t S, P, n_blocks;
     float z_clamp;
     uint32_t img_bytes;
@@ -661,9 +663,16 @@ __global__ void __launch_bounds__(640, 1)
                 tc::tmem_ld4(tmem_row, v);
                 tc::tmem_wait_ld();
                 const float* bo = bias + 64 + (a.s.hidden - 1) * 64;
-                nv.x = expf(fminf(__uint_as_float(v[0]) + bo[0], a.z_clamp));
-                nv.y = expf(fminf(__uint_as_float(v[1]) + bo[1], a.z_clamp));
-                nv.z = expf(fminf(__uint_as_float(v[2]) + bo[2], a.z_clamp));
+                const bool vis = a.s.vis;
+                nv.x = out_act(vis, __uint_as_float(v[0]) + bo[0], a.z_clamp);
+                nv.y = out_act(vis, __uint_as_float(v[1]) + bo[1], a.z_clamp);
+                nv.z = out_act(vis, __uint_as_float(v[2]) + bo[2], a.z_clamp);
+                if (a.env_hd && ok) {  // visibility cache: n = V L_env(w)
+                    const float3 le = env_radiance(env_from(a.env_hd, a.env_nprims), wi);
+                    nv.x *= le.x;
+                    nv.y *= le.y;
+                    nv.z *= le.z;
+                }
             }
             if (row_n && rin) {
                 float* rn = row_n + 3 * ((uint64_t)p0 * S + r);
@@ -865,10 +874,12 @@ static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t sm
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
-                            cudaStream_t st, CachePass pass) {
+                            cudaStream_t st, CachePass pass, EnvSource env) {
     TcArgs a;
     a.unit_div = pass.unit_div;
     a.purpose = pass.purpose;
+    a.env_hd = reinterpret_cast<const SceneHeader*>(env.scene);
+    a.env_nprims = env.n_prims;
     a.W = fd.width;
     a.H = fd.height;
     a.N = fd.n_cache;

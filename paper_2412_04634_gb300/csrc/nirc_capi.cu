@@ -35,6 +35,7 @@ NetShape make_shape(const nirc_config& cfg) {
     s.log2_table = cfg.log2_table;
     s.n_pos = s.hashgrid ? cfg.hash_levels * cfg.feats_per_level : 3 * 2 * cfg.freq_octaves;
     s.sh = cfg.input_encoding == NIRC_INPUT_SH ? 1u : 0u;
+    s.vis = cfg.output == NIRC_OUT_VISIBILITY ? 1u : 0u;
     s.n_dir = s.sh ? kShFeatures : kDirFeatures;
     s.n_surf = s.sh ? kPhiFeatures : kNrmFeatures;
     s.n_in = s.n_pos + s.n_dir + s.n_surf;
@@ -101,6 +102,10 @@ static nirc_status check_config(const nirc_config* c) {
     }
     if (c->input_encoding > NIRC_INPUT_SH) {
         set_error("input_encoding %u unknown", c->input_encoding);
+        return NIRC_ERR_INVALID;
+    }
+    if (c->output > NIRC_OUT_VISIBILITY) {
+        set_error("output %u unknown", c->output);
         return NIRC_ERR_INVALID;
     }
     {
@@ -193,12 +198,13 @@ nirc_status check_frame_args(const char* who, const void* scene, const nirc_fram
         return NIRC_ERR_INVALID;
     }
     if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
-        fd.max_depth > 64 || fd.cache_mode > 2 || fd.light_mode > 1 || P > 0xFFFFFFFFull ||
+        fd.max_depth > 64 || fd.cache_mode > 2 || fd.light_mode > 2 || P > 0xFFFFFFFFull ||
+        (fd.light_mode == 2 && fd.estimator != NIRC_EST_TWO_LEVEL) ||
         fd.estimator > NIRC_EST_MULTI_VERTEX || (fd.estimator == NIRC_EST_BIASED_BTH && fd.n_resid != 0) ||
         (fd.estimator == NIRC_EST_MULTI_VERTEX &&
          (fd.n_cache2 > 1024 || fd.n_cache3 > 1024 || P * fd.n_resid > 0xFFFFFFFFull))) {
         set_error("%s: argument out of range (n_prims 1..%u, N, N2, N3 <= 1024, M <= 64, depth 1..64, "
-                  "light_mode 0..1, estimator 0..2, M = 0 for the biased estimator)",
+                  "light_mode 0..2, estimator 0..2, M = 0 for the biased estimator, light mode 2 two-level only)",
                   who, NIRC_MAX_PRIMS);
         return NIRC_ERR_INVALID;
     }
@@ -253,12 +259,17 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
     }
     timer_begin(h, NIRC_K_CACHE, st);
     const bool tc = tc_supported(h, fd);
+    EnvSource env;  // light mode 2 with a visibility cache: n = V L_env
+    if (fd.light_mode == 2 && h->shape.vis) {
+        env.scene = scene;
+        env.n_prims = fd.n_prims;
+    }
     if (tc) {
         e = launch_cache_tc(h, fd, recs, base, rows, beta, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
-                            count, aux ? aux->row_n : nullptr, h->dev_err, st);
+                            count, aux ? aux->row_n : nullptr, h->dev_err, st, CachePass{}, env);
     } else {
         e = launch_cache_simt(h, fd, recs, base, rows, beta, out, aux ? aux->lc : nullptr, aux ? aux->lr : nullptr, sig,
-                              count, aux ? aux->row_n : nullptr, st);
+                              count, aux ? aux->row_n : nullptr, st, CachePass{}, env);
     }
     bool tc_any = tc;
     if (multi && e == cudaSuccess) {
@@ -523,13 +534,13 @@ struct StateHeader {
     uint64_t n_params;
     uint64_t pad;
 };
-constexpr uint32_t kStateVersion = 2;
+constexpr uint32_t kStateVersion = 3;
 
 bool same_shape(const nirc_config& a, const nirc_config& b) {
     return a.pos_encoding == b.pos_encoding && a.hash_levels == b.hash_levels &&
            a.feats_per_level == b.feats_per_level && a.log2_table == b.log2_table && a.base_res == b.base_res &&
            a.growth == b.growth && a.freq_octaves == b.freq_octaves && a.width == b.width &&
-           a.hidden_layers == b.hidden_layers && a.input_encoding == b.input_encoding;
+           a.hidden_layers == b.hidden_layers && a.input_encoding == b.input_encoding && a.output == b.output;
 }
 }  // namespace
 
@@ -675,7 +686,7 @@ nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims
     }
     if (n_prims < 1 || n_prims > NIRC_MAX_PRIMS || width == 0 || height == 0 ||
         (uint64_t)width * height > 0xFFFFFFFFull || max_depth < 1 || max_depth > 64 || T > 0xFFFFFFFFull ||
-        light_mode > 1) {
+        light_mode > 2) {
         set_error("nirc_gen_train: argument out of range");
         return NIRC_ERR_INVALID;
     }

@@ -600,6 +600,68 @@ __device__ __forceinline__ void phi_features(V3 n, float3 alb, float rough, floa
     one_blob4(rough, e + 11);
 }
 
+// Environment map (light mode 2): a cube map of S x S texels per face after
+// the scene's primitives (S = header reserved[0]; 0: none).
+struct EnvMap {
+    const float4* tex = nullptr;
+    uint32_t S = 0;
+};
+
+// Texel of direction d: the face of the largest |component| (ties: x, then
+// y, then z; face 0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z), column and row from
+// the other two components over |major| mapped from [-1, 1] to [0, S),
+// clamped.  Strict binary32: it picks an integer.
+__device__ __forceinline__ uint32_t env_texel(uint32_t S, V3 d) {
+    const float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    uint32_t face;
+    float m, a, b;
+    if (ax >= ay && ax >= az) {
+        face = d.x >= 0.f ? 0u : 1u;
+        m = ax;
+        a = d.y;
+        b = d.z;
+    } else if (ay >= az) {
+        face = d.y >= 0.f ? 2u : 3u;
+        m = ay;
+        a = d.x;
+        b = d.z;
+    } else {
+        face = d.z >= 0.f ? 4u : 5u;
+        m = az;
+        a = d.x;
+        b = d.y;
+    }
+    const float u = __fmul_rn(__fadd_rn(__fdiv_rn(a, m), 1.f), 0.5f);
+    const float v = __fmul_rn(__fadd_rn(__fdiv_rn(b, m), 1.f), 0.5f);
+    const uint32_t i = min((uint32_t)floorf(__fmul_rn(u, (float)S)), S - 1u);
+    const uint32_t j = min((uint32_t)floorf(__fmul_rn(v, (float)S)), S - 1u);
+    return face * S * S + j * S + i;
+}
+
+// L_env(d): the nearest texel, 0 without a map.
+__device__ __forceinline__ float3 env_radiance(const EnvMap& e, V3 d) {
+    if (!e.S) return make_float3(0.f, 0.f, 0.f);
+    const float4 t = __ldg(e.tex + env_texel(e.S, d));
+    return make_float3(t.x, t.y, t.z);
+}
+
+// The cube map of a scene blob (NULL header: none).
+__device__ __forceinline__ EnvMap env_from(const SceneHeader* hd, uint32_t n_prims) {
+    EnvMap e;
+    if (hd) {
+        e.S = __ldg(&hd->reserved[0]);
+        e.tex = reinterpret_cast<const float4*>(reinterpret_cast<const unsigned char*>(hd) + sizeof(SceneHeader) +
+                                                (size_t)n_prims * 96u);
+    }
+    return e;
+}
+
+// Output activation of the cache network: visibility V = 1 / (1 + exp(-z))
+// (sigmoid), radiance n = exp(min(z, z_clamp)).
+__device__ __forceinline__ float out_act(bool vis, float z, float z_clamp) {
+    return vis ? 1.0f / (1.0f + expf(-z)) : expf(fminf(z, z_clamp));
+}
+
 // Hash-grid level description (precomputed on the host).
 struct GridLevel {
     uint32_t res;    // floor(base * growth^l)

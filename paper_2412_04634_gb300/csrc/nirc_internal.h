@@ -39,6 +39,7 @@ struct NetShape {
     uint32_t n_dir;     // direction features: 16 (frequency) or 25 (spherical harmonics)
     uint32_t n_surf;    // per-surface features after the position: 24 (normal frequency) or 15 (phi)
     uint32_t sh;        // 1 = the paper's input (spherical harmonics + phi)
+    uint32_t vis;       // 1 = visibility output (sigmoid, L2 loss)
     uint32_t n_in;      // network inputs = n_pos + n_dir + n_surf, in the order [pos][dir][surf]
     uint32_t n_pix;     // per-pixel features = n_pos + n_surf
     uint32_t hidden;    // hidden layers (>= 1)
@@ -146,10 +147,16 @@ struct CachePass {
 
 // beta (biased and multi-vertex estimators, else NULL): per-unit throughput
 // applied to both levels; base NULL: zero emission and path-traced part.
+// env (light mode 2 with a visibility cache, else empty): the scene whose
+// cube map multiplies every cache value (L_env of the row's direction).
+struct EnvSource {
+    const void* scene = nullptr;
+    uint32_t n_prims = 0;
+};
 cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                               const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                               float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, cudaStream_t st,
-                              CachePass pass = CachePass{});
+                              CachePass pass = CachePass{}, EnvSource env = EnvSource{});
 cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, const float* dirs, uint64_t n,
                               float* out, cudaStream_t st);
 cudaError_t launch_repack_simt(const nirc_handle* h, cudaStream_t st);
@@ -161,7 +168,7 @@ bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd);
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
-                            cudaStream_t st, CachePass pass = CachePass{});
+                            cudaStream_t st, CachePass pass = CachePass{}, EnvSource env = EnvSource{});
 
 // nirc_train.cu
 size_t train_scratch_bytes(const nirc_handle* h, uint64_t n);

@@ -41,7 +41,16 @@ constexpr uint32_t kBvhMinPrims = 17;
 struct FrameArgs {
     uint32_t W, H, N, M, D, n_prims;
     uint32_t k0, k1;
+    uint32_t env_mode;  // light mode 2: residual rows are one visibility ray times L_env
 };
+
+// The scene's cube map (header reserved[0] = face size, texels after the primitives).
+__device__ __forceinline__ EnvMap scene_env(const SceneHeader& hd, const Prim* __restrict__ gp, uint32_t n_prims) {
+    EnvMap e;
+    e.S = hd.reserved[0];
+    e.tex = reinterpret_cast<const float4*>(gp + n_prims);
+    return e;
+}
 
 // Emitting rectangles in primitive order (the light technique's choices).
 struct Lights {
@@ -473,7 +482,11 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
             }
         } else if (stage == kResidRay) {
             bool end;
-            if constexpr (kNee)
+            if (a.env_mode) {  // light mode 2: V(x, w_j) L_env(w_j), one ray
+                sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+                L = prim < 0 ? env_radiance(scene_env(hd, gp, a.n_prims), d) : make_float3(0.f, 0.f, 0.f);
+                end = true;
+            } else if constexpr (kNee)
                 end = path_segment_nee(tr, gp, lt, prim, t, o, d, beta, L, seg, a.D, a.k0, a.k1, pix, j, sig, pb, a.M,
                                        first_emit, mv, (uint64_t)pix * a.M + j,
                                        make_float3(sw.x * invM, sw.y * invM, sw.z * invM));
@@ -680,7 +693,7 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_gen_train(const SceneHeader* 
                                                           uint32_t H, uint64_t T, uint32_t k0, uint32_t k1,
                                                           uint32_t max_depth, nirc_record* __restrict__ recs,
                                                           float* __restrict__ dirs, float* __restrict__ targets,
-                                                          unsigned long long* __restrict__ work) {
+                                                          unsigned long long* __restrict__ work, uint32_t env_mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
     __shared__ uint32_t s_nlights;
@@ -751,7 +764,12 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_gen_train(const SceneHeader* 
             }
         } else if (stage == kResidRay) {
             bool end;
-            if constexpr (kNee)  // target = L_ind: the first hit's emission is direct light (discarded)
+            if (env_mode) {  // light mode 2: one ray; target V L_env (1) or V (2, visibility cache)
+                sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+                L = make_float3(0.f, 0.f, 0.f);
+                if (prim < 0) L = env_mode == 2 ? make_float3(1.f, 1.f, 1.f) : env_radiance(scene_env(hd, gp, n_prims), d);
+                end = true;
+            } else if constexpr (kNee)  // target = L_ind: the first hit's emission is direct light (discarded)
                 end = path_segment_nee(tr, gp, lt, prim, t, o, d, beta, L, seg, max_depth, k0, k1, ti, 0u, sig, pb, 0u,
                                        first_emit, nullptr, 0, make_float3(0.f, 0.f, 0.f));
             else
@@ -806,7 +824,8 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig, uint32_t* count,
                                  cudaStream_t st, nirc_record* mv_rec, float4* mv_beta, ResidRow* mv_row) {
-    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
+    FrameArgs a{fd.width, fd.height, fd.n_cache,  fd.n_resid,
+                fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame, fd.light_mode == 2 ? 1u : 0u};
     const uint64_t P = (uint64_t)fd.width * fd.height;
     const MvOut mv{mv_rec, mv_beta, mv_row, P * fd.n_resid};
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
@@ -832,7 +851,7 @@ static cudaError_t launch_primary_bth_t(const nirc_handle* h, const SceneHeader*
 
 cudaError_t launch_primary_bth(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd, nirc_record* recs,
                                PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st) {
-    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame};
+    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame, 0u};
     const uint64_t P = (uint64_t)fd.width * fd.height;
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
@@ -844,7 +863,7 @@ template <bool kNee>
 static cudaError_t launch_gen_train_t(const nirc_handle* h, const SceneHeader* hd, const Prim* gp, uint32_t n_prims,
                                       uint32_t W, uint32_t H, uint64_t T, uint32_t frame, uint64_t seed,
                                       uint32_t max_depth, nirc_record* recs, float* dirs, float* targets,
-                                      cudaStream_t st) {
+                                      uint32_t env_mode, cudaStream_t st) {
     const size_t smem = pt_smem(n_prims);
     uint32_t grid = 1;
     cudaError_t e = persistent_grid(k_gen_train<kNee>, smem, T, h->num_sms, &grid);
@@ -852,7 +871,8 @@ static cudaError_t launch_gen_train_t(const nirc_handle* h, const SceneHeader* h
     e = cudaMemsetAsync(h->work_counter + 1, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_gen_train<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
-                                                      max_depth, recs, dirs, targets, h->work_counter + 1);
+                                                      max_depth, recs, dirs, targets, h->work_counter + 1,
+                                                      env_mode);
     return cudaGetLastError();
 }
 
@@ -862,8 +882,11 @@ cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));
     if (light_mode == 1)
-        return launch_gen_train_t<true>(h, hd, gp, n_prims, W, H, T, frame, seed, max_depth, recs, dirs, targets, st);
-    return launch_gen_train_t<false>(h, hd, gp, n_prims, W, H, T, frame, seed, max_depth, recs, dirs, targets, st);
+        return launch_gen_train_t<true>(h, hd, gp, n_prims, W, H, T, frame, seed, max_depth, recs, dirs, targets, 0u,
+                                        st);
+    const uint32_t env_mode = light_mode == 2 ? (h->shape.vis ? 2u : 1u) : 0u;
+    return launch_gen_train_t<false>(h, hd, gp, n_prims, W, H, T, frame, seed, max_depth, recs, dirs, targets,
+                                     env_mode, st);
 }
 
 }  // namespace nirc

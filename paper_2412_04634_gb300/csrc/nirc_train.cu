@@ -260,22 +260,31 @@ __global__ void __launch_bounds__(kTrainThreads, 2)
         float lt = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const bool clamped = !(z[c] <= z_clamp);
-            const float nv = expf(clamped ? z_clamp : z[c]);
+            // radiance: n = exp(min(z, clamp)), dn/dz = n below the clamp; visibility: V = sigmoid(z), dV/dz = V (1 - V)
+            const bool clamped = !s.vis && !(z[c] <= z_clamp);
+            const float nv = out_act(s.vis, z[c], z_clamp);
+            const float dact = s.vis ? nv * (1.f - nv) : (clamped ? 0.f : nv);
             const float f = in_range ? __ldg(targets + 3 * t + c) : 0.f;
             float dz = 0.f;
             if (kind == kLossUpstream) {
                 // f holds dL/dn; the accumulated value is sum dL/dn * n
                 if (valid) {
                     lt += f * nv;
-                    dz = clamped ? 0.f : f * nv;
+                    dz = f * dact;
+                }
+            } else if (s.vis) {
+                // visibility: plain L2, (f - V)^2
+                const float diff = f - nv;
+                if (valid) {
+                    lt += diff * diff * scale;
+                    dz = -2.f * diff * scale * dact;
                 }
             } else {
                 const float den = nv * nv + loss_eps;
                 const float diff = f - nv;
                 if (valid) {
                     lt += diff * diff / den * scale;
-                    dz = clamped ? 0.f : -2.f * diff / den * scale * nv;
+                    dz = -2.f * diff / den * scale * dact;
                 }
             }
             if (in_range) tp.dz[(uint64_t)c * tp.dz_ld + t] = dz;

@@ -22,6 +22,7 @@ NIRC_OK, NIRC_ERR_INVALID, NIRC_ERR_OOM, NIRC_ERR_BUDGET, NIRC_ERR_CUDA, NIRC_ER
 NIRC_FP32_SIMT, NIRC_FP16_TC, NIRC_BF16_TC, NIRC_FP8_E4M3_TC = range(4)
 NIRC_INPUT_FREQ, NIRC_INPUT_SH = range(2)
 NIRC_EST_TWO_LEVEL, NIRC_EST_BIASED_BTH, NIRC_EST_MULTI_VERTEX = range(3)
+NIRC_OUT_RADIANCE, NIRC_OUT_VISIBILITY = range(2)
 NIRC_MAX_PRIMS = 1024
 
 
@@ -40,7 +41,7 @@ class nirc_config(ctypes.Structure):
         ("hidden_layers", ctypes.c_uint32), ("precision", ctypes.c_uint32),
         ("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
         ("adam_eps", ctypes.c_float), ("loss_eps", ctypes.c_float), ("z_clamp", ctypes.c_float),
-        ("input_encoding", ctypes.c_uint32),
+        ("input_encoding", ctypes.c_uint32), ("output", ctypes.c_uint32),
     ]
 
 
@@ -176,7 +177,7 @@ def make_config(cfg: scenes.NetConfig, precision: int = NIRC_FP32_SIMT) -> nirc_
     return nirc_config(cfg.pos_encoding, cfg.hash_levels, cfg.feats_per_level, cfg.log2_table, cfg.base_res,
                        cfg.growth, cfg.freq_octaves, cfg.width, cfg.hidden_layers, precision,
                        cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps, cfg.loss_eps, cfg.z_clamp,
-                       getattr(cfg, "input_encoding", 0))
+                       getattr(cfg, "input_encoding", 0), getattr(cfg, "output", 0))
 
 
 def frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode=0,

@@ -94,6 +94,6 @@ def test_struct_layouts(N):
     assert ctypes.sizeof(N.nirc_completion) == 48
     assert ctypes.sizeof(N.nirc_server_config) == 24
     assert ctypes.sizeof(N.nirc_frame_desc) == 72
-    assert ctypes.sizeof(N.nirc_config) == 68
+    assert ctypes.sizeof(N.nirc_config) == 72
     assert scenes.RECORD_DTYPE.itemsize == 64
     assert scenes.PRIM_DTYPE.itemsize == 96 and scenes.HEADER_DTYPE.itemsize == 96
