@@ -44,6 +44,10 @@ WORKLOAD_SH = ("1080p dynamic Cornell family (256 prims, GGX), the paper's NIRC 
 
 def workload_name(args):
     name = WORKLOAD_SH if getattr(args, "input", "freq") == "sh" else WORKLOAD
+    if getattr(args, "scene", "cornell") == "env":
+        name = ("1080p outdoor scene (ground + 255 spheres/quads, GGX) under a procedural 6 x 64^2 cube-map sky, "
+                "direct environment light (light mode 2), hash-grid cache 16x2 T=2^19, MLP 64x4, N=16 M=1, "
+                f"65536 train samples/frame, {getattr(args, 'output', 'radiance')} cache output")
     if getattr(args, "estimator", "two_level") == "bth":
         name += "; biased estimator (Balanced Termination Heuristic, N cache samples at the stopping vertex, M=0)"
     elif getattr(args, "estimator", "two_level") == "mv":
@@ -86,6 +90,11 @@ def parse_args():
                     help="frame: the 1080p frame step (default); train: the training step alone on "
                          "2^16 / 2^18 / 2^20 samples of the analytic radiance field; serve: the frame-request "
                          "server on a Poisson stream of mixed-resolution requests over 8 resident scenes")
+    ap.add_argument("--scene", choices=["cornell", "env"], default="cornell",
+                    help="env: an outdoor scene under a cube-map sky with direct environment light (light mode 2), "
+                         "the Neural Visibility Cache workload")
+    ap.add_argument("--output", choices=["radiance", "visibility"], default="radiance",
+                    help="cache output: radiance (exp) or visibility (sigmoid, the Neural Visibility Cache)")
     ap.add_argument("--input", choices=["freq", "sh"], default="freq",
                     help="network input of the frame workload: frequency encodings of direction and normal with "
                          "the 16-level hash grid (default), or the paper's (12-level hash grid, spherical "
@@ -97,7 +106,7 @@ def parse_args():
                          "each residual path (--n-cache2 / --n-cache3 cache samples there)")
     ap.add_argument("--n-cache2", type=int, default=5)
     ap.add_argument("--n-cache3", type=int, default=4)
-    ap.add_argument("--light-mode", type=int, choices=[0, 1], default=0,
+    ap.add_argument("--light-mode", type=int, choices=[0, 1, 2], default=0,
                     help="1: the cache carries L_ind, direct light by NEE + MIS (frame and serve workloads)")
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
@@ -186,10 +195,17 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 
 def build_workload(args, seed_offset=0):
+    import dataclasses
     W, H = args.width, args.height
-    base = scenes.cornell_scene(W, H, seed=1 + seed_offset, n_prims=args.prims, glossy=True, moving_emitter=True)
-    frames = [scenes.scene_at_frame(base, f) for f in range(60)]
+    if getattr(args, "scene", "cornell") == "env":
+        sc = scenes.env_scene(W, H, seed=1 + seed_offset, n_prims=args.prims, env_size=64)
+        frames = [sc] * 60
+    else:
+        base = scenes.cornell_scene(W, H, seed=1 + seed_offset, n_prims=args.prims, glossy=True, moving_emitter=True)
+        frames = [scenes.scene_at_frame(base, f) for f in range(60)]
     cfg = scenes.config_paper_1080p() if getattr(args, "input", "freq") == "sh" else scenes.config_1080p()
+    if getattr(args, "output", "radiance") == "visibility":
+        cfg = dataclasses.replace(cfg, output=scenes.OUT_VISIBILITY)
     params = scenes.init_params(cfg, 1 + seed_offset)
     return cfg, params, frames
 
@@ -269,7 +285,9 @@ class FrameRunner:
         ref = torch.zeros((self.P, 4), device=self.dev)
         tmp = torch.empty((self.P, 4), device=self.dev)
         for k in range(n):
-            d = N.frame_desc(self.W, self.H, 0, per, 16, 1000 + k, self.seed, self.n_prims, cache_mode=1)
+            # light mode 2 estimates direct environment light only: its reference does the same
+            d = N.frame_desc(self.W, self.H, 0, per, 16, 1000 + k, self.seed, self.n_prims, cache_mode=1,
+                             light_mode=2 if a.light_mode == 2 else 0)
             N.nirc_estimate_frame(self.cache.h, self.scene_dev[frame_index], d, tmp)
             ref += tmp
         ref /= n
@@ -485,6 +503,7 @@ def run_ours(args):
                    "frames": f"{first}..{first + args.steps - 1} (mod 60)",
                    "l2": "no flush: per-frame working set (~0.6 GB of records, rows, images, tables) > 129 MB L2",
                    "light_mode": args.light_mode, "estimator": args.estimator, "input": args.input,
+                   "scene": args.scene, "output": args.output,
                    "parallelism": f"replicas x{world}"},
         "p50_ms": float(np.percentile(res["step_ms"], 50)), "p99_ms": float(np.percentile(res["step_ms"], 99)),
         "frame_mrse": res["mrse"], "mrse_reference": f"{ref_spp} spp path tracing, depth 16, frame {last_frame}",
@@ -512,7 +531,7 @@ def oracle_step(O, cfg, params64, m, v, blob, args, frame, pix, T_s, seed):
                   estimator=estimator_code(args), n_cache2=n2, n_cache3=n3)
     est = O.estimate(cfg, params64, blob, fd, pixels=pix)
     recs, dirs, tg, _ = O.gen_train(blob, W, H, T_s, frame, seed, args.depth, scenes.RECORD_DTYPE,
-                                    light_mode=args.light_mode)
+                                    light_mode=args.light_mode, visibility=int(cfg.output == scenes.OUT_VISIBILITY))
     loss, g = O.loss_grad(cfg, params64, recs, dirs, tg)
     O.adam_step(params64, m, v, g, 1, cfg.lr, cfg.beta1, cfg.beta2, cfg.adam_eps)
     O.mrse(est["pixel"], est["pixel"])
@@ -848,6 +867,8 @@ def main():
     args = parse_args()
     if args.estimator == "bth":
         args.n_resid = 0  # the biased estimator has no residual level
+    if args.scene == "env":
+        args.light_mode = 2  # direct environment light
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "train":
