@@ -58,7 +58,15 @@ __host__ __device__ inline uint32_t off_w0pix() { return 0; }
 __host__ __device__ inline uint32_t off_w0dir() { return 8192; }
 __host__ __device__ inline uint32_t off_wh(uint32_t l) { return 16384 + 8192 * l; }
 __host__ __device__ inline uint32_t off_wout(uint32_t hidden) { return 16384 + 8192 * (hidden - 1); }
-__host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_wout(hidden) + 2048; }
+// Biases as MMA operands: slot j (hidden layer j + 1, the output layer last)
+// is K columns 16 (j % 4) .. + 15 of 64 x 64 tile j / 4; column 0 holds the
+// 16-bit rounding b_hi of the bias, column 1 the remainder b_lo = b - b_hi,
+// so that the MMA against an all-rows [1, 1, 0, ...] operand adds b to the
+// accumulator with ~22 significant bits.  Then that 8-row ones atom.
+__host__ __device__ inline uint32_t n_btiles(uint32_t hidden) { return (hidden + 3) / 4; }
+__host__ __device__ inline uint32_t off_bmma(uint32_t hidden) { return off_wout(hidden) + 2048; }
+__host__ __device__ inline uint32_t off_ones(uint32_t hidden) { return off_bmma(hidden) + 8192 * n_btiles(hidden); }
+__host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_ones(hidden) + 1024; }
 __host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidden - 1) * 64 + 16; }
 // FP8 weight scales s_w of the hidden layers (16 floats)
 __host__ __device__ inline uint32_t off_scales(uint32_t hidden) { return off_bias(hidden) + n_bias(hidden) * 4; }
@@ -100,7 +108,7 @@ __global__ void k_amax_roll(uint32_t* buf, uint32_t n) {
 }
 
 constexpr uint32_t kMiscBytes = 256;     // mbarriers, TMEM holder, abort flags, FP8 scales and amax
-constexpr uint32_t kWgStride = 35840;  // A 16 KB | H 16 KB | contributions 2 KB | 2 carry slots 128 B (1 KB rounded)
+constexpr uint32_t kWgStride = 35328;  // A 16 KB | H 16 KB | contributions 2 KB | carry slots and warp partials (512 B)
 constexpr uint32_t kOffA = 0, kOffH = 16384, kOffContrib = 32768, kOffCarry = 34816;
 
 template <uint32_t AB>
@@ -156,6 +164,39 @@ __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_
         if (c < 3) v = params[64 * n_in + 64 + (uint64_t)(H - 1) * (64 * 64 + 64) + 3 * 64 + c];
     }
     reinterpret_cast<float*>(img + tcimg::off_bias(H))[j] = v;
+}
+
+// Bias tiles and the ones atom of the weight image (after k_repack_tc has
+// written the FP32 biases): one thread per 16-bit element.
+template <uint32_t AB>
+__global__ void k_repack_bias_mma(uint32_t H, uint8_t* __restrict__ img) {
+    const uint32_t n_tile = 64 * 64 * tcimg::n_btiles(H);
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const float* fb = reinterpret_cast<const float*>(img + tcimg::off_bias(H));
+    auto bits = [](float v) -> uint16_t {
+        return AB == 1 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+    };
+    auto back = [](uint16_t b) -> float {
+        return AB == 1 ? __bfloat162float(__ushort_as_bfloat16(b)) : __half2float(__ushort_as_half(b));
+    };
+    if (idx < n_tile) {
+        const uint32_t tile = idx / 4096, n = (idx % 4096) / 64, k = idx % 64;
+        const uint32_t j = 4 * tile + k / 16, kk = k % 16;
+        uint16_t v = 0;
+        if (j < H && kk < 2) {
+            float b = 0.f;
+            if (j + 1 < H) b = fb[64 + j * 64 + n];              // hidden layer j + 1
+            else if (n < 3) b = fb[64 + (H - 1) * 64 + n];       // output layer
+            const uint16_t hi = bits(b);
+            v = kk == 0 ? hi : bits(b - back(hi));
+        }
+        *reinterpret_cast<uint16_t*>(img + tcimg::off_bmma(H) + tile * 8192 + tc::sw128_offset(n, k)) = v;
+        return;
+    }
+    const uint32_t o = idx - n_tile;
+    if (o >= 8 * 64) return;
+    const uint32_t r = o / 64, k = o % 64;
+    *reinterpret_cast<uint16_t*>(img + tcimg::off_ones(H) + tc::sw128_offset(r, k)) = k < 2 ? bits(1.f) : 0;
 }
 
 struct TcArgs {
@@ -427,6 +468,17 @@ __global__ void __launch_bounds__(640, 1)
             tc::mma_commit(mbar);
         }
     };
+    // 4 K-steps, then the bias slot j as one more K = 16 step against the ones atom
+    const uint32_t ones = sbase + tcimg::off_ones(a.s.hidden), bmma = sbase + tcimg::off_bmma(a.s.hidden);
+    auto issue_k64_bias = [&](uint32_t a_tile, uint32_t b_tile, uint32_t idesc, uint32_t j) {
+        if (t == 0 && !*abort_flag) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (uint32_t s = 0; s < 4; ++s) tc::mma_f16(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), idesc, s);
+            tc::mma_f16(tmem, tc::sdesc_rep8(ones), tc::sdesc(bmma + 8192u * (j >> 2) + 32u * (j & 3u)), idesc, 1);
+            tc::mma_commit(mbar);
+        }
+    };
     auto issue_k64_e4m3 = [&](uint32_t a_tile, uint32_t b_tile) {
         if (t == 0 && !*abort_flag) {
             tc::fence_after_sync();
@@ -624,8 +676,9 @@ __global__ void __launch_bounds__(640, 1)
             }
             wait_mma();
             for (uint32_t l = 0; l < a.s.hidden; ++l) {
-                // epilogue of layer l (l = 0: h_pix already holds b0), then the MMAs of layer l + 1
-                const float* bl = l == 0 ? nullptr : bias + 64 + (l - 1) * 64;
+                // epilogue of layer l (l = 0: h_pix already holds b0; 16-bit hidden layers: the
+                // bias came with the MMA), then the MMAs of layer l + 1
+                const float* bl = (l == 0 || !kF8) ? nullptr : bias + 64 + (l - 1) * 64;
                 const bool next_hidden = l + 1 < a.s.hidden;
                 if (kSh && l == 0) {
                     // layer 0 of the paper's input: + h_pix of the row's pixel (H row pl)
@@ -651,9 +704,9 @@ __global__ void __launch_bounds__(640, 1)
                 sync_wg();
                 if (next_hidden) {
                     if constexpr (kF8) issue_k64_e4m3(tA, sbase + tcimg::off_wh(l));
-                    else issue_k64(tA, sbase + tcimg::off_wh(l), id64);
+                    else issue_k64_bias(tA, sbase + tcimg::off_wh(l), id64, l);
                 } else {
-                    issue_k64(tA, wout, id16);
+                    issue_k64_bias(tA, wout, id16, a.s.hidden - 1u);
                 }
                 wait_mma();
             }
@@ -662,11 +715,10 @@ __global__ void __launch_bounds__(640, 1)
                 uint32_t v[4];
                 tc::tmem_ld4(tmem_row, v);
                 tc::tmem_wait_ld();
-                const float* bo = bias + 64 + (a.s.hidden - 1) * 64;
-                const bool vis = a.s.vis;
-                nv.x = out_act(vis, __uint_as_float(v[0]) + bo[0], a.z_clamp);
-                nv.y = out_act(vis, __uint_as_float(v[1]) + bo[1], a.z_clamp);
-                nv.z = out_act(vis, __uint_as_float(v[2]) + bo[2], a.z_clamp);
+                const bool vis = a.s.vis;  // the output bias came with the MMA
+                nv.x = out_act(vis, __uint_as_float(v[0]), a.z_clamp);
+                nv.y = out_act(vis, __uint_as_float(v[1]), a.z_clamp);
+                nv.z = out_act(vis, __uint_as_float(v[2]), a.z_clamp);
                 if (a.env_hd && ok) {  // visibility cache: n = V L_env(w)
                     const float3 le = env_radiance(env_from(a.env_hd, a.env_nprims), wi);
                     nv.x *= le.x;
@@ -821,16 +873,21 @@ cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
     const uint32_t H = h->shape.hidden;
     const uint32_t n = 64 * 64 * (2 + (H - 1)) + 16 * 64 + tcimg::n_bias(H);
     uint8_t* img = reinterpret_cast<uint8_t*>(h->packed_tc);
+    const uint32_t nb = 64 * 64 * tcimg::n_btiles(H) + 8 * 64;
     if (h->cfg.precision == NIRC_BF16_TC) {
         k_repack_tc<1><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        k_repack_bias_mma<1><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
     } else if (h->cfg.precision == NIRC_FP8_E4M3_TC) {
         if (H > 1) k_weight_scales<<<H - 1, 256, 0, st>>>(h->shape, h->params, img);
         k_repack_tc<2><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
         // FP16 image for the launch that calibrates the activation scales
-        k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params,
-                                                       reinterpret_cast<uint8_t*>(h->packed_tc16));
+        uint8_t* img16 = reinterpret_cast<uint8_t*>(h->packed_tc16);
+        k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img16);
+        k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img16);
     } else {
         k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
     }
     return cudaGetLastError();
 }

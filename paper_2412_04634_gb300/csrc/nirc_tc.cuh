@@ -43,6 +43,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
+// Descriptor of an 8-row SWIZZLE_128B atom read as every 8-row group of an
+// M = 128 operand (stride between 8-row groups 0): all 128 rows repeat it.
+__device__ __forceinline__ uint64_t sdesc_rep8(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>(1u) << 16;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(2u) << 61;
+    return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulate, A/B type (0 = f16,
 // 1 = bf16), both K-major, M x N.
 __device__ __forceinline__ uint32_t idesc_f16(uint32_t ab_type, uint32_t M, uint32_t N) {
