@@ -108,8 +108,13 @@ __global__ void k_amax_roll(uint32_t* buf, uint32_t n) {
 }
 
 constexpr uint32_t kMiscBytes = 256;     // mbarriers, TMEM holder, abort flags, FP8 scales and amax
-constexpr uint32_t kWgStride = 35328;  // A 16 KB | H 16 KB | contributions 2 KB | carry slots and warp partials (512 B)
-constexpr uint32_t kOffA = 0, kOffH = 16384, kOffContrib = 32768, kOffCarry = 34816;
+// Per warpgroup: the two swizzled operand tiles (A 16 KB | H 16 KB, 1024-byte
+// aligned), and apart from them the small arrays (contributions 2 KB | carry
+// slots and warp partials 512 B).
+constexpr uint32_t kWgStride = 32768;
+constexpr uint32_t kOffA = 0, kOffH = 16384;
+constexpr uint32_t kSmallStride = 2560;
+constexpr uint32_t kOffContrib = 0, kOffCarry = 2048;
 
 template <uint32_t AB>
 __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_t* __restrict__ img) {
@@ -386,10 +391,11 @@ __global__ void __launch_bounds__(640, 1)
     const uint32_t n_wg = blockDim.x >> 7;
     const uint32_t wg = threadIdx.x >> 7, t = threadIdx.x & 127u, quarter = t >> 5;
     const uint32_t img_al = (a.img_bytes + 1023u) & ~1023u;
-    const uint32_t wgs = sbase + img_al + wg * kWgStride;  // this warpgroup's region (shared address)
-    uint8_t* wgg = gbase + img_al + wg * kWgStride;        // same, generic pointer
-    const uint32_t misc = sbase + img_al + n_wg * kWgStride;
-    uint8_t* miscg = gbase + img_al + n_wg * kWgStride;
+    const uint32_t wgs = sbase + img_al + wg * kWgStride;  // this warpgroup's operand tiles (shared address)
+    const uint32_t small_al = img_al + n_wg * kWgStride;
+    uint8_t* wgg = gbase + small_al + wg * kSmallStride;   // this warpgroup's small arrays (generic pointer)
+    const uint32_t misc = sbase + small_al + n_wg * kSmallStride;
+    uint8_t* miscg = gbase + small_al + n_wg * kSmallStride;
     const uint32_t mbar = misc + 8u * wg;
     volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(miscg + 64);
     volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(miscg + 80 + 4 * wg);
@@ -865,7 +871,7 @@ __global__ void __launch_bounds__(640, 1)
 }
 
 static size_t tc_smem_bytes(uint32_t img_bytes, uint32_t n_wg) {
-    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * kWgStride + kMiscBytes;
+    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * (kWgStride + kSmallStride) + kMiscBytes;
 }
 
 cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
