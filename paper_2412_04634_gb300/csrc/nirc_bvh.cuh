@@ -279,7 +279,6 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
         const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
         const uint32_t m = b.n_tree;
         uint32_t stack[kBvhStack];
-        float stack_t[kBvhStack];  // entry distance of each postponed subtree's box
         int sp = 0;
         uint32_t node = b.root;
         for (uint32_t visits = 0; visits < 4 * n + 64; ++visits) {
@@ -309,10 +308,7 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
                 }
                 if (h0 && h1) {
                     const bool first0 = t0 <= t1;
-                    if (sp < kBvhStack) {
-                        stack[sp] = first0 ? c1 : c0;
-                        stack_t[sp++] = first0 ? t1 : t0;
-                    }
+                    if (sp < kBvhStack) stack[sp++] = first0 ? c1 : c0;
                     node = first0 ? c0 : c1;
                     continue;
                 }
@@ -321,10 +317,6 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
                     continue;
                 }
             }
-            // next postponed subtree whose box still starts before the nearest hit
-            // (the same bound box_entry applies: a box is inside its parent's, and a
-            // hit lies inside its primitive's box, so nothing skipped can win)
-            while (sp > 0 && stack_t[sp - 1] > best * 1.00001f + 1e-6f) --sp;
             if (sp == 0) break;
             node = stack[--sp];
         }
