@@ -184,3 +184,21 @@ def test_tc_fp8_delayed_scaling_is_deterministic(N):
     lc1, lc2 = runs[0][1][1], runs[0][1][2]
     scale = max(np.abs(lc1).max(), 1e-30)
     assert np.abs(lc1 - lc2).max() <= 0.1 * scale
+
+
+@pytest.mark.parametrize("hidden", [1, 2, 6, 8])
+def test_tc_hidden_layer_counts(N, oracle, hidden):
+    """Other depths: one hidden layer (only the output bias through the MMA),
+    two, and six / eight (two tiles of bias slots; the larger weight image
+    leaves room for four warpgroups per CTA)."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=16, log2_table=12, hidden_layers=hidden)
+    params = scenes.init_params(cfg, 9)
+    rng = np.random.default_rng(9)
+    params[:cfg.n_mlp_params] += rng.normal(0, 0.02, cfg.n_mlp_params).astype(np.float32)
+    params[cfg.n_mlp_params:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params).astype(np.float32)
+    sc = scenes.cornell_scene(48, 40, seed=5, n_prims=64, glossy=True)
+    g = _run_frame(N, cfg, params, sc, 48, 40, 8, 1, 4, 1, 2, precision=1, rows=True)
+    o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(48, 40, 8, 1, 4, 1, 2), rows=True)
+    err = _row_errors(g, o)
+    assert err.max() <= TC_TOL, float(err.max())
+    _compare_frames(g, o, tol=TC_TOL)
