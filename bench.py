@@ -74,6 +74,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "fp8"], default="fp16")
+    ap.add_argument("--train-precision", choices=["fp32", "fp16"], default="fp32",
+                    help="arithmetic of the training step's MLP forward and backward: FP32 SIMT kernels, or the "
+                         "tensor-core training kernel (FP16 operands, per-record scaled deltas)")
     ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
@@ -273,8 +276,9 @@ class FrameRunner:
         self.loss = torch.zeros(1, device=dev)
         self.mrse = torch.zeros(1, dtype=torch.float64, device=dev)
 
-    def set_precision(self, name):
+    def set_precision(self, name, train="fp32"):
         self.N.nirc_set_precision(self.cache.h, _precision_code(self.N, name))
+        self.N.nirc_set_train_precision(self.cache.h, _precision_code(self.N, train))
 
     def reference(self, frame_index, spp):
         """Plain path tracing (zero cache) of one frame, averaged over launches."""
@@ -455,7 +459,7 @@ def run_ours(args):
 
     run = FrameRunner(N, args, cfg, params, frames, dev, seed)
     ref, ref_spp = run.reference(last_frame, args.ref_spp)
-    run.set_precision(args.precision)
+    run.set_precision(args.precision, args.train_precision)
     for f in range(args.warmup):
         run.step(f, ref)
     res = run.timed(ref, first, args.steps, stream, ClockSampler(gpu_id))
@@ -504,6 +508,7 @@ def run_ours(args):
         "config": {"workload": workload_name(args), "width": args.width, "height": args.height, "n_cache": args.n_cache,
                    "n_resid": args.n_resid, "max_depth": args.depth, "prims": run.n_prims,
                    "train_samples": args.train,
+                   "train_precision": {"fp32": "fp32_simt", "fp16": "fp16_tc"}[args.train_precision],
                    "precision": {"fp32": "fp32_simt", "fp16": "fp16_tc", "bf16": "bf16_tc",
                                  "fp8": "fp8_e4m3_tc (hidden layers)"}[args.precision],
                    "frames": f"{first}..{first + args.steps - 1} (mod 60)",
@@ -666,6 +671,7 @@ def run_train_bench(args):
             cache = N.Cache(cfg)
             cache.set_params(params)
             N.nirc_set_train_mode(cache.h, mode == "stored", 1 << 15)
+            N.nirc_set_train_precision(cache.h, _precision_code(N, args.train_precision))
             loss = torch.zeros(1, device=dev)
             for _ in range(warm):
                 N.nirc_train_step(cache.h, rt, dt, tt, loss)
@@ -684,11 +690,14 @@ def run_train_bench(args):
             peak32 = fp32_alu_peak_tflops(props.multi_processor_count, 2070.0)
             fwd_n = 2 if mode == "recompute" else 1
             adam_bytes = cfg.n_params * 28 + cfg.n_hash_params * 2
+            tc = args.train_precision == "fp16"
             out[f"2^{logb} {mode}"] = {
                 "samples_per_s": B / (ms / 1e3), "ms_per_step": round(ms, 4),
                 "phase_ms": {k: round(v, 4) for k, v in ph.items()},
-                "fwd_tflops": round(fwd_n * fwd_f * B / (ph["train_fwd"] / 1e3) / 1e12, 2),
-                "bwd_tflops": round(dx_f * B / (ph["train_bwd"] / 1e3) / 1e12, 2),
+                # the tensor-core kernel runs forward and backward in one launch (timed as train_fwd)
+                "fwd_tflops": None if tc else round(fwd_n * fwd_f * B / (ph["train_fwd"] / 1e3) / 1e12, 2),
+                "bwd_tflops": None if tc else round(dx_f * B / (ph["train_bwd"] / 1e3) / 1e12, 2),
+                "fwd_bwd_tflops": round((fwd_f + dx_f) * B / (ph["train_fwd"] / 1e3) / 1e12, 2) if tc else None,
                 "gradw_tflops": round(dw_f * B / (ph["train_gradw"] / 1e3) / 1e12, 2),
                 "fp32_peak_tflops": round(peak32, 2),
                 "adam_gbs": round(adam_bytes / (ph["adam"] / 1e3) / 1e9, 1),
@@ -709,10 +718,13 @@ def run_train_bench(args):
         "metric": "NIRC training step (fused encoding+MLP fwd, bwd, dense Adam) samples/s",
         "value": first["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "steps": steps, "warmup": warm,
         "ms_per_step": first["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
+        "dtype": "f32" if args.train_precision == "fp32" else "f16",
+        "data": "synthetic",
         "config": {"workload": "training step alone: x ~ U[0,1]^3, directions and normals uniform on the sphere, "
                                "targets = 8 Gaussian lobes in w modulated by 3D sinusoids in x; hash grid 16x2 "
-                               "T=2^19, MLP 64x4; FP32 SIMT kernels",
+                               "T=2^19, MLP 64x4; " + ("FP32 SIMT kernels" if args.train_precision == "fp32" else
+                                                       "tensor-core forward+backward (FP16 operands), FP32 "
+                                                       "weight gradients and Adam"),
                    "flops_per_sample": {"fwd": fwd_f, "bwd_dx": dx_f, "dw": dw_f},
                    "adam_bytes_per_step": int(cfg.n_params * 28 + cfg.n_hash_params * 2),
                    "hbm_peak_gbs": hbm, "recompute_chunk": 1 << 15,

@@ -370,6 +370,25 @@ nirc_status nirc_train_step(nirc_handle* h, const nirc_record* d_records, const 
  * the float atomics in the gradient sums. */
 nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t recompute_chunk);
 
+/* Arithmetic of nirc_train_step's forward and backward through the MLP.
+ * NIRC_FP32_SIMT (default): FP32 on the CUDA cores.  NIRC_FP16_TC: one
+ * tensor-core kernel per chunk runs the forward (FP16 operands, FP32
+ * accumulation in tensor memory, the same weight image as the FP16 frame
+ * path), the loss of eq. 12, and the backward of every layer (FP16
+ * operands; each record's delta row is scaled by an exact power of two
+ * into FP16's range and scaled back after the MMA); the hash-table scatter
+ * (warp-aggregated atomics), the weight gradients from the stored
+ * activations and Adam stay FP32.  The hash-grid features come from the
+ * FP16 copy of the table, as in the FP16 frame path.  Weight gradients
+ * agree with the FP32 ones to about 1e-3 of their maximum, the hash-table
+ * gradient to about 1e-2 (relative L2 norm).  Applies to the relative L2
+ * loss only: nirc_query_bwd and deterministic training keep FP32.  Any
+ * other value returns NIRC_ERR_INVALID; NIRC_ERR_UNSUPPORTED for a network
+ * the kernel does not cover (hidden_layers > 8, or position features other
+ * than 24 or 32: the frequency encoding, or 12 or 16 hash-grid levels).
+ * Allocates the training weight image (about 100 KB) on first use. */
+nirc_status nirc_set_train_precision(nirc_handle* h, uint32_t precision);
+
 /* Deterministic training (on != 0): nirc_train_step and nirc_query_bwd give
  * bit-identical losses, gradients and weights for identical inputs and
  * state, however the GPU schedules the work (the default sums gradients with

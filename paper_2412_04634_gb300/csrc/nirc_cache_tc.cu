@@ -52,25 +52,6 @@
 
 namespace nirc {
 
-namespace tcimg {
-// Tensor-core weight image: 16-bit K-major swizzled matrices, then FP32 biases.
-__host__ __device__ inline uint32_t off_w0pix() { return 0; }
-__host__ __device__ inline uint32_t off_w0dir() { return 8192; }
-__host__ __device__ inline uint32_t off_wh(uint32_t l) { return 16384 + 8192 * l; }
-__host__ __device__ inline uint32_t off_wout(uint32_t hidden) { return 16384 + 8192 * (hidden - 1); }
-// Biases as MMA operands: slot j (hidden layer j + 1, the output layer last)
-// is K columns 16 (j % 4) .. + 15 of 64 x 64 tile j / 4; column 0 holds the
-// 16-bit rounding b_hi of the bias, column 1 the remainder b_lo = b - b_hi,
-// so that the MMA against an all-rows [1, 1, 0, ...] operand adds b to the
-// accumulator with ~22 significant bits.  Then that 8-row ones atom.
-__host__ __device__ inline uint32_t n_btiles(uint32_t hidden) { return (hidden + 3) / 4; }
-__host__ __device__ inline uint32_t off_bmma(uint32_t hidden) { return off_wout(hidden) + 2048; }
-__host__ __device__ inline uint32_t off_ones(uint32_t hidden) { return off_bmma(hidden) + 8192 * n_btiles(hidden); }
-__host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_ones(hidden) + 1024; }
-__host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidden - 1) * 64 + 16; }
-// FP8 weight scales s_w of the hidden layers (16 floats)
-__host__ __device__ inline uint32_t off_scales(uint32_t hidden) { return off_bias(hidden) + n_bias(hidden) * 4; }
-}  // namespace tcimg
 
 size_t tc_image_bytes(uint32_t hidden) { return tcimg::off_scales(hidden) + 64; }
 
@@ -215,31 +196,6 @@ struct TcArgs {
     NetShape s;
     GridParams g;
 };
-
-template <uint32_t AB>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-    return AB ? tc::pack_bf16(lo, hi) : tc::pack_f16(lo, hi);
-}
-template <uint32_t AB>
-__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
-    return AB ? tc::pack_relu_bf16(lo, hi) : tc::pack_relu_f16(lo, hi);
-}
-template <uint32_t AB>
-__device__ __forceinline__ uint16_t to16(float v) {
-    return AB ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
-}
-
-
-// Swizzled 16-byte chunk c (8 elements) of row r of a tile.
-__device__ __forceinline__ void sts_chunk(uint32_t tile, uint32_t r, uint32_t c, uint32_t d0, uint32_t d1, uint32_t d2,
-                                          uint32_t d3) {
-    tc::sts128(tile + (r >> 3) * 1024u + (r & 7u) * 128u + (((c ^ r) & 7u) << 4), d0, d1, d2, d3);
-}
-
-template <uint32_t AB>
-__device__ __forceinline__ void sts_chunk8(uint32_t tile, uint32_t r, uint32_t c, const float* y) {
-    sts_chunk(tile, r, c, pack2<AB>(y[0], y[1]), pack2<AB>(y[2], y[3]), pack2<AB>(y[4], y[5]), pack2<AB>(y[6], y[7]));
-}
 
 // Epilogue of one layer for row r: 64 accumulators from TMEM (two halves of
 // 32 columns), times `mul` (kMul: the FP8 scales s_w s_a of the layer),
@@ -875,6 +831,9 @@ static size_t tc_smem_bytes(uint32_t img_bytes, uint32_t n_wg) {
 }
 
 cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
+    // the tensor-core training image follows the same weights
+    cudaError_t et = launch_repack_train(h, st);
+    if (et != cudaSuccess) return et;
     if (!h->packed_tc) return cudaSuccess;
     const uint32_t H = h->shape.hidden;
     const uint32_t n = 64 * 64 * (2 + (H - 1)) + 16 * 64 + tcimg::n_bias(H);
@@ -895,6 +854,15 @@ cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
         k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
         k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repack_fwd16(const nirc_handle* h, uint8_t* img, cudaStream_t st) {
+    const uint32_t H = h->shape.hidden;
+    const uint32_t n = 64 * 64 * (2 + (H - 1)) + 16 * 64 + tcimg::n_bias(H);
+    const uint32_t nb = 64 * 64 * tcimg::n_btiles(H) + 8 * 64;
+    k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+    k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
     return cudaGetLastError();
 }
 

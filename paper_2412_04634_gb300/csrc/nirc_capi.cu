@@ -458,6 +458,7 @@ nirc_status nirc_destroy(nirc_handle* h) {
     cudaFree(h->hash16);
     cudaFree(h->packed_tc);
     cudaFree(h->packed_tc16);
+    cudaFree(h->packed_train);
     cudaFree(h->fp8_amax);
     cudaFree(h->scratch);
     cudaFree(h->train_scratch);
@@ -722,6 +723,38 @@ nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t 
     }
     h->store_activations = store_activations ? 1 : 0;
     if (!store_activations) h->recompute_chunk = recompute_chunk;
+    return NIRC_OK;
+}
+
+nirc_status nirc_set_train_precision(nirc_handle* h, uint32_t precision) {
+    if (!h || (precision != NIRC_FP32_SIMT && precision != NIRC_FP16_TC)) {
+        set_error("nirc_set_train_precision: NULL handle or precision not NIRC_FP32_SIMT / NIRC_FP16_TC");
+        return NIRC_ERR_INVALID;
+    }
+    if (precision == NIRC_FP32_SIMT) {
+        if (h->packed_train) {
+            cudaError_t e = cudaDeviceSynchronize();
+            cudaFree(h->packed_train);
+            h->packed_train = nullptr;
+            if (e != cudaSuccess) return cuda_status(e, "nirc_set_train_precision");
+        }
+        return NIRC_OK;
+    }
+    if (!train_tc_shape_ok(h->shape)) {
+        set_error("nirc_set_train_precision: tensor-core training covers 1..8 hidden layers and 24 or 32 "
+                  "position features");
+        return NIRC_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!h->packed_train) e = cudaMalloc(&h->packed_train, train_tc_image_bytes(h->shape.hidden));
+    if (e == cudaSuccess) e = cudaMemset(h->packed_train, 0, train_tc_image_bytes(h->shape.hidden));
+    if (e == cudaSuccess) e = launch_repack_train(h, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        cudaFree(h->packed_train);
+        h->packed_train = nullptr;
+        return cuda_status(e, "nirc_set_train_precision");
+    }
     return NIRC_OK;
 }
 

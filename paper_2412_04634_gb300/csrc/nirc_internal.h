@@ -77,6 +77,7 @@ struct nirc_handle {
     void* packed_tc = nullptr;      // tensor-core operand images of the weights
     size_t packed_tc_bytes = 0;
     void* packed_tc16 = nullptr;    // FP16 image used to calibrate FP8 activation scales
+    void* packed_train = nullptr;   // tensor-core training image (FP16 forward and backward); NULL: FP32 training
     uint32_t* fp8_amax = nullptr;   // [0,8) activation amax history, [8,16) current launch (float bits)
     bool fp8_calibrated = false;    // history valid for the current weights
     uint32_t step = 0;              // Adam steps taken
@@ -169,6 +170,28 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
                             cudaStream_t st, CachePass pass = CachePass{}, EnvSource env = EnvSource{});
+
+// nirc_cache_tc.cu: the FP16 cache image (forward part of the training image)
+cudaError_t launch_repack_fwd16(const nirc_handle* h, uint8_t* img, cudaStream_t st);
+
+// nirc_train_tc.cu: the training step's forward and backward on the tensor cores
+// Training buffers of one chunk: encodings, activations and deltas as
+// [feature][ld] columns, dL/dz as [3][dz_ld].
+struct TrainPtrs {
+    float* e;      // [n_in][ld]
+    float* act;    // [hidden][64][ld]
+    float* delta;  // [hidden][64][ld]
+    uint64_t ld;
+    float* dz;     // [3][dz_ld]
+    uint64_t dz_ld;
+};
+size_t train_tc_image_bytes(uint32_t hidden);
+bool train_tc_shape_ok(const NetShape& s);
+bool train_tc_supported(const nirc_handle* h);
+cudaError_t launch_repack_train(const nirc_handle* h, cudaStream_t st);
+cudaError_t launch_train_tc(const nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
+                            uint64_t m, float scale, const TrainPtrs& tp, float* grad_table, float* loss_accum,
+                            cudaStream_t st);
 
 // nirc_train.cu
 size_t train_scratch_bytes(const nirc_handle* h, uint64_t n);

@@ -106,6 +106,32 @@ __device__ __forceinline__ void stage_weights(float* sw, const float* __restrict
     for (uint32_t i = threadIdx.x; i < n_floats / 4; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
+// Add (g0, g1) into the two features of table entry idx.  Lanes of the warp
+// holding the same entry are summed first; the lowest lane of each group
+// issues one 8-byte atomic.  Every lane of the warp must call this together
+// (the caller's loop is warp-uniform); lanes with valid == false contribute
+// nothing.
+__device__ __forceinline__ void scatter_pair(float* __restrict__ gt, uint32_t idx, bool valid, float g0, float g1) {
+    const uint32_t key = valid ? idx : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int lane = threadIdx.x & 31;
+    const unsigned groups = __reduce_max_sync(0xffffffffu, valid ? (unsigned)__popc(peers) : 1u);
+    float s0 = g0, s1 = g1;
+    unsigned rest = peers & ~(1u << lane);
+    for (unsigned i = 1; i < groups; ++i) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        rest &= rest - 1u;
+        const float a0 = __shfl_sync(0xffffffffu, g0, src);
+        const float a1 = __shfl_sync(0xffffffffu, g1, src);
+        if (src != lane) {
+            s0 += a0;
+            s1 += a1;
+        }
+    }
+    if (valid && lane == __ffs(peers) - 1)
+        atomicAdd(reinterpret_cast<float2*>(gt + 2 * (uint64_t)idx), make_float2(s0, s1));
+}
+
 struct Kahan3 {
     float3 s = make_float3(0.f, 0.f, 0.f);
     float3 c = make_float3(0.f, 0.f, 0.f);

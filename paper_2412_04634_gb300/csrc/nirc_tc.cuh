@@ -239,4 +239,54 @@ __device__ __forceinline__ float2 unpack2(uint32_t u) {
 }
 
 }  // namespace tc
+
+// Tensor-core weight image of the cache network (FP16/BF16/FP8 operands):
+// 16-bit K-major swizzled matrices, the bias operands of the MMAs, then FP32
+// biases and the FP8 weight scales.
+namespace tcimg {
+// Tensor-core weight image: 16-bit K-major swizzled matrices, then FP32 biases.
+__host__ __device__ inline uint32_t off_w0pix() { return 0; }
+__host__ __device__ inline uint32_t off_w0dir() { return 8192; }
+__host__ __device__ inline uint32_t off_wh(uint32_t l) { return 16384 + 8192 * l; }
+__host__ __device__ inline uint32_t off_wout(uint32_t hidden) { return 16384 + 8192 * (hidden - 1); }
+// Biases as MMA operands: slot j (hidden layer j + 1, the output layer last)
+// is K columns 16 (j % 4) .. + 15 of 64 x 64 tile j / 4; column 0 holds the
+// 16-bit rounding b_hi of the bias, column 1 the remainder b_lo = b - b_hi,
+// so that the MMA against an all-rows [1, 1, 0, ...] operand adds b to the
+// accumulator with ~22 significant bits.  Then that 8-row ones atom.
+__host__ __device__ inline uint32_t n_btiles(uint32_t hidden) { return (hidden + 3) / 4; }
+__host__ __device__ inline uint32_t off_bmma(uint32_t hidden) { return off_wout(hidden) + 2048; }
+__host__ __device__ inline uint32_t off_ones(uint32_t hidden) { return off_bmma(hidden) + 8192 * n_btiles(hidden); }
+__host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_ones(hidden) + 1024; }
+__host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidden - 1) * 64 + 16; }
+// FP8 weight scales s_w of the hidden layers (16 floats)
+__host__ __device__ inline uint32_t off_scales(uint32_t hidden) { return off_bias(hidden) + n_bias(hidden) * 4; }
+}  // namespace tcimg
+
+// 16-bit packing of A-tile rows (f16 or bf16).
+template <uint32_t AB>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    return AB ? tc::pack_bf16(lo, hi) : tc::pack_f16(lo, hi);
+}
+template <uint32_t AB>
+__device__ __forceinline__ uint32_t pack2_relu(float lo, float hi) {
+    return AB ? tc::pack_relu_bf16(lo, hi) : tc::pack_relu_f16(lo, hi);
+}
+template <uint32_t AB>
+__device__ __forceinline__ uint16_t to16(float v) {
+    return AB ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
+}
+
+
+// Swizzled 16-byte chunk c (8 elements) of row r of a tile.
+__device__ __forceinline__ void sts_chunk(uint32_t tile, uint32_t r, uint32_t c, uint32_t d0, uint32_t d1, uint32_t d2,
+                                          uint32_t d3) {
+    tc::sts128(tile + (r >> 3) * 1024u + (r & 7u) * 128u + (((c ^ r) & 7u) << 4), d0, d1, d2, d3);
+}
+
+template <uint32_t AB>
+__device__ __forceinline__ void sts_chunk8(uint32_t tile, uint32_t r, uint32_t c, const float* y) {
+    sts_chunk(tile, r, c, pack2<AB>(y[0], y[1]), pack2<AB>(y[2], y[3]), pack2<AB>(y[4], y[5]), pack2<AB>(y[6], y[7]));
+}
+
 }  // namespace nirc

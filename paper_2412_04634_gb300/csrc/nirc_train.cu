@@ -62,14 +62,6 @@ constexpr int kGradThreads = 352;  // 16 x 22 tiles of 4 x 4
 // whole batch when stored, one chunk when recomputed); dz covers the whole
 // batch with its own leading dimension, already offset to the launch's first
 // sample.
-struct TrainPtrs {
-    float* e;      // [n_in][ld]
-    float* act;    // [hidden][64][ld]
-    float* delta;  // [hidden][64][ld]
-    uint64_t ld;
-    float* dz;     // [3][dz_ld]
-    uint64_t dz_ld;
-};
 
 enum LossKind : int {
     kLossRelL2 = 0,    // eq. 12 against targets, valid records only
@@ -303,32 +295,6 @@ __global__ void __launch_bounds__(kTrainThreads, 2)
         if (loss_part) loss_part[blockIdx.x] = b;
         else if (loss_accum) atomicAdd(loss_accum, b);
     }
-}
-
-// Add (g0, g1) into the two features of table entry idx.  Lanes of the warp
-// holding the same entry are summed first; the lowest lane of each group
-// issues one 8-byte atomic.  Every lane of the warp must call this together
-// (the caller's loop is warp-uniform); lanes with valid == false contribute
-// nothing.
-__device__ __forceinline__ void scatter_pair(float* __restrict__ gt, uint32_t idx, bool valid, float g0, float g1) {
-    const uint32_t key = valid ? idx : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int lane = threadIdx.x & 31;
-    const unsigned groups = __reduce_max_sync(0xffffffffu, valid ? (unsigned)__popc(peers) : 1u);
-    float s0 = g0, s1 = g1;
-    unsigned rest = peers & ~(1u << lane);
-    for (unsigned i = 1; i < groups; ++i) {
-        const int src = rest ? __ffs(rest) - 1 : lane;
-        rest &= rest - 1u;
-        const float a0 = __shfl_sync(0xffffffffu, g0, src);
-        const float a1 = __shfl_sync(0xffffffffu, g1, src);
-        if (src != lane) {
-            s0 += a0;
-            s1 += a1;
-        }
-    }
-    if (valid && lane == __ffs(peers) - 1)
-        atomicAdd(reinterpret_cast<float2*>(gt + 2 * (uint64_t)idx), make_float2(s0, s1));
 }
 
 __device__ __forceinline__ float dot64(const float* __restrict__ wrow, const float (&d)[64]) {
@@ -611,23 +577,34 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         uint64_t b = (m + kTrainThreads - 1) / kTrainThreads;
         return (uint32_t)(b > max_train_blocks(h) ? max_train_blocks(h) : b);
     };
-    // full-batch forward: loss and dL/dz, activations only when stored
-    timer_begin(h, NIRC_K_TRAIN_FWD, st);
-    const uint32_t fwd_blocks = blocks_for(n);
-    fwd<<<fwd_blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale, h->packed,
-                                                  table, recs, dirs, targets, n, tp, store ? 1 : 0, kind,
-                                                  h->loss_accum, det ? dp.loss_part : nullptr);
-    timer_end(h, NIRC_K_TRAIN_FWD, st);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (det) {
-        k_sum_rows<<<1, 32, 0, st>>>(dp.loss_part, fwd_blocks, 1, h->loss_accum, 0);
+    // tensor-core training (nirc_set_train_precision): forward, loss and
+    // backward of each chunk in one kernel, weight gradients as below
+    const bool tcmode = kind == kLossRelL2 && train_tc_supported(h);
+    if (!tcmode) {
+        // full-batch forward: loss and dL/dz, activations only when stored
+        timer_begin(h, NIRC_K_TRAIN_FWD, st);
+        const uint32_t fwd_blocks = blocks_for(n);
+        fwd<<<fwd_blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale, h->packed,
+                                                      table, recs, dirs, targets, n, tp, store ? 1 : 0, kind,
+                                                      h->loss_accum, det ? dp.loss_part : nullptr);
+        timer_end(h, NIRC_K_TRAIN_FWD, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (det) {
+            k_sum_rows<<<1, 32, 0, st>>>(dp.loss_part, fwd_blocks, 1, h->loss_accum, 0);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
     }
     for (uint64_t c0 = 0; c0 < n; c0 += chunk) {
         const uint64_t m = n - c0 < chunk ? n - c0 : chunk;
         TrainPtrs tc = tp;
         tc.dz = tp.dz + c0;
-        if (!store) {
+        if (tcmode) {
+            timer_begin(h, NIRC_K_TRAIN_FWD, st);
+            e = launch_train_tc(h, recs + c0, dirs + 3 * c0, targets + 3 * c0, m, scale, tc, h->grad + s.hash_off,
+                                h->loss_accum, st);
+            timer_end(h, NIRC_K_TRAIN_FWD, st);
+            if (e != cudaSuccess) return e;
+        } else if (!store) {
             timer_begin(h, NIRC_K_TRAIN_FWD, st);
             fwd<<<blocks_for(m), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
                                                              h->packed, table, recs + c0, dirs + 3 * c0,
@@ -635,12 +612,14 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             timer_end(h, NIRC_K_TRAIN_FWD, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        timer_begin(h, NIRC_K_TRAIN_BWD, st);
-        k_train_bwd<<<blocks_for(m), kTrainThreads, smem_b, st>>>(s, h->grid, h->packed, recs + c0, m, tc,
-                                                                 kind == kLossUpstream ? 1 : 0, h->grad + s.hash_off,
-                                                                 det_hash ? dp.de + c0 : nullptr, n, dp.lvl_max);
-        timer_end(h, NIRC_K_TRAIN_BWD, st);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (!tcmode) {
+            timer_begin(h, NIRC_K_TRAIN_BWD, st);
+            k_train_bwd<<<blocks_for(m), kTrainThreads, smem_b, st>>>(
+                s, h->grid, h->packed, recs + c0, m, tc, kind == kLossUpstream ? 1 : 0, h->grad + s.hash_off,
+                det_hash ? dp.de + c0 : nullptr, n, dp.lvl_max);
+            timer_end(h, NIRC_K_TRAIN_BWD, st);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
 
         // weight gradients, layer 0 = input layer
         GradJobs jobs;

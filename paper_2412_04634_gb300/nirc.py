@@ -107,6 +107,7 @@ def _load():
         "nirc_load_params": ([P, P, i32, P], st),
         "nirc_set_train_mode": ([P, i32, u64], st),
         "nirc_set_deterministic": ([P, i32], st),
+        "nirc_set_train_precision": ([P, u32], st),
         "nirc_query_bwd": ([P, P, P, P, u64, P, P, P], st),
         "nirc_get_params": ([P, P, i32, P], st),
         "nirc_get_grads": ([P, P, i32, P], st),
@@ -222,6 +223,10 @@ def nirc_load_params(h, params: torch.Tensor, stream=None):
 
 def nirc_set_train_mode(h, store_activations: bool = True, recompute_chunk: int = 1 << 15):
     _check(_lib.nirc_set_train_mode(h, 1 if store_activations else 0, recompute_chunk))
+
+
+def nirc_set_train_precision(h, precision: int):
+    _check(_lib.nirc_set_train_precision(h, precision))
 
 
 def nirc_set_deterministic(h, on: bool = True):

@@ -69,6 +69,7 @@ def test_bad_arguments_return_status(N):
     assert N.lib().nirc_query_bwd(None, None, None, None, 5, None, None, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_load_params(None, None, 0, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_set_train_mode(None, 1, 0) == N.NIRC_ERR_INVALID
+    assert N.lib().nirc_set_train_precision(None, 1) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_state_bytes(None) == 0
     assert N.lib().nirc_save_state(None, None, 0, None) == N.NIRC_ERR_INVALID
     assert N.lib().nirc_load_state(None, None, 0, None) == N.NIRC_ERR_INVALID
