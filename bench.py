@@ -74,7 +74,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "fp8"], default="fp16")
-    ap.add_argument("--train-precision", choices=["fp32", "fp16"], default="fp32",
+    ap.add_argument("--train-precision", choices=["fp32", "fp16"], default="fp16",
                     help="arithmetic of the training step's MLP forward and backward: FP32 SIMT kernels, or the "
                          "tensor-core training kernel (FP16 operands, per-record scaled deltas)")
     ap.add_argument("--compare-fp32", type=int, default=1)
