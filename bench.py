@@ -77,6 +77,9 @@ def parse_args():
     ap.add_argument("--train-precision", choices=["fp32", "fp16"], default="fp16",
                     help="arithmetic of the training step's MLP forward and backward: FP32 SIMT kernels, or the "
                          "tensor-core training kernel (FP16 operands, per-record scaled deltas)")
+    ap.add_argument("--overlap-records", type=int, default=1,
+                    help="1: generate each frame's training records on a second stream, concurrently with the "
+                         "frame estimate (they read only the scene); 0: one stream")
     ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
@@ -275,6 +278,7 @@ class FrameRunner:
         self.tgts = torch.empty((T, 3), device=dev)
         self.loss = torch.zeros(1, device=dev)
         self.mrse = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.side = torch.cuda.Stream(device=dev) if getattr(args, "overlap_records", 0) else None
 
     def set_precision(self, name, train="fp32"):
         self.N.nirc_set_precision(self.cache.h, _precision_code(self.N, name))
@@ -304,9 +308,20 @@ class FrameRunner:
         n2, n3 = later_vertex_samples(a)
         d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
                          light_mode=a.light_mode, estimator=estimator_code(a), n_cache2=n2, n_cache3=n3)
-        N.nirc_estimate_frame(h, sc, d, self.img)
-        N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs, self.dirs,
-                         self.tgts, light_mode=a.light_mode)
+        if self.side is not None:
+            # the records of frame f replace those the previous training step read, so the side
+            # stream first waits for everything enqueued so far; the step waits for the records
+            import torch
+            main = torch.cuda.current_stream(self.dev)
+            self.side.wait_stream(main)
+            N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs,
+                             self.dirs, self.tgts, stream=self.side, light_mode=a.light_mode)
+            N.nirc_estimate_frame(h, sc, d, self.img)
+            main.wait_stream(self.side)
+        else:
+            N.nirc_estimate_frame(h, sc, d, self.img)
+            N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs,
+                             self.dirs, self.tgts, light_mode=a.light_mode)
         N.nirc_train_step(h, self.recs, self.dirs, self.tgts, self.loss)
         N.nirc_frame_mrse(self.img, ref, self.mrse)
 
@@ -513,6 +528,8 @@ def run_ours(args):
                                  "fp8": "fp8_e4m3_tc (hidden layers)"}[args.precision],
                    "frames": f"{first}..{first + args.steps - 1} (mod 60)",
                    "l2": "no flush: per-frame working set (~0.6 GB of records, rows, images, tables) > 129 MB L2",
+                   "train_records_stream": "second stream, concurrent with the frame estimate (kernel_ms of "
+                                           "train_records spans the overlap)" if args.overlap_records else "main",
                    "light_mode": args.light_mode, "estimator": args.estimator, "input": args.input,
                    "scene": args.scene, "output": args.output,
                    "parallelism": f"replicas x{world}"},

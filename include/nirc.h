@@ -377,8 +377,10 @@ nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t 
  * path), the loss of eq. 12, and the backward of every layer (FP16
  * operands; each record's delta row is scaled by an exact power of two
  * into FP16's range and scaled back after the MMA); the hash-table scatter
- * (warp-aggregated atomics), the weight gradients from the stored
- * activations and Adam stay FP32.  The hash-grid features come from the
+ * (warp-aggregated atomics) and Adam stay FP32, and the weight gradients
+ * from the stored FP32 activations and deltas run as TF32 tensor-core GEMMs
+ * (cuBLAS, FP32 accumulation) for passes of 2^16 samples or more, FP32
+ * SIMT below.  The hash-grid features come from the
  * FP16 copy of the table, as in the FP16 frame path.  Weight gradients
  * agree with the FP32 ones to about 1e-3 of their maximum, the hash-table
  * gradient to about 1e-2 (relative L2 norm).  Applies to the relative L2

@@ -108,6 +108,9 @@ constexpr size_t kBlasWorkspace = 32u << 20;
 // Below this many samples per pass the hand-written k_grad_w is faster than
 // the library GEMM for these skinny shapes (64 x 72 outputs, K = samples).
 constexpr uint64_t kBlasMinSamples = 1ull << 18;
+// With TF32 tensor-core GEMMs (tensor-core training) the library is faster
+// from 2^16 samples per pass (0.17 vs 0.21 ms at 2^16, 0.13 vs 0.11 ms at 2^15).
+constexpr uint64_t kBlasMinSamplesTf32 = 1ull << 16;
 
 cudaError_t prepare_blas(nirc_handle* h) {
     if (h->blas) return cudaSuccess;
@@ -643,7 +646,7 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         if (gx > n_chunks) gx = n_chunks;
         if (gx < 1) gx = 1;
         timer_begin(h, NIRC_K_TRAIN_GRADW, st);
-        if (!det && m < kBlasMinSamples) {
+        if (!det && m < (tcmode ? kBlasMinSamplesTf32 : kBlasMinSamples)) {
             k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
         } else if (det) {
             k_grad_w<true><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
@@ -652,8 +655,15 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
                 k_sum_rows<<<(uint32_t)((s.n_mlp + 255) / 256), 256, 0, st>>>(dp.gw_part, gx, s.n_mlp, h->grad, 1);
             }
         } else {
-            // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t]
+            // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t];
+            // with tensor-core training the products run on the tensor cores in TF32 (10-bit
+            // mantissas, FP32 range and accumulation)
             cublasHandle_t bh = static_cast<cublasHandle_t>(h->blas);
+            if (cublasSetMathMode(bh, tcmode ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_PEDANTIC_MATH) !=
+                CUBLAS_STATUS_SUCCESS) {
+                timer_end(h, NIRC_K_TRAIN_GRADW, st);
+                return cudaErrorNotSupported;
+            }
             const float one = 1.f;
             for (uint32_t l = 0; l <= s.hidden; ++l) {
                 const GradJob& J = jobs.j[l];

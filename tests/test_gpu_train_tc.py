@@ -1,8 +1,8 @@
 """Tensor-core training (nirc_set_train_precision(NIRC_FP16_TC)): one
 kernel per chunk runs the forward with FP16 operands, the loss of eq. 12 and
 the backward with FP16 operands (deltas scaled per record by a power
-of two) on tcgen05; the weight gradients and the
-hash-table scatter stay FP32.
+of two) on tcgen05; the hash-table scatter stays FP32, the weight gradients
+are TF32 tensor-core GEMMs from 2^16 samples per pass.
 
 Checked against the oracle's FP64 loss and gradient on ragged batches with
 invalid rows, for the frequency input, the 16-level hash grid, the paper's
@@ -105,11 +105,12 @@ def _grad_errors(cfg, g, g_ref):
     return errs, l2, cos
 
 
-@pytest.mark.parametrize("name", list(CONFIGS))
-def test_tc_train_step_matches_oracle(N, oracle, name):
+@pytest.mark.parametrize("name,n", [(k, 5000) for k in CONFIGS] + [("hash16", (1 << 16) + 300)])
+def test_tc_train_step_matches_oracle(N, oracle, name, n):
+    """n = 5000: 39 tiles of 128 and a ragged tail of 8, weight gradients by
+    the FP32 SIMT kernel; n = 2^16 + 300: weight gradients by TF32 GEMMs."""
     cfg = CONFIGS[name]()
     params = _params(cfg, 11)
-    n = 5000  # 39 tiles of 128 and a ragged tail of 8
     recs, dirs, tg = _batch(cfg, n, 12)
     kink = _near_kink(oracle, cfg, params, recs, dirs, margin=KINK_MARGIN)
     recs["flags"][kink] = 0
