@@ -100,7 +100,6 @@ size_t train_scratch_bytes(const nirc_handle* h, uint64_t n) {
     const uint64_t c = chunk_of(h, n);
     uint64_t f = round64(3 * n + c * act_floats_per_sample(h->shape));
     if (h->deterministic) f += det_floats(h, n);
-    else f += round64(c);  // a vector of ones (bias gradients as a GEMV)
     return (size_t)f * sizeof(float) + 256;
 }
 
@@ -138,11 +137,6 @@ void release_blas(nirc_handle* h) {
     cudaFree(h->blas_ws);
     h->blas = nullptr;
     h->blas_ws = nullptr;
-}
-
-__global__ void k_fill(float* __restrict__ p, uint64_t n, float v) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        p[i] = v;
 }
 
 static TrainPtrs carve(void* base, const NetShape& s, uint64_t n, uint64_t chunk) {
@@ -455,6 +449,48 @@ struct GradJob {
     uint64_t ld_dl, ld_x;
     uint32_t out, in;
 };
+// Bias gradients of every layer in one launch: db[o] += sum_t delta[o][t]
+// over the m samples of a pass; row r of the grid walks layer jobs in order
+// (64 rows per hidden layer, `out` rows for the output layer), blockIdx.y
+// splits the samples, one float atomic per block and row.
+struct BiasRows {
+    const float* dl[kMaxHidden + 1];
+    uint32_t ld[kMaxHidden + 1];
+    float* gb[kMaxHidden + 1];
+    uint32_t out[kMaxHidden + 1];
+    uint32_t n_jobs;
+};
+
+__global__ void k_bias_grad(BiasRows br, uint64_t m, uint64_t per_block) {
+    uint32_t r = blockIdx.x, j = 0;
+    while (j < br.n_jobs && r >= br.out[j]) r -= br.out[j++];
+    if (j >= br.n_jobs) return;
+    const float* row = br.dl[j] + (uint64_t)r * br.ld[j];
+    const uint64_t t0 = (uint64_t)blockIdx.y * per_block;
+    const uint64_t t1 = t0 + per_block < m ? t0 + per_block : m;
+    float acc = 0.f;
+    uint64_t tv = t0;  // 16-byte loads where the row allows (per_block is a multiple of 4)
+    if ((reinterpret_cast<uintptr_t>(row) & 15u) == 0) {
+        const uint64_t nv = (t1 - t0) >> 2;
+        const float4* r4 = reinterpret_cast<const float4*>(row + t0);
+        for (uint64_t i = threadIdx.x; i < nv; i += blockDim.x) {
+            const float4 v = __ldg(r4 + i);
+            acc += (v.x + v.y) + (v.z + v.w);
+        }
+        tv = t0 + 4 * nv;
+    }
+    for (uint64_t t = tv + threadIdx.x; t < t1; t += blockDim.x) acc += row[t];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sum = 0.f;
+        for (uint32_t w = 0; w < blockDim.x / 32; ++w) sum += part[w];
+        atomicAdd(br.gb[j] + r, sum);
+    }
+}
+
 struct GradJobs {
     GradJob j[kMaxHidden + 1];
     float* part;     // deterministic mode: block b writes W/b of job l at
@@ -551,15 +587,11 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     const bool det_hash = det && s.hashgrid;
     DetPtrs dp{};
     if (det) dp = carve_det(h, h->train_scratch, n, chunk);
-    float* ones = det ? nullptr
-                      : reinterpret_cast<float*>(h->train_scratch) + round64(3 * n + chunk * act_floats_per_sample(s));
     cudaError_t e;
     if (!det) {
         if ((e = prepare_blas(h)) != cudaSuccess) return e;
         if (cublasSetStream(static_cast<cublasHandle_t>(h->blas), st) != CUBLAS_STATUS_SUCCESS)
             return cudaErrorNotSupported;
-        k_fill<<<(uint32_t)((chunk + 255) / 256 < 1024 ? (chunk + 255) / 256 : 1024), 256, 0, st>>>(ones, chunk, 1.f);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = cudaMemsetAsync(h->grad, 0, s.n_dev * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
@@ -665,16 +697,31 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
                 return cudaErrorNotSupported;
             }
             const float one = 1.f;
+            // (one GEMM per layer: a strided-batched GEMM over the hidden layers, tried, runs
+            // without split-K and takes 10x longer at 2^18 samples)
+            bool ok = true;
+            for (uint32_t l = 0; l <= s.hidden && ok; ++l) {
+                const GradJob& J = jobs.j[l];
+                ok = cublasSgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)J.in, (int)J.out, (int)m, &one, J.x, (int)J.ld_x,
+                                 J.dl, (int)J.ld_dl, &one, J.gw, (int)J.in) == CUBLAS_STATUS_SUCCESS;
+            }
+            if (!ok) {
+                timer_end(h, NIRC_K_TRAIN_GRADW, st);
+                return cudaErrorNotSupported;
+            }
+            BiasRows br;
+            uint32_t rows = 0;
             for (uint32_t l = 0; l <= s.hidden; ++l) {
                 const GradJob& J = jobs.j[l];
-                if (cublasSgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)J.in, (int)J.out, (int)m, &one, J.x, (int)J.ld_x,
-                                J.dl, (int)J.ld_dl, &one, J.gw, (int)J.in) != CUBLAS_STATUS_SUCCESS ||
-                    cublasSgemv(bh, CUBLAS_OP_T, (int)m, (int)J.out, &one, J.dl, (int)J.ld_dl, ones, 1, &one,
-                                J.gw + (uint64_t)J.out * J.in, 1) != CUBLAS_STATUS_SUCCESS) {
-                    timer_end(h, NIRC_K_TRAIN_GRADW, st);
-                    return cudaErrorNotSupported;
-                }
+                br.dl[l] = J.dl;
+                br.ld[l] = (uint32_t)J.ld_dl;
+                br.gb[l] = J.gw + (uint64_t)J.out * J.in;
+                br.out[l] = J.out;
+                rows += J.out;
             }
+            br.n_jobs = s.hidden + 1;
+            const uint64_t per_block = 16384;
+            k_bias_grad<<<dim3(rows, (uint32_t)((m + per_block - 1) / per_block)), 256, 0, st>>>(br, m, per_block);
         }
         timer_end(h, NIRC_K_TRAIN_GRADW, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

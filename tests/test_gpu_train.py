@@ -177,6 +177,31 @@ def test_recompute_matches_stored(N):
     assert np.abs(p1[strong] - p0[strong]).max() <= 1e-6
 
 
+def test_library_weight_gradients_match_simt(N):
+    """Passes of >= 2^18 samples take their weight gradients from cuBLAS
+    (one GEMM per layer, all biases in one reduction kernel); 2^17-sample
+    chunks of the same batch take them from k_grad_w: the two agree up to
+    the order of the sums."""
+    import torch
+    cfg = _hash_cfg(hidden=4)
+    params = scenes.init_params(cfg, 65)
+    n = (1 << 18) + 123
+    recs, dirs, tg = scenes.training_batch(n, seed=66)
+    recs["flags"][::17] = 0
+    rt, dt, tt = N.records_to_tensor(recs), torch.from_numpy(dirs).cuda(), torch.from_numpy(tg).cuda()
+    res = []
+    for store in (True, False):
+        cache = N.Cache(cfg)
+        cache.set_params(params)
+        N.nirc_set_train_mode(cache.h, store, 1 << 17)
+        N.nirc_train_step(cache.h, rt, dt, tt)
+        torch.cuda.synchronize()
+        res.append(cache.get_grads().numpy().astype(np.float64))
+        cache.close()
+    g_blas, g_simt = res
+    _assert_grad_close(cfg, g_blas, g_simt, tol=1e-5)
+
+
 def test_scatter_with_colliding_entries(N, oracle):
     """Many rows share a few positions, so whole warps hit the same table
     entries: the aggregated scatter must still add every contribution."""
