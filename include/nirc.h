@@ -424,10 +424,12 @@ nirc_status nirc_query_bwd(nirc_handle* h, const nirc_record* d_records, const f
 nirc_status nirc_frame_mrse(const float* d_img_rgba, const float* d_ref_rgba, uint64_t n_pixels, float eps,
                             double* d_out, void* stream);
 
-/* Kernel timers.  While enabled, every kernel the handle launches is
- * bracketed by CUDA events on its stream; nirc_timing_read waits for the
- * recorded events and returns the summed device time and launch count per
- * kernel class since the last enable.  Classes: */
+/* Kernel timers.  While enabled, each phase of the handle's work (one or
+ * more kernels) is bracketed by CUDA events on its stream; nirc_timing_read
+ * waits for the recorded events and returns, per kernel class since the
+ * last enable, the summed device time of its phases and the number of the
+ * library's own kernels they launched (cuBLAS kernels inside a phase count
+ * in its time, not in its launches).  Classes: */
 enum {
     NIRC_K_PATH_TRACE = 0,   /* camera hits, records, residual paths */
     NIRC_K_CACHE = 1,        /* cache integral (encodings, MLP, per-pixel sums) */

@@ -310,6 +310,7 @@ cudaError_t launch_cache_simt(const nirc_handle* h, const nirc_frame_desc& fd, c
     const float* table = h->params + h->shape.hash_off;
     kern<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(a, h->packed, table, recs, base, rows, beta,
                                                        reinterpret_cast<float4*>(out_rgba), lc, lr, sig, count, row_n);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
@@ -324,12 +325,14 @@ cudaError_t launch_query_simt(const nirc_handle* h, const nirc_record* recs, con
     const float* table = h->params + h->shape.hash_off;
     kern<<<(uint32_t)blocks, kSimtThreads, smem, st>>>(h->shape, h->grid, h->cfg.z_clamp, h->packed, table, recs, dirs,
                                                        n, out);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
 cudaError_t launch_repack_simt(const nirc_handle* h, cudaStream_t st) {
     const uint32_t n = h->shape.packed_floats;
     k_repack_simt<<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, h->packed);
+    count_kernels(h);
     return cudaGetLastError();
 }
 

@@ -841,18 +841,29 @@ cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
     const uint32_t nb = 64 * 64 * tcimg::n_btiles(H) + 8 * 64;
     if (h->cfg.precision == NIRC_BF16_TC) {
         k_repack_tc<1><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        count_kernels(h);
         k_repack_bias_mma<1><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
+        count_kernels(h);
     } else if (h->cfg.precision == NIRC_FP8_E4M3_TC) {
-        if (H > 1) k_weight_scales<<<H - 1, 256, 0, st>>>(h->shape, h->params, img);
+        if (H > 1) {
+            k_weight_scales<<<H - 1, 256, 0, st>>>(h->shape, h->params, img);
+            count_kernels(h);
+        }
         k_repack_tc<2><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        count_kernels(h);
         k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
+        count_kernels(h);
         // FP16 image for the launch that calibrates the activation scales
         uint8_t* img16 = reinterpret_cast<uint8_t*>(h->packed_tc16);
         k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img16);
+        count_kernels(h);
         k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img16);
+        count_kernels(h);
     } else {
         k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+        count_kernels(h);
         k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
+        count_kernels(h);
     }
     return cudaGetLastError();
 }
@@ -862,7 +873,9 @@ cudaError_t launch_repack_fwd16(const nirc_handle* h, uint8_t* img, cudaStream_t
     const uint32_t n = 64 * 64 * (2 + (H - 1)) + 16 * 64 + tcimg::n_bias(H);
     const uint32_t nb = 64 * 64 * tcimg::n_btiles(H) + 8 * 64;
     k_repack_tc<0><<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+    count_kernels(h);
     k_repack_bias_mma<0><<<(nb + 255) / 256, 256, 0, st>>>(H, img);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
@@ -934,6 +947,7 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     if (grid > (uint32_t)h->num_sms) grid = h->num_sms;
     const __half2* hash = reinterpret_cast<const __half2*>(h->hash16);
     const uint32_t threads = n_wg * 128;
+    count_kernels(h);  // the cache kernel; FP8 adds an amax roll (and a calibration pair) below
     if (h->cfg.precision == NIRC_BF16_TC)
         return launch_tc_instance<1, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba,
                                             lc, lr, sig, count, row_n, err, nullptr);
@@ -948,6 +962,7 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
         e = launch_tc_instance<0, true>(grid, threads, smem, st, a, h->packed_tc16, hash, recs, base, rows, beta, out_rgba,
                                         nullptr, nullptr, nullptr, nullptr, nullptr, err, amax);
         if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
+        count_kernels(h, 2);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const_cast<nirc_handle*>(h)->fp8_calibrated = true;
@@ -955,6 +970,7 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     e = launch_tc_instance<2, true>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba, lc, lr,
                                     sig, count, row_n, err, amax);
     if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
+    count_kernels(h);
     return e == cudaSuccess ? cudaGetLastError() : e;
 }
 

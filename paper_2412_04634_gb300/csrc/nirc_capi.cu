@@ -148,7 +148,7 @@ static void resolve_pending(nirc_handle* h) {
         float ms = 0.f;
         if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
             h->timing_ms[p.cls] += ms;
-            h->timing_launches[p.cls] += 1;
+            h->timing_launches[p.cls] += p.kernels;
         }
     }
     h->n_pending = 0;
@@ -160,6 +160,7 @@ void timer_begin(const nirc_handle* hc, int cls, cudaStream_t st) {
     if (h->n_pending >= kMaxPending) resolve_pending(h);
     auto& p = h->pending[h->n_pending];
     p.cls = cls;
+    p.k0 = h->n_kernels;
     p.start = h->event_pool[2 * h->n_pending];
     p.stop = h->event_pool[2 * h->n_pending + 1];
     cudaEventRecord(p.start, st);
@@ -169,7 +170,9 @@ void timer_end(const nirc_handle* hc, int cls, cudaStream_t st) {
     (void)cls;
     auto* h = const_cast<nirc_handle*>(hc);
     if (!h->timing || !h->pending) return;
-    cudaEventRecord(h->pending[h->n_pending].stop, st);
+    auto& p = h->pending[h->n_pending];
+    cudaEventRecord(p.stop, st);
+    p.kernels = h->n_kernels - p.k0;
     h->n_pending += 1;
 }
 
@@ -301,8 +304,10 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
                                       pass);
             outs[k - 2] = ok;
         }
-        if (e == cudaSuccess)
+        if (e == cudaSuccess) {
             e = launch_mv_accumulate(out, aux ? aux->lr : nullptr, outs[0], outs[1], P, fd.n_resid, st);
+            count_kernels(h);
+        }
     }
     timer_end(h, NIRC_K_CACHE, st);
     if (e == cudaSuccess && tc_any)

@@ -99,8 +99,10 @@ struct nirc_handle {
     struct Pending {
         int cls;
         cudaEvent_t start, stop;
+        uint64_t k0, kernels;  // n_kernels at the start; kernels launched in the interval
     };
     Pending* pending = nullptr;     // recorded, not yet read
+    mutable uint64_t n_kernels = 0; // kernels launched by the handle so far
     int n_pending = 0;
     cudaEvent_t* event_pool = nullptr;
     int n_pool = 0;
@@ -114,6 +116,9 @@ void set_error(const char* fmt, ...);
 nirc_status cuda_status(cudaError_t e, const char* what);
 
 // Bracket one kernel launch with timer events when timing is enabled.
+// Every kernel launch of the library is followed by count_kernels (the
+// timers report kernels per class, not intervals).
+inline void count_kernels(const nirc_handle* h, uint32_t k = 1) { h->n_kernels += k; }
 void timer_begin(const nirc_handle* h, int cls, cudaStream_t st);
 void timer_end(const nirc_handle* h, int cls, cudaStream_t st);
 

@@ -818,6 +818,7 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
     if (e != cudaSuccess) return e;
     k_primary_resid<kNee>
         <<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
@@ -846,6 +847,7 @@ static cudaError_t launch_primary_bth_t(const nirc_handle* h, const SceneHeader*
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_primary_bth<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, beta, sig, count, h->work_counter);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
@@ -873,6 +875,7 @@ static cudaError_t launch_gen_train_t(const nirc_handle* h, const SceneHeader* h
     k_gen_train<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
                                                       max_depth, recs, dirs, targets, h->work_counter + 1,
                                                       env_mode);
+    count_kernels(h);
     return cudaGetLastError();
 }
 

@@ -572,6 +572,7 @@ __global__ void k_hash_to_half(uint64_t n, const float* __restrict__ src, __half
 cudaError_t launch_hash_to_half(const nirc_handle* h, cudaStream_t st) {
     if (!h->shape.n_hash || !h->hash16) return cudaSuccess;
     k_hash_to_half<<<4 * h->num_sms, 256, 0, st>>>(h->shape.n_hash, h->params + h->shape.hash_off, h->hash16);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
@@ -622,10 +623,12 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         fwd<<<fwd_blocks, kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale, h->packed,
                                                       table, recs, dirs, targets, n, tp, store ? 1 : 0, kind,
                                                       h->loss_accum, det ? dp.loss_part : nullptr);
+        count_kernels(h);
         timer_end(h, NIRC_K_TRAIN_FWD, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (det) {
             k_sum_rows<<<1, 32, 0, st>>>(dp.loss_part, fwd_blocks, 1, h->loss_accum, 0);
+            count_kernels(h);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     }
@@ -644,6 +647,7 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             fwd<<<blocks_for(m), kTrainThreads, smem_f, st>>>(s, h->grid, h->cfg.z_clamp, h->cfg.loss_eps, scale,
                                                              h->packed, table, recs + c0, dirs + 3 * c0,
                                                              targets + 3 * c0, m, tc, 1, kLossNone, nullptr, nullptr);
+            count_kernels(h);
             timer_end(h, NIRC_K_TRAIN_FWD, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -652,6 +656,7 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             k_train_bwd<<<blocks_for(m), kTrainThreads, smem_b, st>>>(
                 s, h->grid, h->packed, recs + c0, m, tc, kind == kLossUpstream ? 1 : 0, h->grad + s.hash_off,
                 det_hash ? dp.de + c0 : nullptr, n, dp.lvl_max);
+            count_kernels(h);
             timer_end(h, NIRC_K_TRAIN_BWD, st);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
@@ -680,11 +685,14 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         timer_begin(h, NIRC_K_TRAIN_GRADW, st);
         if (!det && m < (tcmode ? kBlasMinSamplesTf32 : kBlasMinSamples)) {
             k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+            count_kernels(h);
         } else if (det) {
             k_grad_w<true><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
+            count_kernels(h);
             if ((e = cudaGetLastError()) == cudaSuccess) {
                 // chunks add their block partials into grad in chunk order
                 k_sum_rows<<<(uint32_t)((s.n_mlp + 255) / 256), 256, 0, st>>>(dp.gw_part, gx, s.n_mlp, h->grad, 1);
+                count_kernels(h);
             }
         } else {
             // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t];
@@ -722,6 +730,7 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             br.n_jobs = s.hidden + 1;
             const uint64_t per_block = 16384;
             k_bias_grad<<<dim3(rows, (uint32_t)((m + per_block - 1) / per_block)), 256, 0, st>>>(br, m, per_block);
+            count_kernels(h);
         }
         timer_end(h, NIRC_K_TRAIN_GRADW, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -729,9 +738,12 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     if (det_hash) {
         timer_begin(h, NIRC_K_TRAIN_BWD, st);
         k_hash_scatter_fixed<<<4 * h->num_sms, 256, 0, st>>>(h->grid, recs, n, dp.de, dp.lvl_max, dp.acc);
-        if ((e = cudaGetLastError()) == cudaSuccess)
+        count_kernels(h);
+        if ((e = cudaGetLastError()) == cudaSuccess) {
             k_hash_fixed_to_float<<<4 * h->num_sms, 256, 0, st>>>(h->grid, n, dp.lvl_max, dp.acc,
                                                                   h->grad + s.hash_off);
+            count_kernels(h);
+        }
         timer_end(h, NIRC_K_TRAIN_BWD, st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -751,6 +763,7 @@ cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const flo
     timer_begin(h, NIRC_K_ADAM, st);
     k_adam<<<8 * h->num_sms, 256, 0, st>>>(np, h->params, h->adam_m, h->adam_v, h->grad, h->cfg.lr, h->cfg.beta1,
                                           h->cfg.beta2, h->cfg.adam_eps, inv_bc1, inv_bc2, h->hash16, s.hash_off);
+    count_kernels(h);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     e = launch_repack_simt(h, st);
     if (e == cudaSuccess) e = launch_repack_tc(h, st);

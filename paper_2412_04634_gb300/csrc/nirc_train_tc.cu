@@ -467,6 +467,7 @@ cudaError_t launch_repack_train(const nirc_handle* h, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const uint32_t n = 4096u * h->shape.hidden + 3 * 64;
     k_repack_train_bwd<<<(n + 255) / 256, 256, 0, st>>>(h->shape, h->params, img);
+    count_kernels(h);
     return cudaGetLastError();
 }
 
@@ -500,6 +501,7 @@ cudaError_t launch_train_tc(const nirc_handle* h, const nirc_record* recs, const
     kern<<<grid, n_wg * 128, smem, st>>>(a, reinterpret_cast<const uint8_t*>(h->packed_train),
                                          reinterpret_cast<const __half2*>(h->hash16), recs, dirs, targets, tp,
                                          grad_table, loss_accum, h->dev_err);
+    count_kernels(h);
     return cudaGetLastError();
 }
 

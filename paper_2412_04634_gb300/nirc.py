@@ -317,7 +317,7 @@ def nirc_timing_enable(h, enable: bool = True):
 
 
 def nirc_timing_read(h) -> dict:
-    """{class: (total ms, launches)} since the last enable."""
+    """{class: (total ms, kernels launched)} since the last enable."""
     t = nirc_timing()
     _check(_lib.nirc_timing_read(h, ctypes.byref(t)))
     return {name: (t.ms[i], int(t.launches[i])) for i, name in enumerate(K_CLASSES)}
