@@ -325,6 +325,18 @@ class FrameRunner:
         N.nirc_train_step(h, self.recs, self.dirs, self.tgts, self.loss)
         N.nirc_frame_mrse(self.img, ref, self.mrse)
 
+    def rays_per_frame(self, f):
+        """Rays the path-tracing pass of frame f traces (camera rays, path
+        segments, shadow and visibility rays), from the library's counter."""
+        import torch
+        N, a = self.N, self.args
+        n2, n3 = later_vertex_samples(a)
+        d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
+                         light_mode=a.light_mode, estimator=estimator_code(a), n_cache2=n2, n_cache3=n3)
+        r = torch.zeros(1, dtype=torch.int64, device=self.dev)
+        N.nirc_estimate_frame(self.cache.h, self.scene_dev[f % 60], d, self.img, rays=r)
+        return int(r.item())
+
     def timed(self, ref, first, steps, stream, sampler=None):
         """Time `steps` frames on the device (CUDA events on `stream`)."""
         import torch
@@ -494,6 +506,8 @@ def run_ours(args):
     for f in range(args.warmup):
         run.step(f, ref)
     res = run.timed(ref, first, args.steps, stream, ClockSampler(gpu_id))
+    # ray count of the last timed frame (an extra, untimed estimate of the same frame)
+    pt_rays = run.rays_per_frame(first + args.steps - 1)
     e2e = None
     if not args.no_e2e:
         ms, bi, bo = run.e2e(ref, first, args.steps, frames, stream)
@@ -554,6 +568,9 @@ def run_ours(args):
         "frame_mrse": res["mrse"], "mrse_reference": f"{ref_spp} spp path tracing, depth 16, frame {last_frame}",
         "kernel_ms": {k: round(v[0], 4) for k, v in kernel_ms.items()},
         "kernels_per_step": {k: round(v[1], 2) for k, v in kernel_ms.items()},
+        "path_trace_rays": {"rays_per_frame": pt_rays,
+                            "rays_per_s": round(pt_rays / (kernel_ms["path_trace"][0] / 1e3)) if "path_trace" in
+                            kernel_ms else None},
         "fp32_simt": cmp,
         "mrse_rel_diff_vs_fp32": (abs(res["mrse"] - cmp["frame_mrse"]) / cmp["frame_mrse"]) if cmp else None,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

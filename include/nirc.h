@@ -239,13 +239,16 @@ typedef enum nirc_estimator {
  * rejection counts and lobes); count = valid (active) samples per pixel;
  * row_n = the cache value n of every row, W*H*(N+M) x 3 floats in pixel-major,
  * sample-minor order (cache samples first), 0 for rows whose sample is
- * invalid (network mode only). */
+ * invalid (network mode only); rays (one device uint64, not cleared) gains
+ * the number of rays the path-tracing pass traced (camera rays, path
+ * segments, shadow and visibility rays). */
 typedef struct nirc_frame_aux {
     float* lc;
     float* lr;
     uint64_t* sig;
     uint32_t* count;
     float* row_n;
+    uint64_t* rays;
 } nirc_frame_aux;
 
 typedef struct nirc_handle nirc_handle;

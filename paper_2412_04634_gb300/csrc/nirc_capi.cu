@@ -213,7 +213,7 @@ nirc_status check_frame_args(const char* who, const void* scene, const nirc_fram
     }
     if (aux && ((aux->lc && ((uintptr_t)aux->lc & 3u)) || (aux->lr && ((uintptr_t)aux->lr & 3u)) ||
                 (aux->sig && ((uintptr_t)aux->sig & 7u)) || (aux->count && ((uintptr_t)aux->count & 3u)) ||
-                (aux->row_n && ((uintptr_t)aux->row_n & 3u)))) {
+                (aux->row_n && ((uintptr_t)aux->row_n & 3u)) || (aux->rays && ((uintptr_t)aux->rays & 7u)))) {
         set_error("%s: misaligned aux pointer", who);
         return NIRC_ERR_INVALID;
     }
@@ -252,9 +252,10 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
         mv_out = reinterpret_cast<float4*>(q);  // [2][PM], each part round256
     }
     timer_begin(h, NIRC_K_PATH_TRACE, st);
-    cudaError_t e = biased ? launch_primary_bth(h, scene, fd, recs, base, beta, sig, count, st)
+    unsigned long long* rays = aux ? reinterpret_cast<unsigned long long*>(aux->rays) : nullptr;
+    cudaError_t e = biased ? launch_primary_bth(h, scene, fd, recs, base, beta, sig, count, st, rays)
                            : launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st, mv_rec, mv_beta,
-                                                  mv_row);
+                                                  mv_row, rays);
     timer_end(h, NIRC_K_PATH_TRACE, st);
     if (e != cudaSuccess) {
         set_error("%s (path tracing): %s", who, cudaGetErrorString(e));

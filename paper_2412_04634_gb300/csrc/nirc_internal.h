@@ -130,13 +130,15 @@ GridParams make_grid(const nirc_config& cfg);
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig,
                                  uint32_t* count, cudaStream_t st, nirc_record* mv_rec = nullptr,
-                                 float4* mv_beta = nullptr, ResidRow* mv_row = nullptr);
+                                 float4* mv_beta = nullptr, ResidRow* mv_row = nullptr,
+                                 unsigned long long* rays = nullptr);
 // Multi-vertex estimator: out (RGBA) and lr (RGB, may be NULL) of pixel p gain
 // sum over j of o2[p M + j] + o3[p M + j] (either may be NULL).
 cudaError_t launch_mv_accumulate(float* out_rgba, float* lr, const float4* o2, const float4* o3, uint64_t P,
                                  uint32_t M, cudaStream_t st);
 cudaError_t launch_primary_bth(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd, nirc_record* recs,
-                               PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st);
+                               PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st,
+                               unsigned long long* rays = nullptr);
 cudaError_t launch_gen_train(const nirc_handle* h, const void* scene, uint32_t n_prims, uint32_t W, uint32_t H,
                              uint64_t T, uint32_t frame, uint64_t seed, uint32_t max_depth, uint32_t light_mode,
                              nirc_record* recs, float* dirs, float* targets, cudaStream_t st);

@@ -42,6 +42,7 @@ struct FrameArgs {
     uint32_t W, H, N, M, D, n_prims;
     uint32_t k0, k1;
     uint32_t env_mode;  // light mode 2: residual rows are one visibility ray times L_env
+    unsigned long long* rays;  // optional: gains the rays traced
 };
 
 // The scene's cube map (header reserved[0] = face size, texels after the primitives).
@@ -75,10 +76,19 @@ struct Tracer {
     uint32_t n;
     Bvh tree;
     bool bvh;
+    mutable uint32_t rays = 0;  // nearest-hit queries of this thread
     __device__ __forceinline__ int nearest(V3 o, V3 d, float& t) const {
+        ++rays;
         return bvh ? bvh_nearest(tree, prims, n, o, d, t) : trace_nearest(prims, n, o, d, t);
     }
 };
+
+// Add the threads' ray counts to *out (one atomic per converged group).
+__device__ __forceinline__ void add_rays(unsigned long long* out, uint32_t r) {
+    const unsigned m = __activemask();
+    const uint32_t s = __reduce_add_sync(m, r);
+    if ((threadIdx.x & 31u) == (uint32_t)(__ffs(m) - 1)) atomicAdd(out, (unsigned long long)s);
+}
 
 // Shared bytes of the staged geometry and hierarchy (the light list follows, 16-byte aligned).
 __host__ __device__ __forceinline__ size_t pt_geom_bytes(uint32_t n_prims) {
@@ -509,6 +519,7 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
             }
         }
     }
+    if (a.rays) add_rays(a.rays, tr.rays);
 }
 
 // ---------------------------------------------------------------------------
@@ -682,6 +693,7 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_primary_bth(const SceneHeader
         if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
         if (count) count[pix] = 0;
     }
+    if (a.rays) add_rays(a.rays, tr.rays);
 }
 
 // Training paths, organised like k_primary_resid: per path index the pixel
@@ -824,9 +836,10 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
 
 cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd,
                                  nirc_record* recs, PixelBase* base, ResidRow* rows, uint64_t* sig, uint32_t* count,
-                                 cudaStream_t st, nirc_record* mv_rec, float4* mv_beta, ResidRow* mv_row) {
-    FrameArgs a{fd.width, fd.height, fd.n_cache,  fd.n_resid,
-                fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame, fd.light_mode == 2 ? 1u : 0u};
+                                 cudaStream_t st, nirc_record* mv_rec, float4* mv_beta, ResidRow* mv_row,
+                                 unsigned long long* rays) {
+    FrameArgs a{fd.width, fd.height, fd.n_cache,  fd.n_resid, fd.max_depth,
+                fd.n_prims, (uint32_t)fd.seed, fd.frame, fd.light_mode == 2 ? 1u : 0u, rays};
     const uint64_t P = (uint64_t)fd.width * fd.height;
     const MvOut mv{mv_rec, mv_beta, mv_row, P * fd.n_resid};
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
@@ -852,8 +865,10 @@ static cudaError_t launch_primary_bth_t(const nirc_handle* h, const SceneHeader*
 }
 
 cudaError_t launch_primary_bth(const nirc_handle* h, const void* scene, const nirc_frame_desc& fd, nirc_record* recs,
-                               PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st) {
-    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame, 0u};
+                               PixelBase* base, float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st,
+                               unsigned long long* rays) {
+    FrameArgs a{fd.width, fd.height, fd.n_cache, fd.n_resid, fd.max_depth, fd.n_prims, (uint32_t)fd.seed, fd.frame, 0u,
+                rays};
     const uint64_t P = (uint64_t)fd.width * fd.height;
     const auto* hd = reinterpret_cast<const SceneHeader*>(scene);
     const auto* gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(scene) + sizeof(SceneHeader));

@@ -59,7 +59,8 @@ class nirc_frame_desc(ctypes.Structure):
 
 class nirc_frame_aux(ctypes.Structure):
     _fields_ = [("lc", ctypes.c_void_p), ("lr", ctypes.c_void_p),
-                ("sig", ctypes.c_void_p), ("count", ctypes.c_void_p), ("row_n", ctypes.c_void_p)]
+                ("sig", ctypes.c_void_p), ("count", ctypes.c_void_p), ("row_n", ctypes.c_void_p),
+                ("rays", ctypes.c_void_p)]
 
 
 K_CLASSES = ["path_trace", "cache", "train_records", "train_fwd", "train_bwd", "train_gradw", "adam", "query"]
@@ -279,19 +280,19 @@ def nirc_query(h, records: torch.Tensor, dirs: torch.Tensor, out: torch.Tensor, 
 
 
 def nirc_estimate_frame(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba: torch.Tensor,
-                        lc=None, lr=None, sig=None, count=None, row_n=None, stream=None):
-    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n))
-    use_aux = any(x is not None for x in (lc, lr, sig, count, row_n))
+                        lc=None, lr=None, sig=None, count=None, row_n=None, rays=None, stream=None):
+    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n), _ptr(rays))
+    use_aux = any(x is not None for x in (lc, lr, sig, count, row_n, rays))
     _check(_lib.nirc_estimate_frame(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
                                     ctypes.byref(aux) if use_aux else None, _stream(stream)))
 
 
 def nirc_estimate_frame_noalloc(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba: torch.Tensor,
-                                lc=None, lr=None, sig=None, count=None, row_n=None, stream=None):
+                                lc=None, lr=None, sig=None, count=None, row_n=None, rays=None, stream=None):
     """nirc_estimate_frame on the library's fixed scratch area (no device
     allocation during the call; frames up to W*H*(96+32*M) <= 4 MiB)."""
-    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n))
-    use_aux = any(x is not None for x in (lc, lr, sig, count, row_n))
+    aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n), _ptr(rays))
+    use_aux = any(x is not None for x in (lc, lr, sig, count, row_n, rays))
     _check(_lib.nirc_estimate_frame_noalloc(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
                                             ctypes.byref(aux) if use_aux else None, _stream(stream)))
 

@@ -45,3 +45,32 @@ def test_records_on_second_stream_match_serial(N, precision):
     cache.close()
     for a, b in zip(*res):
         assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+
+
+def test_ray_counter(N):
+    """nirc_frame_aux.rays: with no residual paths (M = 0) the path tracer
+    traces exactly one camera ray per pixel; the count is reproducible and
+    grows with M and with the path depth; it does not change the image."""
+    import torch
+    W, H = 160, 120
+    cfg = scenes.config_small()
+    sc = scenes.cornell_scene(W, H, seed=3, n_prims=64, glossy=True)
+    cache = N.Cache(cfg)
+    cache.set_params(scenes.init_params(cfg, 5))
+    scene = N.scene_to_tensor(sc)
+
+    def rays(M, D):
+        r = torch.zeros(1, dtype=torch.int64, device="cuda")
+        out = torch.empty((W * H, 4), device="cuda")
+        N.nirc_estimate_frame(cache.h, scene, N.frame_desc(W, H, 8, M, D, 2, 1, sc.n_prims), out, rays=r)
+        plain = torch.empty_like(out)
+        N.nirc_estimate_frame(cache.h, scene, N.frame_desc(W, H, 8, M, D, 2, 1, sc.n_prims), plain)
+        torch.cuda.synchronize()
+        assert torch.equal(out, plain)
+        return int(r.item())
+
+    assert rays(0, 5) == W * H
+    r1 = rays(1, 5)
+    assert r1 == rays(1, 5)
+    assert W * H < rays(1, 1) < r1 < rays(2, 5)
+    cache.close()
