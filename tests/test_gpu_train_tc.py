@@ -51,6 +51,7 @@ CONFIGS = {
     "hash16_h8": lambda: _hash_cfg(hidden=8),
     "paper_sh": lambda: _hash_cfg(levels=12, input_encoding=scenes.INPUT_SH),
     "paper_sh_vis": lambda: _hash_cfg(levels=12, input_encoding=scenes.INPUT_SH, output=scenes.OUT_VISIBILITY),
+    "hash12_freq": lambda: _hash_cfg(levels=12),
 }
 
 
@@ -105,10 +106,11 @@ def _grad_errors(cfg, g, g_ref):
     return errs, l2, cos
 
 
-@pytest.mark.parametrize("name,n", [(k, 5000) for k in CONFIGS] + [("hash16", (1 << 16) + 300)])
+@pytest.mark.parametrize("name,n", [(k, 5000) for k in CONFIGS] + [("hash16", (1 << 16) + 300), ("hash16", 100)])
 def test_tc_train_step_matches_oracle(N, oracle, name, n):
     """n = 5000: 39 tiles of 128 and a ragged tail of 8, weight gradients by
-    the FP32 SIMT kernel; n = 2^16 + 300: weight gradients by TF32 GEMMs."""
+    the FP32 SIMT kernel; n = 2^16 + 300: weight gradients by TF32 GEMMs;
+    n = 100: one partly filled tile."""
     cfg = CONFIGS[name]()
     params = _params(cfg, 11)
     recs, dirs, tg = _batch(cfg, n, 12)
