@@ -80,6 +80,9 @@ def parse_args():
     ap.add_argument("--overlap-records", type=int, default=1,
                     help="1: generate each frame's training records on a second stream, concurrently with the "
                          "frame estimate (they read only the scene); 0: one stream")
+    ap.add_argument("--pipeline-trace", type=int, default=1,
+                    help="1: trace frame f + 1 (NIRC_PHASE_TRACE, on a third stream) while frame f trains; the "
+                         "path-tracing pass reads no cache weights.  0: each frame estimated in one call")
     ap.add_argument("--compare-fp32", type=int, default=1)
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
@@ -279,6 +282,8 @@ class FrameRunner:
         self.loss = torch.zeros(1, device=dev)
         self.mrse = torch.zeros(1, dtype=torch.float64, device=dev)
         self.side = torch.cuda.Stream(device=dev) if getattr(args, "overlap_records", 0) else None
+        self.pt_stream = torch.cuda.Stream(device=dev) if getattr(args, "pipeline_trace", 0) else None
+        self.traced = None  # (frame, event) of a frame traced ahead
 
     def set_precision(self, name, train="fp32"):
         self.N.nirc_set_precision(self.cache.h, _precision_code(self.N, name))
@@ -301,25 +306,51 @@ class FrameRunner:
         ref /= n
         return ref, n * per
 
-    def step(self, f, ref, scene=None):
+    def desc(self, f, phase=0):
+        N, a = self.N, self.args
+        n2, n3 = later_vertex_samples(a)
+        return N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
+                            light_mode=a.light_mode, estimator=estimator_code(a), n_cache2=n2, n_cache3=n3,
+                            phase=phase)
+
+    def step(self, f, ref, scene=None, next_scene=None, ahead=False):
+        """One frame: estimate, training records, training step, MRSE.  With
+        --pipeline-trace, frame f's path tracing was enqueued by the step
+        before (else it is traced here) and, when `ahead`, frame f + 1's is
+        enqueued here on its own stream once frame f's cache pass has read
+        the scratch, so it overlaps frame f's training: in steady state
+        every step traces one frame, the next one."""
+        import torch
         N, a = self.N, self.args
         sc = self.scene_dev[f % 60] if scene is None else scene
         h = self.cache.h
-        n2, n3 = later_vertex_samples(a)
-        d = N.frame_desc(self.W, self.H, a.n_cache, a.n_resid, a.depth, f, self.seed, self.n_prims,
-                         light_mode=a.light_mode, estimator=estimator_code(a), n_cache2=n2, n_cache3=n3)
+        main = torch.cuda.current_stream(self.dev)
+        pipe = self.pt_stream is not None
+        if pipe:
+            if self.traced is not None and self.traced[0] == f:
+                main.wait_event(self.traced[1])
+            else:
+                N.nirc_estimate_frame(h, sc, self.desc(f, N.NIRC_PHASE_TRACE), None)
+            self.traced = None
         if self.side is not None:
             # the records of frame f replace those the previous training step read, so the side
             # stream first waits for everything enqueued so far; the step waits for the records
-            import torch
-            main = torch.cuda.current_stream(self.dev)
             self.side.wait_stream(main)
             N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs,
                              self.dirs, self.tgts, stream=self.side, light_mode=a.light_mode)
-            N.nirc_estimate_frame(h, sc, d, self.img)
+        N.nirc_estimate_frame(h, sc, self.desc(f, N.NIRC_PHASE_CACHE if pipe else N.NIRC_PHASE_ALL), self.img)
+        if pipe and ahead:
+            ev = torch.cuda.Event()
+            ev.record(main)  # frame f's cache pass has read the scratch
+            self.pt_stream.wait_event(ev)
+            nsc = self.scene_dev[(f + 1) % 60] if next_scene is None else next_scene
+            N.nirc_estimate_frame(h, nsc, self.desc(f + 1, N.NIRC_PHASE_TRACE), None, stream=self.pt_stream)
+            done = torch.cuda.Event()
+            done.record(self.pt_stream)
+            self.traced = (f + 1, done)
+        if self.side is not None:
             main.wait_stream(self.side)
         else:
-            N.nirc_estimate_frame(h, sc, d, self.img)
             N.nirc_gen_train(h, sc, self.n_prims, self.W, self.H, a.train, f, self.seed, a.depth, self.recs,
                              self.dirs, self.tgts, light_mode=a.light_mode)
         N.nirc_train_step(h, self.recs, self.dirs, self.tgts, self.loss)
@@ -352,7 +383,7 @@ class FrameRunner:
         torch.cuda.synchronize(self.dev)
         evs[0].record(stream)
         for k in range(steps):
-            self.step(first + k, ref)
+            self.step(first + k, ref, ahead=True)
             evs[k + 1].record(stream)
         torch.cuda.synchronize(self.dev)
         if world > 1:
@@ -372,7 +403,9 @@ class FrameRunner:
         host_scenes = [torch.from_numpy(f.blob()).pin_memory() for f in frames]
         host_img = [torch.empty((self.P, 4), pin_memory=True) for _ in range(2)]
         host_small = torch.empty(2, dtype=torch.float64, pin_memory=True)
-        dev_scene = torch.empty_like(self.scene_dev[0])
+        # two device scenes: with --pipeline-trace frame f + 1 is traced during step f
+        dev_scenes = [torch.empty_like(self.scene_dev[0]) for _ in range(2)]
+        loaded = [None]  # the frame whose scene is already on the device
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         # the image of frame f leaves on a copy stream while frame f + 1 renders into the
         # other of two device images; frame f + 2 waits for that copy before reusing it
@@ -380,14 +413,19 @@ class FrameRunner:
         copy = torch.cuda.Stream(device=self.dev)
         done = [None, None]
 
-        def one(f):
+        def one(f, ahead):
             main = torch.cuda.current_stream(self.dev)
             b = f % 2
             if done[b] is not None:
                 main.wait_event(done[b])
             self.img = imgs[b]
-            dev_scene.copy_(host_scenes[f % 60], non_blocking=True)
-            self.step(f, ref, scene=dev_scene)
+            if loaded[0] != f:
+                dev_scenes[b].copy_(host_scenes[f % 60], non_blocking=True)
+            loaded[0] = f
+            if self.pt_stream is not None and ahead:
+                dev_scenes[1 - b].copy_(host_scenes[(f + 1) % 60], non_blocking=True)
+                loaded[0] = f + 1
+            self.step(f, ref, scene=dev_scenes[b], next_scene=dev_scenes[1 - b], ahead=ahead)
             host_small[0:1].copy_(self.mrse, non_blocking=True)
             host_small[1:2].copy_(self.loss.double(), non_blocking=True)
             copy.wait_stream(main)
@@ -396,13 +434,14 @@ class FrameRunner:
             done[b] = torch.cuda.Event()
             done[b].record(copy)
 
-        # untimed warm-up of the host-buffer path (first transfers into fresh pinned pages)
+        # untimed warm-up of the host-buffer path (first transfers into fresh pinned pages),
+        # frames first - 3 .. first - 1, the last of which traces frame `first` ahead
         for k in range(3):
-            one(first + k)
+            one(max(0, first - 3 + k), True)
         torch.cuda.synchronize(self.dev)
         e0.record(stream)
         for k in range(steps):
-            one(first + k)
+            one(first + k, True)
         stream.wait_stream(copy)  # the last images are on the host inside the timed region
         e1.record(stream)
         torch.cuda.synchronize(self.dev)
@@ -503,8 +542,8 @@ def run_ours(args):
     run = FrameRunner(N, args, cfg, params, frames, dev, seed)
     ref, ref_spp = run.reference(last_frame, args.ref_spp)
     run.set_precision(args.precision, args.train_precision)
-    for f in range(args.warmup):
-        run.step(f, ref)
+    for f in range(args.warmup):  # the last warm-up step traces the first timed frame ahead
+        run.step(f, ref, ahead=True)
     res = run.timed(ref, first, args.steps, stream, ClockSampler(gpu_id))
     # ray count of the last timed frame (an extra, untimed estimate of the same frame)
     pt_rays = run.rays_per_frame(first + args.steps - 1)
@@ -521,7 +560,7 @@ def run_ours(args):
         run32 = FrameRunner(N, args, cfg, params, frames, dev, seed)
         run32.set_precision("fp32")
         for f in range(args.warmup):
-            run32.step(f, ref)
+            run32.step(f, ref, ahead=True)
         r32 = run32.timed(ref, first, args.steps, stream)
         cmp = {"value": world * rows_per_frame(args) * args.steps / (r32["total_ms"] / 1e3),
                "ms_per_step": r32["total_ms"] / args.steps, "p50_ms": float(np.percentile(r32["step_ms"], 50)),
@@ -561,6 +600,10 @@ def run_ours(args):
                    "l2": "no flush: per-frame working set (~0.6 GB of records, rows, images, tables) > 129 MB L2",
                    "train_records_stream": "second stream, concurrent with the frame estimate (kernel_ms of "
                                            "train_records spans the overlap)" if args.overlap_records else "main",
+                   "path_trace_stream": "third stream: frame f + 1 traced (NIRC_PHASE_TRACE) while frame f "
+                                        "trains; in steady state each timed step traces exactly one frame, the "
+                                        "next (the first timed frame was traced by the last warm-up step)"
+                   if args.pipeline_trace else "main",
                    "light_mode": args.light_mode, "estimator": args.estimator, "input": args.input,
                    "scene": args.scene, "output": args.output,
                    "parallelism": f"replicas x{world}"},

@@ -189,8 +189,27 @@ typedef struct nirc_frame_desc {
     uint32_t estimator;      /* nirc_estimator */
     uint32_t n_cache2;       /* NIRC_EST_MULTI_VERTEX: cache samples at the */
     uint32_t n_cache3;       /* second and third vertex (0..1024) */
-    uint32_t reserved;       /* 0 */
+    uint32_t phase;          /* NIRC_PHASE_ALL (0): the whole estimate.
+                                NIRC_PHASE_TRACE (1): only the path-tracing
+                                pass (camera hits, shading records, residual
+                                paths) into the handle's frame scratch;
+                                d_out_rgba may be NULL and is not written.
+                                NIRC_PHASE_CACHE (2): only the cache integral
+                                and the per-pixel sums, over the scratch of
+                                the handle's last NIRC_PHASE_TRACE call,
+                                whose descriptor must equal this one apart
+                                from the phase (else NIRC_ERR_INVALID); pass
+                                the same scene and aux.  The path-tracing
+                                pass reads no cache weights, so a caller can
+                                trace frame f + 1 while training on frame f
+                                (on another stream, after frame f's cache
+                                pass, which reads the scratch).  A
+                                NIRC_PHASE_ALL call ends the traced state.
+                                nirc_estimate_frame_noalloc and the server
+                                take NIRC_PHASE_ALL only. */
 } nirc_frame_desc;
+
+enum { NIRC_PHASE_ALL = 0, NIRC_PHASE_TRACE = 1, NIRC_PHASE_CACHE = 2 };
 
 /* Estimator of nirc_frame_desc.estimator.
  * NIRC_EST_TWO_LEVEL: eq. L_mlmc at the first camera hit (N cache samples,

@@ -196,8 +196,9 @@ size_t frame_scratch_bytes(uint64_t P, uint32_t M, uint32_t estimator) {
 nirc_status check_frame_args(const char* who, const void* scene, const nirc_frame_desc& fd, const float* out,
                              const nirc_frame_aux* aux) {
     const uint64_t P = (uint64_t)fd.width * fd.height;
-    if (!scene || !out || !aligned16(scene) || !aligned16(out)) {
-        set_error("%s: NULL or misaligned scene/output pointer", who);
+    if (!scene || (!out && fd.phase != NIRC_PHASE_TRACE) || !aligned16(scene) || (out && !aligned16(out)) ||
+        fd.phase > NIRC_PHASE_CACHE) {
+        set_error("%s: NULL or misaligned scene/output pointer, or phase > 2", who);
         return NIRC_ERR_INVALID;
     }
     if (fd.n_prims < 1 || fd.n_prims > NIRC_MAX_PRIMS || fd.n_cache > 1024 || fd.n_resid > 64 || fd.max_depth < 1 ||
@@ -251,15 +252,19 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
         q += round256(2 * PM * sizeof(ResidRow));
         mv_out = reinterpret_cast<float4*>(q);  // [2][PM], each part round256
     }
-    timer_begin(h, NIRC_K_PATH_TRACE, st);
-    unsigned long long* rays = aux ? reinterpret_cast<unsigned long long*>(aux->rays) : nullptr;
-    cudaError_t e = biased ? launch_primary_bth(h, scene, fd, recs, base, beta, sig, count, st, rays)
-                           : launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st, mv_rec, mv_beta,
-                                                  mv_row, rays);
-    timer_end(h, NIRC_K_PATH_TRACE, st);
-    if (e != cudaSuccess) {
-        set_error("%s (path tracing): %s", who, cudaGetErrorString(e));
-        return NIRC_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (fd.phase != NIRC_PHASE_CACHE) {
+        timer_begin(h, NIRC_K_PATH_TRACE, st);
+        unsigned long long* rays = aux ? reinterpret_cast<unsigned long long*>(aux->rays) : nullptr;
+        e = biased ? launch_primary_bth(h, scene, fd, recs, base, beta, sig, count, st, rays)
+                   : launch_primary_resid(h, scene, fd, recs, base, rows, sig, count, st, mv_rec, mv_beta, mv_row,
+                                          rays);
+        timer_end(h, NIRC_K_PATH_TRACE, st);
+        if (e != cudaSuccess) {
+            set_error("%s (path tracing): %s", who, cudaGetErrorString(e));
+            return NIRC_ERR_CUDA;
+        }
+        if (fd.phase == NIRC_PHASE_TRACE) return NIRC_OK;
     }
     timer_begin(h, NIRC_K_CACHE, st);
     const bool tc = tc_supported(h, fd);
@@ -674,9 +679,25 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
     if (P == 0) return NIRC_OK;
     nirc_status s = check_frame_args("nirc_estimate_frame", d_scene, fd, d_out_rgba, aux);
     if (s != NIRC_OK) return s;
-    s = ensure(&h->scratch, &h->scratch_bytes, frame_scratch_bytes(P, fd.n_resid, fd.estimator), "frame");
-    if (s != NIRC_OK) return s;
-    return enqueue_frame("nirc_estimate_frame", h, d_scene, fd, d_out_rgba, aux, h->scratch, (cudaStream_t)stream);
+    if (fd.phase == NIRC_PHASE_CACHE) {
+        // the scratch must hold this frame's traced data: same descriptor apart from the phase
+        nirc_frame_desc a = fd, b = h->traced_desc;
+        a.phase = b.phase = 0;
+        if (!h->traced || std::memcmp(&a, &b, sizeof(a)) != 0) {
+            set_error("nirc_estimate_frame: NIRC_PHASE_CACHE without a NIRC_PHASE_TRACE call of the same frame");
+            return NIRC_ERR_INVALID;
+        }
+    } else {
+        h->traced = false;
+        s = ensure(&h->scratch, &h->scratch_bytes, frame_scratch_bytes(P, fd.n_resid, fd.estimator), "frame");
+        if (s != NIRC_OK) return s;
+    }
+    s = enqueue_frame("nirc_estimate_frame", h, d_scene, fd, d_out_rgba, aux, h->scratch, (cudaStream_t)stream);
+    if (s == NIRC_OK && fd.phase == NIRC_PHASE_TRACE) {
+        h->traced = true;
+        h->traced_desc = fd;
+    }
+    return s;
 }
 
 nirc_status nirc_gen_train(nirc_handle* h, const void* d_scene, uint32_t n_prims, uint32_t width, uint32_t height,

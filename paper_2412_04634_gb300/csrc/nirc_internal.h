@@ -103,6 +103,9 @@ struct nirc_handle {
     };
     Pending* pending = nullptr;     // recorded, not yet read
     mutable uint64_t n_kernels = 0; // kernels launched by the handle so far
+    // split frames (nirc_frame_desc.phase): the descriptor of the last traced frame
+    bool traced = false;
+    nirc_frame_desc traced_desc{};
     int n_pending = 0;
     cudaEvent_t* event_pool = nullptr;
     int n_pool = 0;

@@ -68,6 +68,10 @@ extern "C" nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d
     if (P == 0) return NIRC_OK;
     nirc_status st = check_frame_args("nirc_estimate_frame_noalloc", d_scene, fd, d_out_rgba, aux);
     if (st != NIRC_OK) return st;
+    if (fd.phase != NIRC_PHASE_ALL) {
+        set_error("nirc_estimate_frame_noalloc: split frames (phase != 0) are not supported here");
+        return NIRC_ERR_INVALID;
+    }
     const size_t need = frame_scratch_bytes(P, fd.n_resid, fd.estimator);
     if (need > kNoAllocScratchBytes) {
         set_error("nirc_estimate_frame_noalloc: frame needs %zu bytes of scratch (W*H*(96 + 32*M) rounded), more than "

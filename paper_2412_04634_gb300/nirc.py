@@ -23,6 +23,7 @@ NIRC_FP32_SIMT, NIRC_FP16_TC, NIRC_BF16_TC, NIRC_FP8_E4M3_TC = range(4)
 NIRC_INPUT_FREQ, NIRC_INPUT_SH = range(2)
 NIRC_EST_TWO_LEVEL, NIRC_EST_BIASED_BTH, NIRC_EST_MULTI_VERTEX = range(3)
 NIRC_OUT_RADIANCE, NIRC_OUT_VISIBILITY = range(2)
+NIRC_PHASE_ALL, NIRC_PHASE_TRACE, NIRC_PHASE_CACHE = range(3)
 NIRC_MAX_PRIMS = 1024
 
 
@@ -53,7 +54,7 @@ class nirc_frame_desc(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("n_prims", ctypes.c_uint32),
         ("cache_mode", ctypes.c_uint32), ("cache_const", ctypes.c_float * 3),
         ("light_mode", ctypes.c_uint32), ("estimator", ctypes.c_uint32), ("n_cache2", ctypes.c_uint32),
-        ("n_cache3", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+        ("n_cache3", ctypes.c_uint32), ("phase", ctypes.c_uint32),
     ]
 
 
@@ -183,7 +184,8 @@ def make_config(cfg: scenes.NetConfig, precision: int = NIRC_FP32_SIMT) -> nirc_
 
 
 def frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode=0,
-               cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0, n_cache2=0, n_cache3=0) -> nirc_frame_desc:
+               cache_const=(0.0, 0.0, 0.0), light_mode=0, estimator=0, n_cache2=0, n_cache3=0,
+               phase=0) -> nirc_frame_desc:
     d = nirc_frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims, cache_mode)
     for k in range(3):
         d.cache_const[k] = float(cache_const[k])
@@ -191,6 +193,7 @@ def frame_desc(width, height, n_cache, n_resid, max_depth, frame, seed, n_prims,
     d.estimator = estimator
     d.n_cache2 = n_cache2
     d.n_cache3 = n_cache3
+    d.phase = phase
     return d
 
 
