@@ -402,10 +402,14 @@ nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t 
  * (warp-aggregated atomics) and Adam stay FP32, and the weight gradients
  * from the stored FP32 activations and deltas run as TF32 tensor-core GEMMs
  * (cuBLAS, FP32 accumulation) for passes of 2^16 samples or more, FP32
- * SIMT below.  The hash-grid features come from the
- * FP16 copy of the table, as in the FP16 frame path.  Weight gradients
- * agree with the FP32 ones to about 1e-3 of their maximum, the hash-table
- * gradient to about 1e-2 (relative L2 norm).  Applies to the relative L2
+ * SIMT below.  The hash-grid features come from the FP16 copy of the
+ * table, as in the FP16 frame path.  Weight gradients agree with the FP32
+ * ones to about 1e-3 of their maximum; the hash-table gradient to about
+ * 1e-3 (relative L2 norm) for records whose pre-activations are not within
+ * FP16 rounding of a ReLU kink, and a few percent over batches where many
+ * are (such a record's ReLU can switch, which moves the few table entries
+ * around it).  NIRC_K_TRAIN_FWD times the kernel (forward and backward).
+ * Applies to the relative L2
  * loss only: nirc_query_bwd and deterministic training keep FP32.  Any
  * other value returns NIRC_ERR_INVALID; NIRC_ERR_UNSUPPORTED for a network
  * the kernel does not cover (hidden_layers > 8, or position features other
@@ -456,7 +460,7 @@ enum {
     NIRC_K_PATH_TRACE = 0,   /* camera hits, records, residual paths */
     NIRC_K_CACHE = 1,        /* cache integral (encodings, MLP, per-pixel sums) */
     NIRC_K_TRAIN_RECORDS = 2,/* training-path pass */
-    NIRC_K_TRAIN_FWD = 3,    /* training forward + loss */
+    NIRC_K_TRAIN_FWD = 3,    /* training forward + loss (tensor-core training: + backward) */
     NIRC_K_TRAIN_BWD = 4,    /* backward through the MLP + hash scatter */
     NIRC_K_TRAIN_GRADW = 5,  /* weight-gradient reduction */
     NIRC_K_ADAM = 6,         /* Adam + weight repacking */
