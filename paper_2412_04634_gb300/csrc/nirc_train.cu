@@ -548,17 +548,47 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_w(GradJobs jobs, uint64_t
         }
 }
 
+// Dense bias-corrected Adam over all parameters, four at a time (16-byte
+// loads and stores of the 256-byte aligned arrays); the FP16 copy of the
+// hash table follows its entries.
+__device__ __forceinline__ float adam_one(float gi, float& mi, float& vi, float pi, float lr, float b1, float b2,
+                                          float eps, float inv_bc1, float inv_bc2) {
+    mi = b1 * mi + (1.f - b1) * gi;
+    vi = b2 * vi + (1.f - b2) * gi * gi;
+    return pi - lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
+}
+
 __global__ void k_adam(uint64_t n_params, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                        const float* __restrict__ g, float lr, float b1, float b2, float eps, float inv_bc1,
                        float inv_bc2, __half* __restrict__ hash16, uint64_t hash_off) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_params;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.f - b1) * gi;
-        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n4 = n_params / 4;
+    for (uint64_t q = tid; q < n4; q += stride) {
+        const float4 g4 = reinterpret_cast<const float4*>(g)[q];
+        float4 m4 = reinterpret_cast<const float4*>(m)[q];
+        float4 v4 = reinterpret_cast<const float4*>(v)[q];
+        float4 p4 = reinterpret_cast<const float4*>(p)[q];
+        p4.x = adam_one(g4.x, m4.x, v4.x, p4.x, lr, b1, b2, eps, inv_bc1, inv_bc2);
+        p4.y = adam_one(g4.y, m4.y, v4.y, p4.y, lr, b1, b2, eps, inv_bc1, inv_bc2);
+        p4.z = adam_one(g4.z, m4.z, v4.z, p4.z, lr, b1, b2, eps, inv_bc1, inv_bc2);
+        p4.w = adam_one(g4.w, m4.w, v4.w, p4.w, lr, b1, b2, eps, inv_bc1, inv_bc2);
+        reinterpret_cast<float4*>(m)[q] = m4;
+        reinterpret_cast<float4*>(v)[q] = v4;
+        reinterpret_cast<float4*>(p)[q] = p4;
+        if (hash16) {
+            const uint64_t i = 4 * q;
+            const float pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (i + k >= hash_off) hash16[i + k - hash_off] = __float2half_rn(pv[k]);
+        }
+    }
+    for (uint64_t i = 4 * n4 + tid; i < n_params; i += stride) {
+        float mi = m[i], vi = v[i];
+        const float pi = adam_one(g[i], mi, vi, p[i], lr, b1, b2, eps, inv_bc1, inv_bc2);
         m[i] = mi;
         v[i] = vi;
-        const float pi = p[i] - lr * (mi * inv_bc1) / (sqrtf(vi * inv_bc2) + eps);
         p[i] = pi;
         if (hash16 && i >= hash_off) hash16[i - hash_off] = __float2half_rn(pi);
     }
