@@ -399,10 +399,10 @@ nirc_status nirc_set_train_mode(nirc_handle* h, int store_activations, uint64_t 
  * path), the loss of eq. 12, and the backward of every layer (FP16
  * operands; each record's delta row is scaled by an exact power of two
  * into FP16's range and scaled back after the MMA); the hash-table scatter
- * (warp-aggregated atomics) and Adam stay FP32, and the weight gradients
- * from the stored FP32 activations and deltas run as TF32 tensor-core GEMMs
- * (cuBLAS, FP32 accumulation) for passes of 2^16 samples or more, FP32
- * SIMT below.  The hash-grid features come from the FP16 copy of the
+ * (warp-aggregated atomics) and Adam stay FP32, and the weight and bias
+ * gradients of every layer are one more tensor-core kernel (BF16 operands
+ * rounded from the stored FP32 activations and deltas, FP32 accumulation,
+ * a row of ones giving the bias sums).  The hash-grid features come from the FP16 copy of the
  * table, as in the FP16 frame path.  Weight gradients agree with the FP32
  * ones to about 1e-3 of their maximum; the hash-table gradient to about
  * 1e-3 (relative L2 norm) for records whose pre-activations are not within

@@ -49,6 +49,7 @@
 
 #include <cmath>
 
+#include "nirc_gradw_tc.h"
 #include "nirc_internal.h"
 #include "nirc_simt.cuh"
 
@@ -107,9 +108,6 @@ constexpr size_t kBlasWorkspace = 32u << 20;
 // Below this many samples per pass the hand-written k_grad_w is faster than
 // the library GEMM for these skinny shapes (64 x 72 outputs, K = samples).
 constexpr uint64_t kBlasMinSamples = 1ull << 18;
-// With TF32 tensor-core GEMMs (tensor-core training) the library is faster
-// from 2^16 samples per pass (0.17 vs 0.21 ms at 2^16, 0.13 vs 0.11 ms at 2^15).
-constexpr uint64_t kBlasMinSamplesTf32 = 1ull << 16;
 
 cudaError_t prepare_blas(nirc_handle* h) {
     if (h->blas) return cudaSuccess;
@@ -713,7 +711,19 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
         if (gx > n_chunks) gx = n_chunks;
         if (gx < 1) gx = 1;
         timer_begin(h, NIRC_K_TRAIN_GRADW, st);
-        if (!det && m < (tcmode ? kBlasMinSamplesTf32 : kBlasMinSamples)) {
+        if (tcmode) {
+            // tensor-core training: every layer's dW and db as BF16 MMAs in one launch
+            DwJobs dj;
+            dj.n_jobs = s.hidden + 1;
+            for (uint32_t l = 0; l <= s.hidden; ++l) {
+                const GradJob& J = jobs.j[l];
+                dj.j[l] = DwJob{J.dl, J.x, J.gw, J.ld_dl, J.ld_x, J.out, J.in};
+            }
+            if ((e = launch_grad_w_tc(h, dj, m, st)) != cudaSuccess) {
+                timer_end(h, NIRC_K_TRAIN_GRADW, st);
+                return e;
+            }
+        } else if (!det && m < kBlasMinSamples) {
             k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
             count_kernels(h);
         } else if (det) {
@@ -725,15 +735,8 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
                 count_kernels(h);
             }
         } else {
-            // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t];
-            // with tensor-core training the products run on the tensor cores in TF32 (10-bit
-            // mantissas, FP32 range and accumulation)
+            // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t]
             cublasHandle_t bh = static_cast<cublasHandle_t>(h->blas);
-            if (cublasSetMathMode(bh, tcmode ? CUBLAS_TF32_TENSOR_OP_MATH : CUBLAS_PEDANTIC_MATH) !=
-                CUBLAS_STATUS_SUCCESS) {
-                timer_end(h, NIRC_K_TRAIN_GRADW, st);
-                return cudaErrorNotSupported;
-            }
             const float one = 1.f;
             // (one GEMM per layer: a strided-batched GEMM over the hidden layers, tried, runs
             // without split-K and takes 10x longer at 2^18 samples)

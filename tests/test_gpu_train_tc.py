@@ -1,8 +1,8 @@
 """Tensor-core training (nirc_set_train_precision(NIRC_FP16_TC)): one
 kernel per chunk runs the forward with FP16 operands, the loss of eq. 12 and
 the backward with FP16 operands (deltas scaled per record by a power
-of two) on tcgen05; the hash-table scatter stays FP32, the weight gradients
-are TF32 tensor-core GEMMs from 2^16 samples per pass.
+of two) on tcgen05; the hash-table scatter stays FP32; the weight and bias
+gradients of all layers are a second tcgen05 kernel (BF16 operands).
 
 Checked against the oracle's FP64 loss and gradient on ragged batches with
 invalid rows, for the frequency input, the 16-level hash grid, the paper's
@@ -106,11 +106,12 @@ def _grad_errors(cfg, g, g_ref):
     return errs, l2, cos
 
 
-@pytest.mark.parametrize("name,n", [(k, 5000) for k in CONFIGS] + [("hash16", (1 << 16) + 300), ("hash16", 100)])
+@pytest.mark.parametrize("name,n", [(k, 5000) for k in CONFIGS] + [("hash16", (1 << 16) + 301), ("hash16", 100)])
 def test_tc_train_step_matches_oracle(N, oracle, name, n):
-    """n = 5000: 39 tiles of 128 and a ragged tail of 8, weight gradients by
-    the FP32 SIMT kernel; n = 2^16 + 300: weight gradients by TF32 GEMMs;
-    n = 100: one partly filled tile."""
+    """n = 5000: 39 tiles of 128 and a ragged tail of 8 (16-byte loads in
+    the weight-gradient kernel); n = 2^16 + 301: 115 sample slices of the
+    weight-gradient kernel with a ragged last one, rows of odd length
+    (scalar loads); n = 100: one partly filled tile."""
     cfg = CONFIGS[name]()
     params = _params(cfg, 11)
     recs, dirs, tg = _batch(cfg, n, 12)
