@@ -17,7 +17,7 @@ namespace nirc {
 
 namespace {
 
-constexpr uint32_t kDwThreads = 128;
+constexpr uint32_t kDwThreads = 256;  // two warpgroups share the loads; warps 0-3 own the TMEM lanes
 constexpr uint32_t kDwBlock = 64;       // samples per operand block
 constexpr uint32_t kDwN = 80;           // B rows: inputs, the ones row, zeros
 constexpr uint32_t kDwA = 16384;        // 128 rows x 128 bytes
@@ -120,22 +120,23 @@ __global__ void __launch_bounds__(kDwThreads) k_grad_w_tc(DwJobs jobs, uint64_t 
         }
         tc::fence_after_sync();
     }
-    if (!abort) {
+    if (!abort && warp < 4) {
+        // row t of D (TMEM lane t): 32 columns at a time; column `in` is the bias sum
         const uint32_t trow = tmem + ((32u * warp) << 16);
-        uint32_t v0[32], v1[32], v2[32];
-        tc::tmem_ld32(trow, v0);
-        tc::tmem_ld32(trow + 32u, v1);
-        tc::tmem_ld32(trow + 64u, v2);
-        tc::tmem_wait_ld();
-        if (t < J.out) {
-            float* gw = J.gw + (uint64_t)t * J.in;
-            for (uint32_t i = 0; i < J.in; ++i) {
-                const uint32_t bits = i < 32 ? v0[i] : (i < 64 ? v1[i - 32] : v2[i - 64]);
-                atomicAdd(gw + i, __uint_as_float(bits));
+        float* gw = J.gw + (uint64_t)t * J.in;
+#pragma unroll 1
+        for (uint32_t c0 = 0; c0 < kDwN; c0 += 32) {
+            uint32_t v[32];
+            tc::tmem_ld32(trow + c0, v);
+            tc::tmem_wait_ld();
+            if (t < J.out) {
+#pragma unroll
+                for (uint32_t k = 0; k < 32; ++k) {
+                    const uint32_t i = c0 + k;
+                    if (i < J.in) atomicAdd(gw + i, __uint_as_float(v[k]));
+                    else if (i == J.in) atomicAdd(J.gw + (uint64_t)J.out * J.in + t, __uint_as_float(v[k]));
+                }
             }
-            const uint32_t i = J.in;
-            const uint32_t bb = i < 64 ? v1[i - 32] : v2[i - 64];
-            atomicAdd(J.gw + (uint64_t)J.out * J.in + t, __uint_as_float(bb));
         }
     }
     tc::fence_before_sync();
