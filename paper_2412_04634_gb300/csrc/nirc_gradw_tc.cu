@@ -4,12 +4,13 @@
 //   D [o][i] = sum_t delta[o][t] x[i][t]   (i < in)   = dW
 //   D [o][in] = sum_t delta[o][t]                       = db
 // with A = the delta rows (M = 128: rows >= out are zero) and B = the input
-// rows plus one row of ones (N = 80).  A CTA (one warpgroup) takes one
+// rows plus one row of ones (N = 80).  A CTA (two warpgroups) takes one
 // layer and a slice of the samples, walks it in blocks of 64 samples (a
 // 128-byte BF16 row), converting the FP32 values to BF16 into a 128-byte
 // swizzled operand stage while the MMA of the previous block runs, and adds
-// its 64 x (in + 1) sums into the gradient with float atomics.  Every
-// mbarrier wait is bounded; a timeout sets *err.
+// its out x (in + 1) sums into the gradient with float atomics (warps 0-3,
+// which own the accumulator's TMEM lanes).  Every mbarrier wait is bounded;
+// a timeout sets *err.
 #include "nirc_gradw_tc.h"
 #include "nirc_tc.cuh"
 
@@ -158,8 +159,8 @@ cudaError_t launch_grad_w_tc(const nirc_handle* h, const DwJobs& jobs, uint64_t 
         vec = vec && (J.ld_dl % 4 == 0) && (J.ld_x % 4 == 0) && (reinterpret_cast<uintptr_t>(J.dl) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(J.x) % 16 == 0);
     }
-    // about four CTAs per SM over all jobs (one warpgroup each, 54 KB of shared memory: the
-    // loads of a block are latency-bound), at least 512 samples each (a multiple of the block)
+    // about four CTAs per SM over all jobs (54 KB of shared memory each: the loads of a block
+    // are latency-bound), at least 512 samples each (a multiple of the block)
     const uint64_t want = (4ull * (uint64_t)h->num_sms + jobs.n_jobs - 1) / jobs.n_jobs;
     uint64_t slice = (m + want - 1) / want;
     if (slice < 512) slice = 512;
