@@ -64,10 +64,10 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     tmp = LIB + ".tmp"
-    # cuBLAS (plain GEMMs of the weight gradients) from the same toolkit; the
-    # rpath lets the loader find it without an environment setting
+    # the CUDA runtime from the same toolkit; the rpath lets the loader find
+    # it without an environment setting
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L" + cuda_lib, "-lcublas", "-lcudart",
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L" + cuda_lib, "-lcudart",
            "-Xlinker", "-rpath=" + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -326,9 +326,7 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
 }
 
 nirc_status reserve_train_scratch(nirc_handle* h, uint64_t n) {
-    nirc_status s = ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h, n), "training");
-    if (s == NIRC_OK && !h->deterministic) s = cuda_status(prepare_blas(h), "training (cuBLAS handle)");
-    return s;
+    return ensure(&h->train_scratch, &h->train_scratch_bytes, train_scratch_bytes(h, n), "training");
 }
 
 }  // namespace nirc
@@ -473,7 +471,6 @@ nirc_status nirc_destroy(nirc_handle* h) {
     cudaFree(h->fp8_amax);
     cudaFree(h->scratch);
     cudaFree(h->train_scratch);
-    release_blas(h);
     for (int i = 0; i < h->n_pool; ++i) cudaEventDestroy(h->event_pool[i]);
     delete[] h->event_pool;
     delete[] h->pending;

@@ -87,8 +87,6 @@ struct nirc_handle {
     size_t train_scratch_bytes = 0;
     int store_activations = 1;      // 0: recompute activations chunk by chunk
     int deterministic = 0;          // 1: order-independent gradient sums
-    void* blas = nullptr;           // cuBLAS handle (weight-gradient GEMMs), created on first use
-    void* blas_ws = nullptr;        // its fixed workspace (no allocation inside captured graphs)
     uint64_t recompute_chunk = 1ull << 15;
     float* loss_accum = nullptr;    // one float
     unsigned long long* work_counter = nullptr;  // pixel counter of the path-tracing kernel
@@ -205,8 +203,6 @@ cudaError_t launch_train_tc(const nirc_handle* h, const nirc_record* recs, const
 
 // nirc_train.cu
 size_t train_scratch_bytes(const nirc_handle* h, uint64_t n);
-void release_blas(nirc_handle* h);
-cudaError_t prepare_blas(nirc_handle* h);
 cudaError_t launch_train_step(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* targets,
                               uint64_t n, float* d_loss, cudaStream_t st);
 cudaError_t launch_query_bwd(nirc_handle* h, const nirc_record* recs, const float* dirs, const float* grad_out,

@@ -172,8 +172,7 @@ nirc_status nirc_server::enqueue_request(Req* q, cudaStream_t st) {
     const void* blob = sc.frames + (uint64_t)(q->r.frame % sc.n_frames) * sc.stride;
     float* img = reinterpret_cast<float*>(arena_base + q->img_off);
     void* scratch = arena_base + q->scr_off;
-    if (cfg.train_samples && (sc.h->train_scratch_bytes < train_scratch_bytes(sc.h, cfg.train_samples) ||
-                              (!sc.h->deterministic && !sc.h->blas))) {
+    if (cfg.train_samples && sc.h->train_scratch_bytes < train_scratch_bytes(sc.h, cfg.train_samples)) {
         // the handle's training mode changed after registration; scratch
         // cannot grow inside a batch (it may be captured into a graph)
         set_error("nirc_server: scene %u needs more training scratch than was reserved at registration "

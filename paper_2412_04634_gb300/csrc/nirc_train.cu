@@ -22,7 +22,8 @@
 //                over 32-sample chunks staged in shared memory, combined by
 //                float atomics, or in deterministic mode by block partials
 //                summed in a fixed order); passes of >= 2^18 samples in the
-//                default mode use cuBLAS (FP32 math), faster at that length
+//                default mode use k_grad_w_big (a block per layer and slice
+//                of the samples, double-buffered stages of 64 samples)
 //  k_adam        dense bias-corrected Adam over every parameter (untouched
 //                hash entries have g = 0), FP32 master weights and moments,
 //                FP16 copy of the hash table refreshed in the same pass
@@ -45,8 +46,6 @@
 // that chunk's backward and weight gradients).  Recomputation trades one
 // extra forward for O(chunk) instead of O(n) activation memory; a chunk of
 // 2^15 samples keeps the activation buffer (~78 MB) inside the 129 MB L2.
-#include <cublas_v2.h>
-
 #include <cmath>
 
 #include "nirc_gradw_tc.h"
@@ -104,38 +103,10 @@ size_t train_scratch_bytes(const nirc_handle* h, uint64_t n) {
     return (size_t)f * sizeof(float) + 256;
 }
 
-constexpr size_t kBlasWorkspace = 32u << 20;
-// Below this many samples per pass the hand-written k_grad_w is faster than
-// the library GEMM for these skinny shapes (64 x 72 outputs, K = samples).
-constexpr uint64_t kBlasMinSamples = 1ull << 18;
-
-cudaError_t prepare_blas(nirc_handle* h) {
-    if (h->blas) return cudaSuccess;
-    cublasHandle_t b = nullptr;
-    if (cublasCreate(&b) != CUBLAS_STATUS_SUCCESS) return cudaErrorNotSupported;
-    cudaError_t e = cudaMalloc(&h->blas_ws, kBlasWorkspace);
-    if (e != cudaSuccess) {
-        h->blas_ws = nullptr;
-        cublasDestroy(b);
-        return e;
-    }
-    if (cublasSetWorkspace(b, h->blas_ws, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetMathMode(b, CUBLAS_PEDANTIC_MATH) != CUBLAS_STATUS_SUCCESS) {
-        cublasDestroy(b);
-        cudaFree(h->blas_ws);
-        h->blas_ws = nullptr;
-        return cudaErrorNotSupported;
-    }
-    h->blas = b;
-    return cudaSuccess;
-}
-
-void release_blas(nirc_handle* h) {
-    if (h->blas) cublasDestroy(static_cast<cublasHandle_t>(h->blas));
-    cudaFree(h->blas_ws);
-    h->blas = nullptr;
-    h->blas_ws = nullptr;
-}
+// From this many samples per pass on, the sliced k_grad_w_big computes the
+// weight gradients (k_grad_w's one 32-sample chunk per block iteration leaves
+// it bound by its loads and barriers on long passes).
+constexpr uint64_t kGradBigMinSamples = 1ull << 18;
 
 static TrainPtrs carve(void* base, const NetShape& s, uint64_t n, uint64_t chunk) {
     float* f = reinterpret_cast<float*>(base);
@@ -447,48 +418,6 @@ struct GradJob {
     uint64_t ld_dl, ld_x;
     uint32_t out, in;
 };
-// Bias gradients of every layer in one launch: db[o] += sum_t delta[o][t]
-// over the m samples of a pass; row r of the grid walks layer jobs in order
-// (64 rows per hidden layer, `out` rows for the output layer), blockIdx.y
-// splits the samples, one float atomic per block and row.
-struct BiasRows {
-    const float* dl[kMaxHidden + 1];
-    uint32_t ld[kMaxHidden + 1];
-    float* gb[kMaxHidden + 1];
-    uint32_t out[kMaxHidden + 1];
-    uint32_t n_jobs;
-};
-
-__global__ void k_bias_grad(BiasRows br, uint64_t m, uint64_t per_block) {
-    uint32_t r = blockIdx.x, j = 0;
-    while (j < br.n_jobs && r >= br.out[j]) r -= br.out[j++];
-    if (j >= br.n_jobs) return;
-    const float* row = br.dl[j] + (uint64_t)r * br.ld[j];
-    const uint64_t t0 = (uint64_t)blockIdx.y * per_block;
-    const uint64_t t1 = t0 + per_block < m ? t0 + per_block : m;
-    float acc = 0.f;
-    uint64_t tv = t0;  // 16-byte loads where the row allows (per_block is a multiple of 4)
-    if ((reinterpret_cast<uintptr_t>(row) & 15u) == 0) {
-        const uint64_t nv = (t1 - t0) >> 2;
-        const float4* r4 = reinterpret_cast<const float4*>(row + t0);
-        for (uint64_t i = threadIdx.x; i < nv; i += blockDim.x) {
-            const float4 v = __ldg(r4 + i);
-            acc += (v.x + v.y) + (v.z + v.w);
-        }
-        tv = t0 + 4 * nv;
-    }
-    for (uint64_t t = tv + threadIdx.x; t < t1; t += blockDim.x) acc += row[t];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    __shared__ float part[8];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float sum = 0.f;
-        for (uint32_t w = 0; w < blockDim.x / 32; ++w) sum += part[w];
-        atomicAdd(br.gb[j] + r, sum);
-    }
-}
-
 struct GradJobs {
     GradJob j[kMaxHidden + 1];
     float* part;     // deterministic mode: block b writes W/b of job l at
@@ -543,6 +472,108 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_w(GradJobs jobs, uint64_t
                 if constexpr (kPartial) jobs.part[blockIdx.x * jobs.pstride + (uint64_t)(dst - jobs.grad_base)] = acc[a][b];
                 else atomicAdd(dst, acc[a][b]);
             }
+        }
+}
+
+// Weight and bias gradients of passes of many samples (FP32): one block per
+// (layer, slice of the samples) accumulates the whole dW | db tile of its
+// layer over its slice and adds it into the gradient with float atomics at
+// the end.  The samples stream through shared memory in stages of 64 in the
+// [feature][sample] layout of the stored columns (coalesced loads, the next
+// stage's loads in flight in registers while the current one is consumed);
+// thread (ot, it) owns outputs 4 ot .. 4 ot + 3 and inputs it + 16 b
+// (b < 6, the input after the last one being the bias row of ones), and
+// reads 4 consecutive samples of each with one 16-byte shared load.
+constexpr int kGwStage = 64;
+constexpr int kGwThreads = 256;
+constexpr int kGwRowPad = kGwStage + 4;  // 68 floats: 16-byte rows, rows of consecutive `it` on distinct banks
+constexpr int kGwDsFloats = 64 * kGwRowPad;
+constexpr int kGwDsLoads = 64 * kGwStage / kGwThreads;  // 16
+// NB input groups of 16 rows: inputs + bias row <= 16 NB (5 for up to 79 inputs, 6 for up to 95)
+template <int NB>
+constexpr size_t gw_smem_bytes() { return 2 * (size_t)(kGwDsFloats + 16 * NB * kGwRowPad) * sizeof(float); }
+
+template <int NB>
+__global__ void __launch_bounds__(kGwThreads, 2) k_grad_w_big(GradJobs jobs, uint64_t n, uint64_t slice) {
+    constexpr int kGwXsFloats = 16 * NB * kGwRowPad;
+    constexpr int kGwXsLoads = kGwStage * 16 * NB / kGwThreads;  // 4 NB
+    const GradJob J = jobs.j[blockIdx.y];
+    extern __shared__ __align__(16) float gw_smem[];
+    const int tid = threadIdx.x, ot = tid >> 4, it = tid & 15;
+    const uint64_t t_begin = (uint64_t)blockIdx.x * slice;
+    const uint64_t t_end = t_begin + slice < n ? t_begin + slice : n;
+    if (t_begin >= t_end) return;
+    const int xrows = (int)J.in + 1;  // inputs and the bias row
+    // rows the layer does not use stay zero in both buffers
+    for (int k = tid; k < 2 * (kGwDsFloats + kGwXsFloats); k += kGwThreads) gw_smem[k] = 0.f;
+    float rd[kGwDsLoads], rx[kGwXsLoads];
+    auto fetch = [&](uint64_t t0) {
+#pragma unroll
+        for (int q = 0; q < kGwDsLoads; ++q) {
+            const int idx = tid + kGwThreads * q, o = idx / kGwStage;
+            const uint64_t t = t0 + (uint64_t)(idx % kGwStage);
+            rd[q] = (o < (int)J.out && t < t_end) ? __ldg(J.dl + (uint64_t)o * J.ld_dl + t) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < kGwXsLoads; ++q) {
+            const int idx = tid + kGwThreads * q, i = idx / kGwStage;
+            const uint64_t t = t0 + (uint64_t)(idx % kGwStage);
+            float v = 0.f;
+            if (t < t_end) v = i < (int)J.in ? __ldg(J.x + (uint64_t)i * J.ld_x + t) : (i == (int)J.in ? 1.f : 0.f);
+            rx[q] = v;
+        }
+    };
+    auto stash = [&](int buf) {
+        float* ds = gw_smem + buf * (kGwDsFloats + kGwXsFloats);
+        float* xs = ds + kGwDsFloats;
+#pragma unroll
+        for (int q = 0; q < kGwDsLoads; ++q) {
+            const int idx = tid + kGwThreads * q;
+            ds[(idx / kGwStage) * kGwRowPad + idx % kGwStage] = rd[q];
+        }
+#pragma unroll
+        for (int q = 0; q < kGwXsLoads; ++q) {
+            const int idx = tid + kGwThreads * q, i = idx / kGwStage;
+            if (i < xrows) xs[i * kGwRowPad + idx % kGwStage] = rx[q];
+        }
+    };
+    float acc[4][NB] = {};
+    fetch(t_begin);
+    __syncthreads();  // the zero fill before the first stash
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (uint64_t t0 = t_begin; t0 < t_end; t0 += kGwStage) {
+        const bool more = t0 + kGwStage < t_end;
+        if (more) fetch(t0 + kGwStage);
+        const float* ds = gw_smem + buf * (kGwDsFloats + kGwXsFloats);
+        const float* xs = ds + kGwDsFloats;
+#pragma unroll 4
+        for (int tt = 0; tt < kGwStage; tt += 4) {
+            float4 d[4], x[NB];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) d[a] = *reinterpret_cast<const float4*>(ds + (4 * ot + a) * kGwRowPad + tt);
+#pragma unroll
+            for (int b = 0; b < NB; ++b) x[b] = *reinterpret_cast<const float4*>(xs + (it + 16 * b) * kGwRowPad + tt);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    acc[a][b] += d[a].x * x[b].x + d[a].y * x[b].y + d[a].z * x[b].z + d[a].w * x[b].w;
+        }
+        if (more) {
+            stash(buf ^ 1);
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int o = 4 * ot + a, i = it + 16 * b;
+            if (o < (int)J.out && i <= (int)J.in)
+                atomicAdd(i < (int)J.in ? J.gw + (uint64_t)o * J.in + i : J.gw + (uint64_t)J.out * J.in + o, acc[a][b]);
         }
 }
 
@@ -617,11 +648,6 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
     DetPtrs dp{};
     if (det) dp = carve_det(h, h->train_scratch, n, chunk);
     cudaError_t e;
-    if (!det) {
-        if ((e = prepare_blas(h)) != cudaSuccess) return e;
-        if (cublasSetStream(static_cast<cublasHandle_t>(h->blas), st) != CUBLAS_STATUS_SUCCESS)
-            return cudaErrorNotSupported;
-    }
     if ((e = cudaMemsetAsync(h->grad, 0, s.n_dev * sizeof(float), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(h->loss_accum, 0, sizeof(float), st)) != cudaSuccess) return e;
     if (det_hash) {
@@ -723,7 +749,7 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
                 timer_end(h, NIRC_K_TRAIN_GRADW, st);
                 return e;
             }
-        } else if (!det && m < kBlasMinSamples) {
+        } else if (!det && (m < kGradBigMinSamples || s.n_in + 1 > 96)) {  // k_grad_w_big holds <= 95 inputs
             k_grad_w<false><<<dim3((uint32_t)gx, s.hidden + 1), kGradThreads, 0, st>>>(jobs, m);
             count_kernels(h);
         } else if (det) {
@@ -735,34 +761,22 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
                 count_kernels(h);
             }
         } else {
-            // dW[o][i] += sum_t delta[o][t] x[i][t] (column-major: C(in x out) = X^T D), db[o] += sum_t delta[o][t]
-            cublasHandle_t bh = static_cast<cublasHandle_t>(h->blas);
-            const float one = 1.f;
-            // (one GEMM per layer: a strided-batched GEMM over the hidden layers, tried, runs
-            // without split-K and takes 10x longer at 2^18 samples)
-            bool ok = true;
-            for (uint32_t l = 0; l <= s.hidden && ok; ++l) {
-                const GradJob& J = jobs.j[l];
-                ok = cublasSgemm(bh, CUBLAS_OP_T, CUBLAS_OP_N, (int)J.in, (int)J.out, (int)m, &one, J.x, (int)J.ld_x,
-                                 J.dl, (int)J.ld_dl, &one, J.gw, (int)J.in) == CUBLAS_STATUS_SUCCESS;
-            }
-            if (!ok) {
+            // long passes: one block per (layer, slice of about 4 per SM's share of the samples)
+            uint64_t slice = (m * (s.hidden + 1) + 4ull * h->num_sms - 1) / (4ull * h->num_sms);
+            slice = (slice + kGwStage - 1) / kGwStage * kGwStage;
+            if (slice < 1024) slice = 1024;
+            const uint64_t n_slices = (m + slice - 1) / slice;
+            const bool nb5 = s.n_in + 1 <= 80;
+            const size_t smem = nb5 ? gw_smem_bytes<5>() : gw_smem_bytes<6>();
+            e = cudaFuncSetAttribute(nb5 ? k_grad_w_big<5> : k_grad_w_big<6>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) {
                 timer_end(h, NIRC_K_TRAIN_GRADW, st);
-                return cudaErrorNotSupported;
+                return e;
             }
-            BiasRows br;
-            uint32_t rows = 0;
-            for (uint32_t l = 0; l <= s.hidden; ++l) {
-                const GradJob& J = jobs.j[l];
-                br.dl[l] = J.dl;
-                br.ld[l] = (uint32_t)J.ld_dl;
-                br.gb[l] = J.gw + (uint64_t)J.out * J.in;
-                br.out[l] = J.out;
-                rows += J.out;
-            }
-            br.n_jobs = s.hidden + 1;
-            const uint64_t per_block = 16384;
-            k_bias_grad<<<dim3(rows, (uint32_t)((m + per_block - 1) / per_block)), 256, 0, st>>>(br, m, per_block);
+            const dim3 grid((uint32_t)n_slices, s.hidden + 1);
+            if (nb5) k_grad_w_big<5><<<grid, kGwThreads, smem, st>>>(jobs, m, slice);
+            else k_grad_w_big<6><<<grid, kGwThreads, smem, st>>>(jobs, m, slice);
             count_kernels(h);
         }
         timer_end(h, NIRC_K_TRAIN_GRADW, st);

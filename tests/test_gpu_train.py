@@ -177,11 +177,11 @@ def test_recompute_matches_stored(N):
     assert np.abs(p1[strong] - p0[strong]).max() <= 1e-6
 
 
-def test_library_weight_gradients_match_simt(N):
-    """Passes of >= 2^18 samples take their weight gradients from cuBLAS
-    (one GEMM per layer, all biases in one reduction kernel); 2^17-sample
-    chunks of the same batch take them from k_grad_w: the two agree up to
-    the order of the sums."""
+def test_sliced_weight_gradients_match_chunked(N):
+    """Passes of >= 2^18 samples take their weight and bias gradients from
+    k_grad_w_big (a block per layer and slice of the samples, a ragged last
+    slice and stage here); 2^17-sample chunks of the same batch take them
+    from k_grad_w: the two agree up to the order of the sums."""
     import torch
     cfg = _hash_cfg(hidden=4)
     params = scenes.init_params(cfg, 65)
@@ -198,8 +198,8 @@ def test_library_weight_gradients_match_simt(N):
         torch.cuda.synchronize()
         res.append(cache.get_grads().numpy().astype(np.float64))
         cache.close()
-    g_blas, g_simt = res
-    _assert_grad_close(cfg, g_blas, g_simt, tol=1e-5)
+    g_sliced, g_chunked = res
+    _assert_grad_close(cfg, g_sliced, g_chunked, tol=1e-5)
 
 
 def test_scatter_with_colliding_entries(N, oracle):
