@@ -348,14 +348,20 @@ nirc_status nirc_estimate_frame(nirc_handle* h, const void* d_scene, const nirc_
  * it use this entry point instead.  It runs the same kernels, with the same
  * arguments and results, on a fixed 4 MiB scratch area compiled into the
  * library, and calls no cudaMalloc, cudaFree or other allocating routine.
- * Limit: W * H * (96 + 32 * M) bytes (each of the three parts rounded up to
- * 256) must fit in 4 MiB, e.g. 32,768 pixels at M = 1; larger frames return
- * NIRC_ERR_BUDGET.  The first call on each device looks up the area's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call on a device shares the area
- * and it keeps the last call's contents: calls that overlap on the GPU race
- * on it, so order them on one stream.  Every GPU that loads the library holds
- * the 4 MiB until the process exits. */
+ * Limit, per estimator (P = W * H; each part rounded up to 256 bytes; the
+ * sum must fit in 4 MiB, larger frames return NIRC_ERR_BUDGET and the error
+ * string names the estimator and the bytes needed):
+ *   NIRC_EST_TWO_LEVEL     P * (96 + 32 M)   e.g. 32,768 pixels at M = 1
+ *   NIRC_EST_BIASED_BTH    P * 112           e.g. about 37,400 pixels
+ *   NIRC_EST_MULTI_VERTEX  P * (96 + 288 M)  e.g. about 10,900 pixels at M = 1
+ * The first call on each device looks up the area's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life
+ * of the process; make that first call before any stream capture, and do
+ * not use the library across a cudaDeviceReset (which invalidates the
+ * address, as it does every handle's device memory).  Every call on a device
+ * shares the area and it keeps the last call's contents: calls that overlap
+ * on the GPU race on it, so order them on one stream.  Every GPU that loads
+ * the library holds the 4 MiB until the process exits. */
 nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d_scene, const nirc_frame_desc* desc,
                                         float* d_out_rgba, const nirc_frame_aux* aux, void* stream);
 
@@ -454,8 +460,8 @@ nirc_status nirc_frame_mrse(const float* d_img_rgba, const float* d_ref_rgba, ui
  * more kernels) is bracketed by CUDA events on its stream; nirc_timing_read
  * waits for the recorded events and returns, per kernel class since the
  * last enable, the summed device time of its phases and the number of the
- * library's own kernels they launched (cuBLAS kernels inside a phase count
- * in its time, not in its launches).  Classes: */
+ * library's own kernels they launched (every kernel of a phase is the
+ * library's own).  Classes: */
 enum {
     NIRC_K_PATH_TRACE = 0,   /* camera hits, records, residual paths */
     NIRC_K_CACHE = 1,        /* cache integral (encodings, MLP, per-pixel sums) */

@@ -16,7 +16,9 @@
 // that every GPU loading the library holds until the process exits.  Host
 // code never uses the array's name as an address: the first call on each
 // device looks the device address up with cudaGetSymbolAddress (with that
-// device current) and later calls reuse it.  All calls on a device share the
+// device current) and later calls reuse it for the life of the process (a
+// cudaDeviceReset invalidates it, as it invalidates every handle's device
+// memory).  All calls on a device share the
 // array; calls that overlap on the GPU (different streams, or different
 // handles, without ordering between them) race on it.
 #include <mutex>
@@ -74,9 +76,12 @@ extern "C" nirc_status nirc_estimate_frame_noalloc(nirc_handle* h, const void* d
     }
     const size_t need = frame_scratch_bytes(P, fd.n_resid, fd.estimator);
     if (need > kNoAllocScratchBytes) {
-        set_error("nirc_estimate_frame_noalloc: frame needs %zu bytes of scratch (W*H*(96 + 32*M) rounded), more than "
-                  "the fixed %zu-byte area; use nirc_estimate_frame or a smaller tile",
-                  need, kNoAllocScratchBytes);
+        static const char* const names[3] = {"two-level, W*H*(96 + 32*M)", "biased BTH, W*H*112",
+                                             "multi-vertex, W*H*(96 + 288*M)"};
+        set_error("nirc_estimate_frame_noalloc: a %ux%u frame (estimator %u: %s, M = %u) needs %zu bytes of scratch, "
+                  "more than the fixed %zu-byte area; use nirc_estimate_frame or a smaller tile",
+                  fd.width, fd.height, fd.estimator, fd.estimator < 3 ? names[fd.estimator] : "?", fd.n_resid, need,
+                  kNoAllocScratchBytes);
         return NIRC_ERR_BUDGET;
     }
     int dev = 0;

@@ -293,7 +293,9 @@ def nirc_estimate_frame(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba:
 def nirc_estimate_frame_noalloc(h, scene: torch.Tensor, desc: nirc_frame_desc, out_rgba: torch.Tensor,
                                 lc=None, lr=None, sig=None, count=None, row_n=None, rays=None, stream=None):
     """nirc_estimate_frame on the library's fixed scratch area (no device
-    allocation during the call; frames up to W*H*(96+32*M) <= 4 MiB)."""
+    allocation during the call).  Frames must fit its 4 MiB: W*H*(96+32*M)
+    bytes for the two-level estimator, W*H*112 for the biased (BTH) one,
+    W*H*(96+288*M) for the multi-vertex one."""
     aux = nirc_frame_aux(_ptr(lc), _ptr(lr), _ptr(sig), _ptr(count), _ptr(row_n), _ptr(rays))
     use_aux = any(x is not None for x in (lc, lr, sig, count, row_n, rays))
     _check(_lib.nirc_estimate_frame_noalloc(h, _ptr(scene), ctypes.byref(desc), _ptr(out_rgba),
