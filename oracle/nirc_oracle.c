@@ -1701,7 +1701,7 @@ void orc_gen_train(const uint8_t* blob, uint32_t W, uint32_t H, uint64_t T, uint
  * cache with the upstream gradient gout. */
 static double loss_grad_core(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
                              const double* targets, const double* gout, uint64_t T, const double* den_fixed,
-                             double* grad)
+                             double* grad, int abs_hash)
 {
     uint64_t n_mlp = mlp_param_count(c);
     const double* hash = params + n_mlp;
@@ -1732,13 +1732,14 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
         double e[1024];
         double pre[MAX_LAYERS * MAX_WIDTH], act[MAX_LAYERS * MAX_WIDTH];
         double delta[MAX_WIDTH], delta_prev[MAX_WIDTH > 1024 ? MAX_WIDTH : 1024];
+        double dabs[MAX_WIDTH], dabs_prev[MAX_WIDTH > 1024 ? MAX_WIDTH : 1024];
 #pragma omp for schedule(static)
         for (int64_t t = 0; t < (int64_t)T; t++) {
             if (!gout && !(recs[t].flags & 1u)) continue;
             double z[3];
             encode(c, hash, &recs[t], dirs + 3 * t, e);
             mlp_forward(c, params, e, pre, act, z);
-            double dz[3];
+            double dz[3], dzabs[3];
             double lt = 0.0;
             for (int k = 0; k < 3; k++) {
                 int vis = c->output == 1;
@@ -1761,10 +1762,22 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
                 }
                 /* dn/dz: exp' = n (0 above the clamp), sigmoid' = V (1 - V) */
                 dz[k] = vis ? dn * nv * (1.0 - nv) : (clamped ? 0.0 : dn * nv);
+                /* abs mode: the same with |f| + |n| in place of f - n (the scale of f - n's rounding) */
+                if (abs_hash && !gout) {
+                    double f = targets[3 * t + k];
+                    double den = vis ? 1.0 : nv * nv + c->loss_eps;
+                    double dna = 2.0 * (fabs(f) + fabs(nv)) / den * scale;
+                    dzabs[k] = vis ? dna * nv * (1.0 - nv) : (clamped ? 0.0 : dna * nv);
+                } else {
+                    dzabs[k] = fabs(dz[k]);
+                }
             }
             loss_part[t] = lt;
             /* Walk the layers backwards: delta = dL/d(pre-activation). */
-            for (int k = 0; k < 3; k++) delta[k] = dz[k];
+            for (int k = 0; k < 3; k++) {
+                delta[k] = dz[k];
+                dabs[k] = dzabs[k];
+            }
             int out = 3;
             uint64_t off = n_mlp;
             for (int l = H; l >= 0; l--) {
@@ -1779,14 +1792,23 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
                     for (int i = 0; i < in; i++) gW[(uint64_t)o * in + i] += delta[o] * x[i];
                 }
                 for (int i = 0; i < in; i++) {
-                    double s = 0.0;
-                    for (int o = 0; o < out; o++) s += Wl[(uint64_t)o * in + i] * delta[o];
+                    double s = 0.0, sa = 0.0;
+                    for (int o = 0; o < out; o++) {
+                        s += Wl[(uint64_t)o * in + i] * delta[o];
+                        sa += fabs(Wl[(uint64_t)o * in + i]) * dabs[o];
+                    }
                     delta_prev[i] = s;
+                    dabs_prev[i] = sa;
                 }
                 if (l > 0) {
-                    for (int i = 0; i < in; i++) delta[i] = pre[(l - 1) * MAX_WIDTH + i] > 0.0 ? delta_prev[i] : 0.0;
+                    for (int i = 0; i < in; i++) {
+                        const int on = pre[(l - 1) * MAX_WIDTH + i] > 0.0;
+                        delta[i] = on ? delta_prev[i] : 0.0;
+                        dabs[i] = on ? dabs_prev[i] : 0.0;
+                    }
                 } else {
-                    for (int i = 0; i < n_pos; i++) de_all[(size_t)t * n_pos + i] = delta_prev[i];
+                    for (int i = 0; i < n_pos; i++)
+                        de_all[(size_t)t * n_pos + i] = abs_hash ? dabs_prev[i] : delta_prev[i];
                 }
                 out = in;
             }
@@ -1806,9 +1828,10 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
                 double wts[8];
                 orc_hash_level(c, l, recs[t].p, idx, wts);
                 for (int corner = 0; corner < 8; corner++)
-                    for (int f = 0; f < F; f++)
-                        gh[((uint64_t)l * Tab + idx[corner]) * F + f] +=
-                            wts[corner] * de_all[(size_t)t * n_pos + l * F + f];
+                    for (int f = 0; f < F; f++) {
+                        double contrib = wts[corner] * de_all[(size_t)t * n_pos + l * F + f];
+                        gh[((uint64_t)l * Tab + idx[corner]) * F + f] += abs_hash ? fabs(contrib) : contrib;
+                    }
             }
         }
     }
@@ -1821,7 +1844,22 @@ static double loss_grad_core(const o_cfg* c, const double* params, const o_recor
 double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
                            const double* targets, uint64_t T, const double* den_fixed, double* grad)
 {
-    return loss_grad_core(c, params, recs, dirs, targets, NULL, T, den_fixed, grad);
+    return loss_grad_core(c, params, recs, dirs, targets, NULL, T, den_fixed, grad, 0);
+}
+
+/* orc_train_loss_grad with the hash-table part replaced by its running-error
+ * scale: the same backward with every signed sum replaced by the sum of the
+ * absolute values of its terms, i.e. |f| + |n| in place of f - n in dL/dn,
+ * |W| in place of W through the layers (the ReLU masks kept), and
+ * |w_corner| |dL/de| summed over records and corners.  An entry's rounding
+ * error in any implementation of the backward is bounded by a small multiple
+ * of this scale however much its terms cancel (test tolerances per entry).
+ * When every weight and dL/dz is non-negative it equals the gradient.  The
+ * MLP part is the ordinary gradient. */
+double orc_train_loss_grad_abs(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
+                               const double* targets, uint64_t T, double* grad)
+{
+    return loss_grad_core(c, params, recs, dirs, targets, NULL, T, NULL, grad, 1);
 }
 
 /* Gradient of sum_t sum_ch gout[t][ch] * n(record_t, dir_t) with respect to
@@ -1830,7 +1868,7 @@ double orc_train_loss_grad(const o_cfg* c, const double* params, const o_record*
 double orc_query_grad(const o_cfg* c, const double* params, const o_record* recs, const float* dirs,
                       const double* gout, uint64_t T, double* grad)
 {
-    return loss_grad_core(c, params, recs, dirs, NULL, gout, T, NULL, grad);
+    return loss_grad_core(c, params, recs, dirs, NULL, gout, T, NULL, grad, 0);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -71,6 +71,8 @@ def lib():
         L.orc_sampler_pdf32.restype = ctypes.c_float
         L.orc_train_loss_grad.argtypes = [P, P, P, P, P, u64, P, P]
         L.orc_train_loss_grad.restype = f64
+        L.orc_train_loss_grad_abs.argtypes = [P, P, P, P, P, u64, P]
+        L.orc_train_loss_grad_abs.restype = f64
         L.orc_query_grad.argtypes = [P, P, P, P, P, u64, P]
         L.orc_query_grad.restype = f64
         L.orc_adam_step.argtypes = [u64, P, P, P, P, u32, f64, f64, f64, f64]
@@ -281,6 +283,19 @@ def loss_grad(cfg, params, recs, dirs, targets, den_fixed=None):
     den = None if den_fixed is None else np.ascontiguousarray(den_fixed, np.float64)
     loss = lib().orc_train_loss_grad(ctypes.byref(c), _ptr(p), _ptr(r), _ptr(d), _ptr(t), r.shape[0],
                                      None if den is None else _ptr(den), _ptr(g))
+    return float(loss), g
+
+
+def loss_grad_abs(cfg, params, recs, dirs, targets):
+    """loss_grad with the hash-table part replaced, per entry, by the sum of
+    the absolute values of the records' contributions to it."""
+    c = ocfg(cfg)
+    p = _params64(params)
+    r = np.ascontiguousarray(recs)
+    d = np.ascontiguousarray(dirs, np.float32)
+    t = np.ascontiguousarray(targets, np.float64)
+    g = np.zeros(p.shape[0], np.float64)
+    loss = lib().orc_train_loss_grad_abs(ctypes.byref(c), _ptr(p), _ptr(r), _ptr(d), _ptr(t), r.shape[0], _ptr(g))
     return float(loss), g
 
 

@@ -247,6 +247,99 @@ def test_ggx_mixture_weights_integrate_to_albedo(oracle, rough, theta_o):
     assert np.all(np.abs(mean - integral) < 4 * se + 2e-3 * integral), (mean, integral, se)
 
 
+def _ggx_halfvector_quadrature(wo, albedo, rough, nw=1200, nph=720):
+    """Directional albedo int_{ci > 0} f cos dwi and int_{ci > 0} pdf dwi of
+    the Lambertian + GGX material (textbook formulas: Walter et al. 2007,
+    Smith height-correlated G2, Schlick F0 = 0.04; mixture density 1/2 cosine
+    + 1/2 visible normals of Heitz 2018), integrated over the half vector h.
+    With x = tan^2(theta_h) / alpha^2 and s = 1 / (1 + x), D(h) cos(theta_h)
+    dw_h = ds dphi / (2 pi), so even a lobe of roughness 0.05 is resolved by
+    a uniform grid in (s, phi); dw_i = 4 (wo . h) dw_h for the reflection."""
+    a = float(np.float32(rough) * np.float32(rough))
+    a2 = a * a
+    n = np.array([0.0, 0.0, 1.0])
+    co = float(wo @ n)
+    lo = math.sqrt(a2 + (1 - a2) * co * co)
+    s = (np.arange(nw) + 0.5) / nw
+    ph = (np.arange(nph) + 0.5) / nph * 2 * math.pi
+    S, PH = np.meshgrid(s, ph, indexing="ij")
+    tan_h = a * np.sqrt((1.0 - S) / S)
+    ch = 1.0 / np.sqrt(1.0 + tan_h ** 2)
+    sh = tan_h * ch
+    h = np.stack([sh * np.cos(PH), sh * np.sin(PH), ch], -1)
+    oh = h @ wo
+    wi = 2.0 * oh[..., None] * h - wo
+    ci = wi @ n
+    ok = (ci > 0) & (oh > 0)
+    ci_ok = np.where(ok, ci, 1.0)
+    li = np.sqrt(a2 + (1 - a2) * ci_ok * ci_ok)
+    G2 = 2 * ci_ok * co / (co * li + ci_ok * lo)
+    F = 0.04 + 0.96 * (1 - np.clip(oh, 0.0, 1.0)) ** 5
+    # specular: f_s ci dw_i = F D G2 / (4 ci co) ci 4 (o.h) dw_h, with D cos_h dw_h = ds dphi / (2 pi)
+    spec_w = np.where(ok, F * G2 * oh / (co * ch), 0.0)
+    ds_dphi = (1.0 / nw) * (2 * math.pi / nph) / (2 * math.pi)
+    spec = spec_w.sum() * ds_dphi
+    # density of the visible-normal lobe over valid wi: G1(wo) D / (4 co) dw_i = G1 D (o.h) / co dw_h
+    G1 = 2 * co / (co + lo)
+    p_vn = np.where(ok, G1 * oh / (co * ch), 0.0).sum() * ds_dphi
+    albedo_dir = np.asarray(albedo) + spec  # the Lambertian part integrates to rho over the hemisphere
+    return albedo_dir, 0.5 + 0.5 * p_vn
+
+
+@pytest.mark.parametrize("rough,theta_o", [(0.05, 0.3), (0.05, 1.1), (0.08, 0.7), (0.1, 1.35)])
+def test_ggx_low_roughness_against_halfvector_quadrature(oracle, rough, theta_o):
+    """The low-roughness end of the scenes' U[0.05, 1] roughness, where the
+    GGX lobe is a narrow peak that a quadrature in (cos theta_i, phi) misses
+    and where the denominator's reading (sin^2 + a2 cos^2 from normalised
+    cross and dot products) matters most.  Three checks against textbook
+    formulas integrated over the half vector: the sampler's valid fraction
+    equals the mixture density's mass over the upper hemisphere; the mean of
+    the sample weights f cos / p equals the directional albedo; and the
+    oracle's f cos and density, at its own sampled directions (mostly on the
+    specular peak), equal the textbook formulas pointwise."""
+    n = np.array([0.0, 0.0, 1.0])
+    wo = np.array([math.sin(theta_o), 0.0, math.cos(theta_o)], np.float32)
+    wo64 = wo.astype(np.float64)
+    albedo = (0.3, 0.5, 0.7)
+    rec = _lambert_record(n=n, albedo=albedo, material=scenes.MAT_GGX, roughness=rough, wo=wo)
+    albedo_dir, mass = _ggx_halfvector_quadrature(wo64 / np.linalg.norm(wo64), albedo, rough)
+    # the density over the upper hemisphere cannot exceed 1 (the sampler never lands below twice)
+    assert 0.5 < mass <= 1.0 + 1e-6
+    K = 20000
+    ws = np.zeros((K, 3))
+    n_valid = 0
+    a = float(np.float32(rough) * np.float32(rough))
+    a2 = a * a
+    co = float(wo64 @ n) / np.linalg.norm(wo64)
+    lo = math.sqrt(a2 + (1 - a2) * co * co)
+    checked = 0
+    for i in range(K):
+        wi, w, valid, r, lobe = oracle.sample_bsdf(rec, (11, 3), (i, 0, 2))
+        if not valid:
+            continue
+        n_valid += 1
+        ws[i] = w
+        if i % 40 == 0:  # pointwise: oracle f cos and density vs the textbook formulas at this direction
+            fc, pdf = oracle.bsdf_eval(rec, wi)
+            wv = wi.astype(np.float64)
+            wv /= np.linalg.norm(wv)
+            f = _ggx_brdf(n, wo64 / np.linalg.norm(wo64), wv[None, :], albedo, rough)[0]
+            ci = wv[2]
+            hh = wv + wo64 / np.linalg.norm(wo64)
+            hh /= np.linalg.norm(hh)
+            D = a2 / (math.pi * (hh[2] ** 2 * (a2 - 1) + 1) ** 2)
+            pdf_t = 0.5 * ci / math.pi + 0.5 * D * (2 * co / (co + lo)) / (4 * co)
+            assert abs(pdf - pdf_t) <= 1e-3 * pdf_t, (i, pdf, pdf_t)
+            assert np.all(np.abs(fc - f * ci) <= 1e-3 * np.abs(f * ci)), (i, fc, f * ci)
+            checked += 1
+    assert checked > 300
+    frac = n_valid / K
+    assert abs(frac - mass) < 4 * math.sqrt(mass * (1 - mass) / K) + 1e-3, (frac, mass)
+    mean = ws.mean(0)
+    se = ws.std(0) / math.sqrt(K)
+    assert np.all(np.abs(mean - albedo_dir) < 4 * se + 2e-3 * albedo_dir), (mean, albedo_dir, se)
+
+
 def test_black_material_never_scatters(oracle):
     rec = _lambert_record(material=scenes.MAT_BLACK)
     wi, w, valid, r, lobe = oracle.sample_bsdf(rec, (1, 0), (0, 0, 2))
@@ -672,6 +765,42 @@ def test_gradients_match_finite_differences_hashgrid(oracle):
     # untouched table entries get exactly zero gradient
     untouched = np.setdiff1d(np.arange(cfg.n_mlp_params, cfg.n_params), touched)
     assert np.all(g[untouched] == 0)
+
+
+def test_hash_gradient_error_scale(oracle):
+    """loss_grad_abs, the per-entry running-error scale of the table
+    gradient (the backward with |f| + |n| for f - n and |W| for W).  With
+    every weight, feature and dL/dz non-negative (zero targets make
+    dL/dn = 2 n / (n^2 + eps) / (3T) > 0) no sum cancels and it equals the
+    gradient exactly; in general it bounds the gradient entry by entry and
+    is strictly larger where signs mix.  The MLP part is the gradient."""
+    cfg = scenes.NetConfig(pos_encoding=scenes.POS_HASHGRID, hash_levels=4, log2_table=18,
+                           hidden_layers=2, base_res=16, growth=1.5)
+    nm = cfg.n_mlp_params
+    rng = np.random.default_rng(4)
+    T = 24
+    recs, dirs, tg = scenes.training_batch(T, seed=11)
+    recs["p"][:8] = recs["p"][0]  # several records on one cell
+    recs["flags"][5] = 0          # an invalid record contributes nothing
+    pos = np.abs(scenes.init_params(cfg, 6).astype(np.float64))
+    pos[:nm] += 0.01              # positive biases: every ReLU passes
+    pos[nm:] = rng.uniform(0.0, 0.5, cfg.n_hash_params)
+    zero = np.zeros_like(tg, dtype=np.float64)
+    loss, g = oracle.loss_grad(cfg, pos, recs, dirs, zero)
+    loss_a, ga = oracle.loss_grad_abs(cfg, pos, recs, dirs, zero)
+    assert loss_a == loss and np.array_equal(ga[:nm], g[:nm])
+    assert np.count_nonzero(g[nm:]) > 100 and np.all(g[nm:] >= 0)
+    assert np.allclose(ga[nm:], g[nm:], rtol=1e-12, atol=0)
+    # general weights and targets: a bound entry by entry, strict where signs mix
+    params = scenes.init_params(cfg, 6).astype(np.float64)
+    params[:nm] += rng.normal(0, 0.05, nm)
+    params[nm:] = rng.uniform(-0.5, 0.5, cfg.n_hash_params)
+    loss, g = oracle.loss_grad(cfg, params, recs, dirs, tg.astype(np.float64))
+    _, ga = oracle.loss_grad_abs(cfg, params, recs, dirs, tg.astype(np.float64))
+    assert np.array_equal(ga[:nm], g[:nm])
+    assert np.all(ga[nm:] >= np.abs(g[nm:]) * (1 - 1e-12))
+    assert np.array_equal(ga[nm:] > 0, g[nm:] != 0)
+    assert np.median(ga[nm:][g[nm:] != 0] / np.abs(g[nm:][g[nm:] != 0])) > 1.5
 
 
 def test_gradients_finite_differences_1024_samples(oracle):
