@@ -1,32 +1,45 @@
 // nirc_cache_tc.cu -- tensor-core (tcgen05, TMEM accumulators) evaluation of
-// the cache integral, FP16 or BF16 operands with FP32 accumulation.
+// the cache integral: FP16 operands, split BF16 operands (hi + lo) or E4M3
+// hidden layers, always with FP32 accumulation.
 //
 // Work unit: a block of 128 pixels; with S = N + M rows per pixel it holds
 // exactly S row tiles of 128 rows.  One warpgroup (128 threads, thread t =
 // tile row t = TMEM lane t) owns a block at a time; a CTA runs up to five
 // warpgroups so that one warpgroup's SIMT work (sampling, encodings,
-// epilogues) overlaps another's MMAs.
+// epilogues) overlaps another's MMAs.  Each warpgroup owns a slice of tensor
+// memory: the accumulator D (64 columns) and the A operand of the next MMA
+// (32 columns of packed 16-bit pairs; split BF16: a second 32 for the
+// remainders), so the activations go from TMEM to registers to TMEM and
+// never through shared memory (E4M3 hidden-layer operands excepted, which
+// stay in a swizzled shared tile).
 //
 //  pixel stage   thread t encodes pixel t's surface (hash grid or frequency
-//                position features + normal features) into an A tile; one
+//                position features + normal features) into A; one
 //                128x64x64 MMA with the surface columns of layer 0 gives
 //                h_pix = W0[:, pix] e_pix + b0 for the 128 pixels, stored as a
-//                16-bit K-major operand H (K = pixel index).  This is the
-//                paper's shared per-surface encoding: computed once per
-//                shading point and reused by all its N + M rows.
+//                16-bit K-major operand H in shared memory (K = pixel index).
+//                This is the paper's shared per-surface encoding: computed
+//                once per shading point and reused by all its N + M rows.
 //  row tile      thread t samples its row's direction (cache rows) or reads
-//                it (residual rows), encodes it and writes the A row
+//                it (residual rows), encodes it and writes its A row
 //                [e_dir (16) | one-hot of its pixel within a 48-wide window];
 //                layer 0 = W0_dir e_dir + H onehot (1 + up to 3 MMAs, K = 16
-//                each), then the hidden layers (4 MMAs each) and the output
-//                layer (N = 16, 3 used); each epilogue reads its row from
-//                TMEM, adds the bias, applies ReLU, rounds to 16 bits and
-//                writes the next A tile in shared memory.  The network input
-//                and output never touch global memory.
-//  reduction     per-row contributions w * n go to shared memory; one thread
-//                per pixel sums its rows in sample order (compensated FP32),
-//                carrying a pixel that straddles two tiles, and writes the
-//                pixel (eq. L_mlmc = L_e + L_c + L_r).
+//                each), then the hidden layers (4 MMAs and a bias MMA each)
+//                and the output layer (N = 16, 3 used); each epilogue reads its
+//                row from TMEM, applies ReLU, rounds to 16 bits and writes the
+//                next A row back to TMEM.  The network input and output never
+//                touch global memory.
+//  reduction     per-row contributions w * n go to shared memory in row
+//                order; per pixel and channel one thread adds its rows in
+//                sample order with Kahan compensation (eq. L_mlmc = L_e + L_c
+//                + L_r), carrying the running sum and compensation of a pixel
+//                that straddles two tiles, and one thread per finished pixel
+//                writes it.
+//
+// Split BF16 (NIRC_BF16_TC): every 16-bit operand x is carried as hi =
+// bf16(x) and lo = bf16(x - hi); each K step issues hi*hi + lo*hi + hi*lo,
+// which keeps about 16 significant bits of every product (BF16's 8 bits
+// alone miss the 2e-2 bound on n = exp(z) for trained logits of -6 .. -10).
 //
 // The paper's input (NIRC_INPUT_SH): the pixel stage encodes [position |
 // albedo, one-blob normal and roughness]; H is stored pixel-major (row t =
@@ -52,8 +65,7 @@
 
 namespace nirc {
 
-
-size_t tc_image_bytes(uint32_t hidden) { return tcimg::off_scales(hidden) + 64; }
+size_t tc_image_bytes(uint32_t hidden) { return tcimg::bytes_split(hidden); }
 
 constexpr float kE4M3Max = 448.f;
 
@@ -88,14 +100,163 @@ __global__ void k_amax_roll(uint32_t* buf, uint32_t n) {
     }
 }
 
-constexpr uint32_t kMiscBytes = 256;     // mbarriers, TMEM holder, abort flags, FP8 scales and amax
-// Per warpgroup: the two swizzled operand tiles (A 16 KB | H 16 KB, 1024-byte
-// aligned), and apart from them the small arrays (contributions 2 KB | carry
-// slots and warp partials 512 B).
-constexpr uint32_t kWgStride = 32768;
-constexpr uint32_t kOffA = 0, kOffH = 16384;
-constexpr uint32_t kSmallStride = 2560;
-constexpr uint32_t kOffContrib = 0, kOffCarry = 2048;
+constexpr uint32_t kMiscBytes = 256;  // mbarriers, TMEM holder, abort flags, FP8 scales and amax
+// Per warpgroup, shared memory: the swizzled operand tiles (1024-byte
+// aligned; H, and the E4M3 A tile of FP8 mode or the H remainder of split
+// BF16), then apart from them the reduction arrays: row contributions (128 x
+// 8 floats), finished pixel sums (128 x 10 words) and two carry slots.
+constexpr uint32_t kSmallStride = 9728;
+constexpr uint32_t kOffRows = 0, kOffFin = 4096, kOffCarry = 9216;  // rows 128 x 32 B | 128 pixels x 40 B | carry
+constexpr uint32_t kFinWords = 10;                                  // 7 sums + pad + 64-bit signature
+// Per warpgroup, tensor memory columns: D (64) | A (32) | A remainder (32, split BF16).
+constexpr uint32_t kTmD = 0, kTmA = 64, kTmLo = 96;
+
+template <uint32_t AB>
+constexpr uint32_t wg_tile_bytes() { return AB == 0 ? 16384u : 32768u; }
+template <uint32_t AB>
+constexpr uint32_t wg_tmem_cols() { return AB == 1 ? 128u : 96u; }
+
+struct TcArgs {
+    uint32_t W, H, N, M, k0, k1;
+    uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
+    const SceneHeader* env_hd;   // light mode 2 with a visibility cache: cache values times L_env
+    uint32_t env_nprims;
+    uint32_t S, P, n_blocks;
+    uint64_t s_magic;            // floor(2^40 / S) + 1: x / S = (x * s_magic) >> 40 for x S < 2^40
+    float z_clamp;
+    uint32_t img_bytes;
+    NetShape s;
+    GridParams g;
+};
+
+__device__ __forceinline__ uint32_t div_s(uint32_t x, uint64_t magic) {
+    return (uint32_t)(((uint64_t)x * magic) >> 40);
+}
+
+// relu(lo), relu(hi) rounded to BF16 and the remainders, both packed.
+__device__ __forceinline__ void split_relu_bf16(float lo, float hi, uint32_t& w_hi, uint32_t& w_lo) {
+    const float a = fmaxf(lo, 0.f), b = fmaxf(hi, 0.f);
+    w_hi = tc::pack_bf16(a, b);
+    w_lo = tc::pack_bf16(a - __uint_as_float(w_hi << 16), b - __uint_as_float(w_hi & 0xFFFF0000u));
+}
+__device__ __forceinline__ void split_bf16(float lo, float hi, uint32_t& w_hi, uint32_t& w_lo) {
+    w_hi = tc::pack_bf16(lo, hi);
+    w_lo = tc::pack_bf16(lo - __uint_as_float(w_hi << 16), hi - __uint_as_float(w_hi & 0xFFFF0000u));
+}
+
+// Pack 16 consecutive K elements into 8 words of the operand type (and the
+// remainders when kSplit).
+template <uint32_t AB16, bool kSplit>
+__device__ __forceinline__ void pack8w(const float* x, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if constexpr (kSplit) split_bf16(x[2 * j], x[2 * j + 1], hi[j], lo[j]);
+        else hi[j] = pack2<AB16>(x[2 * j], x[2 * j + 1]);
+    }
+}
+
+// Epilogue of one layer for row r: 64 accumulators from TMEM (two halves of
+// 32 columns), times `mul` (kMul: the FP8 scales s_w s_a of the layer),
+// + bias (none for layer 0 of the frequency input, whose h_pix holds b0, and
+// none for 16-bit layers, whose bias came with the MMA; kHrow: layer 0 of
+// the paper's input adds row `pr` of the pixel-major 16-bit tile at `hrow`,
+// and with kSplit its remainder tile at `hrow_lo`), ReLU, then either
+// 16-bit rounding into the TMEM A operand at `ta` (and the remainders at
+// `ta + 32` with kSplit), or, kF8Out, scaling by 1/s_a of the next layer and
+// E4M3 rounding into the shared A tile.  kRec: the warp's amax of the ReLU
+// outputs goes into the shared word at s_amax (atomicMax on bits).
+template <uint32_t AB16, bool kSplit, bool kF8Out, bool kMul, bool kRec, bool kHrow = false>
+__device__ __forceinline__ void epilogue(uint32_t tD, uint32_t ta, const float* __restrict__ bias, float mul,
+                                         float inv_sa, uint32_t stile, uint32_t r, uint32_t* s_amax,
+                                         uint32_t hrow = 0, uint32_t hrow_lo = 0, uint32_t pr = 0) {
+    float mx = 0.f;
+#pragma unroll
+    for (uint32_t half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        tc::tmem_ld32(tD + 32u * half, v);
+        tc::tmem_wait_ld();
+        float x[32];
+        if constexpr (kHrow) {
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {
+                const uint32_t c = 4u * half + q;
+                const uint32_t off = (pr >> 3) * 1024u + (pr & 7u) * 128u + (((c ^ pr) & 7u) << 4);
+                const uint4 hv = tc::lds128(hrow + off);
+                uint4 hl = make_uint4(0u, 0u, 0u, 0u);
+                if constexpr (kSplit) hl = tc::lds128(hrow_lo + off);
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w}, lw[4] = {hl.x, hl.y, hl.z, hl.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float2 hh = tc::unpack2<AB16>(hw[j]);
+                    if constexpr (kSplit) {
+                        const float2 ll = tc::unpack2<1>(lw[j]);
+                        hh.x += ll.x;
+                        hh.y += ll.y;
+                    }
+                    const float2 a2 = make_float2(__uint_as_float(v[8 * q + 2 * j]), __uint_as_float(v[8 * q + 2 * j + 1]));
+                    const float2 y = kMul ? __ffma2_rn(a2, make_float2(mul, mul), hh) : __fadd2_rn(a2, hh);
+                    x[8 * q + 2 * j] = y.x;
+                    x[8 * q + 2 * j + 1] = y.y;
+                }
+            }
+        } else if (bias) {
+            const float4* b4 = reinterpret_cast<const float4*>(bias + 32u * half);  // 128-bit broadcast loads
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float4 bb = b4[i];
+                const float2 a0 = make_float2(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]));
+                const float2 a1 = make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]));
+                const float2 y0 = kMul ? __ffma2_rn(a0, make_float2(mul, mul), make_float2(bb.x, bb.y))
+                                       : __fadd2_rn(a0, make_float2(bb.x, bb.y));
+                const float2 y1 = kMul ? __ffma2_rn(a1, make_float2(mul, mul), make_float2(bb.z, bb.w))
+                                       : __fadd2_rn(a1, make_float2(bb.z, bb.w));
+                x[4 * i] = y0.x;
+                x[4 * i + 1] = y0.y;
+                x[4 * i + 2] = y1.x;
+                x[4 * i + 3] = y1.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = kMul ? __uint_as_float(v[i]) * mul : __uint_as_float(v[i]);
+        }
+        if constexpr (kRec || kF8Out) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) x[i] = fmaxf(x[i], 0.f);
+        }
+        if constexpr (kRec) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) mx = fmaxf(mx, x[i]);
+        }
+        if constexpr (kF8Out) {
+#pragma unroll
+            for (uint32_t q = 0; q < 2; ++q) {
+                const float* y = x + 16 * q;
+                uint32_t d[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    d[j] = tc::pack_e4m3x4(y[4 * j] * inv_sa, y[4 * j + 1] * inv_sa, y[4 * j + 2] * inv_sa,
+                                           y[4 * j + 3] * inv_sa);
+                sts_chunk(stile, r, 2u * half + q, d[0], d[1], d[2], d[3]);
+            }
+        } else {
+            uint32_t w[16];
+            if constexpr (kSplit) {
+                uint32_t wl[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) split_relu_bf16(x[2 * j], x[2 * j + 1], w[j], wl[j]);
+                tc::tmem_st16(ta + 32u + 16u * half, wl);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) w[j] = pack2_relu<AB16>(x[2 * j], x[2 * j + 1]);
+            }
+            tc::tmem_st16(ta + 16u * half, w);
+        }
+    }
+    if constexpr (kRec) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+        if ((threadIdx.x & 31u) == 0) atomicMax(s_amax, m);
+    }
+}
 
 template <uint32_t AB>
 __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_t* __restrict__ img) {
@@ -135,6 +296,11 @@ __global__ void k_repack_tc(NetShape s, const float* __restrict__ params, uint8_
         }
         const uint16_t bits = AB == 1 ? __bfloat16_as_ushort(__float2bfloat16_rn(v)) : __half_as_ushort(__float2half_rn(v));
         *reinterpret_cast<uint16_t*>(img + off + tc::sw128_offset(n, k)) = bits;
+        if (AB == 1) {  // split operands: the remainder v - bf16(v), rounded to BF16
+            const float rest = v - __bfloat162float(__ushort_as_bfloat16(bits));
+            *reinterpret_cast<uint16_t*>(img + tcimg::off_lo(H) + off + tc::sw128_offset(n, k)) =
+                __bfloat16_as_ushort(__float2bfloat16_rn(rest));
+        }
         return;
     }
     const uint32_t j = idx - n_mat;
@@ -185,106 +351,6 @@ __global__ void k_repack_bias_mma(uint32_t H, uint8_t* __restrict__ img) {
     *reinterpret_cast<uint16_t*>(img + tcimg::off_ones(H) + tc::sw128_offset(r, k)) = k < 2 ? bits(1.f) : 0;
 }
 
-struct TcArgs {
-    uint32_t W, H, N, M, k0, k1;
-    uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
-    const SceneHeader* env_hd;   // light mode 2 with a visibility cache: cache values times L_env
-    uint32_t env_nprims;
-    uint32_t S, P, n_blocks;
-    float z_clamp;
-    uint32_t img_bytes;
-    NetShape s;
-    GridParams g;
-};
-
-// Epilogue of one layer for row r: 64 accumulators from TMEM (two halves of
-// 32 columns), times `mul` (kMul: the FP8 scales s_w s_a of the layer),
-// + bias (none for layer 0 of the frequency input, whose h_pix holds b0;
-// kHrow: layer 0 of the paper's input adds row `pr` of the pixel-major
-// 16-bit tile at `hrow`, h_pix of the row's pixel), ReLU, then either 16-bit
-// rounding into the next A tile (chunks 0-7) or, kF8Out, scaling by 1/s_a of
-// the next layer and E4M3 rounding (chunks 0-3).  kRec: the warp's amax of
-// the ReLU outputs goes into the shared word at s_amax (atomicMax on bits).
-template <uint32_t AB16, bool kF8Out, bool kMul, bool kRec, bool kHrow = false>
-__device__ __forceinline__ void epilogue(uint32_t taddr, const float* __restrict__ bias, float mul, float inv_sa,
-                                         uint32_t tile, uint32_t r, uint32_t* s_amax, uint32_t hrow = 0,
-                                         uint32_t pr = 0) {
-    float mx = 0.f;
-#pragma unroll
-    for (uint32_t half = 0; half < 2; ++half) {
-        uint32_t v[32];
-        tc::tmem_ld32(taddr + 32u * half, v);
-        tc::tmem_wait_ld();
-        float x[32];
-        if constexpr (kHrow) {
-#pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
-                const uint32_t c = 4u * half + q;
-                const uint4 hv = tc::lds128(hrow + (pr >> 3) * 1024u + (pr & 7u) * 128u + (((c ^ pr) & 7u) << 4));
-                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float2 hh = tc::unpack2<AB16>(hw[j]);
-                    const float2 a2 = make_float2(__uint_as_float(v[8 * q + 2 * j]), __uint_as_float(v[8 * q + 2 * j + 1]));
-                    const float2 y = kMul ? __ffma2_rn(a2, make_float2(mul, mul), hh) : __fadd2_rn(a2, hh);
-                    x[8 * q + 2 * j] = y.x;
-                    x[8 * q + 2 * j + 1] = y.y;
-                }
-            }
-        } else if (bias) {
-            const float4* b4 = reinterpret_cast<const float4*>(bias + 32u * half);  // 128-bit broadcast loads
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float4 bb = b4[i];
-                const float2 a0 = make_float2(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]));
-                const float2 a1 = make_float2(__uint_as_float(v[4 * i + 2]), __uint_as_float(v[4 * i + 3]));
-                const float2 y0 = kMul ? __ffma2_rn(a0, make_float2(mul, mul), make_float2(bb.x, bb.y))
-                                       : __fadd2_rn(a0, make_float2(bb.x, bb.y));
-                const float2 y1 = kMul ? __ffma2_rn(a1, make_float2(mul, mul), make_float2(bb.z, bb.w))
-                                       : __fadd2_rn(a1, make_float2(bb.z, bb.w));
-                x[4 * i] = y0.x;
-                x[4 * i + 1] = y0.y;
-                x[4 * i + 2] = y1.x;
-                x[4 * i + 3] = y1.y;
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = kMul ? __uint_as_float(v[i]) * mul : __uint_as_float(v[i]);
-        }
-        if constexpr (kRec || kF8Out) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = fmaxf(x[i], 0.f);
-        }
-        if constexpr (kRec) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) mx = fmaxf(mx, x[i]);
-        }
-        if constexpr (kF8Out) {
-#pragma unroll
-            for (uint32_t q = 0; q < 2; ++q) {
-                const float* y = x + 16 * q;
-                uint32_t d[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    d[j] = tc::pack_e4m3x4(y[4 * j] * inv_sa, y[4 * j + 1] * inv_sa, y[4 * j + 2] * inv_sa,
-                                           y[4 * j + 3] * inv_sa);
-                sts_chunk(tile, r, 2u * half + q, d[0], d[1], d[2], d[3]);
-            }
-        } else {
-#pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
-                const float* y = x + 8 * q;
-                sts_chunk(tile, r, 4u * half + q, pack2_relu<AB16>(y[0], y[1]), pack2_relu<AB16>(y[2], y[3]),
-                          pack2_relu<AB16>(y[4], y[5]), pack2_relu<AB16>(y[6], y[7]));
-            }
-        }
-    }
-    if constexpr (kRec) {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-        if ((threadIdx.x & 31u) == 0) atomicMax(s_amax, m);
-    }
-}
-
 // sin/cos of 2^k a for k = 0..3 from (sin a, cos a), by the double-angle identities.
 __device__ __forceinline__ void octaves(float s, float c, float* e) {
 #pragma unroll
@@ -328,18 +394,20 @@ __device__ __forceinline__ void dir_features_fast(V3 w, float* e) {
     octaves(sp, cp, e + 8);
 }
 
-// AB: 0 FP16, 1 BF16, 2 FP8 hidden layers (FP16 elsewhere).  kAmax: record
-// the amax of every hidden layer's input activations into amax[8 + l].
+// AB: 0 FP16, 1 split BF16, 2 FP8 hidden layers (FP16 elsewhere).  kAmax:
+// record the amax of every hidden layer's input activations into amax[8 + l].
 template <uint32_t AB, bool kAmax, bool kSh>
 __global__ void __launch_bounds__(640, 1)
     k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
                const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
                const ResidRow* __restrict__ rows, const float4* __restrict__ beta, float4* __restrict__ out,
-               float* __restrict__ lc_out,
-               float* __restrict__ lr_out, uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
-               float* __restrict__ row_n, int* __restrict__ err, uint32_t* __restrict__ amax) {
+               float* __restrict__ lc_out, float* __restrict__ lr_out, uint64_t* __restrict__ sig_out,
+               uint32_t* __restrict__ count, float* __restrict__ row_n, int* __restrict__ err,
+               uint32_t* __restrict__ amax) {
     constexpr uint32_t AB16 = AB == 1 ? 1u : 0u;  // type of the 16-bit layers
     constexpr bool kF8 = AB == 2;
+    constexpr bool kSplit = AB == 1;
+    constexpr uint32_t kTile = wg_tile_bytes<AB>();
     extern __shared__ __align__(16) uint8_t smem_raw[];
     const uint32_t raw = tc::smem_u32(smem_raw);
     const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -347,16 +415,14 @@ __global__ void __launch_bounds__(640, 1)
     const uint32_t n_wg = blockDim.x >> 7;
     const uint32_t wg = threadIdx.x >> 7, t = threadIdx.x & 127u, quarter = t >> 5;
     const uint32_t img_al = (a.img_bytes + 1023u) & ~1023u;
-    const uint32_t wgs = sbase + img_al + wg * kWgStride;  // this warpgroup's operand tiles (shared address)
-    const uint32_t small_al = img_al + n_wg * kWgStride;
-    uint8_t* wgg = gbase + small_al + wg * kSmallStride;   // this warpgroup's small arrays (generic pointer)
+    const uint32_t wgs = sbase + img_al + wg * kTile;      // this warpgroup's operand tiles (shared address)
+    const uint32_t small_al = img_al + n_wg * kTile;
+    uint8_t* wgg = gbase + small_al + wg * kSmallStride;   // this warpgroup's reduction arrays (generic pointer)
     const uint32_t misc = sbase + small_al + n_wg * kSmallStride;
     uint8_t* miscg = gbase + small_al + n_wg * kSmallStride;
     const uint32_t mbar = misc + 8u * wg;
     volatile uint32_t* tmem_holder = reinterpret_cast<volatile uint32_t*>(miscg + 64);
     volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(miscg + 80 + 4 * wg);
-    const uint32_t tmem_cols = n_wg <= 1 ? 64u : (n_wg <= 2 ? 128u : (n_wg <= 4 ? 256u : 512u));
-
     uint32_t* s_amax = reinterpret_cast<uint32_t*>(miscg + 128);  // [8]
     float* s_mul = reinterpret_cast<float*>(miscg + 160);         // [8] s_w s_a per hidden slot
     float* s_inv = reinterpret_cast<float*>(miscg + 192);         // [8] 1 / s_a per hidden slot
@@ -367,6 +433,8 @@ __global__ void __launch_bounds__(640, 1)
         float4* dst = reinterpret_cast<float4*>(gbase);
         for (uint32_t i = threadIdx.x; i < a.img_bytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
     }
+    uint32_t tmem_cols = 32;  // power of two >= the warpgroups' slices
+    while (tmem_cols < n_wg * wg_tmem_cols<AB>()) tmem_cols <<= 1;
     if (threadIdx.x < 32) tc::tmem_alloc(misc + 64, tmem_cols);
     if (threadIdx.x == 0) {
         for (uint32_t w = 0; w < n_wg; ++w) {
@@ -392,23 +460,32 @@ __global__ void __launch_bounds__(640, 1)
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tmem_holder + 64u * wg;
-    const uint32_t tmem_row = tmem + ((32u * quarter) << 16);
+    // tensor memory of this warpgroup: D | A | A remainder; lane base 0 for the MMAs,
+    // 32 * quarter for this warp's loads and stores
+    const uint32_t tm = *tmem_holder + wg_tmem_cols<AB>() * wg;
+    const uint32_t lane = (32u * quarter) << 16;
+    const uint32_t tmD = tm + kTmD, tmA = tm + kTmA, tmLo = tm + kTmLo;
+    const uint32_t tDr = tmD + lane, tAr = tmA + lane;
     const uint32_t bar_id = 1 + wg;
     uint32_t phase = 0;
 
+    const uint32_t H = a.s.hidden;
+    const uint32_t lo_off = tcimg::off_lo(H);  // split BF16: remainder tiles at the same relative offsets
     const uint32_t w0pix = sbase + tcimg::off_w0pix(), w0dir = sbase + tcimg::off_w0dir();
-    const uint32_t wout = sbase + tcimg::off_wout(a.s.hidden);
-    const float* bias = reinterpret_cast<const float*>(gbase + tcimg::off_bias(a.s.hidden));
-    const uint32_t tA = wgs + kOffA, tH = wgs + kOffH;
-    float4* s_contrib = reinterpret_cast<float4*>(wgg + kOffContrib);
-    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);  // two slots of 16 floats
+    const uint32_t wout = sbase + tcimg::off_wout(H);
+    const float* bias = reinterpret_cast<const float*>(gbase + tcimg::off_bias(H));
+    const uint32_t tA8 = wgs;                          // FP8: E4M3 A tile of the hidden layers
+    const uint32_t tH = wgs + (kF8 ? 16384u : 0u);     // h_pix operand
+    const uint32_t tHlo = wgs + 16384u;                // split BF16: its remainder
     const uint32_t id64 = tc::idesc_f16(AB16, 128, 64), id16 = tc::idesc_f16(AB16, 128, 16);
     const uint32_t id64_e4m3 = tc::idesc_f16(0, 128, 64);  // E4M3 x E4M3 has type code 0 too
     const uint16_t one16 = AB16 ? 0x3F80u : 0x3C00u;
+    float* s_rows = reinterpret_cast<float*>(wgg + kOffRows);    // [128][8] contributions of the tile's rows
+    uint32_t* s_fin = reinterpret_cast<uint32_t*>(wgg + kOffFin);  // [128][kFinWords] finished pixel sums
+    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);    // 2 slots x 16 floats (sum, comp) x 7
+    uint64_t* s_sigc = reinterpret_cast<uint64_t*>(wgg + kOffCarry + 128);  // 2 signature carry slots
 
     auto sync_wg = [&]() {
-        tc::fence_proxy_async();
         tc::fence_before_sync();
         tc::named_bar(bar_id, 128);
     };
@@ -422,36 +499,51 @@ __global__ void __launch_bounds__(640, 1)
         phase ^= 1u;
         tc::fence_after_sync();
     };
-    auto issue_k64 = [&](uint32_t a_tile, uint32_t b_tile, uint32_t idesc) {
+    // D (+)= A x B^T over K = 16 * n_k with A in TMEM at column a_col (8 columns per
+    // K step) and B the swizzled shared tile at b; split BF16 adds lo*hi and hi*lo.
+    auto mma_ta = [&](uint32_t a_col, uint32_t b, uint32_t idesc, uint32_t n_k, bool acc0) {
+#pragma unroll 1
+        for (uint32_t s = 0; s < n_k; ++s) {
+            tc::mma_f16_ta(tmD, tmA + a_col + 8u * s, tc::sdesc(b + 32u * s), idesc, (acc0 || s > 0) ? 1u : 0u);
+            if constexpr (kSplit) {
+                tc::mma_f16_ta(tmD, tmLo + a_col + 8u * s, tc::sdesc(b + 32u * s), idesc, 1u);
+                tc::mma_f16_ta(tmD, tmA + a_col + 8u * s, tc::sdesc(b + lo_off + 32u * s), idesc, 1u);
+            }
+        }
+    };
+    // 4 K-steps from the TMEM operand, then the bias slot j as one more K = 16 step against the ones atom
+    const uint32_t ones = sbase + tcimg::off_ones(H), bmma = sbase + tcimg::off_bmma(H);
+    auto issue_layer = [&](uint32_t w_tile, uint32_t idesc, uint32_t j) {
         if (t == 0 && !*abort_flag) {
             tc::fence_after_sync();
-#pragma unroll
-            for (uint32_t s = 0; s < 4; ++s) tc::mma_f16(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), idesc, s);
+            mma_ta(0u, w_tile, idesc, 4u, false);
+            tc::mma_f16(tmD, tc::sdesc_rep8(ones), tc::sdesc(bmma + 8192u * (j >> 2) + 32u * (j & 3u)), idesc, 1);
             tc::mma_commit(mbar);
         }
     };
-    // 4 K-steps, then the bias slot j as one more K = 16 step against the ones atom
-    const uint32_t ones = sbase + tcimg::off_ones(a.s.hidden), bmma = sbase + tcimg::off_bmma(a.s.hidden);
-    auto issue_k64_bias = [&](uint32_t a_tile, uint32_t b_tile, uint32_t idesc, uint32_t j) {
-        if (t == 0 && !*abort_flag) {
-            tc::fence_after_sync();
-#pragma unroll
-            for (uint32_t s = 0; s < 4; ++s) tc::mma_f16(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), idesc, s);
-            tc::mma_f16(tmem, tc::sdesc_rep8(ones), tc::sdesc(bmma + 8192u * (j >> 2) + 32u * (j & 3u)), idesc, 1);
-            tc::mma_commit(mbar);
-        }
-    };
-    auto issue_k64_e4m3 = [&](uint32_t a_tile, uint32_t b_tile) {
+    auto issue_e4m3 = [&](uint32_t b_tile) {
         if (t == 0 && !*abort_flag) {
             tc::fence_after_sync();
 #pragma unroll
             for (uint32_t s = 0; s < 2; ++s)
-                tc::mma_e4m3(tmem, tc::sdesc(a_tile + 32 * s), tc::sdesc(b_tile + 32 * s), id64_e4m3, s);
+                tc::mma_e4m3(tmD, tc::sdesc(tA8 + 32 * s), tc::sdesc(b_tile + 32 * s), id64_e4m3, s);
             tc::mma_commit(mbar);
         }
     };
+    // one 8-feature chunk c of this thread's A row (4 columns; the remainders 32 columns further)
+    auto put_chunk = [&](uint32_t c, const float* f) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if constexpr (kSplit) split_bf16(f[2 * j], f[2 * j + 1], hi[j], lo[j]);
+            else hi[j] = pack2<AB16>(f[2 * j], f[2 * j + 1]);
+        }
+        tc::tmem_st4(tAr + 4u * c, hi[0], hi[1], hi[2], hi[3]);
+        if constexpr (kSplit) tc::tmem_st4(tAr + 32u + 4u * c, lo[0], lo[1], lo[2], lo[3]);
+    };
 
     const uint32_t S = a.S;
+    const uint32_t R_full = 128u * S;
     for (uint32_t blk = blockIdx.x * n_wg + wg; blk < a.n_blocks; blk += gridDim.x * n_wg) {
         const uint32_t p0 = blk * 128u;
         const uint32_t npix = min(128u, a.P - p0);
@@ -490,65 +582,86 @@ __global__ void __launch_bounds__(640, 1)
                         f[2 * q] = f0;
                         f[2 * q + 1] = f1;
                     }
-                    sts_chunk8<AB16>(tA, t, c, f);
+                    put_chunk(c, f);
                 }
             } else {
                 freq4(p.x, f);
-                sts_chunk8<AB16>(tA, t, c++, f);
+                put_chunk(c++, f);
                 freq4(p.y, f);
-                sts_chunk8<AB16>(tA, t, c++, f);
+                put_chunk(c++, f);
                 freq4(p.z, f);
-                sts_chunk8<AB16>(tA, t, c++, f);
+                put_chunk(c++, f);
             }
             if constexpr (kSh) {
                 float ph[16];
                 phi_features(n, make_float3(r2.y, r2.z, r2.w), r3.x, ph);
                 ph[15] = 0.f;
-                sts_chunk8<AB16>(tA, t, c++, ph);
-                sts_chunk8<AB16>(tA, t, c++, ph + 8);
+                put_chunk(c++, ph);
+                put_chunk(c++, ph + 8);
             } else {
                 freq4(n.x, f);
-                sts_chunk8<AB16>(tA, t, c++, f);
+                put_chunk(c++, f);
                 freq4(n.y, f);
-                sts_chunk8<AB16>(tA, t, c++, f);
+                put_chunk(c++, f);
                 freq4(n.z, f);
-                sts_chunk8<AB16>(tA, t, c++, f);
+                put_chunk(c++, f);
             }
-            for (; c < 8; ++c) sts_chunk(tA, t, c, 0u, 0u, 0u, 0u);
+            for (uint32_t j = 0; j < 8; ++j) f[j] = 0.f;
+            for (; c < 8; ++c) put_chunk(c, f);
         }
+        tc::tmem_wait_st();
         sync_wg();
-        issue_k64(tA, w0pix, id64);
+        if (t == 0 && !*abort_flag) {
+            tc::fence_after_sync();
+            mma_ta(0u, w0pix, id64, 4u, false);
+            tc::mma_commit(mbar);
+        }
         wait_mma();
         if constexpr (kSh) {
-            // H pixel-major: row t = h_pix of pixel t = accumulator + b0, 16-bit
+            // H pixel-major: row t = h_pix of pixel t = accumulator + b0, 16-bit (+ remainder)
 #pragma unroll
             for (uint32_t half = 0; half < 2; ++half) {
                 uint32_t v[32];
-                tc::tmem_ld32(tmem_row + 32u * half, v);
+                tc::tmem_ld32(tDr + 32u * half, v);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (uint32_t q = 0; q < 4; ++q) {
                     float y[8];
 #pragma unroll
                     for (uint32_t j = 0; j < 8; ++j) y[j] = __uint_as_float(v[8 * q + j]) + bias[32 * half + 8 * q + j];
-                    sts_chunk8<AB16>(tH, t, 4 * half + q, y);
+                    if constexpr (kSplit) {
+                        uint32_t hi[4], lo[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) split_bf16(y[2 * j], y[2 * j + 1], hi[j], lo[j]);
+                        sts_chunk(tH, t, 4 * half + q, hi[0], hi[1], hi[2], hi[3]);
+                        sts_chunk(tHlo, t, 4 * half + q, lo[0], lo[1], lo[2], lo[3]);
+                    } else {
+                        sts_chunk8<AB16>(tH, t, 4 * half + q, y);
+                    }
                 }
             }
         } else {
-            // H operand: element (n = output unit, k = pixel t), h = accumulator + b0
-            const uint32_t hk = tH + (t >> 6) * 8192u;
+            // H operand: element (n = output unit, k = pixel t), h = accumulator + b0 (+ remainder)
+            const uint32_t hk = (t >> 6) * 8192u;
 #pragma unroll
             for (uint32_t half = 0; half < 2; ++half) {
                 uint32_t v[32];
-                tc::tmem_ld32(tmem_row + 32u * half, v);
+                tc::tmem_ld32(tDr + 32u * half, v);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (uint32_t o = 0; o < 32; ++o) {
                     const uint32_t oo = 32u * half + o;
-                    tc::sts16(hk + tc::sw128_offset(oo, t & 63u), to16<AB16>(__uint_as_float(v[o]) + bias[oo]));
+                    const float hv = __uint_as_float(v[o]) + bias[oo];
+                    const uint16_t hb = to16<AB16>(hv);
+                    tc::sts16(tH + hk + tc::sw128_offset(oo, t & 63u), hb);
+                    if constexpr (kSplit) {
+                        const float rest = hv - __uint_as_float((uint32_t)hb << 16);
+                        tc::sts16(tHlo + hk + tc::sw128_offset(oo, t & 63u), to16<1>(rest));
+                    }
                 }
             }
         }
+        tc::fence_proxy_async();  // H is an MMA operand (frequency input)
         sync_wg();
 
         // ------------------------------------------------ row tiles
@@ -557,10 +670,10 @@ __global__ void __launch_bounds__(640, 1)
         for (uint32_t j0 = 0; j0 < R; j0 += 128u, ++jt) {
             const uint32_t r = j0 + t;
             const bool rin = r < R;
-            const uint32_t pl = rin ? r / S : 0u;
+            const uint32_t pl = rin ? div_s(r, a.s_magic) : 0u;
             const uint32_t s = rin ? r - pl * S : 0u;
-            const uint32_t pf = j0 / S;
-            const uint32_t plast = min((j0 + 127u) / S, npix - 1u);
+            const uint32_t pf = div_s(j0, a.s_magic);
+            const uint32_t plast = min(div_s(min(j0 + 127u, R_full - 1u), a.s_magic), npix - 1u);
             // one-hot window [kb, kb + 16 n_oh) covers pixels pf..plast and stays inside H's 128 columns
             const uint32_t n_oh = (plast - (pf & ~15u) + 16u) >> 4;  // <= 3 for S >= 4
             const uint32_t kb = min(pf & ~15u, 128u - 16u * n_oh);
@@ -597,85 +710,98 @@ __global__ void __launch_bounds__(640, 1)
                 }
             }
             if constexpr (kSh) {
-                // columns 0..31: the 25 spherical harmonics, zero padded (layer 0 reads K = 32)
+                // columns 0..31 of the row: the 25 spherical harmonics, zero padded (layer 0 reads K = 32)
                 float e[32];
                 sh_basis25(wi, e);
 #pragma unroll
                 for (int i = 25; i < 32; ++i) e[i] = 0.f;
 #pragma unroll
-                for (uint32_t c = 0; c < 4; ++c) sts_chunk8<AB16>(tA, t, c, e + 8 * c);
+                for (uint32_t c = 0; c < 4; ++c) put_chunk(c, e + 8 * c);
             } else {
                 float e[16];
                 dir_features_fast(wi, e);
-                sts_chunk8<AB16>(tA, t, 0u, e);
-                sts_chunk8<AB16>(tA, t, 1u, e + 8);
-                const uint32_t oh = rin ? pl - kb : 0xFFFFu;  // one-hot position among columns 16..63
+                put_chunk(0u, e);
+                put_chunk(1u, e + 8);
+                // one-hot of the row's pixel among K columns 16..63 (words 8..31 of the row)
+                const uint32_t oh = rin ? pl - kb : 0xFFFFu;
+                const uint32_t ow = oh >> 1, ov = (uint32_t)one16 << ((oh & 1u) * 16u);
+                uint32_t d[16];
 #pragma unroll
-                for (uint32_t c = 2; c < 8; ++c) {
-                    uint32_t d[4] = {0u, 0u, 0u, 0u};
-                    const uint32_t lo = (c - 2) * 8;
-                    if (oh >= lo && oh < lo + 8) {
-                        const uint32_t e2 = oh - lo;
-                        d[e2 >> 1] = (uint32_t)one16 << ((e2 & 1u) * 16);
-                    }
-                    sts_chunk(tA, t, c, d[0], d[1], d[2], d[3]);
-                }
+                for (uint32_t j = 0; j < 16; ++j) d[j] = ow == j ? ov : 0u;
+                tc::tmem_st16(tAr + 8u, d);
+                uint32_t d8[8];
+#pragma unroll
+                for (uint32_t j = 0; j < 8; ++j) d8[j] = ow == 16u + j ? ov : 0u;
+                tc::tmem_st8(tAr + 24u, d8);
             }
+            tc::tmem_wait_st();
             sync_wg();
             if (t == 0 && !*abort_flag) {
                 tc::fence_after_sync();
-                tc::mma_f16(tmem, tc::sdesc(tA), tc::sdesc(w0dir), id64, 0);
                 if constexpr (kSh) {
-                    tc::mma_f16(tmem, tc::sdesc(tA + 32u), tc::sdesc(w0dir + 32u), id64, 1);
+                    mma_ta(0u, w0dir, id64, 2u, false);
                 } else {
+                    mma_ta(0u, w0dir, id64, 1u, false);
                     for (uint32_t qq = 1; qq <= n_oh; ++qq) {
                         const uint32_t kk = kb + 16u * (qq - 1);
-                        tc::mma_f16(tmem, tc::sdesc(tA + 32u * qq),
-                                    tc::sdesc(tH + (kk >> 6) * 8192u + (kk & 63u) * 2u), id64, 1);
+                        const uint32_t hoff = (kk >> 6) * 8192u + (kk & 63u) * 2u;
+                        tc::mma_f16_ta(tmD, tmA + 8u * qq, tc::sdesc(tH + hoff), id64, 1);
+                        if constexpr (kSplit) tc::mma_f16_ta(tmD, tmA + 8u * qq, tc::sdesc(tHlo + hoff), id64, 1);
                     }
                 }
                 tc::mma_commit(mbar);
             }
             wait_mma();
-            for (uint32_t l = 0; l < a.s.hidden; ++l) {
+            for (uint32_t l = 0; l < H; ++l) {
                 // epilogue of layer l (l = 0: h_pix already holds b0; 16-bit hidden layers: the
                 // bias came with the MMA), then the MMAs of layer l + 1
                 const float* bl = (l == 0 || !kF8) ? nullptr : bias + 64 + (l - 1) * 64;
-                const bool next_hidden = l + 1 < a.s.hidden;
+                const bool next_hidden = l + 1 < H;
                 if (kSh && l == 0) {
                     // layer 0 of the paper's input: + h_pix of the row's pixel (H row pl)
                     if constexpr (kF8) {
-                        if (next_hidden) epilogue<0, true, false, true, true>(tmem_row, nullptr, 1.f, s_inv[0], tA, t, s_amax, tH, pl);
-                        else epilogue<0, false, false, false, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, nullptr, tH, pl);
+                        if (next_hidden)
+                            epilogue<0, false, true, false, true, true>(tDr, tAr, nullptr, 1.f, s_inv[0], tA8, t,
+                                                                        s_amax, tH, 0u, pl);
+                        else
+                            epilogue<0, false, false, false, false, true>(tDr, tAr, nullptr, 1.f, 1.f, tA8, t,
+                                                                          nullptr, tH, 0u, pl);
                     } else if constexpr (kAmax) {
-                        if (next_hidden) epilogue<AB16, false, false, true, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, s_amax, tH, pl);
-                        else epilogue<AB16, false, false, false, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, nullptr, tH, pl);
+                        if (next_hidden)
+                            epilogue<AB16, kSplit, false, false, true, true>(tDr, tAr, nullptr, 1.f, 1.f, 0u, t,
+                                                                             s_amax, tH, tHlo, pl);
+                        else
+                            epilogue<AB16, kSplit, false, false, false, true>(tDr, tAr, nullptr, 1.f, 1.f, 0u, t,
+                                                                              nullptr, tH, tHlo, pl);
                     } else {
-                        epilogue<AB16, false, false, false, true>(tmem_row, nullptr, 1.f, 1.f, tA, t, nullptr, tH, pl);
+                        epilogue<AB16, kSplit, false, false, false, true>(tDr, tAr, nullptr, 1.f, 1.f, 0u, t,
+                                                                          nullptr, tH, tHlo, pl);
                     }
                 } else if constexpr (kF8) {
                     const float mul = l == 0 ? 1.f : s_mul[l - 1];
-                    if (next_hidden) epilogue<0, true, true, true>(tmem_row, bl, mul, s_inv[l], tA, t, s_amax + l);
-                    else epilogue<0, false, true, false>(tmem_row, bl, mul, 1.f, tA, t, nullptr);
+                    if (next_hidden) epilogue<0, false, true, true, true>(tDr, tAr, bl, mul, s_inv[l], tA8, t, s_amax + l);
+                    else epilogue<0, false, false, true, false>(tDr, tAr, bl, mul, 1.f, tA8, t, nullptr);
                 } else if constexpr (kAmax) {
-                    if (next_hidden) epilogue<AB16, false, false, true>(tmem_row, bl, 1.f, 1.f, tA, t, s_amax + l);
-                    else epilogue<AB16, false, false, false>(tmem_row, bl, 1.f, 1.f, tA, t, nullptr);
+                    if (next_hidden) epilogue<AB16, kSplit, false, false, true>(tDr, tAr, bl, 1.f, 1.f, 0u, t, s_amax + l);
+                    else epilogue<AB16, kSplit, false, false, false>(tDr, tAr, bl, 1.f, 1.f, 0u, t, nullptr);
                 } else {
-                    epilogue<AB16, false, false, false>(tmem_row, bl, 1.f, 1.f, tA, t, nullptr);
+                    epilogue<AB16, kSplit, false, false, false>(tDr, tAr, bl, 1.f, 1.f, 0u, t, nullptr);
                 }
+                if (kF8 && next_hidden) tc::fence_proxy_async();  // E4M3 operand in shared memory
+                else tc::tmem_wait_st();                           // 16-bit operand in TMEM
                 sync_wg();
                 if (next_hidden) {
-                    if constexpr (kF8) issue_k64_e4m3(tA, sbase + tcimg::off_wh(l));
-                    else issue_k64_bias(tA, sbase + tcimg::off_wh(l), id64, l);
+                    if constexpr (kF8) issue_e4m3(sbase + tcimg::off_wh(l));
+                    else issue_layer(sbase + tcimg::off_wh(l), id64, l);
                 } else {
-                    issue_k64_bias(tA, wout, id16, a.s.hidden - 1u);
+                    issue_layer(wout, id16, H - 1u);
                 }
                 wait_mma();
             }
             float3 nv;
             {
                 uint32_t v[4];
-                tc::tmem_ld4(tmem_row, v);
+                tc::tmem_ld4(tDr, v);
                 tc::tmem_wait_ld();
                 const bool vis = a.s.vis;  // the output bias came with the MMA
                 nv.x = out_act(vis, __uint_as_float(v[0]), a.z_clamp);
@@ -694,124 +820,107 @@ __global__ void __launch_bounds__(640, 1)
                 rn[1] = ok ? nv.y : 0.f;
                 rn[2] = ok ? nv.z : 0.f;
             }
-            // ---- per-pixel sums.  Rows are ordered by pixel, so each pixel is a
-            // contiguous segment: a pairwise tree over the warp's lanes (shuffle
-            // down by 1, 2, 4, 8, 16, adding only within the segment) leaves each
-            // segment's warp-local sum in its first lane, in an order fixed by
-            // the row positions.  That lane then adds the partials of later
-            // warps whose first rows belong to the same pixel and the previous
-            // tile's carry, and either writes the pixel or carries it on.
-            const uint32_t lane = t & 31u, warp = t >> 5;
-            const uint32_t s_row = rin ? r - pl * S : 0u;
-            const bool is_cache = s_row < a.N;
-            float v[7];
+            // ---- per-pixel sums (eq. L_mlmc, L_c, L_r).  Each row's contributions
+            // c_r = w_r n_r (cache rows in channels 0-2, residual rows in 3-5, 1 per
+            // valid cache sample in 6) and its signature word go to shared memory;
+            // then one thread per (pixel, channel) adds the pixel's rows of this tile
+            // in sample order with Kahan compensation, continuing the carried sum and
+            // compensation of a pixel that began in the previous tile, and one thread
+            // per pixel that ends here writes it.
             {
+                const bool is_cache = s < a.N;
                 const float3 cw = ok ? make_float3(w.x * nv.x, w.y * nv.y, w.z * nv.z) : make_float3(0.f, 0.f, 0.f);
-                v[0] = is_cache ? cw.x : 0.f;
-                v[1] = is_cache ? cw.y : 0.f;
-                v[2] = is_cache ? cw.z : 0.f;
-                v[3] = is_cache ? 0.f : cw.x;
-                v[4] = is_cache ? 0.f : cw.y;
-                v[5] = is_cache ? 0.f : cw.z;
-                v[6] = (is_cache && ok) ? 1.f : 0.f;
+                float4* sr = reinterpret_cast<float4*>(s_rows) + 2 * t;
+                sr[0] = is_cache ? make_float4(cw.x, cw.y, cw.z, 0.f) : make_float4(0.f, 0.f, 0.f, cw.x);
+                sr[1] = is_cache ? make_float4(0.f, 0.f, (ok ? 1.f : 0.f), __uint_as_float(word))
+                                 : make_float4(cw.y, cw.z, 0.f, __uint_as_float(word));
             }
-            const uint32_t seg = rin ? pl : 0xFFFFFFFFu;
-#pragma unroll
-            for (uint32_t off = 1; off < 32; off <<= 1) {
-                const uint32_t oseg = __shfl_down_sync(0xffffffffu, seg, off);
-                float o[7];
-#pragma unroll
-                for (int k = 0; k < 7; ++k) o[k] = __shfl_down_sync(0xffffffffu, v[k], off);
-                if (lane + off < 32u && oseg == seg) {
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) v[k] += o[k];
-                }
-            }
-            float* s_part = s_carry + 32;                                              // 4 warps x 8 floats
-            uint64_t* s_sigc = reinterpret_cast<uint64_t*>(s_carry + 64);              // 2 signature carry slots
-            if (lane == 0) {
-#pragma unroll
-                for (int k = 0; k < 7; ++k) s_part[8 * warp + k] = v[k];
-                s_part[8 * warp + 7] = __uint_as_float(seg);
-            }
-            if (sig_out) s_contrib[t] = make_float4(0.f, 0.f, 0.f, __uint_as_float(word));
-            tc::fence_before_sync();
             tc::named_bar(bar_id, 128);
-
-            const uint32_t prev_seg = __shfl_up_sync(0xffffffffu, seg, 1);
-            const bool head = rin && (lane > 0 ? prev_seg != seg
-                                               : (warp == 0 || (j0 + 32u * warp - 1u) / S != pl));
-            if (head) {
-                const uint32_t q = pl;
+            const uint32_t n_q = plast - pf + 1u;  // pixels with rows in this tile
+            const float* cin = s_carry + 16u * (jt & 1u);    // written by the previous tile
+            float* cout = s_carry + 16u * ((jt + 1u) & 1u);  // read by the next tile
+            for (uint32_t j = t; j < 8u * n_q; j += 128u) {
+                const uint32_t qi = j >> 3, ch = j & 7u;
+                const uint32_t q = pf + qi;
                 const uint32_t q_lo = q * S, q_hi = q_lo + S;
-                const float* cin = s_carry + 16u * (jt & 1u);    // written by the previous tile
-                float* cout = s_carry + 16u * ((jt + 1u) & 1u);  // read by the next tile
-                float acc[7];
-                const bool cont_in = q_lo < j0;
-#pragma unroll
-                for (int k = 0; k < 7; ++k) acc[k] = cont_in ? cin[k] : 0.f;
-#pragma unroll
-                for (int k = 0; k < 7; ++k) acc[k] += v[k];
-                for (uint32_t ww = warp + 1; ww < 4; ++ww) {
-                    if (__float_as_uint(s_part[8 * ww + 7]) != seg) break;
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) acc[k] += s_part[8 * ww + k];
-                }
-                // decision signature of the cache samples (sequential, only when requested)
-                uint64_t sig = 0;
-                if (sig_out) {
-                    sig = cont_in ? s_sigc[jt & 1u] : kSigInit;
-                    const bool qvalid = __float_as_uint(__ldg(reinterpret_cast<const float4*>(recs + p0 + q) + 3).z) & 1u;
-                    const uint32_t lo = max(q_lo, j0), hi = min(min(q_hi, j0 + 128u), q_lo + a.N);
-                    if (qvalid)
-                        for (uint32_t rr = lo; rr < hi; ++rr) sig = sig_mix(sig, __float_as_uint(s_contrib[rr - j0].w));
-                }
-                if (q_hi > j0 + 128u) {  // continues in the next tile
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) cout[k] = acc[k];
-                    if (sig_out) s_sigc[(jt + 1u) & 1u] = sig;
-                } else {
-                    const uint32_t gp = p0 + q;
-                    PixelBase b;
-                    if (base) {
-                        b = base[gp];
+                const uint32_t lo = max(q_lo, j0), hi = min(q_hi, j0 + 128u);
+                const bool cont_in = q_lo < j0, cont_out = q_hi > j0 + 128u;
+                if (ch < 7u) {
+                    float sum = cont_in ? cin[2 * ch] : 0.f, comp = cont_in ? cin[2 * ch + 1] : 0.f;
+                    const float* col = s_rows + ch;
+                    for (uint32_t rr = lo; rr < hi; ++rr) {
+                        const float y = col[8u * (rr - j0)] - comp;
+                        const float tt = sum + y;
+                        comp = (tt - sum) - y;
+                        sum = tt;
+                    }
+                    if (cont_out) {
+                        cout[2 * ch] = sum;
+                        cout[2 * ch + 1] = comp;
                     } else {
-                        b.le = b.wl = make_float4(0.f, 0.f, 0.f, 0.f);
+                        s_fin[kFinWords * qi + ch] = __float_as_uint(sum);
                     }
-                    float Lc[3] = {0.f, 0.f, 0.f}, Lr[3] = {b.wl.x, b.wl.y, b.wl.z};
-                    if (a.N) {
-                        const float inv = 1.0f / (float)a.N;
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) Lc[cc] = acc[cc] * inv;
+                } else if (sig_out) {
+                    // decision signature of the cache samples, in sample order
+                    uint64_t sig = cont_in ? s_sigc[jt & 1u] : kSigInit;
+                    const bool qvalid =
+                        __float_as_uint(__ldg(reinterpret_cast<const float4*>(recs + p0 + q) + 3).z) & 1u;
+                    const uint32_t hi_c = min(hi, q_lo + a.N);
+                    if (qvalid)
+                        for (uint32_t rr = lo; rr < hi_c; ++rr) sig = sig_mix(sig, __float_as_uint(s_rows[8u * (rr - j0) + 7u]));
+                    if (cont_out) {
+                        s_sigc[(jt + 1u) & 1u] = sig;
+                    } else {
+                        s_fin[kFinWords * qi + 8] = (uint32_t)sig;
+                        s_fin[kFinWords * qi + 9] = (uint32_t)(sig >> 32);
                     }
-                    if (a.M && a.N) {  // without a cache level nothing is subtracted
-                        const float inv = 1.0f / (float)a.M;
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) Lr[cc] -= acc[3 + cc] * inv;
-                    }
-                    if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
-                        const float4 bt = beta[gp];
-                        const float bb[3] = {bt.x, bt.y, bt.z};
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            Lc[cc] *= bb[cc];
-                            Lr[cc] *= bb[cc];
-                        }
-                    }
-                    out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
-                    if (lc_out) {
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) lc_out[3 * (uint64_t)gp + cc] = Lc[cc];
-                    }
-                    if (lr_out) {
-#pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) lr_out[3 * (uint64_t)gp + cc] = Lr[cc];
-                    }
-                    if (sig_out) sig_out[2 * (uint64_t)gp + 1] = sig;
-                    if (count) count[gp] += (uint32_t)acc[6];
                 }
             }
-            // no barrier here: the next tile's barriers order s_contrib and the carry slots
+            tc::named_bar(bar_id, 128);
+            for (uint32_t qi = t; qi < n_q; qi += 128u) {
+                const uint32_t q = pf + qi;
+                if (q * S + S > j0 + 128u) continue;  // continues in the next tile
+                const uint32_t* fs = s_fin + kFinWords * qi;
+                const uint32_t gp = p0 + q;
+                PixelBase b;
+                if (base) {
+                    b = base[gp];
+                } else {
+                    b.le = b.wl = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                float Lc[3] = {0.f, 0.f, 0.f}, Lr[3] = {b.wl.x, b.wl.y, b.wl.z};
+                if (a.N) {
+                    const float inv = 1.0f / (float)a.N;
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) Lc[cc] = __uint_as_float(fs[cc]) * inv;
+                }
+                if (a.M && a.N) {  // without a cache level nothing is subtracted
+                    const float inv = 1.0f / (float)a.M;
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) Lr[cc] -= __uint_as_float(fs[3 + cc]) * inv;
+                }
+                if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
+                    const float4 bt = beta[gp];
+                    const float bb[3] = {bt.x, bt.y, bt.z};
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        Lc[cc] *= bb[cc];
+                        Lr[cc] *= bb[cc];
+                    }
+                }
+                out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
+                if (lc_out) {
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) lc_out[3 * (uint64_t)gp + cc] = Lc[cc];
+                }
+                if (lr_out) {
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) lr_out[3 * (uint64_t)gp + cc] = Lr[cc];
+                }
+                if (sig_out) sig_out[2 * (uint64_t)gp + 1] = (uint64_t)fs[8] | ((uint64_t)fs[9] << 32);
+                if (count) count[gp] += (uint32_t)__uint_as_float(fs[6]);
+            }
+            // no barrier here: the next tile's barriers order the reduction arrays
         }
     }
 
@@ -826,8 +935,9 @@ __global__ void __launch_bounds__(640, 1)
     }
 }
 
+template <uint32_t AB>
 static size_t tc_smem_bytes(uint32_t img_bytes, uint32_t n_wg) {
-    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * (kWgStride + kSmallStride) + kMiscBytes;
+    return 1024 + ((img_bytes + 1023) & ~1023u) + (size_t)n_wg * (wg_tile_bytes<AB>() + kSmallStride) + kMiscBytes;
 }
 
 cudaError_t launch_repack_tc(const nirc_handle* h, cudaStream_t st) {
@@ -882,7 +992,8 @@ cudaError_t launch_repack_fwd16(const nirc_handle* h, uint8_t* img, cudaStream_t
 bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd) {
     return (h->cfg.precision == NIRC_FP16_TC || h->cfg.precision == NIRC_BF16_TC ||
             h->cfg.precision == NIRC_FP8_E4M3_TC) &&
-           fd.cache_mode == 0 && fd.n_cache + fd.n_resid >= (h->shape.sh ? 1u : 4u) && h->packed_tc != nullptr &&
+           fd.cache_mode == 0 && fd.n_cache + fd.n_resid >= (h->shape.sh ? 1u : 4u) &&
+           fd.n_cache + fd.n_resid < 65536u && h->packed_tc != nullptr &&
            (h->shape.n_pos == 24 || h->shape.n_pos == 32);
 }
 
@@ -915,6 +1026,16 @@ static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t sm
                                               lr, sig, count, row_n, err, amax);
 }
 
+// Warpgroups per CTA for operand type AB: as many as shared and tensor memory hold (<= 5).
+template <uint32_t AB>
+static uint32_t tc_warpgroups(uint32_t img_bytes, int max_smem, size_t* smem) {
+    uint32_t n_wg = 5;
+    while (n_wg > 1 && (tc_smem_bytes<AB>(img_bytes, n_wg) > (size_t)max_smem || n_wg * wg_tmem_cols<AB>() > 512u))
+        --n_wg;
+    *smem = tc_smem_bytes<AB>(img_bytes, n_wg);
+    return n_wg;
+}
+
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
@@ -931,24 +1052,27 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     a.k0 = (uint32_t)fd.seed;
     a.k1 = fd.frame;
     a.S = fd.n_cache + fd.n_resid;
+    a.s_magic = (1ull << 40) / a.S + 1;
     a.P = fd.width * fd.height;
     a.n_blocks = (a.P + 127) / 128;
     a.z_clamp = h->cfg.z_clamp;
-    a.img_bytes = (uint32_t)tc_image_bytes(h->shape.hidden);
     a.s = h->shape;
     a.g = h->grid;
+    const bool split = h->cfg.precision == NIRC_BF16_TC;
+    a.img_bytes = split ? tcimg::bytes_split(h->shape.hidden) : tcimg::bytes_hi(h->shape.hidden);
     int dev = h->device, max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    uint32_t n_wg = 5;
-    while (n_wg > 1 && tc_smem_bytes(a.img_bytes, n_wg) > (size_t)max_smem) --n_wg;
-    const size_t smem = tc_smem_bytes(a.img_bytes, n_wg);
+    size_t smem = 0;
+    const uint32_t n_wg = split ? tc_warpgroups<1>(a.img_bytes, max_smem, &smem)
+                                : (h->cfg.precision == NIRC_FP8_E4M3_TC ? tc_warpgroups<2>(a.img_bytes, max_smem, &smem)
+                                                                       : tc_warpgroups<0>(a.img_bytes, max_smem, &smem));
     if (smem > (size_t)max_smem) return cudaErrorInvalidConfiguration;
     uint32_t grid = (a.n_blocks + n_wg - 1) / n_wg;
     if (grid > (uint32_t)h->num_sms) grid = h->num_sms;
     const __half2* hash = reinterpret_cast<const __half2*>(h->hash16);
     const uint32_t threads = n_wg * 128;
     count_kernels(h);  // the cache kernel; FP8 adds an amax roll (and a calibration pair) below
-    if (h->cfg.precision == NIRC_BF16_TC)
+    if (split)
         return launch_tc_instance<1, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba,
                                             lc, lr, sig, count, row_n, err, nullptr);
     if (h->cfg.precision != NIRC_FP8_E4M3_TC)
@@ -958,7 +1082,8 @@ cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, con
     uint32_t* amax = h->fp8_amax;
     const uint32_t n_slots = h->shape.hidden - 1;
     if (!h->fp8_calibrated) {
-        // one FP16 launch records the activation amax (its image is overwritten below)
+        // one FP16 launch records the activation amax (its image is overwritten below); it
+        // runs with the FP8 launch's warpgroup count, whose shared memory covers the FP16 layout
         e = launch_tc_instance<0, true>(grid, threads, smem, st, a, h->packed_tc16, hash, recs, base, rows, beta, out_rgba,
                                         nullptr, nullptr, nullptr, nullptr, nullptr, err, amax);
         if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);

@@ -83,6 +83,20 @@ __device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t a, uint64_t b
         : "memory");
 }
 
+// The same MMA with A read from tensor memory: row m of A is TMEM lane m
+// (relative to the lane base of the address), its K = 16 elements packed two
+// per 32-bit column, the lower k in the low half (8 columns per MMA).
+__device__ __forceinline__ void mma_f16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        :
+        : "r"(tmem_d), "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
@@ -186,6 +200,30 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 32 lanes x 16 / 8 columns from registers (one row per thread).
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        :
+        : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+          "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :
+                 : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 :
+                 : "r"(taddr), "r"(v0), "r"(v1), "r"(v2), "r"(v3)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // relu(lo), relu(hi) rounded to f16 (bf16) and packed, lo in the low half.
 __device__ __forceinline__ uint32_t pack_relu_f16(float lo, float hi) {
     uint32_t d;
@@ -261,6 +299,12 @@ __host__ __device__ inline uint32_t off_bias(uint32_t hidden) { return off_ones(
 __host__ __device__ inline uint32_t n_bias(uint32_t hidden) { return 64 + (hidden - 1) * 64 + 16; }
 // FP8 weight scales s_w of the hidden layers (16 floats)
 __host__ __device__ inline uint32_t off_scales(uint32_t hidden) { return off_bias(hidden) + n_bias(hidden) * 4; }
+// End of the image the FP16 and FP8 kernels stage.
+__host__ __device__ inline uint32_t bytes_hi(uint32_t hidden) { return off_scales(hidden) + 64; }
+// Split BF16 operands: the remainders W - bf16(W) of the weight matrices,
+// rounded to BF16, in a second region laid out like [0, off_wout + 2048).
+__host__ __device__ inline uint32_t off_lo(uint32_t hidden) { return (bytes_hi(hidden) + 1023u) & ~1023u; }
+__host__ __device__ inline uint32_t bytes_split(uint32_t hidden) { return off_lo(hidden) + off_wout(hidden) + 2048; }
 }  // namespace tcimg
 
 // 16-bit packing of A-tile rows (f16 or bf16).

@@ -10,7 +10,7 @@ import pytest
 
 from paper_2412_04634_gb300 import scenes
 from test_gpu_parity import FP32_TOL, N, _compare_frames, _near_kink, _run_frame  # noqa: F401
-from test_gpu_tc import BF16_MAX_TOL, FP8_P50, FP8_P99, TC_TOL, _check_rows, _row_errors
+from test_gpu_tc import FP8_P50, FP8_P99, TC_TOL, _check_rows, _row_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +70,7 @@ def test_tc_paper_input(N, oracle, prec):
     g = _run_frame(N, cfg, params, sc, 96, 54, 16, 1, 5, 7, 1, precision=code, rows=True)
     o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(96, 54, 16, 1, 5, 7, 1), rows=True)
     _check_rows(_row_errors(g, o), prec)
-    _compare_frames(g, o, tol=TC_TOL if prec == "fp16" else BF16_MAX_TOL)
+    _compare_frames(g, o, tol=TC_TOL)
 
 
 @pytest.mark.parametrize("W,H,Nc,M", [(1, 1, 0, 1), (5, 3, 1, 1), (17, 9, 2, 1), (31, 5, 4, 1), (13, 11, 6, 1),

@@ -2,8 +2,8 @@
 
 The cache is trained on-line for 30 frames of the dynamic 1080p scene (256
 primitives, hash grid 16 x 2 x 2^19, MLP 64 x 4), then frozen; frame 30 is
-rendered with the layer arithmetic FP32 SIMT, FP16, BF16 and FP8 (E4M3
-hidden layers) tensor cores at
+rendered with the layer arithmetic FP32 SIMT, FP16, split BF16 and FP8
+(E4M3 hidden layers) tensor cores at
 N = 4, 8, 16, 32, 64 (M = 1).  For each point, on about 65,536 sampled rows
 (whole pixels, all of their rows): the per-row relative error of the cache
 value n against the oracle (max and 99th percentile, relative to
@@ -136,12 +136,9 @@ def test_precision_sweep(N, oracle, trained):
             # weights (reported); the frame MRSE moves by < 1 %
             assert r["row_err_p99"] <= 0.5, r
             assert r["mrse_rel_diff"] <= 0.05, r
-        elif r["precision"] == "bf16_tc":
-            # BF16 keeps 8 mantissa bits; n = exp(z), so n's relative error is
-            # z's absolute error, which grows with |z| (trained logits of small
-            # radiance are -6 .. -10): ~2.5 % at the 99th percentile, reported
-            assert r["row_err_p99"] <= 4e-2, r
-            assert r["mrse_rel_diff"] <= 0.01, r
         else:
-            assert r["row_err_p99"] <= 2e-2, r
+            # FP16, and BF16 with split (hi + lo) operands: 2e-2 per cache output at the
+            # maximum, although n = exp(z) turns z's absolute error into n's relative
+            # error and trained logits of small radiance are -6 .. -10
+            assert r["row_err_max"] <= 2e-2, r
             assert r["mrse_rel_diff"] <= 0.01, r
