@@ -30,11 +30,11 @@
 //                next A row back to TMEM.  The network input and output never
 //                touch global memory.
 //  reduction     per-row contributions w * n go to shared memory in row
-//                order; per pixel and channel one thread adds its rows in
+//                order; per pixel and channel one lane adds its rows in
 //                sample order with Kahan compensation (eq. L_mlmc = L_e + L_c
 //                + L_r), carrying the running sum and compensation of a pixel
-//                that straddles two tiles, and one thread per finished pixel
-//                writes it.
+//                that straddles two tiles; a pixel's channels are lanes of one
+//                warp, and its first lane writes the finished pixel.
 //
 // Split BF16 (NIRC_BF16_TC): every 16-bit operand x is carried as hi =
 // bf16(x) and lo = bf16(x - hi); each K step issues hi*hi + lo*hi + hi*lo,
@@ -687,6 +687,7 @@ __global__ void __launch_bounds__(640, 1)
                 const float4* rq = reinterpret_cast<const float4*>(recs + p0 + pl);
                 const float4 q0 = __ldg(rq), q1 = __ldg(rq + 1), q2 = __ldg(rq + 2), q3 = __ldg(rq + 3);
                 const uint32_t flags = __float_as_uint(q3.z);
+                word = (flags & 1u) << 31;  // the pixel's record is valid (signature)
                 if (rin && (flags & 1u)) {
                     if (s < a.N) {
                         // Philox counter of the sample: (unit / unit_div, (unit % unit_div) << 16 | s)
@@ -699,7 +700,7 @@ __global__ void __launch_bounds__(640, 1)
                         wi = bs.wi;
                         w = bs.w;
                         ok = bs.valid;
-                        word = bs.word;
+                        word |= bs.word;
                     } else {
                         const ResidRow* rr = rows + (uint64_t)(p0 + pl) * a.M + (s - a.N);
                         const float4 d = __ldg(&rr->wi), ww = __ldg(&rr->w);
@@ -836,16 +837,22 @@ __global__ void __launch_bounds__(640, 1)
                                  : make_float4(cw.y, cw.z, 0.f, __uint_as_float(word));
             }
             tc::named_bar(bar_id, 128);
+            // Jobs: pass k takes pixels 16 k .. 16 k + 15 of the tile; pixel qi's 8 channels are
+            // lanes 8 g .. 8 g + 7 of warp qi % 4 (g = (qi / 4) % 4), so a pixel's channel sums
+            // meet in one warp and its channel-0 lane writes it after a warp barrier.
             const uint32_t n_q = plast - pf + 1u;  // pixels with rows in this tile
             const float* cin = s_carry + 16u * (jt & 1u);    // written by the previous tile
             float* cout = s_carry + 16u * ((jt + 1u) & 1u);  // read by the next tile
-            for (uint32_t j = t; j < 8u * n_q; j += 128u) {
-                const uint32_t qi = j >> 3, ch = j & 7u;
+            const uint32_t lane_t = t & 31u, ch = lane_t & 7u;
+            for (uint32_t k = 0; 16u * k < n_q; ++k) {
+                const uint32_t qi = 16u * k + (t >> 5) + 4u * (lane_t >> 3);
+                const bool active = qi < n_q;
                 const uint32_t q = pf + qi;
                 const uint32_t q_lo = q * S, q_hi = q_lo + S;
                 const uint32_t lo = max(q_lo, j0), hi = min(q_hi, j0 + 128u);
                 const bool cont_in = q_lo < j0, cont_out = q_hi > j0 + 128u;
-                if (ch < 7u) {
+                uint32_t* fs = s_fin + kFinWords * (qi & 127u);
+                if (active && ch < 7u) {
                     float sum = cont_in ? cin[2 * ch] : 0.f, comp = cont_in ? cin[2 * ch + 1] : 0.f;
                     const float* col = s_rows + ch;
                     for (uint32_t rr = lo; rr < hi; ++rr) {
@@ -858,29 +865,26 @@ __global__ void __launch_bounds__(640, 1)
                         cout[2 * ch] = sum;
                         cout[2 * ch + 1] = comp;
                     } else {
-                        s_fin[kFinWords * qi + ch] = __float_as_uint(sum);
+                        fs[ch] = __float_as_uint(sum);
                     }
-                } else if (sig_out) {
-                    // decision signature of the cache samples, in sample order
+                } else if (active && sig_out) {
+                    // decision signature of the cache samples, in sample order (bit 31 of a
+                    // row's word: its pixel's record is valid)
                     uint64_t sig = cont_in ? s_sigc[jt & 1u] : kSigInit;
-                    const bool qvalid =
-                        __float_as_uint(__ldg(reinterpret_cast<const float4*>(recs + p0 + q) + 3).z) & 1u;
                     const uint32_t hi_c = min(hi, q_lo + a.N);
-                    if (qvalid)
-                        for (uint32_t rr = lo; rr < hi_c; ++rr) sig = sig_mix(sig, __float_as_uint(s_rows[8u * (rr - j0) + 7u]));
+                    for (uint32_t rr = lo; rr < hi_c; ++rr) {
+                        const uint32_t wd = __float_as_uint(s_rows[8u * (rr - j0) + 7u]);
+                        if (wd >> 31) sig = sig_mix(sig, wd & 0x7FFFFFFFu);
+                    }
                     if (cont_out) {
                         s_sigc[(jt + 1u) & 1u] = sig;
                     } else {
-                        s_fin[kFinWords * qi + 8] = (uint32_t)sig;
-                        s_fin[kFinWords * qi + 9] = (uint32_t)(sig >> 32);
+                        fs[8] = (uint32_t)sig;
+                        fs[9] = (uint32_t)(sig >> 32);
                     }
                 }
-            }
-            tc::named_bar(bar_id, 128);
-            for (uint32_t qi = t; qi < n_q; qi += 128u) {
-                const uint32_t q = pf + qi;
-                if (q * S + S > j0 + 128u) continue;  // continues in the next tile
-                const uint32_t* fs = s_fin + kFinWords * qi;
+                __syncwarp();
+                if (!active || ch != 0u || cont_out) continue;
                 const uint32_t gp = p0 + q;
                 PixelBase b;
                 if (base) {
