@@ -975,7 +975,7 @@ def run_serve_bench(args):
                    "latency": "server clock from submission to the completion of the request's batch on the device"},
         "runs": results,
         "server_stats": {k: st[k] for k in ("batches", "graph_instantiations", "graph_updates", "max_batch_seen",
-                                            "arena_peak_bytes", "resident_bytes")},
+                                            "arena_peak_bytes", "resident_bytes", "frame_launches")},
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -60,6 +60,8 @@
 //
 // Every mbarrier wait is bounded (about 2 s); a timeout sets *err, stops
 // further MMAs of that warpgroup and the kernel still frees its TMEM.
+#include <cstring>
+
 #include "nirc_internal.h"
 #include "nirc_tc.cuh"
 
@@ -116,17 +118,41 @@ constexpr uint32_t wg_tile_bytes() { return AB == 0 ? 16384u : 32768u; }
 template <uint32_t AB>
 constexpr uint32_t wg_tmem_cols() { return AB == 1 ? 128u : 96u; }
 
+// What every CTA of a launch shares: the network's shape and encoding.
 struct TcArgs {
-    uint32_t W, H, N, M, k0, k1;
-    uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
-    const SceneHeader* env_hd;   // light mode 2 with a visibility cache: cache values times L_env
-    uint32_t env_nprims;
-    uint32_t S, P, n_blocks;
-    uint64_t s_magic;            // floor(2^40 / S) + 1: x / S = (x * s_magic) >> 40 for x S < 2^40
     float z_clamp;
     uint32_t img_bytes;
     NetShape s;
     GridParams g;
+};
+
+// One frame (or cache pass) of a launch: a launch serves up to kTcMaxJobs of
+// them at once (the frame-request server's batches), CTAs [cta0, cta0 +
+// n_cta) working on job j, each staging that job's weight image once.
+struct TcJob {
+    const uint8_t* img;          // weight image (the job's cache)
+    const __half2* hash16;       // FP16 hash table
+    const nirc_record* recs;
+    const PixelBase* base;
+    const ResidRow* rows;
+    const float4* beta;
+    float4* out;
+    float *lc, *lr, *row_n;
+    uint64_t* sig;
+    uint32_t* count;
+    int* err;                    // the cache's bounded-wait flag
+    const SceneHeader* env_hd;   // light mode 2 with a visibility cache: cache values times L_env
+    uint64_t s_magic;            // floor(2^40 / S) + 1: x / S = (x * s_magic) >> 40 for x S < 2^40
+    uint32_t N, M, k0, k1;
+    uint32_t unit_div, purpose;  // Philox counters of the cache samples (CachePass)
+    uint32_t env_nprims;
+    uint32_t S, P, n_blocks;
+    uint32_t cta0, n_cta;
+};
+constexpr uint32_t kTcMaxJobs = 16;
+struct TcJobs {
+    uint32_t n;
+    TcJob j[kTcMaxJobs];
 };
 
 __device__ __forceinline__ uint32_t div_s(uint32_t x, uint64_t magic) {
@@ -398,12 +424,23 @@ __device__ __forceinline__ void dir_features_fast(V3 w, float* e) {
 // record the amax of every hidden layer's input activations into amax[8 + l].
 template <uint32_t AB, bool kAmax, bool kSh>
 __global__ void __launch_bounds__(640, 1)
-    k_cache_tc(TcArgs a, const uint8_t* __restrict__ img_g, const __half2* __restrict__ hash16,
-               const nirc_record* __restrict__ recs, const PixelBase* __restrict__ base,
-               const ResidRow* __restrict__ rows, const float4* __restrict__ beta, float4* __restrict__ out,
-               float* __restrict__ lc_out, float* __restrict__ lr_out, uint64_t* __restrict__ sig_out,
-               uint32_t* __restrict__ count, float* __restrict__ row_n, int* __restrict__ err,
-               uint32_t* __restrict__ amax) {
+    k_cache_tc(TcArgs a, const __grid_constant__ TcJobs jobs, uint32_t* __restrict__ amax) {
+    uint32_t ji = 0;  // this CTA's job
+    while (ji + 1 < jobs.n && blockIdx.x >= jobs.j[ji + 1].cta0) ++ji;
+    const TcJob& J = jobs.j[ji];
+    const uint8_t* __restrict__ img_g = J.img;
+    const __half2* __restrict__ hash16 = J.hash16;
+    const nirc_record* __restrict__ recs = J.recs;
+    const PixelBase* __restrict__ base = J.base;
+    const ResidRow* __restrict__ rows = J.rows;
+    const float4* __restrict__ beta = J.beta;
+    float4* __restrict__ out = J.out;
+    float* __restrict__ lc_out = J.lc;
+    float* __restrict__ lr_out = J.lr;
+    uint64_t* __restrict__ sig_out = J.sig;
+    uint32_t* __restrict__ count = J.count;
+    float* __restrict__ row_n = J.row_n;
+    int* __restrict__ err = J.err;
     constexpr uint32_t AB16 = AB == 1 ? 1u : 0u;  // type of the 16-bit layers
     constexpr bool kF8 = AB == 2;
     constexpr bool kSplit = AB == 1;
@@ -542,11 +579,11 @@ __global__ void __launch_bounds__(640, 1)
         if constexpr (kSplit) tc::tmem_st4(tAr + 32u + 4u * c, lo[0], lo[1], lo[2], lo[3]);
     };
 
-    const uint32_t S = a.S;
+    const uint32_t S = J.S;
     const uint32_t R_full = 128u * S;
-    for (uint32_t blk = blockIdx.x * n_wg + wg; blk < a.n_blocks; blk += gridDim.x * n_wg) {
+    for (uint32_t blk = (blockIdx.x - J.cta0) * n_wg + wg; blk < J.n_blocks; blk += J.n_cta * n_wg) {
         const uint32_t p0 = blk * 128u;
-        const uint32_t npix = min(128u, a.P - p0);
+        const uint32_t npix = min(128u, J.P - p0);
         // ------------------------------------------------ pixel stage
         {
             float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
@@ -670,10 +707,10 @@ __global__ void __launch_bounds__(640, 1)
         for (uint32_t j0 = 0; j0 < R; j0 += 128u, ++jt) {
             const uint32_t r = j0 + t;
             const bool rin = r < R;
-            const uint32_t pl = rin ? div_s(r, a.s_magic) : 0u;
+            const uint32_t pl = rin ? div_s(r, J.s_magic) : 0u;
             const uint32_t s = rin ? r - pl * S : 0u;
-            const uint32_t pf = div_s(j0, a.s_magic);
-            const uint32_t plast = min(div_s(min(j0 + 127u, R_full - 1u), a.s_magic), npix - 1u);
+            const uint32_t pf = div_s(j0, J.s_magic);
+            const uint32_t plast = min(div_s(min(j0 + 127u, R_full - 1u), J.s_magic), npix - 1u);
             // one-hot window [kb, kb + 16 n_oh) covers pixels pf..plast and stays inside H's 128 columns
             const uint32_t n_oh = (plast - (pf & ~15u) + 16u) >> 4;  // <= 3 for S >= 4
             const uint32_t kb = min(pf & ~15u, 128u - 16u * n_oh);
@@ -689,20 +726,20 @@ __global__ void __launch_bounds__(640, 1)
                 const uint32_t flags = __float_as_uint(q3.z);
                 word = (flags & 1u) << 31;  // the pixel's record is valid (signature)
                 if (rin && (flags & 1u)) {
-                    if (s < a.N) {
+                    if (s < J.N) {
                         // Philox counter of the sample: (unit / unit_div, (unit % unit_div) << 16 | s)
                         const uint32_t u = p0 + pl;
-                        const uint32_t c0 = a.unit_div == 1u ? u : u / a.unit_div;
-                        const uint32_t c1 = a.unit_div == 1u ? s : (((u - c0 * a.unit_div) << 16) | s);
+                        const uint32_t c0 = J.unit_div == 1u ? u : u / J.unit_div;
+                        const uint32_t c1 = J.unit_div == 1u ? s : (((u - c0 * J.unit_div) << 16) | s);
                         const BsdfSample bs =
                             sample_bsdf(V3{q0.w, q1.x, q1.y}, V3{q1.z, q1.w, q2.x}, make_float3(q2.y, q2.z, q2.w),
-                                        q3.x, (flags >> 1) & 3u, a.k0, a.k1, c0, c1, a.purpose);
+                                        q3.x, (flags >> 1) & 3u, J.k0, J.k1, c0, c1, J.purpose);
                         wi = bs.wi;
                         w = bs.w;
                         ok = bs.valid;
                         word |= bs.word;
                     } else {
-                        const ResidRow* rr = rows + (uint64_t)(p0 + pl) * a.M + (s - a.N);
+                        const ResidRow* rr = rows + (uint64_t)(p0 + pl) * J.M + (s - J.N);
                         const float4 d = __ldg(&rr->wi), ww = __ldg(&rr->w);
                         wi = V3{d.x, d.y, d.z};
                         w = make_float3(ww.x, ww.y, ww.z);
@@ -808,8 +845,8 @@ __global__ void __launch_bounds__(640, 1)
                 nv.x = out_act(vis, __uint_as_float(v[0]), a.z_clamp);
                 nv.y = out_act(vis, __uint_as_float(v[1]), a.z_clamp);
                 nv.z = out_act(vis, __uint_as_float(v[2]), a.z_clamp);
-                if (a.env_hd && ok) {  // visibility cache: n = V L_env(w)
-                    const float3 le = env_radiance(env_from(a.env_hd, a.env_nprims), wi);
+                if (J.env_hd && ok) {  // visibility cache: n = V L_env(w)
+                    const float3 le = env_radiance(env_from(J.env_hd, J.env_nprims), wi);
                     nv.x *= le.x;
                     nv.y *= le.y;
                     nv.z *= le.z;
@@ -829,7 +866,7 @@ __global__ void __launch_bounds__(640, 1)
             // compensation of a pixel that began in the previous tile, and one thread
             // per pixel that ends here writes it.
             {
-                const bool is_cache = s < a.N;
+                const bool is_cache = s < J.N;
                 const float3 cw = ok ? make_float3(w.x * nv.x, w.y * nv.y, w.z * nv.z) : make_float3(0.f, 0.f, 0.f);
                 float4* sr = reinterpret_cast<float4*>(s_rows) + 2 * t;
                 sr[0] = is_cache ? make_float4(cw.x, cw.y, cw.z, 0.f) : make_float4(0.f, 0.f, 0.f, cw.x);
@@ -871,7 +908,7 @@ __global__ void __launch_bounds__(640, 1)
                     // decision signature of the cache samples, in sample order (bit 31 of a
                     // row's word: its pixel's record is valid)
                     uint64_t sig = cont_in ? s_sigc[jt & 1u] : kSigInit;
-                    const uint32_t hi_c = min(hi, q_lo + a.N);
+                    const uint32_t hi_c = min(hi, q_lo + J.N);
                     for (uint32_t rr = lo; rr < hi_c; ++rr) {
                         const uint32_t wd = __float_as_uint(s_rows[8u * (rr - j0) + 7u]);
                         if (wd >> 31) sig = sig_mix(sig, wd & 0x7FFFFFFFu);
@@ -893,13 +930,13 @@ __global__ void __launch_bounds__(640, 1)
                     b.le = b.wl = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 float Lc[3] = {0.f, 0.f, 0.f}, Lr[3] = {b.wl.x, b.wl.y, b.wl.z};
-                if (a.N) {
-                    const float inv = 1.0f / (float)a.N;
+                if (J.N) {
+                    const float inv = 1.0f / (float)J.N;
 #pragma unroll
                     for (int cc = 0; cc < 3; ++cc) Lc[cc] = __uint_as_float(fs[cc]) * inv;
                 }
-                if (a.M && a.N) {  // without a cache level nothing is subtracted
-                    const float inv = 1.0f / (float)a.M;
+                if (J.M && J.N) {  // without a cache level nothing is subtracted
+                    const float inv = 1.0f / (float)J.M;
 #pragma unroll
                     for (int cc = 0; cc < 3; ++cc) Lr[cc] -= __uint_as_float(fs[3 + cc]) * inv;
                 }
@@ -1003,31 +1040,20 @@ bool tc_supported(const nirc_handle* h, const nirc_frame_desc& fd) {
 
 template <uint32_t AB, bool kAmax, bool kSh>
 static cudaError_t launch_tc_kernel(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
-                                      const void* img, const __half2* hash, const nirc_record* recs,
-                                      const PixelBase* base, const ResidRow* rows, const float4* beta, float* out,
-                                      float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
-                                      uint32_t* amax) {
+                                    const TcJobs& jobs, uint32_t* amax) {
     cudaError_t e =
         cudaFuncSetAttribute(k_cache_tc<AB, kAmax, kSh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_cache_tc<AB, kAmax, kSh><<<grid, threads, smem, st>>>(a, reinterpret_cast<const uint8_t*>(img), hash, recs, base,
-                                                            rows, beta, reinterpret_cast<float4*>(out), lc, lr, sig,
-                                                            count, row_n, err, amax);
+    k_cache_tc<AB, kAmax, kSh><<<grid, threads, smem, st>>>(a, jobs, amax);
     return cudaGetLastError();
 }
 
 // The instance for the network input of a.s (frequency or the paper's).
 template <uint32_t AB, bool kAmax>
 static cudaError_t launch_tc_instance(uint32_t grid, uint32_t threads, size_t smem, cudaStream_t st, const TcArgs& a,
-                                      const void* img, const __half2* hash, const nirc_record* recs,
-                                      const PixelBase* base, const ResidRow* rows, const float4* beta, float* out,
-                                      float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
-                                      uint32_t* amax) {
-    if (a.s.sh)
-        return launch_tc_kernel<AB, kAmax, true>(grid, threads, smem, st, a, img, hash, recs, base, rows, beta, out, lc,
-                                                 lr, sig, count, row_n, err, amax);
-    return launch_tc_kernel<AB, kAmax, false>(grid, threads, smem, st, a, img, hash, recs, base, rows, beta, out, lc,
-                                              lr, sig, count, row_n, err, amax);
+                                      const TcJobs& jobs, uint32_t* amax) {
+    if (a.s.sh) return launch_tc_kernel<AB, kAmax, true>(grid, threads, smem, st, a, jobs, amax);
+    return launch_tc_kernel<AB, kAmax, false>(grid, threads, smem, st, a, jobs, amax);
 }
 
 // Warpgroups per CTA for operand type AB: as many as shared and tensor memory hold (<= 5).
@@ -1040,67 +1066,144 @@ static uint32_t tc_warpgroups(uint32_t img_bytes, int max_smem, size_t* smem) {
     return n_wg;
 }
 
+static TcArgs tc_args(const nirc_handle* h) {
+    TcArgs a;
+    a.z_clamp = h->cfg.z_clamp;
+    a.s = h->shape;
+    a.g = h->grid;
+    a.img_bytes = h->cfg.precision == NIRC_BF16_TC ? tcimg::bytes_split(h->shape.hidden)
+                                                   : tcimg::bytes_hi(h->shape.hidden);
+    return a;
+}
+
+static TcJob tc_job(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs, const PixelBase* base,
+                    const ResidRow* rows, const float4* beta, float* out_rgba, float* lc, float* lr, uint64_t* sig,
+                    uint32_t* count, float* row_n, int* err, CachePass pass, EnvSource env) {
+    TcJob j{};
+    j.img = reinterpret_cast<const uint8_t*>(h->packed_tc);
+    j.hash16 = reinterpret_cast<const __half2*>(h->hash16);
+    j.recs = recs;
+    j.base = base;
+    j.rows = rows;
+    j.beta = beta;
+    j.out = reinterpret_cast<float4*>(out_rgba);
+    j.lc = lc;
+    j.lr = lr;
+    j.row_n = row_n;
+    j.sig = sig;
+    j.count = count;
+    j.err = err;
+    j.env_hd = reinterpret_cast<const SceneHeader*>(env.scene);
+    j.env_nprims = env.n_prims;
+    j.N = fd.n_cache;
+    j.M = fd.n_resid;
+    j.k0 = (uint32_t)fd.seed;
+    j.k1 = fd.frame;
+    j.unit_div = pass.unit_div;
+    j.purpose = pass.purpose;
+    j.S = fd.n_cache + fd.n_resid;
+    j.s_magic = (1ull << 40) / j.S + 1;
+    j.P = fd.width * fd.height;
+    j.n_blocks = (j.P + 127) / 128;
+    return j;
+}
+
+static uint32_t tc_launch_shape(const nirc_handle* h, uint32_t img_bytes, size_t* smem) {
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    const nirc_precision p = (nirc_precision)h->cfg.precision;
+    const uint32_t n_wg = p == NIRC_BF16_TC ? tc_warpgroups<1>(img_bytes, max_smem, smem)
+                                            : (p == NIRC_FP8_E4M3_TC ? tc_warpgroups<2>(img_bytes, max_smem, smem)
+                                                                      : tc_warpgroups<0>(img_bytes, max_smem, smem));
+    return *smem > (size_t)max_smem ? 0u : n_wg;
+}
+
 cudaError_t launch_cache_tc(const nirc_handle* h, const nirc_frame_desc& fd, const nirc_record* recs,
                             const PixelBase* base, const ResidRow* rows, const float4* beta, float* out_rgba,
                             float* lc, float* lr, uint64_t* sig, uint32_t* count, float* row_n, int* err,
                             cudaStream_t st, CachePass pass, EnvSource env) {
-    TcArgs a;
-    a.unit_div = pass.unit_div;
-    a.purpose = pass.purpose;
-    a.env_hd = reinterpret_cast<const SceneHeader*>(env.scene);
-    a.env_nprims = env.n_prims;
-    a.W = fd.width;
-    a.H = fd.height;
-    a.N = fd.n_cache;
-    a.M = fd.n_resid;
-    a.k0 = (uint32_t)fd.seed;
-    a.k1 = fd.frame;
-    a.S = fd.n_cache + fd.n_resid;
-    a.s_magic = (1ull << 40) / a.S + 1;
-    a.P = fd.width * fd.height;
-    a.n_blocks = (a.P + 127) / 128;
-    a.z_clamp = h->cfg.z_clamp;
-    a.s = h->shape;
-    a.g = h->grid;
-    const bool split = h->cfg.precision == NIRC_BF16_TC;
-    a.img_bytes = split ? tcimg::bytes_split(h->shape.hidden) : tcimg::bytes_hi(h->shape.hidden);
-    int dev = h->device, max_smem = 0;
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const TcArgs a = tc_args(h);
+    TcJobs jobs;
+    jobs.n = 1;
+    jobs.j[0] = tc_job(h, fd, recs, base, rows, beta, out_rgba, lc, lr, sig, count, row_n, err, pass, env);
     size_t smem = 0;
-    const uint32_t n_wg = split ? tc_warpgroups<1>(a.img_bytes, max_smem, &smem)
-                                : (h->cfg.precision == NIRC_FP8_E4M3_TC ? tc_warpgroups<2>(a.img_bytes, max_smem, &smem)
-                                                                       : tc_warpgroups<0>(a.img_bytes, max_smem, &smem));
-    if (smem > (size_t)max_smem) return cudaErrorInvalidConfiguration;
-    uint32_t grid = (a.n_blocks + n_wg - 1) / n_wg;
+    const uint32_t n_wg = tc_launch_shape(h, a.img_bytes, &smem);
+    if (!n_wg) return cudaErrorInvalidConfiguration;
+    uint32_t grid = (jobs.j[0].n_blocks + n_wg - 1) / n_wg;
     if (grid > (uint32_t)h->num_sms) grid = h->num_sms;
-    const __half2* hash = reinterpret_cast<const __half2*>(h->hash16);
+    jobs.j[0].cta0 = 0;
+    jobs.j[0].n_cta = grid;
     const uint32_t threads = n_wg * 128;
     count_kernels(h);  // the cache kernel; FP8 adds an amax roll (and a calibration pair) below
-    if (split)
-        return launch_tc_instance<1, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba,
-                                            lc, lr, sig, count, row_n, err, nullptr);
+    if (h->cfg.precision == NIRC_BF16_TC) return launch_tc_instance<1, false>(grid, threads, smem, st, a, jobs, nullptr);
     if (h->cfg.precision != NIRC_FP8_E4M3_TC)
-        return launch_tc_instance<0, false>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba,
-                                            lc, lr, sig, count, row_n, err, nullptr);
+        return launch_tc_instance<0, false>(grid, threads, smem, st, a, jobs, nullptr);
     cudaError_t e = cudaSuccess;
     uint32_t* amax = h->fp8_amax;
     const uint32_t n_slots = h->shape.hidden - 1;
     if (!h->fp8_calibrated) {
         // one FP16 launch records the activation amax (its image is overwritten below); it
         // runs with the FP8 launch's warpgroup count, whose shared memory covers the FP16 layout
-        e = launch_tc_instance<0, true>(grid, threads, smem, st, a, h->packed_tc16, hash, recs, base, rows, beta, out_rgba,
-                                        nullptr, nullptr, nullptr, nullptr, nullptr, err, amax);
+        TcJobs cal = jobs;
+        cal.j[0].img = reinterpret_cast<const uint8_t*>(h->packed_tc16);
+        cal.j[0].lc = cal.j[0].lr = cal.j[0].row_n = nullptr;
+        cal.j[0].sig = nullptr;
+        cal.j[0].count = nullptr;
+        e = launch_tc_instance<0, true>(grid, threads, smem, st, a, cal, amax);
         if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
         count_kernels(h, 2);
         if (e == cudaSuccess) e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const_cast<nirc_handle*>(h)->fp8_calibrated = true;
     }
-    e = launch_tc_instance<2, true>(grid, threads, smem, st, a, h->packed_tc, hash, recs, base, rows, beta, out_rgba, lc, lr,
-                                    sig, count, row_n, err, amax);
+    e = launch_tc_instance<2, true>(grid, threads, smem, st, a, jobs, amax);
     if (e == cudaSuccess) k_amax_roll<<<1, 32, 0, st>>>(amax, n_slots);
     count_kernels(h);
     return e == cudaSuccess ? cudaGetLastError() : e;
+}
+
+bool tc_batchable(const nirc_handle* a, const nirc_handle* b) {
+    return (a->cfg.precision == NIRC_FP16_TC || a->cfg.precision == NIRC_BF16_TC) &&
+           a->cfg.precision == b->cfg.precision && memcmp(&a->shape, &b->shape, sizeof(NetShape)) == 0 &&
+           memcmp(&a->grid, &b->grid, sizeof(GridParams)) == 0 && a->cfg.z_clamp == b->cfg.z_clamp;
+}
+
+cudaError_t launch_cache_tc_batch(const FrameJob* fj, uint32_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (n > kTcMaxJobs) return cudaErrorInvalidValue;
+    const nirc_handle* h0 = fj[0].h;
+    const TcArgs a = tc_args(h0);
+    size_t smem = 0;
+    const uint32_t n_wg = tc_launch_shape(h0, a.img_bytes, &smem);
+    if (!n_wg) return cudaErrorInvalidConfiguration;
+    TcJobs jobs;
+    jobs.n = n;
+    uint64_t rows_total = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const FrameJob& f = fj[i];
+        if (!tc_batchable(h0, f.h) || !tc_supported(f.h, f.fd)) return cudaErrorInvalidValue;
+        jobs.j[i] = tc_job(f.h, f.fd, f.recs, f.base, f.rows, nullptr, f.out, nullptr, nullptr, nullptr, nullptr,
+                           nullptr, f.h->dev_err, CachePass{}, EnvSource{});
+        rows_total += (uint64_t)jobs.j[i].n_blocks * jobs.j[i].S;
+    }
+    // CTAs in proportion to each job's row tiles, at least one each and no more than it can use
+    const uint32_t grid_max = (uint32_t)h0->num_sms;
+    if (grid_max < n) return cudaErrorInvalidConfiguration;
+    uint32_t cta = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        TcJob& j = jobs.j[i];
+        const uint64_t tiles = (uint64_t)j.n_blocks * j.S;
+        uint64_t share = tiles * (grid_max - n) / rows_total + 1;  // the shares add up to <= grid_max
+        const uint64_t useful = (j.n_blocks + n_wg - 1) / n_wg;
+        if (share > useful) share = useful;
+        j.cta0 = cta;
+        j.n_cta = (uint32_t)share;
+        cta += (uint32_t)share;
+    }
+    const uint32_t threads = n_wg * 128;
+    for (uint32_t i = 0; i < n; ++i) count_kernels(fj[i].h);
+    if (h0->cfg.precision == NIRC_BF16_TC) return launch_tc_instance<1, false>(cta, threads, smem, st, a, jobs, nullptr);
+    return launch_tc_instance<0, false>(cta, threads, smem, st, a, jobs, nullptr);
 }
 
 }  // namespace nirc

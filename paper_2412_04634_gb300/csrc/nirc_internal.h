@@ -223,6 +223,25 @@ nirc_status enqueue_frame(const char* who, const nirc_handle* h, const void* sce
 // Grow the handle's training scratch for batches of n (cudaMalloc).
 nirc_status reserve_train_scratch(nirc_handle* h, uint64_t n);
 
+// Frames of several caches in one launch per kernel (the frame-request
+// server's batches): two-level estimator, whole frames, light modes 0 and 1
+// (one light mode per path-tracing launch), one tensor-core precision and
+// network shape across the cache launch (tc_batchable).
+constexpr uint32_t kMaxFrameJobs = 16;
+struct FrameJob {
+    const nirc_handle* h;
+    nirc_frame_desc fd;
+    const void* scene;
+    nirc_record* recs;          // frame scratch, as enqueue_frame carves it
+    PixelBase* base;
+    ResidRow* rows;
+    float* out;                 // RGBA image
+    unsigned long long* work;   // the path tracer's pixel counter, zeroed before the launch
+};
+cudaError_t launch_primary_resid_batch(const FrameJob* fj, uint32_t n, cudaStream_t st);  // nirc_pt.cu
+bool tc_batchable(const nirc_handle* a, const nirc_handle* b);                             // nirc_cache_tc.cu
+cudaError_t launch_cache_tc_batch(const FrameJob* fj, uint32_t n, cudaStream_t st);       // nirc_cache_tc.cu
+
 // nirc_metrics.cu
 cudaError_t launch_mrse(const float* img, const float* ref, uint64_t n, float eps, double* out, cudaStream_t st);
 

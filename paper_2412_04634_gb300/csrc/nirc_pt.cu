@@ -360,15 +360,11 @@ enum : uint32_t { kNeedPixel = 0, kCameraRay = 1, kResidRay = 2, kNoMoreWork = 3
 // lane: a lane whose pixel is done takes the next pixel from a work counter
 // (one atomic per warp), so lanes do not idle while others finish long paths.
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(const SceneHeader* __restrict__ hd_g,
-                                                              const Prim* __restrict__ gp, FrameArgs a,
-                                                              nirc_record* __restrict__ recs,
-                                                              PixelBase* __restrict__ base,
-                                                              ResidRow* __restrict__ rows,
-                                                              uint64_t* __restrict__ sig_out,
-                                                              uint32_t* __restrict__ count,
-                                                              unsigned long long* __restrict__ work,
-                                                              MvOut mvo) {
+__device__ __forceinline__ void primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
+                                              const FrameArgs& a, nirc_record* __restrict__ recs,
+                                              PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
+                                              uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
+                                              unsigned long long* __restrict__ work, const MvOut& mvo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ SceneHeader hd;
     __shared__ uint32_t s_nlights;
@@ -520,6 +516,42 @@ __global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid(cons
         }
     }
     if (a.rays) add_rays(a.rays, tr.rays);
+}
+
+template <bool kNee>
+__global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5)
+    k_primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
+                    nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
+                    uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, unsigned long long* __restrict__ work,
+                    MvOut mvo) {
+    primary_resid<kNee>(hd_g, gp, a, recs, base, rows, sig_out, count, work, mvo);
+}
+
+// Several frames in one launch (the frame-request server's batches): CTAs
+// [cta0, next job's cta0) trace job j's frame, staging its scene once and
+// taking its pixels from its own counter.
+struct PtJob {
+    const SceneHeader* hd;
+    const Prim* gp;
+    FrameArgs a;
+    nirc_record* recs;
+    PixelBase* base;
+    ResidRow* rows;
+    unsigned long long* work;
+    uint32_t cta0;
+};
+struct PtJobs {
+    uint32_t n;
+    PtJob j[kMaxFrameJobs];
+};
+
+template <bool kNee>
+__global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid_batch(const __grid_constant__ PtJobs jobs) {
+    uint32_t ji = 0;
+    while (ji + 1 < jobs.n && blockIdx.x >= jobs.j[ji + 1].cta0) ++ji;
+    const PtJob& J = jobs.j[ji];
+    primary_resid<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, J.work,
+                        MvOut{nullptr, nullptr, nullptr, 0});
 }
 
 // ---------------------------------------------------------------------------
@@ -847,6 +879,62 @@ cudaError_t launch_primary_resid(const nirc_handle* h, const void* scene, const 
     if (fd.light_mode == 1)
         return launch_primary_resid_t<true>(h, hd, gp, a, P, recs, base, rows, sig, count, mv, st);
     return launch_primary_resid_t<false>(h, hd, gp, a, P, recs, base, rows, sig, count, mv, st);
+}
+
+template <bool kNee>
+static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, cudaStream_t st) {
+    const nirc_handle* h0 = fj[0].h;
+    uint32_t max_prims = 0;
+    uint64_t work_total = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        max_prims = max_prims > fj[i].fd.n_prims ? max_prims : fj[i].fd.n_prims;
+        work_total += (uint64_t)fj[i].fd.width * fj[i].fd.height * (1u + fj[i].fd.n_resid);
+    }
+    const size_t smem = pt_smem(max_prims);
+    cudaError_t e = cudaFuncSetAttribute(k_primary_resid_batch<kNee>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primary_resid_batch<kNee>, kPtThreads, smem);
+    if (e != cudaSuccess) return e;
+    const uint64_t grid_max = (uint64_t)(per_sm < 1 ? 1 : per_sm) * (uint64_t)h0->num_sms;
+    if (grid_max < n) return cudaErrorInvalidConfiguration;
+    // CTAs in proportion to each frame's rays (camera + residual paths), at least one
+    // each and no more than one per 128 pixels
+    PtJobs jobs;
+    jobs.n = n;
+    uint32_t cta = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+        const FrameJob& f = fj[i];
+        const uint64_t P = (uint64_t)f.fd.width * f.fd.height;
+        uint64_t share = P * (1u + f.fd.n_resid) * (grid_max - n) / work_total + 1;  // the shares add up to <= grid_max
+        const uint64_t useful = (P + kPtThreads - 1) / kPtThreads;
+        if (share > useful) share = useful;
+        PtJob& j = jobs.j[i];
+        j.hd = reinterpret_cast<const SceneHeader*>(f.scene);
+        j.gp = reinterpret_cast<const Prim*>(reinterpret_cast<const char*>(f.scene) + sizeof(SceneHeader));
+        j.a = FrameArgs{f.fd.width, f.fd.height, f.fd.n_cache, f.fd.n_resid, f.fd.max_depth, f.fd.n_prims,
+                        (uint32_t)f.fd.seed, f.fd.frame, 0u, nullptr};
+        j.recs = f.recs;
+        j.base = f.base;
+        j.rows = f.rows;
+        j.work = f.work;
+        j.cta0 = cta;
+        cta += (uint32_t)share;
+        count_kernels(f.h);
+    }
+    k_primary_resid_batch<kNee><<<cta, kPtThreads, smem, st>>>(jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primary_resid_batch(const FrameJob* fj, uint32_t n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (n > kMaxFrameJobs) return cudaErrorInvalidValue;
+    for (uint32_t i = 1; i < n; ++i)
+        if (fj[i].fd.light_mode != fj[0].fd.light_mode) return cudaErrorInvalidValue;
+    if (fj[0].fd.light_mode == 1) return launch_primary_resid_batch_t<true>(fj, n, st);
+    if (fj[0].fd.light_mode == 0) return launch_primary_resid_batch_t<false>(fj, n, st);
+    return cudaErrorInvalidValue;
 }
 
 template <bool kNee>

@@ -9,10 +9,16 @@
 //             granules, neighbours coalesced on release
 //  scheduler  forms a batch from the FIFO (arrival order, skipping requests
 //             whose scene is busy, stopping at the first that does not fit),
-//             captures the batch into a CUDA graph whose branches are the
-//             requests' kernel chains (fork/join over worker streams),
-//             re-uses the batch slot's executable graph via
-//             cudaGraphExecUpdate when it can, and launches it
+//             captures the batch into a CUDA graph, re-uses the batch
+//             slot's executable graph via cudaGraphExecUpdate when it can,
+//             and launches it.  In the graph the frames of all requests are
+//             one path-tracing launch (per light mode) and one cache-integral
+//             launch over the union of their pixels, CTAs shared out in
+//             proportion to each request's work; then each request's
+//             training pass and step run as their own branch (fork/join over
+//             worker streams).  A batch that cannot share launches (another
+//             precision, network shape or light mode 2 among its caches)
+//             runs each request's whole chain as its own branch.
 //  completer  polls the in-flight batches' events, stamps completion times,
 //             returns frame scratch to the arena and frees the scenes
 #include <algorithm>
@@ -146,6 +152,7 @@ struct nirc_server {
     std::vector<std::vector<cudaEvent_t>> join_ev;     // [slot][request]
     std::vector<std::vector<cudaGraphExec_t>> execs;   // [slot][batch size]
     std::vector<bool> slot_busy;
+    unsigned long long* work_counters = nullptr;       // [slot][request]: path-tracing pixel counters
 
     nirc_server_stats stats{};
     std::thread scheduler, completer;
@@ -153,6 +160,9 @@ struct nirc_server {
     void run_scheduler();
     void run_completer();
     nirc_status enqueue_request(Req* q, cudaStream_t st);
+    nirc_status enqueue_training(Req* q, cudaStream_t st);
+    bool shares_launches(const Batch* b) const;
+    nirc_status enqueue_batch_frames(Batch* b, cudaStream_t st);
     nirc_status launch_batch(Batch* b);
 };
 
@@ -172,19 +182,98 @@ nirc_status nirc_server::enqueue_request(Req* q, cudaStream_t st) {
     const void* blob = sc.frames + (uint64_t)(q->r.frame % sc.n_frames) * sc.stride;
     float* img = reinterpret_cast<float*>(arena_base + q->img_off);
     void* scratch = arena_base + q->scr_off;
-    if (cfg.train_samples && sc.h->train_scratch_bytes < train_scratch_bytes(sc.h, cfg.train_samples)) {
-        // the handle's training mode changed after registration; scratch
-        // cannot grow inside a batch (it may be captured into a graph)
+    nirc_status s = enqueue_frame("nirc_server", sc.h, blob, fd, img, nullptr, scratch, st);
+    if (s == NIRC_OK) {
+        std::lock_guard<std::mutex> lk(mu);
+        stats.frame_launches += 2;  // path tracing and cache integral
+    }
+    if (s != NIRC_OK) return s;
+    return enqueue_training(q, st);
+}
+
+nirc_status nirc_server::enqueue_training(Req* q, cudaStream_t st) {
+    SceneSlot& sc = scenes[q->r.scene];
+    if (cfg.train_samples == 0) return NIRC_OK;
+    if (sc.h->train_scratch_bytes < train_scratch_bytes(sc.h, cfg.train_samples)) {
         set_error("nirc_server: scene %u needs more training scratch than was reserved at registration "
                   "(set the handle's training modes before nirc_server_add_scene)", q->r.scene);
         return NIRC_ERR_BUDGET;
     }
-    nirc_status s = enqueue_frame("nirc_server", sc.h, blob, fd, img, nullptr, scratch, st);
-    if (s != NIRC_OK || cfg.train_samples == 0) return s;
-    cudaError_t e = launch_gen_train(sc.h, blob, sc.n_prims, fd.width, fd.height, cfg.train_samples, fd.frame,
-                                     sc.seed, fd.max_depth, fd.light_mode, sc.trecs, sc.tdirs, sc.ttgts, st);
+    const void* blob = sc.frames + (uint64_t)(q->r.frame % sc.n_frames) * sc.stride;
+    cudaError_t e = launch_gen_train(sc.h, blob, sc.n_prims, q->r.width, q->r.height, cfg.train_samples, q->r.frame,
+                                     sc.seed, q->r.max_depth, q->r.light_mode, sc.trecs, sc.tdirs, sc.ttgts, st);
     if (e == cudaSuccess) e = launch_train_step(sc.h, sc.trecs, sc.tdirs, sc.ttgts, cfg.train_samples, nullptr, st);
     return cuda_status(e, "nirc_server (training)");
+}
+
+// Whether the batch's frames can share one path-tracing launch per light
+// mode and one cache-integral launch.
+bool nirc_server::shares_launches(const Batch* b) const {
+    const nirc_handle* h0 = scenes[b->reqs[0]->r.scene].h;
+    for (const Req* q : b->reqs) {
+        const nirc_handle* h = scenes[q->r.scene].h;
+        nirc_frame_desc fd{};
+        fd.width = q->r.width;
+        fd.height = q->r.height;
+        fd.n_cache = q->r.n_cache;
+        fd.n_resid = q->r.n_resid;
+        if (q->r.light_mode > 1 || h->timing || !tc_batchable(h0, h) || !tc_supported(h, fd)) return false;
+    }
+    return true;
+}
+
+nirc_status nirc_server::enqueue_batch_frames(Batch* b, cudaStream_t st) {
+    const uint32_t n = (uint32_t)b->reqs.size();
+    FrameJob fj[kMaxFrameJobs];
+    unsigned long long* counters = work_counters + (uint64_t)b->slot * kMaxSlots;
+    for (uint32_t i = 0; i < n; ++i) {
+        const Req* q = b->reqs[i];
+        const SceneSlot& sc = scenes[q->r.scene];
+        FrameJob& f = fj[i];
+        f.h = sc.h;
+        f.fd = nirc_frame_desc{};
+        f.fd.width = q->r.width;
+        f.fd.height = q->r.height;
+        f.fd.n_cache = q->r.n_cache;
+        f.fd.n_resid = q->r.n_resid;
+        f.fd.max_depth = q->r.max_depth;
+        f.fd.frame = q->r.frame;
+        f.fd.seed = sc.seed;
+        f.fd.n_prims = sc.n_prims;
+        f.fd.light_mode = q->r.light_mode;
+        f.scene = sc.frames + (uint64_t)(q->r.frame % sc.n_frames) * sc.stride;
+        // frame scratch as enqueue_frame carves it: records | per-pixel bases | residual rows
+        const uint64_t P = (uint64_t)q->r.width * q->r.height;
+        char* sp = arena_base + q->scr_off;
+        f.recs = reinterpret_cast<nirc_record*>(sp);
+        f.base = reinterpret_cast<PixelBase*>(sp + granule(P * sizeof(nirc_record)));
+        f.rows = reinterpret_cast<ResidRow*>(sp + granule(P * sizeof(nirc_record)) + granule(P * sizeof(PixelBase)));
+        f.out = reinterpret_cast<float*>(arena_base + q->img_off);
+        f.work = counters + i;
+    }
+    cudaError_t e = cudaMemsetAsync(counters, 0, n * sizeof(unsigned long long), st);
+    uint32_t launches = 0;
+    for (uint32_t lm = 0; lm <= 1 && e == cudaSuccess; ++lm) {
+        FrameJob sub[kMaxFrameJobs];
+        uint32_t m = 0;
+        for (uint32_t i = 0; i < n; ++i)
+            if (fj[i].fd.light_mode == lm) sub[m++] = fj[i];
+        if (m) {
+            e = launch_primary_resid_batch(sub, m, st);
+            ++launches;
+        }
+    }
+    if (e == cudaSuccess) {
+        e = launch_cache_tc_batch(fj, n, st);
+        ++launches;
+    }
+    for (uint32_t i = 0; i < n && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(fj[i].h->host_err, fj[i].h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(mu);
+        stats.frame_launches += launches;
+    }
+    return cuda_status(e, "nirc_server (batched frames)");
 }
 
 nirc_status nirc_server::launch_batch(Batch* b) {
@@ -197,12 +286,14 @@ nirc_status nirc_server::launch_batch(Batch* b) {
     if (graphs) e = cudaStreamBeginCapture(ls, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return cuda_status(e, "nirc_server (begin capture)");
     nirc_status s = NIRC_OK;
-    e = cudaEventRecord(fork_ev[k], ls);
+    const bool shared = shares_launches(b);
+    if (shared) s = enqueue_batch_frames(b, ls);  // every frame of the batch: one launch per kernel
+    if (s == NIRC_OK) e = cudaEventRecord(fork_ev[k], ls);
     for (size_t i = 0; i < n && e == cudaSuccess && s == NIRC_OK; ++i) {
         cudaStream_t ws = worker_st[k][i];
         e = cudaStreamWaitEvent(ws, fork_ev[k], 0);
         if (e != cudaSuccess) break;
-        s = enqueue_request(b->reqs[i], ws);
+        s = shared ? enqueue_training(b->reqs[i], ws) : enqueue_request(b->reqs[i], ws);
         if (s != NIRC_OK) break;
         e = cudaEventRecord(join_ev[k][i], ws);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ls, join_ev[k][i], 0);
@@ -401,6 +492,11 @@ nirc_status nirc_server_create(const nirc_server_config* cfg, nirc_server** out)
     if (e != cudaSuccess) {
         s->arena_base = nullptr;
         return server_fail(s, cuda_status(e, "nirc_server_create (arena)"));
+    }
+    e = cudaMalloc(&s->work_counters, (size_t)kMaxBatches * kMaxSlots * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        s->work_counters = nullptr;
+        return server_fail(s, cuda_status(e, "nirc_server_create (work counters)"));
     }
     s->arena.init(cfg->budget_bytes);
     const uint32_t B = cfg->max_batches, S = cfg->slots;
@@ -697,6 +793,7 @@ nirc_status nirc_server_destroy(nirc_server* s) {
         cudaFree(sc.ttgts);
     }
     cudaFree(s->arena_base);
+    cudaFree(s->work_counters);
     delete s;
     return NIRC_OK;
 }

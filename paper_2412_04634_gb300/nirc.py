@@ -92,7 +92,8 @@ class nirc_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "batches",
                                                  "graph_instantiations", "graph_updates", "arena_bytes",
                                                  "arena_peak_bytes", "resident_bytes")] + \
-               [(n, ctypes.c_uint32) for n in ("queued", "in_flight", "max_batch_seen", "pad")]
+               [(n, ctypes.c_uint32) for n in ("queued", "in_flight", "max_batch_seen", "pad")] + \
+               [("frame_launches", ctypes.c_uint64)]
 
 
 def _load():

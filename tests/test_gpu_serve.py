@@ -175,3 +175,84 @@ def test_graph_launch_matches_stream_launch(N):
     assert st_s["graph_instantiations"] + st_s["graph_updates"] == 0
     for r in reqs:
         assert np.array_equal(g[r[0]], s[r[0]]), r
+
+
+def _direct_frame(N, cache, frames, W, H, Nc, M, D, frame, seed, light_mode=0):
+    import torch
+    sc = N.scene_to_tensor(frames[frame % len(frames)])
+    out = torch.empty((W * H, 4), device="cuda")
+    N.nirc_estimate_frame(cache.h, sc, N.frame_desc(W, H, Nc, M, D, frame, seed, frames[0].n_prims,
+                                                    light_mode=light_mode), out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _serve_lm(N, requests, precisions, slots=8):
+    """Serve [(id, scene, W, H, Nc, M, depth, frame, light_mode)] over fresh
+    caches (one per entry of `precisions`); all requests are queued before
+    the first poll.  Returns ({id: image}, stats)."""
+    import torch
+    cfg = _hash_cfg()
+    srv = N.Server(64 << 20, slots=slots, max_batches=1, train_samples=T_TRAIN)
+    caches = [_cache(N, cfg, 10 + s, precision=p) for s, p in enumerate(precisions)]
+    for s in range(len(precisions)):
+        srv.add_scene(caches[s], _scene_frames(1 + s), seed=1 + s)
+    for r in requests:
+        srv.submit(*r)
+    shapes = {r[0]: (r[2], r[3]) for r in requests}
+    imgs = {}
+    while len(imgs) < len(requests):
+        for c in srv.poll(wait=True):
+            assert c.status == 0
+            imgs[c.id] = srv.image(c, *shapes[c.id]).cpu().numpy()
+            srv.release(c.id)
+    torch.cuda.synchronize()
+    st = srv.stats()
+    srv.close()
+    for c in caches:
+        c.close()
+    return imgs, st
+
+
+@pytest.mark.parametrize("light_modes", [(0, 0, 0, 0), (0, 1, 1, 0)])
+def test_batch_frames_share_one_launch_per_kernel(N, light_modes):
+    """A batch of requests of different resolutions and N over four caches
+    is one path-tracing launch per light mode and one cache-integral launch
+    over the union of their pixels; each request's image is still exactly
+    the frame a single renderer computes with its cache (first request of
+    every scene: the weights before any served training step)."""
+    sizes = [(64, 48, 8), (32, 32, 4), (80, 40, 16), (48, 48, 32)]
+    reqs = []
+    for k in range(3):
+        for s in range(4):
+            W, H, Nc = sizes[(s + k) % 4]
+            reqs.append((4 * k + s, s, W, H, Nc, 1, 4, k, light_modes[s]))
+    imgs, st = _serve_lm(N, reqs, [1, 1, 1, 1])
+    modes_per_batch = len(set(light_modes))
+    assert st["max_batch_seen"] >= 2
+    assert 2 * st["batches"] <= st["frame_launches"] <= (1 + modes_per_batch) * st["batches"], st
+    if modes_per_batch == 1:
+        assert st["frame_launches"] == 2 * st["batches"], st
+    cfg = _hash_cfg()
+    for s in range(4):
+        W, H, Nc = sizes[s % 4]
+        c = _cache(N, cfg, 10 + s)
+        ref = _direct_frame(N, c, _scene_frames(1 + s), W, H, Nc, 1, 4, 0, 1 + s, light_modes[s])
+        c.close()
+        assert np.array_equal(imgs[s], ref), s
+
+
+def test_batch_of_mixed_precisions_runs_per_request(N):
+    """Caches of different precisions cannot share the cache-integral launch:
+    each request then runs its own frame kernels (two launches each), with
+    the same images as single-renderer calls."""
+    reqs = [(s, s, 48, 32, 8, 1, 4, 0, 0) for s in range(4)]
+    precisions = [1, 2, 1, 2]  # FP16 and split BF16 tensor cores
+    imgs, st = _serve_lm(N, reqs, precisions)
+    assert st["frame_launches"] == 2 * len(reqs), st
+    cfg = _hash_cfg()
+    for s in range(4):
+        c = _cache(N, cfg, 10 + s, precision=precisions[s])
+        ref = _direct_frame(N, c, _scene_frames(1 + s), 48, 32, 8, 1, 4, 0, 1 + s)
+        c.close()
+        assert np.array_equal(imgs[s], ref), s
