@@ -34,7 +34,8 @@
 //                sample order with Kahan compensation (eq. L_mlmc = L_e + L_c
 //                + L_r), carrying the running sum and compensation of a pixel
 //                that straddles two tiles; a pixel's channels are lanes of one
-//                warp, and its first lane writes the finished pixel.
+//                warp, which write the finished pixel.  A tile's sums are
+//                formed while the next tile's layer-0 MMA runs.
 //
 // Split BF16 (NIRC_BF16_TC): every 16-bit operand x is carried as hi =
 // bf16(x) and lo = bf16(x - hi); each K step issues hi*hi + lo*hi + hi*lo,
@@ -105,11 +106,11 @@ __global__ void k_amax_roll(uint32_t* buf, uint32_t n) {
 constexpr uint32_t kMiscBytes = 256;  // mbarriers, TMEM holder, abort flags, FP8 scales and amax
 // Per warpgroup, shared memory: the swizzled operand tiles (1024-byte
 // aligned; H, and the E4M3 A tile of FP8 mode or the H remainder of split
-// BF16), then apart from them the reduction arrays: row contributions (128 x
-// 8 floats), finished pixel sums (128 x 10 words) and two carry slots.
-constexpr uint32_t kSmallStride = 9728;
-constexpr uint32_t kOffRows = 0, kOffFin = 4096, kOffCarry = 9216;  // rows 128 x 32 B | 128 pixels x 40 B | carry
-constexpr uint32_t kFinWords = 10;                                  // 7 sums + pad + 64-bit signature
+// BF16), then apart from them the reduction arrays: row contributions of two
+// tiles (2 x 128 x 8 floats: a tile's sums are formed while the next tile's
+// first MMA runs) and two carry slots.
+constexpr uint32_t kSmallStride = 8192 + 256;
+constexpr uint32_t kOffRows = 0, kOffCarry = 8192;  // two row buffers (128 x 32 B each) | carry slots
 // Per warpgroup, tensor memory columns: D (64) | A (32) | A remainder (32, split BF16).
 constexpr uint32_t kTmD = 0, kTmA = 64, kTmLo = 96;
 
@@ -517,9 +518,8 @@ __global__ void __launch_bounds__(640, 1)
     const uint32_t id64 = tc::idesc_f16(AB16, 128, 64), id16 = tc::idesc_f16(AB16, 128, 16);
     const uint32_t id64_e4m3 = tc::idesc_f16(0, 128, 64);  // E4M3 x E4M3 has type code 0 too
     const uint16_t one16 = AB16 ? 0x3F80u : 0x3C00u;
-    float* s_rows = reinterpret_cast<float*>(wgg + kOffRows);    // [128][8] contributions of the tile's rows
-    uint32_t* s_fin = reinterpret_cast<uint32_t*>(wgg + kOffFin);  // [128][kFinWords] finished pixel sums
-    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);    // 2 slots x 16 floats (sum, comp) x 7
+    float* s_rows2 = reinterpret_cast<float*>(wgg + kOffRows);   // [2][128][8] contributions of a tile's rows
+    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);  // 2 slots x 16 floats (sum, comp) x 7
     uint64_t* s_sigc = reinterpret_cast<uint64_t*>(wgg + kOffCarry + 128);  // 2 signature carry slots
 
     auto sync_wg = [&]() {
@@ -584,6 +584,91 @@ __global__ void __launch_bounds__(640, 1)
     for (uint32_t blk = (blockIdx.x - J.cta0) * n_wg + wg; blk < J.n_blocks; blk += J.n_cta * n_wg) {
         const uint32_t p0 = blk * 128u;
         const uint32_t npix = min(128u, J.P - p0);
+        // ---- per-pixel sums, part 2 (eq. L_mlmc, L_c, L_r) of tile jr (rows j0r .. j0r + 127):
+        // one lane per (pixel, channel) adds the pixel's rows of this tile in sample order with
+        // Kahan compensation, continuing the carried sum and compensation of a pixel that began
+        // in the previous tile.  Pass k takes pixels 16 k .. 16 k + 15 of the tile; pixel qi's 8
+        // channels are lanes 8 g .. 8 g + 7 of warp qi % 4 (g = (qi / 4) % 4), so a finished
+        // pixel's channel sums meet by warp shuffles and its lanes write it.
+        auto reduce_tile = [&](uint32_t jr, uint32_t j0r) {
+            const float* rows_r = s_rows2 + 1024u * (jr & 1u);
+            const uint32_t pf = div_s(j0r, J.s_magic);
+            const uint32_t plast = min(div_s(j0r + 127u, J.s_magic), npix - 1u);
+            const uint32_t n_q = plast - pf + 1u;  // pixels with rows in this tile
+            const float* cin = s_carry + 16u * (jr & 1u);    // written by the previous tile's sums
+            float* cout = s_carry + 16u * ((jr + 1u) & 1u);  // read by the next tile's sums
+            const uint32_t lane_t = t & 31u, ch = lane_t & 7u;
+            for (uint32_t k = 0; 16u * k < n_q; ++k) {
+                const uint32_t qi = 16u * k + (t >> 5) + 4u * (lane_t >> 3);
+                const bool active = qi < n_q;
+                const uint32_t q = pf + qi;
+                const uint32_t q_lo = q * S, q_hi = q_lo + S;
+                const uint32_t lo = max(q_lo, j0r), hi = min(q_hi, j0r + 128u);
+                const bool cont_in = q_lo < j0r, cont_out = q_hi > j0r + 128u;
+                // cache channels (0-2, the count 6, the signature 7) add the pixel's cache
+                // rows, residual channels (3-5) its residual rows
+                const bool resid_ch = ch >= 3u && ch < 6u;
+                const uint32_t r_lo = resid_ch ? max(q_lo + J.N, j0r) : lo;
+                const uint32_t r_hi = resid_ch ? hi : min(q_lo + J.N, hi);
+                float sum = 0.f;
+                uint64_t sig = kSigInit;
+                if (active && ch < 7u) {
+                    float comp = 0.f;
+                    if (cont_in) {
+                        sum = cin[2 * ch];
+                        comp = cin[2 * ch + 1];
+                    }
+                    const float* col = rows_r + ch;
+#pragma unroll 4
+                    for (uint32_t rr = r_lo; rr < r_hi; ++rr) {
+                        const float y = col[8u * (rr - j0r)] - comp;
+                        const float tt = sum + y;
+                        comp = (tt - sum) - y;
+                        sum = tt;
+                    }
+                    if (cont_out) {
+                        cout[2 * ch] = sum;
+                        cout[2 * ch + 1] = comp;
+                    }
+                } else if (active && sig_out) {
+                    // decision signature of the cache samples, in sample order (bit 31 of a
+                    // row's word: its pixel's record is valid)
+                    if (cont_in) sig = s_sigc[jr & 1u];
+                    for (uint32_t rr = r_lo; rr < r_hi; ++rr) {
+                        const uint32_t wd = __float_as_uint(rows_r[8u * (rr - j0r) + 7u]);
+                        if (wd >> 31) sig = sig_mix(sig, wd & 0x7FFFFFFFu);
+                    }
+                    if (cont_out) s_sigc[(jr + 1u) & 1u] = sig;
+                }
+                // colour channel c's lane takes the residual sum of channel c + 3
+                const float resid = __shfl_sync(0xffffffffu, sum, (lane_t & ~7u) | ((ch + 3u) & 7u));
+                if (!active || cont_out) continue;
+                // the finished pixel: lanes 0-2 its colour channels, 3 alpha, 6 the count, 7 the signature
+                const uint32_t gp = p0 + q;
+                if (ch < 3u) {
+                    const float* bp = base ? reinterpret_cast<const float*>(base + gp) : nullptr;
+                    const float le = bp ? bp[ch] : 0.f;
+                    float Lc = 0.f, Lr = bp ? bp[4 + ch] : 0.f;
+                    if (J.N) Lc = sum * (1.0f / (float)J.N);
+                    if (J.M && J.N) Lr -= resid * (1.0f / (float)J.M);  // without a cache level nothing is subtracted
+                    if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
+                        const float bt = reinterpret_cast<const float*>(beta + gp)[ch];
+                        Lc *= bt;
+                        Lr *= bt;
+                    }
+                    reinterpret_cast<float*>(out + gp)[ch] = le + Lc + Lr;
+                    if (lc_out) lc_out[3 * (uint64_t)gp + ch] = Lc;
+                    if (lr_out) lr_out[3 * (uint64_t)gp + ch] = Lr;
+                } else if (ch == 3u) {
+                    reinterpret_cast<float*>(out + gp)[3] = 1.f;
+                } else if (ch == 6u) {
+                    if (count) count[gp] += (uint32_t)sum;
+                } else if (ch == 7u) {
+                    if (sig_out) sig_out[2 * (uint64_t)gp + 1] = sig;
+                }
+            }
+        };
+
         // ------------------------------------------------ pixel stage
         {
             float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
@@ -789,6 +874,7 @@ __global__ void __launch_bounds__(640, 1)
                 }
                 tc::mma_commit(mbar);
             }
+            if (jt > 0) reduce_tile(jt - 1u, j0 - 128u);  // the previous tile's sums, while layer 0 runs
             wait_mma();
             for (uint32_t l = 0; l < H; ++l) {
                 // epilogue of layer l (l = 0: h_pix already holds b0; 16-bit hidden layers: the
@@ -858,111 +944,22 @@ __global__ void __launch_bounds__(640, 1)
                 rn[1] = ok ? nv.y : 0.f;
                 rn[2] = ok ? nv.z : 0.f;
             }
-            // ---- per-pixel sums (eq. L_mlmc, L_c, L_r).  Each row's contributions
-            // c_r = w_r n_r (cache rows in channels 0-2, residual rows in 3-5, 1 per
-            // valid cache sample in 6) and its signature word go to shared memory;
-            // then one thread per (pixel, channel) adds the pixel's rows of this tile
-            // in sample order with Kahan compensation, continuing the carried sum and
-            // compensation of a pixel that began in the previous tile, and one thread
-            // per pixel that ends here writes it.
+            // ---- per-pixel sums, part 1: each row's contributions c_r = w_r n_r (cache
+            // rows in channels 0-2, residual rows in 3-5, 1 per valid cache sample in 6)
+            // and its signature word go to this tile's row buffer; the sums follow while
+            // the next tile's first MMA runs (reduce_tile)
             {
                 const bool is_cache = s < J.N;
                 const float3 cw = ok ? make_float3(w.x * nv.x, w.y * nv.y, w.z * nv.z) : make_float3(0.f, 0.f, 0.f);
-                float4* sr = reinterpret_cast<float4*>(s_rows) + 2 * t;
+                float4* sr = reinterpret_cast<float4*>(s_rows2 + 1024u * (jt & 1u)) + 2 * t;
                 sr[0] = is_cache ? make_float4(cw.x, cw.y, cw.z, 0.f) : make_float4(0.f, 0.f, 0.f, cw.x);
                 sr[1] = is_cache ? make_float4(0.f, 0.f, (ok ? 1.f : 0.f), __uint_as_float(word))
                                  : make_float4(cw.y, cw.z, 0.f, __uint_as_float(word));
             }
-            tc::named_bar(bar_id, 128);
-            // Jobs: pass k takes pixels 16 k .. 16 k + 15 of the tile; pixel qi's 8 channels are
-            // lanes 8 g .. 8 g + 7 of warp qi % 4 (g = (qi / 4) % 4), so a pixel's channel sums
-            // meet in one warp and its channel-0 lane writes it after a warp barrier.
-            const uint32_t n_q = plast - pf + 1u;  // pixels with rows in this tile
-            const float* cin = s_carry + 16u * (jt & 1u);    // written by the previous tile
-            float* cout = s_carry + 16u * ((jt + 1u) & 1u);  // read by the next tile
-            const uint32_t lane_t = t & 31u, ch = lane_t & 7u;
-            for (uint32_t k = 0; 16u * k < n_q; ++k) {
-                const uint32_t qi = 16u * k + (t >> 5) + 4u * (lane_t >> 3);
-                const bool active = qi < n_q;
-                const uint32_t q = pf + qi;
-                const uint32_t q_lo = q * S, q_hi = q_lo + S;
-                const uint32_t lo = max(q_lo, j0), hi = min(q_hi, j0 + 128u);
-                const bool cont_in = q_lo < j0, cont_out = q_hi > j0 + 128u;
-                uint32_t* fs = s_fin + kFinWords * (qi & 127u);
-                if (active && ch < 7u) {
-                    float sum = cont_in ? cin[2 * ch] : 0.f, comp = cont_in ? cin[2 * ch + 1] : 0.f;
-                    const float* col = s_rows + ch;
-                    for (uint32_t rr = lo; rr < hi; ++rr) {
-                        const float y = col[8u * (rr - j0)] - comp;
-                        const float tt = sum + y;
-                        comp = (tt - sum) - y;
-                        sum = tt;
-                    }
-                    if (cont_out) {
-                        cout[2 * ch] = sum;
-                        cout[2 * ch + 1] = comp;
-                    } else {
-                        fs[ch] = __float_as_uint(sum);
-                    }
-                } else if (active && sig_out) {
-                    // decision signature of the cache samples, in sample order (bit 31 of a
-                    // row's word: its pixel's record is valid)
-                    uint64_t sig = cont_in ? s_sigc[jt & 1u] : kSigInit;
-                    const uint32_t hi_c = min(hi, q_lo + J.N);
-                    for (uint32_t rr = lo; rr < hi_c; ++rr) {
-                        const uint32_t wd = __float_as_uint(s_rows[8u * (rr - j0) + 7u]);
-                        if (wd >> 31) sig = sig_mix(sig, wd & 0x7FFFFFFFu);
-                    }
-                    if (cont_out) {
-                        s_sigc[(jt + 1u) & 1u] = sig;
-                    } else {
-                        fs[8] = (uint32_t)sig;
-                        fs[9] = (uint32_t)(sig >> 32);
-                    }
-                }
-                __syncwarp();
-                if (!active || ch != 0u || cont_out) continue;
-                const uint32_t gp = p0 + q;
-                PixelBase b;
-                if (base) {
-                    b = base[gp];
-                } else {
-                    b.le = b.wl = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                float Lc[3] = {0.f, 0.f, 0.f}, Lr[3] = {b.wl.x, b.wl.y, b.wl.z};
-                if (J.N) {
-                    const float inv = 1.0f / (float)J.N;
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) Lc[cc] = __uint_as_float(fs[cc]) * inv;
-                }
-                if (J.M && J.N) {  // without a cache level nothing is subtracted
-                    const float inv = 1.0f / (float)J.M;
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) Lr[cc] -= __uint_as_float(fs[3 + cc]) * inv;
-                }
-                if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
-                    const float4 bt = beta[gp];
-                    const float bb[3] = {bt.x, bt.y, bt.z};
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
-                        Lc[cc] *= bb[cc];
-                        Lr[cc] *= bb[cc];
-                    }
-                }
-                out[gp] = make_float4(b.le.x + Lc[0] + Lr[0], b.le.y + Lc[1] + Lr[1], b.le.z + Lc[2] + Lr[2], 1.f);
-                if (lc_out) {
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) lc_out[3 * (uint64_t)gp + cc] = Lc[cc];
-                }
-                if (lr_out) {
-#pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) lr_out[3 * (uint64_t)gp + cc] = Lr[cc];
-                }
-                if (sig_out) sig_out[2 * (uint64_t)gp + 1] = (uint64_t)fs[8] | ((uint64_t)fs[9] << 32);
-                if (count) count[gp] += (uint32_t)__uint_as_float(fs[6]);
-            }
-            // no barrier here: the next tile's barriers order the reduction arrays
         }
+        // the last tile's sums (its rows staged by every warp before this barrier)
+        tc::named_bar(bar_id, 128);
+        reduce_tile(jt - 1u, (jt - 1u) * 128u);
     }
 
     tc::fence_before_sync();
