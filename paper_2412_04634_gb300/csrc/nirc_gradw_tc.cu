@@ -6,7 +6,7 @@
 // with A = the delta rows (M = 128: rows >= out are zero) and B = the input
 // rows plus one row of ones (N = 80).  A CTA (two warpgroups) takes one
 // layer and a slice of the samples, walks it in blocks of 64 samples (a
-// 128-byte BF16 row), converting the FP32 values to BF16 into a 128-byte
+// 128-byte BF16 row), copying the stored BF16 values into a 128-byte
 // swizzled operand stage while the MMA of the previous block runs, and adds
 // its out x (in + 1) sums into the gradient with float atomics (warps 0-3,
 // which own the accumulator's TMEM lanes).  Every mbarrier wait is bounded;
@@ -26,17 +26,18 @@ constexpr uint32_t kDwB = kDwN * 128;   // 80 rows x 128 bytes
 constexpr uint32_t kDwStage = kDwA + kDwB;
 constexpr uint32_t kDwSmem = 1024 + 2 * kDwStage + 64;
 
+// Eight BF16 samples t .. t + 7 of a row (zeros past t1), packed in pairs.
 template <bool kVec>
-__device__ __forceinline__ void load8(const float* __restrict__ src, uint64_t t, uint64_t t1, float (&v)[8]) {
-    if (kVec && t + 8 <= t1) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(src + t));
-        const float4 b = __ldg(reinterpret_cast<const float4*>(src + t) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else {
+__device__ __forceinline__ uint4 load8(const uint16_t* __restrict__ src, uint64_t t, uint64_t t1) {
+    if (kVec && t + 8 <= t1) return __ldg(reinterpret_cast<const uint4*>(src + t));
+    uint32_t w[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldg(src + t + k) : 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t lo = t + 2 * k < t1 ? __ldg(src + t + 2 * k) : 0u;
+        const uint32_t hi = t + 2 * k + 1 < t1 ? __ldg(src + t + 2 * k + 1) : 0u;
+        w[k] = lo | (hi << 16);
     }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 template <bool kVec>
@@ -95,10 +96,9 @@ __global__ void __launch_bounds__(kDwThreads) k_grad_w_tc(DwJobs jobs, uint64_t 
             const uint32_t row = it >> 3, ch = it & 7u;
             const bool is_a = row < J.out;
             const uint32_t r = is_a ? row : row - J.out;
-            const float* src = is_a ? J.dl + (uint64_t)r * J.ld_dl : J.x + (uint64_t)r * J.ld_x;
-            float v[8];
-            load8<kVec>(src, tb + 8u * ch, t1, v);
-            sts_chunk8<1>(is_a ? tA : tB, r, ch, v);
+            const uint16_t* src = is_a ? J.dl + (uint64_t)r * J.ld_dl : J.x + (uint64_t)r * J.ld_x;
+            const uint4 v = load8<kVec>(src, tb + 8u * ch, t1);
+            sts_chunk(is_a ? tA : tB, r, ch, v.x, v.y, v.z, v.w);
         }
         tc::fence_proxy_async();
         tc::fence_before_sync();
@@ -156,7 +156,7 @@ cudaError_t launch_grad_w_tc(const nirc_handle* h, const DwJobs& jobs, uint64_t 
     for (uint32_t l = 0; l < jobs.n_jobs; ++l) {
         const DwJob& J = jobs.j[l];
         if (J.out == 0 || J.out > 64 || J.in == 0 || J.in + 1 > kDwN) return cudaErrorInvalidValue;
-        vec = vec && (J.ld_dl % 4 == 0) && (J.ld_x % 4 == 0) && (reinterpret_cast<uintptr_t>(J.dl) % 16 == 0) &&
+        vec = vec && (J.ld_dl % 8 == 0) && (J.ld_x % 8 == 0) && (reinterpret_cast<uintptr_t>(J.dl) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(J.x) % 16 == 0);
     }
     // about four CTAs per SM over all jobs (54 KB of shared memory each: the loads of a block

@@ -741,9 +741,17 @@ static cudaError_t train_pass(nirc_handle* h, const nirc_record* recs, const flo
             // tensor-core training: every layer's dW and db as BF16 MMAs in one launch
             DwJobs dj;
             dj.n_jobs = s.hidden + 1;
+            // the tensor-core training kernel stored these buffers as BF16: element (row, sample)
+            // of a buffer at its base + row * ld + sample, so the layers' offsets count 2-byte elements
+            const uint16_t* e16 = reinterpret_cast<const uint16_t*>(tc.e);
+            const uint16_t* act16 = reinterpret_cast<const uint16_t*>(tc.act);
+            const uint16_t* delta16 = reinterpret_cast<const uint16_t*>(tc.delta);
+            const uint16_t* dz16 = reinterpret_cast<const uint16_t*>(tc.dz);
             for (uint32_t l = 0; l <= s.hidden; ++l) {
                 const GradJob& J = jobs.j[l];
-                dj.j[l] = DwJob{J.dl, J.x, J.gw, J.ld_dl, J.ld_x, J.out, J.in};
+                const uint16_t* dl = l == s.hidden ? dz16 : delta16 + (uint64_t)l * kWidth * tc.ld;
+                const uint16_t* x = l == 0 ? e16 : act16 + (uint64_t)(l - 1) * kWidth * tc.ld;
+                dj.j[l] = DwJob{dl, x, J.gw, J.ld_dl, J.ld_x, J.out, J.in};
             }
             if ((e = launch_grad_w_tc(h, dj, m, st)) != cudaSuccess) {
                 timer_end(h, NIRC_K_TRAIN_GRADW, st);

@@ -4,6 +4,11 @@
 // hash-grid scatter, stored activations and deltas for the weight-gradient
 // GEMMs), with the layer products as MMAs.
 //
+// The stored network inputs, activations, deltas and dL/dz are BF16 (the
+// element (row, sample) of a buffer at its base + row * ld + sample, two bytes
+// each): the weight gradients take them as BF16 MMA operands, so the
+// rounding is the one those operands need anyway, at half the bytes.
+//
 // One warpgroup (128 threads; thread = training record = TMEM lane) takes a
 // tile of 128 records at a time, four warpgroups per CTA:
 //  encode    hash-grid features (FP16 copy of the table) and surface
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
         }
     };
     // Forward epilogue: + bias (layer 0 only), ReLU mask, FP32 activations out, FP16 A tile.
-    auto fwd_epilogue = [&](const float* b, float* gact, bool store, uint32_t (&mask)[2]) {
+    auto fwd_epilogue = [&](const float* b, uint16_t* gact, bool store, uint32_t (&mask)[2]) {
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
             uint32_t v[32];
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
             mask[half] = m;
             if (store) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) gact[(uint64_t)(32 * half + i) * tp.ld] = x[i];
+                for (int i = 0; i < 32; ++i) gact[(uint64_t)(32 * half + i) * tp.ld] = to16<1>(x[i]);
             }
 #pragma unroll
             for (uint32_t q = 0; q < 4; ++q) sts_chunk8<0>(tA, t, 4 * half + q, x + 8 * q);
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
     };
     // Backward epilogue: delta = mask * accumulator * 2^e_in, FP32 out, the
     // FP16 A tile scaled by 2^-e of its own row maximum (returned).
-    auto bwd_epilogue = [&](float* gdelta, bool store, const uint32_t (&mask)[2], int e_in) -> int {
+    auto bwd_epilogue = [&](uint16_t* gdelta, bool store, const uint32_t (&mask)[2], int e_in) -> int {
         const float un = pow2i(e_in);
         float m = 0.f;
 #pragma unroll
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
             for (int i = 0; i < 32; ++i) x[i] = (mask[half] >> i) & 1u ? __uint_as_float(v[i]) * un : 0.f;
             if (store) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) gdelta[(uint64_t)(32 * half + i) * tp.ld] = x[i];
+                for (int i = 0; i < 32; ++i) gdelta[(uint64_t)(32 * half + i) * tp.ld] = to16<1>(x[i]);
             }
 #pragma unroll
             for (int i = 0; i < 32; ++i) x[i] *= sc;
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
         }
         const bool valid = in && (__float_as_uint(r3.z) & 1u);
         const V3 p{r0.x, r0.y, r0.z}, nrm{r0.w, r1.x, r1.y};
-        float* ge = tp.e + sidx;
+        uint16_t* ge = reinterpret_cast<uint16_t*>(tp.e) + sidx;
         // ------------------------------------------------ encoding
         {
             float f[8];
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
                     }
                     sts_chunk8<0>(tA, t, c, f);
                     if (in)
-                        for (int q = 0; q < 8; ++q) ge[(uint64_t)(k + q) * tp.ld] = f[q];
+                        for (int q = 0; q < 8; ++q) ge[(uint64_t)(k + q) * tp.ld] = to16<1>(f[q]);
                     k += 8;
                 }
             } else {
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
                     freq4(pv[d], f);
                     sts_chunk8<0>(tA, t, c, f);
                     if (in)
-                        for (int q = 0; q < 8; ++q) ge[(uint64_t)(k + q) * tp.ld] = f[q];
+                        for (int q = 0; q < 8; ++q) ge[(uint64_t)(k + q) * tp.ld] = to16<1>(f[q]);
                     k += 8;
                 }
             }
@@ -304,14 +309,14 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
                 sts_chunk8<0>(tA, t, c++, ph);
                 sts_chunk8<0>(tA, t, c++, ph + 8);
                 if (in)
-                    for (uint32_t q = 0; q < kPhiFeatures; ++q) ge[(uint64_t)(ks + q) * tp.ld] = ph[q];
+                    for (uint32_t q = 0; q < kPhiFeatures; ++q) ge[(uint64_t)(ks + q) * tp.ld] = to16<1>(ph[q]);
             } else {
                 const float nv[3] = {nrm.x, nrm.y, nrm.z};
                 for (int d = 0; d < 3; ++d, ++c) {
                     freq4(nv[d], f);
                     sts_chunk8<0>(tA, t, c, f);
                     if (in)
-                        for (int q = 0; q < 8; ++q) ge[(uint64_t)(ks + 8 * d + q) * tp.ld] = f[q];
+                        for (int q = 0; q < 8; ++q) ge[(uint64_t)(ks + 8 * d + q) * tp.ld] = to16<1>(f[q]);
                 }
             }
             for (; c < 8; ++c) sts_chunk(tA, t, c, 0u, 0u, 0u, 0u);
@@ -330,19 +335,21 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
 #pragma unroll
             for (uint32_t q = 0; q < (kSh ? 4u : 2u); ++q) sts_chunk8<0>(tD, t, q, e + 8 * q);
             if (in)
-                for (uint32_t q = 0; q < n_dir; ++q) ge[(uint64_t)(a.s.n_pos + q) * tp.ld] = e[q];
+                for (uint32_t q = 0; q < n_dir; ++q) ge[(uint64_t)(a.s.n_pos + q) * tp.ld] = to16<1>(e[q]);
         }
         // ------------------------------------------------ forward
         uint32_t mask[kMaxHidden][2];
         sync_wg();
         issue(tA, sbase + tcimg::off_w0pix(), id64, -1, tD, sbase + tcimg::off_w0dir(), kSh ? 2u : 1u);
         wait_mma();
-        fwd_epilogue(bias, tp.act + sidx, in, mask[0]);
+        uint16_t* const act16 = reinterpret_cast<uint16_t*>(tp.act);
+        uint16_t* const delta16 = reinterpret_cast<uint16_t*>(tp.delta);
+        fwd_epilogue(bias, act16 + sidx, in, mask[0]);
         for (uint32_t l = 1; l < H; ++l) {
             sync_wg();
             issue(tA, sbase + tcimg::off_wh(l - 1), id64, (int)(l - 1), 0u, 0u, 0u);
             wait_mma();
-            fwd_epilogue(nullptr, tp.act + (uint64_t)l * 64 * tp.ld + sidx, in, mask[l]);
+            fwd_epilogue(nullptr, act16 + (uint64_t)l * 64 * tp.ld + sidx, in, mask[l]);
         }
         sync_wg();
         issue(tA, sbase + tcimg::off_wout(H), id16, (int)(H - 1), 0u, 0u, 0u);
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
                         dz[c] = -2.f * diff / den * a.scale * dact;
                     }
                 }
-                if (in) tp.dz[(uint64_t)c * tp.dz_ld + sidx] = dz[c];
+                if (in) reinterpret_cast<uint16_t*>(tp.dz)[(uint64_t)c * tp.dz_ld + sidx] = to16<1>(dz[c]);
             }
         }
         // ------------------------------------------------ backward
@@ -390,7 +397,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
             for (uint32_t u = 0; u < 64; ++u) m = fmaxf(m, fabsf(delta_out(u)));
             ex = row_exp(m);
             const float sc = pow2i(-ex);
-            float* gd = tp.delta + (uint64_t)(H - 1) * 64 * tp.ld + sidx;
+            uint16_t* gd = delta16 + (uint64_t)(H - 1) * 64 * tp.ld + sidx;
 #pragma unroll
             for (uint32_t half = 0; half < 2; ++half) {
                 float x[32];
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
                 for (int i = 0; i < 32; ++i) x[i] = delta_out(32 * half + i);
                 if (in) {
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) gd[(uint64_t)(32 * half + i) * tp.ld] = x[i];
+                    for (int i = 0; i < 32; ++i) gd[(uint64_t)(32 * half + i) * tp.ld] = to16<1>(x[i]);
                 }
 #pragma unroll
                 for (int i = 0; i < 32; ++i) x[i] *= sc;
@@ -411,7 +418,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
             sync_wg();
             issue(tA, sbase + trimg::off_wht(H, l - 1), id64, -1, 0u, 0u, 0u);
             wait_mma();
-            ex = bwd_epilogue(tp.delta + (uint64_t)(l - 1) * 64 * tp.ld + sidx, in, mask[l - 1], ex);
+            ex = bwd_epilogue(delta16 + (uint64_t)(l - 1) * 64 * tp.ld + sidx, in, mask[l - 1], ex);
         }
         if (a.s.hashgrid) {
             // dL/de of the position features: W0_pos^T delta_0 (N = 32), scattered like the FP32 backward
