@@ -47,15 +47,19 @@ typedef enum nirc_status {
     NIRC_ERR_UNSUPPORTED = 6  /* configuration not implemented on this path */
 } nirc_status;
 
-/* Arithmetic of the network layers.  FP32_SIMT: plain FP32 FMA kernels.
- * FP16_TC / BF16_TC: tcgen05 tensor-core MMAs with FP16 / BF16 operands and
- * FP32 accumulation in tensor memory.  FP8_E4M3_TC: the hidden 64x64 layers
+/* Arithmetic of the network layers (section "Neural Network Architecture").
+ * FP32_SIMT: plain FP32 FMA kernels.  FP16_TC: tcgen05 tensor-core MMAs with
+ * FP16 operands and FP32 accumulation in tensor memory.  BF16_TC: the same
+ * with every operand carried as two BF16 values, hi = bf16(x) and lo =
+ * bf16(x - hi), and each product formed as hi*hi + lo*hi + hi*lo (about 16
+ * significant bits, three MMAs per product; BF16's own 8 bits do not meet
+ * 2e-2 on n = exp(z) for trained logits).  FP8_E4M3_TC: the hidden 64x64 layers
  * take E4M3 operands (kind::f8f6f4) with per-layer scales, weights scaled
  * by amax|W| / 448 and activations by the amax of the previous launch / 448
  * (delayed scaling; the first launch after new weights or a precision change
  * runs one extra FP16 pass to measure it), FP32 accumulation; the first
  * layer and the output layer stay FP16.  Encodings, sampling, pdfs and the
- * per-pixel sums are FP32 in every mode. */
+ * Kahan-compensated per-pixel sums are FP32 in every mode. */
 typedef enum nirc_precision {
     NIRC_FP32_SIMT = 0,
     NIRC_FP16_TC = 1,
