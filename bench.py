@@ -459,7 +459,6 @@ def recorded_traffic(args, precision):
     """DRAM bytes per launch of the cache kernel from the committed ncu
     record, or None when the record is for another workload or precision,
     or the kernel's sources have changed since the counters were taken."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"k_cache_tc_{precision}_1080p.traffic.txt")
     if not os.path.exists(path) or (args.width, args.height, args.n_cache, args.n_resid) != (1920, 1080, 16, 1) \
             or args.input != "freq":
@@ -471,16 +470,29 @@ def recorded_traffic(args, precision):
         elif ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             rec[k.strip()] = v.strip()
-    h = hashlib.sha256()
     try:
-        for sp in srcs:
-            with open(os.path.join(ROOT, sp), "rb") as f:
-                h.update(f.read())
+        digest = code_sha256(srcs)
     except OSError:
         return None
-    if not srcs or h.hexdigest() != rec.get("sources_sha256"):
+    if not srcs or digest != rec.get("sources_sha256"):
         return None
     return int(rec["dram_bytes_per_launch"])
+
+
+def code_sha256(paths):
+    """SHA-256 of C/CUDA sources with comments and blank space removed, so a
+    documentation edit keeps a counter record valid and a code edit voids it."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for sp in paths:
+        with open(os.path.join(ROOT, sp), encoding="utf-8") as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+        h.update(b"\0")
+    return h.hexdigest()
 
 
 def _roofline(args, cfg, props, kernel_ms, dominant, sm_max, window_s):
