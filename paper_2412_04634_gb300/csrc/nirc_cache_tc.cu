@@ -30,12 +30,13 @@
 //                next A row back to TMEM.  The network input and output never
 //                touch global memory.
 //  reduction     per-row contributions w * n go to shared memory in row
-//                order; per pixel and channel one lane adds its rows in
-//                sample order with Kahan compensation (eq. L_mlmc = L_e + L_c
-//                + L_r), carrying the running sum and compensation of a pixel
-//                that straddles two tiles; a pixel's channels are lanes of one
-//                warp, which write the finished pixel.  A tile's sums are
-//                formed while the next tile's layer-0 MMA runs.
+//                order; per pixel and pair of channels one lane adds its rows
+//                in sample order with Kahan compensation (eq. L_mlmc = L_e +
+//                L_c + L_r; packed FP32 pairs), carrying the running sums and
+//                compensations of a pixel that straddles two tiles; a pixel's
+//                four lanes are lanes of one warp, which write the finished
+//                pixel.  A tile's sums are formed while the next tile's
+//                layer-0 MMA runs.
 //
 // Split BF16 (NIRC_BF16_TC): every 16-bit operand x is carried as hi =
 // bf16(x) and lo = bf16(x - hi); each K step issues hi*hi + lo*hi + hi*lo,
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(640, 1)
     const uint32_t id64_e4m3 = tc::idesc_f16(0, 128, 64);  // E4M3 x E4M3 has type code 0 too
     const uint16_t one16 = AB16 ? 0x3F80u : 0x3C00u;
     float* s_rows2 = reinterpret_cast<float*>(wgg + kOffRows);   // [2][128][8] contributions of a tile's rows
-    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);  // 2 slots x 16 floats (sum, comp) x 7
+    float* s_carry = reinterpret_cast<float*>(wgg + kOffCarry);  // 2 slots x 4 lanes x (sum, comp) pairs
     uint64_t* s_sigc = reinterpret_cast<uint64_t*>(wgg + kOffCarry + 128);  // 2 signature carry slots
 
     auto sync_wg = [&]() {
@@ -585,86 +586,101 @@ __global__ void __launch_bounds__(640, 1)
         const uint32_t p0 = blk * 128u;
         const uint32_t npix = min(128u, J.P - p0);
         // ---- per-pixel sums, part 2 (eq. L_mlmc, L_c, L_r) of tile jr (rows j0r .. j0r + 127):
-        // one lane per (pixel, channel) adds the pixel's rows of this tile in sample order with
-        // Kahan compensation, continuing the carried sum and compensation of a pixel that began
-        // in the previous tile.  Pass k takes pixels 16 k .. 16 k + 15 of the tile; pixel qi's 8
-        // channels are lanes 8 g .. 8 g + 7 of warp qi % 4 (g = (qi / 4) % 4), so a finished
-        // pixel's channel sums meet by warp shuffles and its lanes write it.
+        // four lanes per pixel, each adding a pair of the row buffer's channels over the pixel's
+        // rows of this tile in sample order with Kahan compensation (packed FP32 pairs),
+        // continuing the carried sums and compensations of a pixel that began in the previous
+        // tile: lane g = 0 the cache colours 0 and 1, g = 1 the cache colour 2 and the count
+        // (cache rows), g = 2 the residual colours 0 and 1, g = 3 the residual colour 2
+        // (residual rows; the other half of its pair is the signature word, summed and
+        // dropped).  Pass k takes pixels 32 k .. 32 k + 31 of the tile: pixel qi is lanes
+        // 4 (qi % 8) .. 4 (qi % 8) + 3 of warp (qi / 8 + jr) % 4, so a tile of S >= 16 rows per
+        // pixel keeps one or two warps busy and the others skip the pass; the busy warp, and
+        // with it the scheduler, rotates from tile to tile.  A finished pixel's residual sums
+        // reach its cache lanes by warp shuffles and lanes 0 and 1 write it.
         auto reduce_tile = [&](uint32_t jr, uint32_t j0r) {
             const float* rows_r = s_rows2 + 1024u * (jr & 1u);
             const uint32_t pf = div_s(j0r, J.s_magic);
             const uint32_t plast = min(div_s(j0r + 127u, J.s_magic), npix - 1u);
             const uint32_t n_q = plast - pf + 1u;  // pixels with rows in this tile
-            const float* cin = s_carry + 16u * (jr & 1u);    // written by the previous tile's sums
-            float* cout = s_carry + 16u * ((jr + 1u) & 1u);  // read by the next tile's sums
-            const uint32_t lane_t = t & 31u, ch = lane_t & 7u;
-            for (uint32_t k = 0; 16u * k < n_q; ++k) {
-                const uint32_t qi = 16u * k + (t >> 5) + 4u * (lane_t >> 3);
+            const float4* cin = reinterpret_cast<const float4*>(s_carry + 16u * (jr & 1u));  // previous tile's
+            float4* cout = reinterpret_cast<float4*>(s_carry + 16u * ((jr + 1u) & 1u));     // next tile's
+            const uint32_t lane_t = t & 31u, g = lane_t & 3u;
+            const uint32_t wq = ((t >> 5) - jr) & 3u;  // this warp's pixel octet in a pass
+            for (uint32_t k = 0; 32u * k < n_q; ++k) {
+                if (32u * k + 8u * wq >= n_q) continue;  // warp-uniform: no pixel of this warp in the pass
+                const uint32_t qi = 32u * k + 8u * wq + (lane_t >> 2);
                 const bool active = qi < n_q;
                 const uint32_t q = pf + qi;
                 const uint32_t q_lo = q * S, q_hi = q_lo + S;
                 const uint32_t lo = max(q_lo, j0r), hi = min(q_hi, j0r + 128u);
                 const bool cont_in = q_lo < j0r, cont_out = q_hi > j0r + 128u;
-                // cache channels (0-2, the count 6, the signature 7) add the pixel's cache
-                // rows, residual channels (3-5) its residual rows
-                const bool resid_ch = ch >= 3u && ch < 6u;
-                const uint32_t r_lo = resid_ch ? max(q_lo + J.N, j0r) : lo;
-                const uint32_t r_hi = resid_ch ? hi : min(q_lo + J.N, hi);
-                float sum = 0.f;
-                uint64_t sig = kSigInit;
-                if (active && ch < 7u) {
-                    float comp = 0.f;
+                const uint32_t r_lo = g >= 2u ? max(q_lo + J.N, j0r) : lo;
+                const uint32_t r_hi = g >= 2u ? hi : min(q_lo + J.N, hi);
+                float2 sum = make_float2(0.f, 0.f), comp = sum;  // comp: what the next add must restore
+                if (active) {
                     if (cont_in) {
-                        sum = cin[2 * ch];
-                        comp = cin[2 * ch + 1];
+                        const float4 c = cin[g];
+                        sum = make_float2(c.x, c.y);
+                        comp = make_float2(c.z, c.w);
                     }
-                    const float* col = rows_r + ch;
+                    const float2* col = reinterpret_cast<const float2*>(rows_r) + g;
 #pragma unroll 4
                     for (uint32_t rr = r_lo; rr < r_hi; ++rr) {
-                        const float y = col[8u * (rr - j0r)] - comp;
-                        const float tt = sum + y;
-                        comp = (tt - sum) - y;
+                        const float2 y = __fadd2_rn(col[4u * (rr - j0r)], comp);
+                        const float2 tt = __fadd2_rn(sum, y);
+                        comp = __fadd2_rn(__ffma2_rn(tt, make_float2(-1.f, -1.f), sum), y);  // (sum - tt) + y
                         sum = tt;
                     }
-                    if (cont_out) {
-                        cout[2 * ch] = sum;
-                        cout[2 * ch + 1] = comp;
-                    }
-                } else if (active && sig_out) {
+                    if (cont_out) cout[g] = make_float4(sum.x, sum.y, comp.x, comp.y);
+                }
+                uint64_t sig = kSigInit;
+                if (sig_out && active && g == 3u) {
                     // decision signature of the cache samples, in sample order (bit 31 of a
                     // row's word: its pixel's record is valid)
                     if (cont_in) sig = s_sigc[jr & 1u];
-                    for (uint32_t rr = r_lo; rr < r_hi; ++rr) {
+                    const uint32_t c_lo = lo, c_hi = min(q_lo + J.N, hi);
+                    for (uint32_t rr = c_lo; rr < c_hi; ++rr) {
                         const uint32_t wd = __float_as_uint(rows_r[8u * (rr - j0r) + 7u]);
                         if (wd >> 31) sig = sig_mix(sig, wd & 0x7FFFFFFFu);
                     }
                     if (cont_out) s_sigc[(jr + 1u) & 1u] = sig;
                 }
-                // colour channel c's lane takes the residual sum of channel c + 3
-                const float resid = __shfl_sync(0xffffffffu, sum, (lane_t & ~7u) | ((ch + 3u) & 7u));
+                // cache lane g (0, 1) takes the residual pair of lane g + 2
+                const float rx = __shfl_down_sync(0xffffffffu, sum.x, 2);
+                const float ry = __shfl_down_sync(0xffffffffu, sum.y, 2);
                 if (!active || cont_out) continue;
-                // the finished pixel: lanes 0-2 its colour channels, 3 alpha, 6 the count, 7 the signature
                 const uint32_t gp = p0 + q;
-                if (ch < 3u) {
+                if (g < 2u) {
+                    // the finished pixel: lane 0 colour channels 0 and 1, lane 1 channel 2, alpha and the count
                     const float* bp = base ? reinterpret_cast<const float*>(base + gp) : nullptr;
-                    const float le = bp ? bp[ch] : 0.f;
-                    float Lc = 0.f, Lr = bp ? bp[4 + ch] : 0.f;
-                    if (J.N) Lc = sum * (1.0f / (float)J.N);
-                    if (J.M && J.N) Lr -= resid * (1.0f / (float)J.M);  // without a cache level nothing is subtracted
-                    if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
-                        const float bt = reinterpret_cast<const float*>(beta + gp)[ch];
-                        Lc *= bt;
-                        Lr *= bt;
+                    const uint32_t c0 = 2u * g;
+                    float2 Lc = make_float2(0.f, 0.f);
+                    if (J.N) Lc = make_float2(sum.x * (1.0f / (float)J.N), g ? 0.f : sum.y * (1.0f / (float)J.N));
+                    float2 Lr = bp ? make_float2(bp[4 + c0], g ? 0.f : bp[5]) : make_float2(0.f, 0.f);
+                    if (J.M && J.N) {  // without a cache level nothing is subtracted
+                        Lr.x -= rx * (1.0f / (float)J.M);
+                        if (!g) Lr.y -= ry * (1.0f / (float)J.M);
                     }
-                    reinterpret_cast<float*>(out + gp)[ch] = le + Lc + Lr;
-                    if (lc_out) lc_out[3 * (uint64_t)gp + ch] = Lc;
-                    if (lr_out) lr_out[3 * (uint64_t)gp + ch] = Lr;
-                } else if (ch == 3u) {
-                    reinterpret_cast<float*>(out + gp)[3] = 1.f;
-                } else if (ch == 6u) {
-                    if (count) count[gp] += (uint32_t)sum;
-                } else if (ch == 7u) {
-                    if (sig_out) sig_out[2 * (uint64_t)gp + 1] = sig;
+                    if (beta) {  // the unit's throughput (biased stopping vertex, later vertex of a residual path)
+                        const float* bt = reinterpret_cast<const float*>(beta + gp);
+                        const float b0 = bt[c0], b1 = g ? 0.f : bt[1];
+                        Lc = make_float2(Lc.x * b0, Lc.y * b1);
+                        Lr = make_float2(Lr.x * b0, Lr.y * b1);
+                    }
+                    const float2 le = bp ? make_float2(bp[c0], g ? 0.f : bp[1]) : make_float2(0.f, 0.f);
+                    const float2 o = make_float2(le.x + Lc.x + Lr.x, g ? 1.f : le.y + Lc.y + Lr.y);
+                    reinterpret_cast<float2*>(out + gp)[g] = o;
+                    if (lc_out) {
+                        lc_out[3 * (uint64_t)gp + c0] = Lc.x;
+                        if (!g) lc_out[3 * (uint64_t)gp + 1] = Lc.y;
+                    }
+                    if (lr_out) {
+                        lr_out[3 * (uint64_t)gp + c0] = Lr.x;
+                        if (!g) lr_out[3 * (uint64_t)gp + 1] = Lr.y;
+                    }
+                    if (g && count) count[gp] += (uint32_t)sum.y;
+                } else if (g == 3u && sig_out) {
+                    sig_out[2 * (uint64_t)gp + 1] = sig;
                 }
             }
         };
@@ -945,16 +961,16 @@ __global__ void __launch_bounds__(640, 1)
                 rn[2] = ok ? nv.z : 0.f;
             }
             // ---- per-pixel sums, part 1: each row's contributions c_r = w_r n_r (cache
-            // rows in channels 0-2, residual rows in 3-5, 1 per valid cache sample in 6)
-            // and its signature word go to this tile's row buffer; the sums follow while
+            // rows in channels 0-2 with 1 per valid cache sample in 3, residual rows in 4-6)
+            // and its signature word (7) go to this tile's row buffer; the sums follow while
             // the next tile's first MMA runs (reduce_tile)
             {
                 const bool is_cache = s < J.N;
                 const float3 cw = ok ? make_float3(w.x * nv.x, w.y * nv.y, w.z * nv.z) : make_float3(0.f, 0.f, 0.f);
                 float4* sr = reinterpret_cast<float4*>(s_rows2 + 1024u * (jt & 1u)) + 2 * t;
-                sr[0] = is_cache ? make_float4(cw.x, cw.y, cw.z, 0.f) : make_float4(0.f, 0.f, 0.f, cw.x);
-                sr[1] = is_cache ? make_float4(0.f, 0.f, (ok ? 1.f : 0.f), __uint_as_float(word))
-                                 : make_float4(cw.y, cw.z, 0.f, __uint_as_float(word));
+                sr[0] = is_cache ? make_float4(cw.x, cw.y, cw.z, (ok ? 1.f : 0.f)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                sr[1] = is_cache ? make_float4(0.f, 0.f, 0.f, __uint_as_float(word))
+                                 : make_float4(cw.x, cw.y, cw.z, __uint_as_float(word));
             }
         }
         // the last tile's sums (its rows staged by every warp before this barrier)
