@@ -17,13 +17,15 @@
 //                position features + normal features) into A; one
 //                128x64x64 MMA with the surface columns of layer 0 gives
 //                h_pix = W0[:, pix] e_pix + b0 for the 128 pixels, stored as a
-//                16-bit K-major operand H in shared memory (K = pixel index).
+//                16-bit K-major operand H in shared memory (K = pixel index;
+//                no swizzling, so a K step starts at any multiple of 8 pixels).
 //                This is the paper's shared per-surface encoding: computed
 //                once per shading point and reused by all its N + M rows.
 //  row tile      thread t samples its row's direction (cache rows) or reads
 //                it (residual rows), encodes it and writes its A row
-//                [e_dir (16) | one-hot of its pixel within a 48-wide window];
-//                layer 0 = W0_dir e_dir + H onehot (1 + up to 3 MMAs, K = 16
+//                [e_dir (16) | one-hot of its pixel within a window of the
+//                tile's pixels, 16 columns for S >= 16, up to 48 for S >= 4];
+//                layer 0 = W0_dir e_dir + H onehot (1 + 1..3 MMAs, K = 16
 //                each), then the hidden layers (4 MMAs and a bias MMA each)
 //                and the output layer (N = 16, 3 used); each epilogue reads its
 //                row from TMEM, applies ReLU, rounds to 16 bits and writes the
@@ -779,8 +781,10 @@ __global__ void __launch_bounds__(640, 1)
                 }
             }
         } else {
-            // H operand: element (n = output unit, k = pixel t), h = accumulator + b0 (+ remainder)
-            const uint32_t hk = (t >> 6) * 8192u;
+            // H operand: element (n = output unit, k = pixel t), h = accumulator + b0 (+ remainder),
+            // K-major without swizzling: core matrix (n / 8, t / 8) at (n / 8) * 2048 + (t / 8) * 128,
+            // so a K step may start at any multiple of 8 pixels
+            const uint32_t hk = (t >> 3) * 128u + (t & 7u) * 2u;
 #pragma unroll
             for (uint32_t half = 0; half < 2; ++half) {
                 uint32_t v[32];
@@ -791,10 +795,11 @@ __global__ void __launch_bounds__(640, 1)
                     const uint32_t oo = 32u * half + o;
                     const float hv = __uint_as_float(v[o]) + bias[oo];
                     const uint16_t hb = to16<AB16>(hv);
-                    tc::sts16(tH + hk + tc::sw128_offset(oo, t & 63u), hb);
+                    const uint32_t off = hk + (oo >> 3) * 2048u + (oo & 7u) * 16u;
+                    tc::sts16(tH + off, hb);
                     if constexpr (kSplit) {
                         const float rest = hv - __uint_as_float((uint32_t)hb << 16);
-                        tc::sts16(tHlo + hk + tc::sw128_offset(oo, t & 63u), to16<1>(rest));
+                        tc::sts16(tHlo + off, to16<1>(rest));
                     }
                 }
             }
@@ -812,9 +817,10 @@ __global__ void __launch_bounds__(640, 1)
             const uint32_t s = rin ? r - pl * S : 0u;
             const uint32_t pf = div_s(j0, J.s_magic);
             const uint32_t plast = min(div_s(min(j0 + 127u, R_full - 1u), J.s_magic), npix - 1u);
-            // one-hot window [kb, kb + 16 n_oh) covers pixels pf..plast and stays inside H's 128 columns
-            const uint32_t n_oh = (plast - (pf & ~15u) + 16u) >> 4;  // <= 3 for S >= 4
-            const uint32_t kb = min(pf & ~15u, 128u - 16u * n_oh);
+            // one-hot window [kb, kb + 16 n_oh) covers pixels pf..plast and stays inside H's 128
+            // columns (1 K step for S >= 16, at most 3 for S >= 4)
+            const uint32_t n_oh = (plast - (pf & ~7u) + 16u) >> 4;
+            const uint32_t kb = min(pf & ~7u, 128u - 16u * n_oh);
 
             V3 wi{0.f, 0.f, 1.f};
             float3 w = make_float3(0.f, 0.f, 0.f);
@@ -861,17 +867,16 @@ __global__ void __launch_bounds__(640, 1)
                 dir_features_fast(wi, e);
                 put_chunk(0u, e);
                 put_chunk(1u, e + 8);
-                // one-hot of the row's pixel among K columns 16..63 (words 8..31 of the row)
+                // one-hot of the row's pixel among K columns 16 .. 16 + 16 n_oh (words 8 .. 8 + 8 n_oh
+                // of the row; the MMAs read no further)
                 const uint32_t oh = rin ? pl - kb : 0xFFFFu;
                 const uint32_t ow = oh >> 1, ov = (uint32_t)one16 << ((oh & 1u) * 16u);
-                uint32_t d[16];
+                for (uint32_t qq = 0; qq < n_oh; ++qq) {  // uniform over the warpgroup
+                    uint32_t d8[8];
 #pragma unroll
-                for (uint32_t j = 0; j < 16; ++j) d[j] = ow == j ? ov : 0u;
-                tc::tmem_st16(tAr + 8u, d);
-                uint32_t d8[8];
-#pragma unroll
-                for (uint32_t j = 0; j < 8; ++j) d8[j] = ow == 16u + j ? ov : 0u;
-                tc::tmem_st8(tAr + 24u, d8);
+                    for (uint32_t j = 0; j < 8; ++j) d8[j] = ow == 8u * qq + j ? ov : 0u;
+                    tc::tmem_st8(tAr + 8u + 8u * qq, d8);
+                }
             }
             tc::tmem_wait_st();
             sync_wg();
@@ -882,10 +887,10 @@ __global__ void __launch_bounds__(640, 1)
                 } else {
                     mma_ta(0u, w0dir, id64, 1u, false);
                     for (uint32_t qq = 1; qq <= n_oh; ++qq) {
-                        const uint32_t kk = kb + 16u * (qq - 1);
-                        const uint32_t hoff = (kk >> 6) * 8192u + (kk & 63u) * 2u;
-                        tc::mma_f16_ta(tmD, tmA + 8u * qq, tc::sdesc(tH + hoff), id64, 1);
-                        if constexpr (kSplit) tc::mma_f16_ta(tmD, tmA + 8u * qq, tc::sdesc(tHlo + hoff), id64, 1);
+                        const uint32_t hoff = ((kb >> 3) + 2u * (qq - 1)) * 128u;  // K = kb + 16 (qq - 1)
+                        tc::mma_f16_ta(tmD, tmA + 8u * qq, tc::sdesc_noswz(tH + hoff, 128u, 2048u), id64, 1);
+                        if constexpr (kSplit)
+                            tc::mma_f16_ta(tmD, tmA + 8u * qq, tc::sdesc_noswz(tHlo + hoff, 128u, 2048u), id64, 1);
                     }
                 }
                 tc::mma_commit(mbar);
@@ -944,9 +949,9 @@ __global__ void __launch_bounds__(640, 1)
                 tc::tmem_ld4(tDr, v);
                 tc::tmem_wait_ld();
                 const bool vis = a.s.vis;  // the output bias came with the MMA
-                nv.x = out_act(vis, __uint_as_float(v[0]), a.z_clamp);
-                nv.y = out_act(vis, __uint_as_float(v[1]), a.z_clamp);
-                nv.z = out_act(vis, __uint_as_float(v[2]), a.z_clamp);
+                nv.x = out_act_fast(vis, __uint_as_float(v[0]), a.z_clamp);
+                nv.y = out_act_fast(vis, __uint_as_float(v[1]), a.z_clamp);
+                nv.z = out_act_fast(vis, __uint_as_float(v[2]), a.z_clamp);
                 if (J.env_hd && ok) {  // visibility cache: n = V L_env(w)
                     const float3 le = env_radiance(env_from(J.env_hd, J.env_nprims), wi);
                     nv.x *= le.x;

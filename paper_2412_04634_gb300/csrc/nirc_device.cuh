@@ -661,6 +661,12 @@ __device__ __forceinline__ EnvMap env_from(const SceneHeader* hd, uint32_t n_pri
 __device__ __forceinline__ float out_act(bool vis, float z, float z_clamp) {
     return vis ? 1.0f / (1.0f + expf(-z)) : expf(fminf(z, z_clamp));
 }
+// The same with the hardware exponential (relative error about 2^-22 + |z| 2^-24,
+// results below 2^-126 flushed to zero), for the tensor-core paths, whose
+// 16-bit activations dominate their error.
+__device__ __forceinline__ float out_act_fast(bool vis, float z, float z_clamp) {
+    return vis ? 1.0f / (1.0f + __expf(-z)) : __expf(fminf(z, z_clamp));
+}
 
 // Hash-grid level description (precomputed on the host).
 struct GridLevel {

@@ -54,6 +54,20 @@ __device__ __forceinline__ uint64_t sdesc_rep8(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory matrix descriptor without swizzling, K-major: 8-row x 16-byte
+// core matrices stored as 128 contiguous bytes, the next core matrix along K
+// `lbo` bytes further and the next 8-row group `sbo` bytes further.  The start
+// may sit on any 16-byte core-matrix boundary (K offsets in steps of 8
+// 16-bit elements).
+__device__ __forceinline__ uint64_t sdesc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;  // descriptor version; swizzle mode 0 (none)
+    return d;
+}
+
 // Instruction descriptor of kind::f16: FP32 accumulate, A/B type (0 = f16,
 // 1 = bf16), both K-major, M x N.
 __device__ __forceinline__ uint32_t idesc_f16(uint32_t ab_type, uint32_t M, uint32_t N) {
