@@ -6,10 +6,13 @@
 // node of a hierarchy.  The others get a binary radix tree: conservative
 // AABBs, 30-bit Morton codes of the centroids made unique with the primitive
 // index, a bitonic sort, the topology of Karras (HPG 2012), then boxes
-// bottom-up.  A query tests the large list, then walks the tree in near-first
-// order with a short stack, entering a child box only when a ray could hit
-// it no later than the best hit so far (with slack).  Primitives are tested
-// with the same strict binary32 routines as the brute-force loop, keeping the
+// bottom-up.  Each internal node stores the boxes of its two children (64
+// bytes: one visit is four 16-byte shared loads), a leaf child being one
+// primitive.  A query tests the large list, then walks the tree in near-first
+// order with a stack, testing a leaf child's primitive as soon as its box is
+// hit and entering an internal child only when a ray could hit its box no
+// later than the best hit so far (with slack).  Primitives are tested with
+// the same strict binary32 routines as the brute-force loop, keeping the
 // smallest (t, primitive index): boxes are expanded and pruning is
 // conservative, so the result equals the brute-force nearest hit exactly.
 #pragma once
@@ -18,14 +21,12 @@
 
 namespace nirc {
 
-struct __align__(16) BvhNode {
-    float4 lo;  // xyz = box min, w = left child (bits; bit 31 set = leaf, low bits = primitive)
-    float4 hi;  // xyz = box max, w = right child
-};
-
+// Internal node i of the tree is 4 float4 at nodes[4 i]: child 0's box (min
+// xyz | child 0 bits in w, max xyz | child 1 bits in w), then child 1's box
+// (min xyz, max xyz).  Child bits: bit 31 set = leaf, low bits = primitive;
+// otherwise the internal node's index.
 struct Bvh {
-    const BvhNode* nodes;
-    const float4* boxes;    // conservative primitive boxes (lo, hi per primitive)
+    const float4* nodes;
     const uint32_t* large;  // primitives tested by brute force
     uint32_t n_large;
     uint32_t n_tree;        // leaves of the tree
@@ -39,7 +40,7 @@ constexpr int kBvhStack = 64;  // >= tree depth (at most 62 for 64-bit unique ke
 __host__ __device__ inline size_t bvh_smem_bytes(uint32_t n) {
     uint32_t np2 = 1;
     while (np2 < n) np2 <<= 1;
-    return (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode) + (size_t)np2 * 8 + (size_t)n * 32 + (size_t)n * 4 * 2 + 16;
+    return (size_t)(n > 1 ? n - 1 : 1) * 64 + (size_t)np2 * 8 + (size_t)n * 32 + (size_t)n * 4 * 3 + 16;
 }
 
 __device__ __forceinline__ uint32_t expand_bits10(uint32_t v) {
@@ -59,8 +60,9 @@ __device__ __forceinline__ int lcp_delta(const unsigned long long* keys, int n, 
 __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, unsigned char* mem) {
     uint32_t np2 = 1;
     while (np2 < n) np2 <<= 1;
-    BvhNode* nodes = reinterpret_cast<BvhNode*>(mem);
-    unsigned char* p = mem + (size_t)(n > 1 ? n - 1 : 1) * sizeof(BvhNode);
+    float4* nodes = reinterpret_cast<float4*>(mem);
+    float* nodef = reinterpret_cast<float*>(mem);  // the same, by component
+    unsigned char* p = mem + (size_t)(n > 1 ? n - 1 : 1) * 64;
     unsigned long long* keys = reinterpret_cast<unsigned long long*>(p);
     p += (size_t)np2 * 8;
     float4* box = reinterpret_cast<float4*>(p);  // 2 per primitive: lo, hi
@@ -68,6 +70,8 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
     uint32_t* large = reinterpret_cast<uint32_t*>(p);
     p += (size_t)n * 4;
     int* done = reinterpret_cast<int*>(p);  // internal node state
+    p += (size_t)n * 4;
+    uint32_t* parent = reinterpret_cast<uint32_t*>(p);  // internal node -> parent * 2 + side (root: ~0)
     p += (size_t)n * 4;
     float* scal = reinterpret_cast<float*>(p);  // [centroid min, 1/extent, n_large, n_small]
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
@@ -132,7 +136,6 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
     const float cmin = scal[0], cinv = scal[1];
     Bvh out;
     out.nodes = nodes;
-    out.boxes = box;
     out.large = large;
     out.n_large = __float_as_uint(scal[2]);
     out.n_tree = __float_as_uint(scal[3]);
@@ -195,36 +198,51 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
         const int lo = min(i, j), hi = max(i, j);
         const uint32_t left = lo == gamma ? (kLeafBit | (uint32_t)(keys[gamma] & 0x3FFu)) : (uint32_t)gamma;
         const uint32_t right = hi == gamma + 1 ? (kLeafBit | (uint32_t)(keys[gamma + 1] & 0x3FFu)) : (uint32_t)(gamma + 1);
-        nodes[i].lo.w = __uint_as_float(left);
-        nodes[i].hi.w = __uint_as_float(right);
+        // child bits, and the box of a leaf child in its slot; an internal child writes its
+        // own box into the slot when it is finished (step 5)
+        nodef[16 * i + 3] = __uint_as_float(left);
+        nodef[16 * i + 7] = __uint_as_float(right);
+        const uint32_t ch[2] = {left, right};
+        for (int k = 0; k < 2; ++k) {
+            if (ch[k] & kLeafBit) {
+                const uint32_t q = ch[k] & ~kLeafBit;
+                const float4 l = box[2 * q], h = box[2 * q + 1];
+                float* slot = nodef + 16 * i + 8 * k;
+                slot[0] = l.x;
+                slot[1] = l.y;
+                slot[2] = l.z;
+                slot[4] = h.x;
+                slot[5] = h.y;
+                slot[6] = h.z;
+            } else {
+                parent[ch[k]] = 2u * (uint32_t)i + (uint32_t)k;
+            }
+        }
         done[i] = 0;
     }
+    if (tid == 0) parent[0] = ~0u;  // node 0 is the root
     __syncthreads();
-    // 5. boxes bottom-up.  done: 0 = open, 2 = box written this round (not
-    // yet usable by parents), 1 = finished.
+    // 5. boxes bottom-up: a node whose internal children are finished takes the union of
+    // its two slots and writes it into its parent's slot.  done: 0 = open, 2 = box
+    // written this round (not yet usable by the parent), 1 = finished.
     for (int iter = 0; iter < 64; ++iter) {
         for (uint32_t i = tid; i + 1 < m; i += nt) {
             if (done[i] != 0) continue;
-            const uint32_t c[2] = {__float_as_uint(nodes[i].lo.w), __float_as_uint(nodes[i].hi.w)};
-            float4 bl[2], bh[2];
-            bool ready = true;
-            for (int k = 0; k < 2; ++k) {
-                if (c[k] & kLeafBit) {
-                    const uint32_t pidx = c[k] & ~kLeafBit;
-                    bl[k] = box[2 * pidx];
-                    bh[k] = box[2 * pidx + 1];
-                } else if (done[c[k]] == 1) {
-                    bl[k] = nodes[c[k]].lo;
-                    bh[k] = nodes[c[k]].hi;
-                } else {
-                    ready = false;
-                }
-            }
+            const float* nd = nodef + 16 * i;
+            const uint32_t c0 = __float_as_uint(nd[3]), c1 = __float_as_uint(nd[7]);
+            const bool ready = ((c0 & kLeafBit) || (c0 + 1 < m && done[c0] == 1)) &&
+                               ((c1 & kLeafBit) || (c1 + 1 < m && done[c1] == 1));
             if (!ready) continue;
-            nodes[i].lo = make_float4(fminf(bl[0].x, bl[1].x), fminf(bl[0].y, bl[1].y), fminf(bl[0].z, bl[1].z),
-                                      nodes[i].lo.w);
-            nodes[i].hi = make_float4(fmaxf(bh[0].x, bh[1].x), fmaxf(bh[0].y, bh[1].y), fmaxf(bh[0].z, bh[1].z),
-                                      nodes[i].hi.w);
+            const uint32_t pa = parent[i];
+            if (pa != ~0u && (pa >> 1) + 1 < m) {
+                float* slot = nodef + 16 * (pa >> 1) + 8 * (pa & 1u);
+                slot[0] = fminf(nd[0], nd[8]);
+                slot[1] = fminf(nd[1], nd[9]);
+                slot[2] = fminf(nd[2], nd[10]);
+                slot[4] = fmaxf(nd[4], nd[12]);
+                slot[5] = fmaxf(nd[5], nd[13]);
+                slot[6] = fmaxf(nd[6], nd[14]);
+            }
             done[i] = 2;
         }
         __syncthreads();
@@ -275,47 +293,42 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
     float best = __int_as_float(0x7f800000);
     int idx = -1;
     for (uint32_t k = 0; k < b.n_large; ++k) test_prim(prims, b.large[k], o, d, best, idx);
-    if (b.n_tree >= 1) {
+    if (b.n_tree == 1) {
+        if ((b.root & ~kLeafBit) < n) test_prim(prims, b.root & ~kLeafBit, o, d, best, idx);
+    } else if (b.n_tree >= 2) {
         const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
         const uint32_t m = b.n_tree;
         uint32_t stack[kBvhStack];
         int sp = 0;
         uint32_t node = b.root;
         for (uint32_t visits = 0; visits < 4 * n + 64; ++visits) {
-            const bool leaf = node & kLeafBit;
-            if (leaf) {
-                if ((node & ~kLeafBit) < n) test_prim(prims, node & ~kLeafBit, o, d, best, idx);
-            } else if (node + 1 < m) {
-                const BvhNode nd = b.nodes[node];
-                const uint32_t c0 = __float_as_uint(nd.lo.w), c1 = __float_as_uint(nd.hi.w);
-                float t0 = 0.f, t1 = 0.f;
-                bool h0, h1;
-                if (c0 & kLeafBit) {
-                    const uint32_t q = c0 & ~kLeafBit;
-                    h0 = q < n && box_entry(b.boxes[2 * q], b.boxes[2 * q + 1], o, inv, best, t0);
-                } else if (c0 + 1 < m) {
-                    h0 = box_entry(b.nodes[c0].lo, b.nodes[c0].hi, o, inv, best, t0);
-                } else {
-                    h0 = false;
-                }
-                if (c1 & kLeafBit) {
-                    const uint32_t q = c1 & ~kLeafBit;
-                    h1 = q < n && box_entry(b.boxes[2 * q], b.boxes[2 * q + 1], o, inv, best, t1);
-                } else if (c1 + 1 < m) {
-                    h1 = box_entry(b.nodes[c1].lo, b.nodes[c1].hi, o, inv, best, t1);
-                } else {
-                    h1 = false;
-                }
-                if (h0 && h1) {
-                    const bool first0 = t0 <= t1;
-                    if (sp < kBvhStack) stack[sp++] = first0 ? c1 : c0;
-                    node = first0 ? c0 : c1;
-                    continue;
-                }
-                if (h0 || h1) {
-                    node = h0 ? c0 : c1;
-                    continue;
-                }
+            const float4* q = b.nodes + 4 * node;
+            const float4 l0 = q[0], h0b = q[1], l1 = q[2], h1b = q[3];
+            const uint32_t c0 = __float_as_uint(l0.w), c1 = __float_as_uint(h0b.w);
+            float t0 = 0.f, t1 = 0.f;
+            bool h0 = box_entry(l0, h0b, o, inv, best, t0);
+            bool h1 = box_entry(l1, h1b, o, inv, best, t1);
+            // leaf children: their primitive right away (the second against the updated best)
+            if (h0 && (c0 & kLeafBit)) {
+                if ((c0 & ~kLeafBit) < n) test_prim(prims, c0 & ~kLeafBit, o, d, best, idx);
+                h0 = false;
+            }
+            if (h1 && (c1 & kLeafBit)) {
+                if ((c1 & ~kLeafBit) < n && t1 <= best * 1.00001f + 1e-6f)
+                    test_prim(prims, c1 & ~kLeafBit, o, d, best, idx);
+                h1 = false;
+            }
+            h0 = h0 && c0 + 1 < m;
+            h1 = h1 && c1 + 1 < m;
+            if (h0 && h1) {
+                const bool first0 = t0 <= t1;
+                if (sp < kBvhStack) stack[sp++] = first0 ? c1 : c0;
+                node = first0 ? c0 : c1;
+                continue;
+            }
+            if (h0 || h1) {
+                node = h0 ? c0 : c1;
+                continue;
             }
             if (sp == 0) break;
             node = stack[--sp];

@@ -35,7 +35,13 @@
 
 namespace nirc {
 
-constexpr int kPtThreads = 128;
+// Threads per CTA.  One CTA per SM, so that each SM holds one copy of the
+// geometry and hierarchy in shared memory and the rest of the unified cache
+// serves as L1 (the traversal stacks live in local memory): 20 warps, or 16
+// for the kernels that need more than 96 registers a thread.
+template <bool kNee>
+constexpr int pt_threads() { return kNee ? 512 : 640; }
+constexpr int kPtThreadsAux = 512;  // k_primary_bth, k_gen_train
 constexpr uint32_t kBvhMinPrims = 17;
 
 struct FrameArgs {
@@ -107,7 +113,7 @@ __device__ __forceinline__ Tracer setup_scene(const SceneHeader* __restrict__ hd
     Tracer tr;
     tr.prims = sp;
     tr.n = n_prims;
-    tr.tree = Bvh{nullptr, nullptr, nullptr, 0u, 0u, 0u};
+    tr.tree = Bvh{nullptr, nullptr, 0u, 0u, 0u};
     tr.bvh = n_prims >= kBvhMinPrims;
     if (tr.bvh) {
         tr.tree = bvh_build(sp, n_prims, smem + (size_t)n_prims * sizeof(PrimGeom));
@@ -519,7 +525,7 @@ __device__ __forceinline__ void primary_resid(const SceneHeader* __restrict__ hd
 }
 
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5)
+__global__ void __launch_bounds__(pt_threads<kNee>(), 1)
     k_primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
                     nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
                     uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, unsigned long long* __restrict__ work,
@@ -546,7 +552,7 @@ struct PtJobs {
 };
 
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreads, kNee ? 4 : 5) k_primary_resid_batch(const __grid_constant__ PtJobs jobs) {
+__global__ void __launch_bounds__(pt_threads<kNee>(), 1) k_primary_resid_batch(const __grid_constant__ PtJobs jobs) {
     uint32_t ji = 0;
     while (ji + 1 < jobs.n && blockIdx.x >= jobs.j[ji + 1].cta0) ++ji;
     const PtJob& J = jobs.j[ji];
@@ -617,7 +623,7 @@ __device__ __forceinline__ float3 weighted_emission(const Tracer& tr, const Prim
 // throughput up to it are what the cache kernel completes.  One pixel per
 // lane, pixels from the work counter.
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreads, 4) k_primary_bth(const SceneHeader* __restrict__ hd_g,
+__global__ void __launch_bounds__(kPtThreadsAux, 1) k_primary_bth(const SceneHeader* __restrict__ hd_g,
                                                                 const Prim* __restrict__ gp, FrameArgs a,
                                                                 nirc_record* __restrict__ recs,
                                                                 PixelBase* __restrict__ base,
@@ -732,7 +738,7 @@ __global__ void __launch_bounds__(kPtThreads, 4) k_primary_bth(const SceneHeader
 // pick, camera ray, record and first direction, then the path's segments;
 // one ray per busy lane per iteration.
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreads, 4) k_gen_train(const SceneHeader* __restrict__ hd_g,
+__global__ void __launch_bounds__(kPtThreadsAux, 1) k_gen_train(const SceneHeader* __restrict__ hd_g,
                                                           const Prim* __restrict__ gp, uint32_t n_prims, uint32_t W,
                                                           uint32_t H, uint64_t T, uint32_t k0, uint32_t k1,
                                                           uint32_t max_depth, nirc_record* __restrict__ recs,
@@ -835,14 +841,14 @@ static size_t pt_smem(uint32_t n_prims) {
 }
 
 template <typename K>
-static cudaError_t persistent_grid(K kernel, size_t smem, uint64_t work, int num_sms, uint32_t* grid) {
+static cudaError_t persistent_grid(K kernel, int threads, size_t smem, uint64_t work, int num_sms, uint32_t* grid) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPtThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const uint64_t need = (work + kPtThreads - 1) / kPtThreads;
+    const uint64_t need = (work + threads - 1) / threads;
     uint64_t g = (uint64_t)per_sm * (uint64_t)num_sms;
     if (g > need) g = need;
     *grid = (uint32_t)(g < 1 ? 1 : g);
@@ -856,12 +862,12 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
                                           cudaStream_t st) {
     const size_t smem = pt_smem(a.n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_primary_resid<kNee>, smem, P, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_primary_resid<kNee>, pt_threads<kNee>(), smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     k_primary_resid<kNee>
-        <<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+        <<<grid, pt_threads<kNee>(), smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
     count_kernels(h);
     return cudaGetLastError();
 }
@@ -895,12 +901,12 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primary_resid_batch<kNee>, kPtThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primary_resid_batch<kNee>, pt_threads<kNee>(), smem);
     if (e != cudaSuccess) return e;
     const uint64_t grid_max = (uint64_t)(per_sm < 1 ? 1 : per_sm) * (uint64_t)h0->num_sms;
     if (grid_max < n) return cudaErrorInvalidConfiguration;
     // CTAs in proportion to each frame's rays (camera + residual paths), at least one
-    // each and no more than one per 128 pixels
+    // each and no more than one per CTA-width of pixels
     PtJobs jobs;
     jobs.n = n;
     uint32_t cta = 0;
@@ -908,7 +914,7 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         const FrameJob& f = fj[i];
         const uint64_t P = (uint64_t)f.fd.width * f.fd.height;
         uint64_t share = P * (1u + f.fd.n_resid) * (grid_max - n) / work_total + 1;  // the shares add up to <= grid_max
-        const uint64_t useful = (P + kPtThreads - 1) / kPtThreads;
+        const uint64_t useful = (P + pt_threads<kNee>() - 1) / pt_threads<kNee>();
         if (share > useful) share = useful;
         PtJob& j = jobs.j[i];
         j.hd = reinterpret_cast<const SceneHeader*>(f.scene);
@@ -923,7 +929,7 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         cta += (uint32_t)share;
         count_kernels(f.h);
     }
-    k_primary_resid_batch<kNee><<<cta, kPtThreads, smem, st>>>(jobs);
+    k_primary_resid_batch<kNee><<<cta, pt_threads<kNee>(), smem, st>>>(jobs);
     return cudaGetLastError();
 }
 
@@ -943,11 +949,11 @@ static cudaError_t launch_primary_bth_t(const nirc_handle* h, const SceneHeader*
                                         float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st) {
     const size_t smem = pt_smem(a.n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_primary_bth<kNee>, smem, P, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_primary_bth<kNee>, kPtThreadsAux, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_primary_bth<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, beta, sig, count, h->work_counter);
+    k_primary_bth<kNee><<<grid, kPtThreadsAux, smem, st>>>(hd, gp, a, recs, base, beta, sig, count, h->work_counter);
     count_kernels(h);
     return cudaGetLastError();
 }
@@ -971,11 +977,11 @@ static cudaError_t launch_gen_train_t(const nirc_handle* h, const SceneHeader* h
                                       uint32_t env_mode, cudaStream_t st) {
     const size_t smem = pt_smem(n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_gen_train<kNee>, smem, T, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_gen_train<kNee>, kPtThreadsAux, smem, T, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter + 1, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_gen_train<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
+    k_gen_train<kNee><<<grid, kPtThreadsAux, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
                                                       max_depth, recs, dirs, targets, h->work_counter + 1,
                                                       env_mode);
     count_kernels(h);
