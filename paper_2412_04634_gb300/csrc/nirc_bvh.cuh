@@ -256,16 +256,23 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
     return out;
 }
 
-__device__ __forceinline__ bool box_entry(const float4& lo, const float4& hi, V3 o, float3 inv, float best,
+// Slab test of box [lo, hi] against the ray with reciprocal direction inv and
+// ooi = -o * inv: slab parameters t = fma(x, inv, ooi).  The roundings move a
+// slab plane by about (|o| + L) 2^-24 along its axis for a box at distance L
+// along the ray; since |o| <= m + L (m the box's largest coordinate), that
+// stays far inside the box's expansion 1e-5 (1 + m) plus the 1e-5 L relative
+// slack below, so the test is conservative, axis-parallel rays (|inv| up to
+// 1e30) included.  tcap: the best hit with slack.
+__device__ __forceinline__ bool box_entry(const float4& lo, const float4& hi, float3 inv, float3 ooi, float tcap,
                                           float& tnear) {
-    const float tx0 = (lo.x - o.x) * inv.x, tx1 = (hi.x - o.x) * inv.x;
-    const float ty0 = (lo.y - o.y) * inv.y, ty1 = (hi.y - o.y) * inv.y;
-    const float tz0 = (lo.z - o.z) * inv.z, tz1 = (hi.z - o.z) * inv.z;
+    const float tx0 = fmaf(lo.x, inv.x, ooi.x), tx1 = fmaf(hi.x, inv.x, ooi.x);
+    const float ty0 = fmaf(lo.y, inv.y, ooi.y), ty1 = fmaf(hi.y, inv.y, ooi.y);
+    const float tz0 = fmaf(lo.z, inv.z, ooi.z), tz1 = fmaf(hi.z, inv.z, ooi.z);
     const float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
     const float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
     tnear = tmin;
     // conservative: slack on both ends (boxes are expanded as well)
-    return tmax * 1.00001f + 1e-6f >= fmaxf(tmin, 0.f) && tmin <= best * 1.00001f + 1e-6f;
+    return tmax * 1.00001f + 1e-6f >= fmaxf(tmin, 0.f) && tmin <= tcap;
 }
 
 __device__ __forceinline__ float safe_inv(float d) {
@@ -297,6 +304,7 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
         if ((b.root & ~kLeafBit) < n) test_prim(prims, b.root & ~kLeafBit, o, d, best, idx);
     } else if (b.n_tree >= 2) {
         const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
+        const float3 ooi = make_float3(-o.x * inv.x, -o.y * inv.y, -o.z * inv.z);
         const uint32_t m = b.n_tree;
         uint32_t stack[kBvhStack];
         int sp = 0;
@@ -306,8 +314,9 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
             const float4 l0 = q[0], h0b = q[1], l1 = q[2], h1b = q[3];
             const uint32_t c0 = __float_as_uint(l0.w), c1 = __float_as_uint(h0b.w);
             float t0 = 0.f, t1 = 0.f;
-            bool h0 = box_entry(l0, h0b, o, inv, best, t0);
-            bool h1 = box_entry(l1, h1b, o, inv, best, t1);
+            const float tcap = best * 1.00001f + 1e-6f;
+            bool h0 = box_entry(l0, h0b, inv, ooi, tcap, t0);
+            bool h1 = box_entry(l1, h1b, inv, ooi, tcap, t1);
             // leaf children: their primitive right away (the second against the updated best)
             if (h0 && (c0 & kLeafBit)) {
                 if ((c0 & ~kLeafBit) < n) test_prim(prims, c0 & ~kLeafBit, o, d, best, idx);
