@@ -23,8 +23,9 @@
  *    request that does not fit stops the scan (no overtaking on memory, so
  *    large frames are not starved).
  *  - A batch is launched as ONE CUDA graph.  In it the frames of all its
- *    requests are one path-tracing launch (per light mode) and one
- *    cache-integral launch over the union of their pixels (each request's
+ *    requests are one launch of each path-tracing pass (camera, residual;
+ *    per light mode) and one cache-integral launch over the union of their
+ *    pixels (each request's
  *    CTAs in proportion to its work, so requests of different resolution
  *    and N share the GPU inside one kernel); then each request's training
  *    pass and step run as their own branch of the graph.  When the caches
@@ -93,7 +94,7 @@ typedef struct nirc_server_stats {
     uint64_t submitted, completed, failed, batches, graph_instantiations, graph_updates;
     uint64_t arena_bytes, arena_peak_bytes, resident_bytes;
     uint32_t queued, in_flight, max_batch_seen, pad;
-    uint64_t frame_launches;     /* path-tracing + cache-integral launches issued for frames */
+    uint64_t frame_launches;     /* path-tracing (camera, residual) + cache-integral launches for frames */
 } nirc_server_stats;
 
 /* Create a server on the current CUDA device: reserves budget_bytes of device

@@ -1,19 +1,21 @@
 // nirc_pt.cu -- path-tracing kernels of the two-level estimator.
 //
-// k_primary_resid: per pixel, the camera ray (1 spp, Philox jitter), the
-//   shading record of the first hit (paper: surface parameter buffer), and
-//   the residual level's M BSDF-sampled directions with their path-traced
-//   incident radiance L_j (eq. L_r, the L_i term), Russian roulette with
-//   termination probability 0.1 (paper: section "Results", implementation
-//   paragraph).  Lanes regenerate work: one ray per busy lane per iteration,
-//   new pixels from a work counter as old ones finish.
+// k_camera, then k_resid: per pixel, the camera ray (1 spp, Philox jitter)
+//   and the shading record of the first hit (paper: surface parameter
+//   buffer), traced by the camera pass with consecutive pixels on
+//   consecutive lanes; then the residual level's M BSDF-sampled directions
+//   with their path-traced incident radiance L_j (eq. L_r, the L_i term),
+//   Russian roulette with termination probability 0.1 (paper: section
+//   "Results", implementation paragraph), by the residual pass from the
+//   records.  In the residual pass lanes regenerate work: one ray per busy
+//   lane per iteration, new pixels from a work counter as old ones finish.
 // k_gen_train: the separate training pass (section "Cache application"):
 //   T paths from uniformly drawn pixels, one record per path, organised the
 //   same way.
 //
 // k_primary_bth: the biased estimator's camera path (Balanced Termination
 //   Heuristic), see below.
-// Multi-vertex estimator: k_primary_resid also hands the cache kernels the
+// Multi-vertex estimator: k_resid also hands the cache kernels the
 //   records, throughputs and continuation rows of each residual path's
 //   second and third vertex (MvOut).
 //
@@ -356,17 +358,19 @@ __device__ __forceinline__ uint64_t fetch_work(unsigned long long* work, bool ne
     return first + (uint64_t)__popc(needm & ((1u << lane) - 1u));
 }
 
-// Lane state of k_primary_resid: which pixel, which ray is in flight.
+// Lane state of the residual pass and the training pass: which pixel (path),
+// which ray is in flight.
 enum : uint32_t { kNeedPixel = 0, kCameraRay = 1, kResidRay = 2, kNoMoreWork = 3 };
 
-// Per pixel: the camera ray, the shading record, then for j = 0..M-1 a
-// residual direction and its path (eq. L_r's L_j), exactly in the order and
-// with the Philox counters of a sequential loop.  The loop is organised as a
-// per-lane state machine so that every iteration traces one ray per busy
-// lane: a lane whose pixel is done takes the next pixel from a work counter
-// (one atomic per warp), so lanes do not idle while others finish long paths.
+// Residual pass: per pixel the camera pass hit (its record, emission and
+// signature so far), for j = 0..M-1 a residual direction and its path (eq.
+// L_r's L_j), exactly in the order and with the Philox counters of a
+// sequential loop.  The loop is organised as a per-lane state machine so
+// that every iteration traces one ray per busy lane: a lane whose pixel is
+// done takes the next pixel from a work counter (one atomic per warp), so
+// lanes do not idle while others finish long paths.
 template <bool kNee>
-__device__ __forceinline__ void primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
+__device__ __forceinline__ void resid_pass(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
                                               const FrameArgs& a, nirc_record* __restrict__ recs,
                                               PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
                                               uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
@@ -437,62 +441,39 @@ __device__ __forceinline__ void primary_resid(const SceneHeader* __restrict__ hd
         const bool need = stage == kNeedPixel;
         const uint64_t mine = fetch_work(work, need);
         if (need) {
-            if (mine < P) {
-                pix = (uint32_t)mine;
-                const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
-                camera_ray(hd, a.W, a.H, pix % a.W, pix / a.W, u01(r.x), u01(r.y), o, d);
-                stage = kCameraRay;
-            } else {
+            if (mine >= P) {
                 stage = kNoMoreWork;
+            } else {
+                // the camera pass traced the pixel: its record, emission and signature so far
+                pix = (uint32_t)mine;
+                const float4* q = reinterpret_cast<const float4*>(recs + pix);
+                const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+                const uint32_t rflags = __float_as_uint(q3.z);
+                stage = kNeedPixel;  // a camera miss: the camera pass wrote the whole pixel
+                if (rflags & 1u) {
+                    sp = V3{q0.x, q0.y, q0.z};
+                    sn = V3{q0.w, q1.x, q1.y};
+                    swo = V3{q1.z, q1.w, q2.x};
+                    salb = make_float3(q2.y, q2.z, q2.w);
+                    srough = q3.x;
+                    smat = (rflags >> 1) & 3u;
+                    const float4 b = base[pix].le;
+                    le = make_float3(b.x, b.y, b.z);
+                    sig = sig_out ? sig_out[2 * (uint64_t)pix] : kSigInit;
+                    wl = make_float3(0.f, 0.f, 0.f);
+                    nvalid = 0;
+                    j = 0;
+                    stage = next_residual();
+                }
             }
         }
         if (__all_sync(0xffffffffu, stage == kNoMoreWork)) break;
 
         float t = 0.f;
         int prim = -1;
-        if (stage == kCameraRay || stage == kResidRay) prim = tr.nearest(o, d, t);
+        if (stage == kResidRay) prim = tr.nearest(o, d, t);
 
-        if (stage == kCameraRay) {
-            sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
-            if (prim < 0) {
-                float4* q = reinterpret_cast<float4*>(recs + pix);
-                q[0] = q[1] = q[2] = q[3] = make_float4(0.f, 0.f, 0.f, 0.f);
-                base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
-                base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
-                ResidRow* my_rows = rows + (uint64_t)pix * a.M;
-                for (uint32_t jj = 0; jj < a.M; ++jj) {
-                    my_rows[jj].wi = make_float4(0.f, 0.f, 1.f, 0.f);
-                    my_rows[jj].w = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (mv) mv_clear(mv, (uint64_t)pix * a.M + jj);
-                }
-                if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
-                if (count) count[pix] = 0;
-                stage = kNeedPixel;
-            } else {
-                const Hit h = hit_info(tr.prims[prim], o, d, t);
-                const Prim* Pp = gp + prim;
-                const uint32_t pflags = __ldg(&Pp->flags);
-                smat = pflags & 3u;
-                write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (smat << 1));
-                le = make_float3(0.f, 0.f, 0.f);
-                if (h.front || (pflags & EMIT_TWO_SIDED))
-                    le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
-                salb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
-                srough = __ldg(&Pp->roughness);
-                sp = h.p;
-                sn = h.n;
-                swo = sneg(d);
-                wl = make_float3(0.f, 0.f, 0.f);
-                nvalid = 0;
-                j = 0;
-                if constexpr (kNee) {
-                    // direct light at the shading point: one light sample against the M residual directions
-                    sig = sig_mix(sig, nee_sample(tr, gp, lt, sp, sn, swo, salb, srough, smat, a.M, a.k0, a.k1, pix,
-                                                  0u, PURPOSE_LIGHT, le));
-                }
-                stage = next_residual();
-            }
-        } else if (stage == kResidRay) {
+        if (stage == kResidRay) {
             bool end;
             if (a.env_mode) {  // light mode 2: V(x, w_j) L_env(w_j), one ray
                 sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
@@ -524,18 +505,92 @@ __device__ __forceinline__ void primary_resid(const SceneHeader* __restrict__ hd
     if (a.rays) add_rays(a.rays, tr.rays);
 }
 
+// Camera pass: one camera ray per pixel, consecutive pixels on consecutive
+// lanes (a warp's rays are nearly parallel and walk the hierarchy alike).  A
+// hit writes the shading record, the emission seen (plus, in light mode 1,
+// the light sample at the shading point) and the signature so far, which the
+// residual pass continues; a miss writes the whole pixel.
 template <bool kNee>
-__global__ void __launch_bounds__(pt_threads<kNee>(), 1)
-    k_primary_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
-                    nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
-                    uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, unsigned long long* __restrict__ work,
-                    MvOut mvo) {
-    primary_resid<kNee>(hd_g, gp, a, recs, base, rows, sig_out, count, work, mvo);
+__device__ __forceinline__ void camera_pass(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
+                                            const FrameArgs& a, nirc_record* __restrict__ recs,
+                                            PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
+                                            uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count,
+                                            const MvOut& mvo, uint32_t cta, uint32_t n_cta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ SceneHeader hd;
+    __shared__ uint32_t s_nlights;
+    const Tracer tr = setup_scene(hd_g, gp, a.n_prims, smem_raw, &hd);
+    Lights lt{nullptr, 0u};
+    if constexpr (kNee)
+        lt = collect_lights(gp, a.n_prims, reinterpret_cast<uint16_t*>(smem_raw + pt_geom_bytes(a.n_prims)),
+                            &s_nlights);
+    const MvOut* mv = mvo.rec ? &mvo : nullptr;
+    const uint64_t P = (uint64_t)a.W * a.H;
+    const uint64_t stride = (uint64_t)n_cta * blockDim.x;  // CTAs [0, n_cta) of the frame, this one cta
+    for (uint64_t q = (uint64_t)cta * blockDim.x + threadIdx.x; q < P; q += stride) {
+        const uint32_t pix = (uint32_t)q;
+        const U4 r = philox(a.k0, a.k1, pix, 0u, 0u, PURPOSE_CAMERA);
+        V3 o, d;
+        camera_ray(hd, a.W, a.H, pix % a.W, pix / a.W, u01(r.x), u01(r.y), o, d);
+        float t = 0.f;
+        const int prim = tr.nearest(o, d, t);
+        uint64_t sig = sig_mix(kSigInit, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
+        if (prim < 0) {
+            float4* qr = reinterpret_cast<float4*>(recs + pix);
+            qr[0] = qr[1] = qr[2] = qr[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            base[pix].le = make_float4(0.f, 0.f, 0.f, 0.f);
+            base[pix].wl = make_float4(0.f, 0.f, 0.f, 0.f);
+            ResidRow* my_rows = rows + (uint64_t)pix * a.M;
+            for (uint32_t jj = 0; jj < a.M; ++jj) {
+                my_rows[jj].wi = make_float4(0.f, 0.f, 1.f, 0.f);
+                my_rows[jj].w = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (mv) mv_clear(mv, (uint64_t)pix * a.M + jj);
+            }
+            if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+            if (count) count[pix] = 0;
+            continue;
+        }
+        const Hit h = hit_info(tr.prims[prim], o, d, t);
+        const Prim* Pp = gp + prim;
+        const uint32_t pflags = __ldg(&Pp->flags);
+        const uint32_t smat = pflags & 3u;
+        write_record(recs + pix, h, d, Pp, (uint32_t)prim, 1u | (smat << 1));
+        float3 le = make_float3(0.f, 0.f, 0.f);
+        if (h.front || (pflags & EMIT_TWO_SIDED))
+            le = make_float3(__ldg(&Pp->emission[0]), __ldg(&Pp->emission[1]), __ldg(&Pp->emission[2]));
+        if constexpr (kNee) {
+            // direct light at the shading point: one light sample against the M residual directions
+            const float3 salb = make_float3(__ldg(&Pp->albedo[0]), __ldg(&Pp->albedo[1]), __ldg(&Pp->albedo[2]));
+            sig = sig_mix(sig, nee_sample(tr, gp, lt, h.p, h.n, sneg(d), salb, __ldg(&Pp->roughness), smat, a.M,
+                                          a.k0, a.k1, pix, 0u, PURPOSE_LIGHT, le));
+        }
+        base[pix].le = make_float4(le.x, le.y, le.z, 0.f);
+        if (sig_out) sig_out[2 * (uint64_t)pix] = sig;
+    }
+    if (a.rays) add_rays(a.rays, tr.rays);
 }
 
-// Several frames in one launch (the frame-request server's batches): CTAs
-// [cta0, next job's cta0) trace job j's frame, staging its scene once and
-// taking its pixels from its own counter.
+template <bool kNee>
+__global__ void __launch_bounds__(pt_threads<kNee>(), 1)
+    k_camera(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
+             nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
+             uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, MvOut mvo) {
+    camera_pass<kNee>(hd_g, gp, a, recs, base, rows, sig_out, count, mvo, blockIdx.x, gridDim.x);
+}
+
+// Residual pass: the residual paths of the pixels the camera pass hit.
+template <bool kNee>
+__global__ void __launch_bounds__(pt_threads<kNee>(), 1)
+    k_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
+            nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
+            uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, unsigned long long* __restrict__ work,
+            MvOut mvo) {
+    resid_pass<kNee>(hd_g, gp, a, recs, base, rows, sig_out, count, work, mvo);
+}
+
+// Several frames in one launch of each pass (the frame-request server's
+// batches): CTAs [cta0, cta0 + n_cta) trace job j's frame, staging its scene
+// once; the residual pass takes its pixels from the job's own counter.
 struct PtJob {
     const SceneHeader* hd;
     const Prim* gp;
@@ -544,20 +599,31 @@ struct PtJob {
     PixelBase* base;
     ResidRow* rows;
     unsigned long long* work;
-    uint32_t cta0;
+    uint32_t cta0, n_cta;
 };
 struct PtJobs {
     uint32_t n;
     PtJob j[kMaxFrameJobs];
 };
 
-template <bool kNee>
-__global__ void __launch_bounds__(pt_threads<kNee>(), 1) k_primary_resid_batch(const __grid_constant__ PtJobs jobs) {
+__device__ __forceinline__ const PtJob& pt_job(const PtJobs& jobs) {
     uint32_t ji = 0;
     while (ji + 1 < jobs.n && blockIdx.x >= jobs.j[ji + 1].cta0) ++ji;
-    const PtJob& J = jobs.j[ji];
-    primary_resid<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, J.work,
-                        MvOut{nullptr, nullptr, nullptr, 0});
+    return jobs.j[ji];
+}
+
+template <bool kNee>
+__global__ void __launch_bounds__(pt_threads<kNee>(), 1) k_camera_batch(const __grid_constant__ PtJobs jobs) {
+    const PtJob& J = pt_job(jobs);
+    camera_pass<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, MvOut{nullptr, nullptr, nullptr, 0},
+                      blockIdx.x - J.cta0, J.n_cta);
+}
+
+template <bool kNee>
+__global__ void __launch_bounds__(pt_threads<kNee>(), 1) k_resid_batch(const __grid_constant__ PtJobs jobs) {
+    const PtJob& J = pt_job(jobs);
+    resid_pass<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, J.work,
+                     MvOut{nullptr, nullptr, nullptr, 0});
 }
 
 // ---------------------------------------------------------------------------
@@ -734,7 +800,7 @@ __global__ void __launch_bounds__(kPtThreadsAux, 1) k_primary_bth(const SceneHea
     if (a.rays) add_rays(a.rays, tr.rays);
 }
 
-// Training paths, organised like k_primary_resid: per path index the pixel
+// Training paths, organised like the residual pass: per path index the pixel
 // pick, camera ray, record and first direction, then the path's segments;
 // one ray per busy lane per iteration.
 template <bool kNee>
@@ -862,12 +928,15 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
                                           cudaStream_t st) {
     const size_t smem = pt_smem(a.n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_primary_resid<kNee>, pt_threads<kNee>(), smem, P, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_camera<kNee>, pt_threads<kNee>(), smem, P, h->num_sms, &grid);
+    if (e != cudaSuccess) return e;
+    k_camera<kNee><<<grid, pt_threads<kNee>(), smem, st>>>(hd, gp, a, recs, base, rows, sig, count, mv);
+    count_kernels(h);
+    e = persistent_grid(k_resid<kNee>, pt_threads<kNee>(), smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_primary_resid<kNee>
-        <<<grid, pt_threads<kNee>(), smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+    k_resid<kNee><<<grid, pt_threads<kNee>(), smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
     count_kernels(h);
     return cudaGetLastError();
 }
@@ -897,12 +966,16 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         work_total += (uint64_t)fj[i].fd.width * fj[i].fd.height * (1u + fj[i].fd.n_resid);
     }
     const size_t smem = pt_smem(max_prims);
-    cudaError_t e = cudaFuncSetAttribute(k_primary_resid_batch<kNee>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_camera_batch<kNee>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_resid_batch<kNee>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_primary_resid_batch<kNee>, pt_threads<kNee>(), smem);
+    int per_sm = 0, per_sm_r = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_camera_batch<kNee>, pt_threads<kNee>(), smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k_resid_batch<kNee>, pt_threads<kNee>(), smem);
     if (e != cudaSuccess) return e;
+    per_sm = per_sm < per_sm_r ? per_sm : per_sm_r;
     const uint64_t grid_max = (uint64_t)(per_sm < 1 ? 1 : per_sm) * (uint64_t)h0->num_sms;
     if (grid_max < n) return cudaErrorInvalidConfiguration;
     // CTAs in proportion to each frame's rays (camera + residual paths), at least one
@@ -926,10 +999,14 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         j.rows = f.rows;
         j.work = f.work;
         j.cta0 = cta;
+        j.n_cta = (uint32_t)share;
         cta += (uint32_t)share;
-        count_kernels(f.h);
+        count_kernels(f.h, 2);  // its share of the two launches
     }
-    k_primary_resid_batch<kNee><<<cta, pt_threads<kNee>(), smem, st>>>(jobs);
+    k_camera_batch<kNee><<<cta, pt_threads<kNee>(), smem, st>>>(jobs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resid_batch<kNee><<<cta, pt_threads<kNee>(), smem, st>>>(jobs);
     return cudaGetLastError();
 }
 

@@ -12,11 +12,11 @@
 //             captures the batch into a CUDA graph, re-uses the batch
 //             slot's executable graph via cudaGraphExecUpdate when it can,
 //             and launches it.  In the graph the frames of all requests are
-//             one path-tracing launch (per light mode) and one cache-integral
-//             launch over the union of their pixels, CTAs shared out in
-//             proportion to each request's work; then each request's
-//             training pass and step run as their own branch (fork/join over
-//             worker streams).  A batch that cannot share launches (another
+//             one launch of each path-tracing pass (camera, residual; per
+//             light mode) and one cache-integral launch over the union of
+//             their pixels, CTAs shared out in proportion to each
+//             request's work; then each request's training pass and step
+//             run as their own branch (fork/join over worker streams).  A batch that cannot share launches (another
 //             precision, network shape or light mode 2 among its caches)
 //             runs each request's whole chain as its own branch.
 //  completer  polls the in-flight batches' events, stamps completion times,
@@ -185,7 +185,7 @@ nirc_status nirc_server::enqueue_request(Req* q, cudaStream_t st) {
     nirc_status s = enqueue_frame("nirc_server", sc.h, blob, fd, img, nullptr, scratch, st);
     if (s == NIRC_OK) {
         std::lock_guard<std::mutex> lk(mu);
-        stats.frame_launches += 2;  // path tracing and cache integral
+        stats.frame_launches += 3;  // camera pass, residual pass, cache integral
     }
     if (s != NIRC_OK) return s;
     return enqueue_training(q, st);
@@ -206,8 +206,8 @@ nirc_status nirc_server::enqueue_training(Req* q, cudaStream_t st) {
     return cuda_status(e, "nirc_server (training)");
 }
 
-// Whether the batch's frames can share one path-tracing launch per light
-// mode and one cache-integral launch.
+// Whether the batch's frames can share one launch per path-tracing pass
+// and light mode and one cache-integral launch.
 bool nirc_server::shares_launches(const Batch* b) const {
     const nirc_handle* h0 = scenes[b->reqs[0]->r.scene].h;
     for (const Req* q : b->reqs) {
@@ -260,7 +260,7 @@ nirc_status nirc_server::enqueue_batch_frames(Batch* b, cudaStream_t st) {
             if (fj[i].fd.light_mode == lm) sub[m++] = fj[i];
         if (m) {
             e = launch_primary_resid_batch(sub, m, st);
-            ++launches;
+            launches += 2;  // camera and residual passes
         }
     }
     if (e == cudaSuccess) {
