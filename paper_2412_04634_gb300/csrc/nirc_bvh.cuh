@@ -102,35 +102,59 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
         box[2 * i + 1] = make_float4(hi.x + e, hi.y + e, hi.z + e, 0.f);
     }
     __syncthreads();
-    // 2. large / small split and centroid bounds of the small primitives (serial, n <= 1024)
-    if (tid == 0) {
+    // 2. large / small split and centroid bounds of the small primitives (warp 0; the large
+    // list in index order by ballot compaction)
+    if (tid < 32) {
         float3 slo = make_float3(3e38f, 3e38f, 3e38f), shi = make_float3(-3e38f, -3e38f, -3e38f);
-        for (uint32_t i = 0; i < n; ++i) {
+        for (uint32_t i = tid; i < n; i += 32) {
             const float4 l = box[2 * i], h = box[2 * i + 1];
             slo = make_float3(fminf(slo.x, l.x), fminf(slo.y, l.y), fminf(slo.z, l.z));
             shi = make_float3(fmaxf(shi.x, h.x), fmaxf(shi.y, h.y), fmaxf(shi.z, h.z));
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            slo.x = fminf(slo.x, __shfl_xor_sync(0xffffffffu, slo.x, off));
+            slo.y = fminf(slo.y, __shfl_xor_sync(0xffffffffu, slo.y, off));
+            slo.z = fminf(slo.z, __shfl_xor_sync(0xffffffffu, slo.z, off));
+            shi.x = fmaxf(shi.x, __shfl_xor_sync(0xffffffffu, shi.x, off));
+            shi.y = fmaxf(shi.y, __shfl_xor_sync(0xffffffffu, shi.y, off));
+            shi.z = fmaxf(shi.z, __shfl_xor_sync(0xffffffffu, shi.z, off));
+        }
         const float scene = fmaxf(fmaxf(shi.x - slo.x, shi.y - slo.y), shi.z - slo.z);
         uint32_t nl = 0;
         float mn = 3e38f, mx = -3e38f;
-        for (uint32_t i = 0; i < n; ++i) {
-            const float4 l = box[2 * i], h = box[2 * i + 1];
-            const float ext = fmaxf(fmaxf(h.x - l.x, h.y - l.y), h.z - l.z);
-            if (ext > 0.5f * scene) {
-                large[nl++] = i;
-                box[2 * i].w = 1.f;  // marks a large primitive
-                continue;
+        for (uint32_t i0 = 0; i0 < n; i0 += 32) {
+            const uint32_t i = i0 + tid;
+            bool lg = false;
+            if (i < n) {
+                const float4 l = box[2 * i], h = box[2 * i + 1];
+                const float ext = fmaxf(fmaxf(h.x - l.x, h.y - l.y), h.z - l.z);
+                lg = ext > 0.5f * scene;
+                if (lg) {
+                    box[2 * i].w = 1.f;  // marks a large primitive
+                } else {
+                    const float c[3] = {0.5f * (l.x + h.x), 0.5f * (l.y + h.y), 0.5f * (l.z + h.z)};
+                    for (int d = 0; d < 3; ++d) {
+                        mn = fminf(mn, c[d]);
+                        mx = fmaxf(mx, c[d]);
+                    }
+                }
             }
-            const float c[3] = {0.5f * (l.x + h.x), 0.5f * (l.y + h.y), 0.5f * (l.z + h.z)};
-            for (int d = 0; d < 3; ++d) {
-                mn = fminf(mn, c[d]);
-                mx = fmaxf(mx, c[d]);
-            }
+            const unsigned m = __ballot_sync(0xffffffffu, lg);
+            if (lg) large[nl + __popc(m & ((1u << tid) - 1u))] = i;
+            nl += __popc(m);
         }
-        scal[0] = mn;
-        scal[1] = mx > mn ? 1.0f / (mx - mn) : 1.0f;
-        scal[2] = __uint_as_float(nl);
-        scal[3] = __uint_as_float(n - nl);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        }
+        if (tid == 0) {
+            scal[0] = mn;
+            scal[1] = mx > mn ? 1.0f / (mx - mn) : 1.0f;
+            scal[2] = __uint_as_float(nl);
+            scal[3] = __uint_as_float(n - nl);
+        }
     }
     __syncthreads();
     const float cmin = scal[0], cinv = scal[1];
@@ -218,41 +242,38 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
                 parent[ch[k]] = 2u * (uint32_t)i + (uint32_t)k;
             }
         }
-        done[i] = 0;
+        done[i] = (int)((left & kLeafBit) == 0u) + (int)((right & kLeafBit) == 0u);  // internal children pending
     }
     if (tid == 0) parent[0] = ~0u;  // node 0 is the root
     __syncthreads();
-    // 5. boxes bottom-up: a node whose internal children are finished takes the union of
-    // its two slots and writes it into its parent's slot.  done: 0 = open, 2 = box
-    // written this round (not yet usable by the parent), 1 = finished.
-    for (int iter = 0; iter < 64; ++iter) {
-        for (uint32_t i = tid; i + 1 < m; i += nt) {
-            if (done[i] != 0) continue;
-            const float* nd = nodef + 16 * i;
-            const uint32_t c0 = __float_as_uint(nd[3]), c1 = __float_as_uint(nd[7]);
-            const bool ready = ((c0 & kLeafBit) || (c0 + 1 < m && done[c0] == 1)) &&
-                               ((c1 & kLeafBit) || (c1 + 1 < m && done[c1] == 1));
-            if (!ready) continue;
+    // 5. boxes bottom-up (the atomic scheme of Karras): a finished node writes the union of its
+    // two slots into its parent's slot and counts itself off the parent's pending children;
+    // the child that finishes a parent goes on with it.  Walks start at the nodes whose
+    // children are both leaves, marked (-1) before any walk runs.
+    for (uint32_t i = tid; i + 1 < m; i += nt)
+        if (done[i] == 0) done[i] = -1;
+    __syncthreads();
+    for (uint32_t i0 = tid; i0 + 1 < m; i0 += nt) {
+        if (done[i0] != -1) continue;
+        uint32_t i = i0;
+        for (int steps = 0; steps < 64; ++steps) {
             const uint32_t pa = parent[i];
-            if (pa != ~0u && (pa >> 1) + 1 < m) {
-                float* slot = nodef + 16 * (pa >> 1) + 8 * (pa & 1u);
-                slot[0] = fminf(nd[0], nd[8]);
-                slot[1] = fminf(nd[1], nd[9]);
-                slot[2] = fminf(nd[2], nd[10]);
-                slot[4] = fmaxf(nd[4], nd[12]);
-                slot[5] = fmaxf(nd[5], nd[13]);
-                slot[6] = fmaxf(nd[6], nd[14]);
-            }
-            done[i] = 2;
+            if (pa == ~0u || (pa >> 1) + 1 >= m) break;  // the root (or a malformed link)
+            const volatile float* nd = nodef + 16 * i;
+            volatile float* slot = nodef + 16 * (pa >> 1) + 8 * (pa & 1u);
+            slot[0] = fminf(nd[0], nd[8]);
+            slot[1] = fminf(nd[1], nd[9]);
+            slot[2] = fminf(nd[2], nd[10]);
+            slot[4] = fmaxf(nd[4], nd[12]);
+            slot[5] = fmaxf(nd[5], nd[13]);
+            slot[6] = fmaxf(nd[6], nd[14]);
+            __threadfence_block();
+            if (atomicSub(&done[pa >> 1], 1) != 1) break;  // its other child is not finished yet
+            __threadfence_block();
+            i = pa >> 1;
         }
-        __syncthreads();
-        int all = 1;
-        for (uint32_t i = tid; i + 1 < m; i += nt) {
-            if (done[i] == 2) done[i] = 1;
-            if (done[i] == 0) all = 0;
-        }
-        if (__syncthreads_and(all)) break;
     }
+    __syncthreads();
     return out;
 }
 
