@@ -13,17 +13,17 @@
 // tile of 128 records at a time, four warpgroups per CTA:
 //  encode    hash-grid features (FP16 copy of the table) and surface
 //            features into the A tile, direction features into a second
-//            A tile; the FP32 values go to the e buffer for dW0
+//            A tile; the values go to the e buffer (BF16) for dW0
 //  forward   layer 0 = W0_surf e_surf + W0_dir e_dir (4 + 1 or 2 MMAs), the
 //            hidden and output layers with their biases added by an MMA
 //            against the ones atom (the cache kernel's FP16 image); each
 //            epilogue keeps the ReLU mask of its 64 units as two 32-bit
-//            words, stores the FP32 activations and writes the FP16 A tile
+//            words, stores the activations (BF16) and writes the FP16 A tile
 //  loss      n = exp(min(z, z_clamp)) (or the visibility sigmoid), the
 //            sample's term of eq. 12 and dL/dz
 //  backward  delta of the last hidden layer = mask (W_out^T dL/dz) in FP32;
 //            then delta_{l-1} = mask (W_l^T delta_l) as FP16 MMAs against
-//            the transposed weights; FP32 deltas stored for dW; finally
+//            the transposed weights; deltas stored (BF16) for dW; finally
 //            dL/de_pos = W0_pos^T delta_0 (one MMA, N = 32) scattered into
 //            the hash-table gradient like the FP32 backward.  The deltas
 //            span many orders of magnitude (they carry the 1 / (3 n) of the
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kTrWarpgroups * 128, 1)
             tc::mma_commit(mbar);
         }
     };
-    // Forward epilogue: + bias (layer 0 only), ReLU mask, FP32 activations out, FP16 A tile.
+    // Forward epilogue: + bias (layer 0 only), ReLU mask, activations out (BF16), FP16 A tile.
     auto fwd_epilogue = [&](const float* b, uint16_t* gact, bool store, uint32_t (&mask)[2]) {
 #pragma unroll
         for (uint32_t half = 0; half < 2; ++half) {
