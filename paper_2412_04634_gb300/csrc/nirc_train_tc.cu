@@ -2,7 +2,7 @@
 // tensor cores (tcgen05, TMEM accumulators): the same loss, gradients and
 // buffers as the FP32 kernels of nirc_train.cu (relative L2 of eq. 12,
 // hash-grid scatter, stored activations and deltas for the weight-gradient
-// GEMMs), with the layer products as MMAs.
+// kernels), with the layer products as MMAs.
 //
 // The stored network inputs, activations, deltas and dL/dz are BF16 (the
 // element (row, sample) of a buffer at its base + row * ld + sample, two bytes
