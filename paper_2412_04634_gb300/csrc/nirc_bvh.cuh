@@ -21,10 +21,12 @@
 
 namespace nirc {
 
-// Internal node i of the tree is 4 float4 at nodes[4 i]: child 0's box (min
-// xyz | child 0 bits in w, max xyz | child 1 bits in w), then child 1's box
-// (min xyz, max xyz).  Child bits: bit 31 set = leaf, low bits = primitive;
-// otherwise the internal node's index.
+// Internal node i of the tree is 16 floats at nodes[4 i]: the two children's
+// boxes component by component, child 0 then child 1 (min x, min y, min z,
+// max x, max y, max z: floats 2 c + k for component c of child k), so that
+// both children's slab parameters come from packed FP32 pairs; then the
+// child bits (floats 12, 13).  Child bits: bit 31 set = leaf, low bits =
+// primitive; otherwise the internal node's index.
 struct Bvh {
     const float4* nodes;
     const uint32_t* large;  // primitives tested by brute force
@@ -224,20 +226,20 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
         const uint32_t right = hi == gamma + 1 ? (kLeafBit | (uint32_t)(keys[gamma + 1] & 0x3FFu)) : (uint32_t)(gamma + 1);
         // child bits, and the box of a leaf child in its slot; an internal child writes its
         // own box into the slot when it is finished (step 5)
-        nodef[16 * i + 3] = __uint_as_float(left);
-        nodef[16 * i + 7] = __uint_as_float(right);
+        nodef[16 * i + 12] = __uint_as_float(left);
+        nodef[16 * i + 13] = __uint_as_float(right);
         const uint32_t ch[2] = {left, right};
         for (int k = 0; k < 2; ++k) {
             if (ch[k] & kLeafBit) {
                 const uint32_t q = ch[k] & ~kLeafBit;
                 const float4 l = box[2 * q], h = box[2 * q + 1];
-                float* slot = nodef + 16 * i + 8 * k;
+                float* slot = nodef + 16 * i + k;  // component c at slot[2 c]
                 slot[0] = l.x;
-                slot[1] = l.y;
-                slot[2] = l.z;
-                slot[4] = h.x;
-                slot[5] = h.y;
-                slot[6] = h.z;
+                slot[2] = l.y;
+                slot[4] = l.z;
+                slot[6] = h.x;
+                slot[8] = h.y;
+                slot[10] = h.z;
             } else {
                 parent[ch[k]] = 2u * (uint32_t)i + (uint32_t)k;
             }
@@ -260,13 +262,13 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
             const uint32_t pa = parent[i];
             if (pa == ~0u || (pa >> 1) + 1 >= m) break;  // the root (or a malformed link)
             const volatile float* nd = nodef + 16 * i;
-            volatile float* slot = nodef + 16 * (pa >> 1) + 8 * (pa & 1u);
-            slot[0] = fminf(nd[0], nd[8]);
-            slot[1] = fminf(nd[1], nd[9]);
-            slot[2] = fminf(nd[2], nd[10]);
-            slot[4] = fmaxf(nd[4], nd[12]);
-            slot[5] = fmaxf(nd[5], nd[13]);
-            slot[6] = fmaxf(nd[6], nd[14]);
+            volatile float* slot = nodef + 16 * (pa >> 1) + (pa & 1u);  // component c at slot[2 c]
+            slot[0] = fminf(nd[0], nd[1]);
+            slot[2] = fminf(nd[2], nd[3]);
+            slot[4] = fminf(nd[4], nd[5]);
+            slot[6] = fmaxf(nd[6], nd[7]);
+            slot[8] = fmaxf(nd[8], nd[9]);
+            slot[10] = fmaxf(nd[10], nd[11]);
             __threadfence_block();
             if (atomicSub(&done[pa >> 1], 1) != 1) break;  // its other child is not finished yet
             __threadfence_block();
@@ -277,20 +279,18 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
     return out;
 }
 
-// Slab test of box [lo, hi] against the ray with reciprocal direction inv and
-// ooi = -o * inv: slab parameters t = fma(x, inv, ooi).  The roundings move a
-// slab plane by about (|o| + L) 2^-24 along its axis for a box at distance L
-// along the ray; since |o| <= m + L (m the box's largest coordinate), that
-// stays far inside the box's expansion 1e-5 (1 + m) plus the 1e-5 L relative
-// slack below, so the test is conservative, axis-parallel rays (|inv| up to
-// 1e30) included.  tcap: the best hit with slack.
-__device__ __forceinline__ bool box_entry(const float4& lo, const float4& hi, float3 inv, float3 ooi, float tcap,
-                                          float& tnear) {
-    const float tx0 = fmaf(lo.x, inv.x, ooi.x), tx1 = fmaf(hi.x, inv.x, ooi.x);
-    const float ty0 = fmaf(lo.y, inv.y, ooi.y), ty1 = fmaf(hi.y, inv.y, ooi.y);
-    const float tz0 = fmaf(lo.z, inv.z, ooi.z), tz1 = fmaf(hi.z, inv.z, ooi.z);
-    const float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fminf(tz0, tz1));
-    const float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+// Slab test of a box against the ray from its slab parameters t = fma(x,
+// 1/d, -o/d) for its min (l) and max (h) planes per axis.  The roundings
+// move a slab plane by about (|o| + L) 2^-24 along its axis for a box at
+// distance L along the ray; since |o| <= m + L (m the box's largest
+// coordinate), that stays far inside the box's expansion 1e-5 (1 + m) plus
+// the 1e-5 L relative slack below, so the test is conservative,
+// axis-parallel rays (|1/d| up to 1e30) included.  tcap: the best hit with
+// slack.
+__device__ __forceinline__ bool slab_entry(float lx, float hx, float ly, float hy, float lz, float hz, float tcap,
+                                           float& tnear) {
+    const float tmin = fmaxf(fmaxf(fminf(lx, hx), fminf(ly, hy)), fminf(lz, hz));
+    const float tmax = fminf(fminf(fmaxf(lx, hx), fmaxf(ly, hy)), fmaxf(lz, hz));
     tnear = tmin;
     // conservative: slack on both ends (boxes are expanded as well)
     return tmax * 1.00001f + 1e-6f >= fmaxf(tmin, 0.f) && tmin <= tcap;
@@ -326,18 +326,27 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
     } else if (b.n_tree >= 2) {
         const float3 inv = make_float3(safe_inv(d.x), safe_inv(d.y), safe_inv(d.z));
         const float3 ooi = make_float3(-o.x * inv.x, -o.y * inv.y, -o.z * inv.z);
+        const float2 ix2 = make_float2(inv.x, inv.x), iy2 = make_float2(inv.y, inv.y), iz2 = make_float2(inv.z, inv.z);
+        const float2 ox2 = make_float2(ooi.x, ooi.x), oy2 = make_float2(ooi.y, ooi.y), oz2 = make_float2(ooi.z, ooi.z);
         const uint32_t m = b.n_tree;
         uint32_t stack[kBvhStack];
         int sp = 0;
         uint32_t node = b.root;
         for (uint32_t visits = 0; visits < 4 * n + 64; ++visits) {
             const float4* q = b.nodes + 4 * node;
-            const float4 l0 = q[0], h0b = q[1], l1 = q[2], h1b = q[3];
-            const uint32_t c0 = __float_as_uint(l0.w), c1 = __float_as_uint(h0b.w);
+            const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+            const uint32_t c0 = __float_as_uint(q3.x), c1 = __float_as_uint(q3.y);
+            // slab parameters of both children, one packed FMA per plane pair
+            const float2 tlx = __ffma2_rn(make_float2(q0.x, q0.y), ix2, ox2);
+            const float2 tly = __ffma2_rn(make_float2(q0.z, q0.w), iy2, oy2);
+            const float2 tlz = __ffma2_rn(make_float2(q1.x, q1.y), iz2, oz2);
+            const float2 thx = __ffma2_rn(make_float2(q1.z, q1.w), ix2, ox2);
+            const float2 thy = __ffma2_rn(make_float2(q2.x, q2.y), iy2, oy2);
+            const float2 thz = __ffma2_rn(make_float2(q2.z, q2.w), iz2, oz2);
             float t0 = 0.f, t1 = 0.f;
             const float tcap = best * 1.00001f + 1e-6f;
-            bool h0 = box_entry(l0, h0b, inv, ooi, tcap, t0);
-            bool h1 = box_entry(l1, h1b, inv, ooi, tcap, t1);
+            bool h0 = slab_entry(tlx.x, thx.x, tly.x, thy.x, tlz.x, thz.x, tcap, t0);
+            bool h1 = slab_entry(tlx.y, thx.y, tly.y, thy.y, tlz.y, thz.y, tcap, t1);
             // leaf children: their primitive right away (the second against the updated best)
             if (h0 && (c0 & kLeafBit)) {
                 if ((c0 & ~kLeafBit) < n) test_prim(prims, c0 & ~kLeafBit, o, d, best, idx);
