@@ -305,7 +305,8 @@ __device__ __forceinline__ void test_prim(const PrimGeom* __restrict__ prims, ui
                                           int& idx) {
     const PrimGeom& g = prims[pi];
     float t;
-    const bool hit = (__float_as_uint(g.n_kind.w) == KIND_SPHERE) ? hit_sphere(g, o, d, t) : hit_rect(g, o, d, t);
+    const bool hit =
+        (__float_as_uint(g.n_kind.w) == KIND_SPHERE) ? hit_sphere(g, o, d, t) : hit_rect_within(g, o, d, best, t);
     if (hit && (t < best || (t == best && (int)pi < idx))) {
         best = t;
         idx = (int)pi;
