@@ -296,9 +296,12 @@ __device__ __forceinline__ bool slab_entry(float lx, float hx, float ly, float h
     return tmax * 1.00001f + 1e-6f >= fmaxf(tmin, 0.f) && tmin <= tcap;
 }
 
+// 1 / d for the slab tests, |d| raised to at least 1e-30 (sign kept), by the
+// fast reciprocal: its few-ulp error moves slab planes by far less than the
+// boxes' expansion and the tests' slack.
 __device__ __forceinline__ float safe_inv(float d) {
     const float dd = fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
-    return 1.0f / dd;
+    return __fdividef(1.0f, dd);
 }
 
 __device__ __forceinline__ void test_prim(const PrimGeom* __restrict__ prims, uint32_t pi, V3 o, V3 d, float& best,
