@@ -304,6 +304,29 @@ __device__ __forceinline__ float safe_inv(float d) {
     return __fdividef(1.0f, dd);
 }
 
+// hit_rect for a caller that only needs hits no farther than `best`: a
+// rectangle whose plane lies behind the ray or beyond best is rejected on the
+// fast quotient (a few ulp; rejection only outside a 0.1 % margin, so no
+// hit that hit_rect would report at t <= best is lost); the others take
+// hit_rect's exact steps, so an accepted t is hit_rect's.
+__device__ __forceinline__ bool hit_rect_within(const PrimGeom& g, V3 o, V3 d, float best, float& t_out) {
+    const V3 n{g.n_kind.x, g.n_kind.y, g.n_kind.z};
+    const float denom = sdot(n, d);
+    if (denom == 0.0f) return false;
+    const V3 a{g.a_r.x, g.a_r.y, g.a_r.z};
+    const float num = sdot(n, ssub(a, o));
+    const float ta = __fdividef(num, denom);
+    if (!(ta > 0.999f * kTMin) || ta > 1.001f * best) return false;
+    const float t = __fdiv_rn(num, denom);
+    if (!(t > kTMin)) return false;
+    const V3 rel = ssub(smadd(o, t, d), a);
+    const float al = __fmul_rn(sdot(rel, V3{g.u_iuu.x, g.u_iuu.y, g.u_iuu.z}), g.u_iuu.w);
+    const float be = __fmul_rn(sdot(rel, V3{g.v_ivv.x, g.v_ivv.y, g.v_ivv.z}), g.v_ivv.w);
+    if (!(al >= 0.0f && al <= 1.0f && be >= 0.0f && be <= 1.0f)) return false;
+    t_out = t;
+    return true;
+}
+
 __device__ __forceinline__ void test_prim(const PrimGeom* __restrict__ prims, uint32_t pi, V3 o, V3 d, float& best,
                                           int& idx) {
     const PrimGeom& g = prims[pi];
