@@ -39,11 +39,16 @@ namespace nirc {
 
 // Threads per CTA.  One CTA per SM, so that each SM holds one copy of the
 // geometry and hierarchy in shared memory and the rest of the unified cache
-// serves as L1 (the traversal stacks live in local memory): 20 warps, or 16
-// for the kernels that need more than 96 registers a thread.
+// serves as L1 (the traversal stacks and register spills live in local
+// memory).  The traversal is latency-bound: 32 warps at 64 registers (some
+// spilled to L1) beat 20 at 96 (residual pass at 1080p: 1.00 vs 1.11 ms;
+// light mode 1 3.09 vs 3.33 ms at 16 warps; the biased camera path 0.33 vs
+// 0.44 ms).  The training pass keeps 512-thread CTAs: its 65,536 paths would
+// fill only 64 CTAs of 1024.
 template <bool kNee>
-constexpr int pt_threads() { return kNee ? 512 : 640; }
-constexpr int kPtThreadsAux = 512;  // k_primary_bth, k_gen_train
+constexpr int pt_threads() { return 1024; }
+constexpr int kPtThreadsBth = 1024;   // k_primary_bth
+constexpr int kPtThreadsTrain = 512;  // k_gen_train
 constexpr uint32_t kBvhMinPrims = 17;
 
 struct FrameArgs {
@@ -689,7 +694,7 @@ __device__ __forceinline__ float3 weighted_emission(const Tracer& tr, const Prim
 // throughput up to it are what the cache kernel completes.  One pixel per
 // lane, pixels from the work counter.
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreadsAux, 1) k_primary_bth(const SceneHeader* __restrict__ hd_g,
+__global__ void __launch_bounds__(kPtThreadsBth, 1) k_primary_bth(const SceneHeader* __restrict__ hd_g,
                                                                 const Prim* __restrict__ gp, FrameArgs a,
                                                                 nirc_record* __restrict__ recs,
                                                                 PixelBase* __restrict__ base,
@@ -804,7 +809,7 @@ __global__ void __launch_bounds__(kPtThreadsAux, 1) k_primary_bth(const SceneHea
 // pick, camera ray, record and first direction, then the path's segments;
 // one ray per busy lane per iteration.
 template <bool kNee>
-__global__ void __launch_bounds__(kPtThreadsAux, 1) k_gen_train(const SceneHeader* __restrict__ hd_g,
+__global__ void __launch_bounds__(kPtThreadsTrain, 1) k_gen_train(const SceneHeader* __restrict__ hd_g,
                                                           const Prim* __restrict__ gp, uint32_t n_prims, uint32_t W,
                                                           uint32_t H, uint64_t T, uint32_t k0, uint32_t k1,
                                                           uint32_t max_depth, nirc_record* __restrict__ recs,
@@ -1026,11 +1031,11 @@ static cudaError_t launch_primary_bth_t(const nirc_handle* h, const SceneHeader*
                                         float4* beta, uint64_t* sig, uint32_t* count, cudaStream_t st) {
     const size_t smem = pt_smem(a.n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_primary_bth<kNee>, kPtThreadsAux, smem, P, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_primary_bth<kNee>, kPtThreadsBth, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_primary_bth<kNee><<<grid, kPtThreadsAux, smem, st>>>(hd, gp, a, recs, base, beta, sig, count, h->work_counter);
+    k_primary_bth<kNee><<<grid, kPtThreadsBth, smem, st>>>(hd, gp, a, recs, base, beta, sig, count, h->work_counter);
     count_kernels(h);
     return cudaGetLastError();
 }
@@ -1054,11 +1059,11 @@ static cudaError_t launch_gen_train_t(const nirc_handle* h, const SceneHeader* h
                                       uint32_t env_mode, cudaStream_t st) {
     const size_t smem = pt_smem(n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_gen_train<kNee>, kPtThreadsAux, smem, T, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_gen_train<kNee>, kPtThreadsTrain, smem, T, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter + 1, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_gen_train<kNee><<<grid, kPtThreadsAux, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
+    k_gen_train<kNee><<<grid, kPtThreadsTrain, smem, st>>>(hd, gp, n_prims, W, H, T, (uint32_t)seed, frame ^ kTrainKeyBit,
                                                       max_depth, recs, dirs, targets, h->work_counter + 1,
                                                       env_mode);
     count_kernels(h);
