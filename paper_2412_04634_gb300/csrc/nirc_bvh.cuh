@@ -339,15 +339,20 @@ __device__ __forceinline__ void test_prim(const PrimGeom* __restrict__ prims, ui
     }
 }
 
-// Nearest hit: the large list, then the tree; same (t, index) result as
-// trace_nearest.  Child indices are range-checked and the walk is capped at
-// 4n + 64 visits, so a malformed tree yields a wrong answer (caught by the
-// parity tests) rather than an out-of-range read or an endless loop.
-__device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ prims, uint32_t n, V3 o, V3 d,
-                                  float& t_hit) {
-    float best = __int_as_float(0x7f800000);
-    int idx = -1;
-    for (uint32_t k = 0; k < b.n_large; ++k) test_prim(prims, b.large[k], o, d, best, idx);
+// The walk behind both queries: the large list, then the tree, keeping the
+// smallest (t, index) starting from (best, idx); kFirstCloser stops as soon
+// as anything beats the starting pair.  Child indices are range-checked and
+// the walk is capped at 4n + 64 visits, so a malformed tree yields a wrong
+// answer (caught by the parity tests) rather than an out-of-range read or an
+// endless loop.
+template <bool kFirstCloser>
+__device__ inline int bvh_walk(const Bvh& b, const PrimGeom* __restrict__ prims, uint32_t n, V3 o, V3 d,
+                               float& best, int idx) {
+    const int idx0 = idx;
+    for (uint32_t k = 0; k < b.n_large; ++k) {
+        test_prim(prims, b.large[k], o, d, best, idx);
+        if (kFirstCloser && idx != idx0) return idx;
+    }
     if (b.n_tree == 1) {
         if ((b.root & ~kLeafBit) < n) test_prim(prims, b.root & ~kLeafBit, o, d, best, idx);
     } else if (b.n_tree >= 2) {
@@ -384,6 +389,7 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
                     test_prim(prims, c1 & ~kLeafBit, o, d, best, idx);
                 h1 = false;
             }
+            if (kFirstCloser && idx != idx0) break;
             h0 = h0 && c0 + 1 < m;
             h1 = h1 && c1 + 1 < m;
             if (h0 && h1) {
@@ -400,8 +406,26 @@ __device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ pri
             node = stack[--sp];
         }
     }
+    return idx;
+}
+
+// Nearest hit: same (t, index) result as trace_nearest.
+__device__ inline int bvh_nearest(const Bvh& b, const PrimGeom* __restrict__ prims, uint32_t n, V3 o, V3 d,
+                                  float& t_hit) {
+    float best = __int_as_float(0x7f800000);
+    const int idx = bvh_walk<false>(b, prims, n, o, d, best, -1);
     t_hit = best;
     return idx;
+}
+
+// Whether a primitive other than li comes before (t_l, li) in the (t, index)
+// order along the ray: with (t_l, li) li's own hit, the same decision as
+// "the nearest hit is not li", but the walk prunes everything beyond t_l and
+// stops at the first primitive in front.
+__device__ inline bool bvh_occluded(const Bvh& b, const PrimGeom* __restrict__ prims, uint32_t n, V3 o, V3 d,
+                                    float t_l, int li) {
+    float best = t_l;
+    return bvh_walk<true>(b, prims, n, o, d, best, li) != li;
 }
 
 }  // namespace nirc

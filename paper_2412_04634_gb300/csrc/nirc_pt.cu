@@ -94,6 +94,14 @@ struct Tracer {
         ++rays;
         return bvh ? bvh_nearest(tree, prims, n, o, d, t) : trace_nearest(prims, n, o, d, t);
     }
+    // Whether the nearest hit along (o, d) is another primitive than li, given
+    // li's own hit at t_l (shadow rays).
+    __device__ __forceinline__ bool occluded(V3 o, V3 d, float t_l, int li) const {
+        ++rays;
+        if (bvh) return bvh_occluded(tree, prims, n, o, d, t_l, li);
+        float t;
+        return trace_nearest(prims, n, o, d, t) != li;
+    }
 };
 
 // Add the threads' ray counts to *out (one atomic per converged group).
@@ -193,9 +201,11 @@ __device__ __forceinline__ uint32_t nee_sample(const Tracer& tr, const Prim* __r
     const bool ok = cx > 0.f && (cl > 0.f || ((__ldg(&L->flags) & EMIT_TWO_SIDED) && cl < 0.f));
     uint32_t word = e | ((uint32_t)ok << 16);
     if (!ok) return word;
-    float t;
-    const int hit = tr.nearest(p, w, t);
-    const bool visible = hit == (int)li && fabsf(__fsub_rn(t, dist)) <= __fmul_rn(1e-3f, dist);
+    // visible: the nearest hit along w is the light, at the sampled distance (the light's own
+    // hit first, then an occlusion walk that prunes everything beyond it)
+    float t = 0.f;
+    const bool visible = hit_rect(g, p, w, t) && fabsf(__fsub_rn(t, dist)) <= __fmul_rn(1e-3f, dist) &&
+                         !tr.occluded(p, w, t, (int)li);
     word |= (uint32_t)visible << 17;
     if (!visible) return word;
     const BsdfEval be = bsdf_eval(n, wo, w, alb, rough, mat);
