@@ -45,8 +45,7 @@ namespace nirc {
 // light mode 1 3.09 vs 3.33 ms at 16 warps; the biased camera path 0.33 vs
 // 0.44 ms).  The training pass keeps 512-thread CTAs: its 65,536 paths would
 // fill only 64 CTAs of 1024.
-template <bool kNee>
-constexpr int pt_threads() { return 1024; }
+constexpr int kPtThreads = 1024;      // k_camera, k_resid and their batched forms
 constexpr int kPtThreadsBth = 1024;   // k_primary_bth
 constexpr int kPtThreadsTrain = 512;  // k_gen_train
 constexpr uint32_t kBvhMinPrims = 17;
@@ -586,7 +585,7 @@ __device__ __forceinline__ void camera_pass(const SceneHeader* __restrict__ hd_g
 }
 
 template <bool kNee>
-__global__ void __launch_bounds__(pt_threads<kNee>(), 1)
+__global__ void __launch_bounds__(kPtThreads, 1)
     k_camera(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
              nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
              uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, MvOut mvo) {
@@ -595,7 +594,7 @@ __global__ void __launch_bounds__(pt_threads<kNee>(), 1)
 
 // Residual pass: the residual paths of the pixels the camera pass hit.
 template <bool kNee>
-__global__ void __launch_bounds__(pt_threads<kNee>(), 1)
+__global__ void __launch_bounds__(kPtThreads, 1)
     k_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
             nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
             uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, unsigned long long* __restrict__ work,
@@ -628,14 +627,14 @@ __device__ __forceinline__ const PtJob& pt_job(const PtJobs& jobs) {
 }
 
 template <bool kNee>
-__global__ void __launch_bounds__(pt_threads<kNee>(), 1) k_camera_batch(const __grid_constant__ PtJobs jobs) {
+__global__ void __launch_bounds__(kPtThreads, 1) k_camera_batch(const __grid_constant__ PtJobs jobs) {
     const PtJob& J = pt_job(jobs);
     camera_pass<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, MvOut{nullptr, nullptr, nullptr, 0},
                       blockIdx.x - J.cta0, J.n_cta);
 }
 
 template <bool kNee>
-__global__ void __launch_bounds__(pt_threads<kNee>(), 1) k_resid_batch(const __grid_constant__ PtJobs jobs) {
+__global__ void __launch_bounds__(kPtThreads, 1) k_resid_batch(const __grid_constant__ PtJobs jobs) {
     const PtJob& J = pt_job(jobs);
     resid_pass<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, J.work,
                      MvOut{nullptr, nullptr, nullptr, 0});
@@ -943,15 +942,15 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
                                           cudaStream_t st) {
     const size_t smem = pt_smem(a.n_prims);
     uint32_t grid = 1;
-    cudaError_t e = persistent_grid(k_camera<kNee>, pt_threads<kNee>(), smem, P, h->num_sms, &grid);
+    cudaError_t e = persistent_grid(k_camera<kNee>, kPtThreads, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
-    k_camera<kNee><<<grid, pt_threads<kNee>(), smem, st>>>(hd, gp, a, recs, base, rows, sig, count, mv);
+    k_camera<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, mv);
     count_kernels(h);
-    e = persistent_grid(k_resid<kNee>, pt_threads<kNee>(), smem, P, h->num_sms, &grid);
+    e = persistent_grid(k_resid<kNee>, kPtThreads, smem, P, h->num_sms, &grid);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_resid<kNee><<<grid, pt_threads<kNee>(), smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+    k_resid<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
     count_kernels(h);
     return cudaGetLastError();
 }
@@ -986,9 +985,9 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         e = cudaFuncSetAttribute(k_resid_batch<kNee>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, per_sm_r = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_camera_batch<kNee>, pt_threads<kNee>(), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_camera_batch<kNee>, kPtThreads, smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k_resid_batch<kNee>, pt_threads<kNee>(), smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_r, k_resid_batch<kNee>, kPtThreads, smem);
     if (e != cudaSuccess) return e;
     per_sm = per_sm < per_sm_r ? per_sm : per_sm_r;
     const uint64_t grid_max = (uint64_t)(per_sm < 1 ? 1 : per_sm) * (uint64_t)h0->num_sms;
@@ -1002,7 +1001,7 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         const FrameJob& f = fj[i];
         const uint64_t P = (uint64_t)f.fd.width * f.fd.height;
         uint64_t share = P * (1u + f.fd.n_resid) * (grid_max - n) / work_total + 1;  // the shares add up to <= grid_max
-        const uint64_t useful = (P + pt_threads<kNee>() - 1) / pt_threads<kNee>();
+        const uint64_t useful = (P + kPtThreads - 1) / kPtThreads;
         if (share > useful) share = useful;
         PtJob& j = jobs.j[i];
         j.hd = reinterpret_cast<const SceneHeader*>(f.scene);
@@ -1018,10 +1017,10 @@ static cudaError_t launch_primary_resid_batch_t(const FrameJob* fj, uint32_t n, 
         cta += (uint32_t)share;
         count_kernels(f.h, 2);  // its share of the two launches
     }
-    k_camera_batch<kNee><<<cta, pt_threads<kNee>(), smem, st>>>(jobs);
+    k_camera_batch<kNee><<<cta, kPtThreads, smem, st>>>(jobs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resid_batch<kNee><<<cta, pt_threads<kNee>(), smem, st>>>(jobs);
+    k_resid_batch<kNee><<<cta, kPtThreads, smem, st>>>(jobs);
     return cudaGetLastError();
 }
 
