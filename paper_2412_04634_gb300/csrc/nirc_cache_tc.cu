@@ -553,16 +553,16 @@ __global__ void __launch_bounds__(640, 1)
     };
     // 4 K-steps from the TMEM operand, then the bias slot j as one more K = 16 step against the ones atom
     const uint32_t ones = sbase + tcimg::off_ones(H), bmma = sbase + tcimg::off_bmma(H);
-    auto issue_layer = [&](uint32_t w_tile, uint32_t idesc, uint32_t j) {
-        if (t == 0 && !*abort_flag) {
+    auto issue_layer = [&](uint32_t w_tile, uint32_t idesc, uint32_t j, uint32_t issuer) {
+        if (t == issuer && !*abort_flag) {
             tc::fence_after_sync();
             mma_ta(0u, w_tile, idesc, 4u, false);
             tc::mma_f16(tmD, tc::sdesc_rep8(ones), tc::sdesc(bmma + 8192u * (j >> 2) + 32u * (j & 3u)), idesc, 1);
             tc::mma_commit(mbar);
         }
     };
-    auto issue_e4m3 = [&](uint32_t b_tile) {
-        if (t == 0 && !*abort_flag) {
+    auto issue_e4m3 = [&](uint32_t b_tile, uint32_t issuer) {
+        if (t == issuer && !*abort_flag) {
             tc::fence_after_sync();
 #pragma unroll
             for (uint32_t s = 0; s < 2; ++s)
@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(640, 1)
             }
             tc::tmem_wait_st();
             sync_wg();
-            if (t == 0 && !*abort_flag) {
+            if (t == 32u * (jt & 3u) && !*abort_flag) {  // the issuing warp rotates from tile to tile
                 tc::fence_after_sync();
                 if constexpr (kSh) {
                     mma_ta(0u, w0dir, id64, 2u, false);
@@ -936,10 +936,10 @@ __global__ void __launch_bounds__(640, 1)
                 else tc::tmem_wait_st();                           // 16-bit operand in TMEM
                 sync_wg();
                 if (next_hidden) {
-                    if constexpr (kF8) issue_e4m3(sbase + tcimg::off_wh(l));
-                    else issue_layer(sbase + tcimg::off_wh(l), id64, l);
+                    if constexpr (kF8) issue_e4m3(sbase + tcimg::off_wh(l), 32u * ((jt + l + 1u) & 3u));
+                    else issue_layer(sbase + tcimg::off_wh(l), id64, l, 32u * ((jt + l + 1u) & 3u));
                 } else {
-                    issue_layer(wout, id16, H - 1u);
+                    issue_layer(wout, id16, H - 1u, 32u * ((jt + l + 1u) & 3u));
                 }
                 wait_mma();
             }
