@@ -382,8 +382,11 @@ enum : uint32_t { kNeedPixel = 0, kCameraRay = 1, kResidRay = 2, kNoMoreWork = 3
 // sequential loop.  The loop is organised as a per-lane state machine so
 // that every iteration traces one ray per busy lane: a lane whose pixel is
 // done takes the next pixel from a work counter (one atomic per warp), so
-// lanes do not idle while others finish long paths.
-template <bool kNee>
+// lanes do not idle while others finish long paths.  kExtra compiles in the
+// multi-vertex outputs and light mode 2 (environment visibility); frames
+// with neither run the instance without that code, which keeps the loop
+// smaller in the instruction cache.
+template <bool kNee, bool kExtra>
 __device__ __forceinline__ void resid_pass(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp,
                                               const FrameArgs& a, nirc_record* __restrict__ recs,
                                               PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
@@ -397,7 +400,8 @@ __device__ __forceinline__ void resid_pass(const SceneHeader* __restrict__ hd_g,
     if constexpr (kNee)
         lt = collect_lights(gp, a.n_prims, reinterpret_cast<uint16_t*>(smem_raw + pt_geom_bytes(a.n_prims)),
                             &s_nlights);
-    const MvOut* mv = mvo.rec ? &mvo : nullptr;  // multi-vertex estimator: later-vertex data per residual path
+    // multi-vertex estimator: later-vertex data per residual path (kExtra instances only)
+    const MvOut* mv = (kExtra && mvo.rec) ? &mvo : nullptr;
     const float invM = a.M ? 1.0f / (float)a.M : 0.f;
 
     const uint64_t P = (uint64_t)a.W * a.H;
@@ -489,7 +493,7 @@ __device__ __forceinline__ void resid_pass(const SceneHeader* __restrict__ hd_g,
 
         if (stage == kResidRay) {
             bool end;
-            if (a.env_mode) {  // light mode 2: V(x, w_j) L_env(w_j), one ray
+            if (kExtra && a.env_mode) {  // light mode 2: V(x, w_j) L_env(w_j), one ray
                 sig = sig_mix(sig, prim < 0 ? 0xFFFFFFFFu : (uint32_t)prim);
                 L = prim < 0 ? env_radiance(scene_env(hd, gp, a.n_prims), d) : make_float3(0.f, 0.f, 0.f);
                 end = true;
@@ -593,13 +597,13 @@ __global__ void __launch_bounds__(kPtThreads, 1)
 }
 
 // Residual pass: the residual paths of the pixels the camera pass hit.
-template <bool kNee>
+template <bool kNee, bool kExtra>
 __global__ void __launch_bounds__(kPtThreads, 1)
     k_resid(const SceneHeader* __restrict__ hd_g, const Prim* __restrict__ gp, FrameArgs a,
             nirc_record* __restrict__ recs, PixelBase* __restrict__ base, ResidRow* __restrict__ rows,
             uint64_t* __restrict__ sig_out, uint32_t* __restrict__ count, unsigned long long* __restrict__ work,
             MvOut mvo) {
-    resid_pass<kNee>(hd_g, gp, a, recs, base, rows, sig_out, count, work, mvo);
+    resid_pass<kNee, kExtra>(hd_g, gp, a, recs, base, rows, sig_out, count, work, mvo);
 }
 
 // Several frames in one launch of each pass (the frame-request server's
@@ -636,7 +640,9 @@ __global__ void __launch_bounds__(kPtThreads, 1) k_camera_batch(const __grid_con
 template <bool kNee>
 __global__ void __launch_bounds__(kPtThreads, 1) k_resid_batch(const __grid_constant__ PtJobs jobs) {
     const PtJob& J = pt_job(jobs);
-    resid_pass<kNee>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, J.work,
+    // batched frames are light mode 0 or 1 with the two-level estimator (their FrameArgs carry
+    // env_mode 0, and no multi-vertex outputs), so the instance without those paths serves them
+    resid_pass<kNee, false>(J.hd, J.gp, J.a, J.recs, J.base, J.rows, nullptr, nullptr, J.work,
                      MvOut{nullptr, nullptr, nullptr, 0});
 }
 
@@ -946,11 +952,17 @@ static cudaError_t launch_primary_resid_t(const nirc_handle* h, const SceneHeade
     if (e != cudaSuccess) return e;
     k_camera<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, mv);
     count_kernels(h);
-    e = persistent_grid(k_resid<kNee>, kPtThreads, smem, P, h->num_sms, &grid);
-    if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(h->work_counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    k_resid<kNee><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+    if (mv.rec || a.env_mode) {  // the multi-vertex outputs or light mode 2: the instance with those paths
+        e = persistent_grid(k_resid<kNee, true>, kPtThreads, smem, P, h->num_sms, &grid);
+        if (e != cudaSuccess) return e;
+        k_resid<kNee, true><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+    } else {
+        e = persistent_grid(k_resid<kNee, false>, kPtThreads, smem, P, h->num_sms, &grid);
+        if (e != cudaSuccess) return e;
+        k_resid<kNee, false><<<grid, kPtThreads, smem, st>>>(hd, gp, a, recs, base, rows, sig, count, h->work_counter, mv);
+    }
     count_kernels(h);
     return cudaGetLastError();
 }
