@@ -2,9 +2,13 @@
 // the cache integral: FP16 operands, split BF16 operands (hi + lo) or E4M3
 // hidden layers, always with FP32 accumulation.
 //
-// Work unit: a block of 128 pixels; with S = N + M rows per pixel it holds
-// exactly S row tiles of 128 rows.  One warpgroup (128 threads, thread t =
-// tile row t = TMEM lane t) owns a block at a time; a CTA runs up to five
+// Work unit: a block of up to 128 pixels; with S = N + M rows per pixel a
+// full block holds exactly S row tiles of 128 rows.  One warpgroup (128
+// threads, thread t = tile row t = TMEM lane t) owns a block at a time:
+// whole blocks round robin over the launch's warpgroups, then the pixels
+// left after the last whole round in equal smaller blocks, one per
+// warpgroup (at 1080p a last round of whole blocks ran on 48 of the 152
+// SMs); a CTA runs up to five
 // warpgroups so that one warpgroup's SIMT work (sampling, encodings,
 // epilogues) overlaps another's MMAs.  Each warpgroup owns a slice of tensor
 // memory: the accumulator D (64 columns) and the A operand of the next MMA
@@ -584,9 +588,19 @@ __global__ void __launch_bounds__(640, 1)
 
     const uint32_t S = J.S;
     const uint32_t R_full = 128u * S;
-    for (uint32_t blk = (blockIdx.x - J.cta0) * n_wg + wg; blk < J.n_blocks; blk += J.n_cta * n_wg) {
-        const uint32_t p0 = blk * 128u;
-        const uint32_t npix = min(128u, J.P - p0);
+    // blocks of 128 pixels dealt round robin over the job's warpgroups in whole rounds; the
+    // pixels left after the last whole round are split evenly (one block of up to 128 pixels
+    // each), so no warpgroup runs a whole extra block while the others have finished
+    const uint32_t wg_job = (blockIdx.x - J.cta0) * n_wg + wg, n_wg_job = J.n_cta * n_wg;
+    const uint32_t rounds = (J.P / 128u) / n_wg_job;
+    const uint32_t tail0 = rounds * n_wg_job * 128u, tail = J.P - tail0;
+    for (uint32_t k = 0; k <= rounds; ++k) {
+        uint32_t p0 = (k * n_wg_job + wg_job) * 128u, npix = 128u;
+        if (k == rounds) {
+            p0 = tail0 + (uint32_t)((uint64_t)tail * wg_job / n_wg_job);
+            npix = tail0 + (uint32_t)((uint64_t)tail * (wg_job + 1u) / n_wg_job) - p0;
+            if (npix == 0u) break;
+        }
         // ---- per-pixel sums, part 2 (eq. L_mlmc, L_c, L_r) of tile jr (rows j0r .. j0r + 127):
         // four lanes per pixel, each adding a pair of the row buffer's channels over the pixel's
         // rows of this tile in sample order with Kahan compensation (packed FP32 pairs),
