@@ -708,9 +708,12 @@ __global__ void __launch_bounds__(640, 1)
                 const float4* rq = reinterpret_cast<const float4*>(recs + p0 + t);
                 r0 = __ldg(rq);
                 r1 = __ldg(rq + 1);
-                // the record's second half and the pixel's residual rows, read by the row tiles
+                // into L2, what later stages read first: the record's second half and the pixel's
+                // residual rows (row tiles), its base and throughput (per-pixel sums)
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(rq + 2));
                 if (J.M) asm volatile("prefetch.global.L2 [%0];" ::"l"(rows + (uint64_t)(p0 + t) * J.M));
+                if (base) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + p0 + t));
+                if (beta) asm volatile("prefetch.global.L2 [%0];" ::"l"(beta + p0 + t));
                 if constexpr (kSh) {
                     r2 = __ldg(rq + 2);
                     r3 = __ldg(rq + 3);
