@@ -5,7 +5,7 @@
 // kept in a short list tested by brute force first; they would overlap every
 // node of a hierarchy.  The others get a binary radix tree: conservative
 // AABBs, 30-bit Morton codes of the centroids made unique with the primitive
-// index, a bitonic sort, the topology of Karras (HPG 2012), then boxes
+// index, a rank sort, the topology of Karras (HPG 2012), then boxes
 // bottom-up.  Each internal node stores the boxes of its two children (64
 // bytes: one visit is four 16-byte shared loads), a leaf child being one
 // primitive.  A query tests the large list, then walks the tree in near-first
@@ -182,21 +182,30 @@ __device__ inline Bvh bvh_build(const PrimGeom* __restrict__ prims, uint32_t n, 
         keys[i] = k;
     }
     __syncthreads();
-    // 3. bitonic sort of np2 keys
-    for (uint32_t size = 2; size <= np2; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-            for (uint32_t t = tid; t < np2 / 2; t += nt) {
-                const uint32_t i = 2 * t - (t & (stride - 1));
-                const uint32_t j = i + stride;
-                const bool up = (i & size) == 0;
-                const unsigned long long a = keys[i], b = keys[j];
-                if ((a > b) == up) {
-                    keys[i] = b;
-                    keys[j] = a;
-                }
+    // 3. sort: each small primitive's key goes to its rank, the number of smaller keys (the
+    // primitive index in the low bits makes those keys unique; the ~0 keys of large primitives
+    // and padding are never smaller and are not placed: nothing reads keys past the small
+    // ones).  Four lanes count one key's rank over interleaved quarters of the keys (four
+    // consecutive words per load, no bank conflict) and add their counts by shuffles; the
+    // sorted keys are staged in done[] (high words) and parent[] (low words), unused until 4.
+    {
+        uint32_t* hiw = reinterpret_cast<uint32_t*>(done);
+        const uint32_t span = (4u * n + 31u) & ~31u;  // whole warps, so every shuffle sees all lanes
+        for (uint32_t u = tid; u < span; u += nt) {
+            const uint32_t i = u >> 2, q = u & 3u;
+            const unsigned long long ki = i < n ? keys[i] : ~0ull;
+            uint32_t c = 0;
+            for (uint32_t j = q; j < n; j += 4u) c += keys[j] < ki ? 1u : 0u;
+            c += __shfl_xor_sync(0xffffffffu, c, 1);
+            c += __shfl_xor_sync(0xffffffffu, c, 2);
+            if (q == 0u && ki != ~0ull) {
+                hiw[c] = (uint32_t)(ki >> 32);
+                parent[c] = (uint32_t)ki;
             }
-            __syncthreads();
         }
+        __syncthreads();
+        for (uint32_t i = tid; i < out.n_tree; i += nt) keys[i] = ((unsigned long long)hiw[i] << 32) | parent[i];
+        __syncthreads();
     }
     const uint32_t m = out.n_tree;
     if (m <= 1) {
