@@ -3,11 +3,14 @@
 // relative squared error (paper:
 // MRSE, used for every equal-time comparison), mean over pixels and RGB of
 // (I - R)^2 / (R^2 + eps).  Each term is formed in binary32 (IEEE divide;
-// at most four roundings, ~2.4e-7 relative) and the frame-level sum is
-// accumulated in FP64, the only FP64 arithmetic on the GPU (FP64 divides
-// would make this HBM-light kernel bound by the FP64 unit).  Grid-stride
-// float4 reads, per-thread FP64 sums, warp and block reductions, one FP64
-// atomic add per block into the zeroed output.
+// at most four roundings, ~2.4e-7 relative).  A thread adds its terms into a
+// pair of binary32 values (hi + lo: TwoSum (Knuth) gives each add's exact
+// rounding error, which lo collects), so its partial sum carries about 48
+// significant bits; the pairs are then combined in FP64 (warp and block
+// reductions, one FP64 atomic add per block into the zeroed output).  GB300's
+// FP64 unit is slow: the former per-term FP64 adds (six FP64 operations per
+// pixel) bound this HBM-light kernel, which now issues three per thread.
+// Grid-stride float4 reads.
 #include "nirc_internal.h"
 
 namespace nirc {
@@ -21,11 +24,20 @@ __device__ __forceinline__ float rel_sq(float a, float b, float eps) {
 
 __global__ void __launch_bounds__(kMrseThreads) k_mrse(const float4* __restrict__ img, const float4* __restrict__ ref,
                                                       uint64_t n, float eps, double scale, double* __restrict__ out) {
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;  // this thread's terms: hi + lo
     for (uint64_t i = (uint64_t)blockIdx.x * kMrseThreads + threadIdx.x; i < n; i += (uint64_t)gridDim.x * kMrseThreads) {
         const float4 a = __ldg(img + i), b = __ldg(ref + i);
-        acc += (double)rel_sq(a.x, b.x, eps) + (double)rel_sq(a.y, b.y, eps) + (double)rel_sq(a.z, b.z, eps);
+        const float t[3] = {rel_sq(a.x, b.x, eps), rel_sq(a.y, b.y, eps), rel_sq(a.z, b.z, eps)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float sum = __fadd_rn(hi, t[k]);
+            const float bv = __fsub_rn(sum, hi);  // TwoSum: hi + t = sum + err exactly
+            const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bv)), __fsub_rn(t[k], bv));
+            lo = __fadd_rn(lo, err);
+            hi = sum;
+        }
     }
+    double acc = (double)hi + (double)lo;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     __shared__ double part[kMrseThreads / 32];
     if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
@@ -87,7 +99,7 @@ cudaError_t launch_mrse(const float* img, const float* ref, uint64_t n, float ep
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     uint64_t blocks = (n + kMrseThreads - 1) / kMrseThreads;
-    if (blocks > (uint64_t)sms * 4) blocks = (uint64_t)sms * 4;
+    if (blocks > (uint64_t)sms * 8) blocks = (uint64_t)sms * 8;  // 8 blocks of 256 threads per SM
     k_mrse<<<(uint32_t)blocks, kMrseThreads, 0, st>>>(reinterpret_cast<const float4*>(img),
                                                       reinterpret_cast<const float4*>(ref), n, eps,
                                                       1.0 / (3.0 * (double)n), out);
