@@ -830,6 +830,18 @@ __global__ void __launch_bounds__(640, 1)
         // ------------------------------------------------ row tiles
         const uint32_t R = npix * S;
         uint32_t jt = 0;
+        // kCarry: a lane's record for the next tile is loaded while the current tile's output
+        // layer runs (16 registers across the output epilogue; the instances whose register
+        // budget has no room for them load it at the tile's start)
+        constexpr bool kCarry = AB == 0 && !kAmax && !kSh;
+        float4 nq0, nq1, nq2, nq3;
+        if constexpr (kCarry) {
+            const float4* rq = reinterpret_cast<const float4*>(recs + p0 + (t < R ? div_s(t, J.s_magic) : 0u));
+            nq0 = __ldg(rq);
+            nq1 = __ldg(rq + 1);
+            nq2 = __ldg(rq + 2);
+            nq3 = __ldg(rq + 3);
+        }
         for (uint32_t j0 = 0; j0 < R; j0 += 128u, ++jt) {
             const uint32_t r = j0 + t;
             const bool rin = r < R;
@@ -847,9 +859,20 @@ __global__ void __launch_bounds__(640, 1)
             bool ok = false;
             uint32_t word = 0;
             {
-                // all four words of the record at once (one L1 round trip)
-                const float4* rq = reinterpret_cast<const float4*>(recs + p0 + pl);
-                const float4 q0 = __ldg(rq), q1 = __ldg(rq + 1), q2 = __ldg(rq + 2), q3 = __ldg(rq + 3);
+                // all four words of the record at once (one round trip; with kCarry already here)
+                float4 q0, q1, q2, q3;
+                if constexpr (kCarry) {
+                    q0 = nq0;
+                    q1 = nq1;
+                    q2 = nq2;
+                    q3 = nq3;
+                } else {
+                    const float4* rq = reinterpret_cast<const float4*>(recs + p0 + pl);
+                    q0 = __ldg(rq);
+                    q1 = __ldg(rq + 1);
+                    q2 = __ldg(rq + 2);
+                    q3 = __ldg(rq + 3);
+                }
                 const uint32_t flags = __float_as_uint(q3.z);
                 word = (flags & 1u) << 31;  // the pixel's record is valid (signature)
                 if (rin && (flags & 1u)) {
@@ -960,6 +983,16 @@ __global__ void __launch_bounds__(640, 1)
                     else issue_layer(sbase + tcimg::off_wh(l), id64, l, 32u * ((jt + l + 1u) & 3u));
                 } else {
                     issue_layer(wout, id16, H - 1u, 32u * ((jt + l + 1u) & 3u));
+                    if constexpr (kCarry) {
+                        if (r + 128u < R) {  // the next tile's record of this lane's row (rows past R: unused)
+                            const float4* rq =
+                                reinterpret_cast<const float4*>(recs + p0 + div_s(r + 128u, J.s_magic));
+                            nq0 = __ldg(rq);
+                            nq1 = __ldg(rq + 1);
+                            nq2 = __ldg(rq + 2);
+                            nq3 = __ldg(rq + 3);
+                        }
+                    }
                 }
                 wait_mma();
             }
