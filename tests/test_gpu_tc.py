@@ -85,7 +85,11 @@ def test_tc_full_size_sampled_pixels(N, oracle):
     W, H = 1920, 1080
     sc = scenes.cornell_scene(W, H, seed=1, n_prims=256, glossy=True, moving_emitter=True, frame=11)
     g = _run_frame(N, cfg, params, sc, W, H, 16, 1, 5, 11, 1, precision=1, rows=True)
-    pix = np.unique(np.concatenate([rng.integers(0, W * H, 300), [0, 127, 128, W * H - 1]])).astype(np.uint32)
+    # with 152 SMs x 5 warpgroups, whole 128-pixel blocks cover pixels < 21 x 760 x 128 and the
+    # remaining 30,720 are split into 760 blocks of 40-41 pixels: probe both sides of those seams
+    tail0 = 21 * 760 * 128
+    seams = [tail0 - 1, tail0, tail0 + 40, tail0 + 41, tail0 + 30720 * 379 // 760, W * H - 2]
+    pix = np.unique(np.concatenate([rng.integers(0, W * H, 300), [0, 127, 128, W * H - 1], seams])).astype(np.uint32)
     o = oracle.estimate(cfg, params, sc.blob(), oracle.oframe(W, H, 16, 1, 5, 11, 1), pixels=pix, rows=True)
     sub = {k: v[pix] for k, v in g.items()}
     err = _row_errors(sub, o)
