@@ -495,6 +495,21 @@ def code_sha256(paths):
     return h.hexdigest()
 
 
+def dominant_class(timing, args):
+    """The kernel class with the most device time among the library's timers
+    ({class: (total ms, launches)}).  Classes whose phases run beside another
+    stream's kernels time spans (they include waits for the SMs the other
+    stream holds), not device time, and are left out: the training-record pass
+    beside the cache pass, the training step beside the next frame's path
+    tracing."""
+    spans = set()
+    if getattr(args, "overlap_records", 0):
+        spans.add("train_records")
+    if getattr(args, "pipeline_trace", 0):
+        spans |= {"train_fwd", "train_bwd", "train_gradw", "adam"}
+    return max((k for k, v in timing.items() if v[1] and k not in spans), key=lambda k: timing[k][0])
+
+
 def _roofline(args, cfg, props, kernel_ms, dominant, sm_max, window_s):
     fl_frame, per_row, per_pixel = flops_per_frame(cfg, args)
     P = args.width * args.height
@@ -595,15 +610,7 @@ def run_ours(args):
     value = world * rows_per_frame(args) * args.steps / (res["total_ms"] / 1e3)
     # per frame: device ms of each kernel class and the library kernels it launched
     kernel_ms = {k: (v[0] / args.steps, v[1] / args.steps) for k, v in timing.items() if v[1]}
-    # classes whose phases run beside another stream's kernels time spans (they include waits for the
-    # SMs the other stream holds), not device time: the training-record pass beside the cache pass,
-    # the training step beside the next frame's path tracing; the dominant kernel is taken from the rest
-    spans = set()
-    if getattr(args, "overlap_records", 0):
-        spans.add("train_records")
-    if getattr(args, "pipeline_trace", 0):
-        spans |= {"train_fwd", "train_bwd", "train_gradw", "adam"}
-    dominant = max((k for k in kernel_ms if k not in spans), key=lambda k: timing[k][0])
+    dominant = dominant_class(timing, args)
     launches = sum(v[1] for v in timing.values()) + args.steps  # library kernels + one MRSE launch per step
     sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     roofline = _roofline(args, cfg, props, kernel_ms, dominant, sm_max, res["total_ms"] / 1e3)
